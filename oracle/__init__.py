@@ -1,0 +1,209 @@
+"""FP64 CPU oracle of the GMNN energy, forces, virial and parameter gradient.
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the benchmark's
+CPU-baseline / reference leg may import this package.  The GPU library never does, and
+this package never imports the GPU library.
+
+``gm_oracle.c`` is the oracle proper (plain loops, FP64, OpenMP over atoms, built with
+-ffp-contract=off); ``torch_ref.py`` is an independent restatement in PyTorch FP64 whose
+derivatives come from autograd and which cross-checks the hand-derived chain rules.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from pathlib import Path
+
+import numpy as np
+
+HERE = Path(__file__).resolve().parent
+SRC = HERE / "gm_oracle.c"
+LIB = HERE / "liboracle.so"
+
+_lib = None
+
+
+def build(force: bool = False) -> Path:
+    """Compile the oracle into oracle/liboracle.so (gcc, OpenMP, no FP contraction)."""
+    if LIB.exists() and not force and LIB.stat().st_mtime >= SRC.stat().st_mtime:
+        return LIB
+    cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fPIC", "-shared", "-fopenmp",
+           "-ffp-contract=off", "-fno-fast-math", "-o", str(LIB), str(SRC), "-lm"]
+    subprocess.run(cmd, check=True)
+    return LIB
+
+
+class _Model(ctypes.Structure):
+    _fields_ = [("n_species", ctypes.c_int), ("n_basis", ctypes.c_int), ("n_radial", ctypes.c_int),
+                ("n_hidden", ctypes.c_int), ("activation", ctypes.c_int),
+                ("r_min", ctypes.c_double), ("r_cut", ctypes.c_double)] + \
+               [(k, ctypes.POINTER(ctypes.c_double)) for k in
+                ("beta", "W1", "b1", "W2", "b2", "w3", "b3", "sigma", "mu")]
+
+
+class _Grad(ctypes.Structure):
+    _fields_ = [(k, ctypes.POINTER(ctypes.c_double)) for k in
+                ("beta", "W1", "b1", "W2", "b2", "w3", "b3", "sigma", "mu")]
+
+
+PARAM_NAMES = ("beta", "W1", "b1", "W2", "b2", "w3", "b3", "sigma", "mu")
+ACTIVATIONS = {"tanh": 0, "silu": 1}
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        _lib = ctypes.CDLL(str(LIB))
+        _lib.or_neighbors.restype = ctypes.c_int
+        _lib.or_energy_forces.restype = ctypes.c_int
+        _lib.or_param_grad.restype = ctypes.c_int
+        _lib.or_loss.restype = ctypes.c_double
+        _lib.or_feature_table.restype = ctypes.c_int
+        _lib.or_num_threads.restype = ctypes.c_int
+    return _lib
+
+
+def _p(a, ct=ctypes.c_double):
+    return a.ctypes.data_as(ctypes.POINTER(ct)) if a is not None else None
+
+
+def _model(desc, params, keep):
+    arrs = {k: np.ascontiguousarray(params[k], np.float64) for k in PARAM_NAMES}
+    keep.extend(arrs.values())
+    return _Model(int(desc["n_species"]), int(desc.get("n_basis", 7)), int(desc.get("n_radial", 5)),
+                  int(desc["n_hidden"]), ACTIVATIONS[desc.get("activation", "silu")],
+                  float(desc.get("r_min", 0.5)), float(desc["r_cut"]),
+                  *[_p(arrs[k]) for k in PARAM_NAMES])
+
+
+class NeighborList:
+    """CSR neighbour list: row_ptr int64 [N+1], col int32 [P], shift int32 [P, 3]."""
+
+    def __init__(self, row_ptr, col, shift):
+        self.row_ptr, self.col, self.shift = row_ptr, col, shift
+
+    @property
+    def n_pairs(self):
+        return int(self.row_ptr[-1])
+
+    def triples(self):
+        """Pairs as an int64 [P, 5] array (i, j, n0, n1, n2), sorted lexicographically."""
+        n = len(self.row_ptr) - 1
+        i = np.repeat(np.arange(n, dtype=np.int64), np.diff(self.row_ptr))
+        t = np.column_stack([i, self.col.astype(np.int64), self.shift.astype(np.int64)])
+        order = np.lexsort(t.T[::-1])
+        return t[order]
+
+
+def neighbors(batch, r_cut, capacity=None) -> NeighborList:
+    """Brute-force O(N^2 x images) neighbour list (FP64, strict r < r_cut)."""
+    L = lib()
+    pos = np.ascontiguousarray(batch.pos, np.float64)
+    cell = np.ascontiguousarray(batch.cell, np.float64).reshape(-1, 9)
+    pbc = np.ascontiguousarray(batch.pbc, np.uint8)
+    ap = np.ascontiguousarray(batch.atom_ptr, np.int32)
+    cap = capacity or max(1024, 200 * batch.n_atoms)
+    while True:
+        pi = np.empty(cap, np.int32)
+        pj = np.empty(cap, np.int32)
+        ps = np.empty((cap, 3), np.int32)
+        n = ctypes.c_int64(0)
+        rc = L.or_neighbors(ctypes.c_int(batch.n_structures), _p(ap, ctypes.c_int), _p(pos), _p(cell),
+                            _p(pbc, ctypes.c_ubyte), ctypes.c_double(r_cut), ctypes.c_int64(cap),
+                            _p(pi, ctypes.c_int), _p(pj, ctypes.c_int), _p(ps, ctypes.c_int), ctypes.byref(n))
+        if rc == 0:
+            break
+        cap = int(n.value) + 16
+    P = int(n.value)
+    counts = np.bincount(pi[:P], minlength=batch.n_atoms)
+    row_ptr = np.zeros(batch.n_atoms + 1, np.int64)
+    row_ptr[1:] = np.cumsum(counts)
+    return NeighborList(row_ptr, np.ascontiguousarray(pj[:P]), np.ascontiguousarray(ps[:P]))
+
+
+def energy_forces(batch, desc, params, nl: NeighborList, virial=True, psi=False, features=False):
+    """Energies (per structure and per atom), forces, virials and optional intermediates."""
+    L = lib()
+    keep = []
+    m = _model(desc, params, keep)
+    N, B = batch.n_atoms, batch.n_structures
+    nr = int(desc.get("n_radial", 5))
+    nf = L.or_feature_table(ctypes.c_int(nr), None, None)
+    out = {"E": np.zeros(B), "E_atom": np.zeros(N), "F": np.zeros((N, 3))}
+    out["virial"] = np.zeros((B, 3, 3)) if virial else None
+    out["psi"] = np.zeros((N, nr, 20)) if psi else None
+    out["G"] = np.zeros((N, nf)) if features else None
+    pos = np.ascontiguousarray(batch.pos, np.float64)
+    cell = np.ascontiguousarray(batch.cell, np.float64).reshape(-1, 9)
+    spec = np.ascontiguousarray(batch.species, np.int32)
+    ap = np.ascontiguousarray(batch.atom_ptr, np.int32)
+    rp = np.ascontiguousarray(nl.row_ptr, np.int64)
+    col = np.ascontiguousarray(nl.col, np.int32)
+    sh = np.ascontiguousarray(nl.shift, np.int32)
+    rc = L.or_energy_forces(ctypes.byref(m), ctypes.c_int(B), _p(ap, ctypes.c_int), _p(pos),
+                            _p(spec, ctypes.c_int), _p(cell), _p(rp, ctypes.c_int64), _p(col, ctypes.c_int),
+                            _p(sh, ctypes.c_int), _p(out["E"]), _p(out["E_atom"]), _p(out["F"]),
+                            _p(out["virial"]), _p(out["psi"]), _p(out["G"]))
+    if rc != 0:
+        raise RuntimeError(f"or_energy_forces failed ({rc})")
+    return out
+
+
+def loss(batch, E, E_ref, F, F_ref, wE=1.0, wF=1.0):
+    """Force-matching loss and its gradients (gE [B], gF [N, 3])."""
+    L = lib()
+    ap = np.ascontiguousarray(batch.atom_ptr, np.int32)
+    gE = np.zeros(batch.n_structures)
+    gF = np.zeros((batch.n_atoms, 3))
+    arrs = [np.ascontiguousarray(a, np.float64) for a in (E, E_ref, F, F_ref)]
+    val = L.or_loss(ctypes.c_int(batch.n_structures), _p(ap, ctypes.c_int), *[_p(a) for a in arrs],
+                    ctypes.c_double(wE), ctypes.c_double(wF), _p(gE), _p(gF))
+    return val, gE, gF
+
+
+def param_grad(batch, desc, params, nl: NeighborList, gE, gF):
+    """d/dtheta of sum_b gE_b E_b + sum_i gF_i . F_i, as a dict of named arrays."""
+    L = lib()
+    keep = []
+    m = _model(desc, params, keep)
+    grads = {k: np.zeros_like(np.asarray(params[k], np.float64)) for k in PARAM_NAMES}
+    g = _Grad(*[_p(grads[k]) for k in PARAM_NAMES])
+    pos = np.ascontiguousarray(batch.pos, np.float64)
+    cell = np.ascontiguousarray(batch.cell, np.float64).reshape(-1, 9)
+    spec = np.ascontiguousarray(batch.species, np.int32)
+    ap = np.ascontiguousarray(batch.atom_ptr, np.int32)
+    rp = np.ascontiguousarray(nl.row_ptr, np.int64)
+    col = np.ascontiguousarray(nl.col, np.int32)
+    sh = np.ascontiguousarray(nl.shift, np.int32)
+    gE = np.ascontiguousarray(gE, np.float64)
+    gF = np.ascontiguousarray(gF, np.float64).reshape(-1, 3)
+    rc = L.or_param_grad(ctypes.byref(m), ctypes.c_int(batch.n_structures), _p(ap, ctypes.c_int), _p(pos),
+                         _p(spec, ctypes.c_int), _p(cell), _p(rp, ctypes.c_int64), _p(col, ctypes.c_int),
+                         _p(sh, ctypes.c_int), _p(gE), _p(gF), ctypes.byref(g))
+    if rc != 0:
+        raise RuntimeError(f"or_param_grad failed ({rc})")
+    return grads
+
+
+def feature_table(n_radial=5):
+    """(family [F], tensor-state offsets [F, 3]) of the contraction features."""
+    L = lib()
+    nf = L.or_feature_table(ctypes.c_int(n_radial), None, None)
+    fam = np.zeros(nf, np.int32)
+    off = np.zeros((nf, 3), np.int32)
+    L.or_feature_table(ctypes.c_int(n_radial), _p(fam, ctypes.c_int), _p(off, ctypes.c_int))
+    return fam, off
+
+
+def num_threads():
+    return int(lib().or_num_threads())
+
+
+def omp_env(threads: int | None):
+    """Environment for a child process that should use ``threads`` OpenMP threads."""
+    env = dict(os.environ)
+    if threads:
+        env["OMP_NUM_THREADS"] = str(threads)
+    return env

@@ -1,0 +1,64 @@
+"""Seeded synthetic GMNN parameters (no trained weights exist here).
+
+Only random draws happen here: shapes follow the model (species-pair coefficients,
+two hidden layers, linear output, per-species scale and shift), scales follow common
+initialisations.  Returned as a dict of named float64 arrays; each side (oracle, GPU
+binding) packs them its own way.
+
+    beta  [S, S, n_radial, n_basis]  ~ N(0, (24 / nbar)^2)   (rank-0 moments ~ O(1),
+                                     so that all eight contraction families contribute)
+    W1    [n_features, H]            Xavier normal
+    b1    [H]                        ~ N(0, 0.1^2)
+    W2    [H, H]                     Xavier normal
+    b2    [H]                        ~ N(0, 0.1^2)
+    w3    [H]                        Xavier normal (fan_out 1)
+    b3    [1]                        ~ N(0, 0.1^2)
+    sigma [S]                        ~ U(0.5, 1.5)
+    mu    [S]                        ~ N(0, 1)
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+N_FEATURES = 360
+BETA_SCALE = 24.0
+
+
+def param_shapes(n_species: int, n_hidden: int, n_radial=5, n_basis=7, n_features=N_FEATURES):
+    S, H = n_species, n_hidden
+    return {
+        "beta": (S, S, n_radial, n_basis),
+        "W1": (n_features, H),
+        "b1": (H,),
+        "W2": (H, H),
+        "b2": (H,),
+        "w3": (H,),
+        "b3": (1,),
+        "sigma": (S,),
+        "mu": (S,),
+    }
+
+
+def make_params(n_species: int, n_hidden: int, seed: int, nbar: float,
+                n_radial=5, n_basis=7, n_features=N_FEATURES):
+    rng = np.random.default_rng([seed, 41])
+    sh = param_shapes(n_species, n_hidden, n_radial, n_basis, n_features)
+
+    def xavier(fan_in, fan_out, shape):
+        return rng.normal(0.0, math.sqrt(2.0 / (fan_in + fan_out)), shape)
+
+    H = n_hidden
+    p = {
+        "beta": rng.normal(0.0, BETA_SCALE / nbar, sh["beta"]),
+        "W1": xavier(n_features, H, sh["W1"]),
+        "b1": rng.normal(0.0, 0.1, sh["b1"]),
+        "W2": xavier(H, H, sh["W2"]),
+        "b2": rng.normal(0.0, 0.1, sh["b2"]),
+        "w3": xavier(H, 1, sh["w3"]),
+        "b3": rng.normal(0.0, 0.1, sh["b3"]),
+        "sigma": rng.uniform(0.5, 1.5, sh["sigma"]),
+        "mu": rng.normal(0.0, 1.0, sh["mu"]),
+    }
+    return {k: np.ascontiguousarray(v, dtype=np.float64) for k, v in p.items()}
