@@ -1,0 +1,181 @@
+/*
+ * gm.h -- C ABI of libgm: Gaussian Moment Neural Network (GMNN) energies, forces and
+ * force-matching parameter gradients on an NVIDIA B300 (sm_103a).
+ *
+ * The model (paper: "Apax", section "Machine Learning Interatomic Potentials"):
+ *   E(S)         = sum_i E_i                                     Eq. energy_sum
+ *   Psi_{i,L,s}  = sum_{j != i} R_{Zi,Zj,s}(r_ij) rhat_ij^{(x)L}  Eq. basis_fn, L = 0..3
+ *   G_i          = full tensor contractions of Psi_i             Eq. contraction
+ *   E_i          = sigma_{Zi} NN(G_i) + mu_{Zi}                  Eq. scale_shift
+ *   F_i          = -dE/dr_i, virial = -dE/d(strain)              (forces and virials as
+ *                                                                 gradients, section
+ *                                                                 "Model Abstractions")
+ * Readings where the paper is silent:
+ *   radial basis  Phi_k(r) = exp(-gamma (r - mu_k)^2), mu_k = r_min + k (r_cut - r_min)/(n_basis-1),
+ *                 gamma = n_basis^2 / r_cut^2 ("equidistant Gaussians")
+ *   cutoff        f_c(r) = (cos(pi r / r_cut) + 1)/2 for r < r_cut
+ *   radial fns    R_s(r) = f_c(r) n_basis^{-1/2} sum_k beta[Zi][Zj][s][k] Phi_k(r), ordered pair
+ *   features      360 invariants in 8 families (Psi0; Psi1.Psi1; Psi2:Psi2; Psi3:Psi3;
+ *                 tr Psi2 Psi2 Psi2; Psi1 Psi2 Psi1; Psi3 Psi3 Psi2; Psi1 Psi3 Psi2), each
+ *                 with its radial-index symmetry removed, family-major, lexicographic in
+ *                 (s1, s2, s3)
+ *   network       NN = w3 . phi(W2^T phi(W1^T G + b1) + b2) + b3, phi = tanh or SiLU
+ *   neighbours    all (i, j, n) with |r'_j - r'_i + n.cell| < r_cut, except (j == i, n == 0);
+ *                 periodic self-images count; r' are positions wrapped into the cell
+ *
+ * Conventions (every entry point):
+ *   - Units: Angstrom and eV.  Energies and virials FP64; forces FP32 (eV/A).
+ *   - The caller owns every buffer.  Entry points never allocate or free memory, except
+ *     gm_model_create / gm_model_destroy, which own the model's repacked weight copies.
+ *   - Device pointers are CUDA global memory of the current device.  All work is
+ *     enqueued on `stream` (a cudaStream_t, passed as struct CUstream_st*); calls do not
+ *     synchronise the host.
+ *   - The synchronous return value reports argument, shape and launch errors only.
+ *     Conditions found on the device are written to *status_dev (an int32 the caller
+ *     zeroes before a step): the first error wins; later kernels of the same step see a
+ *     non-zero status and skip their work.  The caller reads it after synchronising.
+ *   - Version 1 supports orthorhombic, fully periodic cells, n_basis = 7, n_radial = 5
+ *     and 64 <= n_hidden <= 512 with n_hidden % 64 == 0; anything else returns
+ *     GM_ERR_UNSUPPORTED (host-detectable) or writes it to *status_dev (cell shape).
+ */
+#ifndef GM_H
+#define GM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st; /* cudaStream_t is struct CUstream_st* */
+
+typedef enum {
+    GM_OK = 0,
+    GM_ERR_ARG = 1,         /* NULL pointer, bad size or misaligned pointer */
+    GM_ERR_CAPACITY = 2,    /* neighbour list needs more than nl->capacity pairs */
+    GM_ERR_UNSUPPORTED = 3, /* configuration outside version 1 (see above) */
+    GM_ERR_CUDA = 4,        /* a CUDA runtime call or kernel launch failed */
+    GM_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+    GM_ERR_SPECIES = 6,     /* a species index outside [0, n_species) */
+    GM_ERR_WORKSPACE = 7    /* ws_bytes smaller than gm_workspace_size() */
+} gm_status;
+
+typedef enum { GM_ACT_TANH = 0, GM_ACT_SILU = 1 } gm_activation;
+
+typedef enum {
+    GM_PREC_FP32 = 0,  /* moments, contractions and network in FP32 (FFMA) */
+    GM_PREC_MIXED = 1  /* network GEMMs in BF16 on tcgen05 tensor cores with FP32
+                          accumulation; everything else as GM_PREC_FP32 */
+} gm_precision;
+
+typedef struct {
+    int32_t n_species;  /* S, 1..16 */
+    int32_t n_basis;    /* radial basis functions (7) */
+    int32_t n_radial;   /* radial functions (5, giving 360 features) */
+    int32_t n_hidden;   /* H, width of both hidden layers */
+    int32_t activation; /* gm_activation */
+    int32_t precision;  /* gm_precision */
+    double r_min;       /* first Gaussian centre (A) */
+    double r_cut;       /* cutoff radius (A) */
+} gm_model_desc;
+
+typedef struct gm_model gm_model; /* opaque */
+
+/* A batch of B periodic structures, N atoms in total (ragged, no padding). */
+typedef struct {
+    int32_t n_structures;     /* B >= 1 */
+    int32_t n_atoms;          /* N >= 0 */
+    const int32_t *atom_ptr;  /* device [B+1]; structure b owns atoms atom_ptr[b]..atom_ptr[b+1]-1 */
+    const double *pos;        /* device [N][3] Cartesian positions (any image) */
+    const int32_t *species;   /* device [N], 0 <= species < n_species */
+    const double *cell;       /* device [B][3][3], rows are lattice vectors */
+    const uint8_t *pbc;       /* device [B][3] periodic flags (version 1: all 1) */
+} gm_system;
+
+/* CSR neighbour list over the batch's global atom indices.  Within row i the pairs are
+ * ordered by stencil cell, then by neighbour index (deterministic). */
+typedef struct {
+    int64_t capacity;   /* entries available in col and shift */
+    int32_t *row_ptr;   /* device [N+1] */
+    int32_t *col;       /* device [capacity]: neighbour atom j */
+    int8_t *shift;      /* device [capacity][4]: (n0, n1, n2, 0); the displacement is
+                           r_j - r_i + n0 a + n1 b + n2 c with the caller's positions */
+    int64_t *n_pairs;   /* device scalar: number of pairs found (also set on overflow) */
+} gm_nlist;
+
+/* Workspace kinds for gm_workspace_size. */
+enum { GM_OP_NEIGHBORS = 0, GM_OP_ENERGY_FORCES = 1, GM_OP_PARAM_GRAD = 2 };
+
+/* Number of FP32 parameters.  Flat layout of theta, in this order:
+ *   beta[S][S][n_radial][n_basis], W1[360][H], b1[H], W2[H][H], b2[H], w3[H], b3[1],
+ *   sigma[S], mu[S]   (row-major; W1 maps features to the first hidden layer). */
+int64_t gm_param_count(const gm_model_desc *desc);
+
+/* Create a model handle (allocates its device weight copies on the current device).
+ * Errors: GM_ERR_ARG, GM_ERR_UNSUPPORTED, GM_ERR_CUDA. */
+gm_status gm_model_create(const gm_model_desc *desc, gm_model **out);
+
+/* Copy theta (device, FP32, gm_param_count entries, layout above) into the model and
+ * repack the network weights for the kernels (transposed and padded, FP32 and BF16).
+ * Asynchronous on `stream`; theta may be reused once the stream reaches this point. */
+gm_status gm_model_set_params(gm_model *m, const float *theta_dev, struct CUstream_st *stream);
+
+void gm_model_destroy(gm_model *m);
+
+/* Bytes of workspace an operation needs (op = GM_OP_*).  nl_capacity is the neighbour
+ * list capacity the caller will pass.  Errors: GM_ERR_ARG. */
+gm_status gm_workspace_size(const gm_model *m, int32_t n_structures, int32_t n_atoms,
+                            int64_t nl_capacity, int32_t op, size_t *bytes);
+
+/* Neighbour search (cell list, FP32 distance filter with an exact FP64 decision near the
+ * cutoff).  Paper: neighbour lists within the cutoff including multiple periodic images
+ * for small cells (section "Deployment").  Writes nl->row_ptr, nl->col, nl->shift and
+ * *nl->n_pairs.  If more than nl->capacity pairs exist, writes GM_ERR_CAPACITY to
+ * *status_dev, the required count to *nl->n_pairs, and leaves col/shift unwritten. */
+gm_status gm_build_neighbors(const gm_model *m, const gm_system *sys, gm_nlist *nl, void *ws,
+                             size_t ws_bytes, int32_t *status_dev, struct CUstream_st *stream);
+
+/* Energies and forces (Eqs. energy_sum, basis_fn, contraction, scale_shift; F = -dE/dr).
+ *   energy  device [B] FP64, overwritten
+ *   forces  device [N][3] FP32, overwritten
+ *   virial  device [B][9] FP64 (-dE/d strain, row-major), overwritten; may be NULL
+ * The neighbour list must describe sys (as written by gm_build_neighbors or equivalent). */
+gm_status gm_energy_forces(const gm_model *m, const gm_system *sys, const gm_nlist *nl, double *energy,
+                           float *forces, double *virial, void *ws, size_t ws_bytes, int32_t *status_dev,
+                           struct CUstream_st *stream);
+
+/* Parameter gradient of a loss through energies and forces:
+ *   grad_theta = d/dtheta [ sum_b dL_dE[b] E_b + sum_i dL_dF[i] . F_i ]
+ * (section "Training": loss terms on energies and forces).  dL_dE device [B] FP64,
+ * dL_dF device [N][3] FP32, grad_theta device [gm_param_count] FP32, overwritten.
+ * Moments are recomputed from the positions; no per-pair state is stored. */
+gm_status gm_param_grad(const gm_model *m, const gm_system *sys, const gm_nlist *nl, const double *dL_dE,
+                        const float *dL_dF, float *grad_theta, void *ws, size_t ws_bytes,
+                        int32_t *status_dev, struct CUstream_st *stream);
+
+/* Force-matching loss L = wE/B sum_b ((E_b - E_ref_b)/N_b)^2 + wF/(3N) sum_i |F_i - F_ref_i|^2
+ * and its gradients (section "Training": weighted energy and force terms, per-atom
+ * division).  loss device scalar FP64; dL_dE device [B] FP64; dL_dF device [N][3] FP32. */
+gm_status gm_force_matching_loss(const gm_system *sys, const double *energy, const double *energy_ref,
+                                 const float *forces, const float *forces_ref, double w_energy,
+                                 double w_forces, double *loss, double *dL_dE, float *dL_dF,
+                                 int32_t *status_dev, struct CUstream_st *stream);
+
+/* Diagnostics: the descriptor of every atom.  psi device [N][n_radial][20] FP32 (unique
+ * moment components per radial function: rank 0; x y z; xx xy xz yy yz zz; xxx xxy xxz
+ * xyy xyz xzz yyy yyz yzz zzz), features device [N][360] FP32 (may be NULL).
+ * Workspace as GM_OP_ENERGY_FORCES. */
+gm_status gm_descriptors(const gm_model *m, const gm_system *sys, const gm_nlist *nl, float *psi,
+                         float *features, void *ws, size_t ws_bytes, int32_t *status_dev,
+                         struct CUstream_st *stream);
+
+const char *gm_status_string(gm_status s);
+
+/* Detail of the last synchronous error on the calling thread ("" if none). */
+const char *gm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GM_H */

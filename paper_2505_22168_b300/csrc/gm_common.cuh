@@ -1,0 +1,209 @@
+// gm_common.cuh -- shared definitions of the libgm CUDA kernels (sm_103a).
+//
+// Moments are stored per atom as [n_radial = 5][20] FP32 unique components of the
+// symmetric tensors Psi_{L,s} (Eq. basis_fn), L = 0..3:
+//   c = 0        rank 0
+//   c = 1..3     x y z
+//   c = 4..9     xx xy xz yy yz zz
+//   c = 10..19   xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz
+// Component c of rank L is the monomial ux^nx uy^ny uz^nz (nx+ny+nz = L) summed over
+// neighbours with weight R_s.  A full-tensor entry Psi[a][b][c] equals the unique
+// component with the same exponents, so full-tensor formulas read and write unique
+// registers through idx2/idx3 (writes into the unique adjoint sum all permutations,
+// which is exactly the gradient with respect to the unique component).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace gm {
+
+constexpr int NR = 5;            // radial functions
+constexpr int NB = 7;            // radial basis functions
+constexpr int NC = 20;           // unique moment components per radial function
+constexpr int NPSI = NR * NC;    // 100 moment values per atom
+constexpr int NF = 360;          // invariant features (Eq. contraction, 8 families)
+constexpr int NFP = 384;         // features padded to a multiple of 64
+constexpr int MAX_S = 16;        // species
+constexpr int TILE_M = 128;      // atom rows per GEMM tile
+
+// exponent code nx*16 + ny*4 + nz of unique component c
+__host__ __device__ constexpr int comp_code(int c) {
+    switch (c) {
+    case 0: return 0;
+    case 1: return 16; case 2: return 4; case 3: return 1;
+    case 4: return 32; case 5: return 20; case 6: return 17; case 7: return 8; case 8: return 5;
+    case 9: return 2;
+    case 10: return 48; case 11: return 36; case 12: return 33; case 13: return 24; case 14: return 21;
+    case 15: return 18; case 16: return 12; case 17: return 9; case 18: return 6;
+    default: return 3;
+    }
+}
+__host__ __device__ constexpr int comp_nx(int c) { return comp_code(c) >> 4; }
+__host__ __device__ constexpr int comp_ny(int c) { return (comp_code(c) >> 2) & 3; }
+__host__ __device__ constexpr int comp_nz(int c) { return comp_code(c) & 3; }
+__host__ __device__ constexpr int comp_rank(int c) { return c == 0 ? 0 : (c < 4 ? 1 : (c < 10 ? 2 : 3)); }
+
+__host__ __device__ constexpr int code_to_comp(int code) {
+    switch (code) {
+    case 0: return 0;
+    case 16: return 1; case 4: return 2; case 1: return 3;
+    case 32: return 4; case 20: return 5; case 17: return 6; case 8: return 7; case 5: return 8;
+    case 2: return 9;
+    case 48: return 10; case 36: return 11; case 33: return 12; case 24: return 13; case 21: return 14;
+    case 18: return 15; case 12: return 16; case 9: return 17; case 6: return 18;
+    default: return 19;
+    }
+}
+__host__ __device__ constexpr int axis_code(int a) { return a == 0 ? 16 : (a == 1 ? 4 : 1); }
+// unique index of full rank-1/2/3 entries
+__host__ __device__ constexpr int idx1(int a) { return 1 + a; }
+__host__ __device__ constexpr int idx2(int a, int b) { return code_to_comp(axis_code(a) + axis_code(b)); }
+__host__ __device__ constexpr int idx3(int a, int b, int c) {
+    return code_to_comp(axis_code(a) + axis_code(b) + axis_code(c));
+}
+
+// ---------------------------------------------------------------- feature indexing
+// Family-major; within a family lexicographic in (s1, s2, s3) subject to:
+//   #1 s;  #2,#3,#4 s1<=s2;  #5 s1<=s2<=s3;  #6 s1<=s3;  #7 s1<=s2;  #8 free.
+constexpr int FAM_OFF1 = 0, FAM_OFF2 = 5, FAM_OFF3 = 20, FAM_OFF4 = 35, FAM_OFF5 = 50,
+              FAM_OFF6 = 85, FAM_OFF7 = 160, FAM_OFF8 = 235;
+
+__host__ __device__ constexpr int pair_le_index(int s1, int s2) {  // s1 <= s2
+    int n = 0;
+    for (int a = 0; a < NR; ++a)
+        for (int b = a; b < NR; ++b) {
+            if (a == s1 && b == s2) return n;
+            ++n;
+        }
+    return -1;
+}
+__host__ __device__ constexpr int f5_index(int s1, int s2, int s3) {  // s1<=s2<=s3
+    int n = 0;
+    for (int a = 0; a < NR; ++a)
+        for (int b = a; b < NR; ++b)
+            for (int c = b; c < NR; ++c) {
+                if (a == s1 && b == s2 && c == s3) return n;
+                ++n;
+            }
+    return -1;
+}
+__host__ __device__ constexpr int f6_index(int s1, int s2, int s3) {  // s1<=s3
+    int n = 0;
+    for (int a = 0; a < NR; ++a)
+        for (int b = 0; b < NR; ++b)
+            for (int c = a; c < NR; ++c) {
+                if (a == s1 && b == s2 && c == s3) return n;
+                ++n;
+            }
+    return -1;
+}
+__host__ __device__ constexpr int f7_index(int s1, int s2, int s3) {  // s1<=s2
+    int n = 0;
+    for (int a = 0; a < NR; ++a)
+        for (int b = a; b < NR; ++b)
+            for (int c = 0; c < NR; ++c) {
+                if (a == s1 && b == s2 && c == s3) return n;
+                ++n;
+            }
+    return -1;
+}
+__host__ __device__ constexpr int f8_index(int s1, int s2, int s3) { return (s1 * NR + s2) * NR + s3; }
+
+// ---------------------------------------------------------------- status word
+__device__ __forceinline__ void set_status(int32_t *st, int32_t code) {
+    if (st) atomicCAS(st, 0, code);
+}
+__device__ __forceinline__ bool status_bad(const int32_t *st) {
+    return st && *reinterpret_cast<const volatile int32_t *>(st) != 0;
+}
+
+// structure index of atom i: largest b with atom_ptr[b] <= i
+__device__ __forceinline__ int structure_of(const int32_t *__restrict__ atom_ptr, int n_struct, int i) {
+    int lo = 0, hi = n_struct - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(atom_ptr + mid) <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------- activations
+// ACT: 0 = tanh, 1 = SiLU.  Returns phi(z); d1 = phi'(z).
+template <int ACT>
+__device__ __forceinline__ float act_fwd(float z, float &d1) {
+    if (ACT == 0) {
+        float t = tanhf(z);
+        d1 = 1.0f - t * t;
+        return t;
+    } else {
+        float s = 1.0f / (1.0f + expf(-z));
+        d1 = s * (1.0f + z * (1.0f - s));
+        return z * s;
+    }
+}
+// phi, phi', phi'' (parameter-gradient tangent pass)
+template <int ACT>
+__device__ __forceinline__ float act_fwd2(float z, float &d1, float &d2) {
+    if (ACT == 0) {
+        float t = tanhf(z);
+        d1 = 1.0f - t * t;
+        d2 = -2.0f * t * d1;
+        return t;
+    } else {
+        float s = 1.0f / (1.0f + expf(-z));
+        d1 = s * (1.0f + z * (1.0f - s));
+        d2 = s * (1.0f - s) * (2.0f + z * (1.0f - 2.0f * s));
+        return z * s;
+    }
+}
+
+// ---------------------------------------------------------------- radial part
+// Model constants the pair kernels need (beta is pre-scaled by n_basis^{-1/2}).
+struct RadialConst {
+    float r_cut, inv_r_cut, gamma;
+    float mu[NB];
+};
+
+// f_c Phi_k (B) and optionally its r-derivative (dB) for the 7 Gaussians.
+template <bool DERIV>
+__device__ __forceinline__ void radial_basis(const RadialConst &rc, float r, float (&B)[NB], float (&dB)[NB]) {
+    float sp, cp;
+    sincospif(r * rc.inv_r_cut, &sp, &cp);
+    const bool inside = r < rc.r_cut;
+    const float fc = inside ? 0.5f * (cp + 1.0f) : 0.0f;
+    const float dfc = inside ? -0.5f * 3.14159265358979323846f * rc.inv_r_cut * sp : 0.0f;
+#pragma unroll
+    for (int k = 0; k < NB; ++k) {
+        const float t = r - rc.mu[k];
+        const float ph = expf(-rc.gamma * t * t);
+        B[k] = fc * ph;
+        if (DERIV) dB[k] = dfc * ph - 2.0f * rc.gamma * t * ph * fc;
+    }
+}
+
+// the 20 monomials m_c(u) of the unit vector
+__device__ __forceinline__ void monomials(float ux, float uy, float uz, float (&m)[NC]) {
+    const float xx = ux * ux, yy = uy * uy, zz = uz * uz;
+    m[0] = 1.0f;
+    m[1] = ux; m[2] = uy; m[3] = uz;
+    m[4] = xx; m[5] = ux * uy; m[6] = ux * uz; m[7] = yy; m[8] = uy * uz; m[9] = zz;
+    m[10] = xx * ux; m[11] = xx * uy; m[12] = xx * uz; m[13] = ux * yy; m[14] = ux * uy * uz;
+    m[15] = ux * zz; m[16] = yy * uy; m[17] = yy * uz; m[18] = uy * zz; m[19] = zz * uz;
+}
+
+// integer power for small exponents
+__device__ __forceinline__ float ipow(float x, int n) {
+    return n == 0 ? 1.0f : (n == 1 ? x : (n == 2 ? x * x : x * x * x));
+}
+
+// d m_c / d u_axis (axis 0, 1, 2); with constant c and axis it folds to a product
+__device__ __forceinline__ float dmono(int c, int axis, float ux, float uy, float uz) {
+    const int nx = comp_nx(c), ny = comp_ny(c), nz = comp_nz(c);
+    if (axis == 0) return nx == 0 ? 0.0f : nx * ipow(ux, nx - 1) * ipow(uy, ny) * ipow(uz, nz);
+    if (axis == 1) return ny == 0 ? 0.0f : ny * ipow(ux, nx) * ipow(uy, ny - 1) * ipow(uz, nz);
+    return nz == 0 ? 0.0f : nz * ipow(ux, nx) * ipow(uy, ny) * ipow(uz, nz - 1);
+}
+
+}  // namespace gm

@@ -1,0 +1,242 @@
+// gm_pair.cu -- per-pair kernels: Gaussian moments (Eq. basis_fn) and forces.
+//
+// One group of TPA lanes per centre atom i walks i's CSR row; lanes take every TPA-th
+// neighbour, so a warp covers 32/TPA atoms.  Per pair: the minimum-image displacement
+// d = (r_j - r_i) + n.L is formed in FP64 and rounded to FP32; everything after that
+// (r, rhat, basis, radial functions, monomials) is FP32.
+//
+// Moments:  Psi_i[s][c] = sum_j R_s(r_ij) m_c(rhat_ij)  (unique components m_c, see
+//           gm_common.cuh), reduced across the TPA lanes with warp shuffles.
+// Forces:   given g_i[s][c] = dE/dPsi_i[s][c], the pair gradient is
+//              dE/dd_b = u_b (sum_c A'_c m_c - (1/r) sum_c L_c A_c m_c) + (1/r) sum_c A_c dm_c/du_b
+//           with A_c = sum_s g[s][c] R_s and A'_c = sum_s g[s][c] R'_s (using Euler's
+//           relation sum_a u_a dm_c/du_a = L_c m_c for the tangential projection).
+//           F_i += dE/dd_ij and F_j -= dE/dd_ij (float atomics for the j side), and the
+//           per-atom virial -d (x) dE/dd is accumulated for an FP64 per-structure sum.
+#include "gm_internal.h"
+#include "gm_pair.h"
+
+namespace gm {
+
+__device__ __forceinline__ int clamp_species(int z, int S, int32_t *status) {
+    if (z < 0 || z >= S) {
+        set_status(status, GM_ERR_SPECIES);
+        return z < 0 ? 0 : S - 1;
+    }
+    return z;
+}
+
+__device__ __forceinline__ void pair_displacement(const double *__restrict__ pos, double xi, double yi, double zi,
+                                                  int j, char4 sh, double Lx, double Ly, double Lz, float &fx,
+                                                  float &fy, float &fz) {
+    const double dx = (pos[3 * j] - xi) + (double)sh.x * Lx;
+    const double dy = (pos[3 * j + 1] - yi) + (double)sh.y * Ly;
+    const double dz = (pos[3 * j + 2] - zi) + (double)sh.z * Lz;
+    fx = (float)dx;
+    fy = (float)dy;
+    fz = (float)dz;
+}
+
+template <int TPA>
+__global__ void __launch_bounds__(256) k_moments(PairArgs a, float *__restrict__ psi) {
+    extern __shared__ float sbeta[];
+    const int nbeta = a.S * a.S * NR * NB;
+    for (int q = threadIdx.x; q < nbeta; q += blockDim.x) sbeta[q] = a.beta[q];
+    __syncthreads();
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int atom = g / TPA, sub = g % TPA;
+    const bool active = atom < a.N;
+    float acc[NPSI];
+#pragma unroll
+    for (int q = 0; q < NPSI; ++q) acc[q] = 0.0f;
+    if (active) {
+        const int b = structure_of(a.atom_ptr, a.B, atom);
+        const double Lx = a.cell[9 * b], Ly = a.cell[9 * b + 4], Lz = a.cell[9 * b + 8];
+        const double xi = a.pos[3 * atom], yi = a.pos[3 * atom + 1], zi = a.pos[3 * atom + 2];
+        const int zsi = clamp_species(a.species[atom], a.S, a.status);
+        const float *brow = sbeta + zsi * a.S * (NR * NB);
+        const int p1 = a.row_ptr[atom + 1];
+        for (int p = a.row_ptr[atom] + sub; p < p1; p += TPA) {
+            const int j = a.col[p];
+            float fx, fy, fz;
+            pair_displacement(a.pos, xi, yi, zi, j, a.shift[p], Lx, Ly, Lz, fx, fy, fz);
+            const float r = sqrtf(fx * fx + fy * fy + fz * fz);
+            const float rinv = 1.0f / r;
+            float B[NB], dB[NB];
+            radial_basis<false>(a.rc, r, B, dB);
+            const float *bt = brow + clamp_species(a.species[j], a.S, a.status) * (NR * NB);
+            float R[NR];
+#pragma unroll
+            for (int s = 0; s < NR; ++s) {
+                float v = 0.0f;
+#pragma unroll
+                for (int k = 0; k < NB; ++k) v = fmaf(bt[s * NB + k], B[k], v);
+                R[s] = v;
+            }
+            float m[NC];
+            monomials(fx * rinv, fy * rinv, fz * rinv, m);
+#pragma unroll
+            for (int s = 0; s < NR; ++s)
+#pragma unroll
+                for (int c = 0; c < NC; ++c) acc[s * NC + c] = fmaf(R[s], m[c], acc[s * NC + c]);
+        }
+    }
+    if (TPA > 1) {
+#pragma unroll
+        for (int off = TPA / 2; off > 0; off >>= 1)
+#pragma unroll
+            for (int q = 0; q < NPSI; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], off);
+    }
+    if (!active) return;
+    float *out = psi + (size_t)atom * NPSI;
+    if (TPA == 1) {
+        float4 *o4 = reinterpret_cast<float4 *>(out);
+#pragma unroll
+        for (int q = 0; q < NPSI / 4; ++q) o4[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < NPSI; ++q)
+            if (q % TPA == sub) out[q] = acc[q];
+    }
+}
+
+template <int TPA>
+__global__ void __launch_bounds__(256) k_forces(PairArgs a, const float *__restrict__ dpsi, float *__restrict__ F,
+                                                float *__restrict__ vir_atom) {
+    extern __shared__ float sbeta[];
+    const int nbeta = a.S * a.S * NR * NB;
+    for (int q = threadIdx.x; q < nbeta; q += blockDim.x) sbeta[q] = a.beta[q];
+    __syncthreads();
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int atom = gt / TPA, sub = gt % TPA;
+    const bool active = atom < a.N;
+    float Fi[3] = {0.0f, 0.0f, 0.0f};
+    float V[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) V[q] = 0.0f;
+    if (active) {
+        float g[NPSI];
+        const float4 *g4 = reinterpret_cast<const float4 *>(dpsi + (size_t)atom * NPSI);
+#pragma unroll
+        for (int q = 0; q < NPSI / 4; ++q) {
+            const float4 v = g4[q];
+            g[4 * q] = v.x; g[4 * q + 1] = v.y; g[4 * q + 2] = v.z; g[4 * q + 3] = v.w;
+        }
+        const int b = structure_of(a.atom_ptr, a.B, atom);
+        const double Lx = a.cell[9 * b], Ly = a.cell[9 * b + 4], Lz = a.cell[9 * b + 8];
+        const double xi = a.pos[3 * atom], yi = a.pos[3 * atom + 1], zi = a.pos[3 * atom + 2];
+        const int zsi = clamp_species(a.species[atom], a.S, a.status);
+        const float *brow = sbeta + zsi * a.S * (NR * NB);
+        const int p1 = a.row_ptr[atom + 1];
+        for (int p = a.row_ptr[atom] + sub; p < p1; p += TPA) {
+            const int j = a.col[p];
+            float fx, fy, fz;
+            pair_displacement(a.pos, xi, yi, zi, j, a.shift[p], Lx, Ly, Lz, fx, fy, fz);
+            const float r = sqrtf(fx * fx + fy * fy + fz * fz);
+            const float rinv = 1.0f / r;
+            const float ux = fx * rinv, uy = fy * rinv, uz = fz * rinv;
+            float B[NB], dB[NB];
+            radial_basis<true>(a.rc, r, B, dB);
+            const float *bt = brow + clamp_species(a.species[j], a.S, a.status) * (NR * NB);
+            float R[NR], Rp[NR];
+#pragma unroll
+            for (int s = 0; s < NR; ++s) {
+                float v = 0.0f, w = 0.0f;
+#pragma unroll
+                for (int k = 0; k < NB; ++k) {
+                    v = fmaf(bt[s * NB + k], B[k], v);
+                    w = fmaf(bt[s * NB + k], dB[k], w);
+                }
+                R[s] = v;
+                Rp[s] = w;
+            }
+            float m[NC];
+            monomials(ux, uy, uz, m);
+            float S1 = 0.0f, S2 = 0.0f, Q0 = 0.0f, Q1 = 0.0f, Q2 = 0.0f;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                float Ac = 0.0f, Apc = 0.0f;
+#pragma unroll
+                for (int s = 0; s < NR; ++s) {
+                    Ac = fmaf(g[s * NC + c], R[s], Ac);
+                    Apc = fmaf(g[s * NC + c], Rp[s], Apc);
+                }
+                S1 = fmaf(Apc, m[c], S1);
+                if (comp_rank(c) > 0) {
+                    S2 = fmaf((float)comp_rank(c) * Ac, m[c], S2);
+                    Q0 = fmaf(Ac, dmono(c, 0, ux, uy, uz), Q0);
+                    Q1 = fmaf(Ac, dmono(c, 1, ux, uy, uz), Q1);
+                    Q2 = fmaf(Ac, dmono(c, 2, ux, uy, uz), Q2);
+                }
+            }
+            const float radial_term = S1 - S2 * rinv;
+            const float gx = fmaf(ux, radial_term, Q0 * rinv);
+            const float gy = fmaf(uy, radial_term, Q1 * rinv);
+            const float gz = fmaf(uz, radial_term, Q2 * rinv);
+            Fi[0] += gx; Fi[1] += gy; Fi[2] += gz;
+            atomicAdd(F + 3 * j, -gx);
+            atomicAdd(F + 3 * j + 1, -gy);
+            atomicAdd(F + 3 * j + 2, -gz);
+            V[0] -= fx * gx; V[1] -= fx * gy; V[2] -= fx * gz;
+            V[3] -= fy * gx; V[4] -= fy * gy; V[5] -= fy * gz;
+            V[6] -= fz * gx; V[7] -= fz * gy; V[8] -= fz * gz;
+        }
+    }
+    if (TPA > 1) {
+#pragma unroll
+        for (int off = TPA / 2; off > 0; off >>= 1) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) Fi[q] += __shfl_xor_sync(0xffffffffu, Fi[q], off);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) V[q] += __shfl_xor_sync(0xffffffffu, V[q], off);
+        }
+    }
+    if (!active || sub != 0) return;
+    atomicAdd(F + 3 * atom, Fi[0]);
+    atomicAdd(F + 3 * atom + 1, Fi[1]);
+    atomicAdd(F + 3 * atom + 2, Fi[2]);
+    if (vir_atom) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) vir_atom[(size_t)atom * 9 + q] = V[q];
+    }
+}
+
+template <int TPA>
+static void launch_moments_t(const PairArgs &a, float *psi, cudaStream_t st) {
+    const int threads = 256;
+    const long long total = (long long)a.N * TPA;
+    const int blocks = (int)((total + threads - 1) / threads);
+    const size_t smem = sizeof(float) * a.S * a.S * NR * NB;
+    if (blocks > 0) k_moments<TPA><<<blocks, threads, smem, st>>>(a, psi);
+}
+
+template <int TPA>
+static void launch_forces_t(const PairArgs &a, const float *dpsi, float *F, float *vir, cudaStream_t st) {
+    const int threads = 256;
+    const long long total = (long long)a.N * TPA;
+    const int blocks = (int)((total + threads - 1) / threads);
+    const size_t smem = sizeof(float) * a.S * a.S * NR * NB;
+    if (blocks > 0) k_forces<TPA><<<blocks, threads, smem, st>>>(a, dpsi, F, vir);
+}
+
+void launch_moments(const PairArgs &a, int tpa, float *psi, cudaStream_t st) {
+    switch (tpa) {
+    case 1: launch_moments_t<1>(a, psi, st); break;
+    case 2: launch_moments_t<2>(a, psi, st); break;
+    case 4: launch_moments_t<4>(a, psi, st); break;
+    case 8: launch_moments_t<8>(a, psi, st); break;
+    default: launch_moments_t<16>(a, psi, st); break;
+    }
+}
+
+void launch_forces(const PairArgs &a, int tpa, const float *dpsi, float *F, float *vir, cudaStream_t st) {
+    switch (tpa) {
+    case 1: launch_forces_t<1>(a, dpsi, F, vir, st); break;
+    case 2: launch_forces_t<2>(a, dpsi, F, vir, st); break;
+    case 4: launch_forces_t<4>(a, dpsi, F, vir, st); break;
+    case 8: launch_forces_t<8>(a, dpsi, F, vir, st); break;
+    default: launch_forces_t<16>(a, dpsi, F, vir, st); break;
+    }
+}
+
+}  // namespace gm

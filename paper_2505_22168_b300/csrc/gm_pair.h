@@ -1,0 +1,25 @@
+// gm_pair.h -- launchers of the per-pair kernels (moments, forces, parameter-gradient pair passes).
+#pragma once
+
+#include "gm_internal.h"
+
+namespace gm {
+
+struct PairArgs {
+    int N, B, S;
+    const int32_t *atom_ptr;
+    const double *pos;
+    const int32_t *species;
+    const double *cell;
+    const int32_t *row_ptr;
+    const int32_t *col;
+    const char4 *shift;
+    const float *beta;  // [S][S][NR][NB], pre-scaled by n_basis^{-1/2}
+    RadialConst rc;
+    int32_t *status;
+};
+
+void launch_moments(const PairArgs &a, int tpa, float *psi, cudaStream_t st);
+void launch_forces(const PairArgs &a, int tpa, const float *dpsi, float *F, float *vir_atom, cudaStream_t st);
+
+}  // namespace gm
