@@ -50,6 +50,12 @@ extern "C" {
 
 struct CUstream_st; /* cudaStream_t is struct CUstream_st* */
 
+#if defined(__GNUC__)
+#define GM_API __attribute__((visibility("default")))
+#else
+#define GM_API
+#endif
+
 typedef enum {
     GM_OK = 0,
     GM_ERR_ARG = 1,         /* NULL pointer, bad size or misaligned pointer */
@@ -110,22 +116,22 @@ enum { GM_OP_NEIGHBORS = 0, GM_OP_ENERGY_FORCES = 1, GM_OP_PARAM_GRAD = 2 };
 /* Number of FP32 parameters.  Flat layout of theta, in this order:
  *   beta[S][S][n_radial][n_basis], W1[360][H], b1[H], W2[H][H], b2[H], w3[H], b3[1],
  *   sigma[S], mu[S]   (row-major; W1 maps features to the first hidden layer). */
-int64_t gm_param_count(const gm_model_desc *desc);
+GM_API int64_t gm_param_count(const gm_model_desc *desc);
 
 /* Create a model handle (allocates its device weight copies on the current device).
  * Errors: GM_ERR_ARG, GM_ERR_UNSUPPORTED, GM_ERR_CUDA. */
-gm_status gm_model_create(const gm_model_desc *desc, gm_model **out);
+GM_API gm_status gm_model_create(const gm_model_desc *desc, gm_model **out);
 
 /* Copy theta (device, FP32, gm_param_count entries, layout above) into the model and
  * repack the network weights for the kernels (transposed and padded, FP32 and BF16).
  * Asynchronous on `stream`; theta may be reused once the stream reaches this point. */
-gm_status gm_model_set_params(gm_model *m, const float *theta_dev, struct CUstream_st *stream);
+GM_API gm_status gm_model_set_params(gm_model *m, const float *theta_dev, struct CUstream_st *stream);
 
-void gm_model_destroy(gm_model *m);
+GM_API void gm_model_destroy(gm_model *m);
 
 /* Bytes of workspace an operation needs (op = GM_OP_*).  nl_capacity is the neighbour
  * list capacity the caller will pass.  Errors: GM_ERR_ARG. */
-gm_status gm_workspace_size(const gm_model *m, int32_t n_structures, int32_t n_atoms,
+GM_API gm_status gm_workspace_size(const gm_model *m, int32_t n_structures, int32_t n_atoms,
                             int64_t nl_capacity, int32_t op, size_t *bytes);
 
 /* Neighbour search (cell list, FP32 distance filter with an exact FP64 decision near the
@@ -133,7 +139,7 @@ gm_status gm_workspace_size(const gm_model *m, int32_t n_structures, int32_t n_a
  * for small cells (section "Deployment").  Writes nl->row_ptr, nl->col, nl->shift and
  * *nl->n_pairs.  If more than nl->capacity pairs exist, writes GM_ERR_CAPACITY to
  * *status_dev, the required count to *nl->n_pairs, and leaves col/shift unwritten. */
-gm_status gm_build_neighbors(const gm_model *m, const gm_system *sys, gm_nlist *nl, void *ws,
+GM_API gm_status gm_build_neighbors(const gm_model *m, const gm_system *sys, gm_nlist *nl, void *ws,
                              size_t ws_bytes, int32_t *status_dev, struct CUstream_st *stream);
 
 /* Energies and forces (Eqs. energy_sum, basis_fn, contraction, scale_shift; F = -dE/dr).
@@ -141,7 +147,7 @@ gm_status gm_build_neighbors(const gm_model *m, const gm_system *sys, gm_nlist *
  *   forces  device [N][3] FP32, overwritten
  *   virial  device [B][9] FP64 (-dE/d strain, row-major), overwritten; may be NULL
  * The neighbour list must describe sys (as written by gm_build_neighbors or equivalent). */
-gm_status gm_energy_forces(const gm_model *m, const gm_system *sys, const gm_nlist *nl, double *energy,
+GM_API gm_status gm_energy_forces(const gm_model *m, const gm_system *sys, const gm_nlist *nl, double *energy,
                            float *forces, double *virial, void *ws, size_t ws_bytes, int32_t *status_dev,
                            struct CUstream_st *stream);
 
@@ -150,14 +156,14 @@ gm_status gm_energy_forces(const gm_model *m, const gm_system *sys, const gm_nli
  * (section "Training": loss terms on energies and forces).  dL_dE device [B] FP64,
  * dL_dF device [N][3] FP32, grad_theta device [gm_param_count] FP32, overwritten.
  * Moments are recomputed from the positions; no per-pair state is stored. */
-gm_status gm_param_grad(const gm_model *m, const gm_system *sys, const gm_nlist *nl, const double *dL_dE,
+GM_API gm_status gm_param_grad(const gm_model *m, const gm_system *sys, const gm_nlist *nl, const double *dL_dE,
                         const float *dL_dF, float *grad_theta, void *ws, size_t ws_bytes,
                         int32_t *status_dev, struct CUstream_st *stream);
 
 /* Force-matching loss L = wE/B sum_b ((E_b - E_ref_b)/N_b)^2 + wF/(3N) sum_i |F_i - F_ref_i|^2
  * and its gradients (section "Training": weighted energy and force terms, per-atom
  * division).  loss device scalar FP64; dL_dE device [B] FP64; dL_dF device [N][3] FP32. */
-gm_status gm_force_matching_loss(const gm_system *sys, const double *energy, const double *energy_ref,
+GM_API gm_status gm_force_matching_loss(const gm_system *sys, const double *energy, const double *energy_ref,
                                  const float *forces, const float *forces_ref, double w_energy,
                                  double w_forces, double *loss, double *dL_dE, float *dL_dF,
                                  int32_t *status_dev, struct CUstream_st *stream);
@@ -166,14 +172,14 @@ gm_status gm_force_matching_loss(const gm_system *sys, const double *energy, con
  * moment components per radial function: rank 0; x y z; xx xy xz yy yz zz; xxx xxy xxz
  * xyy xyz xzz yyy yyz yzz zzz), features device [N][360] FP32 (may be NULL).
  * Workspace as GM_OP_ENERGY_FORCES. */
-gm_status gm_descriptors(const gm_model *m, const gm_system *sys, const gm_nlist *nl, float *psi,
+GM_API gm_status gm_descriptors(const gm_model *m, const gm_system *sys, const gm_nlist *nl, float *psi,
                          float *features, void *ws, size_t ws_bytes, int32_t *status_dev,
                          struct CUstream_st *stream);
 
-const char *gm_status_string(gm_status s);
+GM_API const char *gm_status_string(gm_status s);
 
 /* Detail of the last synchronous error on the calling thread ("" if none). */
-const char *gm_last_error(void);
+GM_API const char *gm_last_error(void);
 
 #ifdef __cplusplus
 }

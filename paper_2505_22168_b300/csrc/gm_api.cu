@@ -1,0 +1,432 @@
+// gm_api.cu -- the extern "C" entry points of libgm (declared in include/gm.h).
+//
+// Energy + forces pipeline (one stream, no host synchronisation, no allocation):
+//   moments (pair kernel)  -> psi [N][100]
+//   contraction forward    -> G [Mp][384]
+//   L1 GEMM  G W1          -> A1, D1          (phi, phi' of the first hidden layer)
+//   L2 GEMM  A1 W2         -> dZ2, partial output sums (energies)
+//   B1 GEMM  dZ2 W2^T      -> dZ1
+//   B0 GEMM  dZ1 W1^T      -> dG [Mp][384]
+//   contraction backward   -> dpsi [N][100]
+//   forces (pair kernel)   -> F [N][3], per-atom virial
+//   per-structure FP64 reduction -> E [B], W [B][9]
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+
+#include <string>
+
+#include "gm_contract.h"
+#include "gm_gemm.h"
+#include "gm_internal.h"
+#include "gm_pair.h"
+#include "gm_reduce.h"
+
+using namespace gm;
+
+static thread_local std::string g_last_error;
+
+static gm_status fail(gm_status s, const char *msg) {
+    g_last_error = msg;
+    return s;
+}
+
+struct gm_model {
+    gm_model_desc d;
+    int S, H;
+    int64_t n_param;
+    RadialConst rc;
+    int pair_tpa;          // lanes per atom in the pair kernels (0 = automatic)
+    char *buf;             // one device allocation holding everything below
+    size_t buf_bytes;
+    float *beta;           // [S][S][5][7] * n_basis^{-1/2}
+    float *W1t;            // [H][384]  forward  (B[n=h][k=f])
+    float *W1p;            // [384][H]  backward (B[n=f][k=h])
+    float *W2t;            // [H][H]    forward  (B[n][k] = W2[k][n])
+    float *W2;             // [H][H]    backward (B[n][k] = W2[n][k])
+    __nv_bfloat16 *W1t_h, *W1p_h, *W2t_h, *W2_h;
+    float *b1, *b2, *w3, *b3, *sigma, *mu;
+};
+
+namespace {
+
+struct Layout {
+    size_t beta, W1t, W1p, W2t, W2, W1t_h, W1p_h, W2t_h, W2_h, b1, b2, w3, b3, sigma, mu, total;
+};
+
+Layout model_layout(int S, int H) {
+    Layout L;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t start = (off + 255) & ~size_t(255);
+        off = start + bytes;
+        return start;
+    };
+    L.beta = take(sizeof(float) * S * S * NR * NB);
+    L.W1t = take(sizeof(float) * H * NFP);
+    L.W1p = take(sizeof(float) * NFP * H);
+    L.W2t = take(sizeof(float) * H * H);
+    L.W2 = take(sizeof(float) * H * H);
+    L.W1t_h = take(2 * (size_t)H * NFP);
+    L.W1p_h = take(2 * (size_t)NFP * H);
+    L.W2t_h = take(2 * (size_t)H * H);
+    L.W2_h = take(2 * (size_t)H * H);
+    L.b1 = take(sizeof(float) * H);
+    L.b2 = take(sizeof(float) * H);
+    L.w3 = take(sizeof(float) * H);
+    L.b3 = take(sizeof(float) * 4);
+    L.sigma = take(sizeof(float) * S);
+    L.mu = take(sizeof(float) * S);
+    L.total = off;
+    return L;
+}
+
+struct ThetaOff {
+    int64_t beta, W1, b1, W2, b2, w3, b3, sigma, mu, total;
+};
+
+ThetaOff theta_offsets(int S, int H) {
+    ThetaOff o;
+    o.beta = 0;
+    o.W1 = o.beta + (int64_t)S * S * NR * NB;
+    o.b1 = o.W1 + (int64_t)NF * H;
+    o.W2 = o.b1 + H;
+    o.b2 = o.W2 + (int64_t)H * H;
+    o.w3 = o.b2 + H;
+    o.b3 = o.w3 + H;
+    o.sigma = o.b3 + 1;
+    o.mu = o.sigma + S;
+    o.total = o.mu + S;
+    return o;
+}
+
+__global__ void k_repack(const float *__restrict__ th, ThetaOff o, int S, int H, float beta_scale, gm_model m) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t nbeta = (int64_t)S * S * NR * NB;
+    for (int64_t q = tid; q < nbeta; q += stride) m.beta[q] = th[o.beta + q] * beta_scale;
+    for (int64_t q = tid; q < (int64_t)H * NFP; q += stride) {
+        // W1t[h][f] and W1p[f][h] for f < 384
+        const int h = (int)(q / NFP), f = (int)(q % NFP);
+        const float v = f < NF ? th[o.W1 + (int64_t)f * H + h] : 0.0f;
+        m.W1t[q] = v;
+        m.W1t_h[q] = __float2bfloat16_rn(v);
+        const int64_t qp = (int64_t)f * H + h;
+        m.W1p[qp] = v;
+        m.W1p_h[qp] = __float2bfloat16_rn(v);
+    }
+    for (int64_t q = tid; q < (int64_t)H * H; q += stride) {
+        const int r = (int)(q / H), c = (int)(q % H);
+        const float v = th[o.W2 + q];  // W2[r][c]
+        m.W2[q] = v;
+        m.W2_h[q] = __float2bfloat16_rn(v);
+        const int64_t qt = (int64_t)c * H + r;  // W2t[c][r] = W2[r][c]
+        m.W2t[qt] = v;
+        m.W2t_h[qt] = __float2bfloat16_rn(v);
+    }
+    for (int64_t q = tid; q < H; q += stride) {
+        m.b1[q] = th[o.b1 + q];
+        m.b2[q] = th[o.b2 + q];
+        m.w3[q] = th[o.w3 + q];
+    }
+    for (int64_t q = tid; q < S; q += stride) {
+        m.sigma[q] = th[o.sigma + q];
+        m.mu[q] = th[o.mu + q];
+    }
+    if (tid == 0) m.b3[0] = th[o.b3];
+}
+
+int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+struct EfWs {
+    float *psi, *dpsi, *G, *A1, *D1, *dZ2, *dZ1, *dG, *nn_part, *vir_atom;
+};
+
+EfWs carve_ef(Carve &c, int N, int H) {
+    EfWs w;
+    const int Mp = round_up(N, TILE_M);
+    const size_t n1 = N > 0 ? (size_t)N : 1, m1 = Mp > 0 ? (size_t)Mp : 1;
+    w.psi = c.take<float>(n1 * NPSI);
+    w.dpsi = c.take<float>(n1 * NPSI);
+    w.G = c.take<float>(m1 * NFP);
+    w.A1 = c.take<float>(m1 * H);
+    w.D1 = c.take<float>(m1 * H);
+    w.dZ2 = c.take<float>(m1 * H);
+    w.dZ1 = c.take<float>(m1 * H);
+    w.dG = c.take<float>(m1 * NFP);
+    w.nn_part = c.take<float>(m1 * (H / 64));
+    w.vir_atom = c.take<float>(n1 * 9);
+    return w;
+}
+
+size_t ef_workspace_bytes(int N, int H) {
+    Carve c(reinterpret_cast<void *>(256), ~size_t(0) >> 1);
+    carve_ef(c, N, H);
+    return c.off + 256;
+}
+
+bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+gm_status check_system(const gm_model *m, const gm_system *s) {
+    if (!m || !s) return fail(GM_ERR_ARG, "null model or system");
+    if (s->n_structures < 1 || s->n_atoms < 0) return fail(GM_ERR_ARG, "n_structures must be >= 1 and n_atoms >= 0");
+    if (!s->atom_ptr || !s->cell || !s->pbc) return fail(GM_ERR_ARG, "atom_ptr, cell and pbc must be non-null");
+    if (s->n_atoms > 0 && (!s->pos || !s->species)) return fail(GM_ERR_ARG, "pos and species must be non-null");
+    if (!aligned(s->pos, 8) || !aligned(s->cell, 8) || !aligned(s->atom_ptr, 4) || !aligned(s->species, 4))
+        return fail(GM_ERR_ARG, "misaligned system pointer");
+    return GM_OK;
+}
+
+gm_status check_nlist(const gm_system *s, const gm_nlist *nl, bool need_pairs) {
+    if (!nl || !nl->row_ptr || !nl->n_pairs) return fail(GM_ERR_ARG, "null neighbour list field");
+    if (nl->capacity < 0) return fail(GM_ERR_ARG, "negative capacity");
+    if (nl->capacity > 0 && (!nl->col || !nl->shift)) return fail(GM_ERR_ARG, "null col/shift with capacity > 0");
+    if (!aligned(nl->shift, 4) || !aligned(nl->col, 4) || !aligned(nl->row_ptr, 4))
+        return fail(GM_ERR_ARG, "misaligned neighbour list pointer");
+    (void)s;
+    (void)need_pairs;
+    return GM_OK;
+}
+
+PairArgs pair_args(const gm_model *m, const gm_system *s, const gm_nlist *nl, int32_t *status) {
+    PairArgs a;
+    a.N = s->n_atoms;
+    a.B = s->n_structures;
+    a.S = m->S;
+    a.atom_ptr = s->atom_ptr;
+    a.pos = s->pos;
+    a.species = s->species;
+    a.cell = s->cell;
+    a.row_ptr = nl->row_ptr;
+    a.col = nl->col;
+    a.shift = reinterpret_cast<const char4 *>(nl->shift);
+    a.beta = m->beta;
+    a.rc = m->rc;
+    a.status = status;
+    return a;
+}
+
+int choose_tpa(const gm_model *m, int N) {
+    if (m->pair_tpa > 0) return m->pair_tpa;
+    if (N >= 65536) return 1;
+    if (N >= 16384) return 2;
+    if (N >= 4096) return 4;
+    return 8;
+}
+
+gm_status launch_status() {
+    cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess) return fail(GM_ERR_CUDA, cudaGetErrorString(e));
+    return GM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t gm_param_count(const gm_model_desc *d) {
+    if (!d || d->n_species < 1 || d->n_hidden < 1) return -1;
+    return theta_offsets(d->n_species, d->n_hidden).total;
+}
+
+gm_status gm_model_create(const gm_model_desc *d, gm_model **out) {
+    if (!d || !out) return fail(GM_ERR_ARG, "null argument");
+    *out = nullptr;
+    if (d->n_species < 1 || d->n_species > MAX_S) return fail(GM_ERR_UNSUPPORTED, "n_species must be in 1..16");
+    if (d->n_basis != NB || d->n_radial != NR) return fail(GM_ERR_UNSUPPORTED, "n_basis must be 7 and n_radial 5");
+    if (d->n_hidden < 64 || d->n_hidden > 512 || d->n_hidden % 64 != 0)
+        return fail(GM_ERR_UNSUPPORTED, "n_hidden must be a multiple of 64 in 64..512");
+    if (d->activation != GM_ACT_TANH && d->activation != GM_ACT_SILU) return fail(GM_ERR_ARG, "bad activation");
+    if (d->precision != GM_PREC_FP32 && d->precision != GM_PREC_MIXED) return fail(GM_ERR_ARG, "bad precision");
+    if (!(d->r_cut > 0.0) || !(d->r_min >= 0.0) || !(d->r_min < d->r_cut)) return fail(GM_ERR_ARG, "bad radii");
+    gm_model *m = new gm_model();
+    m->d = *d;
+    m->S = d->n_species;
+    m->H = d->n_hidden;
+    m->n_param = theta_offsets(m->S, m->H).total;
+    m->rc.r_cut = (float)d->r_cut;
+    m->rc.inv_r_cut = (float)(1.0 / d->r_cut);
+    m->rc.gamma = (float)((double)(NB * NB) / (d->r_cut * d->r_cut));
+    for (int k = 0; k < NB; ++k) m->rc.mu[k] = (float)(d->r_min + k * (d->r_cut - d->r_min) / (NB - 1));
+    const char *env = getenv("GM_PAIR_TPA");
+    m->pair_tpa = env ? atoi(env) : 0;
+    if (m->pair_tpa != 0 && m->pair_tpa != 1 && m->pair_tpa != 2 && m->pair_tpa != 4 && m->pair_tpa != 8 &&
+        m->pair_tpa != 16)
+        m->pair_tpa = 0;
+    Layout L = model_layout(m->S, m->H);
+    m->buf_bytes = L.total;
+    if (cudaMalloc(&m->buf, L.total) != cudaSuccess) {
+        delete m;
+        return fail(GM_ERR_CUDA, "cudaMalloc of model weights failed");
+    }
+    cudaMemset(m->buf, 0, L.total);
+    m->beta = reinterpret_cast<float *>(m->buf + L.beta);
+    m->W1t = reinterpret_cast<float *>(m->buf + L.W1t);
+    m->W1p = reinterpret_cast<float *>(m->buf + L.W1p);
+    m->W2t = reinterpret_cast<float *>(m->buf + L.W2t);
+    m->W2 = reinterpret_cast<float *>(m->buf + L.W2);
+    m->W1t_h = reinterpret_cast<__nv_bfloat16 *>(m->buf + L.W1t_h);
+    m->W1p_h = reinterpret_cast<__nv_bfloat16 *>(m->buf + L.W1p_h);
+    m->W2t_h = reinterpret_cast<__nv_bfloat16 *>(m->buf + L.W2t_h);
+    m->W2_h = reinterpret_cast<__nv_bfloat16 *>(m->buf + L.W2_h);
+    m->b1 = reinterpret_cast<float *>(m->buf + L.b1);
+    m->b2 = reinterpret_cast<float *>(m->buf + L.b2);
+    m->w3 = reinterpret_cast<float *>(m->buf + L.w3);
+    m->b3 = reinterpret_cast<float *>(m->buf + L.b3);
+    m->sigma = reinterpret_cast<float *>(m->buf + L.sigma);
+    m->mu = reinterpret_cast<float *>(m->buf + L.mu);
+    *out = m;
+    return GM_OK;
+}
+
+gm_status gm_model_set_params(gm_model *m, const float *theta, struct CUstream_st *stream) {
+    if (!m || !theta) return fail(GM_ERR_ARG, "null argument");
+    if (!aligned(theta, 4)) return fail(GM_ERR_ARG, "misaligned theta");
+    ThetaOff o = theta_offsets(m->S, m->H);
+    const float scale = (float)(1.0 / sqrt((double)NB));
+    k_repack<<<296, 256, 0, stream>>>(theta, o, m->S, m->H, scale, *m);
+    return launch_status();
+}
+
+void gm_model_destroy(gm_model *m) {
+    if (!m) return;
+    cudaFree(m->buf);
+    delete m;
+}
+
+gm_status gm_workspace_size(const gm_model *m, int32_t n_structures, int32_t n_atoms, int64_t nl_capacity,
+                            int32_t op, size_t *bytes) {
+    if (!m || !bytes || n_structures < 1 || n_atoms < 0 || nl_capacity < 0) return fail(GM_ERR_ARG, "bad argument");
+    switch (op) {
+    case GM_OP_NEIGHBORS: *bytes = nl_workspace_bytes(n_structures, n_atoms); return GM_OK;
+    case GM_OP_ENERGY_FORCES: *bytes = ef_workspace_bytes(n_atoms, m->H); return GM_OK;
+    case GM_OP_PARAM_GRAD: *bytes = ef_workspace_bytes(n_atoms, m->H); return GM_OK;
+    default: return fail(GM_ERR_ARG, "unknown op");
+    }
+}
+
+gm_status gm_build_neighbors(const gm_model *m, const gm_system *sys, gm_nlist *nl, void *ws, size_t ws_bytes,
+                             int32_t *status, struct CUstream_st *stream) {
+    gm_status s = check_system(m, sys);
+    if (s != GM_OK) return s;
+    if ((s = check_nlist(sys, nl, false)) != GM_OK) return s;
+    if (!status) return fail(GM_ERR_ARG, "null status");
+    if (ws_bytes < nl_workspace_bytes(sys->n_structures, sys->n_atoms)) return fail(GM_ERR_WORKSPACE, "workspace too small");
+    s = nl_build(*sys, m->d.r_cut, m->S, *nl, ws, ws_bytes, status, stream);
+    if (s != GM_OK) return fail(s, "neighbour build launch failed");
+    return launch_status();
+}
+
+static gm_status forward_to_features(const gm_model *m, const gm_system *sys, const gm_nlist *nl, EfWs &w,
+                                     float *psi_out, float *features_out, int32_t *status, cudaStream_t st) {
+    const int N = sys->n_atoms;
+    const int Mp = round_up(N, TILE_M);
+    PairArgs a = pair_args(m, sys, nl, status);
+    float *psi = psi_out ? psi_out : w.psi;
+    launch_moments(a, choose_tpa(m, N), psi, st);
+    launch_contract_fwd_f32(psi, N, Mp, w.G, features_out, st);
+    w.psi = psi;
+    return launch_status();
+}
+
+gm_status gm_energy_forces(const gm_model *m, const gm_system *sys, const gm_nlist *nl, double *energy, float *forces,
+                           double *virial, void *ws, size_t ws_bytes, int32_t *status, struct CUstream_st *stream) {
+    gm_status s = check_system(m, sys);
+    if (s != GM_OK) return s;
+    if ((s = check_nlist(sys, nl, true)) != GM_OK) return s;
+    if (!energy || !status || (sys->n_atoms > 0 && !forces)) return fail(GM_ERR_ARG, "null output");
+    if (m->d.precision != GM_PREC_FP32) return fail(GM_ERR_UNSUPPORTED, "mixed precision path not available");
+    const int N = sys->n_atoms, B = sys->n_structures, H = m->H;
+    Carve c(ws, ws_bytes);
+    EfWs w = carve_ef(c, N, H);
+    if (!c.ok) return fail(GM_ERR_WORKSPACE, "workspace too small");
+    cudaStream_t st = stream;
+    const int Mp = round_up(N, TILE_M);
+    if (N > 0) {
+        if ((s = forward_to_features(m, sys, nl, w, nullptr, nullptr, status, st)) != GM_OK) return s;
+        EpiArgs e{};
+        e.n_atoms = N;
+        e.n_species = m->S;
+        e.species = sys->species;
+        // L1
+        e.bias = m->b1;
+        e.out0 = w.A1;
+        e.out1 = w.D1;
+        gemm_f32(EPI_L1, m->d.activation, w.G, m->W1t, Mp, H, NFP, e, st);
+        // L2
+        e.bias = m->b2;
+        e.w3 = m->w3;
+        e.sigma = m->sigma;
+        e.out0 = w.dZ2;
+        e.out1 = nullptr;
+        e.nn_part = w.nn_part;
+        gemm_f32(EPI_L2, m->d.activation, w.A1, m->W2t, Mp, H, H, e, st);
+        // B1
+        e.out0 = w.dZ1;
+        e.aux = w.D1;
+        gemm_f32(EPI_B1, 0, w.dZ2, m->W2, Mp, H, H, e, st);
+        // B0
+        e.out0 = w.dG;
+        gemm_f32(EPI_STORE, 0, w.dZ1, m->W1p, Mp, NFP, H, e, st);
+        launch_contract_bwd(w.psi, w.dG, N, w.dpsi, st);
+        if (cudaMemsetAsync(forces, 0, sizeof(float) * 3 * (size_t)N, st) != cudaSuccess)
+            return fail(GM_ERR_CUDA, "memset of forces failed");
+        PairArgs a = pair_args(m, sys, nl, status);
+        launch_forces(a, choose_tpa(m, N), w.dpsi, forces, virial ? w.vir_atom : nullptr, st);
+    }
+    launch_struct_reduce(B, sys->atom_ptr, sys->species, m->S, m->sigma, m->mu, m->b3, w.nn_part, H / 64,
+                         virial ? w.vir_atom : nullptr, energy, virial, st);
+    return launch_status();
+}
+
+gm_status gm_descriptors(const gm_model *m, const gm_system *sys, const gm_nlist *nl, float *psi, float *features,
+                         void *ws, size_t ws_bytes, int32_t *status, struct CUstream_st *stream) {
+    gm_status s = check_system(m, sys);
+    if (s != GM_OK) return s;
+    if ((s = check_nlist(sys, nl, true)) != GM_OK) return s;
+    if (!psi || !status) return fail(GM_ERR_ARG, "null output");
+    if (!aligned(psi, 16)) return fail(GM_ERR_ARG, "psi must be 16-byte aligned");
+    Carve c(ws, ws_bytes);
+    EfWs w = carve_ef(c, sys->n_atoms, m->H);
+    if (!c.ok) return fail(GM_ERR_WORKSPACE, "workspace too small");
+    if (sys->n_atoms == 0) return GM_OK;
+    return forward_to_features(m, sys, nl, w, psi, features, status, stream);
+}
+
+gm_status gm_param_grad(const gm_model *m, const gm_system *sys, const gm_nlist *nl, const double *dL_dE,
+                        const float *dL_dF, float *grad_theta, void *ws, size_t ws_bytes, int32_t *status,
+                        struct CUstream_st *stream) {
+    (void)m; (void)sys; (void)nl; (void)dL_dE; (void)dL_dF; (void)grad_theta; (void)ws; (void)ws_bytes;
+    (void)status; (void)stream;
+    return fail(GM_ERR_UNSUPPORTED, "parameter gradient not available yet");
+}
+
+gm_status gm_force_matching_loss(const gm_system *sys, const double *energy, const double *energy_ref,
+                                 const float *forces, const float *forces_ref, double w_energy, double w_forces,
+                                 double *loss, double *dL_dE, float *dL_dF, int32_t *status,
+                                 struct CUstream_st *stream) {
+    if (!sys || !energy || !energy_ref || !loss || !dL_dE || !status || !sys->atom_ptr)
+        return fail(GM_ERR_ARG, "null argument");
+    if (sys->n_atoms > 0 && (!forces || !forces_ref || !dL_dF)) return fail(GM_ERR_ARG, "null force argument");
+    launch_loss(sys->n_structures, sys->n_atoms, sys->atom_ptr, energy, energy_ref, forces, forces_ref, w_energy,
+                w_forces, loss, dL_dE, dL_dF, stream);
+    return launch_status();
+}
+
+const char *gm_status_string(gm_status s) {
+    switch (s) {
+    case GM_OK: return "ok";
+    case GM_ERR_ARG: return "invalid argument";
+    case GM_ERR_CAPACITY: return "neighbour list capacity exceeded";
+    case GM_ERR_UNSUPPORTED: return "unsupported configuration";
+    case GM_ERR_CUDA: return "CUDA error";
+    case GM_ERR_TIMEOUT: return "device wait timed out";
+    case GM_ERR_SPECIES: return "species index out of range";
+    case GM_ERR_WORKSPACE: return "workspace too small";
+    }
+    return "unknown status";
+}
+
+const char *gm_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

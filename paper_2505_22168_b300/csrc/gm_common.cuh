@@ -45,23 +45,21 @@ __host__ __device__ constexpr int comp_ny(int c) { return (comp_code(c) >> 2) & 
 __host__ __device__ constexpr int comp_nz(int c) { return comp_code(c) & 3; }
 __host__ __device__ constexpr int comp_rank(int c) { return c == 0 ? 0 : (c < 4 ? 1 : (c < 10 ? 2 : 3)); }
 
-__host__ __device__ constexpr int code_to_comp(int code) {
-    switch (code) {
-    case 0: return 0;
-    case 16: return 1; case 4: return 2; case 1: return 3;
-    case 32: return 4; case 20: return 5; case 17: return 6; case 8: return 7; case 5: return 8;
-    case 2: return 9;
-    case 48: return 10; case 36: return 11; case 33: return 12; case 24: return 13; case 21: return 14;
-    case 18: return 15; case 12: return 16; case 9: return 17; case 6: return 18;
-    default: return 19;
-    }
-}
-__host__ __device__ constexpr int axis_code(int a) { return a == 0 ? 16 : (a == 1 ? 4 : 1); }
-// unique index of full rank-1/2/3 entries
+// tetrahedral and triangular numbers (closed forms keep every index a cheap constant)
+__host__ __device__ constexpr int tri(int n) { return n * (n + 1) / 2; }
+__host__ __device__ constexpr int tet(int n) { return n * (n + 1) * (n + 2) / 6; }
+__host__ __device__ constexpr int imin(int a, int b) { return a < b ? a : b; }
+__host__ __device__ constexpr int imax(int a, int b) { return a < b ? b : a; }
+// unique index of full rank-1/2/3 entries (sorted index tuples in lexicographic order)
 __host__ __device__ constexpr int idx1(int a) { return 1 + a; }
-__host__ __device__ constexpr int idx2(int a, int b) { return code_to_comp(axis_code(a) + axis_code(b)); }
+__host__ __device__ constexpr int idx2(int a, int b) {
+    return 4 + tri(3) - tri(3 - imin(a, b)) + (imax(a, b) - imin(a, b));
+}
+__host__ __device__ constexpr int idx3s(int a, int b, int c) {  // a <= b <= c
+    return 10 + tet(3) - tet(3 - a) + tri(3 - a) - tri(3 - b) + (c - b);
+}
 __host__ __device__ constexpr int idx3(int a, int b, int c) {
-    return code_to_comp(axis_code(a) + axis_code(b) + axis_code(c));
+    return idx3s(imin(imin(a, b), c), imax(imin(a, b), imin(imax(a, b), c)), imax(imax(a, b), c));
 }
 
 // ---------------------------------------------------------------- feature indexing
@@ -71,43 +69,16 @@ constexpr int FAM_OFF1 = 0, FAM_OFF2 = 5, FAM_OFF3 = 20, FAM_OFF4 = 35, FAM_OFF5
               FAM_OFF6 = 85, FAM_OFF7 = 160, FAM_OFF8 = 235;
 
 __host__ __device__ constexpr int pair_le_index(int s1, int s2) {  // s1 <= s2
-    int n = 0;
-    for (int a = 0; a < NR; ++a)
-        for (int b = a; b < NR; ++b) {
-            if (a == s1 && b == s2) return n;
-            ++n;
-        }
-    return -1;
+    return tri(NR) - tri(NR - s1) + (s2 - s1);
 }
-__host__ __device__ constexpr int f5_index(int s1, int s2, int s3) {  // s1<=s2<=s3
-    int n = 0;
-    for (int a = 0; a < NR; ++a)
-        for (int b = a; b < NR; ++b)
-            for (int c = b; c < NR; ++c) {
-                if (a == s1 && b == s2 && c == s3) return n;
-                ++n;
-            }
-    return -1;
+__host__ __device__ constexpr int f5_index(int s1, int s2, int s3) {  // s1 <= s2 <= s3
+    return tet(NR) - tet(NR - s1) + tri(NR - s1) - tri(NR - s2) + (s3 - s2);
 }
-__host__ __device__ constexpr int f6_index(int s1, int s2, int s3) {  // s1<=s3
-    int n = 0;
-    for (int a = 0; a < NR; ++a)
-        for (int b = 0; b < NR; ++b)
-            for (int c = a; c < NR; ++c) {
-                if (a == s1 && b == s2 && c == s3) return n;
-                ++n;
-            }
-    return -1;
+__host__ __device__ constexpr int f6_index(int s1, int s2, int s3) {  // s1 <= s3
+    return NR * (tri(NR) - tri(NR - s1)) + s2 * (NR - s1) + (s3 - s1);
 }
-__host__ __device__ constexpr int f7_index(int s1, int s2, int s3) {  // s1<=s2
-    int n = 0;
-    for (int a = 0; a < NR; ++a)
-        for (int b = a; b < NR; ++b)
-            for (int c = 0; c < NR; ++c) {
-                if (a == s1 && b == s2 && c == s3) return n;
-                ++n;
-            }
-    return -1;
+__host__ __device__ constexpr int f7_index(int s1, int s2, int s3) {  // s1 <= s2
+    return pair_le_index(s1, s2) * NR + s3;
 }
 __host__ __device__ constexpr int f8_index(int s1, int s2, int s3) { return (s1 * NR + s2) * NR + s3; }
 

@@ -1,0 +1,35 @@
+// gm_gemm.h -- network GEMMs with fused epilogues (FP32 SIMT and BF16 tcgen05 paths).
+//
+// Every GEMM computes C[m][n] = sum_k A[m][k] * B[n][k]: A holds per-atom rows (M padded
+// to a multiple of 128), B is a weight matrix stored with K contiguous.  The network of
+// Eq. scale_shift runs as four of them per energy+forces evaluation:
+//   L1  Z1 = G W1:        A1 = phi(Z1 + b1), D1 = phi'(Z1 + b1)
+//   L2  Z2 = A1 W2:       a2 = phi(Z2 + b2); per-tile partial sum of a2 . w3 (energy);
+//                         dZ2 = sigma_Z w3 phi'(Z2 + b2)          (dE_i/dZ2)
+//   B1  dA1 = dZ2 W2^T:   dZ1 = dA1 * D1
+//   B0  dG = dZ1 W1^T     (stored FP32)
+#pragma once
+
+#include "gm_internal.h"
+
+namespace gm {
+
+enum { EPI_L1 = 0, EPI_L2 = 1, EPI_B1 = 2, EPI_STORE = 3 };
+
+struct EpiArgs {
+    const float *bias;       // [N] (L1, L2)
+    const float *w3;         // [N] (L2)
+    const float *sigma;      // [S] (L2)
+    const int32_t *species;  // [n_atoms] (L2)
+    int n_atoms, n_species;
+    void *out0;              // A1 (L1), dZ2 (L2), dZ1 (B1), C (STORE); row stride N
+    void *out1;              // D1 (L1)
+    const void *aux;         // D1 (B1)
+    float *nn_part;          // [M][N/64] (L2): partial output-layer sums per 64 columns
+};
+
+// FP32 SIMT path (gm_gemm_simt.cu).  M % 128 == 0, N % 64 == 0, K % 16 == 0.
+void gemm_f32(int epi, int act, const float *A, const float *B, int M, int N, int K, const EpiArgs &e,
+              cudaStream_t st);
+
+}  // namespace gm

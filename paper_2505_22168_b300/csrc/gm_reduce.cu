@@ -1,0 +1,97 @@
+// gm_reduce.cu -- per-structure FP64 reductions and the force-matching loss.
+//
+//   E_i = sigma_Z (sum of output-layer partials + b3) + mu_Z      (Eq. scale_shift)
+//   E_b = sum_{i in b} E_i in FP64                               (Eq. energy_sum)
+//   W_b = sum_{i in b} W_i in FP64 (per-atom virials from the force kernel)
+//   loss (section "Training": energy and force terms, per-atom division of the energy term)
+// One block per structure, fixed summation order (deterministic).
+#include "gm_internal.h"
+#include "gm_reduce.h"
+
+namespace gm {
+
+__device__ __forceinline__ double block_sum_double(double v, double *sh) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0)
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) r += sh[q];
+    return r;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(256) k_struct_reduce(int B, const int32_t *__restrict__ atom_ptr,
+                                                       const int32_t *__restrict__ species, int S,
+                                                       const float *__restrict__ sigma, const float *__restrict__ mu,
+                                                       const float *__restrict__ b3, const float *__restrict__ nn_part,
+                                                       int nparts, const float *__restrict__ vir_atom,
+                                                       double *energy, double *virial) {
+    __shared__ double sh[8];
+    const int b = blockIdx.x;
+    const int a0 = atom_ptr[b], a1 = atom_ptr[b + 1];
+    double e = 0.0, v[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) v[q] = 0.0;
+    const float bias = b3[0];
+    for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
+        float nn = bias;
+        for (int t = 0; t < nparts; ++t) nn += nn_part[(size_t)i * nparts + t];
+        const int z = min(max(species[i], 0), S - 1);
+        e += (double)fmaf(sigma[z], nn, mu[z]);
+        if (vir_atom)
+#pragma unroll
+            for (int q = 0; q < 9; ++q) v[q] += (double)vir_atom[(size_t)i * 9 + q];
+    }
+    const double et = block_sum_double(e, sh);
+    if (threadIdx.x == 0) energy[b] = et;
+    if (virial) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const double vt = block_sum_double(v[q], sh);
+            if (threadIdx.x == 0) virial[9 * b + q] = vt;
+        }
+    }
+}
+
+void launch_struct_reduce(int B, const int32_t *atom_ptr, const int32_t *species, int S, const float *sigma,
+                          const float *mu, const float *b3, const float *nn_part, int nparts, const float *vir_atom,
+                          double *energy, double *virial, cudaStream_t st) {
+    if (B > 0)
+        k_struct_reduce<<<B, 256, 0, st>>>(B, atom_ptr, species, S, sigma, mu, b3, nn_part, nparts, vir_atom, energy,
+                                           virial);
+}
+
+// Force-matching loss: one block; FP64 accumulation in a fixed order.
+__global__ void __launch_bounds__(1024) k_loss(int B, int N, const int32_t *__restrict__ atom_ptr,
+                                               const double *__restrict__ E, const double *__restrict__ Eref,
+                                               const float *__restrict__ F, const float *__restrict__ Fref, double wE,
+                                               double wF, double *loss, double *gE, float *gF) {
+    __shared__ double sh[32];
+    double le = 0.0, lf = 0.0;
+    for (int b = threadIdx.x; b < B; b += blockDim.x) {
+        const double nb = (double)(atom_ptr[b + 1] - atom_ptr[b]);
+        const double d = nb > 0.0 ? (E[b] - Eref[b]) / nb : 0.0;
+        le += d * d;
+        gE[b] = nb > 0.0 ? 2.0 * wE / B * d / nb : 0.0;
+    }
+    const double cF = N > 0 ? 2.0 * wF / (3.0 * N) : 0.0;
+    for (int q = threadIdx.x; q < 3 * N; q += blockDim.x) {
+        const double d = (double)F[q] - (double)Fref[q];
+        lf += d * d;
+        gF[q] = (float)(cF * d);
+    }
+    const double se = block_sum_double(le, sh);
+    __syncthreads();
+    const double sf = block_sum_double(lf, sh);
+    if (threadIdx.x == 0) *loss = wE / B * se + (N > 0 ? wF / (3.0 * N) * sf : 0.0);
+}
+
+void launch_loss(int B, int N, const int32_t *atom_ptr, const double *E, const double *Eref, const float *F,
+                 const float *Fref, double wE, double wF, double *loss, double *gE, float *gF, cudaStream_t st) {
+    k_loss<<<1, 1024, 0, st>>>(B, N, atom_ptr, E, Eref, F, Fref, wE, wF, loss, gE, gF);
+}
+
+}  // namespace gm

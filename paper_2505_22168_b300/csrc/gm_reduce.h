@@ -1,0 +1,15 @@
+// gm_reduce.h -- FP64 per-structure reductions and the loss kernel.
+#pragma once
+
+#include "gm_internal.h"
+
+namespace gm {
+
+void launch_struct_reduce(int B, const int32_t *atom_ptr, const int32_t *species, int S, const float *sigma,
+                          const float *mu, const float *b3, const float *nn_part, int nparts, const float *vir_atom,
+                          double *energy, double *virial, cudaStream_t st);
+
+void launch_loss(int B, int N, const int32_t *atom_ptr, const double *E, const double *Eref, const float *F,
+                 const float *Fref, double wE, double wF, double *loss, double *gE, float *gF, cudaStream_t st);
+
+}  // namespace gm
