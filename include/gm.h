@@ -176,6 +176,9 @@ GM_API gm_status gm_descriptors(const gm_model *m, const gm_system *sys, const g
                          float *features, void *ws, size_t ws_bytes, int32_t *status_dev,
                          struct CUstream_st *stream);
 
+/* Zero the device status word (cudaMemsetAsync on `stream`); call before each step. */
+GM_API gm_status gm_status_clear(int32_t *status_dev, struct CUstream_st *stream);
+
 GM_API const char *gm_status_string(gm_status s);
 
 /* Detail of the last synchronous error on the calling thread ("" if none). */

@@ -57,6 +57,8 @@ def lib():
         build()
         _lib = ctypes.CDLL(str(LIB))
         _lib.or_neighbors.restype = ctypes.c_int
+        _lib.or_neighbor_rows.restype = ctypes.c_int
+        _lib.or_descriptors.restype = ctypes.c_int
         _lib.or_energy_forces.restype = ctypes.c_int
         _lib.or_param_grad.restype = ctypes.c_int
         _lib.or_loss.restype = ctypes.c_double
@@ -121,6 +123,60 @@ def neighbors(batch, r_cut, capacity=None) -> NeighborList:
     row_ptr = np.zeros(batch.n_atoms + 1, np.int64)
     row_ptr[1:] = np.cumsum(counts)
     return NeighborList(row_ptr, np.ascontiguousarray(pj[:P]), np.ascontiguousarray(ps[:P]))
+
+
+def neighbor_rows(batch, r_cut, rows) -> NeighborList:
+    """The brute-force neighbour list restricted to the centre atoms in ``rows`` (other
+    rows are empty); same rule and arithmetic as neighbors()."""
+    L = lib()
+    pos = np.ascontiguousarray(batch.pos, np.float64)
+    cell = np.ascontiguousarray(batch.cell, np.float64).reshape(-1, 9)
+    pbc = np.ascontiguousarray(batch.pbc, np.uint8)
+    ap = np.ascontiguousarray(batch.atom_ptr, np.int32)
+    rows = np.ascontiguousarray(np.unique(rows), np.int32)
+    cap = 400 * len(rows) + 1024
+    while True:
+        pi = np.empty(cap, np.int32)
+        pj = np.empty(cap, np.int32)
+        ps = np.empty((cap, 3), np.int32)
+        n = ctypes.c_int64(0)
+        rc = L.or_neighbor_rows(ctypes.c_int(batch.n_structures), _p(ap, ctypes.c_int), _p(pos), _p(cell),
+                                _p(pbc, ctypes.c_ubyte), ctypes.c_double(r_cut), ctypes.c_int(len(rows)),
+                                _p(rows, ctypes.c_int), ctypes.c_int64(cap), _p(pi, ctypes.c_int),
+                                _p(pj, ctypes.c_int), _p(ps, ctypes.c_int), ctypes.byref(n))
+        if rc == 0:
+            break
+        cap = int(n.value) + 16
+    P = int(n.value)
+    counts = np.bincount(pi[:P], minlength=batch.n_atoms)
+    row_ptr = np.zeros(batch.n_atoms + 1, np.int64)
+    row_ptr[1:] = np.cumsum(counts)
+    return NeighborList(row_ptr, np.ascontiguousarray(pj[:P]), np.ascontiguousarray(ps[:P]))
+
+
+def descriptors(batch, desc, params, nl: NeighborList, rows):
+    """Moments [len(rows), nr, 20] and features [len(rows), nf] of the atoms in ``rows``."""
+    L = lib()
+    keep = []
+    m = _model(desc, params, keep)
+    nr = int(desc.get("n_radial", 5))
+    nf = L.or_feature_table(ctypes.c_int(nr), None, None)
+    rows = np.ascontiguousarray(rows, np.int32)
+    psi = np.zeros((len(rows), nr, 20))
+    G = np.zeros((len(rows), nf))
+    pos = np.ascontiguousarray(batch.pos, np.float64)
+    cell = np.ascontiguousarray(batch.cell, np.float64).reshape(-1, 9)
+    spec = np.ascontiguousarray(batch.species, np.int32)
+    ap = np.ascontiguousarray(batch.atom_ptr, np.int32)
+    rp = np.ascontiguousarray(nl.row_ptr, np.int64)
+    col = np.ascontiguousarray(nl.col, np.int32)
+    sh = np.ascontiguousarray(nl.shift, np.int32)
+    rc = L.or_descriptors(ctypes.byref(m), ctypes.c_int(batch.n_structures), _p(ap, ctypes.c_int), _p(pos),
+                          _p(spec, ctypes.c_int), _p(cell), _p(rp, ctypes.c_int64), _p(col, ctypes.c_int),
+                          _p(sh, ctypes.c_int), ctypes.c_int(len(rows)), _p(rows, ctypes.c_int), _p(psi), _p(G))
+    if rc != 0:
+        raise RuntimeError(f"or_descriptors failed ({rc})")
+    return psi, G
 
 
 def energy_forces(batch, desc, params, nl: NeighborList, virial=True, psi=False, features=False):

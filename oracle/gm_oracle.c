@@ -126,9 +126,32 @@ static void wrap_structure(int n, const double *pos, const double *cell, const u
 /* Brute-force neighbour list of a batch.  Pairs are written grouped by centre atom i
  * (global indices), so that row_ptr can be formed by counting.  Returns 0 on success,
  * 1 when more than cap pairs exist (n_pairs then holds the required count). */
+static int neighbors_impl(int n_struct, const int *atom_ptr, const double *pos, const double *cell,
+                          const unsigned char *pbc, double r_cut, const unsigned char *want_row, int64_t cap,
+                          int *pi, int *pj, int *pshift, int64_t *n_pairs);
+
 int or_neighbors(int n_struct, const int *atom_ptr, const double *pos, const double *cell,
                  const unsigned char *pbc, double r_cut, int64_t cap, int *pi, int *pj, int *pshift,
                  int64_t *n_pairs) {
+    return neighbors_impl(n_struct, atom_ptr, pos, cell, pbc, r_cut, NULL, cap, pi, pj, pshift, n_pairs);
+}
+
+/* Rows of the same neighbour list for the centre atoms listed in rows[] only (same rule,
+ * same arithmetic); used to check large systems on sampled atoms. */
+int or_neighbor_rows(int n_struct, const int *atom_ptr, const double *pos, const double *cell,
+                     const unsigned char *pbc, double r_cut, int n_rows, const int *rows, int64_t cap, int *pi,
+                     int *pj, int *pshift, int64_t *n_pairs) {
+    const int N = atom_ptr[n_struct];
+    unsigned char *want = (unsigned char *)calloc(N ? N : 1, 1);
+    for (int q = 0; q < n_rows; ++q) want[rows[q]] = 1;
+    int rc = neighbors_impl(n_struct, atom_ptr, pos, cell, pbc, r_cut, want, cap, pi, pj, pshift, n_pairs);
+    free(want);
+    return rc;
+}
+
+static int neighbors_impl(int n_struct, const int *atom_ptr, const double *pos, const double *cell,
+                          const unsigned char *pbc, double r_cut, const unsigned char *want_row, int64_t cap,
+                          int *pi, int *pj, int *pshift, int64_t *n_pairs) {
     int64_t np = 0;
     const double rc2 = r_cut * r_cut;
     for (int b = 0; b < n_struct; ++b) {
@@ -149,7 +172,8 @@ int or_neighbors(int n_struct, const int *atom_ptr, const double *pos, const dou
             nmax[a] = pb[a] ? (int)ceil(r_cut / w) + 1 : 0;
         }
         const int ortho = is_orthorhombic(C);
-        for (int i = 0; i < n; ++i)
+        for (int i = 0; i < n; ++i) {
+            if (want_row && !want_row[a0 + i]) continue;
             for (int j = 0; j < n; ++j)
                 for (int n0 = -nmax[0]; n0 <= nmax[0]; ++n0)
                     for (int n1 = -nmax[1]; n1 <= nmax[1]; ++n1)
@@ -177,6 +201,7 @@ int or_neighbors(int n_struct, const int *atom_ptr, const double *pos, const dou
                             }
                             ++np;
                         }
+        }
         free(xw);
         free(m);
     }
@@ -581,6 +606,61 @@ int or_energy_forces(const or_model *M, int n_struct, const int *atom_ptr, const
     free(Ea);
     ctx_free(&cx);
     return err;
+}
+
+/* ------------------------------------------------------------------ descriptors */
+
+/* Moments (unique components, [nr][20]) and features of the atoms listed in rows[],
+ * from their CSR rows (other rows are ignored).  Same arithmetic as or_energy_forces. */
+int or_descriptors(const or_model *M, int n_struct, const int *atom_ptr, const double *pos, const int *species,
+                   const double *cell, const int64_t *row_ptr, const int *col, const int *shift, int n_rows,
+                   const int *rows, double *psi_out, double *G_out) {
+    if (M->n_radial > OR_MAXR || M->n_basis > 16) return 2;
+    ctx_t cx;
+    ctx_init(M, &cx);
+    const int nr = cx.nr, nt = cx.nt, nf = cx.nf;
+#pragma omp parallel
+    {
+        double *T = (double *)malloc(sizeof(double) * nt);
+        double Y[4][27], dY[4][27][3], R[OR_MAXR], dR[OR_MAXR];
+        pair_basis pb;
+        static const int I2[6] = {0, 1, 2, 4, 5, 8};
+        static const int I3[10] = {0, 1, 2, 4, 5, 8, 13, 14, 17, 26};
+#pragma omp for schedule(dynamic, 4)
+        for (int q = 0; q < n_rows; ++q) {
+            const int i = rows[q];
+            const double *C = cell + 9 * struct_of(n_struct, atom_ptr, i);
+            memset(T, 0, sizeof(double) * nt);
+            for (int64_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p) {
+                double d[3];
+                const int j = col[p];
+                displacement(pos, C, i, j, shift + 3 * p, d);
+                double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                basis_eval(M, r, &pb);
+                radial(M, species[i], species[j], &pb, R, dR);
+                double u[3] = {d[0] / r, d[1] / r, d[2] / r};
+                monomials(u, r, Y, dY);
+                for (int s = 0; s < nr; ++s)
+                    for (int L = 0; L < 4; ++L) {
+                        double *t = T + toff(nr, L, s);
+                        for (int c = 0; c < TSIZE[L]; ++c) t[c] += R[s] * Y[L][c];
+                    }
+            }
+            double *po = psi_out + (size_t)q * nr * 20;
+            for (int s = 0; s < nr; ++s) {
+                po[20 * s] = T[toff(nr, 0, s)];
+                for (int a = 0; a < 3; ++a) po[20 * s + 1 + a] = T[toff(nr, 1, s) + a];
+                for (int a = 0; a < 6; ++a) po[20 * s + 4 + a] = T[toff(nr, 2, s) + I2[a]];
+                for (int a = 0; a < 10; ++a) po[20 * s + 10 + a] = T[toff(nr, 3, s) + I3[a]];
+            }
+            for (int f = 0; f < nf; ++f)
+                G_out[(size_t)q * nf + f] =
+                    fam_val(cx.ft[f].fam, T + cx.ft[f].off[0], T + cx.ft[f].off[1], T + cx.ft[f].off[2]);
+        }
+        free(T);
+    }
+    ctx_free(&cx);
+    return 0;
 }
 
 /* ------------------------------------------------------------------ loss */

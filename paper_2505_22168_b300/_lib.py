@@ -1,0 +1,158 @@
+"""ctypes declarations of libgm (include/gm.h), with the same function names.
+
+Argument marshalling only: every entry point takes plain integers (device pointers, sizes,
+the CUDA stream handle) and ctypes structs; no computation happens here.  A missing or
+unloadable libgm.so raises immediately -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+LIB_PATH = Path(__file__).resolve().parent / "libgm.so"
+
+GM_OK, GM_ERR_ARG, GM_ERR_CAPACITY, GM_ERR_UNSUPPORTED, GM_ERR_CUDA, GM_ERR_TIMEOUT, GM_ERR_SPECIES, \
+    GM_ERR_WORKSPACE = range(8)
+GM_ACT_TANH, GM_ACT_SILU = 0, 1
+GM_PREC_FP32, GM_PREC_MIXED = 0, 1
+GM_OP_NEIGHBORS, GM_OP_ENERGY_FORCES, GM_OP_PARAM_GRAD = 0, 1, 2
+
+STATUS_NAMES = {0: "GM_OK", 1: "GM_ERR_ARG", 2: "GM_ERR_CAPACITY", 3: "GM_ERR_UNSUPPORTED", 4: "GM_ERR_CUDA",
+                5: "GM_ERR_TIMEOUT", 6: "GM_ERR_SPECIES", 7: "GM_ERR_WORKSPACE"}
+
+# every exported symbol of include/gm.h
+EXPORTS = ("gm_param_count", "gm_model_create", "gm_model_set_params", "gm_model_destroy", "gm_workspace_size",
+           "gm_build_neighbors", "gm_energy_forces", "gm_param_grad", "gm_force_matching_loss", "gm_descriptors",
+           "gm_status_clear", "gm_status_string", "gm_last_error")
+
+
+class GmModelDesc(ctypes.Structure):
+    _fields_ = [("n_species", ctypes.c_int32), ("n_basis", ctypes.c_int32), ("n_radial", ctypes.c_int32),
+                ("n_hidden", ctypes.c_int32), ("activation", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("r_min", ctypes.c_double), ("r_cut", ctypes.c_double)]
+
+
+class GmSystem(ctypes.Structure):
+    _fields_ = [("n_structures", ctypes.c_int32), ("n_atoms", ctypes.c_int32), ("atom_ptr", ctypes.c_void_p),
+                ("pos", ctypes.c_void_p), ("species", ctypes.c_void_p), ("cell", ctypes.c_void_p),
+                ("pbc", ctypes.c_void_p)]
+
+
+class GmNlist(ctypes.Structure):
+    _fields_ = [("capacity", ctypes.c_int64), ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p),
+                ("shift", ctypes.c_void_p), ("n_pairs", ctypes.c_void_p)]
+
+
+class GmError(RuntimeError):
+    def __init__(self, code, where, detail=""):
+        self.code = code
+        super().__init__(f"{where}: {STATUS_NAMES.get(code, code)} {detail}".strip())
+
+
+_lib = None
+_P = ctypes.c_void_p
+
+
+def load():
+    """Load libgm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not LIB_PATH.exists():
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2505_22168_b300.build`")
+    lib = ctypes.CDLL(str(LIB_PATH))
+    st = ctypes.c_int
+    sig = {
+        "gm_param_count": (ctypes.c_int64, [ctypes.POINTER(GmModelDesc)]),
+        "gm_model_create": (st, [ctypes.POINTER(GmModelDesc), ctypes.POINTER(_P)]),
+        "gm_model_set_params": (st, [_P, _P, _P]),
+        "gm_model_destroy": (None, [_P]),
+        "gm_workspace_size": (st, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32,
+                                   ctypes.POINTER(ctypes.c_size_t)]),
+        "gm_build_neighbors": (st, [_P, ctypes.POINTER(GmSystem), ctypes.POINTER(GmNlist), _P, ctypes.c_size_t, _P, _P]),
+        "gm_energy_forces": (st, [_P, ctypes.POINTER(GmSystem), ctypes.POINTER(GmNlist), _P, _P, _P, _P,
+                                  ctypes.c_size_t, _P, _P]),
+        "gm_param_grad": (st, [_P, ctypes.POINTER(GmSystem), ctypes.POINTER(GmNlist), _P, _P, _P, _P,
+                               ctypes.c_size_t, _P, _P]),
+        "gm_force_matching_loss": (st, [ctypes.POINTER(GmSystem), _P, _P, _P, _P, ctypes.c_double, ctypes.c_double,
+                                        _P, _P, _P, _P, _P]),
+        "gm_descriptors": (st, [_P, ctypes.POINTER(GmSystem), ctypes.POINTER(GmNlist), _P, _P, _P, ctypes.c_size_t,
+                                _P, _P]),
+        "gm_status_clear": (st, [_P, _P]),
+        "gm_status_string": (ctypes.c_char_p, [st]),
+        "gm_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def check(code, where):
+    """Raise GmError for a non-zero synchronous status."""
+    if code != GM_OK:
+        detail = load().gm_last_error().decode()
+        raise GmError(code, where, detail)
+
+
+# thin wrappers with the C names ------------------------------------------------------
+
+def gm_param_count(desc: GmModelDesc) -> int:
+    return int(load().gm_param_count(ctypes.byref(desc)))
+
+
+def gm_model_create(desc: GmModelDesc) -> int:
+    h = _P()
+    check(load().gm_model_create(ctypes.byref(desc), ctypes.byref(h)), "gm_model_create")
+    return h.value
+
+
+def gm_model_set_params(model: int, theta_ptr: int, stream: int):
+    check(load().gm_model_set_params(model, theta_ptr, stream), "gm_model_set_params")
+
+
+def gm_model_destroy(model: int):
+    load().gm_model_destroy(model)
+
+
+def gm_workspace_size(model: int, n_structures: int, n_atoms: int, capacity: int, op: int) -> int:
+    out = ctypes.c_size_t(0)
+    check(load().gm_workspace_size(model, n_structures, n_atoms, capacity, op, ctypes.byref(out)),
+          "gm_workspace_size")
+    return int(out.value)
+
+
+def gm_build_neighbors(model, sys: GmSystem, nl: GmNlist, ws, ws_bytes, status, stream):
+    check(load().gm_build_neighbors(model, ctypes.byref(sys), ctypes.byref(nl), ws, ws_bytes, status, stream),
+          "gm_build_neighbors")
+
+
+def gm_energy_forces(model, sys: GmSystem, nl: GmNlist, energy, forces, virial, ws, ws_bytes, status, stream):
+    check(load().gm_energy_forces(model, ctypes.byref(sys), ctypes.byref(nl), energy, forces, virial, ws, ws_bytes,
+                                  status, stream), "gm_energy_forces")
+
+
+def gm_param_grad(model, sys: GmSystem, nl: GmNlist, dL_dE, dL_dF, grad_theta, ws, ws_bytes, status, stream):
+    check(load().gm_param_grad(model, ctypes.byref(sys), ctypes.byref(nl), dL_dE, dL_dF, grad_theta, ws, ws_bytes,
+                               status, stream), "gm_param_grad")
+
+
+def gm_force_matching_loss(sys: GmSystem, energy, energy_ref, forces, forces_ref, w_energy, w_forces, loss, dL_dE,
+                           dL_dF, status, stream):
+    check(load().gm_force_matching_loss(ctypes.byref(sys), energy, energy_ref, forces, forces_ref, w_energy, w_forces,
+                                        loss, dL_dE, dL_dF, status, stream), "gm_force_matching_loss")
+
+
+def gm_descriptors(model, sys: GmSystem, nl: GmNlist, psi, features, ws, ws_bytes, status, stream):
+    check(load().gm_descriptors(model, ctypes.byref(sys), ctypes.byref(nl), psi, features, ws, ws_bytes, status,
+                                stream), "gm_descriptors")
+
+
+def gm_status_clear(status, stream):
+    check(load().gm_status_clear(status, stream), "gm_status_clear")
+
+
+def gm_status_string(code: int) -> str:
+    return load().gm_status_string(code).decode()

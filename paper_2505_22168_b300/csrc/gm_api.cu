@@ -413,6 +413,12 @@ gm_status gm_force_matching_loss(const gm_system *sys, const double *energy, con
     return launch_status();
 }
 
+gm_status gm_status_clear(int32_t *status, struct CUstream_st *stream) {
+    if (!status) return fail(GM_ERR_ARG, "null status");
+    if (cudaMemsetAsync(status, 0, sizeof(int32_t), stream) != cudaSuccess) return fail(GM_ERR_CUDA, "memset failed");
+    return GM_OK;
+}
+
 const char *gm_status_string(gm_status s) {
     switch (s) {
     case GM_OK: return "ok";

@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(256) k_moments(PairArgs a, float *__restrict__
     __syncthreads();
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int atom = g / TPA, sub = g % TPA;
-    const bool active = atom < a.N;
+    const bool active = atom < a.N && !status_bad(a.status);
     float acc[NPSI];
 #pragma unroll
     for (int q = 0; q < NPSI; ++q) acc[q] = 0.0f;
@@ -58,6 +58,10 @@ __global__ void __launch_bounds__(256) k_moments(PairArgs a, float *__restrict__
         const int p1 = a.row_ptr[atom + 1];
         for (int p = a.row_ptr[atom] + sub; p < p1; p += TPA) {
             const int j = a.col[p];
+            if ((unsigned)j >= (unsigned)a.N) {
+                set_status(a.status, GM_ERR_ARG);
+                continue;
+            }
             float fx, fy, fz;
             pair_displacement(a.pos, xi, yi, zi, j, a.shift[p], Lx, Ly, Lz, fx, fy, fz);
             const float r = sqrtf(fx * fx + fy * fy + fz * fz);
@@ -109,7 +113,7 @@ __global__ void __launch_bounds__(256) k_forces(PairArgs a, const float *__restr
     __syncthreads();
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
     const int atom = gt / TPA, sub = gt % TPA;
-    const bool active = atom < a.N;
+    const bool active = atom < a.N && !status_bad(a.status);
     float Fi[3] = {0.0f, 0.0f, 0.0f};
     float V[9];
 #pragma unroll
@@ -130,6 +134,10 @@ __global__ void __launch_bounds__(256) k_forces(PairArgs a, const float *__restr
         const int p1 = a.row_ptr[atom + 1];
         for (int p = a.row_ptr[atom] + sub; p < p1; p += TPA) {
             const int j = a.col[p];
+            if ((unsigned)j >= (unsigned)a.N) {
+                set_status(a.status, GM_ERR_ARG);
+                continue;
+            }
             float fx, fy, fz;
             pair_displacement(a.pos, xi, yi, zi, j, a.shift[p], Lx, Ly, Lz, fx, fy, fz);
             const float r = sqrtf(fx * fx + fy * fy + fz * fz);

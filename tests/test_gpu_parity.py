@@ -1,0 +1,228 @@
+"""GPU parity against the FP64 oracle, through the C ABI.
+
+Neighbour sets are compared bit for bit (as sorted (i, j, shift) triples).  Energies,
+forces, virials and descriptors are compared element by element within the tolerance
+stated for the FP32 path (1e-5 relative on energy per atom and force RMS).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from synth.systems import make_batch
+from tests.parity import ELEMENT_FACTOR, TOL, energy_error, force_error, subset, virial_error
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2505_22168_b300 import build
+    build.build()
+
+
+def _gm():
+    from paper_2505_22168_b300 import GMNN, DeviceSystem
+    return GMNN, DeviceSystem
+
+
+def _model(desc, params, precision="fp32"):
+    GMNN, _ = _gm()
+    return GMNN(desc, params, precision=precision)
+
+
+def _nl_pair(batch, desc, params):
+    GMNN, DeviceSystem = _gm()
+    m = GMNN(desc, params)
+    sysd = DeviceSystem(batch)
+    nl = m.build_neighbors(sysd)
+    return m, sysd, nl
+
+
+@pytest.fixture(scope="module")
+def li_small():
+    b, d, p = synth.config(3)
+    return subset(b, range(24)), d, p
+
+
+# ------------------------------------------------------------------ neighbour lists
+
+def _assert_same_pairs(batch, desc, params):
+    _, _, nl = _nl_pair(batch, desc, params)
+    got = nl.triples()
+    want = oracle.neighbors(batch, desc["r_cut"]).triples()
+    assert got.shape == want.shape
+    assert np.array_equal(got, want)
+    assert int(nl.n_pairs.item()) == len(want)
+
+
+def test_neighbors_config1():
+    b, d, p = synth.config(1)
+    _assert_same_pairs(b, d, p)
+
+
+def test_neighbors_small_boxes_multi_image(li_small):
+    b, d, p = li_small
+    L = b.cell[:, 0, 0]
+    assert (L < 2 * d["r_cut"]).any()          # several images of one neighbour occur
+    _assert_same_pairs(b, d, p)
+
+
+@pytest.mark.parametrize("rc,count", [(0.99, 0), (1.01, 6), (1.5, 18), (2.1, 32), (2.5, 80)])
+def test_neighbors_self_images(rc, count):
+    _, d, p = synth.config(1)
+    d = dict(d, r_cut=rc, r_min=0.1)
+    b = make_batch([(np.array([[0.3, 0.6, 0.9]]), np.array([0]), np.eye(3))], 5)
+    _, _, nl = _nl_pair(b, d, p)
+    assert int(nl.n_pairs.item()) == count
+    assert np.array_equal(nl.triples(), oracle.neighbors(b, rc).triples())
+
+
+def test_neighbors_outside_cell_ragged_and_empty():
+    """Positions far outside the cell, structures of different sizes, and an empty one."""
+    _, d, p = synth.config(1)
+    rng = np.random.default_rng(3)
+    structs = []
+    for L, n in ((4.0, 5), (7.0, 40), (9.0, 0), (5.5, 17), (12.0, 130)):
+        structs.append((rng.uniform(-2 * L, 3 * L, (n, 3)), rng.integers(0, 5, n), L * np.eye(3)))
+    b = make_batch(structs, 5)
+    _assert_same_pairs(b, dict(d, r_cut=3.3), p)
+
+
+def test_neighbors_exactly_at_cutoff():
+    _, d, p = synth.config(1)
+    pos = np.array([[1.0, 1.0, 1.0], [1.0 + 2.5, 1.0, 1.0], [1.0, 1.0 + np.nextafter(2.5, 0.0), 1.0]])
+    b = make_batch([(pos, np.array([0, 1, 2]), 20 * np.eye(3))], 5)
+    _assert_same_pairs(b, dict(d, r_cut=2.5, r_min=0.2), p)
+
+
+def test_neighbors_capacity_overflow_reports_required_count():
+    from paper_2505_22168_b300 import NeighborList, _lib
+    b, d, p = synth.config(1)
+    m, sysd, _ = _nl_pair(b, d, p)
+    small = NeighborList(sysd.n_atoms, 100, m.device)
+    m.build_neighbors(sysd, small, check=False)
+    assert m.read_status() == _lib.GM_ERR_CAPACITY
+    assert int(small.n_pairs.item()) == oracle.neighbors(b, d["r_cut"]).n_pairs
+
+
+def test_non_orthorhombic_cell_is_unsupported():
+    from paper_2505_22168_b300 import _lib
+    b, d, p = synth.config(1)
+    cell = b.cell[0].copy()
+    cell[1, 0] = 0.5
+    b2 = make_batch([(b.pos, b.species, cell)], 5)
+    GMNN, DeviceSystem = _gm()
+    m = GMNN(d, p)
+    m.build_neighbors(DeviceSystem(b2), check=False)
+    assert m.read_status() == _lib.GM_ERR_UNSUPPORTED
+
+
+def test_bad_species_is_reported():
+    from paper_2505_22168_b300 import _lib
+    b, d, p = synth.config(1)
+    spec = b.species.copy()
+    spec[7] = 9
+    b2 = make_batch([(b.pos, spec, b.cell[0])], 5)
+    GMNN, DeviceSystem = _gm()
+    m = GMNN(d, p)
+    m.build_neighbors(DeviceSystem(b2), check=False)
+    assert m.read_status() == _lib.GM_ERR_SPECIES
+
+
+# ------------------------------------------------------------------ energies and forces
+
+def _ef_parity(batch, desc, params, precision="fp32", virial=True):
+    m, sysd, nl = _nl_pair(batch, desc, params)
+    if precision != "fp32":
+        m = _model(desc, params, precision)
+    E, F, W = m.energy_forces(sysd, nl, virial=virial)
+    m.check_status()
+    ref = oracle.energy_forces(batch, desc, params, oracle.neighbors(batch, desc["r_cut"]))
+    tol = TOL[precision]
+    e = energy_error(E.cpu().numpy(), ref, batch)
+    f_rms, f_max = force_error(F.cpu().numpy().astype(np.float64), ref)
+    assert e <= tol, e
+    assert f_rms <= tol, f_rms
+    assert f_max <= ELEMENT_FACTOR * tol, f_max
+    if virial:
+        assert virial_error(W.cpu().numpy(), ref) <= 10 * tol
+    return e, f_rms
+
+
+@pytest.mark.parametrize("act", ["tanh", "silu"])
+def test_energy_forces_config1(act):
+    b, d, p = synth.config(1, activation=act)
+    _ef_parity(b, d, p)
+
+
+def test_energy_forces_ragged_li3po4_batch(li_small):
+    b, d, p = li_small
+    _ef_parity(b, d, p)
+
+
+def test_energy_forces_config2_h512():
+    b, d, p = synth.config(2)
+    _ef_parity(b, d, p)
+
+
+def test_energy_forces_emim_batch_with_empty_structure():
+    b4, d, p = synth.config(4)
+    b = subset(b4, [0, 3, 5])
+    empty = (np.zeros((0, 3)), np.zeros(0, np.int32), 12.0 * np.eye(3))
+    structs = [(b.pos[b.atom_ptr[k]:b.atom_ptr[k + 1]], b.species[b.atom_ptr[k]:b.atom_ptr[k + 1]], b.cell[k])
+               for k in range(b.n_structures)]
+    b = make_batch(structs[:1] + [empty] + structs[1:], 5)
+    _ef_parity(b, d, p)
+
+
+def test_descriptors_match_oracle():
+    b, d, p = synth.config(1)
+    m, sysd, nl = _nl_pair(b, d, p)
+    psi, G = m.descriptors(sysd, nl)
+    m.check_status()
+    ref = oracle.energy_forces(b, d, p, oracle.neighbors(b, d["r_cut"]), psi=True, features=True)
+    scale_psi = np.abs(ref["psi"]).max()
+    assert np.abs(psi.cpu().numpy() - ref["psi"]).max() <= 1e-5 * scale_psi
+    for lo, hi in ((0, 5), (5, 20), (20, 35), (35, 50), (50, 85), (85, 160), (160, 235), (235, 360)):
+        g, r = G.cpu().numpy()[:, lo:hi], ref["G"][:, lo:hi]
+        assert np.abs(g - r).max() <= 1e-5 * np.abs(r).max(), (lo, hi)
+
+
+def test_energy_forces_deterministic_energy():
+    b, d, p = synth.config(1)
+    m, sysd, nl = _nl_pair(b, d, p)
+    E1, _, _ = m.energy_forces(sysd, nl)
+    E2, _, _ = m.energy_forces(sysd, nl)
+    assert float(E1.item()) == float(E2.item())
+
+
+# ------------------------------------------------------------------ full size
+
+def test_full_size_li3po4_sampled_rows_and_properties():
+    """131,072 atoms (launch configuration of the benchmark): the neighbour rows and the
+    descriptors of 48 sampled atoms equal the oracle's; every pair has its mirror
+    (j, i, -n); the net force vanishes."""
+    b, d, p = synth.config(5)
+    m, sysd, nl = _nl_pair(b, d, p)
+    E, F, _ = m.energy_forces(sysd, nl)
+    m.check_status()
+    psi, G = m.descriptors(sysd, nl)
+    m.check_status()
+    rows = np.sort(np.random.default_rng(9).choice(b.n_atoms, 48, replace=False))
+    t = nl.triples()
+    onl = oracle.neighbor_rows(b, d["r_cut"], rows)
+    assert np.array_equal(t[np.isin(t[:, 0], rows)], onl.triples())
+    opsi, oG = oracle.descriptors(b, d, p, onl, rows)
+    assert np.abs(psi.cpu().numpy()[rows] - opsi).max() <= 1e-5 * np.abs(opsi).max()
+    assert np.abs(G.cpu().numpy()[rows] - oG).max() <= 1e-5 * np.abs(oG).max()
+    mirror = np.column_stack([t[:, 1], t[:, 0], -t[:, 2], -t[:, 3], -t[:, 4]])
+    mirror = mirror[np.lexsort(mirror.T[::-1])]
+    assert np.array_equal(t, mirror)
+    Fn = F.cpu().numpy().astype(np.float64)
+    assert np.abs(Fn.sum(0)).max() <= 1e-4 * np.sqrt((Fn ** 2).mean()) * np.sqrt(b.n_atoms)
+    assert np.isfinite(E.cpu().numpy()).all()

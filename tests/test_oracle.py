@@ -411,3 +411,17 @@ def test_param_grad_matches_finite_differences(cfg1):
                 vals.append(_loss_value(b, d, p2, nl, Eref, Fref)[0])
             fd = (vals[0] - vals[1]) / (2 * h)
             assert abs(fd - flat[e]) <= 1e-5 * np.abs(flat).max() + 1e-12, (k, e, fd, flat[e])
+
+
+def test_row_subset_functions_agree_with_full_oracle(cfg1):
+    """The sampled-row neighbour list and descriptors used for full-size checks are the
+    rows of the full oracle, bit for bit."""
+    b, d, p = cfg1
+    nl = oracle.neighbors(b, d["r_cut"])
+    rows = [0, 13, 50, 95]
+    part = oracle.neighbor_rows(b, d["r_cut"], rows)
+    full = nl.triples()
+    assert np.array_equal(full[np.isin(full[:, 0], rows)], part.triples())
+    psi, G = oracle.descriptors(b, d, p, part, rows)
+    ref = oracle.energy_forces(b, d, p, nl, psi=True, features=True)
+    assert np.array_equal(psi, ref["psi"][rows]) and np.array_equal(G, ref["G"][rows])
