@@ -1,0 +1,416 @@
+#!/usr/bin/env python
+"""Energy+force throughput of the B300 GMNN path (atom-steps/s).
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+One step = the whole hot path on one batch: cell-list neighbour rebuild, moments,
+contractions, network forward and backward, forces, FP64 energy/virial reductions.
+Headline workload: the 1536-atom EMIM+BF4- box (64 ion pairs, r_cut 6 A, MLP 2x512)
+with a seeded 0.01 A random walk of the positions every step; the 131,072-atom Li3PO4
+box is reported under "variants".  Each timed step is bracketed by CUDA events on the
+library's stream; a 256 MiB buffer is written between timed steps (outside the events)
+to flush L2.  Under torchrun every rank runs its own replica (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "energy+force atom-steps/s at 1.5k & 131k atoms; mixed vs plain FP32 path"
+UNIT = "atom-steps/s"
+FP32_ALU_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # 148 SMs x 128 FP32 lanes x FMA x 2.032 GHz
+FLUSH_BYTES = 256 << 20
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ----------------------------------------------------------------------------- workloads
+
+WORKLOADS = {
+    2: "emim-64pairs-1536 (configs[1]: EMIM+BF4-, 1536 atoms, L=25.43 A, r_cut 6 A, MLP 2x512, 0.01 A jitter/step)",
+    5: "li3po4-131072 (configs[4]: Li3PO4-like crystal, 131072 atoms, L=109.49 A, r_cut 6 A, MLP 2x512)",
+}
+
+
+def jitter_path(batch, seed, steps, sigma=0.01):
+    """Positions for `steps` consecutive steps of a seeded random walk (host, FP64)."""
+    rng = np.random.default_rng([seed, 51])
+    pos = np.empty((steps,) + batch.pos.shape)
+    cur = batch.pos.copy()
+    for k in range(steps):
+        cur = cur + rng.normal(0.0, sigma, cur.shape)
+        pos[k] = cur
+    return pos
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = Path(tempfile.mkstemp(prefix="gm_clocks_", suffix=".csv")[1])
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for line in self.path.read_text().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        self.path.unlink(missing_ok=True)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[q] for r in rows for q in range(4) if r[5 + q].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
+
+
+# ----------------------------------------------------------------------------- roofline
+
+def algorithmic_work(stage, n_atoms, n_pairs, H):
+    """(amount, unit) of algorithmic work of one launch of a stage; see the design doc."""
+    F = 360
+    if stage == "gemm_l1" or stage == "gemm_b0":
+        return 2.0 * n_atoms * F * H, "flop"
+    if stage == "gemm_l2" or stage == "gemm_b1":
+        return 2.0 * n_atoms * H * H, "flop"
+    if stage == "moments":
+        return 330.0 * n_pairs, "flop"
+    if stage == "forces":
+        return 800.0 * n_pairs, "flop"
+    if stage == "contract_fwd":
+        return 8.8e3 * n_atoms, "flop"
+    if stage == "contract_bwd":
+        return 2.8e4 * n_atoms, "flop"
+    if stage == "neighbors":
+        # positions in, sorted copies, CSR out (col 4 B + shift 4 B per pair)
+        return 24.0 * n_atoms * 3 + 8.0 * n_pairs + 4.0 * n_atoms, "byte"
+    if stage == "reduce":
+        return 4.0 * n_atoms * (H // 64 + 2), "byte"
+    return 0.0, "flop"
+
+
+def roofline(stages, n_atoms, n_pairs, H, precision, peaks, sustained):
+    busy = {k: v for k, v in stages.items() if v[1] > 0}
+    if not busy:
+        return None, {}
+    per = {k: v[0] / v[1] for k, v in busy.items()}
+    total = sum(v[0] for v in busy.values())
+    share = {k: round(v[0] / total, 4) for k, v in busy.items()}
+    top = max(per, key=lambda k: busy[k][0])
+    work, unit = algorithmic_work(top, n_atoms, n_pairs, H)
+    sec = per[top] / 1e3
+    if unit == "byte":
+        achieved = work / sec / 1e9
+        peak = peaks.get("hbm_gbs", 6400.0)
+        out = {"bound": "hbm", "unit": "GB/s", "peak_source": "measured hbm_gbs" if "hbm_gbs" in peaks else "fallback"}
+    elif top.startswith("gemm") and precision == "mixed":
+        achieved = work / sec / 1e12
+        key = "bf16_tflops_sustained" if sustained else "bf16_tflops"
+        peak = peaks.get(key, 1400.0 if sustained else 1800.0)
+        out = {"bound": "tensor", "unit": "TFLOP/s", "peak_source": f"measured {key}" if key in peaks else "fallback"}
+    else:
+        achieved = work / sec / 1e12
+        peak = FP32_ALU_PEAK_TFLOPS
+        out = {"bound": "alu", "unit": "TFLOP/s",
+               "peak_source": "derived: 148 SMs x 128 FP32 FMA/clk x 2 flop x 2032 MHz"}
+    out.update({"kernel": top, "achieved": round(achieved, 3), "peak": round(peak, 2),
+                "frac": round(achieved / peak, 4), "traffic": None, "ms_per_launch": round(per[top], 5),
+                "algorithmic_work_per_launch": work, "work_unit": unit})
+    return out, share
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def run_gpu(args, cfg, precision, steps, warmup, world, rank, measure_e2e, clock_sampler=None):
+    import torch
+
+    import synth
+    from paper_2505_22168_b300 import GMNN, DeviceSystem, _lib
+
+    batch, desc, params = synth.config(cfg)
+    model = GMNN(desc, params, precision=precision)
+    sysd = DeviceSystem(batch)
+    nl = model.build_neighbors(sysd)
+    path = jitter_path(batch, 7000 + cfg, warmup + steps) if cfg == 2 else None
+    n = batch.n_atoms
+    if path is not None:
+        pos_dev = [torch.as_tensor(path[k], device=model.device) for k in range(warmup + steps)]
+    else:
+        pos_dev = [sysd.pos] * (warmup + steps)
+    # capacity with headroom for the jitter (checked after the run)
+    cap = int(nl.capacity * 1.05) + 1024
+    from paper_2505_22168_b300 import NeighborList
+    nl = NeighborList(n, cap, model.device)
+    out = (torch.empty(batch.n_structures, dtype=torch.float64, device=model.device),
+           torch.empty(n, 3, dtype=torch.float32, device=model.device), None)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=model.device)
+    stream = torch.cuda.current_stream()
+
+    def step(k):
+        sysd.pos = pos_dev[k]
+        model.clear_status()
+        model.build_neighbors(sysd, nl, check=False)
+        model.energy_forces(sysd, nl, out=out, clear=False)
+
+    for k in range(warmup):
+        step(k)
+    stream.synchronize()
+    if model.read_status() != 0:
+        raise RuntimeError(f"device status {model.read_status()} during warm-up")
+    n_pairs = int(nl.n_pairs.item())
+
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    stream.synchronize()
+    _lib.gm_profile_reset()
+    _lib.gm_profile_enable(args.stage_timing)
+    if clock_sampler is not None:
+        clock_sampler.__enter__()
+    for k in range(steps):
+        flush.zero_()
+        ev0[k].record(stream)
+        step(warmup + k)
+        ev1[k].record(stream)
+    stream.synchronize()
+    if clock_sampler is not None:
+        clock_sampler.__exit__(None, None, None)
+    _lib.gm_profile_enable(False)
+    stages, launches = _lib.gm_profile_collect()
+    status = model.read_status()
+    if status != 0:
+        raise RuntimeError(f"device status {_lib.STATUS_NAMES.get(status, status)} in the timed region")
+    ms = sum(ev0[k].elapsed_time(ev1[k]) for k in range(steps))
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device=model.device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    res = {"ms_total": ms, "ms_per_step": ms / steps, "n_atoms": n, "n_pairs": n_pairs, "stages": stages,
+           "launches": launches, "H": desc["n_hidden"], "value": world * n * steps / (ms / 1e3)}
+
+    if measure_e2e:
+        # end to end through the public API with host buffers: pinned positions in,
+        # energies and forces out, copies inside the timed region
+        e2e_steps = min(steps, 30)
+        host_pos = [torch.as_tensor(path[warmup + k] if path is not None else batch.pos).pin_memory()
+                    for k in range(e2e_steps)]
+        E_host = torch.empty(batch.n_structures, dtype=torch.float64).pin_memory()
+        F_host = torch.empty(n, 3, dtype=torch.float32).pin_memory()
+        pos_buf = torch.empty_like(sysd.pos)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(e2e_steps):
+            pos_buf.copy_(host_pos[k], non_blocking=True)
+            sysd.pos = pos_buf
+            model.clear_status()
+            model.build_neighbors(sysd, nl, check=False)
+            model.energy_forces(sysd, nl, out=out, clear=False)
+            E_host.copy_(out[0], non_blocking=True)
+            F_host.copy_(out[1], non_blocking=True)
+            stream.synchronize()
+        wall = time.perf_counter() - t0
+        if model.read_status() != 0:
+            raise RuntimeError("device status set during the end-to-end run")
+        res["e2e"] = {"value": world * n * e2e_steps / wall, "unit": UNIT,
+                      "h2d_bytes_per_step": int(host_pos[0].numel() * 8),
+                      "d2h_bytes_per_step": int(E_host.numel() * 8 + F_host.numel() * 4), "steps": e2e_steps}
+    del pos_dev, flush
+    return res
+
+
+# ----------------------------------------------------------------------------- CPU (oracle)
+
+def oracle_step_seconds(cfg, budget_s, max_evals=None):
+    """Time the FP64 oracle (brute-force neighbours + energy/forces) on the workload's
+    structure; repeats until budget_s of CPU time or max_evals evaluations."""
+    import oracle
+    import synth
+
+    batch, desc, params = synth.config(cfg)
+    oracle.build()
+    times = []
+    t_start = time.perf_counter()
+    while True:
+        t0 = time.perf_counter()
+        nl = oracle.neighbors(batch, desc["r_cut"])
+        oracle.energy_forces(batch, desc, params, nl, virial=True)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_start >= budget_s or (max_evals and len(times) >= max_evals):
+            break
+    return batch.n_atoms, times, oracle.num_threads()
+
+
+def cpu_baseline(cfg, budget_s):
+    n, times, threads = oracle_step_seconds(cfg, budget_s)
+    value = n * len(times) / sum(times)
+    return {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{len(times)} full evaluations (brute-force neighbours + E/F/virial, FP64) of the "
+                      f"{n}-atom workload, {sum(times):.1f} s on {threads} OpenMP threads"}
+
+
+# ----------------------------------------------------------------------------- main
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["auto", "fp32", "mixed"], default="auto")
+    ap.add_argument("--config", type=int, choices=[2, 5], default=2)
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--stage-timing", type=int, default=1)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        n, times, threads = oracle_step_seconds(args.config, budget_s=1e9, max_evals=args.warmup + args.steps)
+        timed = times[args.warmup:] if len(times) > args.warmup else times
+        value = n * len(timed) / sum(timed)
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": len(timed), "warmup": args.warmup, "ms_per_step": 1e3 * sum(timed) / len(timed),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": WORKLOADS[args.config], "path": "FP64 CPU oracle (plain C + OpenMP)"},
+                "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                 "sample": f"{len(timed)} timed full evaluations of the {n}-atom workload"},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    else:
+        torch.cuda.set_device(0)
+
+    from paper_2505_22168_b300 import build
+    build.build()
+    precision = args.precision
+    if precision == "auto":
+        precision = "mixed" if _mixed_available() else "fp32"
+
+    peaks = {}
+    pk = ROOT / "MEASURED_PEAKS.json"
+    if pk.exists():
+        peaks = json.loads(pk.read_text())
+
+    sampler = ClockSampler(local_rank)
+    head = run_gpu(args, args.config, precision, args.steps, args.warmup, world, rank, True, sampler)
+    clocks = sampler.summary()
+    roof, share = roofline(head["stages"], head["n_atoms"], head["n_pairs"], head["H"], precision, peaks,
+                           sustained=False)
+
+    variants = []
+    if not args.no_variants:
+        for cfg in (2, 5):
+            for prec in ("fp32", "mixed"):
+                if (cfg, prec) == (args.config, precision):
+                    continue
+                if prec == "mixed" and not _mixed_available():
+                    continue
+                steps = max(5, args.steps // (5 if cfg == 5 else 1))
+                r = run_gpu(args, cfg, prec, steps, args.warmup, world, rank, False)
+                rf, sh = roofline(r["stages"], r["n_atoms"], r["n_pairs"], r["H"], prec, peaks, sustained=False)
+                variants.append({"workload": WORKLOADS[cfg], "precision": prec, "value": r["value"], "unit": UNIT,
+                                 "ms_per_step": r["ms_per_step"], "steps": steps, "n_pairs": r["n_pairs"],
+                                 "dominant": rf["kernel"] if rf else None, "roofline_frac": rf["frac"] if rf else None,
+                                 "stage_share": sh})
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.config, args.cpu_seconds)
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    line = {
+        "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16+f32" if precision == "mixed" else "f32", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.config], "precision": precision, "n_atoms": head["n_atoms"],
+                   "n_pairs": head["n_pairs"], "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "256 MiB buffer written between timed steps (outside the step events)",
+                   "neighbour_rebuild": "every step", "stage_timing_events": bool(args.stage_timing)},
+        "roofline": roof, "stage_share": share, "cpu_baseline": cpu, "e2e": head.get("e2e"),
+        "gpu_launches": head["launches"], "clocks": clocks, "variants": variants,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def _mixed_available():
+    try:
+        from paper_2505_22168_b300 import _lib
+        return bool(getattr(_lib, "MIXED_AVAILABLE", False))
+    except Exception:
+        return False
+
+
+if __name__ == "__main__":
+    main()

@@ -176,6 +176,18 @@ GM_API gm_status gm_descriptors(const gm_model *m, const gm_system *sys, const g
                          float *features, void *ws, size_t ws_bytes, int32_t *status_dev,
                          struct CUstream_st *stream);
 
+/* Stage timing (the library's built-in tracing).  While enabled, every pipeline stage
+ * of gm_build_neighbors / gm_energy_forces / gm_param_grad is bracketed by CUDA events
+ * recorded on the call's stream.  gm_profile_collect synchronises those events and
+ * returns, per stage, the summed milliseconds and the number of timed occurrences since
+ * the last reset, plus the number of kernels the library launched since the last reset
+ * (counted whether or not timing is enabled).  Stages are numbered 0..gm_profile_n_stages()-1. */
+GM_API void gm_profile_enable(int on);
+GM_API void gm_profile_reset(void);
+GM_API int gm_profile_n_stages(void);
+GM_API const char *gm_profile_stage_name(int stage);
+GM_API gm_status gm_profile_collect(double *stage_ms, int64_t *stage_count, int n_stages, int64_t *kernel_launches);
+
 /* Zero the device status word (cudaMemsetAsync on `stream`); call before each step. */
 GM_API gm_status gm_status_clear(int32_t *status_dev, struct CUstream_st *stream);
 

@@ -23,7 +23,8 @@ STATUS_NAMES = {0: "GM_OK", 1: "GM_ERR_ARG", 2: "GM_ERR_CAPACITY", 3: "GM_ERR_UN
 # every exported symbol of include/gm.h
 EXPORTS = ("gm_param_count", "gm_model_create", "gm_model_set_params", "gm_model_destroy", "gm_workspace_size",
            "gm_build_neighbors", "gm_energy_forces", "gm_param_grad", "gm_force_matching_loss", "gm_descriptors",
-           "gm_status_clear", "gm_status_string", "gm_last_error")
+           "gm_status_clear", "gm_status_string", "gm_last_error", "gm_profile_enable", "gm_profile_reset",
+           "gm_profile_n_stages", "gm_profile_stage_name", "gm_profile_collect")
 
 
 class GmModelDesc(ctypes.Structure):
@@ -81,6 +82,11 @@ def load():
         "gm_status_clear": (st, [_P, _P]),
         "gm_status_string": (ctypes.c_char_p, [st]),
         "gm_last_error": (ctypes.c_char_p, []),
+        "gm_profile_enable": (None, [ctypes.c_int]),
+        "gm_profile_reset": (None, []),
+        "gm_profile_n_stages": (ctypes.c_int, []),
+        "gm_profile_stage_name": (ctypes.c_char_p, [ctypes.c_int]),
+        "gm_profile_collect": (st, [_P, _P, ctypes.c_int, _P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -156,3 +162,24 @@ def gm_status_clear(status, stream):
 
 def gm_status_string(code: int) -> str:
     return load().gm_status_string(code).decode()
+
+
+def gm_profile_enable(on: bool):
+    load().gm_profile_enable(1 if on else 0)
+
+
+def gm_profile_reset():
+    load().gm_profile_reset()
+
+
+def gm_profile_collect():
+    """({stage name: (total ms, count)}, kernel launches since the last reset)."""
+    lib = load()
+    n = lib.gm_profile_n_stages()
+    ms = (ctypes.c_double * n)()
+    cnt = (ctypes.c_int64 * n)()
+    launches = ctypes.c_int64(0)
+    check(lib.gm_profile_collect(ctypes.addressof(ms), ctypes.addressof(cnt), n, ctypes.addressof(launches)),
+          "gm_profile_collect")
+    stages = {lib.gm_profile_stage_name(q).decode(): (ms[q], cnt[q]) for q in range(n)}
+    return stages, int(launches.value)

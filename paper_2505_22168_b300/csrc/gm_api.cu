@@ -14,7 +14,10 @@
 #include <stdio.h>
 #include <stdlib.h>
 
+#include <atomic>
+#include <mutex>
 #include <string>
+#include <vector>
 
 #include "gm_contract.h"
 #include "gm_gemm.h"
@@ -30,6 +33,50 @@ static gm_status fail(gm_status s, const char *msg) {
     g_last_error = msg;
     return s;
 }
+
+// ------------------------------------------------------------------ tracing
+namespace gm {
+static std::atomic<int64_t> g_launches{0};
+static std::atomic<bool> g_prof{false};
+static std::mutex g_prof_mu;
+struct PendingStage {
+    int stage;
+    cudaEvent_t a, b;
+};
+static std::vector<PendingStage> g_pending;
+static std::vector<cudaEvent_t> g_event_pool;
+static double g_stage_ms[N_STAGES];
+static int64_t g_stage_cnt[N_STAGES];
+
+static cudaEvent_t pool_event() {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_event_pool.empty()) {
+        cudaEvent_t e = g_event_pool.back();
+        g_event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void note_launches(int n) { g_launches += n; }
+
+StageScope::StageScope(int s, cudaStream_t stream) : stage(s), st(stream), ev0(nullptr) {
+    if (!g_prof) return;
+    cudaEvent_t e = pool_event();
+    cudaEventRecord(e, st);
+    ev0 = e;
+}
+
+StageScope::~StageScope() {
+    if (!ev0) return;
+    cudaEvent_t e = pool_event();
+    cudaEventRecord(e, st);
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_pending.push_back({stage, static_cast<cudaEvent_t>(ev0), e});
+}
+}  // namespace gm
 
 struct gm_model {
     gm_model_desc d;
@@ -285,6 +332,7 @@ gm_status gm_model_set_params(gm_model *m, const float *theta, struct CUstream_s
     ThetaOff o = theta_offsets(m->S, m->H);
     const float scale = (float)(1.0 / sqrt((double)NB));
     k_repack<<<296, 256, 0, stream>>>(theta, o, m->S, m->H, scale, *m);
+    note_launches(1);
     return launch_status();
 }
 
@@ -312,7 +360,10 @@ gm_status gm_build_neighbors(const gm_model *m, const gm_system *sys, gm_nlist *
     if ((s = check_nlist(sys, nl, false)) != GM_OK) return s;
     if (!status) return fail(GM_ERR_ARG, "null status");
     if (ws_bytes < nl_workspace_bytes(sys->n_structures, sys->n_atoms)) return fail(GM_ERR_WORKSPACE, "workspace too small");
-    s = nl_build(*sys, m->d.r_cut, m->S, *nl, ws, ws_bytes, status, stream);
+    {
+        StageScope sc(ST_NEIGHBORS, stream);
+        s = nl_build(*sys, m->d.r_cut, m->S, *nl, ws, ws_bytes, status, stream);
+    }
     if (s != GM_OK) return fail(s, "neighbour build launch failed");
     return launch_status();
 }
@@ -323,8 +374,14 @@ static gm_status forward_to_features(const gm_model *m, const gm_system *sys, co
     const int Mp = round_up(N, TILE_M);
     PairArgs a = pair_args(m, sys, nl, status);
     float *psi = psi_out ? psi_out : w.psi;
-    launch_moments(a, choose_tpa(m, N), psi, st);
-    launch_contract_fwd_f32(psi, N, Mp, w.G, features_out, st);
+    {
+        StageScope sc(ST_MOMENTS, st);
+        launch_moments(a, choose_tpa(m, N), psi, st);
+    }
+    {
+        StageScope sc(ST_CONTRACT_FWD, st);
+        launch_contract_fwd_f32(psi, N, Mp, w.G, features_out, st);
+    }
     w.psi = psi;
     return launch_status();
 }
@@ -352,7 +409,10 @@ gm_status gm_energy_forces(const gm_model *m, const gm_system *sys, const gm_nli
         e.bias = m->b1;
         e.out0 = w.A1;
         e.out1 = w.D1;
-        gemm_f32(EPI_L1, m->d.activation, w.G, m->W1t, Mp, H, NFP, e, st);
+        {
+            StageScope sc(ST_GEMM_L1, st);
+            gemm_f32(EPI_L1, m->d.activation, w.G, m->W1t, Mp, H, NFP, e, st);
+        }
         // L2
         e.bias = m->b2;
         e.w3 = m->w3;
@@ -360,20 +420,34 @@ gm_status gm_energy_forces(const gm_model *m, const gm_system *sys, const gm_nli
         e.out0 = w.dZ2;
         e.out1 = nullptr;
         e.nn_part = w.nn_part;
-        gemm_f32(EPI_L2, m->d.activation, w.A1, m->W2t, Mp, H, H, e, st);
+        {
+            StageScope sc(ST_GEMM_L2, st);
+            gemm_f32(EPI_L2, m->d.activation, w.A1, m->W2t, Mp, H, H, e, st);
+        }
         // B1
         e.out0 = w.dZ1;
         e.aux = w.D1;
-        gemm_f32(EPI_B1, 0, w.dZ2, m->W2, Mp, H, H, e, st);
+        {
+            StageScope sc(ST_GEMM_B1, st);
+            gemm_f32(EPI_B1, 0, w.dZ2, m->W2, Mp, H, H, e, st);
+        }
         // B0
         e.out0 = w.dG;
-        gemm_f32(EPI_STORE, 0, w.dZ1, m->W1p, Mp, NFP, H, e, st);
-        launch_contract_bwd(w.psi, w.dG, N, w.dpsi, st);
+        {
+            StageScope sc(ST_GEMM_B0, st);
+            gemm_f32(EPI_STORE, 0, w.dZ1, m->W1p, Mp, NFP, H, e, st);
+        }
+        {
+            StageScope sc(ST_CONTRACT_BWD, st);
+            launch_contract_bwd(w.psi, w.dG, N, w.dpsi, st);
+        }
         if (cudaMemsetAsync(forces, 0, sizeof(float) * 3 * (size_t)N, st) != cudaSuccess)
             return fail(GM_ERR_CUDA, "memset of forces failed");
         PairArgs a = pair_args(m, sys, nl, status);
+        StageScope sc(ST_FORCES, st);
         launch_forces(a, choose_tpa(m, N), w.dpsi, forces, virial ? w.vir_atom : nullptr, st);
     }
+    StageScope sc(ST_REDUCE, st);
     launch_struct_reduce(B, sys->atom_ptr, sys->species, m->S, m->sigma, m->mu, m->b3, w.nn_part, H / 64,
                          virial ? w.vir_atom : nullptr, energy, virial, st);
     return launch_status();
@@ -411,6 +485,51 @@ gm_status gm_force_matching_loss(const gm_system *sys, const double *energy, con
     launch_loss(sys->n_structures, sys->n_atoms, sys->atom_ptr, energy, energy_ref, forces, forces_ref, w_energy,
                 w_forces, loss, dL_dE, dL_dF, stream);
     return launch_status();
+}
+
+void gm_profile_enable(int on) { g_prof = on != 0; }
+
+void gm_profile_reset(void) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (auto &p : g_pending) {
+        g_event_pool.push_back(p.a);
+        g_event_pool.push_back(p.b);
+    }
+    g_pending.clear();
+    for (int q = 0; q < N_STAGES; ++q) {
+        g_stage_ms[q] = 0.0;
+        g_stage_cnt[q] = 0;
+    }
+    g_launches = 0;
+}
+
+int gm_profile_n_stages(void) { return N_STAGES; }
+
+const char *gm_profile_stage_name(int s) {
+    static const char *names[N_STAGES] = {"neighbors", "moments", "contract_fwd", "gemm_l1", "gemm_l2",
+                                          "gemm_b1", "gemm_b0", "contract_bwd", "forces", "reduce",
+                                          "pg_pair_fwd", "pg_network", "pg_pair_bwd"};
+    return (s >= 0 && s < N_STAGES) ? names[s] : "";
+}
+
+gm_status gm_profile_collect(double *stage_ms, int64_t *stage_count, int n_stages, int64_t *kernel_launches) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (auto &p : g_pending) {
+        float ms = 0.0f;
+        if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            g_stage_ms[p.stage] += ms;
+            g_stage_cnt[p.stage] += 1;
+        }
+        g_event_pool.push_back(p.a);
+        g_event_pool.push_back(p.b);
+    }
+    g_pending.clear();
+    for (int q = 0; q < n_stages && q < N_STAGES; ++q) {
+        if (stage_ms) stage_ms[q] = g_stage_ms[q];
+        if (stage_count) stage_count[q] = g_stage_cnt[q];
+    }
+    if (kernel_launches) *kernel_launches = g_launches;
+    return GM_OK;
 }
 
 gm_status gm_status_clear(int32_t *status, struct CUstream_st *stream) {

@@ -425,14 +425,20 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_contract_bwd(const float *__r
 void launch_contract_fwd_f32(const float *psi, int N, int Mp, float *G, float *features_out, cudaStream_t st) {
     const int blocks = (Mp + CT_ATOMS - 1) / CT_ATOMS;
     const size_t smem = sizeof(float) * CT_ATOMS * GT_STRIDE;
-    if (blocks > 0) k_contract_fwd<float><<<blocks, CT_THREADS, smem, st>>>(psi, N, Mp, G, features_out);
+    if (blocks > 0) {
+        k_contract_fwd<float><<<blocks, CT_THREADS, smem, st>>>(psi, N, Mp, G, features_out);
+        note_launches(1);
+    }
 }
 
 void launch_contract_fwd_bf16(const float *psi, int N, int Mp, __nv_bfloat16 *G, float *features_out,
                               cudaStream_t st) {
     const int blocks = (Mp + CT_ATOMS - 1) / CT_ATOMS;
     const size_t smem = sizeof(float) * CT_ATOMS * GT_STRIDE;
-    if (blocks > 0) k_contract_fwd<__nv_bfloat16><<<blocks, CT_THREADS, smem, st>>>(psi, N, Mp, G, features_out);
+    if (blocks > 0) {
+        k_contract_fwd<__nv_bfloat16><<<blocks, CT_THREADS, smem, st>>>(psi, N, Mp, G, features_out);
+        note_launches(1);
+    }
 }
 
 void launch_contract_bwd(const float *psi, const float *dG, int N, float *dpsi, cudaStream_t st) {
@@ -443,7 +449,10 @@ void launch_contract_bwd(const float *psi, const float *dG, int N, float *dpsi, 
         cudaFuncSetAttribute(k_contract_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
-    if (blocks > 0) k_contract_bwd<<<blocks, CT_THREADS, smem, st>>>(psi, dG, N, dpsi);
+    if (blocks > 0) {
+        k_contract_bwd<<<blocks, CT_THREADS, smem, st>>>(psi, dG, N, dpsi);
+        note_launches(1);
+    }
 }
 
 }  // namespace gm

@@ -39,6 +39,20 @@ struct NlStruct {
     float eps2;      // half-width of the FP32 band around r_cut^2 decided in FP64
 };
 
+// ---- tracing (gm_api.cu): kernel-launch counter and stage timing
+enum Stage {
+    ST_NEIGHBORS = 0, ST_MOMENTS, ST_CONTRACT_FWD, ST_GEMM_L1, ST_GEMM_L2, ST_GEMM_B1, ST_GEMM_B0,
+    ST_CONTRACT_BWD, ST_FORCES, ST_REDUCE, ST_PG_PAIR_FWD, ST_PG_NETWORK, ST_PG_PAIR_BWD, N_STAGES
+};
+void note_launches(int n);
+struct StageScope {
+    int stage;
+    cudaStream_t st;
+    void *ev0;
+    StageScope(int s, cudaStream_t stream);
+    ~StageScope();
+};
+
 // ---- neighbour search (gm_nlist.cu)
 size_t nl_workspace_bytes(int n_struct, int n_atoms);
 gm_status nl_build(const gm_system &sys, double r_cut, int n_species, gm_nlist &nl, void *ws, size_t ws_bytes,

@@ -94,6 +94,7 @@ void exclusive_scan(const int32_t *in, int32_t *out, int n, int32_t *tmp, cudaSt
     if (nb > 0) k_scan_local<<<nb, SCAN_THREADS, 0, st>>>(in, out, n, tmp);
     k_scan_sums<<<1, 1024, 0, st>>>(tmp, nb, out + n);
     if (nb > 0) k_scan_add<<<nb, SCAN_THREADS, 0, st>>>(out, n, tmp);
+    note_launches(nb > 0 ? 3 : 1);
 }
 
 // ------------------------------------------------------------------ setup
@@ -358,10 +359,12 @@ gm_status nl_build(const gm_system &sys, double r_cut, int n_species, gm_nlist &
     if (cudaMemsetAsync(w.ccount, 0, sizeof(int32_t) * ncmax, st) != cudaSuccess) return GM_ERR_CUDA;
     if (cudaMemsetAsync(w.cfill, 0, sizeof(int32_t) * ncmax, st) != cudaSuccess) return GM_ERR_CUDA;
     k_nl_setup<<<1, 1024, 0, st>>>(B, sys.atom_ptr, sys.cell, sys.pbc, r_cut, w.S, status);
+    note_launches(1);
     const int tb = 256;
     if (N > 0) {
         k_nl_bin<<<(N + tb - 1) / tb, tb, 0, st>>>(N, B, sys.atom_ptr, sys.pos, sys.species, n_species, w.S, w.sid,
                                                    w.xw, w.mimg, w.cellid, w.ccount, status);
+        note_launches(1);
     }
     exclusive_scan(w.ccount, w.cstart, ncmax, w.scan_tmp, st);
     if (N > 0) {
@@ -376,9 +379,11 @@ gm_status nl_build(const gm_system &sys, double r_cut, int n_species, gm_nlist &
         k_nl_search<true><<<(N + tb - 1) / tb, tb, 0, st>>>(N, w.S, w.sid, w.cellid, w.cstart, w.xs, w.xw, w.mimg,
                                                             r_cut, rc2f, nullptr, nl.row_ptr, nl.capacity, nl.col,
                                                             reinterpret_cast<char4 *>(nl.shift), status);
+        note_launches(5);
     } else {
         exclusive_scan(w.counts, nl.row_ptr, 0, w.scan_tmp, st);
         k_nl_total<<<1, 1, 0, st>>>(nl.row_ptr, nl.capacity, nl.n_pairs, status);
+        note_launches(1);
     }
     return cudaPeekAtLastError() == cudaSuccess ? GM_OK : GM_ERR_CUDA;
 }

@@ -215,7 +215,10 @@ static void launch_moments_t(const PairArgs &a, float *psi, cudaStream_t st) {
     const long long total = (long long)a.N * TPA;
     const int blocks = (int)((total + threads - 1) / threads);
     const size_t smem = sizeof(float) * a.S * a.S * NR * NB;
-    if (blocks > 0) k_moments<TPA><<<blocks, threads, smem, st>>>(a, psi);
+    if (blocks > 0) {
+        k_moments<TPA><<<blocks, threads, smem, st>>>(a, psi);
+        note_launches(1);
+    }
 }
 
 template <int TPA>
@@ -224,7 +227,10 @@ static void launch_forces_t(const PairArgs &a, const float *dpsi, float *F, floa
     const long long total = (long long)a.N * TPA;
     const int blocks = (int)((total + threads - 1) / threads);
     const size_t smem = sizeof(float) * a.S * a.S * NR * NB;
-    if (blocks > 0) k_forces<TPA><<<blocks, threads, smem, st>>>(a, dpsi, F, vir);
+    if (blocks > 0) {
+        k_forces<TPA><<<blocks, threads, smem, st>>>(a, dpsi, F, vir);
+        note_launches(1);
+    }
 }
 
 void launch_moments(const PairArgs &a, int tpa, float *psi, cudaStream_t st) {

@@ -59,9 +59,11 @@ __global__ void __launch_bounds__(256) k_struct_reduce(int B, const int32_t *__r
 void launch_struct_reduce(int B, const int32_t *atom_ptr, const int32_t *species, int S, const float *sigma,
                           const float *mu, const float *b3, const float *nn_part, int nparts, const float *vir_atom,
                           double *energy, double *virial, cudaStream_t st) {
-    if (B > 0)
+    if (B > 0) {
         k_struct_reduce<<<B, 256, 0, st>>>(B, atom_ptr, species, S, sigma, mu, b3, nn_part, nparts, vir_atom, energy,
                                            virial);
+        note_launches(1);
+    }
 }
 
 // Force-matching loss: one block; FP64 accumulation in a fixed order.
@@ -92,6 +94,7 @@ __global__ void __launch_bounds__(1024) k_loss(int B, int N, const int32_t *__re
 void launch_loss(int B, int N, const int32_t *atom_ptr, const double *E, const double *Eref, const float *F,
                  const float *Fref, double wE, double wF, double *loss, double *gE, float *gF, cudaStream_t st) {
     k_loss<<<1, 1024, 0, st>>>(B, N, atom_ptr, E, Eref, F, Fref, wE, wF, loss, gE, gF);
+    note_launches(1);
 }
 
 }  // namespace gm
