@@ -151,6 +151,25 @@ GM_API gm_status gm_energy_forces(const gm_model *m, const gm_system *sys, const
                            float *forces, double *virial, void *ws, size_t ws_bytes, int32_t *status_dev,
                            struct CUstream_st *stream);
 
+/* Neighbour search that allocates nothing and needs no workspace (the paper has no
+ * counterpart; this is a convenience of this library).  Same inputs, outputs, rule and
+ * status reporting as gm_build_neighbors, for callers that cannot hand the library
+ * device memory: host programs whose own allocator owns all device memory (an MD engine
+ * embedding the library), or step loops that must not call cudaMalloc because its
+ * implicit synchronisation would stall the other streams mid-step.
+ * Scratch is a fixed 8 MiB array in the library's own device memory (a file-scope
+ * __device__ variable that every GPU loading the library holds until the process exits),
+ * which fits systems of up to about 100,000 atoms: exactly, those whose
+ * gm_workspace_size(..., GM_OP_NEIGHBORS) is at most 8 MiB.  Larger systems return
+ * GM_ERR_WORKSPACE (gm_last_error says why) without launching anything.
+ * The first call on a device, with that device current, looks up the array's device
+ * address (cudaGetSymbolAddress) and caches it; make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents (the build
+ * clears what must start at zero), so calls that overlap on the GPU -- concurrent
+ * streams or threads -- race; serialise them. */
+GM_API gm_status gm_build_neighbors_noalloc(const gm_model *m, const gm_system *sys, gm_nlist *nl,
+                                            int32_t *status_dev, struct CUstream_st *stream);
+
 /* Parameter gradient of a loss through energies and forces:
  *   grad_theta = d/dtheta [ sum_b dL_dE[b] E_b + sum_i dL_dF[i] . F_i ]
  * (section "Training": loss terms on energies and forces).  dL_dE device [B] FP64,

@@ -269,6 +269,11 @@ gm_status launch_status() {
 
 }  // namespace
 
+namespace gm {
+const gm_model_desc *model_desc(const gm_model *m) { return &m->d; }
+gm_status set_last_error(gm_status s, const char *msg) { return fail(s, msg); }
+}  // namespace gm
+
 extern "C" {
 
 int64_t gm_param_count(const gm_model_desc *d) {

@@ -53,6 +53,10 @@ struct StageScope {
     ~StageScope();
 };
 
+// ---- model and error accessors (gm_api.cu)
+const gm_model_desc *model_desc(const gm_model *m);
+gm_status set_last_error(gm_status s, const char *msg);
+
 // ---- neighbour search (gm_nlist.cu)
 size_t nl_workspace_bytes(int n_struct, int n_atoms);
 gm_status nl_build(const gm_system &sys, double r_cut, int n_species, gm_nlist &nl, void *ws, size_t ws_bytes,
