@@ -385,10 +385,88 @@ static gm_status forward_to_features(const gm_model *m, const gm_system *sys, co
     }
     {
         StageScope sc(ST_CONTRACT_FWD, st);
-        launch_contract_fwd_f32(psi, N, Mp, w.G, features_out, st);
+        if (m->d.precision == GM_PREC_MIXED && features_out == nullptr)
+            launch_contract_fwd_bf16(psi, N, Mp, reinterpret_cast<__nv_bfloat16 *>(w.G), nullptr, st);
+        else
+            launch_contract_fwd_f32(psi, N, Mp, w.G, features_out, st);
     }
     w.psi = psi;
     return launch_status();
+}
+
+// The four network GEMMs: features -> energies (partial sums) and dE/dG.
+static gm_status network_fwd_bwd(const gm_model *m, const gm_system *sys, EfWs &w, int Mp, int32_t *status,
+                                 cudaStream_t st) {
+    const int H = m->H;
+    EpiArgs e{};
+    e.n_atoms = sys->n_atoms;
+    e.n_species = m->S;
+    e.species = sys->species;
+    e.w3 = m->w3;
+    e.sigma = m->sigma;
+    e.nn_part = w.nn_part;
+    if (m->d.precision == GM_PREC_MIXED) {
+        typedef __nv_bfloat16 bf;
+        bf *G = reinterpret_cast<bf *>(w.G), *A1 = reinterpret_cast<bf *>(w.A1), *D1 = reinterpret_cast<bf *>(w.D1);
+        bf *dZ2 = reinterpret_cast<bf *>(w.dZ2), *dZ1 = reinterpret_cast<bf *>(w.dZ1);
+        gm_status s;
+        e.bias = m->b1;
+        e.out0 = A1;
+        e.out1 = D1;
+        {
+            StageScope sc(ST_GEMM_L1, st);
+            if ((s = gemm_bf16(EPI_L1, m->d.activation, G, m->W1t_h, Mp, H, NFP, e, status, st)) != GM_OK)
+                return fail(s, "tcgen05 GEMM L1 failed");
+        }
+        e.bias = m->b2;
+        e.out0 = dZ2;
+        e.out1 = nullptr;
+        {
+            StageScope sc(ST_GEMM_L2, st);
+            if ((s = gemm_bf16(EPI_L2, m->d.activation, A1, m->W2t_h, Mp, H, H, e, status, st)) != GM_OK)
+                return fail(s, "tcgen05 GEMM L2 failed");
+        }
+        e.out0 = dZ1;
+        e.aux = D1;
+        {
+            StageScope sc(ST_GEMM_B1, st);
+            if ((s = gemm_bf16(EPI_B1, 0, dZ2, m->W2_h, Mp, H, H, e, status, st)) != GM_OK)
+                return fail(s, "tcgen05 GEMM B1 failed");
+        }
+        e.out0 = w.dG;
+        {
+            StageScope sc(ST_GEMM_B0, st);
+            if ((s = gemm_bf16(EPI_STORE, 0, dZ1, m->W1p_h, Mp, NFP, H, e, status, st)) != GM_OK)
+                return fail(s, "tcgen05 GEMM B0 failed");
+        }
+        return GM_OK;
+    }
+    e.bias = m->b1;
+    e.out0 = w.A1;
+    e.out1 = w.D1;
+    {
+        StageScope sc(ST_GEMM_L1, st);
+        gemm_f32(EPI_L1, m->d.activation, w.G, m->W1t, Mp, H, NFP, e, st);
+    }
+    e.bias = m->b2;
+    e.out0 = w.dZ2;
+    e.out1 = nullptr;
+    {
+        StageScope sc(ST_GEMM_L2, st);
+        gemm_f32(EPI_L2, m->d.activation, w.A1, m->W2t, Mp, H, H, e, st);
+    }
+    e.out0 = w.dZ1;
+    e.aux = w.D1;
+    {
+        StageScope sc(ST_GEMM_B1, st);
+        gemm_f32(EPI_B1, 0, w.dZ2, m->W2, Mp, H, H, e, st);
+    }
+    e.out0 = w.dG;
+    {
+        StageScope sc(ST_GEMM_B0, st);
+        gemm_f32(EPI_STORE, 0, w.dZ1, m->W1p, Mp, NFP, H, e, st);
+    }
+    return GM_OK;
 }
 
 gm_status gm_energy_forces(const gm_model *m, const gm_system *sys, const gm_nlist *nl, double *energy, float *forces,
@@ -397,7 +475,6 @@ gm_status gm_energy_forces(const gm_model *m, const gm_system *sys, const gm_nli
     if (s != GM_OK) return s;
     if ((s = check_nlist(sys, nl, true)) != GM_OK) return s;
     if (!energy || !status || (sys->n_atoms > 0 && !forces)) return fail(GM_ERR_ARG, "null output");
-    if (m->d.precision != GM_PREC_FP32) return fail(GM_ERR_UNSUPPORTED, "mixed precision path not available");
     const int N = sys->n_atoms, B = sys->n_structures, H = m->H;
     Carve c(ws, ws_bytes);
     EfWs w = carve_ef(c, N, H);
@@ -406,42 +483,7 @@ gm_status gm_energy_forces(const gm_model *m, const gm_system *sys, const gm_nli
     const int Mp = round_up(N, TILE_M);
     if (N > 0) {
         if ((s = forward_to_features(m, sys, nl, w, nullptr, nullptr, status, st)) != GM_OK) return s;
-        EpiArgs e{};
-        e.n_atoms = N;
-        e.n_species = m->S;
-        e.species = sys->species;
-        // L1
-        e.bias = m->b1;
-        e.out0 = w.A1;
-        e.out1 = w.D1;
-        {
-            StageScope sc(ST_GEMM_L1, st);
-            gemm_f32(EPI_L1, m->d.activation, w.G, m->W1t, Mp, H, NFP, e, st);
-        }
-        // L2
-        e.bias = m->b2;
-        e.w3 = m->w3;
-        e.sigma = m->sigma;
-        e.out0 = w.dZ2;
-        e.out1 = nullptr;
-        e.nn_part = w.nn_part;
-        {
-            StageScope sc(ST_GEMM_L2, st);
-            gemm_f32(EPI_L2, m->d.activation, w.A1, m->W2t, Mp, H, H, e, st);
-        }
-        // B1
-        e.out0 = w.dZ1;
-        e.aux = w.D1;
-        {
-            StageScope sc(ST_GEMM_B1, st);
-            gemm_f32(EPI_B1, 0, w.dZ2, m->W2, Mp, H, H, e, st);
-        }
-        // B0
-        e.out0 = w.dG;
-        {
-            StageScope sc(ST_GEMM_B0, st);
-            gemm_f32(EPI_STORE, 0, w.dZ1, m->W1p, Mp, NFP, H, e, st);
-        }
+        if ((s = network_fwd_bwd(m, sys, w, Mp, status, st)) != GM_OK) return s;
         {
             StageScope sc(ST_CONTRACT_BWD, st);
             launch_contract_bwd(w.psi, w.dG, N, w.dpsi, st);

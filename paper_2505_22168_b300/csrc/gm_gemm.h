@@ -32,4 +32,11 @@ struct EpiArgs {
 void gemm_f32(int epi, int act, const float *A, const float *B, int M, int N, int K, const EpiArgs &e,
               cudaStream_t st);
 
+// BF16 tcgen05 path (gm_gemm_tc.cu).  M % 128 == 0, N % 64 == 0, K % 64 == 0; A [M][K] and
+// B [N][K] BF16 with 16-byte aligned rows.  L1/L2/B1 outputs are BF16, STORE is FP32.
+// forced_bn = 0 picks the tile width from the problem size (64, 128 or 256 columns).
+gm_status gemm_bf16(int epi, int act, const __nv_bfloat16 *A, const __nv_bfloat16 *B, int M, int N, int K,
+                    const EpiArgs &e, int32_t *status, cudaStream_t st, int forced_bn = 0);
+int tc_choose_bn(int M, int N, int forced);
+
 }  // namespace gm

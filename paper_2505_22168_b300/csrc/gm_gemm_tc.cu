@@ -1,0 +1,117 @@
+// gm_gemm_tc.cu -- host side of the tcgen05 BF16 GEMM: TMA tensor maps, tile choice, launch.
+#include <cudaTypedefs.h>
+
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include "gm_gemm_tc.cuh"
+
+namespace gm {
+
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+using MapKey = std::tuple<const void *, int, int, int>;
+std::mutex g_map_mu;
+std::map<MapKey, CUtensorMap> g_maps;
+
+// 2-D BF16 tensor [rows][inner] (inner contiguous), box 64 x box_rows, 128-byte swizzle.
+bool tensor_map(const void *base, int inner, int rows, int box_rows, CUtensorMap *out) {
+    const MapKey key{base, inner, rows, box_rows};
+    std::lock_guard<std::mutex> lk(g_map_mu);
+    auto it = g_maps.find(key);
+    if (it != g_maps.end()) {
+        *out = it->second;
+        return true;
+    }
+    auto fn = encode_fn();
+    if (!fn) return false;
+    CUtensorMap m;
+    cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)inner * 2};
+    cuuint32_t box[2] = {(cuuint32_t)tc::BK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return false;
+    if (g_maps.size() > 256) g_maps.clear();
+    g_maps.emplace(key, m);
+    *out = m;
+    return true;
+}
+
+template <int BN, int EPI, int ACT>
+cudaError_t launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, int M, int N, int K, const EpiArgs &e,
+                      int32_t *status, cudaStream_t st) {
+    static bool attr_set = false;
+    const size_t smem = tc::smem_bytes_for(BN);
+    if (!attr_set) {
+        cudaError_t err = cudaFuncSetAttribute(tc::k_gemm_tc<BN, EPI, ACT>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+        attr_set = true;
+    }
+    dim3 grid(M / tc::BM, N / BN);
+    tc::k_gemm_tc<BN, EPI, ACT><<<grid, 128, smem, st>>>(ma, mb, M, N, K, e, status);
+    return cudaPeekAtLastError();
+}
+
+template <int BN>
+cudaError_t dispatch_epi(int epi, int act, const CUtensorMap &ma, const CUtensorMap &mb, int M, int N, int K,
+                         const EpiArgs &e, int32_t *status, cudaStream_t st) {
+    switch (epi) {
+    case EPI_L1:
+        return act == 0 ? launch_tc<BN, EPI_L1, 0>(ma, mb, M, N, K, e, status, st)
+                        : launch_tc<BN, EPI_L1, 1>(ma, mb, M, N, K, e, status, st);
+    case EPI_L2:
+        return act == 0 ? launch_tc<BN, EPI_L2, 0>(ma, mb, M, N, K, e, status, st)
+                        : launch_tc<BN, EPI_L2, 1>(ma, mb, M, N, K, e, status, st);
+    case EPI_B1: return launch_tc<BN, EPI_B1, 0>(ma, mb, M, N, K, e, status, st);
+    default: return launch_tc<BN, EPI_STORE, 0>(ma, mb, M, N, K, e, status, st);
+    }
+}
+
+}  // namespace
+
+int tc_choose_bn(int M, int N, int forced) {
+    if (forced == 64 || forced == 128 || forced == 256) return (N % forced == 0) ? forced : 64;
+    const long long tiles_m = M / tc::BM;
+    if (N % 256 == 0 && tiles_m * (N / 256) >= 148) return 256;
+    if (N % 128 == 0 && tiles_m * (N / 128) >= 148) return 128;
+    if (N % 128 == 0 && tiles_m * (N / 64) > 2 * 148) return 128;
+    return 64;
+}
+
+gm_status gemm_bf16(int epi, int act, const __nv_bfloat16 *A, const __nv_bfloat16 *B, int M, int N, int K,
+                    const EpiArgs &e, int32_t *status, cudaStream_t st, int forced_bn) {
+    if (M <= 0) return GM_OK;
+    if (M % tc::BM || K % tc::BK || N % 64) return GM_ERR_UNSUPPORTED;
+    const int bn = tc_choose_bn(M, N, forced_bn);
+    CUtensorMap ma, mb;
+    if (!tensor_map(A, K, M, tc::BM, &ma) || !tensor_map(B, K, N, bn, &mb)) return GM_ERR_CUDA;
+    cudaError_t err;
+    switch (bn) {
+    case 256: err = dispatch_epi<256>(epi, act, ma, mb, M, N, K, e, status, st); break;
+    case 128: err = dispatch_epi<128>(epi, act, ma, mb, M, N, K, e, status, st); break;
+    default: err = dispatch_epi<64>(epi, act, ma, mb, M, N, K, e, status, st); break;
+    }
+    note_launches(1);
+    return err == cudaSuccess ? GM_OK : GM_ERR_CUDA;
+}
+
+}  // namespace gm

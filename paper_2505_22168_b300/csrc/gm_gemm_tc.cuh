@@ -1,0 +1,317 @@
+// gm_gemm_tc.cuh -- BF16 network GEMM on the 5th-generation tensor cores (tcgen05), sm_103a.
+//
+// C[m][n] = sum_k A[m][k] B[n][k] with A, B BF16 (K contiguous), FP32 accumulation in TMEM,
+// and the epilogues of gm_gemm.h.  One CTA computes a 128 x BN tile:
+//   warp 0 lane 0  TMA producer: 64-wide K blocks of A (128 rows) and B (BN rows) into a
+//                  STAGES-deep shared-memory ring (128-byte swizzle), mbarrier complete_tx
+//   warp 1 lane 0  MMA issuer: 4 x tcgen05.mma (M=128, N=BN, K=16) per K block into one
+//                  TMEM accumulator; tcgen05.commit frees the stage, a final commit
+//                  signals the epilogue
+//   warps 0..3     epilogue: tcgen05.ld 32 lanes x 32 columns per chunk (thread = row)
+// Every wait on an mbarrier is bounded (about one second of %globaltimer); on expiry the
+// kernel records GM_ERR_TIMEOUT in the status word, waits (bounded) for the copies it
+// issued, releases its TMEM and returns.
+#pragma once
+
+#include <cuda.h>
+
+#include "gm_gemm.h"
+
+namespace gm {
+namespace tc {
+
+constexpr int BM = 128;
+constexpr int BK = 64;                      // BF16 elements per 128-byte swizzle row
+constexpr int A_STAGE_BYTES = BM * BK * 2;  // 16 KiB
+constexpr uint64_t WAIT_NS = 1000000000ull; // bound of every wait
+
+__host__ __device__ constexpr int stages_for(int bn) { return bn >= 256 ? 4 : 6; }
+__host__ __device__ constexpr int tmem_cols_for(int bn) { return bn <= 32 ? 32 : (bn <= 64 ? 64 : (bn <= 128 ? 128 : 256)); }
+__host__ __device__ constexpr size_t smem_bytes_for(int bn) {
+    return (size_t)stages_for(bn) * (A_STAGE_BYTES + bn * BK * 2) + 1024 + 256;
+}
+
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t now_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(su32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase of the given parity; false on timeout or abort.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = now_ns();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (now_ns() - t0 > WAIT_NS) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int c_inner, int c_row) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            su32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(su32(bar)), "r"(c_inner), "r"(c_row)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(slot)), "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major, M = 128, N = bn.
+__host__ __device__ constexpr uint32_t instr_desc(int bn) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+                 : "memory");
+}
+
+// 32 TMEM lanes x 32 consecutive 32-bit columns; thread t of the warp gets lane (base + t).
+__device__ __forceinline__ void tmem_ld_32cols(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+__device__ __forceinline__ uint4 pack8_bf16(const float *x) {
+    uint4 o;
+    __nv_bfloat162 h0 = __floats2bfloat162_rn(x[0], x[1]), h1 = __floats2bfloat162_rn(x[2], x[3]);
+    __nv_bfloat162 h2 = __floats2bfloat162_rn(x[4], x[5]), h3 = __floats2bfloat162_rn(x[6], x[7]);
+    o.x = *reinterpret_cast<uint32_t *>(&h0);
+    o.y = *reinterpret_cast<uint32_t *>(&h1);
+    o.z = *reinterpret_cast<uint32_t *>(&h2);
+    o.w = *reinterpret_cast<uint32_t *>(&h3);
+    return o;
+}
+
+__device__ __forceinline__ void unpack8_bf16(uint4 u, float *x) {
+    const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&u);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        float2 f = __bfloat1622float2(h[q]);
+        x[2 * q] = f.x;
+        x[2 * q + 1] = f.y;
+    }
+}
+
+// Epilogue of one row segment of 32 columns starting at column n (multiple of 32).
+template <int EPI, int ACT>
+__device__ __forceinline__ void epilogue32(const EpiArgs &e, int m, int n, int N, float (&v)[32], float &part) {
+    if (EPI == EPI_STORE) {
+        float4 *o = reinterpret_cast<float4 *>(static_cast<float *>(e.out0) + (size_t)m * N + n);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    } else if (EPI == EPI_B1) {
+        const uint4 *d = reinterpret_cast<const uint4 *>(static_cast<const __nv_bfloat16 *>(e.aux) + (size_t)m * N + n);
+        uint4 *o = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(e.out0) + (size_t)m * N + n);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float g[8], y[8];
+            unpack8_bf16(d[q], g);
+#pragma unroll
+            for (int t = 0; t < 8; ++t) y[t] = v[8 * q + t] * g[t];
+            o[q] = pack8_bf16(y);
+        }
+    } else if (EPI == EPI_L1) {
+        uint4 *oa = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(e.out0) + (size_t)m * N + n);
+        uint4 *od = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(e.out1) + (size_t)m * N + n);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float a[8], d[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) a[t] = act_fwd<ACT>(v[8 * q + t] + __ldg(e.bias + n + 8 * q + t), d[t]);
+            oa[q] = pack8_bf16(a);
+            od[q] = pack8_bf16(d);
+        }
+    } else {  // EPI_L2
+        const float sg = m < e.n_atoms ? e.sigma[min(max(e.species[m], 0), e.n_species - 1)] : 0.0f;
+        uint4 *o = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(e.out0) + (size_t)m * N + n);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float dz[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                float d;
+                const int c = n + 8 * q + t;
+                const float a = act_fwd<ACT>(v[8 * q + t] + __ldg(e.bias + c), d);
+                const float w = __ldg(e.w3 + c);
+                part = fmaf(a, w, part);
+                dz[t] = sg * w * d;
+            }
+            o[q] = pack8_bf16(dz);
+        }
+    }
+}
+
+template <int BN, int EPI, int ACT>
+__global__ void __launch_bounds__(128, 1)
+    k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N, int K,
+              EpiArgs e, int32_t *status) {
+    constexpr int STAGES = stages_for(BN);
+    constexpr int B_STAGE_BYTES = BN * BK * 2;
+    constexpr int STAGE_BYTES = A_STAGE_BYTES + B_STAGE_BYTES;
+    constexpr uint32_t TMEM_COLS = tmem_cols_for(BN);
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
+    uint64_t *empty = full + STAGES;
+    uint64_t *done = empty + STAGES;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int KB = K / BK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full + s, 1);
+            mbar_init(empty + s, 1);
+        }
+        mbar_init(done, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0) {
+        tmem_alloc(tmem_slot, TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer
+        int issued = 0;
+        for (int kb = 0; kb < KB; ++kb) {
+            const int s = kb % STAGES;
+            if (kb >= STAGES && !mbar_wait(empty + s, ((kb / STAGES) - 1) & 1, abort_flag)) {
+                *abort_flag = 1;
+                break;
+            }
+            uint8_t *a_dst = smem + s * STAGE_BYTES;
+            uint8_t *b_dst = a_dst + A_STAGE_BYTES;
+            mbar_expect_tx(full + s, STAGE_BYTES);
+            tma_load_2d(a_dst, &tmA, full + s, kb * BK, m0);
+            tma_load_2d(b_dst, &tmB, full + s, kb * BK, n0);
+            ++issued;
+        }
+        if (*abort_flag) {
+            // let the copies already issued land before the CTA exits (bounded)
+            for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb) {
+                volatile int never = 0;
+                mbar_wait(full + (kb % STAGES), (kb / STAGES) & 1, &never);
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer
+        constexpr uint32_t idesc = instr_desc(BN);
+        bool ok = true;
+        for (int kb = 0; kb < KB; ++kb) {
+            const int s = kb % STAGES;
+            if (!mbar_wait(full + s, (kb / STAGES) & 1, abort_flag)) {
+                *abort_flag = 1;
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t a_base = su32(smem + s * STAGE_BYTES);
+            const uint32_t b_base = a_base + A_STAGE_BYTES;
+#pragma unroll
+            for (int k = 0; k < BK / 16; ++k)
+                umma_bf16(tmem, smem_desc(a_base + 32 * k), smem_desc(b_base + 32 * k), idesc, (kb | k) != 0);
+            umma_commit(empty + s);
+        }
+        if (ok) umma_commit(done);
+    }
+    __syncwarp();
+
+    // ---------------- epilogue: thread = row m0 + 32 warp + lane
+    const bool ready = mbar_wait(done, 0, abort_flag);
+    tc_fence_after();
+    if (ready) {
+        const int m = m0 + warp * 32 + lane;
+        float part = 0.0f;
+#pragma unroll 1
+        for (int c = 0; c < BN / 32; ++c) {
+            float v[32];
+            tmem_ld_32cols(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
+            epilogue32<EPI, ACT>(e, m, n0 + c * 32, N, v, part);
+            if (EPI == EPI_L2 && (c & 1)) {
+                e.nn_part[(size_t)m * (N / 64) + (n0 + c * 32) / 64] = part;
+                part = 0.0f;
+            }
+        }
+    } else if (threadIdx.x == 0) {
+        set_status(status, GM_ERR_TIMEOUT);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
+}
+
+}  // namespace tc
+}  // namespace gm

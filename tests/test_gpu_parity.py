@@ -180,6 +180,18 @@ def test_energy_forces_emim_batch_with_empty_structure():
     _ef_parity(b, d, p)
 
 
+@pytest.mark.parametrize("cfg,act", [(1, "tanh"), (1, "silu"), (2, "silu")])
+def test_energy_forces_mixed_precision(cfg, act):
+    """BF16 network on tcgen05 tensor cores (FP32 accumulation), everything else FP32."""
+    b, d, p = synth.config(cfg, activation=act)
+    _ef_parity(b, d, p, precision="mixed")
+
+
+def test_energy_forces_mixed_ragged_li3po4_batch(li_small):
+    b, d, p = li_small
+    _ef_parity(b, d, p, precision="mixed")
+
+
 def test_descriptors_match_oracle():
     b, d, p = synth.config(1)
     m, sysd, nl = _nl_pair(b, d, p)
