@@ -129,6 +129,17 @@ GM_API gm_status gm_model_set_params(gm_model *m, const float *theta_dev, struct
 
 GM_API void gm_model_destroy(gm_model *m);
 
+/* Tuning knobs of a model (they change speed, not results beyond rounding):
+ *   GM_TUNE_PAIR_TPA    lanes per atom in the pair kernels: 0 = by system size, or 1, 2, 4, 8, 16
+ *   GM_TUNE_SPLIT_MASK  mixed path: network GEMMs that run with hi/lo split-BF16 operands
+ *                       (three tensor-core passes) -- bit 1 first layer, 2 second layer,
+ *                       4 and 8 the two backward GEMMs; default 12 (backward GEMMs), which
+ *                       keeps forces within 2e-3 of the FP64 result
+ *   GM_TUNE_GEMM_BN     mixed path: tensor-core tile width 64, 128 or 256 (0 = by size)
+ * Errors: GM_ERR_ARG for an unknown key or value. */
+enum { GM_TUNE_PAIR_TPA = 0, GM_TUNE_SPLIT_MASK = 1, GM_TUNE_GEMM_BN = 2 };
+GM_API gm_status gm_model_set_tuning(gm_model *m, int32_t key, int32_t value);
+
 /* Bytes of workspace an operation needs (op = GM_OP_*).  nl_capacity is the neighbour
  * list capacity the caller will pass.  Errors: GM_ERR_ARG. */
 GM_API gm_status gm_workspace_size(const gm_model *m, int32_t n_structures, int32_t n_atoms,

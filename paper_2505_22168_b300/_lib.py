@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "GM_OK", 1: "GM_ERR_ARG", 2: "GM_ERR_CAPACITY", 3: "GM_ERR_UN
 EXPORTS = ("gm_param_count", "gm_model_create", "gm_model_set_params", "gm_model_destroy", "gm_workspace_size",
            "gm_build_neighbors", "gm_energy_forces", "gm_param_grad", "gm_force_matching_loss", "gm_descriptors",
            "gm_status_clear", "gm_status_string", "gm_last_error", "gm_profile_enable", "gm_profile_reset",
-           "gm_profile_n_stages", "gm_profile_stage_name", "gm_profile_collect", "gm_build_neighbors_noalloc")
+           "gm_profile_n_stages", "gm_profile_stage_name", "gm_profile_collect", "gm_build_neighbors_noalloc", "gm_model_set_tuning")
 
 
 class GmModelDesc(ctypes.Structure):
@@ -89,6 +89,7 @@ def load():
         "gm_profile_stage_name": (ctypes.c_char_p, [ctypes.c_int]),
         "gm_profile_collect": (st, [_P, _P, ctypes.c_int, _P]),
         "gm_build_neighbors_noalloc": (st, [_P, ctypes.POINTER(GmSystem), ctypes.POINTER(GmNlist), _P, _P]),
+        "gm_model_set_tuning": (st, [_P, ctypes.c_int32, ctypes.c_int32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -121,6 +122,13 @@ def gm_model_set_params(model: int, theta_ptr: int, stream: int):
     check(load().gm_model_set_params(model, theta_ptr, stream), "gm_model_set_params")
 
 
+GM_TUNE_PAIR_TPA, GM_TUNE_SPLIT_MASK, GM_TUNE_GEMM_BN = 0, 1, 2
+
+
+def gm_model_set_tuning(model: int, key: int, value: int):
+    check(load().gm_model_set_tuning(model, key, value), "gm_model_set_tuning")
+
+
 def gm_model_destroy(model: int):
     load().gm_model_destroy(model)
 
@@ -140,7 +148,7 @@ def gm_build_neighbors(model, sys: GmSystem, nl: GmNlist, ws, ws_bytes, status, 
 def gm_build_neighbors_noalloc(model, sys: GmSystem, nl: GmNlist, status, stream):
     """Neighbour build without a workspace (fixed scratch inside the library; see gm.h)."""
     check(load().gm_build_neighbors_noalloc(model, ctypes.byref(sys), ctypes.byref(nl), status, stream),
-          "gm_build_neighbors_noalloc")
+          "gm_build_neighbors_noalloc", "gm_model_set_tuning")
 
 
 def gm_energy_forces(model, sys: GmSystem, nl: GmNlist, energy, forces, virial, ws, ws_bytes, status, stream):

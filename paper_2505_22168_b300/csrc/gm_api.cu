@@ -91,7 +91,9 @@ struct gm_model {
     float *W1p;            // [384][H]  backward (B[n=f][k=h])
     float *W2t;            // [H][H]    forward  (B[n][k] = W2[k][n])
     float *W2;             // [H][H]    backward (B[n][k] = W2[n][k])
-    __nv_bfloat16 *W1t_h, *W1p_h, *W2t_h, *W2_h;
+    __nv_bfloat16 *W1t_h, *W1p_h, *W2t_h, *W2_h;   // BF16 hi/lo pairs, rows [hi(K) | lo(K)]
+    int split_mask;        // GEMMs run with three hi/lo passes: 1 L1, 2 L2, 4 B1, 8 B0
+    int gemm_bn;           // tensor-core tile width (0 = by size)
     float *b1, *b2, *w3, *b3, *sigma, *mu;
 };
 
@@ -114,10 +116,10 @@ Layout model_layout(int S, int H) {
     L.W1p = take(sizeof(float) * NFP * H);
     L.W2t = take(sizeof(float) * H * H);
     L.W2 = take(sizeof(float) * H * H);
-    L.W1t_h = take(2 * (size_t)H * NFP);
-    L.W1p_h = take(2 * (size_t)NFP * H);
-    L.W2t_h = take(2 * (size_t)H * H);
-    L.W2_h = take(2 * (size_t)H * H);
+    L.W1t_h = take(4 * (size_t)H * NFP);
+    L.W1p_h = take(4 * (size_t)NFP * H);
+    L.W2t_h = take(4 * (size_t)H * H);
+    L.W2_h = take(4 * (size_t)H * H);
     L.b1 = take(sizeof(float) * H);
     L.b2 = take(sizeof(float) * H);
     L.w3 = take(sizeof(float) * H);
@@ -147,6 +149,13 @@ ThetaOff theta_offsets(int S, int H) {
     return o;
 }
 
+// BF16 weight copy as a hi/lo pair: row r of a [rows][K] matrix becomes [hi(K) | lo(K)].
+__device__ __forceinline__ void put_split(__nv_bfloat16 *dst, int K, int r, int k, float v) {
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    dst[(size_t)r * 2 * K + k] = hi;
+    dst[(size_t)r * 2 * K + K + k] = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+
 __global__ void k_repack(const float *__restrict__ th, ThetaOff o, int S, int H, float beta_scale, gm_model m) {
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -157,19 +166,19 @@ __global__ void k_repack(const float *__restrict__ th, ThetaOff o, int S, int H,
         const int h = (int)(q / NFP), f = (int)(q % NFP);
         const float v = f < NF ? th[o.W1 + (int64_t)f * H + h] : 0.0f;
         m.W1t[q] = v;
-        m.W1t_h[q] = __float2bfloat16_rn(v);
+        put_split(m.W1t_h, NFP, h, f, v);
         const int64_t qp = (int64_t)f * H + h;
         m.W1p[qp] = v;
-        m.W1p_h[qp] = __float2bfloat16_rn(v);
+        put_split(m.W1p_h, H, f, h, v);
     }
     for (int64_t q = tid; q < (int64_t)H * H; q += stride) {
         const int r = (int)(q / H), c = (int)(q % H);
         const float v = th[o.W2 + q];  // W2[r][c]
         m.W2[q] = v;
-        m.W2_h[q] = __float2bfloat16_rn(v);
+        put_split(m.W2_h, H, r, c, v);
         const int64_t qt = (int64_t)c * H + r;  // W2t[c][r] = W2[r][c]
         m.W2t[qt] = v;
-        m.W2t_h[qt] = __float2bfloat16_rn(v);
+        put_split(m.W2t_h, H, c, r, v);
     }
     for (int64_t q = tid; q < H; q += stride) {
         m.b1[q] = th[o.b1 + q];
@@ -300,11 +309,9 @@ gm_status gm_model_create(const gm_model_desc *d, gm_model **out) {
     m->rc.inv_r_cut = (float)(1.0 / d->r_cut);
     m->rc.gamma = (float)((double)(NB * NB) / (d->r_cut * d->r_cut));
     for (int k = 0; k < NB; ++k) m->rc.mu[k] = (float)(d->r_min + k * (d->r_cut - d->r_min) / (NB - 1));
-    const char *env = getenv("GM_PAIR_TPA");
-    m->pair_tpa = env ? atoi(env) : 0;
-    if (m->pair_tpa != 0 && m->pair_tpa != 1 && m->pair_tpa != 2 && m->pair_tpa != 4 && m->pair_tpa != 8 &&
-        m->pair_tpa != 16)
-        m->pair_tpa = 0;
+    m->pair_tpa = 0;
+    m->split_mask = 12;
+    m->gemm_bn = 0;
     Layout L = model_layout(m->S, m->H);
     m->buf_bytes = L.total;
     if (cudaMalloc(&m->buf, L.total) != cudaSuccess) {
@@ -339,6 +346,26 @@ gm_status gm_model_set_params(gm_model *m, const float *theta, struct CUstream_s
     k_repack<<<296, 256, 0, stream>>>(theta, o, m->S, m->H, scale, *m);
     note_launches(1);
     return launch_status();
+}
+
+gm_status gm_model_set_tuning(gm_model *m, int32_t key, int32_t value) {
+    if (!m) return fail(GM_ERR_ARG, "null model");
+    switch (key) {
+    case GM_TUNE_PAIR_TPA:
+        if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8 && value != 16)
+            return fail(GM_ERR_ARG, "pair TPA must be 0, 1, 2, 4, 8 or 16");
+        m->pair_tpa = value;
+        return GM_OK;
+    case GM_TUNE_SPLIT_MASK:
+        if (value < 0 || value > 15) return fail(GM_ERR_ARG, "split mask must be in 0..15");
+        m->split_mask = value;
+        return GM_OK;
+    case GM_TUNE_GEMM_BN:
+        if (value != 0 && value != 64 && value != 128 && value != 256) return fail(GM_ERR_ARG, "bad GEMM tile width");
+        m->gemm_bn = value;
+        return GM_OK;
+    }
+    return fail(GM_ERR_ARG, "unknown tuning key");
 }
 
 void gm_model_destroy(gm_model *m) {
@@ -407,7 +434,9 @@ static gm_status network_fwd_bwd(const gm_model *m, const gm_system *sys, EfWs &
     e.nn_part = w.nn_part;
     if (m->d.precision == GM_PREC_MIXED) {
         typedef __nv_bfloat16 bf;
-        bf *G = reinterpret_cast<bf *>(w.G), *A1 = reinterpret_cast<bf *>(w.A1), *D1 = reinterpret_cast<bf *>(w.D1);
+        bf *G = reinterpret_cast<bf *>(w.G), *A1 = reinterpret_cast<bf *>(w.A1);
+        float *D1 = w.D1;
+        const int sp = m->split_mask;
         bf *dZ2 = reinterpret_cast<bf *>(w.dZ2), *dZ1 = reinterpret_cast<bf *>(w.dZ1);
         gm_status s;
         e.bias = m->b1;
@@ -415,7 +444,7 @@ static gm_status network_fwd_bwd(const gm_model *m, const gm_system *sys, EfWs &
         e.out1 = D1;
         {
             StageScope sc(ST_GEMM_L1, st);
-            if ((s = gemm_bf16(EPI_L1, m->d.activation, G, m->W1t_h, Mp, H, NFP, e, status, st)) != GM_OK)
+            if ((s = gemm_bf16(EPI_L1, m->d.activation, G, m->W1t_h, Mp, H, NFP, (sp & 1) != 0, e, status, st, m->gemm_bn)) != GM_OK)
                 return fail(s, "tcgen05 GEMM L1 failed");
         }
         e.bias = m->b2;
@@ -423,20 +452,20 @@ static gm_status network_fwd_bwd(const gm_model *m, const gm_system *sys, EfWs &
         e.out1 = nullptr;
         {
             StageScope sc(ST_GEMM_L2, st);
-            if ((s = gemm_bf16(EPI_L2, m->d.activation, A1, m->W2t_h, Mp, H, H, e, status, st)) != GM_OK)
+            if ((s = gemm_bf16(EPI_L2, m->d.activation, A1, m->W2t_h, Mp, H, H, (sp & 2) != 0, e, status, st, m->gemm_bn)) != GM_OK)
                 return fail(s, "tcgen05 GEMM L2 failed");
         }
         e.out0 = dZ1;
         e.aux = D1;
         {
             StageScope sc(ST_GEMM_B1, st);
-            if ((s = gemm_bf16(EPI_B1, 0, dZ2, m->W2_h, Mp, H, H, e, status, st)) != GM_OK)
+            if ((s = gemm_bf16(EPI_B1, 0, dZ2, m->W2_h, Mp, H, H, (sp & 4) != 0, e, status, st, m->gemm_bn)) != GM_OK)
                 return fail(s, "tcgen05 GEMM B1 failed");
         }
         e.out0 = w.dG;
         {
             StageScope sc(ST_GEMM_B0, st);
-            if ((s = gemm_bf16(EPI_STORE, 0, dZ1, m->W1p_h, Mp, NFP, H, e, status, st)) != GM_OK)
+            if ((s = gemm_bf16(EPI_STORE, 0, dZ1, m->W1p_h, Mp, NFP, H, (sp & 8) != 0, e, status, st, m->gemm_bn)) != GM_OK)
                 return fail(s, "tcgen05 GEMM B0 failed");
         }
         return GM_OK;

@@ -216,7 +216,15 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_contract_fwd(const float *__r
         const int r = idx / NFP, f = idx - r * NFP, m = m0 + r;
         if (m >= Mp) continue;
         const float v = f < NF ? tile[r * GT_STRIDE + f] : 0.0f;
-        G[(size_t)m * NFP + f] = to_out<OutT>(v);
+        if (sizeof(OutT) == 2) {
+            // BF16 operand as a hi/lo pair: row [hi(384) | lo(384)]
+            const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+            const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+            reinterpret_cast<__nv_bfloat16 *>(G)[(size_t)m * 2 * NFP + f] = hi;
+            reinterpret_cast<__nv_bfloat16 *>(G)[(size_t)m * 2 * NFP + NFP + f] = lo;
+        } else {
+            G[(size_t)m * NFP + f] = to_out<OutT>(v);
+        }
         if (G32 != nullptr && f < NF && m < N) G32[(size_t)m * NF + f] = v;
     }
 }

@@ -5,7 +5,8 @@
 
 namespace gm {
 
-// psi [N][100] FP32 -> G [Mp][384] (FP32 or BF16; rows >= N and columns >= 360 zero).
+// psi [N][100] FP32 -> G [Mp][384] FP32, or G [Mp][2*384] BF16 hi/lo pairs (rows >= N and
+// feature columns >= 360 zero).
 // features_out [N][360] FP32 (optional copy for diagnostics, may be NULL).
 void launch_contract_fwd_f32(const float *psi, int N, int Mp, float *G, float *features_out, cudaStream_t st);
 void launch_contract_fwd_bf16(const float *psi, int N, int Mp, __nv_bfloat16 *G, float *features_out,

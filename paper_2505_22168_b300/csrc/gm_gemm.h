@@ -27,15 +27,21 @@ struct EpiArgs {
     const void *aux;         // D1 (B1)
     float *nn_part;          // [M][N/64] (L2): partial output-layer sums per 64 columns
 };
+// BF16 operands of the tcgen05 path are stored as hi/lo pairs, [rows][2K]: columns [0, K)
+// hold hi = bf16(x), columns [K, 2K) hold lo = bf16(x - hi).  A GEMM run with split = 0
+// reads the hi half only; with split = 1 it accumulates hi*hi + lo*hi + hi*lo (three
+// tensor-core passes, about FP32 accuracy).  The BF16 outputs of L1/L2/B1 are written in
+// the same [M][2N] layout; D1 (phi') is kept in FP32.
 
 // FP32 SIMT path (gm_gemm_simt.cu).  M % 128 == 0, N % 64 == 0, K % 16 == 0.
 void gemm_f32(int epi, int act, const float *A, const float *B, int M, int N, int K, const EpiArgs &e,
               cudaStream_t st);
 
-// BF16 tcgen05 path (gm_gemm_tc.cu).  M % 128 == 0, N % 64 == 0, K % 64 == 0; A [M][K] and
-// B [N][K] BF16 with 16-byte aligned rows.  L1/L2/B1 outputs are BF16, STORE is FP32.
+// BF16 tcgen05 path (gm_gemm_tc.cu).  M % 128 == 0, N % 64 == 0, K % 64 == 0; A [M][2K] and
+// B [N][2K] BF16 hi/lo pairs with 16-byte aligned rows.  L1/L2/B1 outputs are BF16 hi/lo
+// pairs [M][2N] (D1 FP32 [M][N]), STORE is FP32 [M][N].
 // forced_bn = 0 picks the tile width from the problem size (64, 128 or 256 columns).
-gm_status gemm_bf16(int epi, int act, const __nv_bfloat16 *A, const __nv_bfloat16 *B, int M, int N, int K,
+gm_status gemm_bf16(int epi, int act, const __nv_bfloat16 *A, const __nv_bfloat16 *B, int M, int N, int K, int split,
                     const EpiArgs &e, int32_t *status, cudaStream_t st, int forced_bn = 0);
 int tc_choose_bn(int M, int N, int forced);
 

@@ -56,8 +56,8 @@ bool tensor_map(const void *base, int inner, int rows, int box_rows, CUtensorMap
 }
 
 template <int BN, int EPI, int ACT>
-cudaError_t launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, int M, int N, int K, const EpiArgs &e,
-                      int32_t *status, cudaStream_t st) {
+cudaError_t launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, int M, int N, int K, int split,
+                      const EpiArgs &e, int32_t *status, cudaStream_t st) {
     static bool attr_set = false;
     const size_t smem = tc::smem_bytes_for(BN);
     if (!attr_set) {
@@ -67,22 +67,22 @@ cudaError_t launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, int M, int N
         attr_set = true;
     }
     dim3 grid(M / tc::BM, N / BN);
-    tc::k_gemm_tc<BN, EPI, ACT><<<grid, 128, smem, st>>>(ma, mb, M, N, K, e, status);
+    tc::k_gemm_tc<BN, EPI, ACT><<<grid, 128, smem, st>>>(ma, mb, M, N, K, split, e, status);
     return cudaPeekAtLastError();
 }
 
 template <int BN>
 cudaError_t dispatch_epi(int epi, int act, const CUtensorMap &ma, const CUtensorMap &mb, int M, int N, int K,
-                         const EpiArgs &e, int32_t *status, cudaStream_t st) {
+                         int split, const EpiArgs &e, int32_t *status, cudaStream_t st) {
     switch (epi) {
     case EPI_L1:
-        return act == 0 ? launch_tc<BN, EPI_L1, 0>(ma, mb, M, N, K, e, status, st)
-                        : launch_tc<BN, EPI_L1, 1>(ma, mb, M, N, K, e, status, st);
+        return act == 0 ? launch_tc<BN, EPI_L1, 0>(ma, mb, M, N, K, split, e, status, st)
+                        : launch_tc<BN, EPI_L1, 1>(ma, mb, M, N, K, split, e, status, st);
     case EPI_L2:
-        return act == 0 ? launch_tc<BN, EPI_L2, 0>(ma, mb, M, N, K, e, status, st)
-                        : launch_tc<BN, EPI_L2, 1>(ma, mb, M, N, K, e, status, st);
-    case EPI_B1: return launch_tc<BN, EPI_B1, 0>(ma, mb, M, N, K, e, status, st);
-    default: return launch_tc<BN, EPI_STORE, 0>(ma, mb, M, N, K, e, status, st);
+        return act == 0 ? launch_tc<BN, EPI_L2, 0>(ma, mb, M, N, K, split, e, status, st)
+                        : launch_tc<BN, EPI_L2, 1>(ma, mb, M, N, K, split, e, status, st);
+    case EPI_B1: return launch_tc<BN, EPI_B1, 0>(ma, mb, M, N, K, split, e, status, st);
+    default: return launch_tc<BN, EPI_STORE, 0>(ma, mb, M, N, K, split, e, status, st);
     }
 }
 
@@ -97,18 +97,19 @@ int tc_choose_bn(int M, int N, int forced) {
     return 64;
 }
 
-gm_status gemm_bf16(int epi, int act, const __nv_bfloat16 *A, const __nv_bfloat16 *B, int M, int N, int K,
+gm_status gemm_bf16(int epi, int act, const __nv_bfloat16 *A, const __nv_bfloat16 *B, int M, int N, int K, int split,
                     const EpiArgs &e, int32_t *status, cudaStream_t st, int forced_bn) {
     if (M <= 0) return GM_OK;
     if (M % tc::BM || K % tc::BK || N % 64) return GM_ERR_UNSUPPORTED;
     const int bn = tc_choose_bn(M, N, forced_bn);
     CUtensorMap ma, mb;
-    if (!tensor_map(A, K, M, tc::BM, &ma) || !tensor_map(B, K, N, bn, &mb)) return GM_ERR_CUDA;
+    // operands are [rows][2K] hi/lo pairs
+    if (!tensor_map(A, 2 * K, M, tc::BM, &ma) || !tensor_map(B, 2 * K, N, bn, &mb)) return GM_ERR_CUDA;
     cudaError_t err;
     switch (bn) {
-    case 256: err = dispatch_epi<256>(epi, act, ma, mb, M, N, K, e, status, st); break;
-    case 128: err = dispatch_epi<128>(epi, act, ma, mb, M, N, K, e, status, st); break;
-    default: err = dispatch_epi<64>(epi, act, ma, mb, M, N, K, e, status, st); break;
+    case 256: err = dispatch_epi<256>(epi, act, ma, mb, M, N, K, split, e, status, st); break;
+    case 128: err = dispatch_epi<128>(epi, act, ma, mb, M, N, K, split, e, status, st); break;
+    default: err = dispatch_epi<64>(epi, act, ma, mb, M, N, K, split, e, status, st); break;
     }
     note_launches(1);
     return err == cudaSuccess ? GM_OK : GM_ERR_CUDA;

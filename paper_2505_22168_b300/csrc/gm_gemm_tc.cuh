@@ -145,6 +145,18 @@ __device__ __forceinline__ uint4 pack8_bf16(const float *x) {
     return o;
 }
 
+// hi/lo split of 8 values: hi = bf16(x), lo = bf16(x - hi)
+__device__ __forceinline__ void pack8_split(const float *x, uint4 &hi, uint4 &lo) {
+    float h[8], l[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        h[t] = __bfloat162float(__float2bfloat16_rn(x[t]));
+        l[t] = x[t] - h[t];
+    }
+    hi = pack8_bf16(h);
+    lo = pack8_bf16(l);
+}
+
 __device__ __forceinline__ void unpack8_bf16(uint4 u, float *x) {
     const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&u);
 #pragma unroll
@@ -156,37 +168,41 @@ __device__ __forceinline__ void unpack8_bf16(uint4 u, float *x) {
 }
 
 // Epilogue of one row segment of 32 columns starting at column n (multiple of 32).
+// BF16 outputs go to [m][n] (hi) and [m][N + n] (lo) of a [M][2N] array.
 template <int EPI, int ACT>
 __device__ __forceinline__ void epilogue32(const EpiArgs &e, int m, int n, int N, float (&v)[32], float &part) {
     if (EPI == EPI_STORE) {
         float4 *o = reinterpret_cast<float4 *>(static_cast<float *>(e.out0) + (size_t)m * N + n);
 #pragma unroll
         for (int q = 0; q < 8; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-    } else if (EPI == EPI_B1) {
-        const uint4 *d = reinterpret_cast<const uint4 *>(static_cast<const __nv_bfloat16 *>(e.aux) + (size_t)m * N + n);
-        uint4 *o = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(e.out0) + (size_t)m * N + n);
+        return;
+    }
+    __nv_bfloat16 *ob = static_cast<__nv_bfloat16 *>(e.out0) + (size_t)m * 2 * N + n;
+    uint4 *ohi = reinterpret_cast<uint4 *>(ob), *olo = reinterpret_cast<uint4 *>(ob + N);
+    if (EPI == EPI_B1) {
+        const float4 *d = reinterpret_cast<const float4 *>(static_cast<const float *>(e.aux) + (size_t)m * N + n);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            float g[8], y[8];
-            unpack8_bf16(d[q], g);
+            const float4 g0 = d[2 * q], g1 = d[2 * q + 1];
+            const float g[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+            float y[8];
 #pragma unroll
             for (int t = 0; t < 8; ++t) y[t] = v[8 * q + t] * g[t];
-            o[q] = pack8_bf16(y);
+            pack8_split(y, ohi[q], olo[q]);
         }
     } else if (EPI == EPI_L1) {
-        uint4 *oa = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(e.out0) + (size_t)m * N + n);
-        uint4 *od = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(e.out1) + (size_t)m * N + n);
+        float4 *od = reinterpret_cast<float4 *>(static_cast<float *>(e.out1) + (size_t)m * N + n);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             float a[8], d[8];
 #pragma unroll
             for (int t = 0; t < 8; ++t) a[t] = act_fwd<ACT>(v[8 * q + t] + __ldg(e.bias + n + 8 * q + t), d[t]);
-            oa[q] = pack8_bf16(a);
-            od[q] = pack8_bf16(d);
+            pack8_split(a, ohi[q], olo[q]);
+            od[2 * q] = make_float4(d[0], d[1], d[2], d[3]);
+            od[2 * q + 1] = make_float4(d[4], d[5], d[6], d[7]);
         }
     } else {  // EPI_L2
         const float sg = m < e.n_atoms ? e.sigma[min(max(e.species[m], 0), e.n_species - 1)] : 0.0f;
-        uint4 *o = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(e.out0) + (size_t)m * N + n);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             float dz[8];
@@ -199,7 +215,7 @@ __device__ __forceinline__ void epilogue32(const EpiArgs &e, int m, int n, int N
                 part = fmaf(a, w, part);
                 dz[t] = sg * w * d;
             }
-            o[q] = pack8_bf16(dz);
+            pack8_split(dz, ohi[q], olo[q]);
         }
     }
 }
@@ -207,7 +223,7 @@ __device__ __forceinline__ void epilogue32(const EpiArgs &e, int m, int n, int N
 template <int BN, int EPI, int ACT>
 __global__ void __launch_bounds__(128, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N, int K,
-              EpiArgs e, int32_t *status) {
+              int split, EpiArgs e, int32_t *status) {
     constexpr int STAGES = stages_for(BN);
     constexpr int B_STAGE_BYTES = BN * BK * 2;
     constexpr int STAGE_BYTES = A_STAGE_BYTES + B_STAGE_BYTES;
@@ -222,7 +238,8 @@ __global__ void __launch_bounds__(128, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-    const int KB = K / BK;
+    const int KB1 = K / BK;                 // K blocks of one pass
+    const int KB = split ? 3 * KB1 : KB1;   // passes: hi*hi (+ lo*hi + hi*lo)
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -254,9 +271,10 @@ __global__ void __launch_bounds__(128, 1)
             }
             uint8_t *a_dst = smem + s * STAGE_BYTES;
             uint8_t *b_dst = a_dst + A_STAGE_BYTES;
+            const int pass = kb / KB1, kk = kb - pass * KB1;
             mbar_expect_tx(full + s, STAGE_BYTES);
-            tma_load_2d(a_dst, &tmA, full + s, kb * BK, m0);
-            tma_load_2d(b_dst, &tmB, full + s, kb * BK, n0);
+            tma_load_2d(a_dst, &tmA, full + s, (pass == 1 ? K : 0) + kk * BK, m0);
+            tma_load_2d(b_dst, &tmB, full + s, (pass == 2 ? K : 0) + kk * BK, n0);
             ++issued;
         }
         if (*abort_flag) {
@@ -290,7 +308,7 @@ __global__ void __launch_bounds__(128, 1)
     __syncwarp();
 
     // ---------------- epilogue: thread = row m0 + 32 warp + lane
-    const bool ready = mbar_wait(done, 0, abort_flag);
+    const bool ready = __all_sync(0xffffffffu, mbar_wait(done, 0, abort_flag));
     tc_fence_after();
     if (ready) {
         const int m = m0 + warp * 32 + lane;

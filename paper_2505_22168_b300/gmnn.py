@@ -122,6 +122,13 @@ class GMNN:
         self.theta = th
         L.gm_model_set_params(self.handle, _ptr(th), _stream())
 
+    def set_tuning(self, pair_tpa=None, split_mask=None, gemm_bn=None):
+        """Speed knobs of the library (gm_model_set_tuning); None leaves a knob unchanged."""
+        for key, val in ((L.GM_TUNE_PAIR_TPA, pair_tpa), (L.GM_TUNE_SPLIT_MASK, split_mask),
+                         (L.GM_TUNE_GEMM_BN, gemm_bn)):
+            if val is not None:
+                L.gm_model_set_tuning(self.handle, key, int(val))
+
     # -------------------------------------------------------------- buffers
     def workspace(self, op, sysd: DeviceSystem, capacity=0):
         need = L.gm_workspace_size(self.handle, sysd.n_structures, sysd.n_atoms, capacity, op)
