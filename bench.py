@@ -60,9 +60,52 @@ def jitter_path(batch, seed, steps, sigma=0.01):
 
 # ----------------------------------------------------------------------------- clocks
 
+class _Nvml:
+    """Read-only NVML queries through ctypes (libnvidia-ml ships with the driver)."""
+
+    CLOCK_SM = 1
+
+    def __init__(self):
+        import ctypes
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        rc = self.lib.nvmlInit_v2()
+        if rc != 0:
+            raise RuntimeError(f"nvmlInit_v2 returned {rc}")
+
+    def handle(self, uuid, index):
+        ct = self.ct
+        h = ct.c_void_p()
+        if uuid and self.lib.nvmlDeviceGetHandleByUUID(ct.c_char_p(uuid.encode()), ct.byref(h)) == 0:
+            return h
+        if self.lib.nvmlDeviceGetHandleByIndex_v2(ct.c_uint(index), ct.byref(h)) == 0:
+            return h
+        raise RuntimeError("no NVML handle")
+
+    def clock(self, h):
+        v = self.ct.c_uint()
+        return v.value if self.lib.nvmlDeviceGetClockInfo(h, self.CLOCK_SM, self.ct.byref(v)) == 0 else None
+
+    def max_clock(self, h):
+        v = self.ct.c_uint()
+        return v.value if self.lib.nvmlDeviceGetMaxClockInfo(h, self.CLOCK_SM, self.ct.byref(v)) == 0 else None
+
+    def reasons(self, h):
+        v = self.ct.c_ulonglong()
+        for name in ("nvmlDeviceGetCurrentClocksEventReasons", "nvmlDeviceGetCurrentClocksThrottleReasons"):
+            f = getattr(self.lib, name, None)
+            if f is not None and f(h, self.ct.byref(v)) == 0:
+                return v.value
+        return 0
+
+    def power_w(self, h):
+        v = self.ct.c_uint()
+        return v.value / 1000.0 if self.lib.nvmlDeviceGetPowerUsage(h, self.ct.byref(v)) == 0 else None
+
+
 class ClockSampler:
     """SM clock, power and clock-event reasons sampled every 10 ms through NVML (read
-    only) while the timed region runs; falls back to nothing if NVML is unavailable."""
+    only) while the timed region runs."""
 
     REASONS = {"hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40,
                "sw_power_cap": 0x4}
@@ -73,32 +116,20 @@ class ClockSampler:
         self._thread = None
         self.handle = None
         self.max_mhz = None
+        self.error = None
         try:
-            import pynvml
             import torch
-            pynvml.nvmlInit()
             uuid = str(torch.cuda.get_device_properties(torch_device).uuid)
-            try:
-                self.handle = pynvml.nvmlDeviceGetHandleByUUID(uuid if uuid.startswith("GPU-") else "GPU-" + uuid)
-            except Exception:
-                self.handle = pynvml.nvmlDeviceGetHandleByIndex(torch_device)
-            self.nv = pynvml
-            self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self.handle, pynvml.NVML_CLOCK_SM)
-        except Exception:
+            uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+            self.nv = _Nvml()
+            self.handle = self.nv.handle(uuid, torch_device)
+            self.max_mhz = self.nv.max_clock(self.handle)
+        except Exception as exc:
             self.handle = None
+            self.error = f"{type(exc).__name__}: {exc}"
 
     def _sample(self):
-        nv = self.nv
-        clk = nv.nvmlDeviceGetClockInfo(self.handle, nv.NVML_CLOCK_SM)
-        try:
-            reasons = nv.nvmlDeviceGetCurrentClocksEventReasons(self.handle)
-        except Exception:
-            reasons = nv.nvmlDeviceGetCurrentClocksThrottleReasons(self.handle)
-        try:
-            power = nv.nvmlDeviceGetPowerUsage(self.handle) / 1000.0
-        except Exception:
-            power = None
-        self.samples.append((clk, reasons, power))
+        self.samples.append((self.nv.clock(self.handle), self.nv.reasons(self.handle), self.nv.power_w(self.handle)))
 
     def _run(self):
         while not self._stop.is_set():
@@ -125,13 +156,14 @@ class ClockSampler:
                 pass
 
     def summary(self):
-        if not self.samples:
-            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["unavailable"], "samples": 0}
-        clks = [c for c, _, _ in self.samples]
+        clks = [c for c, _, _ in self.samples if c is not None]
+        if not clks:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["unavailable"], "samples": 0,
+                    "error": self.error}
         reasons = sorted({name for _, r, _ in self.samples for name, bit in self.REASONS.items() if r & bit})
         powers = [p for _, _, p in self.samples if p is not None]
         return {"sm_mhz": statistics.median(clks), "sm_max_mhz": self.max_mhz, "reasons": reasons,
-                "samples": len(self.samples), "power_w_max": max(powers) if powers else None, "source": "NVML"}
+                "samples": len(clks), "power_w_max": max(powers) if powers else None, "source": "NVML"}
 
 
 # ----------------------------------------------------------------------------- roofline

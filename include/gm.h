@@ -130,7 +130,7 @@ GM_API gm_status gm_model_set_params(gm_model *m, const float *theta_dev, struct
 GM_API void gm_model_destroy(gm_model *m);
 
 /* Tuning knobs of a model (they change speed, not results beyond rounding):
- *   GM_TUNE_PAIR_TPA    lanes per atom in the pair kernels: 0 = by system size, or 1, 2, 4, 8, 16
+ *   GM_TUNE_PAIR_TPA    lanes per atom in the pair kernels: 0 = by system size, or 1, 2, 4, 8, 16, 32
  *   GM_TUNE_SPLIT_MASK  mixed path: network GEMMs that run with hi/lo split-BF16 operands
  *                       (three tensor-core passes) -- bit 1 first layer, 2 second layer,
  *                       4 and 8 the two backward GEMMs; default 12 (backward GEMMs), which

@@ -148,7 +148,7 @@ def gm_build_neighbors(model, sys: GmSystem, nl: GmNlist, ws, ws_bytes, status, 
 def gm_build_neighbors_noalloc(model, sys: GmSystem, nl: GmNlist, status, stream):
     """Neighbour build without a workspace (fixed scratch inside the library; see gm.h)."""
     check(load().gm_build_neighbors_noalloc(model, ctypes.byref(sys), ctypes.byref(nl), status, stream),
-          "gm_build_neighbors_noalloc", "gm_model_set_tuning")
+          "gm_build_neighbors_noalloc")
 
 
 def gm_energy_forces(model, sys: GmSystem, nl: GmNlist, energy, forces, virial, ws, ws_bytes, status, stream):

@@ -196,9 +196,10 @@ int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
 struct EfWs {
     float *psi, *dpsi, *G, *A1, *D1, *dZ2, *dZ1, *dG, *nn_part, *vir_atom;
+    double *red_part;
 };
 
-EfWs carve_ef(Carve &c, int N, int H) {
+EfWs carve_ef(Carve &c, int B, int N, int H) {
     EfWs w;
     const int Mp = round_up(N, TILE_M);
     const size_t n1 = N > 0 ? (size_t)N : 1, m1 = Mp > 0 ? (size_t)Mp : 1;
@@ -212,12 +213,13 @@ EfWs carve_ef(Carve &c, int N, int H) {
     w.dG = c.take<float>(m1 * NFP);
     w.nn_part = c.take<float>(m1 * (H / 64));
     w.vir_atom = c.take<float>(n1 * 9);
+    w.red_part = c.take<double>(reduce_partial_doubles(B, N));
     return w;
 }
 
-size_t ef_workspace_bytes(int N, int H) {
+size_t ef_workspace_bytes(int B, int N, int H) {
     Carve c(reinterpret_cast<void *>(256), ~size_t(0) >> 1);
-    carve_ef(c, N, H);
+    carve_ef(c, B, N, H);
     return c.off + 256;
 }
 
@@ -264,10 +266,11 @@ PairArgs pair_args(const gm_model *m, const gm_system *s, const gm_nlist *nl, in
 
 int choose_tpa(const gm_model *m, int N) {
     if (m->pair_tpa > 0) return m->pair_tpa;
-    if (N >= 65536) return 1;
+    // measured on B300 (EMIM 1536 atoms: 32; Li3PO4 67k and 131k atoms: 1)
+    if (N >= 49152) return 1;
     if (N >= 16384) return 2;
-    if (N >= 4096) return 4;
-    return 8;
+    if (N >= 4096) return 8;
+    return 32;
 }
 
 gm_status launch_status() {
@@ -352,8 +355,8 @@ gm_status gm_model_set_tuning(gm_model *m, int32_t key, int32_t value) {
     if (!m) return fail(GM_ERR_ARG, "null model");
     switch (key) {
     case GM_TUNE_PAIR_TPA:
-        if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8 && value != 16)
-            return fail(GM_ERR_ARG, "pair TPA must be 0, 1, 2, 4, 8 or 16");
+        if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8 && value != 16 && value != 32)
+            return fail(GM_ERR_ARG, "pair TPA must be 0, 1, 2, 4, 8, 16 or 32");
         m->pair_tpa = value;
         return GM_OK;
     case GM_TUNE_SPLIT_MASK:
@@ -379,8 +382,8 @@ gm_status gm_workspace_size(const gm_model *m, int32_t n_structures, int32_t n_a
     if (!m || !bytes || n_structures < 1 || n_atoms < 0 || nl_capacity < 0) return fail(GM_ERR_ARG, "bad argument");
     switch (op) {
     case GM_OP_NEIGHBORS: *bytes = nl_workspace_bytes(n_structures, n_atoms); return GM_OK;
-    case GM_OP_ENERGY_FORCES: *bytes = ef_workspace_bytes(n_atoms, m->H); return GM_OK;
-    case GM_OP_PARAM_GRAD: *bytes = ef_workspace_bytes(n_atoms, m->H); return GM_OK;
+    case GM_OP_ENERGY_FORCES: *bytes = ef_workspace_bytes(n_structures, n_atoms, m->H); return GM_OK;
+    case GM_OP_PARAM_GRAD: *bytes = ef_workspace_bytes(n_structures, n_atoms, m->H); return GM_OK;
     default: return fail(GM_ERR_ARG, "unknown op");
     }
 }
@@ -506,7 +509,7 @@ gm_status gm_energy_forces(const gm_model *m, const gm_system *sys, const gm_nli
     if (!energy || !status || (sys->n_atoms > 0 && !forces)) return fail(GM_ERR_ARG, "null output");
     const int N = sys->n_atoms, B = sys->n_structures, H = m->H;
     Carve c(ws, ws_bytes);
-    EfWs w = carve_ef(c, N, H);
+    EfWs w = carve_ef(c, B, N, H);
     if (!c.ok) return fail(GM_ERR_WORKSPACE, "workspace too small");
     cudaStream_t st = stream;
     const int Mp = round_up(N, TILE_M);
@@ -524,8 +527,8 @@ gm_status gm_energy_forces(const gm_model *m, const gm_system *sys, const gm_nli
         launch_forces(a, choose_tpa(m, N), w.dpsi, forces, virial ? w.vir_atom : nullptr, st);
     }
     StageScope sc(ST_REDUCE, st);
-    launch_struct_reduce(B, sys->atom_ptr, sys->species, m->S, m->sigma, m->mu, m->b3, w.nn_part, H / 64,
-                         virial ? w.vir_atom : nullptr, energy, virial, st);
+    launch_struct_reduce(B, N, sys->atom_ptr, sys->species, m->S, m->sigma, m->mu, m->b3, w.nn_part, H / 64,
+                         virial ? w.vir_atom : nullptr, w.red_part, energy, virial, st);
     return launch_status();
 }
 
@@ -537,7 +540,7 @@ gm_status gm_descriptors(const gm_model *m, const gm_system *sys, const gm_nlist
     if (!psi || !status) return fail(GM_ERR_ARG, "null output");
     if (!aligned(psi, 16)) return fail(GM_ERR_ARG, "psi must be 16-byte aligned");
     Carve c(ws, ws_bytes);
-    EfWs w = carve_ef(c, sys->n_atoms, m->H);
+    EfWs w = carve_ef(c, sys->n_structures, sys->n_atoms, m->H);
     if (!c.ok) return fail(GM_ERR_WORKSPACE, "workspace too small");
     if (sys->n_atoms == 0) return GM_OK;
     return forward_to_features(m, sys, nl, w, psi, features, status, stream);

@@ -13,9 +13,9 @@
 //   setup    per-structure cell grid (cells >= r_cut, at most max(1, n_atoms) cells)
 //   bin      wrap positions, cell index, atomic histogram
 //   scan     cell offsets
-//   scatter  atoms into cells; sortcells orders each cell by atom index (deterministic)
-//            and packs FP32 wrapped positions (float4 with the atom index in w)
-//   search   count pass -> scan -> row_ptr -> fill pass (same candidate order)
+//   scatter  atoms into cells (atomic slots); sortcells (one warp per cell) packs each
+//            cell's FP32 wrapped positions in ascending atom index (float4, index in w)
+//   search   one warp per atom: count pass -> scan -> row_ptr -> fill pass (same order)
 #include <math.h>
 
 #include "gm_internal.h"
@@ -217,37 +217,45 @@ __global__ void __launch_bounds__(256) k_nl_scatter(int N, const int32_t *__rest
     sorted[cstart[c] + slot] = i;
 }
 
-__global__ void __launch_bounds__(256) k_nl_sortcells(int ncells, const int32_t *__restrict__ cstart, int32_t *sorted,
+// One warp per cell: each atom's position in the cell is its rank among the cell's atom
+// indices (all distinct), so the packed order is ascending atom index (deterministic).
+__global__ void __launch_bounds__(256) k_nl_sortcells(int ncells, const int32_t *__restrict__ cstart,
+                                                      const int32_t *__restrict__ unsorted,
                                                       const double *__restrict__ xw, float4 *xs) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (c >= ncells) return;
-    const int s0 = cstart[c], s1 = cstart[c + 1];
-    for (int k = s0 + 1; k < s1; ++k) {
-        const int v = sorted[k];
-        int q = k - 1;
-        while (q >= s0 && sorted[q] > v) {
-            sorted[q + 1] = sorted[q];
-            --q;
-        }
-        sorted[q + 1] = v;
-    }
-    for (int k = s0; k < s1; ++k) {
-        const int i = sorted[k];
-        xs[k] = make_float4((float)xw[3 * i], (float)xw[3 * i + 1], (float)xw[3 * i + 2], __int_as_float(i));
+    const int s0 = cstart[c], n = cstart[c + 1] - s0;
+    for (int e = lane; e < n; e += 32) {
+        const int v = unsorted[s0 + e];
+        int r = 0;
+        for (int q = 0; q < n; ++q) r += unsorted[s0 + q] < v;
+        xs[s0 + r] = make_float4((float)xw[3 * v], (float)xw[3 * v + 1], (float)xw[3 * v + 2], __int_as_float(v));
     }
 }
 
 __device__ __forceinline__ int floordiv(int v, int n) { return v >= 0 ? v / n : -((-v + n - 1) / n); }
 
 // ------------------------------------------------------------------ search
-template <bool FILL>
+// G lanes per centre atom (atoms taken in cell order for locality; G = 32 for small
+// systems, 8 for large ones, whose cells hold about 20 candidates); lanes test G
+// candidates of a cell at a time.  The fill pass places accepted pairs with a ballot over
+// the group, so the row order is the candidate order (stencil cell, then ascending
+// neighbour index) in both passes.
+template <bool FILL, int G>
 __global__ void __launch_bounds__(256) k_nl_search(int N, const NlStruct *__restrict__ S, const int32_t *__restrict__ sid,
                                                    const int32_t *__restrict__ cellid, const int32_t *__restrict__ cstart,
                                                    const float4 *__restrict__ xs, const double *__restrict__ xw,
                                                    const int32_t *__restrict__ mimg, double rc, float rc2f,
                                                    int32_t *counts, const int32_t *__restrict__ row_ptr, int64_t cap,
                                                    int32_t *col, char4 *shift, int32_t *status) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    // G lanes per centre atom (G = 8 or 32); the ballots below involve only the group
+    const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const int lane = threadIdx.x % G;
+    constexpr unsigned low_mask = (G == 32) ? 0xffffffffu : ((1u << (G % 32)) - 1u);
+    const int group_shift = (threadIdx.x & 31) & ~(G - 1);
+    const unsigned group_mask = low_mask << group_shift;
+    const int t = gid;
     if (t >= N) return;
     if (FILL) {
         if ((int64_t)row_ptr[N] > cap) return;
@@ -262,6 +270,7 @@ __global__ void __launch_bounds__(256) k_nl_search(int N, const NlStruct *__rest
     const float lo = rc2f - q.eps2, hi = rc2f + q.eps2;
     const int mi0 = mimg[3 * i], mi1 = mimg[3 * i + 1], mi2 = mimg[3 * i + 2];
     const double xi0 = xw[3 * i], xi1 = xw[3 * i + 1], xi2 = xw[3 * i + 2];
+    const unsigned below = (1u << lane) - 1u;
     int out = FILL ? row_ptr[i] : 0;
     int cnt = 0;
     for (int dz = -q.K[2]; dz <= q.K[2]; ++dz) {
@@ -273,41 +282,49 @@ __global__ void __launch_bounds__(256) k_nl_search(int N, const NlStruct *__rest
                 const int c = q.cell0 + (cz * q.nc[1] + cy) * q.nc[0] + cx;
                 const float sx = (float)nx * q.Lf[0], sy = (float)ny * q.Lf[1], sz = (float)nz * q.Lf[2];
                 const bool zero_shift = (nx | ny | nz) == 0;
-                const int k1 = cstart[c + 1];
-                for (int k = cstart[c]; k < k1; ++k) {
-                    const float4 o = xs[k];
-                    const int j = __float_as_int(o.w);
-                    if (zero_shift && j == i) continue;
-                    const float fx = (o.x - me.x) + sx, fy = (o.y - me.y) + sy, fz = (o.z - me.z) + sz;
-                    const float r2 = fx * fx + fy * fy + fz * fz;
-                    bool in;
-                    if (r2 < lo) in = true;
-                    else if (r2 > hi) in = false;
-                    else {
-                        const double d0 = __dadd_rn(__dsub_rn(xw[3 * j], xi0), __dmul_rn((double)nx, q.L[0]));
-                        const double d1 = __dadd_rn(__dsub_rn(xw[3 * j + 1], xi1), __dmul_rn((double)ny, q.L[1]));
-                        const double d2 = __dadd_rn(__dsub_rn(xw[3 * j + 2], xi2), __dmul_rn((double)nz, q.L[2]));
-                        const double r2d = __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2));
-                        in = r2d < rc2;
+                const int k0 = cstart[c], k1 = cstart[c + 1];
+                for (int base = k0; base < k1; base += G) {
+                    const int k = base + lane;
+                    bool in = false;
+                    int j = 0;
+                    if (k < k1) {
+                        const float4 o = xs[k];
+                        j = __float_as_int(o.w);
+                        if (!(zero_shift && j == i)) {
+                            const float fx = (o.x - me.x) + sx, fy = (o.y - me.y) + sy, fz = (o.z - me.z) + sz;
+                            const float r2 = fx * fx + fy * fy + fz * fz;
+                            if (r2 < lo) in = true;
+                            else if (r2 <= hi) {
+                                const double d0 = __dadd_rn(__dsub_rn(xw[3 * j], xi0), __dmul_rn((double)nx, q.L[0]));
+                                const double d1 = __dadd_rn(__dsub_rn(xw[3 * j + 1], xi1), __dmul_rn((double)ny, q.L[1]));
+                                const double d2 = __dadd_rn(__dsub_rn(xw[3 * j + 2], xi2), __dmul_rn((double)nz, q.L[2]));
+                                const double r2d =
+                                    __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2));
+                                in = r2d < rc2;
+                            }
+                        }
                     }
-                    if (!in) continue;
+                    const unsigned ball = (__ballot_sync(group_mask, in) >> group_shift) & low_mask;
                     if (FILL) {
-                        const int s0 = nx - mimg[3 * j] + mi0;
-                        const int s1 = ny - mimg[3 * j + 1] + mi1;
-                        const int s2 = nz - mimg[3 * j + 2] + mi2;
-                        if (s0 < -127 || s0 > 127 || s1 < -127 || s1 > 127 || s2 < -127 || s2 > 127)
-                            set_status(status, GM_ERR_UNSUPPORTED);
-                        col[out] = j;
-                        shift[out] = make_char4((signed char)s0, (signed char)s1, (signed char)s2, 0);
-                        ++out;
+                        if (in) {
+                            const int pos = out + __popc(ball & below);
+                            const int s0 = nx - mimg[3 * j] + mi0;
+                            const int s1 = ny - mimg[3 * j + 1] + mi1;
+                            const int s2 = nz - mimg[3 * j + 2] + mi2;
+                            if (s0 < -127 || s0 > 127 || s1 < -127 || s1 > 127 || s2 < -127 || s2 > 127)
+                                set_status(status, GM_ERR_UNSUPPORTED);
+                            col[pos] = j;
+                            shift[pos] = make_char4((signed char)s0, (signed char)s1, (signed char)s2, 0);
+                        }
+                        out += __popc(ball);
                     } else {
-                        ++cnt;
+                        cnt += __popc(ball);
                     }
                 }
             }
         }
     }
-    if (!FILL) counts[i] = cnt;
+    if (!FILL && lane == 0) counts[i] = cnt;
 }
 
 __global__ void k_nl_total(const int32_t *__restrict__ rowN, int64_t cap, int64_t *n_pairs, int32_t *status) {
@@ -319,7 +336,7 @@ __global__ void k_nl_total(const int32_t *__restrict__ rowN, int64_t cap, int64_
 // ------------------------------------------------------------------ host
 struct NlWs {
     NlStruct *S;
-    int32_t *sid, *mimg, *cellid, *ccount, *cstart, *cfill, *sorted, *counts, *scan_tmp;
+    int32_t *sid, *mimg, *cellid, *ccount, *cstart, *cfill, *unsorted, *counts, *scan_tmp;
     double *xw;
     float4 *xs;
 };
@@ -336,7 +353,7 @@ static NlWs carve_nl(Carve &c, int B, int N) {
     w.ccount = c.take<int32_t>(ncmax);
     w.cstart = c.take<int32_t>(ncmax + 1);
     w.cfill = c.take<int32_t>(ncmax);
-    w.sorted = c.take<int32_t>(n1);
+    w.unsorted = c.take<int32_t>(n1);
     w.xs = c.take<float4>(n1);
     w.counts = c.take<int32_t>(n1);
     w.scan_tmp = c.take<int32_t>(scan_tmp_ints(ncmax + 1 > N ? ncmax + 1 : N));
@@ -368,17 +385,29 @@ gm_status nl_build(const gm_system &sys, double r_cut, int n_species, gm_nlist &
     }
     exclusive_scan(w.ccount, w.cstart, ncmax, w.scan_tmp, st);
     if (N > 0) {
-        k_nl_scatter<<<(N + tb - 1) / tb, tb, 0, st>>>(N, w.cellid, w.cstart, w.cfill, w.sorted);
-        k_nl_sortcells<<<(ncmax + tb - 1) / tb, tb, 0, st>>>(ncmax, w.cstart, w.sorted, w.xw, w.xs);
+        k_nl_scatter<<<(N + tb - 1) / tb, tb, 0, st>>>(N, w.cellid, w.cstart, w.cfill, w.unsorted);
+        const int G = N >= 16384 ? 8 : 32;
+        const long long warps_cells = (long long)ncmax * 32, warps_atoms = (long long)N * G;
+        k_nl_sortcells<<<(int)((warps_cells + tb - 1) / tb), tb, 0, st>>>(ncmax, w.cstart, w.unsorted, w.xw, w.xs);
         const float rc2f = (float)(r_cut * r_cut);
-        k_nl_search<false><<<(N + tb - 1) / tb, tb, 0, st>>>(N, w.S, w.sid, w.cellid, w.cstart, w.xs, w.xw, w.mimg,
-                                                             r_cut, rc2f, w.counts, nullptr, 0, nullptr, nullptr,
-                                                             status);
+        if (G == 8)
+            k_nl_search<false, 8><<<(int)((warps_atoms + tb - 1) / tb), tb, 0, st>>>(
+                N, w.S, w.sid, w.cellid, w.cstart, w.xs, w.xw, w.mimg, r_cut, rc2f, w.counts, nullptr, 0, nullptr,
+                nullptr, status);
+        else
+            k_nl_search<false, 32><<<(int)((warps_atoms + tb - 1) / tb), tb, 0, st>>>(
+                N, w.S, w.sid, w.cellid, w.cstart, w.xs, w.xw, w.mimg, r_cut, rc2f, w.counts, nullptr, 0, nullptr,
+                nullptr, status);
         exclusive_scan(w.counts, nl.row_ptr, N, w.scan_tmp, st);
         k_nl_total<<<1, 1, 0, st>>>(nl.row_ptr + N, nl.capacity, nl.n_pairs, status);
-        k_nl_search<true><<<(N + tb - 1) / tb, tb, 0, st>>>(N, w.S, w.sid, w.cellid, w.cstart, w.xs, w.xw, w.mimg,
-                                                            r_cut, rc2f, nullptr, nl.row_ptr, nl.capacity, nl.col,
-                                                            reinterpret_cast<char4 *>(nl.shift), status);
+        if (G == 8)
+            k_nl_search<true, 8><<<(int)((warps_atoms + tb - 1) / tb), tb, 0, st>>>(
+                N, w.S, w.sid, w.cellid, w.cstart, w.xs, w.xw, w.mimg, r_cut, rc2f, nullptr, nl.row_ptr, nl.capacity,
+                nl.col, reinterpret_cast<char4 *>(nl.shift), status);
+        else
+            k_nl_search<true, 32><<<(int)((warps_atoms + tb - 1) / tb), tb, 0, st>>>(
+                N, w.S, w.sid, w.cellid, w.cstart, w.xs, w.xw, w.mimg, r_cut, rc2f, nullptr, nl.row_ptr, nl.capacity,
+                nl.col, reinterpret_cast<char4 *>(nl.shift), status);
         note_launches(5);
     } else {
         exclusive_scan(w.counts, nl.row_ptr, 0, w.scan_tmp, st);

@@ -26,16 +26,36 @@ __device__ __forceinline__ int clamp_species(int z, int S, int32_t *status) {
     return z;
 }
 
-__device__ __forceinline__ void pair_displacement(const double *__restrict__ pos, double xi, double yi, double zi,
-                                                  int j, char4 sh, double Lx, double Ly, double Lz, float &fx,
-                                                  float &fy, float &fz) {
-    const double dx = (pos[3 * j] - xi) + (double)sh.x * Lx;
-    const double dy = (pos[3 * j + 1] - yi) + (double)sh.y * Ly;
-    const double dz = (pos[3 * j + 2] - zi) + (double)sh.z * Lz;
-    fx = (float)dx;
-    fy = (float)dy;
-    fz = (float)dz;
+__device__ __forceinline__ void pair_displacement(double xj, double yj, double zj, double xi, double yi, double zi,
+                                                  char4 sh, double Lx, double Ly, double Lz, float &fx, float &fy,
+                                                  float &fz) {
+    fx = (float)((xj - xi) + (double)sh.x * Lx);
+    fy = (float)((yj - yi) + (double)sh.y * Ly);
+    fz = (float)((zj - zi) + (double)sh.z * Lz);
 }
+
+// The next neighbour of a row, loaded one iteration ahead (index, shift, FP64 position).
+struct NextPair {
+    int j;
+    bool ok;
+    char4 sh;
+    double x, y, z;
+    __device__ __forceinline__ void load(const PairArgs &a, int p, int p1) {
+        ok = false;
+        if (p < p1) {
+            j = a.col[p];
+            sh = a.shift[p];
+            ok = (unsigned)j < (unsigned)a.N;
+            if (ok) {
+                x = a.pos[3 * j];
+                y = a.pos[3 * j + 1];
+                z = a.pos[3 * j + 2];
+            } else {
+                set_status(a.status, GM_ERR_ARG);
+            }
+        }
+    }
+};
 
 template <int TPA>
 __global__ void __launch_bounds__(256) k_moments(PairArgs a, float *__restrict__ psi) {
@@ -56,14 +76,15 @@ __global__ void __launch_bounds__(256) k_moments(PairArgs a, float *__restrict__
         const int zsi = clamp_species(a.species[atom], a.S, a.status);
         const float *brow = sbeta + zsi * a.S * (NR * NB);
         const int p1 = a.row_ptr[atom + 1];
+        NextPair nx;
+        nx.load(a, a.row_ptr[atom] + sub, p1);
         for (int p = a.row_ptr[atom] + sub; p < p1; p += TPA) {
-            const int j = a.col[p];
-            if ((unsigned)j >= (unsigned)a.N) {
-                set_status(a.status, GM_ERR_ARG);
-                continue;
-            }
+            const NextPair cur = nx;
+            nx.load(a, p + TPA, p1);
+            if (!cur.ok) continue;
+            const int j = cur.j;
             float fx, fy, fz;
-            pair_displacement(a.pos, xi, yi, zi, j, a.shift[p], Lx, Ly, Lz, fx, fy, fz);
+            pair_displacement(cur.x, cur.y, cur.z, xi, yi, zi, cur.sh, Lx, Ly, Lz, fx, fy, fz);
             const float r = sqrtf(fx * fx + fy * fy + fz * fz);
             const float rinv = 1.0f / r;
             float B[NB], dB[NB];
@@ -132,14 +153,15 @@ __global__ void __launch_bounds__(256) k_forces(PairArgs a, const float *__restr
         const int zsi = clamp_species(a.species[atom], a.S, a.status);
         const float *brow = sbeta + zsi * a.S * (NR * NB);
         const int p1 = a.row_ptr[atom + 1];
+        NextPair nx;
+        nx.load(a, a.row_ptr[atom] + sub, p1);
         for (int p = a.row_ptr[atom] + sub; p < p1; p += TPA) {
-            const int j = a.col[p];
-            if ((unsigned)j >= (unsigned)a.N) {
-                set_status(a.status, GM_ERR_ARG);
-                continue;
-            }
+            const NextPair cur = nx;
+            nx.load(a, p + TPA, p1);
+            if (!cur.ok) continue;
+            const int j = cur.j;
             float fx, fy, fz;
-            pair_displacement(a.pos, xi, yi, zi, j, a.shift[p], Lx, Ly, Lz, fx, fy, fz);
+            pair_displacement(cur.x, cur.y, cur.z, xi, yi, zi, cur.sh, Lx, Ly, Lz, fx, fy, fz);
             const float r = sqrtf(fx * fx + fy * fy + fz * fz);
             const float rinv = 1.0f / r;
             const float ux = fx * rinv, uy = fy * rinv, uz = fz * rinv;
@@ -239,7 +261,8 @@ void launch_moments(const PairArgs &a, int tpa, float *psi, cudaStream_t st) {
     case 2: launch_moments_t<2>(a, psi, st); break;
     case 4: launch_moments_t<4>(a, psi, st); break;
     case 8: launch_moments_t<8>(a, psi, st); break;
-    default: launch_moments_t<16>(a, psi, st); break;
+    case 16: launch_moments_t<16>(a, psi, st); break;
+    default: launch_moments_t<32>(a, psi, st); break;
     }
 }
 
@@ -249,7 +272,8 @@ void launch_forces(const PairArgs &a, int tpa, const float *dpsi, float *F, floa
     case 2: launch_forces_t<2>(a, dpsi, F, vir, st); break;
     case 4: launch_forces_t<4>(a, dpsi, F, vir, st); break;
     case 8: launch_forces_t<8>(a, dpsi, F, vir, st); break;
-    default: launch_forces_t<16>(a, dpsi, F, vir, st); break;
+    case 16: launch_forces_t<16>(a, dpsi, F, vir, st); break;
+    default: launch_forces_t<32>(a, dpsi, F, vir, st); break;
     }
 }
 

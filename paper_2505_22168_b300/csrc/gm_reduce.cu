@@ -3,6 +3,7 @@
 //   E_i = sigma_Z (sum of output-layer partials + b3) + mu_Z      (Eq. scale_shift)
 //   E_b = sum_{i in b} E_i in FP64                               (Eq. energy_sum)
 //   W_b = sum_{i in b} W_i in FP64 (per-atom virials from the force kernel)
+// Sums run over fixed chunks of atoms and then over chunks in order (deterministic).
 //   loss (section "Training": energy and force terms, per-atom division of the energy term)
 // One block per structure, fixed summation order (deterministic).
 #include "gm_internal.h"
@@ -23,45 +24,72 @@ __device__ __forceinline__ double block_sum_double(double v, double *sh) {
     return r;  // valid in thread 0
 }
 
-__global__ void __launch_bounds__(256) k_struct_reduce(int B, const int32_t *__restrict__ atom_ptr,
-                                                       const int32_t *__restrict__ species, int S,
-                                                       const float *__restrict__ sigma, const float *__restrict__ mu,
-                                                       const float *__restrict__ b3, const float *__restrict__ nn_part,
-                                                       int nparts, const float *__restrict__ vir_atom,
-                                                       double *energy, double *virial) {
-    __shared__ double sh[8];
-    const int b = blockIdx.x;
-    const int a0 = atom_ptr[b], a1 = atom_ptr[b + 1];
-    double e = 0.0, v[9];
-#pragma unroll
-    for (int q = 0; q < 9; ++q) v[q] = 0.0;
+// Phase 1: block k takes atoms [k*CH, (k+1)*CH); one warp per structure overlapping the
+// chunk sums E_i (and the per-atom virials) of its atoms in the chunk and stores the
+// partial at slot (b + k).  Consecutive chunks share at most one structure, so these
+// slots never collide and structure b finds its partials at b + k for the chunks k it
+// spans.  Phase 2 adds them in chunk order (deterministic).
+__global__ void __launch_bounds__(256) k_reduce_partial(int B, int N, const int32_t *__restrict__ atom_ptr,
+                                                        const int32_t *__restrict__ species, int S,
+                                                        const float *__restrict__ sigma, const float *__restrict__ mu,
+                                                        const float *__restrict__ b3,
+                                                        const float *__restrict__ nn_part, int nparts,
+                                                        const float *__restrict__ vir_atom, double *part) {
+    const int k = blockIdx.x;
+    const int c0 = k * REDUCE_CHUNK, c1 = min(N, c0 + REDUCE_CHUNK);
+    const int bf = structure_of(atom_ptr, B, c0), bl = structure_of(atom_ptr, B, c1 - 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const float bias = b3[0];
-    for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
-        float nn = bias;
-        for (int t = 0; t < nparts; ++t) nn += nn_part[(size_t)i * nparts + t];
-        const int z = min(max(species[i], 0), S - 1);
-        e += (double)fmaf(sigma[z], nn, mu[z]);
-        if (vir_atom)
+    for (int b = bf + warp; b <= bl; b += blockDim.x >> 5) {
+        const int lo = max(atom_ptr[b], c0), hi = min(atom_ptr[b + 1], c1);
+        double acc[10];
 #pragma unroll
-            for (int q = 0; q < 9; ++q) v[q] += (double)vir_atom[(size_t)i * 9 + q];
-    }
-    const double et = block_sum_double(e, sh);
-    if (threadIdx.x == 0) energy[b] = et;
-    if (virial) {
+        for (int q = 0; q < 10; ++q) acc[q] = 0.0;
+        for (int i = lo + lane; i < hi; i += 32) {
+            float nn = bias;
+            for (int t = 0; t < nparts; ++t) nn += nn_part[(size_t)i * nparts + t];
+            const int z = min(max(species[i], 0), S - 1);
+            acc[0] += (double)fmaf(sigma[z], nn, mu[z]);
+            if (vir_atom)
 #pragma unroll
-        for (int q = 0; q < 9; ++q) {
-            const double vt = block_sum_double(v[q], sh);
-            if (threadIdx.x == 0) virial[9 * b + q] = vt;
+                for (int q = 0; q < 9; ++q) acc[1 + q] += (double)vir_atom[(size_t)i * 9 + q];
         }
+#pragma unroll
+        for (int q = 0; q < 10; ++q)
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) acc[q] += __shfl_down_sync(0xffffffffu, acc[q], off);
+        if (lane == 0)
+#pragma unroll
+            for (int q = 0; q < 10; ++q) part[(size_t)(b + k) * 10 + q] = acc[q];
     }
 }
 
-void launch_struct_reduce(int B, const int32_t *atom_ptr, const int32_t *species, int S, const float *sigma,
+__global__ void __launch_bounds__(256) k_reduce_final(int B, const int32_t *__restrict__ atom_ptr,
+                                                      const double *__restrict__ part, double *energy,
+                                                      double *virial) {
+    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (b >= B) return;
+    const int a0 = atom_ptr[b], a1 = atom_ptr[b + 1];
+    double s = 0.0;
+    if (a1 > a0 && lane < 10)
+        for (int k = a0 / REDUCE_CHUNK; k <= (a1 - 1) / REDUCE_CHUNK; ++k) s += part[(size_t)(b + k) * 10 + lane];
+    if (lane == 0) energy[b] = s;
+    else if (lane < 10 && virial) virial[9 * b + lane - 1] = s;
+}
+
+size_t reduce_partial_doubles(int B, int N) { return (size_t)(B + (N + REDUCE_CHUNK - 1) / REDUCE_CHUNK + 1) * 10; }
+
+void launch_struct_reduce(int B, int N, const int32_t *atom_ptr, const int32_t *species, int S, const float *sigma,
                           const float *mu, const float *b3, const float *nn_part, int nparts, const float *vir_atom,
-                          double *energy, double *virial, cudaStream_t st) {
+                          double *part, double *energy, double *virial, cudaStream_t st) {
+    const int chunks = (N + REDUCE_CHUNK - 1) / REDUCE_CHUNK;
+    if (chunks > 0) {
+        k_reduce_partial<<<chunks, 256, 0, st>>>(B, N, atom_ptr, species, S, sigma, mu, b3, nn_part, nparts, vir_atom,
+                                                 part);
+        note_launches(1);
+    }
     if (B > 0) {
-        k_struct_reduce<<<B, 256, 0, st>>>(B, atom_ptr, species, S, sigma, mu, b3, nn_part, nparts, vir_atom, energy,
-                                           virial);
+        k_reduce_final<<<(B * 32 + 255) / 256, 256, 0, st>>>(B, atom_ptr, part, energy, virial);
         note_launches(1);
     }
 }

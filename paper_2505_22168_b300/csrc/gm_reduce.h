@@ -5,9 +5,11 @@
 
 namespace gm {
 
-void launch_struct_reduce(int B, const int32_t *atom_ptr, const int32_t *species, int S, const float *sigma,
+constexpr int REDUCE_CHUNK = 1024;  // atoms per block of the first reduction phase
+size_t reduce_partial_doubles(int B, int N);
+void launch_struct_reduce(int B, int N, const int32_t *atom_ptr, const int32_t *species, int S, const float *sigma,
                           const float *mu, const float *b3, const float *nn_part, int nparts, const float *vir_atom,
-                          double *energy, double *virial, cudaStream_t st);
+                          double *part, double *energy, double *virial, cudaStream_t st);
 
 void launch_loss(int B, int N, const int32_t *atom_ptr, const double *E, const double *Eref, const float *F,
                  const float *Fref, double wE, double wF, double *loss, double *gE, float *gF, cudaStream_t st);
