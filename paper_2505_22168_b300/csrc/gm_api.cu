@@ -23,6 +23,7 @@
 #include "gm_gemm.h"
 #include "gm_internal.h"
 #include "gm_pair.h"
+#include "gm_pgrad.h"
 #include "gm_reduce.h"
 
 using namespace gm;
@@ -223,6 +224,44 @@ size_t ef_workspace_bytes(int B, int N, int H) {
     return c.off + 256;
 }
 
+struct PgWs {
+    float *psi, *psid, *psib, *psidb, *GG, *Gbs, *Z, *A1s, *P1, *Q1, *Zd1, *Zb2s, *Zb1s, *Y3, *t_sig, *t_c, *t_cs,
+        *beta_part, *wg_part;
+};
+
+PgWs carve_pg(Carve &c, int N, int H, int S) {
+    PgWs w;
+    const int Mp = round_up(N, TILE_M);
+    const size_t n1 = N > 0 ? (size_t)N : 1, m1 = Mp > 0 ? (size_t)Mp : 1;
+    w.psi = c.take<float>(n1 * NPSI);
+    w.psid = c.take<float>(n1 * NPSI);
+    w.psib = c.take<float>(n1 * NPSI);
+    w.psidb = c.take<float>(n1 * NPSI);
+    w.GG = c.take<float>(2 * m1 * NFP);
+    w.Gbs = c.take<float>(2 * m1 * NFP);
+    w.Z = c.take<float>(2 * m1 * H);
+    w.A1s = c.take<float>(2 * m1 * H);
+    w.P1 = c.take<float>(m1 * H);
+    w.Q1 = c.take<float>(m1 * H);
+    w.Zd1 = c.take<float>(m1 * H);
+    w.Zb2s = c.take<float>(2 * m1 * H);
+    w.Zb1s = c.take<float>(2 * m1 * H);
+    w.Y3 = c.take<float>(m1 * H);
+    w.t_sig = c.take<float>(m1);
+    w.t_c = c.take<float>(m1);
+    w.t_cs = c.take<float>(m1);
+    w.beta_part = c.take<float>((size_t)(pg_beta_blocks(N) + 1) * S * S * NR * NB);
+    const int ks = wgrad_ksplit(2 * Mp);
+    w.wg_part = c.take<float>((size_t)ks * NFP * (H > NFP ? H : NFP) + (size_t)ks * H * H);
+    return w;
+}
+
+size_t pg_workspace_bytes(int N, int H, int S) {
+    Carve c(reinterpret_cast<void *>(256), ~size_t(0) >> 1);
+    carve_pg(c, N, H, S);
+    return c.off + 256;
+}
+
 bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 gm_status check_system(const gm_model *m, const gm_system *s) {
@@ -383,7 +422,7 @@ gm_status gm_workspace_size(const gm_model *m, int32_t n_structures, int32_t n_a
     switch (op) {
     case GM_OP_NEIGHBORS: *bytes = nl_workspace_bytes(n_structures, n_atoms); return GM_OK;
     case GM_OP_ENERGY_FORCES: *bytes = ef_workspace_bytes(n_structures, n_atoms, m->H); return GM_OK;
-    case GM_OP_PARAM_GRAD: *bytes = ef_workspace_bytes(n_structures, n_atoms, m->H); return GM_OK;
+    case GM_OP_PARAM_GRAD: *bytes = pg_workspace_bytes(n_atoms, m->H, m->S); return GM_OK;
     default: return fail(GM_ERR_ARG, "unknown op");
     }
 }
@@ -549,9 +588,58 @@ gm_status gm_descriptors(const gm_model *m, const gm_system *sys, const gm_nlist
 gm_status gm_param_grad(const gm_model *m, const gm_system *sys, const gm_nlist *nl, const double *dL_dE,
                         const float *dL_dF, float *grad_theta, void *ws, size_t ws_bytes, int32_t *status,
                         struct CUstream_st *stream) {
-    (void)m; (void)sys; (void)nl; (void)dL_dE; (void)dL_dF; (void)grad_theta; (void)ws; (void)ws_bytes;
-    (void)status; (void)stream;
-    return fail(GM_ERR_UNSUPPORTED, "parameter gradient not available yet");
+    gm_status s = check_system(m, sys);
+    if (s != GM_OK) return s;
+    if ((s = check_nlist(sys, nl, true)) != GM_OK) return s;
+    if (!dL_dE || !grad_theta || !status || (sys->n_atoms > 0 && !dL_dF)) return fail(GM_ERR_ARG, "null argument");
+    const int N = sys->n_atoms, B = sys->n_structures, H = m->H, S = m->S;
+    Carve c(ws, ws_bytes);
+    PgWs w = carve_pg(c, N, H, S);
+    if (!c.ok) return fail(GM_ERR_WORKSPACE, "workspace too small");
+    cudaStream_t st = stream;
+    const ThetaOff o = theta_offsets(S, H);
+    if (cudaMemsetAsync(grad_theta, 0, sizeof(float) * o.total, st) != cudaSuccess)
+        return fail(GM_ERR_CUDA, "memset of the gradient failed");
+    if (N == 0) return launch_status();
+    const int Mp = round_up(N, TILE_M);
+    const int act = m->d.activation;
+    PairArgs a = pair_args(m, sys, nl, status);
+    {   // primal and tangent moments, features and their tangents
+        StageScope sc(ST_PG_PAIR_FWD, st);
+        launch_moments(a, choose_tpa(m, N), w.psi, st);
+        launch_moments_tangent(a, dL_dF, w.psid, st);
+        launch_contract_fwd_dual(w.psi, w.psid, N, Mp, w.GG, st);
+    }
+    {   // network forward (primal + tangent rows) and reverse
+        StageScope sc(ST_PG_NETWORK, st);
+        EpiArgs e{};
+        e.out0 = w.Z;
+        gemm_f32(EPI_STORE, 0, w.GG, m->W1t, 2 * Mp, H, NFP, e, st);
+        pg_act1(act, Mp, H, w.Z, m->b1, w.A1s, w.P1, w.Q1, w.Zd1, st);
+        gemm_f32(EPI_STORE, 0, w.A1s, m->W2t, 2 * Mp, H, H, e, st);
+        pg_act2(act, N, Mp, H, B, sys->atom_ptr, sys->species, S, dL_dE, m->sigma, m->w3, m->b2, m->b3, w.Z, w.Zb2s,
+                w.Y3, w.t_sig, w.t_c, w.t_cs, st);
+        gemm_f32(EPI_STORE, 0, w.Zb2s, m->W2, 2 * Mp, H, H, e, st);         // a1 adjoints (primal, tangent)
+        pg_act1b(Mp, H, w.Z, w.P1, w.Q1, w.Zd1, w.Zb1s, st);
+        e.out0 = w.Gbs;
+        gemm_f32(EPI_STORE, 0, w.Zb1s, m->W1p, 2 * Mp, NFP, H, e, st);     // feature adjoints
+        // weight and bias gradients
+        wgrad(w.GG, NFP, w.Zb1s, H, 2 * Mp, NFP, H, NF, w.wg_part, grad_theta + o.W1, st);
+        wgrad(w.A1s, H, w.Zb2s, H, 2 * Mp, H, H, H, w.wg_part, grad_theta + o.W2, st);
+        colsum(Mp, H, w.Zb1s, grad_theta + o.b1, st);
+        colsum(Mp, H, w.Zb2s, grad_theta + o.b2, st);
+        colsum(Mp, H, w.Y3, grad_theta + o.w3, st);
+        pg_tail(N, sys->species, S, w.t_sig, w.t_c, w.t_cs, grad_theta + o.sigma, grad_theta + o.mu,
+                grad_theta + o.b3, st);
+    }
+    {   // moment adjoints and the species-pair coefficient gradient
+        StageScope sc(ST_PG_PAIR_BWD, st);
+        launch_contract_bwd_dual(w.psi, w.psid, w.Gbs, N, Mp, w.psib, w.psidb, st);
+        launch_pg_beta(a, dL_dF, w.psib, w.psidb, w.beta_part, st);
+        pg_beta_reduce(pg_beta_blocks(N), S * S * NR * NB, (float)(1.0 / sqrt((double)NB)), w.beta_part,
+                       grad_theta + o.beta, st);
+    }
+    return launch_status();
 }
 
 gm_status gm_force_matching_loss(const gm_system *sys, const double *energy, const double *energy_ref,

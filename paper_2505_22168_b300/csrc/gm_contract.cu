@@ -37,6 +37,32 @@ constexpr int AC_STRIDE = NPSI + 1;
 #define AM(s, a, b) A[(s) * NC + idx2(a, b)]
 #define AT(s, a, b, c) A[(s) * NC + idx3(a, b, c)]
 
+// Forward-mode dual number (value, derivative along a tangent direction).  The features
+// are polynomials of the moments, so running the same group code on duals gives exact
+// tangents (parameter gradient: dG along dPsi, and the second-order term of the adjoint).
+struct Dual {
+    float v, d;
+};
+__device__ __forceinline__ float mad(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ Dual mad(Dual a, Dual b, Dual c) { return {fmaf(a.v, b.v, c.v), fmaf(a.d, b.v, fmaf(a.v, b.d, c.d))}; }
+__device__ __forceinline__ Dual mad(float a, Dual b, Dual c) { return {fmaf(a, b.v, c.v), fmaf(a, b.d, c.d)}; }
+__device__ __forceinline__ Dual mad(Dual a, float b, Dual c) { return {fmaf(a.v, b, c.v), fmaf(a.d, b, c.d)}; }
+__device__ __forceinline__ Dual operator+(Dual a, Dual b) { return {a.v + b.v, a.d + b.d}; }
+__device__ __forceinline__ Dual &operator+=(Dual &a, Dual b) { a.v += b.v; a.d += b.d; return a; }
+__device__ __forceinline__ Dual &operator+=(Dual &a, float b) { a.v += b; return a; }
+__device__ __forceinline__ Dual operator*(float a, Dual b) { return {a * b.v, a * b.d}; }
+__device__ __forceinline__ Dual operator*(Dual a, Dual b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }
+template <typename T> __device__ __forceinline__ T zero();
+template <> __device__ __forceinline__ float zero<float>() { return 0.0f; }
+template <> __device__ __forceinline__ Dual zero<Dual>() { return {0.0f, 0.0f}; }
+
+// feature stores: plain values to one tile row, duals to a value row and a tangent row
+struct FeatOut {
+    float *v, *d;
+    __device__ __forceinline__ void put(int f, float x) const { v[f] = x; }
+    __device__ __forceinline__ void put(int f, Dual x) const { v[f] = x.v; d[f] = x.d; }
+};
+
 __host__ __device__ constexpr bool f7_group_has(int part, int s1) {
     return part == 3 ? s1 == 0 : (part == 4 ? (s1 == 1 || s1 == 4) : (s1 == 2 || s1 == 3));
 }
@@ -57,54 +83,54 @@ __device__ __forceinline__ void load_psi(const float *__restrict__ psi, int m, i
 }
 
 // ------------------------------------------------------------------ forward groups
-template <int PART>
-__device__ __forceinline__ void fwd_group(const float (&P)[NPSI], float *gt) {
+template <int PART, typename T>
+__device__ __forceinline__ void fwd_group(const T (&P)[NPSI], const FeatOut &gt) {
     if (PART == 0) {
 #pragma unroll
-        for (int s = 0; s < NR; ++s) gt[FAM_OFF1 + s] = P[s * NC];
+        for (int s = 0; s < NR; ++s) gt.put(FAM_OFF1 + s, P[s * NC]);
 #pragma unroll
         for (int s1 = 0; s1 < NR; ++s1)
 #pragma unroll
             for (int s2 = s1; s2 < NR; ++s2) {
-                float f2 = 0.0f, f3 = 0.0f, f4 = 0.0f;
+                T f2 = zero<T>(), f3 = zero<T>(), f4 = zero<T>();
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    f2 = fmaf(PV(s1, a), PV(s2, a), f2);
+                    f2 = mad(PV(s1, a), PV(s2, a), f2);
 #pragma unroll
                     for (int b = 0; b < 3; ++b) {
-                        f3 = fmaf(PM(s1, a, b), PM(s2, a, b), f3);
+                        f3 = mad(PM(s1, a, b), PM(s2, a, b), f3);
 #pragma unroll
-                        for (int c = 0; c < 3; ++c) f4 = fmaf(PT(s1, a, b, c), PT(s2, a, b, c), f4);
+                        for (int c = 0; c < 3; ++c) f4 = mad(PT(s1, a, b, c), PT(s2, a, b, c), f4);
                     }
                 }
                 const int q = pair_le_index(s1, s2);
-                gt[FAM_OFF2 + q] = f2;
-                gt[FAM_OFF3 + q] = f3;
-                gt[FAM_OFF4 + q] = f4;
+                gt.put(FAM_OFF2 + q, f2);
+                gt.put(FAM_OFF3 + q, f3);
+                gt.put(FAM_OFF4 + q, f4);
             }
     } else if (PART == 1) {
 #pragma unroll
         for (int s1 = 0; s1 < NR; ++s1)
 #pragma unroll
             for (int s2 = s1; s2 < NR; ++s2) {
-                float Nm[3][3];
+                T Nm[3][3];
 #pragma unroll
                 for (int a = 0; a < 3; ++a)
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        float v = 0.0f;
+                        T v = zero<T>();
 #pragma unroll
-                        for (int b = 0; b < 3; ++b) v = fmaf(PM(s1, a, b), PM(s2, b, c), v);
+                        for (int b = 0; b < 3; ++b) v = mad(PM(s1, a, b), PM(s2, b, c), v);
                         Nm[a][c] = v;
                     }
 #pragma unroll
                 for (int s3 = s2; s3 < NR; ++s3) {
-                    float f = 0.0f;
+                    T f = zero<T>();
 #pragma unroll
                     for (int a = 0; a < 3; ++a)
 #pragma unroll
-                        for (int c = 0; c < 3; ++c) f = fmaf(Nm[a][c], PM(s3, c, a), f);
-                    gt[FAM_OFF5 + f5_index(s1, s2, s3)] = f;
+                        for (int c = 0; c < 3; ++c) f = mad(Nm[a][c], PM(s3, c, a), f);
+                    gt.put(FAM_OFF5 + f5_index(s1, s2, s3), f);
                 }
             }
     } else if (PART == 2) {
@@ -112,20 +138,20 @@ __device__ __forceinline__ void fwd_group(const float (&P)[NPSI], float *gt) {
         for (int s2 = 0; s2 < NR; ++s2)
 #pragma unroll
             for (int s3 = 0; s3 < NR; ++s3) {
-                float w[3];
+                T w[3];
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    float v = 0.0f;
+                    T v = zero<T>();
 #pragma unroll
-                    for (int b = 0; b < 3; ++b) v = fmaf(PM(s2, a, b), PV(s3, b), v);
+                    for (int b = 0; b < 3; ++b) v = mad(PM(s2, a, b), PV(s3, b), v);
                     w[a] = v;
                 }
 #pragma unroll
                 for (int s1 = 0; s1 <= s3; ++s1) {
-                    float f = 0.0f;
+                    T f = zero<T>();
 #pragma unroll
-                    for (int a = 0; a < 3; ++a) f = fmaf(PV(s1, a), w[a], f);
-                    gt[FAM_OFF6 + f6_index(s1, s2, s3)] = f;
+                    for (int a = 0; a < 3; ++a) f = mad(PV(s1, a), w[a], f);
+                    gt.put(FAM_OFF6 + f6_index(s1, s2, s3), f);
                 }
             }
     } else if (PART >= 3 && PART <= 5) {
@@ -134,26 +160,26 @@ __device__ __forceinline__ void fwd_group(const float (&P)[NPSI], float *gt) {
             if (!f7_group_has(PART, s1)) continue;
 #pragma unroll
             for (int s2 = s1; s2 < NR; ++s2) {
-                float Q[3][3];
+                T Q[3][3];
 #pragma unroll
                 for (int c = 0; c < 3; ++c)
 #pragma unroll
                     for (int d = 0; d < 3; ++d) {
-                        float v = 0.0f;
+                        T v = zero<T>();
 #pragma unroll
                         for (int a = 0; a < 3; ++a)
 #pragma unroll
-                            for (int b = 0; b < 3; ++b) v = fmaf(PT(s1, a, b, c), PT(s2, a, b, d), v);
+                            for (int b = 0; b < 3; ++b) v = mad(PT(s1, a, b, c), PT(s2, a, b, d), v);
                         Q[c][d] = v;
                     }
 #pragma unroll
                 for (int s3 = 0; s3 < NR; ++s3) {
-                    float f = 0.0f;
+                    T f = zero<T>();
 #pragma unroll
                     for (int c = 0; c < 3; ++c)
 #pragma unroll
-                        for (int d = 0; d < 3; ++d) f = fmaf(Q[c][d], PM(s3, c, d), f);
-                    gt[FAM_OFF7 + f7_index(s1, s2, s3)] = f;
+                        for (int d = 0; d < 3; ++d) f = mad(Q[c][d], PM(s3, c, d), f);
+                    gt.put(FAM_OFF7 + f7_index(s1, s2, s3), f);
                 }
             }
         }
@@ -163,22 +189,22 @@ __device__ __forceinline__ void fwd_group(const float (&P)[NPSI], float *gt) {
             if (!f8_group_has(PART, s2)) continue;
 #pragma unroll
             for (int s3 = 0; s3 < NR; ++s3) {
-                float U[3];
+                T U[3];
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    float v = 0.0f;
+                    T v = zero<T>();
 #pragma unroll
                     for (int b = 0; b < 3; ++b)
 #pragma unroll
-                        for (int c = 0; c < 3; ++c) v = fmaf(PT(s2, a, b, c), PM(s3, b, c), v);
+                        for (int c = 0; c < 3; ++c) v = mad(PT(s2, a, b, c), PM(s3, b, c), v);
                     U[a] = v;
                 }
 #pragma unroll
                 for (int s1 = 0; s1 < NR; ++s1) {
-                    float f = 0.0f;
+                    T f = zero<T>();
 #pragma unroll
-                    for (int a = 0; a < 3; ++a) f = fmaf(PV(s1, a), U[a], f);
-                    gt[FAM_OFF8 + f8_index(s1, s2, s3)] = f;
+                    for (int a = 0; a < 3; ++a) f = mad(PV(s1, a), U[a], f);
+                    gt.put(FAM_OFF8 + f8_index(s1, s2, s3), f);
                 }
             }
         }
@@ -200,7 +226,7 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_contract_fwd(const float *__r
     const int m0 = blockIdx.x * CT_ATOMS;
     float P[NPSI];
     load_psi(psi, m0 + lane, N, P);
-    float *gt = tile + lane * GT_STRIDE;
+    const FeatOut gt{tile + lane * GT_STRIDE, nullptr};
     switch (warp) {
     case 0: fwd_group<0>(P, gt); break;
     case 1: fwd_group<1>(P, gt); break;
@@ -230,8 +256,8 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_contract_fwd(const float *__r
 }
 
 // ------------------------------------------------------------------ backward groups
-template <int PART>
-__device__ __forceinline__ void bwd_group(const float (&P)[NPSI], const float *gb, float (&A)[NPSI]) {
+template <int PART, typename T>
+__device__ __forceinline__ void bwd_group(const T (&P)[NPSI], const float *gb, T (&A)[NPSI]) {
     if (PART == 0) {
 #pragma unroll
         for (int s = 0; s < NR; ++s) A[s * NC] += gb[FAM_OFF1 + s];
@@ -243,16 +269,16 @@ __device__ __forceinline__ void bwd_group(const float (&P)[NPSI], const float *g
                 const float g2 = gb[FAM_OFF2 + q], g3 = gb[FAM_OFF3 + q], g4 = gb[FAM_OFF4 + q];
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    AV(s1, a) = fmaf(g2, PV(s2, a), AV(s1, a));
-                    AV(s2, a) = fmaf(g2, PV(s1, a), AV(s2, a));
+                    AV(s1, a) = mad(g2, PV(s2, a), AV(s1, a));
+                    AV(s2, a) = mad(g2, PV(s1, a), AV(s2, a));
 #pragma unroll
                     for (int b = 0; b < 3; ++b) {
-                        AM(s1, a, b) = fmaf(g3, PM(s2, a, b), AM(s1, a, b));
-                        AM(s2, a, b) = fmaf(g3, PM(s1, a, b), AM(s2, a, b));
+                        AM(s1, a, b) = mad(g3, PM(s2, a, b), AM(s1, a, b));
+                        AM(s2, a, b) = mad(g3, PM(s1, a, b), AM(s2, a, b));
 #pragma unroll
                         for (int c = 0; c < 3; ++c) {
-                            AT(s1, a, b, c) = fmaf(g4, PT(s2, a, b, c), AT(s1, a, b, c));
-                            AT(s2, a, b, c) = fmaf(g4, PT(s1, a, b, c), AT(s2, a, b, c));
+                            AT(s1, a, b, c) = mad(g4, PT(s2, a, b, c), AT(s1, a, b, c));
+                            AT(s2, a, b, c) = mad(g4, PT(s1, a, b, c), AT(s2, a, b, c));
                         }
                     }
                 }
@@ -269,16 +295,16 @@ __device__ __forceinline__ void bwd_group(const float (&P)[NPSI], const float *g
                     for (int a = 0; a < 3; ++a)
 #pragma unroll
                         for (int b = 0; b < 3; ++b) {
-                            float v1 = 0.0f, v2 = 0.0f, v3 = 0.0f;
+                            T v1 = zero<T>(), v2 = zero<T>(), v3 = zero<T>();
 #pragma unroll
                             for (int c = 0; c < 3; ++c) {
-                                v1 = fmaf(PM(s2, a, c), PM(s3, c, b), v1);   // d/d(M1)_ba -> (M2 M3)_ab
-                                v2 = fmaf(PM(s3, a, c), PM(s1, c, b), v2);   // d/d(M2)_ba -> (M3 M1)_ab
-                                v3 = fmaf(PM(s1, a, c), PM(s2, c, b), v3);   // d/d(M3)_ba -> (M1 M2)_ab
+                                v1 = mad(PM(s2, a, c), PM(s3, c, b), v1);   // d/d(M1)_ba -> (M2 M3)_ab
+                                v2 = mad(PM(s3, a, c), PM(s1, c, b), v2);   // d/d(M2)_ba -> (M3 M1)_ab
+                                v3 = mad(PM(s1, a, c), PM(s2, c, b), v3);   // d/d(M3)_ba -> (M1 M2)_ab
                             }
-                            AM(s1, b, a) = fmaf(g, v1, AM(s1, b, a));
-                            AM(s2, b, a) = fmaf(g, v2, AM(s2, b, a));
-                            AM(s3, b, a) = fmaf(g, v3, AM(s3, b, a));
+                            AM(s1, b, a) = mad(g, v1, AM(s1, b, a));
+                            AM(s2, b, a) = mad(g, v2, AM(s2, b, a));
+                            AM(s3, b, a) = mad(g, v3, AM(s3, b, a));
                         }
                 }
     } else if (PART == 2) {
@@ -291,15 +317,15 @@ __device__ __forceinline__ void bwd_group(const float (&P)[NPSI], const float *g
                     const float g = gb[FAM_OFF6 + f6_index(s1, s2, s3)];
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
-                        float w13 = 0.0f, w31 = 0.0f;
+                        T w13 = zero<T>(), w31 = zero<T>();
 #pragma unroll
                         for (int b = 0; b < 3; ++b) {
-                            w13 = fmaf(PM(s2, a, b), PV(s3, b), w13);
-                            w31 = fmaf(PM(s2, a, b), PV(s1, b), w31);
-                            AM(s2, a, b) = fmaf(g * PV(s1, a), PV(s3, b), AM(s2, a, b));
+                            w13 = mad(PM(s2, a, b), PV(s3, b), w13);
+                            w31 = mad(PM(s2, a, b), PV(s1, b), w31);
+                            AM(s2, a, b) = mad(g * PV(s1, a), PV(s3, b), AM(s2, a, b));
                         }
-                        AV(s1, a) = fmaf(g, w13, AV(s1, a));
-                        AV(s3, a) = fmaf(g, w31, AV(s3, a));
+                        AV(s1, a) = mad(g, w13, AV(s1, a));
+                        AV(s3, a) = mad(g, w31, AV(s3, a));
                     }
                 }
     } else if (PART >= 3 && PART <= 5) {
@@ -308,18 +334,18 @@ __device__ __forceinline__ void bwd_group(const float (&P)[NPSI], const float *g
             if (!f7_group_has(PART, s1)) continue;
 #pragma unroll
             for (int s2 = s1; s2 < NR; ++s2) {
-                float Mw[3][3], Q[3][3];
+                T Mw[3][3], Q[3][3];
 #pragma unroll
                 for (int c = 0; c < 3; ++c)
 #pragma unroll
                     for (int d = 0; d < 3; ++d) {
-                        float v = 0.0f, w = 0.0f;
+                        T v = zero<T>(), w = zero<T>();
 #pragma unroll
-                        for (int s3 = 0; s3 < NR; ++s3) w = fmaf(gb[FAM_OFF7 + f7_index(s1, s2, s3)], PM(s3, c, d), w);
+                        for (int s3 = 0; s3 < NR; ++s3) w = mad(gb[FAM_OFF7 + f7_index(s1, s2, s3)], PM(s3, c, d), w);
 #pragma unroll
                         for (int a = 0; a < 3; ++a)
 #pragma unroll
-                            for (int b = 0; b < 3; ++b) v = fmaf(PT(s1, a, b, c), PT(s2, a, b, d), v);
+                            for (int b = 0; b < 3; ++b) v = mad(PT(s1, a, b, c), PT(s2, a, b, d), v);
                         Mw[c][d] = w;
                         Q[c][d] = v;
                     }
@@ -329,7 +355,7 @@ __device__ __forceinline__ void bwd_group(const float (&P)[NPSI], const float *g
 #pragma unroll
                     for (int c = 0; c < 3; ++c)
 #pragma unroll
-                        for (int d = 0; d < 3; ++d) AM(s3, c, d) = fmaf(g, Q[c][d], AM(s3, c, d));
+                        for (int d = 0; d < 3; ++d) AM(s3, c, d) = mad(g, Q[c][d], AM(s3, c, d));
                 }
 #pragma unroll
                 for (int a = 0; a < 3; ++a)
@@ -337,11 +363,11 @@ __device__ __forceinline__ void bwd_group(const float (&P)[NPSI], const float *g
                     for (int b = 0; b < 3; ++b)
 #pragma unroll
                         for (int c = 0; c < 3; ++c) {
-                            float t1 = 0.0f, t2 = 0.0f;
+                            T t1 = zero<T>(), t2 = zero<T>();
 #pragma unroll
                             for (int d = 0; d < 3; ++d) {
-                                t1 = fmaf(PT(s2, a, b, d), Mw[c][d], t1);   // d/d(T1)_abc
-                                t2 = fmaf(PT(s1, a, b, d), Mw[d][c], t2);   // d/d(T2)_abc
+                                t1 = mad(PT(s2, a, b, d), Mw[c][d], t1);   // d/d(T1)_abc
+                                t2 = mad(PT(s1, a, b, d), Mw[d][c], t2);   // d/d(T2)_abc
                             }
                             AT(s1, a, b, c) += t1;
                             AT(s2, a, b, c) += t2;
@@ -354,16 +380,16 @@ __device__ __forceinline__ void bwd_group(const float (&P)[NPSI], const float *g
             if (!f8_group_has(PART, s2)) continue;
 #pragma unroll
             for (int s3 = 0; s3 < NR; ++s3) {
-                float U[3], Vw[3];
+                T U[3], Vw[3];
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    float v = 0.0f, w = 0.0f;
+                    T v = zero<T>(), w = zero<T>();
 #pragma unroll
                     for (int b = 0; b < 3; ++b)
 #pragma unroll
-                        for (int c = 0; c < 3; ++c) v = fmaf(PT(s2, a, b, c), PM(s3, b, c), v);
+                        for (int c = 0; c < 3; ++c) v = mad(PT(s2, a, b, c), PM(s3, b, c), v);
 #pragma unroll
-                    for (int s1 = 0; s1 < NR; ++s1) w = fmaf(gb[FAM_OFF8 + f8_index(s1, s2, s3)], PV(s1, a), w);
+                    for (int s1 = 0; s1 < NR; ++s1) w = mad(gb[FAM_OFF8 + f8_index(s1, s2, s3)], PV(s1, a), w);
                     U[a] = v;
                     Vw[a] = w;
                 }
@@ -371,7 +397,7 @@ __device__ __forceinline__ void bwd_group(const float (&P)[NPSI], const float *g
                 for (int s1 = 0; s1 < NR; ++s1) {
                     const float g = gb[FAM_OFF8 + f8_index(s1, s2, s3)];
 #pragma unroll
-                    for (int a = 0; a < 3; ++a) AV(s1, a) = fmaf(g, U[a], AV(s1, a));
+                    for (int a = 0; a < 3; ++a) AV(s1, a) = mad(g, U[a], AV(s1, a));
                 }
 #pragma unroll
                 for (int a = 0; a < 3; ++a)
@@ -379,8 +405,8 @@ __device__ __forceinline__ void bwd_group(const float (&P)[NPSI], const float *g
                     for (int b = 0; b < 3; ++b)
 #pragma unroll
                         for (int c = 0; c < 3; ++c) {
-                            AT(s2, a, b, c) = fmaf(Vw[a], PM(s3, b, c), AT(s2, a, b, c));
-                            AM(s3, b, c) = fmaf(Vw[a], PT(s2, a, b, c), AM(s3, b, c));
+                            AT(s2, a, b, c) = mad(Vw[a], PM(s3, b, c), AT(s2, a, b, c));
+                            AM(s3, b, c) = mad(Vw[a], PT(s2, a, b, c), AM(s3, b, c));
                         }
             }
         }
@@ -429,7 +455,163 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_contract_bwd(const float *__r
     }
 }
 
+// ------------------------------------------------------------------ parameter-gradient variants
+// Dual forward: features G and their tangents Gd = dG/dPsi . Psid, written as the stacked
+// GEMM operand GG [2 Mp][384] (rows m: G, rows Mp + m: Gd; FP32).
+__global__ void __launch_bounds__(CT_THREADS, 1) k_contract_fwd_dual(const float *__restrict__ psi,
+                                                                     const float *__restrict__ psid, int N, int Mp,
+                                                                     float *__restrict__ GG) {
+    extern __shared__ float tiles[];
+    float *tv = tiles, *td = tiles + CT_ATOMS * GT_STRIDE;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * CT_ATOMS;
+    Dual P[NPSI];
+    {
+        float a[NPSI], b[NPSI];
+        load_psi(psi, m0 + lane, N, a);
+        load_psi(psid, m0 + lane, N, b);
+#pragma unroll
+        for (int q = 0; q < NPSI; ++q) P[q] = {a[q], b[q]};
+    }
+    const FeatOut gt{tv + lane * GT_STRIDE, td + lane * GT_STRIDE};
+    switch (warp) {
+    case 0: fwd_group<0>(P, gt); break;
+    case 1: fwd_group<1>(P, gt); break;
+    case 2: fwd_group<2>(P, gt); break;
+    case 3: fwd_group<3>(P, gt); break;
+    case 4: fwd_group<4>(P, gt); break;
+    case 5: fwd_group<5>(P, gt); break;
+    case 6: fwd_group<6>(P, gt); break;
+    default: fwd_group<7>(P, gt); break;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < CT_ATOMS * NFP; idx += CT_THREADS) {
+        const int r = idx / NFP, f = idx - r * NFP, m = m0 + r;
+        if (m >= Mp) continue;
+        GG[(size_t)m * NFP + f] = f < NF ? tv[r * GT_STRIDE + f] : 0.0f;
+        GG[(size_t)(Mp + m) * NFP + f] = f < NF ? td[r * GT_STRIDE + f] : 0.0f;
+    }
+}
+
+// Dual backward.  With Gb = dJ/dG and Gdb = dJ/dGd (stacked in Gbs [2 Mp][384]):
+//   psib  = J^T Gb + (dJ^T/dPsi . Psid) Gdb   (adjoint of the moments)
+//   psidb = J^T Gdb                            (adjoint of the tangent moments)
+// where J = dG/dPsi.  The second term is the tangent part of J^T Gdb evaluated on duals.
+__global__ void __launch_bounds__(CT_THREADS, 1) k_contract_bwd_dual(const float *__restrict__ psi,
+                                                                     const float *__restrict__ psid,
+                                                                     const float *__restrict__ Gbs, int N, int Mp,
+                                                                     float *__restrict__ psib,
+                                                                     float *__restrict__ psidb) {
+    extern __shared__ float sm[];
+    float *gtile = sm;                                // Gb
+    float *gdtile = sm + CT_ATOMS * GT_STRIDE;         // Gdb
+    float *acc1 = gdtile + CT_ATOMS * GT_STRIDE;       // psib
+    float *acc2 = acc1 + CT_ATOMS * AC_STRIDE;         // psidb
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * CT_ATOMS;
+    for (int idx = threadIdx.x; idx < CT_ATOMS * NF; idx += CT_THREADS) {
+        const int r = idx / NF, f = idx - r * NF, m = m0 + r;
+        gtile[r * GT_STRIDE + f] = m < N ? Gbs[(size_t)m * NFP + f] : 0.0f;
+        gdtile[r * GT_STRIDE + f] = m < N ? Gbs[(size_t)(Mp + m) * NFP + f] : 0.0f;
+    }
+    __syncthreads();
+    float *arow1 = acc1 + lane * AC_STRIDE, *arow2 = acc2 + lane * AC_STRIDE;
+    {   // J^T Gb
+        float P[NPSI], A[NPSI];
+        load_psi(psi, m0 + lane, N, P);
+#pragma unroll
+        for (int q = 0; q < NPSI; ++q) A[q] = 0.0f;
+        const float *gb = gtile + lane * GT_STRIDE;
+        switch (warp) {
+        case 0: bwd_group<0>(P, gb, A); break;
+        case 1: bwd_group<1>(P, gb, A); break;
+        case 2: bwd_group<2>(P, gb, A); break;
+        case 3: bwd_group<3>(P, gb, A); break;
+        case 4: bwd_group<4>(P, gb, A); break;
+        case 5: bwd_group<5>(P, gb, A); break;
+        case 6: bwd_group<6>(P, gb, A); break;
+        default: bwd_group<7>(P, gb, A); break;
+        }
+        for (int w = 0; w < CT_THREADS / 32; ++w) {
+            if (warp == w) {
+#pragma unroll
+                for (int q = 0; q < NPSI; ++q) arow1[q] = (w == 0 ? 0.0f : arow1[q]) + A[q];
+            }
+            __syncthreads();
+        }
+    }
+    {   // J^T Gdb on duals: value -> psidb, tangent -> second-order part of psib
+        Dual P[NPSI], A[NPSI];
+        {
+            float a[NPSI], b[NPSI];
+            load_psi(psi, m0 + lane, N, a);
+            load_psi(psid, m0 + lane, N, b);
+#pragma unroll
+            for (int q = 0; q < NPSI; ++q) {
+                P[q] = {a[q], b[q]};
+                A[q] = {0.0f, 0.0f};
+            }
+        }
+        const float *gb = gdtile + lane * GT_STRIDE;
+        switch (warp) {
+        case 0: bwd_group<0>(P, gb, A); break;
+        case 1: bwd_group<1>(P, gb, A); break;
+        case 2: bwd_group<2>(P, gb, A); break;
+        case 3: bwd_group<3>(P, gb, A); break;
+        case 4: bwd_group<4>(P, gb, A); break;
+        case 5: bwd_group<5>(P, gb, A); break;
+        case 6: bwd_group<6>(P, gb, A); break;
+        default: bwd_group<7>(P, gb, A); break;
+        }
+        for (int w = 0; w < CT_THREADS / 32; ++w) {
+            if (warp == w) {
+#pragma unroll
+                for (int q = 0; q < NPSI; ++q) {
+                    arow1[q] += A[q].d;
+                    arow2[q] = (w == 0 ? 0.0f : arow2[q]) + A[q].v;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int idx = threadIdx.x; idx < CT_ATOMS * NPSI; idx += CT_THREADS) {
+        const int r = idx / NPSI, q = idx - r * NPSI, m = m0 + r;
+        if (m < N) {
+            psib[(size_t)m * NPSI + q] = acc1[r * AC_STRIDE + q];
+            psidb[(size_t)m * NPSI + q] = acc2[r * AC_STRIDE + q];
+        }
+    }
+}
+
 // ------------------------------------------------------------------ launchers
+void launch_contract_fwd_dual(const float *psi, const float *psid, int N, int Mp, float *GG, cudaStream_t st) {
+    const int blocks = (Mp + CT_ATOMS - 1) / CT_ATOMS;
+    const size_t smem = sizeof(float) * 2 * CT_ATOMS * GT_STRIDE;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_contract_fwd_dual, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    if (blocks > 0) {
+        k_contract_fwd_dual<<<blocks, CT_THREADS, smem, st>>>(psi, psid, N, Mp, GG);
+        note_launches(1);
+    }
+}
+
+void launch_contract_bwd_dual(const float *psi, const float *psid, const float *Gbs, int N, int Mp, float *psib,
+                              float *psidb, cudaStream_t st) {
+    const int blocks = (N + CT_ATOMS - 1) / CT_ATOMS;
+    const size_t smem = sizeof(float) * (2 * CT_ATOMS * GT_STRIDE + 2 * CT_ATOMS * AC_STRIDE);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_contract_bwd_dual, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    if (blocks > 0) {
+        k_contract_bwd_dual<<<blocks, CT_THREADS, smem, st>>>(psi, psid, Gbs, N, Mp, psib, psidb);
+        note_launches(1);
+    }
+}
 void launch_contract_fwd_f32(const float *psi, int N, int Mp, float *G, float *features_out, cudaStream_t st) {
     const int blocks = (Mp + CT_ATOMS - 1) / CT_ATOMS;
     const size_t smem = sizeof(float) * CT_ATOMS * GT_STRIDE;

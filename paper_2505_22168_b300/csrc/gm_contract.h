@@ -14,4 +14,10 @@ void launch_contract_fwd_bf16(const float *psi, int N, int Mp, __nv_bfloat16 *G,
 // dE/dG [Mp][384] FP32 and psi -> dE/dpsi [N][100] FP32 (unique components)
 void launch_contract_bwd(const float *psi, const float *dG, int N, float *dpsi, cudaStream_t st);
 
+// Parameter gradient: GG [2Mp][384] = [G; dG/dPsi . psid]; and from Gbs = [dJ/dG; dJ/dGd]
+// the moment adjoints psib, psidb [N][100] (see gm_contract.cu).
+void launch_contract_fwd_dual(const float *psi, const float *psid, int N, int Mp, float *GG, cudaStream_t st);
+void launch_contract_bwd_dual(const float *psi, const float *psid, const float *Gbs, int N, int Mp, float *psib,
+                              float *psidb, cudaStream_t st);
+
 }  // namespace gm

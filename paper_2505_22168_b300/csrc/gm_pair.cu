@@ -231,6 +231,159 @@ __global__ void __launch_bounds__(256) k_forces(PairArgs a, const float *__restr
     }
 }
 
+// Tangent moments for the parameter gradient: dPsi_i/dt when every position moves along
+// v (= dL/dF), i.e. d_ij changes by v_j - v_i.  Per pair and component c of rank L:
+//   d/dt [R_s m_c] = R'_s w m_c + R_s (D_c - L_c m_c w) / r,  w = u . dd,  D_c = dd . dm_c/du.
+template <int TPA>
+__global__ void __launch_bounds__(256) k_moments_tangent(PairArgs a, const float *__restrict__ vel,
+                                                         float *__restrict__ psid) {
+    extern __shared__ float sbeta[];
+    const int nbeta = a.S * a.S * NR * NB;
+    for (int q = threadIdx.x; q < nbeta; q += blockDim.x) sbeta[q] = a.beta[q];
+    __syncthreads();
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int atom = g / TPA, sub = g % TPA;
+    const bool active = atom < a.N && !status_bad(a.status);
+    float acc[NPSI];
+#pragma unroll
+    for (int q = 0; q < NPSI; ++q) acc[q] = 0.0f;
+    if (active) {
+        const int b = structure_of(a.atom_ptr, a.B, atom);
+        const double Lx = a.cell[9 * b], Ly = a.cell[9 * b + 4], Lz = a.cell[9 * b + 8];
+        const double xi = a.pos[3 * atom], yi = a.pos[3 * atom + 1], zi = a.pos[3 * atom + 2];
+        const float vix = vel[3 * atom], viy = vel[3 * atom + 1], viz = vel[3 * atom + 2];
+        const int zsi = clamp_species(a.species[atom], a.S, a.status);
+        const float *brow = sbeta + zsi * a.S * (NR * NB);
+        const int p1 = a.row_ptr[atom + 1];
+        NextPair nx;
+        nx.load(a, a.row_ptr[atom] + sub, p1);
+        for (int p = a.row_ptr[atom] + sub; p < p1; p += TPA) {
+            const NextPair cur = nx;
+            nx.load(a, p + TPA, p1);
+            if (!cur.ok) continue;
+            const int j = cur.j;
+            float fx, fy, fz;
+            pair_displacement(cur.x, cur.y, cur.z, xi, yi, zi, cur.sh, Lx, Ly, Lz, fx, fy, fz);
+            const float r = sqrtf(fx * fx + fy * fy + fz * fz);
+            const float rinv = 1.0f / r;
+            const float ux = fx * rinv, uy = fy * rinv, uz = fz * rinv;
+            const float ddx = vel[3 * j] - vix, ddy = vel[3 * j + 1] - viy, ddz = vel[3 * j + 2] - viz;
+            const float w = ux * ddx + uy * ddy + uz * ddz;
+            float B[NB], dB[NB];
+            radial_basis<true>(a.rc, r, B, dB);
+            const float *bt = brow + clamp_species(a.species[j], a.S, a.status) * (NR * NB);
+            float R[NR], Rp[NR];
+#pragma unroll
+            for (int s = 0; s < NR; ++s) {
+                float x = 0.0f, y = 0.0f;
+#pragma unroll
+                for (int k = 0; k < NB; ++k) {
+                    x = fmaf(bt[s * NB + k], B[k], x);
+                    y = fmaf(bt[s * NB + k], dB[k], y);
+                }
+                R[s] = x;
+                Rp[s] = y * w;
+            }
+            float m[NC];
+            monomials(ux, uy, uz, m);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const float Dc = ddx * dmono(c, 0, ux, uy, uz) + ddy * dmono(c, 1, ux, uy, uz) +
+                                 ddz * dmono(c, 2, ux, uy, uz);
+                const float ang = (Dc - (float)comp_rank(c) * m[c] * w) * rinv;
+#pragma unroll
+                for (int s = 0; s < NR; ++s) acc[s * NC + c] = fmaf(Rp[s], m[c], fmaf(R[s], ang, acc[s * NC + c]));
+            }
+        }
+    }
+    if (TPA > 1) {
+#pragma unroll
+        for (int off = TPA / 2; off > 0; off >>= 1)
+#pragma unroll
+            for (int q = 0; q < NPSI; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], off);
+    }
+    if (!active) return;
+    float *out = psid + (size_t)atom * NPSI;
+#pragma unroll
+    for (int q = 0; q < NPSI; ++q)
+        if (q % TPA == sub) out[q] = acc[q];
+}
+
+// Species-pair coefficient gradient.  With psib = dJ/dPsi and psidb = dJ/dPsid of atom i,
+// per pair and radial function s (coefficients pre-scaled by n_basis^{-1/2}):
+//   dJ/dbeta[zi][zj][s][k] += B_k (P1_s + P3_s / r) + B'_k w P2_s
+//   P1_s = sum_c psib[s][c] m_c,  P2_s = sum_c psidb[s][c] m_c,
+//   P3_s = sum_c psidb[s][c] (D_c - L_c m_c w)
+// accumulated per block in shared memory, block partials written to part[block][S S 35].
+template <int TPA>
+__global__ void __launch_bounds__(256) k_pg_beta(PairArgs a, const float *__restrict__ vel,
+                                                 const float *__restrict__ psib, const float *__restrict__ psidb,
+                                                 float *__restrict__ part) {
+    extern __shared__ float sm[];
+    const int nbeta = a.S * a.S * NR * NB;
+    float *acc = sm;
+    for (int q = threadIdx.x; q < nbeta; q += blockDim.x) acc[q] = 0.0f;
+    __syncthreads();
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int atom = g / TPA, sub = g % TPA;
+    const bool active = atom < a.N && !status_bad(a.status);
+    if (active) {
+        float pb[NPSI], pdb[NPSI];
+#pragma unroll
+        for (int q = 0; q < NPSI; ++q) {
+            pb[q] = psib[(size_t)atom * NPSI + q];
+            pdb[q] = psidb[(size_t)atom * NPSI + q];
+        }
+        const int b = structure_of(a.atom_ptr, a.B, atom);
+        const double Lx = a.cell[9 * b], Ly = a.cell[9 * b + 4], Lz = a.cell[9 * b + 8];
+        const double xi = a.pos[3 * atom], yi = a.pos[3 * atom + 1], zi = a.pos[3 * atom + 2];
+        const float vix = vel[3 * atom], viy = vel[3 * atom + 1], viz = vel[3 * atom + 2];
+        const int zsi = clamp_species(a.species[atom], a.S, a.status);
+        const int p1 = a.row_ptr[atom + 1];
+        NextPair nx;
+        nx.load(a, a.row_ptr[atom] + sub, p1);
+        for (int p = a.row_ptr[atom] + sub; p < p1; p += TPA) {
+            const NextPair cur = nx;
+            nx.load(a, p + TPA, p1);
+            if (!cur.ok) continue;
+            const int j = cur.j;
+            float fx, fy, fz;
+            pair_displacement(cur.x, cur.y, cur.z, xi, yi, zi, cur.sh, Lx, Ly, Lz, fx, fy, fz);
+            const float r = sqrtf(fx * fx + fy * fy + fz * fz);
+            const float rinv = 1.0f / r;
+            const float ux = fx * rinv, uy = fy * rinv, uz = fz * rinv;
+            const float ddx = vel[3 * j] - vix, ddy = vel[3 * j + 1] - viy, ddz = vel[3 * j + 2] - viz;
+            const float w = ux * ddx + uy * ddy + uz * ddz;
+            float B[NB], dB[NB];
+            radial_basis<true>(a.rc, r, B, dB);
+            float m[NC], ang[NC];
+            monomials(ux, uy, uz, m);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const float Dc = ddx * dmono(c, 0, ux, uy, uz) + ddy * dmono(c, 1, ux, uy, uz) +
+                                 ddz * dmono(c, 2, ux, uy, uz);
+                ang[c] = Dc - (float)comp_rank(c) * m[c] * w;
+            }
+            float *dst = acc + (zsi * a.S + clamp_species(a.species[j], a.S, a.status)) * (NR * NB);
+#pragma unroll
+            for (int s = 0; s < NR; ++s) {
+                float P1 = 0.0f, P2 = 0.0f, P3 = 0.0f;
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    P1 = fmaf(pb[s * NC + c], m[c], P1);
+                    P2 = fmaf(pdb[s * NC + c], m[c], P2);
+                    P3 = fmaf(pdb[s * NC + c], ang[c], P3);
+                }
+                const float alpha = fmaf(P3, rinv, P1), gam = w * P2;
+#pragma unroll
+                for (int k = 0; k < NB; ++k) atomicAdd(dst + s * NB + k, fmaf(B[k], alpha, dB[k] * gam));
+            }
+        }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < nbeta; q += blockDim.x) part[(size_t)blockIdx.x * nbeta + q] = acc[q];
+}
+
 template <int TPA>
 static void launch_moments_t(const PairArgs &a, float *psi, cudaStream_t st) {
     const int threads = 256;
@@ -274,6 +427,34 @@ void launch_forces(const PairArgs &a, int tpa, const float *dpsi, float *F, floa
     case 8: launch_forces_t<8>(a, dpsi, F, vir, st); break;
     case 16: launch_forces_t<16>(a, dpsi, F, vir, st); break;
     default: launch_forces_t<32>(a, dpsi, F, vir, st); break;
+    }
+}
+
+}  // namespace gm
+
+namespace gm {
+
+void launch_moments_tangent(const PairArgs &a, const float *vel, float *psid, cudaStream_t st) {
+    const int threads = 256, TPA = 4;
+    const long long total = (long long)a.N * TPA;
+    const int blocks = (int)((total + threads - 1) / threads);
+    const size_t smem = sizeof(float) * a.S * a.S * NR * NB;
+    if (blocks > 0) {
+        k_moments_tangent<TPA><<<blocks, threads, smem, st>>>(a, vel, psid);
+        note_launches(1);
+    }
+}
+
+int pg_beta_blocks(int N) { return (N * 4 + 255) / 256; }
+
+void launch_pg_beta(const PairArgs &a, const float *vel, const float *psib, const float *psidb, float *part,
+                    cudaStream_t st) {
+    const int threads = 256, TPA = 4;
+    const int blocks = pg_beta_blocks(a.N);
+    const size_t smem = sizeof(float) * a.S * a.S * NR * NB;
+    if (blocks > 0) {
+        k_pg_beta<TPA><<<blocks, threads, smem, st>>>(a, vel, psib, psidb, part);
+        note_launches(1);
     }
 }
 

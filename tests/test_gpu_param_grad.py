@@ -1,0 +1,106 @@
+"""GPU force-matching loss and parameter gradient (force double-backward) against the FP64
+oracle, through the C ABI and through the torch.autograd.Function.
+
+Tolerance (no figure is stated for the gradient): relative L2 error per parameter group
+<= 1e-4 for the FP32 kernels, and element-wise |error| <= 1e-3 x max|group|."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.parity import subset
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+GROUPS = ("beta", "W1", "b1", "W2", "b2", "w3", "b3", "sigma", "mu")
+TOL_L2 = 1e-4
+TOL_ELEM = 1e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2505_22168_b300 import build
+    build.build()
+
+
+def _setup(batch, desc, params, precision="fp32", seed=11):
+    from paper_2505_22168_b300 import GMNN, DeviceSystem
+    m = GMNN(desc, params, precision=precision)
+    sysd = DeviceSystem(batch)
+    nl = m.build_neighbors(sysd)
+    onl = oracle.neighbors(batch, desc["r_cut"])
+    ref = oracle.energy_forces(batch, desc, params, onl)
+    rng = np.random.default_rng(seed)
+    Eref = ref["E"] + rng.normal(0, 0.5, ref["E"].shape)
+    Fref = ref["F"] + rng.normal(0, 0.1, ref["F"].shape)
+    return m, sysd, nl, onl, ref, Eref, Fref
+
+
+def _compare(g_dev, go, n_species, n_hidden):
+    from paper_2505_22168_b300 import unpack_theta
+    g = unpack_theta(g_dev.cpu().numpy().astype(np.float64), n_species, n_hidden)
+    for k in GROUPS:
+        ref = go[k].reshape(-1)
+        got = g[k].reshape(-1)
+        scale = np.linalg.norm(ref)
+        assert scale > 0, k
+        rel = np.linalg.norm(got - ref) / scale
+        assert rel <= TOL_L2, (k, rel)
+        assert np.abs(got - ref).max() <= TOL_ELEM * np.abs(ref).max(), k
+
+
+def _param_grad_case(batch, desc, params):
+    m, sysd, nl, onl, ref, Eref, Fref = _setup(batch, desc, params)
+    E, F, _ = m.energy_forces(sysd, nl)
+    m.check_status()
+    Eref_d = torch.as_tensor(Eref, device=m.device)
+    Fref_d = torch.as_tensor(Fref, dtype=torch.float32, device=m.device)
+    loss, gE, gF = m.force_matching_loss(sysd, E, Eref_d, F, Fref_d)
+    g = m.param_grad(sysd, nl, gE, gF)
+    m.check_status()
+    L_o, gE_o, gF_o = oracle.loss(batch, ref["E"], Eref, ref["F"], Fref)
+    assert abs(float(loss.item()) - L_o) <= 1e-5 * abs(L_o)
+    assert np.abs(gE.cpu().numpy() - gE_o).max() <= 1e-5 * np.abs(gE_o).max()
+    assert np.abs(gF.cpu().numpy() - gF_o).max() <= 1e-4 * np.abs(gF_o).max()
+    go = oracle.param_grad(batch, desc, params, onl, gE_o, gF_o)
+    _compare(g, go, desc["n_species"], desc["n_hidden"])
+
+
+@pytest.mark.parametrize("act", ["tanh", "silu"])
+def test_param_grad_config1(act):
+    b, d, p = synth.config(1, activation=act)
+    _param_grad_case(b, d, p)
+
+
+def test_param_grad_emim_batch():
+    """Several EMIM boxes of different sizes (the training workload's structure)."""
+    b4, d, p = synth.config(4)
+    _param_grad_case(subset(b4, [0, 1, 2, 5]), d, p)
+
+
+def test_param_grad_small_li3po4_boxes_multi_image():
+    b3, d, p = synth.config(3)
+    p = dict(p)
+    _param_grad_case(subset(b3, range(6)), d, p)
+
+
+def test_autograd_function_backward_matches_oracle():
+    """theta.grad from loss.backward() through GMNNFunction equals the oracle's gradient of
+    the same loss (computed here with torch ops on the outputs)."""
+    from paper_2505_22168_b300 import GMNNFunction, pack_theta
+    b, d, p = synth.config(1, activation="silu")
+    m, sysd, nl, onl, ref, Eref, Fref = _setup(b, d, p)
+    theta = torch.as_tensor(pack_theta(p), device=m.device).requires_grad_(True)
+    E, F = GMNNFunction.apply(theta, m, sysd, nl)
+    nat = torch.as_tensor(np.diff(b.atom_ptr), dtype=torch.float64, device=m.device)
+    L = (((E - torch.as_tensor(Eref, device=m.device)) / nat) ** 2).mean() + \
+        ((F.double() - torch.as_tensor(Fref, device=m.device)) ** 2).sum() / (3 * b.n_atoms)
+    L.backward()
+    m.check_status()
+    _, gE_o, gF_o = oracle.loss(b, ref["E"], Eref, ref["F"], Fref)
+    go = oracle.param_grad(b, d, p, onl, gE_o, gF_o)
+    _compare(theta.grad, go, d["n_species"], d["n_hidden"])
