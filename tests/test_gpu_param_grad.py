@@ -57,16 +57,21 @@ def _param_grad_case(batch, desc, params):
     m, sysd, nl, onl, ref, Eref, Fref = _setup(batch, desc, params)
     E, F, _ = m.energy_forces(sysd, nl)
     m.check_status()
+    # the loss kernel, on the GPU's own energies and forces
     Eref_d = torch.as_tensor(Eref, device=m.device)
     Fref_d = torch.as_tensor(Fref, dtype=torch.float32, device=m.device)
     loss, gE, gF = m.force_matching_loss(sysd, E, Eref_d, F, Fref_d)
-    g = m.param_grad(sysd, nl, gE, gF)
+    L_g, gE_g, gF_g = oracle.loss(batch, E.cpu().numpy(), Eref, F.cpu().numpy().astype(np.float64),
+                                  Fref_d.cpu().numpy().astype(np.float64))
+    assert abs(float(loss.item()) - L_g) <= 1e-12 * abs(L_g)
+    assert np.abs(gE.cpu().numpy() - gE_g).max() <= 1e-12 * np.abs(gE_g).max()
+    assert np.abs(gF.cpu().numpy() - gF_g).max() <= 1e-6 * np.abs(gF_g).max()
+    # the parameter gradient, with the oracle's dL/dE and dL/dF fed to both sides
+    _, gE_o, gF_o = oracle.loss(batch, ref["E"], Eref, ref["F"], Fref)
+    g = m.param_grad(sysd, nl, torch.as_tensor(gE_o, device=m.device),
+                     torch.as_tensor(gF_o, dtype=torch.float32, device=m.device))
     m.check_status()
-    L_o, gE_o, gF_o = oracle.loss(batch, ref["E"], Eref, ref["F"], Fref)
-    assert abs(float(loss.item()) - L_o) <= 1e-5 * abs(L_o)
-    assert np.abs(gE.cpu().numpy() - gE_o).max() <= 1e-5 * np.abs(gE_o).max()
-    assert np.abs(gF.cpu().numpy() - gF_o).max() <= 1e-4 * np.abs(gF_o).max()
-    go = oracle.param_grad(batch, desc, params, onl, gE_o, gF_o)
+    go = oracle.param_grad(batch, desc, params, onl, gE_o, gF_o.astype(np.float32).astype(np.float64))
     _compare(g, go, desc["n_species"], desc["n_hidden"])
 
 
@@ -101,6 +106,7 @@ def test_autograd_function_backward_matches_oracle():
         ((F.double() - torch.as_tensor(Fref, device=m.device)) ** 2).sum() / (3 * b.n_atoms)
     L.backward()
     m.check_status()
-    _, gE_o, gF_o = oracle.loss(b, ref["E"], Eref, ref["F"], Fref)
+    # the oracle's gradient of the same loss at the same (GPU) energies and forces
+    _, gE_o, gF_o = oracle.loss(b, E.detach().cpu().numpy(), Eref, F.detach().cpu().numpy().astype(np.float64), Fref)
     go = oracle.param_grad(b, d, p, onl, gE_o, gF_o)
     _compare(theta.grad, go, d["n_species"], d["n_hidden"])
