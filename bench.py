@@ -103,66 +103,82 @@ class _Nvml:
         return v.value / 1000.0 if self.lib.nvmlDeviceGetPowerUsage(h, self.ct.byref(v)) == 0 else None
 
 
+_SAMPLER_CHILD = r"""
+import sys, time, select
+sys.path.insert(0, sys.argv[3])
+from bench import _Nvml
+nv = _Nvml()
+h = nv.handle(sys.argv[1], int(sys.argv[2]))
+print("max", nv.max_clock(h), flush=True)
+while True:
+    print("s", nv.clock(h), nv.reasons(h), nv.power_w(h), flush=True)
+    r, _, _ = select.select([sys.stdin], [], [], 0.01)
+    if r:
+        break
+"""
+
+
 class ClockSampler:
-    """SM clock, power and clock-event reasons sampled every 10 ms through NVML (read
-    only) while the timed region runs."""
+    """SM clock, power and clock-event reasons sampled every 10 ms through NVML (read only)
+    by a child process while the timed region runs (no contention with the launch loop)."""
 
     REASONS = {"hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40,
                "sw_power_cap": 0x4}
 
     def __init__(self, torch_device=0):
-        self.samples = []
-        self._stop = threading.Event()
-        self._thread = None
-        self.handle = None
-        self.max_mhz = None
+        self.proc = None
+        self.lines = []
         self.error = None
+        self.uuid, self.index = "", torch_device
         try:
             import torch
             uuid = str(torch.cuda.get_device_properties(torch_device).uuid)
-            uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
-            self.nv = _Nvml()
-            self.handle = self.nv.handle(uuid, torch_device)
-            self.max_mhz = self.nv.max_clock(self.handle)
+            self.uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
         except Exception as exc:
-            self.handle = None
             self.error = f"{type(exc).__name__}: {exc}"
 
-    def _sample(self):
-        self.samples.append((self.nv.clock(self.handle), self.nv.reasons(self.handle), self.nv.power_w(self.handle)))
-
-    def _run(self):
-        while not self._stop.is_set():
-            try:
-                self._sample()
-            except Exception:
-                pass
-            self._stop.wait(0.01)
-
     def __enter__(self):
-        if self.handle is not None:
-            self._sample()
-            self._thread = threading.Thread(target=self._run, daemon=True)
-            self._thread.start()
+        try:
+            self.proc = subprocess.Popen([sys.executable, "-c", _SAMPLER_CHILD, self.uuid, str(self.index), str(ROOT)],
+                                         stdin=subprocess.PIPE, stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                                         text=True)
+            first = self.proc.stdout.readline()      # wait until sampling has started
+            self.lines.append(first)
+        except Exception as exc:
+            self.error = f"{type(exc).__name__}: {exc}"
+            self.proc = None
         return self
 
     def __exit__(self, *exc):
-        if self._thread is not None:
-            self._stop.set()
-            self._thread.join(timeout=2)
-            try:
-                self._sample()
-            except Exception:
-                pass
+        if self.proc is None:
+            return
+        try:
+            out, err = self.proc.communicate(input="stop\n", timeout=10)
+            self.lines += out.splitlines()
+            if err.strip():
+                self.error = err.strip().splitlines()[-1]
+        except Exception as exc:
+            self.proc.kill()
+            self.error = f"{type(exc).__name__}: {exc}"
 
     def summary(self):
-        clks = [c for c, _, _ in self.samples if c is not None]
+        max_mhz, clks, reasons, powers = None, [], set(), []
+        for line in self.lines:
+            p = line.split()
+            if not p:
+                continue
+            if p[0] == "max" and len(p) > 1 and p[1] != "None":
+                max_mhz = int(p[1])
+            elif p[0] == "s" and len(p) >= 4 and p[1] != "None":
+                clks.append(int(p[1]))
+                r = int(p[2])
+                reasons |= {name for name, bit in self.REASONS.items() if r & bit}
+                if p[3] != "None":
+                    powers.append(float(p[3]))
         if not clks:
-            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["unavailable"], "samples": 0,
+            return {"sm_mhz": None, "sm_max_mhz": max_mhz, "reasons": ["unavailable"], "samples": 0,
                     "error": self.error}
-        reasons = sorted({name for _, r, _ in self.samples for name, bit in self.REASONS.items() if r & bit})
-        powers = [p for _, _, p in self.samples if p is not None]
-        return {"sm_mhz": statistics.median(clks), "sm_max_mhz": self.max_mhz, "reasons": reasons,
+        return {"sm_mhz": statistics.median(clks), "sm_max_mhz": max_mhz, "reasons": sorted(reasons),
                 "samples": len(clks), "power_w_max": max(powers) if powers else None, "source": "NVML"}
 
 
@@ -248,11 +264,12 @@ def run_gpu(args, cfg, precision, steps, warmup, world, rank, measure_e2e, clock
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=model.device)
     stream = torch.cuda.current_stream()
 
-    def step(k):
-        sysd.pos = pos_dev[k]
-        model.clear_status()
-        model.build_neighbors(sysd, nl, check=False)
-        model.energy_forces(sysd, nl, out=out, clear=False)
+    pos_buf = torch.empty_like(sysd.pos)
+    sysd.pos = pos_buf
+
+    def step(k):                       # stream launches
+        pos_buf.copy_(pos_dev[k])
+        model.step(sysd, nl, out)
 
     for k in range(warmup):
         step(k)
@@ -261,30 +278,51 @@ def run_gpu(args, cfg, precision, steps, warmup, world, rank, measure_e2e, clock
         raise RuntimeError(f"device status {model.read_status()} during warm-up")
     n_pairs = int(nl.n_pairs.item())
 
+    # per-step launch count (library kernels), measured on one uncaptured step
+    _lib.gm_profile_reset()
+    step(0)
+    stream.synchronize()
+    per_step_launches = _lib.gm_profile_collect()[1]
+
+    graph = model.capture_step(sysd, nl, out) if args.graph else None
+
+    def timed(k, use_graph):
+        flush.zero_()
+        ev0[k].record(stream)
+        if use_graph:
+            pos_buf.copy_(pos_dev[warmup + k])
+            graph.replay()
+        else:
+            step(warmup + k)
+        ev1[k].record(stream)
+
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
     stream.synchronize()
-    _lib.gm_profile_reset()
-    _lib.gm_profile_enable(args.stage_timing)
     if clock_sampler is not None:
         clock_sampler.__enter__()
     for k in range(steps):
-        flush.zero_()
-        ev0[k].record(stream)
-        step(warmup + k)
-        ev1[k].record(stream)
+        timed(k, graph is not None)
     stream.synchronize()
     if clock_sampler is not None:
         clock_sampler.__exit__(None, None, None)
-    _lib.gm_profile_enable(False)
-    stages, launches = _lib.gm_profile_collect()
     status = model.read_status()
     if status != 0:
         raise RuntimeError(f"device status {_lib.STATUS_NAMES.get(status, status)} in the timed region")
     ms = sum(ev0[k].elapsed_time(ev1[k]) for k in range(steps))
+    launches = per_step_launches * steps
+    # stage timing: the same steps launched on the stream with the library's stage events
+    _lib.gm_profile_reset()
+    _lib.gm_profile_enable(args.stage_timing)
+    for k in range(steps):
+        timed(k, False)
+    stream.synchronize()
+    _lib.gm_profile_enable(False)
+    stages, _ = _lib.gm_profile_collect()
+    ms_stream = sum(ev0[k].elapsed_time(ev1[k]) for k in range(steps))
     if world > 1:
         import torch.distributed as dist
         t = torch.tensor([ms], dtype=torch.float64, device=model.device)
@@ -292,7 +330,9 @@ def run_gpu(args, cfg, precision, steps, warmup, world, rank, measure_e2e, clock
         ms = float(t.item())
         dist.barrier()
     res = {"ms_total": ms, "ms_per_step": ms / steps, "n_atoms": n, "n_pairs": n_pairs, "stages": stages,
-           "launches": launches, "H": desc["n_hidden"], "value": world * n * steps / (ms / 1e3)}
+           "launches": launches, "H": desc["n_hidden"], "value": world * n * steps / (ms / 1e3),
+           "launch_mode": "cuda-graph replay" if graph is not None else "stream launches",
+           "ms_per_step_stream_with_stage_events": ms_stream / steps}
 
     if measure_e2e:
         # end to end through the public API with host buffers: pinned positions in,
@@ -302,15 +342,14 @@ def run_gpu(args, cfg, precision, steps, warmup, world, rank, measure_e2e, clock
                     for k in range(e2e_steps)]
         E_host = torch.empty(batch.n_structures, dtype=torch.float64).pin_memory()
         F_host = torch.empty(n, 3, dtype=torch.float32).pin_memory()
-        pos_buf = torch.empty_like(sysd.pos)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for k in range(e2e_steps):
             pos_buf.copy_(host_pos[k], non_blocking=True)
-            sysd.pos = pos_buf
-            model.clear_status()
-            model.build_neighbors(sysd, nl, check=False)
-            model.energy_forces(sysd, nl, out=out, clear=False)
+            if graph is not None:
+                graph.replay()
+            else:
+                model.step(sysd, nl, out)
             E_host.copy_(out[0], non_blocking=True)
             F_host.copy_(out[1], non_blocking=True)
             stream.synchronize()
@@ -322,6 +361,63 @@ def run_gpu(args, cfg, precision, steps, warmup, world, rank, measure_e2e, clock
                       "d2h_bytes_per_step": int(E_host.numel() * 8 + F_host.numel() * 4), "steps": e2e_steps}
     del pos_dev, flush
     return res
+
+
+def run_train(args, steps, warmup):
+    """Training step on configs[3] (32 EMIM+BF4- boxes of 96-384 atoms, MLP 2x128): neighbour
+    rebuild, energies and forces, force-matching loss against teacher labels, and the
+    parameter gradient.  Reference labels come from the FP64 oracle with the teacher's
+    parameters (set-up, untimed)."""
+    import torch
+
+    import oracle
+    import synth
+    from synth.configs import teacher_params
+    from paper_2505_22168_b300 import GMNN, DeviceSystem, _lib
+
+    batch, desc, params = synth.config(4)
+    onl = oracle.neighbors(batch, desc["r_cut"])
+    teach = oracle.energy_forces(batch, desc, teacher_params(4), onl, virial=False)
+    model = GMNN(desc, params, precision="fp32")
+    sysd = DeviceSystem(batch)
+    nl = model.build_neighbors(sysd)
+    from paper_2505_22168_b300 import NeighborList
+    nl = NeighborList(batch.n_atoms, int(nl.capacity * 1.05) + 1024, model.device)
+    Eref = torch.as_tensor(teach["E"], device=model.device)
+    Fref = torch.as_tensor(teach["F"], dtype=torch.float32, device=model.device)
+    stream = torch.cuda.current_stream()
+    out = (torch.empty(batch.n_structures, dtype=torch.float64, device=model.device),
+           torch.empty(batch.n_atoms, 3, dtype=torch.float32, device=model.device), None)
+
+    def step():
+        model.clear_status()
+        model.build_neighbors(sysd, nl, check=False)
+        model.energy_forces(sysd, nl, out=out, clear=False)
+        loss, gE, gF = model.force_matching_loss(sysd, out[0], Eref, out[1], Fref)
+        return model.param_grad(sysd, nl, gE, gF, clear=False)
+
+    for _ in range(warmup):
+        step()
+    stream.synchronize()
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    _lib.gm_profile_reset()
+    _lib.gm_profile_enable(args.stage_timing)
+    for k in range(steps):
+        ev0[k].record(stream)
+        step()
+        ev1[k].record(stream)
+    stream.synchronize()
+    _lib.gm_profile_enable(False)
+    stages, launches = _lib.gm_profile_collect()
+    if model.read_status() != 0:
+        raise RuntimeError("device status set in the training run")
+    ms = sum(ev0[k].elapsed_time(ev1[k]) for k in range(steps))
+    total = sum(v[0] for v in stages.values() if v[1] > 0) or 1.0
+    return {"workload": "emim-train-32 (configs[3]: 32 EMIM+BF4- boxes, 7920 atoms, r_cut 5 A, MLP 2x128)",
+            "precision": "fp32", "step": "neighbours + energy/forces + loss + parameter gradient",
+            "value": batch.n_atoms * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+            "steps": steps, "stage_share": {k: round(v[0] / total, 4) for k, v in stages.items() if v[1] > 0}}
 
 
 # ----------------------------------------------------------------------------- CPU (oracle)
@@ -368,6 +464,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--stage-timing", type=int, default=1)
+    ap.add_argument("--graph", type=int, default=1, help="replay the step as a CUDA graph")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -433,6 +530,9 @@ def main():
                                  "dominant": rf["kernel"] if rf else None, "roofline_frac": rf["frac"] if rf else None,
                                  "stage_share": sh})
 
+    if not args.no_variants:
+        variants.append(run_train(args, max(5, args.steps // 5), args.warmup))
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.config, args.cpu_seconds)
@@ -448,7 +548,9 @@ def main():
         "config": {"workload": WORKLOADS[args.config], "precision": precision, "n_atoms": head["n_atoms"],
                    "n_pairs": head["n_pairs"], "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "256 MiB buffer written between timed steps (outside the step events)",
-                   "neighbour_rebuild": "every step", "stage_timing_events": bool(args.stage_timing)},
+                   "neighbour_rebuild": "every step", "launch_mode": head["launch_mode"],
+                   "stage_timing": "library stage events on a second pass of the same steps launched on the stream "
+                                   f"({head['ms_per_step_stream_with_stage_events']:.4f} ms/step)"},
         "roofline": roof, "stage_share": share, "cpu_baseline": cpu, "e2e": head.get("e2e"),
         "gpu_launches": head["launches"], "clocks": clocks, "variants": variants,
     }

@@ -212,7 +212,7 @@ EfWs carve_ef(Carve &c, int B, int N, int H) {
     w.dZ2 = c.take<float>(m1 * H);
     w.dZ1 = c.take<float>(m1 * H);
     w.dG = c.take<float>(m1 * NFP);
-    w.nn_part = c.take<float>(m1 * (H / 64));
+    w.nn_part = c.take<float>(m1 * (H / 32));
     w.vir_atom = c.take<float>(n1 * 9);
     w.red_part = c.take<double>(reduce_partial_doubles(B, N));
     return w;
@@ -566,7 +566,7 @@ gm_status gm_energy_forces(const gm_model *m, const gm_system *sys, const gm_nli
         launch_forces(a, choose_tpa(m, N), w.dpsi, forces, virial ? w.vir_atom : nullptr, st);
     }
     StageScope sc(ST_REDUCE, st);
-    launch_struct_reduce(B, N, sys->atom_ptr, sys->species, m->S, m->sigma, m->mu, m->b3, w.nn_part, H / 64,
+    launch_struct_reduce(B, N, sys->atom_ptr, sys->species, m->S, m->sigma, m->mu, m->b3, w.nn_part, H / 32,
                          virial ? w.vir_atom : nullptr, w.red_part, energy, virial, st);
     return launch_status();
 }

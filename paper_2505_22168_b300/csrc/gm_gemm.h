@@ -4,7 +4,7 @@
 // to a multiple of 128), B is a weight matrix stored with K contiguous.  The network of
 // Eq. scale_shift runs as four of them per energy+forces evaluation:
 //   L1  Z1 = G W1:        A1 = phi(Z1 + b1), D1 = phi'(Z1 + b1)
-//   L2  Z2 = A1 W2:       a2 = phi(Z2 + b2); per-tile partial sum of a2 . w3 (energy);
+//   L2  Z2 = A1 W2:       a2 = phi(Z2 + b2); partial sums of a2 . w3 per 32 columns (energy);
 //                         dZ2 = sigma_Z w3 phi'(Z2 + b2)          (dE_i/dZ2)
 //   B1  dA1 = dZ2 W2^T:   dZ1 = dA1 * D1
 //   B0  dG = dZ1 W1^T     (stored FP32)
@@ -25,7 +25,7 @@ struct EpiArgs {
     void *out0;              // A1 (L1), dZ2 (L2), dZ1 (B1), C (STORE); row stride N
     void *out1;              // D1 (L1)
     const void *aux;         // D1 (B1)
-    float *nn_part;          // [M][N/64] (L2): partial output-layer sums per 64 columns
+    float *nn_part;          // [M][N/32] (L2): partial output-layer sums per 32 columns
 };
 // BF16 operands of the tcgen05 path are stored as hi/lo pairs, [rows][2K]: columns [0, K)
 // hold hi = bf16(x), columns [K, 2K) hold lo = bf16(x - hi).  A GEMM run with split = 0

@@ -96,8 +96,8 @@ __global__ void __launch_bounds__(256) k_gemm_f32(const float *__restrict__ A, c
             }
             *reinterpret_cast<float4 *>(o0) = make_float4(dz[0], dz[1], dz[2], dz[3]);
 #pragma unroll
-            for (int off = 8; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
-            if (tx == 0) e.nn_part[(size_t)m * (N / SB_N) + blockIdx.y] = part;
+            for (int off = 4; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+            if ((tx & 7) == 0) e.nn_part[(size_t)m * (N / 32) + (n0 + tx * 4) / 32] = part;
         }
     }
 }

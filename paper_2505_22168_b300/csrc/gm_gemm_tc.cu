@@ -67,7 +67,7 @@ cudaError_t launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, int M, int N
         attr_set = true;
     }
     dim3 grid(M / tc::BM, N / BN);
-    tc::k_gemm_tc<BN, EPI, ACT><<<grid, 128, smem, st>>>(ma, mb, M, N, K, split, e, status);
+    tc::k_gemm_tc<BN, EPI, ACT><<<grid, 256, smem, st>>>(ma, mb, M, N, K, split, e, status);
     return cudaPeekAtLastError();
 }
 

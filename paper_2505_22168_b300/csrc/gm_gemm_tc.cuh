@@ -7,7 +7,8 @@
 //   warp 1 lane 0  MMA issuer: 4 x tcgen05.mma (M=128, N=BN, K=16) per K block into one
 //                  TMEM accumulator; tcgen05.commit frees the stage, a final commit
 //                  signals the epilogue
-//   warps 0..3     epilogue: tcgen05.ld 32 lanes x 32 columns per chunk (thread = row)
+//   warps 0..7     epilogue: tcgen05.ld 32 lanes x 32 columns per chunk (thread = row;
+//                  warps w and w + 4 share TMEM lanes and split the columns)
 // Every wait on an mbarrier is bounded (about one second of %globaltimer); on expiry the
 // kernel records GM_ERR_TIMEOUT in the status word, waits (bounded) for the copies it
 // issued, releases its TMEM and returns.
@@ -167,6 +168,16 @@ __device__ __forceinline__ void unpack8_bf16(uint4 u, float *x) {
     }
 }
 
+// Activation for the BF16 path: SiLU with the fast exponential and division (their
+// error is far below BF16 rounding); tanh stays accurate (its derivative gates forces).
+template <int ACT>
+__device__ __forceinline__ float act_fast(float z, float &d1) {
+    if (ACT == 0) return act_fwd<0>(z, d1);
+    const float s = __fdividef(1.0f, 1.0f + __expf(-z));
+    d1 = s * (1.0f + z * (1.0f - s));
+    return z * s;
+}
+
 // Epilogue of one row segment of 32 columns starting at column n (multiple of 32).
 // BF16 outputs go to [m][n] (hi) and [m][N + n] (lo) of a [M][2N] array.
 template <int EPI, int ACT>
@@ -196,7 +207,7 @@ __device__ __forceinline__ void epilogue32(const EpiArgs &e, int m, int n, int N
         for (int q = 0; q < 4; ++q) {
             float a[8], d[8];
 #pragma unroll
-            for (int t = 0; t < 8; ++t) a[t] = act_fwd<ACT>(v[8 * q + t] + __ldg(e.bias + n + 8 * q + t), d[t]);
+            for (int t = 0; t < 8; ++t) a[t] = act_fast<ACT>(v[8 * q + t] + __ldg(e.bias + n + 8 * q + t), d[t]);
             pack8_split(a, ohi[q], olo[q]);
             od[2 * q] = make_float4(d[0], d[1], d[2], d[3]);
             od[2 * q + 1] = make_float4(d[4], d[5], d[6], d[7]);
@@ -210,7 +221,7 @@ __device__ __forceinline__ void epilogue32(const EpiArgs &e, int m, int n, int N
             for (int t = 0; t < 8; ++t) {
                 float d;
                 const int c = n + 8 * q + t;
-                const float a = act_fwd<ACT>(v[8 * q + t] + __ldg(e.bias + c), d);
+                const float a = act_fast<ACT>(v[8 * q + t] + __ldg(e.bias + c), d);
                 const float w = __ldg(e.w3 + c);
                 part = fmaf(a, w, part);
                 dz[t] = sg * w * d;
@@ -221,7 +232,7 @@ __device__ __forceinline__ void epilogue32(const EpiArgs &e, int m, int n, int N
 }
 
 template <int BN, int EPI, int ACT>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(256, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N, int K,
               int split, EpiArgs e, int32_t *status) {
     constexpr int STAGES = stages_for(BN);
@@ -307,21 +318,20 @@ __global__ void __launch_bounds__(128, 1)
     }
     __syncwarp();
 
-    // ---------------- epilogue: thread = row m0 + 32 warp + lane
+    // ---------------- epilogue: 8 warps; warp w reads TMEM lanes 32 (w % 4) .. +31 (rows)
+    // and column half w / 4; thread = row m0 + 32 (w % 4) + lane
     const bool ready = __all_sync(0xffffffffu, mbar_wait(done, 0, abort_flag));
     tc_fence_after();
     if (ready) {
-        const int m = m0 + warp * 32 + lane;
-        float part = 0.0f;
+        const int quad = warp & 3, half = warp >> 2;
+        const int m = m0 + quad * 32 + lane;
+        constexpr int CH = BN / 64;  // 32-column chunks per half
 #pragma unroll 1
-        for (int c = 0; c < BN / 32; ++c) {
-            float v[32];
-            tmem_ld_32cols(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
+        for (int c = half * CH; c < (half + 1) * CH; ++c) {
+            float v[32], part = 0.0f;
+            tmem_ld_32cols(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(c * 32), v);
             epilogue32<EPI, ACT>(e, m, n0 + c * 32, N, v, part);
-            if (EPI == EPI_L2 && (c & 1)) {
-                e.nn_part[(size_t)m * (N / 64) + (n0 + c * 32) / 64] = part;
-                part = 0.0f;
-            }
+            if (EPI == EPI_L2) e.nn_part[(size_t)m * (N / 32) + (n0 + c * 32) / 32] = part;
         }
     } else if (threadIdx.x == 0) {
         set_status(status, GM_ERR_TIMEOUT);

@@ -106,6 +106,32 @@ __global__ void __launch_bounds__(256) k_moments(PairArgs a, float *__restrict__
                 for (int c = 0; c < NC; ++c) acc[s * NC + c] = fmaf(R[s], m[c], acc[s * NC + c]);
         }
     }
+    if (TPA >= 8) {
+        // reduce-scatter by recursive halving: after log2(TPA) steps each lane holds
+        // 128/TPA consecutive sums (of 100 values padded to 128), ~124 shuffles for TPA 32
+        float v[128];
+#pragma unroll
+        for (int q = 0; q < 128; ++q) v[q] = q < NPSI ? acc[q] : 0.0f;
+        int start = 0;
+#pragma unroll
+        for (int off = TPA / 2, len = 64; off > 0; off >>= 1, len >>= 1) {
+            const bool upper = (sub & off) != 0;
+#pragma unroll
+            for (int q = 0; q < len; ++q) {
+                const float send = upper ? v[q] : v[len + q];
+                const float keep = upper ? v[len + q] : v[q];
+                v[q] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+            }
+            start += upper ? len : 0;
+        }
+        if (!active) return;
+        float *out = psi + (size_t)atom * NPSI;
+        constexpr int per = 128 / TPA;
+#pragma unroll
+        for (int q = 0; q < per; ++q)
+            if (start + q < NPSI) out[start + q] = v[q];
+        return;
+    }
     if (TPA > 1) {
 #pragma unroll
         for (int off = TPA / 2; off > 0; off >>= 1)

@@ -24,36 +24,41 @@ __device__ __forceinline__ double block_sum_double(double v, double *sh) {
     return r;  // valid in thread 0
 }
 
-// Phase 1: block k takes atoms [k*CH, (k+1)*CH); one warp per structure overlapping the
-// chunk sums E_i (and the per-atom virials) of its atoms in the chunk and stores the
-// partial at slot (b + k).  Consecutive chunks share at most one structure, so these
-// slots never collide and structure b finds its partials at b + k for the chunks k it
-// spans.  Phase 2 adds them in chunk order (deterministic).
-__global__ void __launch_bounds__(256) k_reduce_partial(int B, int N, const int32_t *__restrict__ atom_ptr,
-                                                        const int32_t *__restrict__ species, int S,
-                                                        const float *__restrict__ sigma, const float *__restrict__ mu,
-                                                        const float *__restrict__ b3,
-                                                        const float *__restrict__ nn_part, int nparts,
-                                                        const float *__restrict__ vir_atom, double *part) {
+// Phase 1: block k takes atoms [k*CH, (k+1)*CH), one atom per thread: E_i (and the
+// per-atom virial) go to shared memory, then one warp per structure overlapping the chunk
+// sums its run and stores the partial at slot (b + k).  Consecutive chunks share at most
+// one structure, so these slots never collide and structure b finds its partials at
+// b + k for the chunks k it spans.  Phase 2 adds them in chunk order (deterministic).
+__global__ void __launch_bounds__(REDUCE_CHUNK) k_reduce_partial(int B, int N, const int32_t *__restrict__ atom_ptr,
+                                                                 const int32_t *__restrict__ species, int S,
+                                                                 const float *__restrict__ sigma,
+                                                                 const float *__restrict__ mu,
+                                                                 const float *__restrict__ b3,
+                                                                 const float *__restrict__ nn_part, int nparts,
+                                                                 const float *__restrict__ vir_atom, double *part) {
+    __shared__ float vals[10][REDUCE_CHUNK];
     const int k = blockIdx.x;
     const int c0 = k * REDUCE_CHUNK, c1 = min(N, c0 + REDUCE_CHUNK);
+    const int i = c0 + threadIdx.x;
+    if (i < c1) {
+        float nn = b3[0];
+        for (int t = 0; t < nparts; ++t) nn += nn_part[(size_t)i * nparts + t];
+        const int z = min(max(species[i], 0), S - 1);
+        vals[0][threadIdx.x] = fmaf(sigma[z], nn, mu[z]);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) vals[1 + q][threadIdx.x] = vir_atom ? vir_atom[(size_t)i * 9 + q] : 0.0f;
+    }
+    __syncthreads();
     const int bf = structure_of(atom_ptr, B, c0), bl = structure_of(atom_ptr, B, c1 - 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const float bias = b3[0];
-    for (int b = bf + warp; b <= bl; b += blockDim.x >> 5) {
-        const int lo = max(atom_ptr[b], c0), hi = min(atom_ptr[b + 1], c1);
+    for (int b = bf + warp; b <= bl; b += REDUCE_CHUNK / 32) {
+        const int lo = max(atom_ptr[b], c0) - c0, hi = min(atom_ptr[b + 1], c1) - c0;
         double acc[10];
 #pragma unroll
         for (int q = 0; q < 10; ++q) acc[q] = 0.0;
-        for (int i = lo + lane; i < hi; i += 32) {
-            float nn = bias;
-            for (int t = 0; t < nparts; ++t) nn += nn_part[(size_t)i * nparts + t];
-            const int z = min(max(species[i], 0), S - 1);
-            acc[0] += (double)fmaf(sigma[z], nn, mu[z]);
-            if (vir_atom)
+        for (int t = lo + lane; t < hi; t += 32)
 #pragma unroll
-                for (int q = 0; q < 9; ++q) acc[1 + q] += (double)vir_atom[(size_t)i * 9 + q];
-        }
+            for (int q = 0; q < 10; ++q) acc[q] += (double)vals[q][t];
 #pragma unroll
         for (int q = 0; q < 10; ++q)
 #pragma unroll
@@ -84,7 +89,7 @@ void launch_struct_reduce(int B, int N, const int32_t *atom_ptr, const int32_t *
                           double *part, double *energy, double *virial, cudaStream_t st) {
     const int chunks = (N + REDUCE_CHUNK - 1) / REDUCE_CHUNK;
     if (chunks > 0) {
-        k_reduce_partial<<<chunks, 256, 0, st>>>(B, N, atom_ptr, species, S, sigma, mu, b3, nn_part, nparts, vir_atom,
+        k_reduce_partial<<<chunks, REDUCE_CHUNK, 0, st>>>(B, N, atom_ptr, species, S, sigma, mu, b3, nn_part, nparts, vir_atom,
                                                  part);
         note_launches(1);
     }

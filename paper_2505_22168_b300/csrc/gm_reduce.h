@@ -5,7 +5,7 @@
 
 namespace gm {
 
-constexpr int REDUCE_CHUNK = 1024;  // atoms per block of the first reduction phase
+constexpr int REDUCE_CHUNK = 256;   // atoms per block (one per thread) of the first reduction phase
 size_t reduce_partial_doubles(int B, int N);
 void launch_struct_reduce(int B, int N, const int32_t *atom_ptr, const int32_t *species, int S, const float *sigma,
                           const float *mu, const float *b3, const float *nn_part, int nparts, const float *vir_atom,

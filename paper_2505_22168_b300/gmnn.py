@@ -193,6 +193,28 @@ class GMNN:
                            _ptr(self.status), _stream())
         return E, F, W
 
+    def step(self, sysd: DeviceSystem, nl: NeighborList, out):
+        """One MD-style step on the current stream: clear the status word, rebuild the
+        neighbour list into nl (fixed capacity) and evaluate energies and forces into out."""
+        self.clear_status()
+        self.build_neighbors(sysd, nl, check=False)
+        return self.energy_forces(sysd, nl, out=out, clear=False)
+
+    def capture_step(self, sysd: DeviceSystem, nl: NeighborList, out):
+        """CUDA graph of step() for fixed buffers (sysd.pos, nl, out, the workspaces).
+        Replay it after writing new positions into sysd.pos.  Library stage timing must be
+        off while capturing."""
+        side = torch.cuda.Stream(device=self.device)
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            self.step(sysd, nl, out)       # warm: workspaces, kernel attributes, tensor maps
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.current_stream().synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            self.step(sysd, nl, out)
+        return graph
+
     def descriptors(self, sysd: DeviceSystem, nl: NeighborList, features=True):
         psi = torch.empty(sysd.n_atoms, 5, 20, dtype=torch.float32, device=self.device)
         G = torch.empty(sysd.n_atoms, 360, dtype=torch.float32, device=self.device) if features else None
