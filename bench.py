@@ -199,6 +199,16 @@ def algorithmic_work(stage, n_atoms, n_pairs, H):
         return 8.8e3 * n_atoms, "flop"
     if stage == "contract_bwd":
         return 2.8e4 * n_atoms, "flop"
+    if stage == "nl_bin":
+        # positions and species in; wrapped copies, image counts, cell ids, structure ids,
+        # the cell-ordered atom list and the sorted float4 copies out
+        return (28.0 + 48.0 + 8.0 + 44.0) * n_atoms, "byte"
+    if stage == "nl_count":
+        return (16.0 + 4.0) * n_atoms, "byte"
+    if stage == "nl_scan":
+        return 8.0 * n_atoms, "byte"
+    if stage == "nl_fill":
+        return 16.0 * n_atoms + 4.0 * n_atoms + 8.0 * n_pairs, "byte"
     if stage == "neighbors":
         # positions in, sorted copies, CSR out (col 4 B + shift 4 B per pair)
         return 24.0 * n_atoms * 3 + 8.0 * n_pairs + 4.0 * n_atoms, "byte"
@@ -209,6 +219,8 @@ def algorithmic_work(stage, n_atoms, n_pairs, H):
 
 def roofline(stages, n_atoms, n_pairs, H, precision, peaks, sustained):
     busy = {k: v for k, v in stages.items() if v[1] > 0}
+    if any(k.startswith("nl_") for k in busy):
+        busy.pop("neighbors", None)   # its sub-stages are timed on their own
     if not busy:
         return None, {}
     per = {k: v[0] / v[1] for k, v in busy.items()}
@@ -314,15 +326,33 @@ def run_gpu(args, cfg, precision, steps, warmup, world, rank, measure_e2e, clock
         raise RuntimeError(f"device status {_lib.STATUS_NAMES.get(status, status)} in the timed region")
     ms = sum(ev0[k].elapsed_time(ev1[k]) for k in range(steps))
     launches = per_step_launches * steps
-    # stage timing: the same steps launched on the stream with the library's stage events
-    _lib.gm_profile_reset()
-    _lib.gm_profile_enable(args.stage_timing)
-    for k in range(steps):
-        timed(k, False)
-    stream.synchronize()
-    _lib.gm_profile_enable(False)
-    stages, _ = _lib.gm_profile_collect()
-    ms_stream = sum(ev0[k].elapsed_time(ev1[k]) for k in range(steps))
+    # stage timing: a second pass over the same steps with the library's stage events; in
+    # graph mode a second graph is captured with the events as record nodes and read after
+    # every replay, so the stage times carry no host launch gaps
+    stages, ms_stream = {}, float("nan")
+    if args.stage_timing:
+        _lib.gm_profile_enable(True)
+        gprof = model.capture_step(sysd, nl, out) if graph is not None else None
+        _lib.gm_profile_reset()
+        for k in range(steps):
+            flush.zero_()
+            ev0[k].record(stream)
+            pos_buf.copy_(pos_dev[warmup + k])
+            if gprof is not None:
+                gprof.replay()
+            else:
+                model.step(sysd, nl, out)
+            ev1[k].record(stream)
+            if gprof is not None:          # read this replay's record nodes
+                stream.synchronize()
+                stages, _ = _lib.gm_profile_collect()
+        stream.synchronize()
+        _lib.gm_profile_enable(False)
+        if gprof is None:
+            stages, _ = _lib.gm_profile_collect()
+        _lib.gm_profile_forget_graphs()
+        del gprof
+        ms_stream = sum(ev0[k].elapsed_time(ev1[k]) for k in range(steps))
     if world > 1:
         import torch.distributed as dist
         t = torch.tensor([ms], dtype=torch.float64, device=model.device)
@@ -413,6 +443,8 @@ def run_train(args, steps, warmup):
     if model.read_status() != 0:
         raise RuntimeError("device status set in the training run")
     ms = sum(ev0[k].elapsed_time(ev1[k]) for k in range(steps))
+    if any(k.startswith("nl_") and v[1] > 0 for k, v in stages.items()):
+        stages = {k: v for k, v in stages.items() if k != "neighbors"}
     total = sum(v[0] for v in stages.values() if v[1] > 0) or 1.0
     return {"workload": "emim-train-32 (configs[3]: 32 EMIM+BF4- boxes, 7920 atoms, r_cut 5 A, MLP 2x128)",
             "precision": "fp32", "step": "neighbours + energy/forces + loss + parameter gradient",
@@ -549,8 +581,10 @@ def main():
                    "n_pairs": head["n_pairs"], "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "256 MiB buffer written between timed steps (outside the step events)",
                    "neighbour_rebuild": "every step", "launch_mode": head["launch_mode"],
-                   "stage_timing": "library stage events on a second pass of the same steps launched on the stream "
-                                   f"({head['ms_per_step_stream_with_stage_events']:.4f} ms/step)"},
+                   "stage_timing": "library stage events on a second pass of the same steps "
+                                   + ("(a second graph with event-record nodes, "
+                                      if head["launch_mode"] == "cuda-graph replay" else "(stream launches, ")
+                                   + f"{head['ms_per_step_stream_with_stage_events']:.4f} ms/step)"},
         "roofline": roof, "stage_share": share, "cpu_baseline": cpu, "e2e": head.get("e2e"),
         "gpu_launches": head["launches"], "clocks": clocks, "variants": variants,
     }

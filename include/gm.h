@@ -217,6 +217,12 @@ GM_API void gm_profile_reset(void);
 GM_API int gm_profile_n_stages(void);
 GM_API const char *gm_profile_stage_name(int stage);
 GM_API gm_status gm_profile_collect(double *stage_ms, int64_t *stage_count, int n_stages, int64_t *kernel_launches);
+/* Stages recorded while the stream is being captured into a CUDA graph become external
+ * event-record nodes of that graph.  gm_profile_collect adds their times again at every
+ * call, so call it once after each replay, with the stream synchronised.
+ * gm_profile_forget_graphs stops reading them (the events themselves stay allocated, since
+ * a graph may still record them). */
+GM_API void gm_profile_forget_graphs(void);
 
 /* Zero the device status word (cudaMemsetAsync on `stream`); call before each step. */
 GM_API gm_status gm_status_clear(int32_t *status_dev, struct CUstream_st *stream);

@@ -25,7 +25,8 @@ STATUS_NAMES = {0: "GM_OK", 1: "GM_ERR_ARG", 2: "GM_ERR_CAPACITY", 3: "GM_ERR_UN
 EXPORTS = ("gm_param_count", "gm_model_create", "gm_model_set_params", "gm_model_destroy", "gm_workspace_size",
            "gm_build_neighbors", "gm_energy_forces", "gm_param_grad", "gm_force_matching_loss", "gm_descriptors",
            "gm_status_clear", "gm_status_string", "gm_last_error", "gm_profile_enable", "gm_profile_reset",
-           "gm_profile_n_stages", "gm_profile_stage_name", "gm_profile_collect", "gm_build_neighbors_noalloc", "gm_model_set_tuning")
+           "gm_profile_n_stages", "gm_profile_stage_name", "gm_profile_collect", "gm_build_neighbors_noalloc", "gm_model_set_tuning",
+           "gm_profile_forget_graphs")
 
 
 class GmModelDesc(ctypes.Structure):
@@ -90,6 +91,7 @@ def load():
         "gm_profile_collect": (st, [_P, _P, ctypes.c_int, _P]),
         "gm_build_neighbors_noalloc": (st, [_P, ctypes.POINTER(GmSystem), ctypes.POINTER(GmNlist), _P, _P]),
         "gm_model_set_tuning": (st, [_P, ctypes.c_int32, ctypes.c_int32]),
+        "gm_profile_forget_graphs": (None, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -186,6 +188,10 @@ def gm_profile_enable(on: bool):
 
 def gm_profile_reset():
     load().gm_profile_reset()
+
+
+def gm_profile_forget_graphs():
+    load().gm_profile_forget_graphs()
 
 
 def gm_profile_collect():

@@ -45,6 +45,7 @@ struct PendingStage {
     cudaEvent_t a, b;
 };
 static std::vector<PendingStage> g_pending;
+static std::vector<PendingStage> g_graph_stages;  // event-record nodes of captured graphs
 static std::vector<cudaEvent_t> g_event_pool;
 static double g_stage_ms[N_STAGES];
 static int64_t g_stage_cnt[N_STAGES];
@@ -63,19 +64,34 @@ static cudaEvent_t pool_event() {
 
 void note_launches(int n) { g_launches += n; }
 
-StageScope::StageScope(int s, cudaStream_t stream) : stage(s), st(stream), ev0(nullptr) {
+// While a stream is being captured into a CUDA graph the events become external
+// event-record nodes: every replay records them again, and gm_profile_collect reads them
+// after each replay (the caller synchronises first).
+StageScope::StageScope(int s, cudaStream_t stream) : stage(s), st(stream), ev0(nullptr), in_graph(false) {
     if (!g_prof) return;
-    cudaEvent_t e = pool_event();
-    cudaEventRecord(e, st);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cs);
+    in_graph = cs == cudaStreamCaptureStatusActive;
+    cudaEvent_t e = nullptr;
+    if (in_graph) cudaEventCreate(&e);
+    else e = pool_event();
+    if (in_graph) cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+    else cudaEventRecord(e, st);
     ev0 = e;
 }
 
 StageScope::~StageScope() {
     if (!ev0) return;
-    cudaEvent_t e = pool_event();
-    cudaEventRecord(e, st);
+    cudaEvent_t e = nullptr;
+    if (in_graph) {
+        cudaEventCreate(&e);
+        cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+    } else {
+        e = pool_event();
+        cudaEventRecord(e, st);
+    }
     std::lock_guard<std::mutex> lk(g_prof_mu);
-    g_pending.push_back({stage, static_cast<cudaEvent_t>(ev0), e});
+    (in_graph ? g_graph_stages : g_pending).push_back({stage, static_cast<cudaEvent_t>(ev0), e});
 }
 }  // namespace gm
 
@@ -670,12 +686,18 @@ void gm_profile_reset(void) {
     g_launches = 0;
 }
 
+void gm_profile_forget_graphs(void) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_graph_stages.clear();  // the events stay alive: a graph may still record them
+}
+
 int gm_profile_n_stages(void) { return N_STAGES; }
 
 const char *gm_profile_stage_name(int s) {
     static const char *names[N_STAGES] = {"neighbors", "moments", "contract_fwd", "gemm_l1", "gemm_l2",
                                           "gemm_b1", "gemm_b0", "contract_bwd", "forces", "reduce",
-                                          "pg_pair_fwd", "pg_network", "pg_pair_bwd"};
+                                          "pg_pair_fwd", "pg_network", "pg_pair_bwd", "nl_bin", "nl_count",
+                                          "nl_scan", "nl_fill"};
     return (s >= 0 && s < N_STAGES) ? names[s] : "";
 }
 
@@ -691,6 +713,13 @@ gm_status gm_profile_collect(double *stage_ms, int64_t *stage_count, int n_stage
         g_event_pool.push_back(p.b);
     }
     g_pending.clear();
+    for (auto &p : g_graph_stages) {
+        float ms = 0.0f;
+        if (cudaEventQuery(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            g_stage_ms[p.stage] += ms;
+            g_stage_cnt[p.stage] += 1;
+        }
+    }
     for (int q = 0; q < n_stages && q < N_STAGES; ++q) {
         if (stage_ms) stage_ms[q] = g_stage_ms[q];
         if (stage_count) stage_count[q] = g_stage_cnt[q];

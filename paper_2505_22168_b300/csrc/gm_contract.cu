@@ -109,10 +109,13 @@ __device__ __forceinline__ void fwd_group(const T (&P)[NPSI], const FeatOut &gt)
                 gt.put(FAM_OFF4 + q, f4);
             }
     } else if (PART == 1) {
+        // fixed trip counts with guards: triangular bounds left the loops rolled and the
+        // moments in local memory
 #pragma unroll
         for (int s1 = 0; s1 < NR; ++s1)
 #pragma unroll
-            for (int s2 = s1; s2 < NR; ++s2) {
+            for (int s2 = 0; s2 < NR; ++s2) {
+                if (s2 < s1) continue;
                 T Nm[3][3];
 #pragma unroll
                 for (int a = 0; a < 3; ++a)
@@ -124,7 +127,8 @@ __device__ __forceinline__ void fwd_group(const T (&P)[NPSI], const FeatOut &gt)
                         Nm[a][c] = v;
                     }
 #pragma unroll
-                for (int s3 = s2; s3 < NR; ++s3) {
+                for (int s3 = 0; s3 < NR; ++s3) {
+                    if (s3 < s2) continue;
                     T f = zero<T>();
 #pragma unroll
                     for (int a = 0; a < 3; ++a)
@@ -212,13 +216,6 @@ __device__ __forceinline__ void fwd_group(const T (&P)[NPSI], const FeatOut &gt)
 }
 
 template <typename OutT>
-__device__ __forceinline__ OutT to_out(float v);
-template <>
-__device__ __forceinline__ float to_out<float>(float v) { return v; }
-template <>
-__device__ __forceinline__ __nv_bfloat16 to_out<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
-
-template <typename OutT>
 __global__ void __launch_bounds__(CT_THREADS, 1) k_contract_fwd(const float *__restrict__ psi, int N, int Mp,
                                                                 OutT *__restrict__ G, float *__restrict__ G32) {
     extern __shared__ float tile[];
@@ -238,20 +235,33 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_contract_fwd(const float *__r
     default: fwd_group<7>(P, gt); break;
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < CT_ATOMS * NFP; idx += CT_THREADS) {
-        const int r = idx / NFP, f = idx - r * NFP, m = m0 + r;
+    // 16-byte stores of 8 columns (BF16: a hi/lo row pair [hi(384) | lo(384)]) or 4 columns
+    constexpr int CW = sizeof(OutT) == 2 ? 8 : 4, NCW = NFP / CW;
+    for (int idx = threadIdx.x; idx < CT_ATOMS * NCW; idx += CT_THREADS) {
+        const int r = idx / NCW, c = idx - r * NCW, m = m0 + r;
         if (m >= Mp) continue;
-        const float v = f < NF ? tile[r * GT_STRIDE + f] : 0.0f;
-        if (sizeof(OutT) == 2) {
-            // BF16 operand as a hi/lo pair: row [hi(384) | lo(384)]
-            const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-            const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-            reinterpret_cast<__nv_bfloat16 *>(G)[(size_t)m * 2 * NFP + f] = hi;
-            reinterpret_cast<__nv_bfloat16 *>(G)[(size_t)m * 2 * NFP + NFP + f] = lo;
+        float v[CW];
+#pragma unroll
+        for (int j = 0; j < CW; ++j) v[j] = c * CW + j < NF ? tile[r * GT_STRIDE + c * CW + j] : 0.0f;
+        if constexpr (sizeof(OutT) == 2) {
+            __align__(16) __nv_bfloat16 hi[8], lo[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                hi[j] = __float2bfloat16_rn(v[j]);
+                lo[j] = __float2bfloat16_rn(v[j] - __bfloat162float(hi[j]));
+            }
+            __nv_bfloat16 *row = reinterpret_cast<__nv_bfloat16 *>(G) + (size_t)m * 2 * NFP + c * 8;
+            *reinterpret_cast<uint4 *>(row) = *reinterpret_cast<const uint4 *>(hi);
+            *reinterpret_cast<uint4 *>(row + NFP) = *reinterpret_cast<const uint4 *>(lo);
         } else {
-            G[(size_t)m * NFP + f] = to_out<OutT>(v);
+            *reinterpret_cast<float4 *>(G + (size_t)m * NFP + c * 4) = make_float4(v[0], v[1], v[2], v[3]);
         }
-        if (G32 != nullptr && f < NF && m < N) G32[(size_t)m * NF + f] = v;
+    }
+    if (G32 != nullptr) {
+        for (int idx = threadIdx.x; idx < CT_ATOMS * NF; idx += CT_THREADS) {
+            const int r = idx / NF, f = idx - r * NF, m = m0 + r;
+            if (m < N) G32[(size_t)m * NF + f] = tile[r * GT_STRIDE + f];
+        }
     }
 }
 
@@ -413,6 +423,31 @@ __device__ __forceinline__ void bwd_group(const T (&P)[NPSI], const float *gb, T
     }
 }
 
+// Stage the 360 leading columns of 32 rows of a [.][384] FP32 matrix into shared memory
+// (row stride GT_STRIDE, rows past N zero).  Every thread issues all of its 16-byte loads
+// before the first store, so the block waits for one memory latency instead of one per row.
+__device__ __forceinline__ void stage_rows(const float *__restrict__ src, int m0, int N, float *tile) {
+    constexpr int V4 = NF / 4, TOT = CT_ATOMS * V4, PER = (TOT + CT_THREADS - 1) / CT_THREADS;
+    float4 v[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int idx = threadIdx.x + u * CT_THREADS;
+        const int r = idx / V4, q = idx - r * V4;
+        v[u] = (idx < TOT && m0 + r < N) ? __ldg(reinterpret_cast<const float4 *>(src + (size_t)(m0 + r) * NFP) + q)
+                                         : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int idx = threadIdx.x + u * CT_THREADS;
+        if (idx < TOT) {
+            const int r = idx / V4, q = idx - r * V4;
+            float *d = tile + r * GT_STRIDE + 4 * q;
+            d[0] = v[u].x; d[1] = v[u].y; d[2] = v[u].z; d[3] = v[u].w;
+        }
+    }
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(CT_THREADS, 1) k_contract_bwd(const float *__restrict__ psi,
                                                                 const float *__restrict__ dG, int N,
                                                                 float *__restrict__ dpsi) {
@@ -421,11 +456,7 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_contract_bwd(const float *__r
     float *acc = sm + CT_ATOMS * GT_STRIDE;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * CT_ATOMS;
-    for (int idx = threadIdx.x; idx < CT_ATOMS * NF; idx += CT_THREADS) {
-        const int r = idx / NF, f = idx - r * NF, m = m0 + r;
-        gtile[r * GT_STRIDE + f] = m < N ? dG[(size_t)m * NFP + f] : 0.0f;
-    }
-    __syncthreads();
+    stage_rows(dG, m0, N, gtile);
     float P[NPSI], A[NPSI];
     load_psi(psi, m0 + lane, N, P);
 #pragma unroll
@@ -485,11 +516,19 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_contract_fwd_dual(const float
     default: fwd_group<7>(P, gt); break;
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < CT_ATOMS * NFP; idx += CT_THREADS) {
-        const int r = idx / NFP, f = idx - r * NFP, m = m0 + r;
+    constexpr int NC4 = NFP / 4;
+    for (int idx = threadIdx.x; idx < CT_ATOMS * NC4; idx += CT_THREADS) {
+        const int r = idx / NC4, c = idx - r * NC4, m = m0 + r;
         if (m >= Mp) continue;
-        GG[(size_t)m * NFP + f] = f < NF ? tv[r * GT_STRIDE + f] : 0.0f;
-        GG[(size_t)(Mp + m) * NFP + f] = f < NF ? td[r * GT_STRIDE + f] : 0.0f;
+        float v[4], d[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const bool in = c * 4 + j < NF;
+            v[j] = in ? tv[r * GT_STRIDE + c * 4 + j] : 0.0f;
+            d[j] = in ? td[r * GT_STRIDE + c * 4 + j] : 0.0f;
+        }
+        *reinterpret_cast<float4 *>(GG + (size_t)m * NFP + c * 4) = make_float4(v[0], v[1], v[2], v[3]);
+        *reinterpret_cast<float4 *>(GG + (size_t)(Mp + m) * NFP + c * 4) = make_float4(d[0], d[1], d[2], d[3]);
     }
 }
 
@@ -509,12 +548,8 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_contract_bwd_dual(const float
     float *acc2 = acc1 + CT_ATOMS * AC_STRIDE;         // psidb
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * CT_ATOMS;
-    for (int idx = threadIdx.x; idx < CT_ATOMS * NF; idx += CT_THREADS) {
-        const int r = idx / NF, f = idx - r * NF, m = m0 + r;
-        gtile[r * GT_STRIDE + f] = m < N ? Gbs[(size_t)m * NFP + f] : 0.0f;
-        gdtile[r * GT_STRIDE + f] = m < N ? Gbs[(size_t)(Mp + m) * NFP + f] : 0.0f;
-    }
-    __syncthreads();
+    stage_rows(Gbs, m0, N, gtile);
+    stage_rows(Gbs + (size_t)Mp * NFP, m0, N, gdtile);
     float *arow1 = acc1 + lane * AC_STRIDE, *arow2 = acc2 + lane * AC_STRIDE;
     {   // J^T Gb
         float P[NPSI], A[NPSI];

@@ -42,13 +42,15 @@ struct NlStruct {
 // ---- tracing (gm_api.cu): kernel-launch counter and stage timing
 enum Stage {
     ST_NEIGHBORS = 0, ST_MOMENTS, ST_CONTRACT_FWD, ST_GEMM_L1, ST_GEMM_L2, ST_GEMM_B1, ST_GEMM_B0,
-    ST_CONTRACT_BWD, ST_FORCES, ST_REDUCE, ST_PG_PAIR_FWD, ST_PG_NETWORK, ST_PG_PAIR_BWD, N_STAGES
+    ST_CONTRACT_BWD, ST_FORCES, ST_REDUCE, ST_PG_PAIR_FWD, ST_PG_NETWORK, ST_PG_PAIR_BWD, ST_NL_BIN, ST_NL_COUNT,
+    ST_NL_SCAN, ST_NL_FILL, N_STAGES
 };
 void note_launches(int n);
 struct StageScope {
     int stage;
     cudaStream_t st;
     void *ev0;
+    bool in_graph;
     StageScope(int s, cudaStream_t stream);
     ~StageScope();
 };

@@ -18,6 +18,8 @@
 //   search   one warp per atom: count pass -> scan -> row_ptr -> fill pass (same order)
 #include <math.h>
 
+#include <optional>
+
 #include "gm_internal.h"
 
 namespace gm {
@@ -373,6 +375,8 @@ gm_status nl_build(const gm_system &sys, double r_cut, int n_species, gm_nlist &
     NlWs w = carve_nl(c, B, N);
     if (!c.ok) return GM_ERR_WORKSPACE;
     const int ncmax = N + B;
+    std::optional<StageScope> scope;  // sub-stage events (profiling only)
+    scope.emplace(ST_NL_BIN, st);
     if (cudaMemsetAsync(w.ccount, 0, sizeof(int32_t) * ncmax, st) != cudaSuccess) return GM_ERR_CUDA;
     if (cudaMemsetAsync(w.cfill, 0, sizeof(int32_t) * ncmax, st) != cudaSuccess) return GM_ERR_CUDA;
     k_nl_setup<<<1, 1024, 0, st>>>(B, sys.atom_ptr, sys.cell, sys.pbc, r_cut, w.S, status);
@@ -390,6 +394,8 @@ gm_status nl_build(const gm_system &sys, double r_cut, int n_species, gm_nlist &
         const long long warps_cells = (long long)ncmax * 32, warps_atoms = (long long)N * G;
         k_nl_sortcells<<<(int)((warps_cells + tb - 1) / tb), tb, 0, st>>>(ncmax, w.cstart, w.unsorted, w.xw, w.xs);
         const float rc2f = (float)(r_cut * r_cut);
+        scope.reset();
+        scope.emplace(ST_NL_COUNT, st);
         if (G == 8)
             k_nl_search<false, 8><<<(int)((warps_atoms + tb - 1) / tb), tb, 0, st>>>(
                 N, w.S, w.sid, w.cellid, w.cstart, w.xs, w.xw, w.mimg, r_cut, rc2f, w.counts, nullptr, 0, nullptr,
@@ -398,8 +404,12 @@ gm_status nl_build(const gm_system &sys, double r_cut, int n_species, gm_nlist &
             k_nl_search<false, 32><<<(int)((warps_atoms + tb - 1) / tb), tb, 0, st>>>(
                 N, w.S, w.sid, w.cellid, w.cstart, w.xs, w.xw, w.mimg, r_cut, rc2f, w.counts, nullptr, 0, nullptr,
                 nullptr, status);
+        scope.reset();
+        scope.emplace(ST_NL_SCAN, st);
         exclusive_scan(w.counts, nl.row_ptr, N, w.scan_tmp, st);
         k_nl_total<<<1, 1, 0, st>>>(nl.row_ptr + N, nl.capacity, nl.n_pairs, status);
+        scope.reset();
+        scope.emplace(ST_NL_FILL, st);
         if (G == 8)
             k_nl_search<true, 8><<<(int)((warps_atoms + tb - 1) / tb), tb, 0, st>>>(
                 N, w.S, w.sid, w.cellid, w.cstart, w.xs, w.xw, w.mimg, r_cut, rc2f, nullptr, nl.row_ptr, nl.capacity,

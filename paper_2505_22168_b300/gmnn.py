@@ -202,8 +202,9 @@ class GMNN:
 
     def capture_step(self, sysd: DeviceSystem, nl: NeighborList, out):
         """CUDA graph of step() for fixed buffers (sysd.pos, nl, out, the workspaces).
-        Replay it after writing new positions into sysd.pos.  Library stage timing must be
-        off while capturing."""
+        Replay it after writing new positions into sysd.pos.  With library stage timing on
+        while capturing, the stage events become record nodes of the graph: read them with
+        gm_profile_collect after each replay."""
         side = torch.cuda.Stream(device=self.device)
         side.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(side):
