@@ -209,6 +209,10 @@ def algorithmic_work(stage, n_atoms, n_pairs, H):
         return 8.0 * n_atoms, "byte"
     if stage == "nl_fill":
         return 16.0 * n_atoms + 4.0 * n_atoms + 8.0 * n_pairs, "byte"
+    if stage == "nl_coop":
+        # the whole cooperative build: positions and species in, binned copies, counts and
+        # the CSR list out (col 4 B + shift 4 B per pair)
+        return (28.0 + 48.0 + 8.0 + 44.0 + 20.0 + 8.0 + 20.0) * n_atoms + 8.0 * n_pairs, "byte"
     if stage == "neighbors":
         # positions in, sorted copies, CSR out (col 4 B + shift 4 B per pair)
         return 24.0 * n_atoms * 3 + 8.0 * n_pairs + 4.0 * n_atoms, "byte"

@@ -110,7 +110,10 @@ typedef struct {
     int64_t *n_pairs;   /* device scalar: number of pairs found (also set on overflow) */
 } gm_nlist;
 
-/* Workspace kinds for gm_workspace_size. */
+/* Workspace kinds for gm_workspace_size.  For GM_OP_NEIGHBORS the size includes a search
+ * slab of about 1.5 x capacity / n_atoms entries per atom, which lets the build test every
+ * candidate pair once; gm_build_neighbors also accepts a workspace without room for the slab
+ * (then it tests the candidates twice: count, then fill). */
 enum { GM_OP_NEIGHBORS = 0, GM_OP_ENERGY_FORCES = 1, GM_OP_PARAM_GRAD = 2 };
 
 /* Number of FP32 parameters.  Flat layout of theta, in this order:
@@ -129,15 +132,28 @@ GM_API gm_status gm_model_set_params(gm_model *m, const float *theta_dev, struct
 
 GM_API void gm_model_destroy(gm_model *m);
 
-/* Tuning knobs of a model (they change speed, not results beyond rounding):
+/* Tuning knobs of a model (they change speed, not results beyond rounding; the neighbour
+ * knobs change nothing in the list):
  *   GM_TUNE_PAIR_TPA    lanes per atom in the pair kernels: 0 = by system size, or 1, 2, 4, 8, 16, 32
  *   GM_TUNE_SPLIT_MASK  mixed path: network GEMMs that run with hi/lo split-BF16 operands
  *                       (three tensor-core passes) -- bit 1 first layer, 2 second layer,
  *                       4 and 8 the two backward GEMMs; default 12 (backward GEMMs), which
  *                       keeps forces within 2e-3 of the FP64 result
  *   GM_TUNE_GEMM_BN     mixed path: tensor-core tile width 64, 128 or 256 (0 = by size)
+ *   GM_TUNE_NL_MODE     neighbour build as one cooperative launch (GM_NL_MODE_AUTO, the
+ *                       default when the device supports it) or one launch per phase
+ *                       (GM_NL_MODE_PHASES)
+ *   GM_TUNE_NL_SPLIT    work items sharing one home cell in the neighbour search: 0 = by size, 1..16
+ *   GM_TUNE_NL_BLOCKS   blocks of the cooperative neighbour launch: 0 = by size, else 1..4096
+ *                       (capped at what the device keeps resident)
+ *   GM_TUNE_NL_TWO_PASS 1: count-then-fill neighbour search even when the workspace holds the
+ *                       search slab (0, the default: one search pass and a compaction)
+ *   GM_TUNE_NL_ITEMS    neighbour search work items: 0 = by size, 1 = one home cell (part) per
+ *                       block with shared staging, 2 = one per warp
  * Errors: GM_ERR_ARG for an unknown key or value. */
-enum { GM_TUNE_PAIR_TPA = 0, GM_TUNE_SPLIT_MASK = 1, GM_TUNE_GEMM_BN = 2 };
+enum { GM_TUNE_PAIR_TPA = 0, GM_TUNE_SPLIT_MASK = 1, GM_TUNE_GEMM_BN = 2, GM_TUNE_NL_MODE = 3, GM_TUNE_NL_SPLIT = 4,
+       GM_TUNE_NL_BLOCKS = 5, GM_TUNE_NL_TWO_PASS = 6, GM_TUNE_NL_ITEMS = 7 };
+enum { GM_NL_MODE_AUTO = 0, GM_NL_MODE_PHASES = 1 };
 GM_API gm_status gm_model_set_tuning(gm_model *m, int32_t key, int32_t value);
 
 /* Bytes of workspace an operation needs (op = GM_OP_*).  nl_capacity is the neighbour

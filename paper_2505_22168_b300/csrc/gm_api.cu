@@ -111,6 +111,7 @@ struct gm_model {
     __nv_bfloat16 *W1t_h, *W1p_h, *W2t_h, *W2_h;   // BF16 hi/lo pairs, rows [hi(K) | lo(K)]
     int split_mask;        // GEMMs run with three hi/lo passes: 1 L1, 2 L2, 4 B1, 8 B0
     int gemm_bn;           // tensor-core tile width (0 = by size)
+    NlTuning nl;           // neighbour build launch shape
     float *b1, *b2, *w3, *b3, *sigma, *mu;
 };
 
@@ -338,6 +339,7 @@ gm_status launch_status() {
 
 namespace gm {
 const gm_model_desc *model_desc(const gm_model *m) { return &m->d; }
+const NlTuning &nl_tuning(const gm_model *m) { return m->nl; }
 gm_status set_last_error(gm_status s, const char *msg) { return fail(s, msg); }
 }  // namespace gm
 
@@ -370,6 +372,7 @@ gm_status gm_model_create(const gm_model_desc *d, gm_model **out) {
     m->pair_tpa = 0;
     m->split_mask = 12;
     m->gemm_bn = 0;
+    m->nl = NlTuning();
     Layout L = model_layout(m->S, m->H);
     m->buf_bytes = L.total;
     if (cudaMalloc(&m->buf, L.total) != cudaSuccess) {
@@ -422,6 +425,26 @@ gm_status gm_model_set_tuning(gm_model *m, int32_t key, int32_t value) {
         if (value != 0 && value != 64 && value != 128 && value != 256) return fail(GM_ERR_ARG, "bad GEMM tile width");
         m->gemm_bn = value;
         return GM_OK;
+    case GM_TUNE_NL_MODE:
+        if (value != GM_NL_MODE_AUTO && value != GM_NL_MODE_PHASES) return fail(GM_ERR_ARG, "bad neighbour mode");
+        m->nl.mode = value;
+        return GM_OK;
+    case GM_TUNE_NL_SPLIT:
+        if (value < 0 || value > 16) return fail(GM_ERR_ARG, "neighbour split must be in 0..16");
+        m->nl.split = value;
+        return GM_OK;
+    case GM_TUNE_NL_BLOCKS:
+        if (value < 0 || value > 4096) return fail(GM_ERR_ARG, "neighbour blocks must be in 0..4096");
+        m->nl.blocks = value;
+        return GM_OK;
+    case GM_TUNE_NL_ITEMS:
+        if (value < 0 || value > 2) return fail(GM_ERR_ARG, "neighbour item mode must be 0, 1 or 2");
+        m->nl.items = value;
+        return GM_OK;
+    case GM_TUNE_NL_TWO_PASS:
+        if (value != 0 && value != 1) return fail(GM_ERR_ARG, "neighbour two-pass flag must be 0 or 1");
+        m->nl.two_pass = value;
+        return GM_OK;
     }
     return fail(GM_ERR_ARG, "unknown tuning key");
 }
@@ -436,7 +459,7 @@ gm_status gm_workspace_size(const gm_model *m, int32_t n_structures, int32_t n_a
                             int32_t op, size_t *bytes) {
     if (!m || !bytes || n_structures < 1 || n_atoms < 0 || nl_capacity < 0) return fail(GM_ERR_ARG, "bad argument");
     switch (op) {
-    case GM_OP_NEIGHBORS: *bytes = nl_workspace_bytes(n_structures, n_atoms); return GM_OK;
+    case GM_OP_NEIGHBORS: *bytes = nl_workspace_bytes(n_structures, n_atoms, nl_capacity); return GM_OK;
     case GM_OP_ENERGY_FORCES: *bytes = ef_workspace_bytes(n_structures, n_atoms, m->H); return GM_OK;
     case GM_OP_PARAM_GRAD: *bytes = pg_workspace_bytes(n_atoms, m->H, m->S); return GM_OK;
     default: return fail(GM_ERR_ARG, "unknown op");
@@ -449,10 +472,11 @@ gm_status gm_build_neighbors(const gm_model *m, const gm_system *sys, gm_nlist *
     if (s != GM_OK) return s;
     if ((s = check_nlist(sys, nl, false)) != GM_OK) return s;
     if (!status) return fail(GM_ERR_ARG, "null status");
-    if (ws_bytes < nl_workspace_bytes(sys->n_structures, sys->n_atoms)) return fail(GM_ERR_WORKSPACE, "workspace too small");
+    if (ws_bytes < nl_workspace_min_bytes(sys->n_structures, sys->n_atoms))
+        return fail(GM_ERR_WORKSPACE, "workspace too small");
     {
         StageScope sc(ST_NEIGHBORS, stream);
-        s = nl_build(*sys, m->d.r_cut, m->S, *nl, ws, ws_bytes, status, stream);
+        s = nl_build(*sys, m->d.r_cut, m->S, *nl, ws, ws_bytes, status, stream, m->nl);
     }
     if (s != GM_OK) return fail(s, "neighbour build launch failed");
     return launch_status();
@@ -697,7 +721,7 @@ const char *gm_profile_stage_name(int s) {
     static const char *names[N_STAGES] = {"neighbors", "moments", "contract_fwd", "gemm_l1", "gemm_l2",
                                           "gemm_b1", "gemm_b0", "contract_bwd", "forces", "reduce",
                                           "pg_pair_fwd", "pg_network", "pg_pair_bwd", "nl_bin", "nl_count",
-                                          "nl_scan", "nl_fill"};
+                                          "nl_scan", "nl_fill", "nl_coop"};
     return (s >= 0 && s < N_STAGES) ? names[s] : "";
 }
 

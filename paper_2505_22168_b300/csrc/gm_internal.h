@@ -27,23 +27,12 @@ struct Carve {
     }
 };
 
-// Per-structure cell-list geometry (device, in the neighbour workspace).
-struct NlStruct {
-    double L[3];     // orthorhombic box edges
-    double cs[3];    // cell edge per axis (>= r_cut unless the box is smaller)
-    int nc[3];       // cells per axis
-    int K[3];        // stencil half-width per axis (cells)
-    int cell0;       // first global cell index of this structure
-    int a0, n;       // atoms
-    float Lf[3];     // edges in FP32 (distance filter)
-    float eps2;      // half-width of the FP32 band around r_cut^2 decided in FP64
-};
 
 // ---- tracing (gm_api.cu): kernel-launch counter and stage timing
 enum Stage {
     ST_NEIGHBORS = 0, ST_MOMENTS, ST_CONTRACT_FWD, ST_GEMM_L1, ST_GEMM_L2, ST_GEMM_B1, ST_GEMM_B0,
     ST_CONTRACT_BWD, ST_FORCES, ST_REDUCE, ST_PG_PAIR_FWD, ST_PG_NETWORK, ST_PG_PAIR_BWD, ST_NL_BIN, ST_NL_COUNT,
-    ST_NL_SCAN, ST_NL_FILL, N_STAGES
+    ST_NL_SCAN, ST_NL_FILL, ST_NL_COOP, N_STAGES
 };
 void note_launches(int n);
 struct StageScope {
@@ -60,12 +49,17 @@ const gm_model_desc *model_desc(const gm_model *m);
 gm_status set_last_error(gm_status s, const char *msg);
 
 // ---- neighbour search (gm_nlist.cu)
-size_t nl_workspace_bytes(int n_struct, int n_atoms);
+struct NlTuning {
+    int mode = GM_NL_MODE_AUTO;   // GM_NL_MODE_* of gm.h
+    int split = 0;                // blocks per home cell in the search passes (0 = by size)
+    int blocks = 0;               // blocks of the cooperative launch (0 = by size)
+    int two_pass = 0;             // 1: count and fill passes even when the workspace holds the slab
+    int items = 0;                // search work items: 0 = by size, 1 = per block, 2 = per warp
+};
+const NlTuning &nl_tuning(const gm_model *m);
+size_t nl_workspace_bytes(int n_struct, int n_atoms, int64_t capacity);   // with the search slab
+size_t nl_workspace_min_bytes(int n_struct, int n_atoms);                  // two-pass search
 gm_status nl_build(const gm_system &sys, double r_cut, int n_species, gm_nlist &nl, void *ws, size_t ws_bytes,
-                   int32_t *status, cudaStream_t st);
-
-// ---- device-wide exclusive scan (gm_nlist.cu): out[0..n] with out[n] = total
-size_t scan_tmp_ints(int n);
-void exclusive_scan(const int32_t *in, int32_t *out, int n, int32_t *tmp, cudaStream_t st);
+                   int32_t *status, cudaStream_t st, const NlTuning &tune);
 
 }  // namespace gm

@@ -9,13 +9,27 @@
 // or outside a band around r_cut^2 whose half-width bounds the FP32 rounding error, so
 // FP64 arithmetic (slow on B300) runs only for the rare candidates inside the band.
 //
-// Pipeline (all on one stream, no host synchronisation):
-//   setup    per-structure cell grid (cells >= r_cut, at most max(1, n_atoms) cells)
+// Phases (one stream, no host synchronisation):
+//   setup    per-structure cell grid (cells >= r_cut, at most max(1, n_atoms) cells) and
+//            the global cell numbering; zero the cell histograms
 //   bin      wrap positions, cell index, atomic histogram
-//   scan     cell offsets
-//   scatter  atoms into cells (atomic slots); sortcells (one warp per cell) packs each
-//            cell's FP32 wrapped positions in ascending atom index (float4, index in w)
-//   search   one warp per atom: count pass -> scan -> row_ptr -> fill pass (same order)
+//   scan     cell offsets (block chunks, then the carry of the earlier chunks)
+//   scatter  atoms into cells (atomic slots)
+//   sort     one warp per cell packs the cell's FP32 wrapped positions in ascending atom
+//            index (float4, index in w)
+//   count    one warp per work item (a home cell, or one of `split` interleaved parts of its
+//            atoms): the lanes take 32 candidates of the 27 stencil cells (each with its
+//            periodic image) at a time and test them against every home atom of the item
+//   scan     row offsets; n_pairs and the capacity check
+//   fill     the count pass again, writing col and shift through a ballot prefix
+// The row order is stencil cell (dz, dy, dx ascending) then ascending neighbour index, the
+// same in both passes.  Structures whose box is shorter than r_cut along some axis (several
+// images of a cell per stencil direction) take a per-atom loop over the stencil instead.
+// Scans of up to NL_SCAN_ONE_BLOCK entries run in one block.
+//
+// All phases run in ONE cooperative launch with grid-wide barriers between them (each a
+// bounded wait: after about one second it records GM_ERR_TIMEOUT and the kernel returns),
+// or, selected by a tuning knob, as one launch per phase.
 #include <math.h>
 
 #include <optional>
@@ -24,156 +38,252 @@
 
 namespace gm {
 
-// ------------------------------------------------------------------ scan
-constexpr int SCAN_THREADS = 256;
-constexpr int SCAN_BLOCK = SCAN_THREADS * 4;
+constexpr int NL_THREADS = 256;
+constexpr int NL_WARPS = NL_THREADS / 32;
+constexpr int NL_SCAN_SUB = NL_THREADS * 4;
+constexpr int NL_SCAN_ONE_BLOCK = 4096;
+constexpr int NL_HOME_STENCIL = 13;     // (0, 0, 0) in the 27-cell stencil
+constexpr int NL_MAX_BLOCKS = 4096;
 
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_local(const int32_t *__restrict__ in, int32_t *out, int n,
-                                                             int32_t *block_sums) {
-    __shared__ int32_t s[SCAN_THREADS];
-    const int t = threadIdx.x;
-    const int base = blockIdx.x * SCAN_BLOCK + t * 4;
-    int v[4], sum = 0;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        v[q] = (base + q < n) ? in[base + q] : 0;
-        sum += v[q];
-    }
-    s[t] = sum;
-    __syncthreads();
-    for (int off = 1; off < SCAN_THREADS; off <<= 1) {
-        int x = t >= off ? s[t - off] : 0;
-        __syncthreads();
-        s[t] += x;
-        __syncthreads();
-    }
-    int excl = s[t] - sum;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        if (base + q < n) out[base + q] = excl;
-        excl += v[q];
-    }
-    if (t == SCAN_THREADS - 1) block_sums[blockIdx.x] = s[t];
+// Per-structure cell-list geometry (device, in the neighbour workspace).
+struct NlStruct {
+    double L[3];      // orthorhombic box edges
+    double invL[3];   // 1 / L (rounded): wrap fast path
+    double inv_cs[3]; // cells per unit length (cell edge >= r_cut unless the box is smaller)
+    int nc[3];        // cells per axis
+    int K[3];         // stencil half-width per axis (cells)
+    int cell0;        // first global cell index of this structure
+    int a0, n;        // atoms
+    float Lf[3];      // edges in FP32 (distance filter)
+    float eps2;       // half-width of the FP32 band around r_cut^2 decided in FP64
+};
+
+// Per-axis integers as three signed bytes (x | y << 8 | z << 16); bit 31 marks a value
+// outside -127..127 (the consumer then works with the full integers).
+constexpr unsigned NL_FAR = 0x80000000u;
+__device__ __forceinline__ unsigned bytes3(int x, int y, int z) {
+    const bool ok = x >= -127 && x <= 127 && y >= -127 && y <= 127 && z >= -127 && z <= 127;
+    return ok ? ((unsigned)(x & 255) | ((unsigned)(y & 255) << 8) | ((unsigned)(z & 255) << 16)) : NL_FAR;
+}
+__device__ __forceinline__ int byte_at(unsigned p, int axis) { return (int)(signed char)((p >> (8 * axis)) & 255u); }
+
+// Slab entries hold the shift as a code 0..26 of (s0, s1, s2) in {-1, 0, 1}^3; NL_NOCODE
+// for any other shift (its row is searched again during the compaction).
+constexpr unsigned NL_NOCODE = 31u;
+__device__ __forceinline__ unsigned shift_code(unsigned sb) {
+    if (sb & NL_FAR) return NL_NOCODE;
+    const int s0 = byte_at(sb, 0), s1 = byte_at(sb, 1), s2 = byte_at(sb, 2);
+    const bool ok = s0 >= -1 && s0 <= 1 && s1 >= -1 && s1 <= 1 && s2 >= -1 && s2 <= 1;
+    return ok ? (unsigned)((s0 + 1) + 3 * (s1 + 1) + 9 * (s2 + 1)) : NL_NOCODE;
 }
 
-__global__ void __launch_bounds__(1024) k_scan_sums(int32_t *block_sums, int nb, int32_t *total_out) {
-    __shared__ int32_t s[1024];
-    __shared__ int32_t carry;
-    const int t = threadIdx.x;
-    if (t == 0) carry = 0;
+// a + b per byte for two bytes3 values; NL_FAR if either is far or a sum leaves -127..127
+__device__ __forceinline__ unsigned bytes3_add(unsigned a, unsigned b) {
+    if ((a | b) & NL_FAR) return NL_FAR;
+    const unsigned s = __vadd4(a, b);
+    const bool wrapped = __vaddss4(a, b) != s;
+    const bool minus128 = __vcmpeq4(s | 0xFF000000u, 0x80808080u) != 0u;
+    return (wrapped || minus128) ? NL_FAR : s;
+}
+
+struct NlArgs {
+    int N, B, n_species, ncmax, split;
+    const int32_t *atom_ptr;
+    const double *pos;
+    const int32_t *species;
+    const double *cell;
+    const uint8_t *pbc;
+    double rc;
+    float rc2f;
+    NlStruct *S;
+    int32_t *ncells;        // device scalar: cells of all structures
+    int32_t *cellid, *ccount, *cstart, *cfill, *unsorted, *counts, *bsum, *mimg;
+    uint32_t *xsm;          // image counts of the sorted atoms (bytes3 of mimg)
+    uint32_t *mpk;          // image counts by atom index (bytes3 of mimg)
+    uint32_t *slab;         // single-pass search: row i at i * maxn, entries j | shift code << 27
+    int maxn;               // slab row length (0: two-pass search, no slab)
+    int block_items;        // 1: block-level search items, 0: warp-level
+    uint8_t *redo;          // 1: row searched again during the compaction
+    int32_t *redo_list, *n_redo;
+    double *xw;
+    float4 *xs;
+    int32_t *row_ptr, *col;
+    char4 *shift;
+    int64_t cap;
+    int64_t *n_pairs;
+    unsigned *bar;          // grid barrier: [0] arrivals, [1] generation
+    int32_t *status;
+};
+
+__device__ __forceinline__ unsigned long long nl_clock_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier of a cooperative launch (all blocks co-resident).  Thread 0 of each block
+// reads the generation, arrives with a release-acquire increment (the block's writes were
+// ordered before it by the block barrier), and waits with acquire loads until the last
+// arrival resets the count and advances the generation.  The wait is bounded: on expiry the
+// status word gets GM_ERR_TIMEOUT and false is returned (the caller returns, so every block
+// leaves within one more bounded wait).
+__device__ bool nl_grid_sync(unsigned *bar, int32_t *status) {
+    __shared__ int expired;
     __syncthreads();
-    for (int chunk = 0; chunk < nb; chunk += 1024) {
-        const int idx = chunk + t;
-        const int v = idx < nb ? block_sums[idx] : 0;
-        s[t] = v;
-        __syncthreads();
-        for (int off = 1; off < 1024; off <<= 1) {
-            int x = t >= off ? s[t - off] : 0;
-            __syncthreads();
-            s[t] += x;
-            __syncthreads();
+    if (threadIdx.x == 0) {
+        expired = 0;
+        unsigned g, arrived;
+        asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(bar + 1) : "memory");
+        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(arrived) : "l"(bar) : "memory");
+        if (arrived == gridDim.x - 1) {
+            asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(bar) : "memory");
+            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar + 1) : "memory");
+        } else {
+            const unsigned long long t0 = nl_clock_ns();
+            unsigned now;
+            for (;;) {
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(now) : "l"(bar + 1) : "memory");
+                if (now != g) break;
+                if (nl_clock_ns() - t0 > 1000000000ull) {
+                    set_status(status, GM_ERR_TIMEOUT);
+                    expired = 1;
+                    break;
+                }
+                __nanosleep(32);
+            }
         }
-        if (idx < nb) block_sums[idx] = carry + s[t] - v;
-        __syncthreads();
-        if (t == 1023) carry += s[1023];
-        __syncthreads();
     }
-    if (t == 0) *total_out = carry;
+    __syncthreads();
+    return expired == 0;
 }
 
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_add(int32_t *out, int n, const int32_t *__restrict__ block_sums) {
-    const int add = block_sums[blockIdx.x];
-    const int base = blockIdx.x * SCAN_BLOCK + threadIdx.x * 4;
+__device__ __forceinline__ int floordiv(int v, int n) { return v >= 0 ? v / n : -((-v + n - 1) / n); }
+
+// ------------------------------------------------------------------ block scan helpers
+// Exclusive scan of v over the block; *total gets the block sum.
+__device__ __forceinline__ int block_exclusive_scan(int v, int *total) {
+    __shared__ int warp_sums[NL_WARPS];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = v;
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-        if (base + q < n) out[base + q] += add;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    int wpre = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < NL_WARPS; ++w) {
+        const int s = warp_sums[w];
+        wpre += w < warp ? s : 0;
+        tot += s;
+    }
+    __syncthreads();
+    *total = tot;
+    return wpre + x - v;
 }
 
-size_t scan_tmp_ints(int n) { return (size_t)((n + SCAN_BLOCK - 1) / SCAN_BLOCK) + 1; }
-
-void exclusive_scan(const int32_t *in, int32_t *out, int n, int32_t *tmp, cudaStream_t st) {
-    const int nb = (n + SCAN_BLOCK - 1) / SCAN_BLOCK;
-    if (nb > 0) k_scan_local<<<nb, SCAN_THREADS, 0, st>>>(in, out, n, tmp);
-    k_scan_sums<<<1, 1024, 0, st>>>(tmp, nb, out + n);
-    if (nb > 0) k_scan_add<<<nb, SCAN_THREADS, 0, st>>>(out, n, tmp);
-    note_launches(nb > 0 ? 3 : 1);
+__device__ __forceinline__ int block_sum(int v) {
+    __shared__ int warp_sums[NL_WARPS];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) warp_sums[warp] = v;
+    __syncthreads();
+    int tot = 0;
+#pragma unroll
+    for (int w = 0; w < NL_WARPS; ++w) tot += warp_sums[w];
+    __syncthreads();
+    return tot;
 }
 
 // ------------------------------------------------------------------ setup
-__global__ void __launch_bounds__(1024) k_nl_setup(int B, const int32_t *__restrict__ atom_ptr,
-                                                   const double *__restrict__ cell, const uint8_t *__restrict__ pbc,
-                                                   double rc, NlStruct *S, int32_t *status) {
-    __shared__ int32_t s[1024];
-    __shared__ int32_t carry;
-    const int t = threadIdx.x;
-    if (t == 0) carry = 0;
-    __syncthreads();
-    for (int chunk = 0; chunk < B; chunk += 1024) {
-        const int b = chunk + t;
-        NlStruct q;
-        int ncell = 0;
-        if (b < B) {
-            const double *C = cell + 9 * b;
-            const bool ortho = C[1] == 0.0 && C[2] == 0.0 && C[3] == 0.0 && C[5] == 0.0 && C[6] == 0.0 && C[7] == 0.0;
-            const bool periodic = pbc[3 * b] && pbc[3 * b + 1] && pbc[3 * b + 2];
-            const bool positive = C[0] > 0.0 && C[4] > 0.0 && C[8] > 0.0;
-            q.a0 = atom_ptr[b];
-            q.n = atom_ptr[b + 1] - q.a0;
-            bool ok = ortho && periodic && positive;
-            long long nc[3];
-            for (int a = 0; a < 3; ++a) {
-                q.L[a] = ok ? C[4 * a] : 1.0;
-                double f = floor(q.L[a] / (rc * (1.0 + 1e-5)));
-                nc[a] = f < 1.0 ? 1 : (f > 1024.0 ? 1024 : (long long)f);
+// Cell grid of structure b (FP64, fixed operation order).  Returns its number of cells.
+__device__ int nl_struct_setup(const NlArgs &a, int b, NlStruct &q) {
+    const double *C = a.cell + 9 * b;
+    const bool ortho = C[1] == 0.0 && C[2] == 0.0 && C[3] == 0.0 && C[5] == 0.0 && C[6] == 0.0 && C[7] == 0.0;
+    const bool periodic = a.pbc[3 * b] && a.pbc[3 * b + 1] && a.pbc[3 * b + 2];
+    const bool positive = C[0] > 0.0 && C[4] > 0.0 && C[8] > 0.0;
+    q.a0 = a.atom_ptr[b];
+    q.n = a.atom_ptr[b + 1] - q.a0;
+    bool ok = ortho && periodic && positive;
+    long long nc[3];
+    const double cells_per_len = 1.0 / (a.rc * (1.0 + 1e-5));   // cell edge >= r_cut (1 + 1e-5)
+    for (int d = 0; d < 3; ++d) {
+        q.L[d] = ok ? C[4 * d] : 1.0;
+        q.invL[d] = 1.0 / q.L[d];
+        const double f = floor(q.L[d] * cells_per_len);
+        nc[d] = f < 1.0 ? 1 : (f > 1024.0 ? 1024 : (long long)f);
+    }
+    const long long limit = q.n > 1 ? q.n : 1;
+    while (nc[0] * nc[1] * nc[2] > limit) {
+        int am = 0;
+        if (nc[1] > nc[am]) am = 1;
+        if (nc[2] > nc[am]) am = 2;
+        nc[am] -= 1;
+    }
+    int Kmax = 0;
+    double Lmax = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        q.nc[d] = (int)nc[d];
+        q.inv_cs[d] = (double)nc[d] * q.invL[d];
+        int K = (int)ceil(a.rc * q.inv_cs[d] + 1e-6);
+        if (K > 100) { ok = false; K = 0; }
+        q.K[d] = ok ? K : 0;
+        q.Lf[d] = (float)q.L[d];
+        Kmax = K > Kmax ? K : Kmax;
+        Lmax = q.L[d] > Lmax ? q.L[d] : Lmax;
+    }
+    if (!ok) set_status(a.status, GM_ERR_UNSUPPORTED);
+    // FP32 filter error per axis: the roundings of the two wrapped coordinates and of the
+    // image offset (each <= 2^-24 L), of the shifted coordinate (<= 2^-24 2L) and of the
+    // difference (<= 2^-24 r_cut near the cutoff) stay below 2^-24 L (8 + 4K); the band
+    // bounds the resulting r^2 error near r_cut
+    const double u = 5.9604644775390625e-8;  // 2^-24
+    const double e = u * Lmax * (8.0 + 4.0 * Kmax);
+    q.eps2 = (float)(4.0 * (2.0 * 1.7320508075688772 * e * a.rc + 3.0 * e * e + 4.0 * u * a.rc * a.rc) + 1e-30);
+    return q.nc[0] * q.nc[1] * q.nc[2];
+}
+
+// Block 0 builds the per-structure grids and the global cell numbering; every block
+// zeroes its share of the cell histograms.
+__device__ void ph_setup(const NlArgs &a, int bid, int nb) {
+    if (bid == 0) {
+        int carry = 0;
+        for (int chunk = 0; chunk < a.B; chunk += NL_THREADS) {
+            const int b = chunk + threadIdx.x;
+            NlStruct q;
+            const int ncell = b < a.B ? nl_struct_setup(a, b, q) : 0;
+            int tot;
+            const int pre = block_exclusive_scan(ncell, &tot);
+            if (b < a.B) {
+                q.cell0 = carry + pre;
+                a.S[b] = q;
             }
-            const long long limit = q.n > 1 ? q.n : 1;
-            while (nc[0] * nc[1] * nc[2] > limit) {
-                int am = 0;
-                if (nc[1] > nc[am]) am = 1;
-                if (nc[2] > nc[am]) am = 2;
-                nc[am] -= 1;
-            }
-            int Kmax = 0;
-            double Lmax = 0.0;
-            for (int a = 0; a < 3; ++a) {
-                q.nc[a] = (int)nc[a];
-                q.cs[a] = q.L[a] / (double)nc[a];
-                int K = (int)ceil(rc / q.cs[a] + 1e-6);
-                if (K > 100) { ok = false; K = 0; }
-                q.K[a] = ok ? K : 0;
-                q.Lf[a] = (float)q.L[a];
-                Kmax = K > Kmax ? K : Kmax;
-                Lmax = q.L[a] > Lmax ? q.L[a] : Lmax;
-            }
-            if (!ok) set_status(status, GM_ERR_UNSUPPORTED);
-            // |FP32 displacement error| per axis <= 2^-24 L (6 + 2K); bound r^2 error near r_cut
-            const double u = 5.9604644775390625e-8;  // 2^-24
-            const double e = u * Lmax * (8.0 + 4.0 * Kmax);
-            q.eps2 = (float)(4.0 * (2.0 * 1.7320508075688772 * e * rc + 3.0 * e * e + 4.0 * u * rc * rc) + 1e-30);
-            ncell = q.nc[0] * q.nc[1] * q.nc[2];
+            carry += tot;
         }
-        s[t] = ncell;
-        __syncthreads();
-        for (int off = 1; off < 1024; off <<= 1) {
-            int x = t >= off ? s[t - off] : 0;
-            __syncthreads();
-            s[t] += x;
-            __syncthreads();
+        if (threadIdx.x == 0) {
+            *a.ncells = carry;
+            *a.n_redo = 0;
         }
-        if (b < B) {
-            q.cell0 = carry + s[t] - ncell;
-            S[b] = q;
-        }
-        __syncthreads();
-        if (t == 1023) carry += s[1023];
-        __syncthreads();
+    }
+    for (int c = bid * NL_THREADS + threadIdx.x; c < a.ncmax; c += nb * NL_THREADS) {
+        a.ccount[c] = 0;
+        a.cfill[c] = 0;
     }
 }
 
 // ------------------------------------------------------------------ bin
-// Wrap of one coordinate; the same correctly rounded sequence as the oracle.
-__device__ __forceinline__ double wrap_axis(double x, double L, int &m_out) {
-    double m = floor(__ddiv_rn(x, L));
+// Wrap of one coordinate; the same correctly rounded sequence as the oracle.  The image
+// count m = floor(x / L) needs the floor of the correctly rounded quotient; the product with
+// the rounded reciprocal is within a few ulps of it, so its floor is that floor whenever the
+// product is more than 1e-9 from an integer (|quotient| < 1e6); otherwise the division decides.
+__device__ __forceinline__ double wrap_axis(double x, double L, double invL, int &m_out) {
+    const double qa = __dmul_rn(x, invL);
+    double m = floor(qa);
+    const double fr = qa - m;
+    if (!(fr > 1e-9 && fr < 1.0 - 1e-9 && fabs(qa) < 1e6)) m = floor(__ddiv_rn(x, L));
     double xw = __dsub_rn(x, __dmul_rn(m, L));
     if (xw < 0.0) { m -= 1.0; xw = __dsub_rn(x, __dmul_rn(m, L)); }
     if (xw >= L) { m += 1.0; xw = __dsub_rn(x, __dmul_rn(m, L)); }
@@ -182,98 +292,181 @@ __device__ __forceinline__ double wrap_axis(double x, double L, int &m_out) {
     return xw;
 }
 
-__global__ void __launch_bounds__(256) k_nl_bin(int N, int B, const int32_t *__restrict__ atom_ptr,
-                                                const double *__restrict__ pos, const int32_t *__restrict__ species,
-                                                int n_species, const NlStruct *__restrict__ S, int32_t *sid, double *xw,
-                                                int32_t *mimg, int32_t *cellid, int32_t *ccount, int32_t *status) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const int b = structure_of(atom_ptr, B, i);
-    sid[i] = b;
-    const int z = species[i];
-    if (z < 0 || z >= n_species) set_status(status, GM_ERR_SPECIES);
-    const NlStruct &q = S[b];
-    int ic[3];
-    for (int a = 0; a < 3; ++a) {
-        const double x = pos[3 * i + a];
-        int m;
-        const double w = wrap_axis(x, q.L[a], m);
-        if (!(fabs(x) < 1.0e6 * q.L[a])) set_status(status, GM_ERR_UNSUPPORTED);
-        xw[3 * i + a] = w;
-        mimg[3 * i + a] = m;
-        int c = (int)floor(__ddiv_rn(w, q.cs[a]));
-        c = c < 0 ? 0 : (c >= q.nc[a] ? q.nc[a] - 1 : c);
-        ic[a] = c;
+// Work spread over blocks first: warp w of block bid takes the 32-atom chunks
+// bid + nb (w + 8 k), so a small system occupies many SMs.
+__device__ void ph_bin(const NlArgs &a, int bid, int nb) {
+    const int lane = threadIdx.x & 31;
+    for (int ch = bid + nb * (threadIdx.x >> 5); ch * 32 < a.N; ch += nb * NL_WARPS) {
+        const int i = ch * 32 + lane;
+        if (i >= a.N) continue;
+        const int b = structure_of(a.atom_ptr, a.B, i);
+        const int z = a.species[i];
+        if (z < 0 || z >= a.n_species) set_status(a.status, GM_ERR_SPECIES);
+        const NlStruct &q = a.S[b];
+        int ic[3];
+        for (int d = 0; d < 3; ++d) {
+            const double x = a.pos[3 * i + d];
+            int m;
+            const double w = wrap_axis(x, q.L[d], q.invL[d], m);
+            if (!(fabs(x) < 1.0e6 * q.L[d])) set_status(a.status, GM_ERR_UNSUPPORTED);
+            a.xw[3 * i + d] = w;
+            a.mimg[3 * i + d] = m;
+            int c = (int)floor(w * q.inv_cs[d]);
+            c = c < 0 ? 0 : (c >= q.nc[d] ? q.nc[d] - 1 : c);
+            ic[d] = c;
+        }
+        const int cid = q.cell0 + (ic[2] * q.nc[1] + ic[1]) * q.nc[0] + ic[0];
+        a.cellid[i] = cid;
+        a.mpk[i] = bytes3(a.mimg[3 * i], a.mimg[3 * i + 1], a.mimg[3 * i + 2]);
+        atomicAdd(a.ccount + cid, 1);
     }
-    const int cid = q.cell0 + (ic[2] * q.nc[1] + ic[1]) * q.nc[0] + ic[0];
-    cellid[i] = cid;
-    atomicAdd(ccount + cid, 1);
 }
 
-__global__ void __launch_bounds__(256) k_nl_scatter(int N, const int32_t *__restrict__ cellid,
-                                                    const int32_t *__restrict__ cstart, int32_t *cfill, int32_t *sorted) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const int c = cellid[i];
-    const int slot = atomicAdd(cfill + c, 1);
-    sorted[cstart[c] + slot] = i;
+// ------------------------------------------------------------------ scan
+// Exclusive scan of src[0..n) into dst[0..n] (dst[n] = total) by nb blocks: phase 1 scans
+// the blocks' chunks and records their sums, phase 2 adds the sums of the earlier chunks.
+__device__ void ph_scan1(const int32_t *src, int32_t *dst, int n, int32_t *bsum, int bid, int nb) {
+    const int chunk = (n + nb - 1) / nb;
+    const int c0 = min(n, bid * chunk), c1 = min(n, c0 + chunk);
+    int carry = 0;
+    for (int s = c0; s < c1; s += NL_SCAN_SUB) {
+        const int base = s + threadIdx.x * 4;
+        int v[4], sum = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[k] = base + k < c1 ? src[base + k] : 0;
+            sum += v[k];
+        }
+        int tot;
+        int pre = carry + block_exclusive_scan(sum, &tot);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (base + k < c1) dst[base + k] = pre;
+            pre += v[k];
+        }
+        carry += tot;
+    }
+    if (threadIdx.x == 0) bsum[bid] = carry;
+}
+
+__device__ void ph_scan2(int32_t *dst, int n, const int32_t *bsum, int bid, int nb, int64_t cap, int64_t *n_pairs,
+                         int32_t *status) {
+    int part = 0;
+    for (int k = threadIdx.x; k < bid; k += NL_THREADS) part += bsum[k];
+    const int off = block_sum(part);
+    const int chunk = (n + nb - 1) / nb;
+    const int c0 = min(n, bid * chunk), c1 = min(n, c0 + chunk);
+    if (off != 0)
+        for (int k = c0 + threadIdx.x; k < c1; k += NL_THREADS) dst[k] += off;
+    if (bid == nb - 1 && threadIdx.x == 0) {
+        const int total = off + bsum[bid];
+        dst[n] = total;
+        if (n_pairs) {
+            *n_pairs = total;
+            if ((int64_t)total > cap) set_status(status, GM_ERR_CAPACITY);
+        }
+    }
+}
+
+// Exclusive scan of src[0..n) into dst[0..n] by block 0 alone (n small).
+__device__ void ph_scan_one(const int32_t *src, int32_t *dst, int n, int bid, int64_t cap, int64_t *n_pairs,
+                            int32_t *status) {
+    if (bid != 0) return;
+    int carry = 0;
+    for (int s = 0; s < n; s += NL_SCAN_SUB) {
+        const int base = s + threadIdx.x * 4;
+        int v[4], sum = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[k] = base + k < n ? src[base + k] : 0;
+            sum += v[k];
+        }
+        int tot;
+        int pre = carry + block_exclusive_scan(sum, &tot);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (base + k < n) dst[base + k] = pre;
+            pre += v[k];
+        }
+        carry += tot;
+    }
+    if (threadIdx.x == 0) {
+        dst[n] = carry;
+        if (n_pairs) {
+            *n_pairs = carry;
+            if ((int64_t)carry > cap) set_status(status, GM_ERR_CAPACITY);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ scatter and sort
+__device__ void ph_scatter(const NlArgs &a, int bid, int nb) {
+    const int lane = threadIdx.x & 31;
+    for (int ch = bid + nb * (threadIdx.x >> 5); ch * 32 < a.N; ch += nb * NL_WARPS) {
+        const int i = ch * 32 + lane;
+        if (i >= a.N) continue;
+        const int c = a.cellid[i];
+        const int slot = atomicAdd(a.cfill + c, 1);
+        a.unsorted[a.cstart[c] + slot] = i;
+    }
 }
 
 // One warp per cell: each atom's position in the cell is its rank among the cell's atom
 // indices (all distinct), so the packed order is ascending atom index (deterministic).
-__global__ void __launch_bounds__(256) k_nl_sortcells(int ncells, const int32_t *__restrict__ cstart,
-                                                      const int32_t *__restrict__ unsorted,
-                                                      const double *__restrict__ xw, float4 *xs) {
-    const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+__device__ void ph_sort(const NlArgs &a, int bid, int nb) {
     const int lane = threadIdx.x & 31;
-    if (c >= ncells) return;
-    const int s0 = cstart[c], n = cstart[c + 1] - s0;
-    for (int e = lane; e < n; e += 32) {
-        const int v = unsorted[s0 + e];
-        int r = 0;
-        for (int q = 0; q < n; ++q) r += unsorted[s0 + q] < v;
-        xs[s0 + r] = make_float4((float)xw[3 * v], (float)xw[3 * v + 1], (float)xw[3 * v + 2], __int_as_float(v));
+    const int ncells = *a.ncells;
+    for (int c = bid + nb * (threadIdx.x >> 5); c < ncells; c += nb * NL_WARPS) {
+        const int s0 = a.cstart[c], n = a.cstart[c + 1] - s0;
+        for (int e = lane; e < n; e += 32) {
+            const int v = a.unsorted[s0 + e];
+            int r = 0;
+            for (int k = 0; k < n; ++k) r += a.unsorted[s0 + k] < v;
+            a.xs[s0 + r] = make_float4((float)a.xw[3 * v], (float)a.xw[3 * v + 1], (float)a.xw[3 * v + 2],
+                                       __int_as_float(v));
+            a.xsm[s0 + r] = a.mpk[v];
+        }
     }
 }
 
-__device__ __forceinline__ int floordiv(int v, int n) { return v >= 0 ? v / n : -((-v + n - 1) / n); }
-
 // ------------------------------------------------------------------ search
-// G lanes per centre atom (atoms taken in cell order for locality; G = 32 for small
-// systems, 8 for large ones, whose cells hold about 20 candidates); lanes test G
-// candidates of a cell at a time.  The fill pass places accepted pairs with a ballot over
-// the group, so the row order is the candidate order (stencil cell, then ascending
-// neighbour index) in both passes.
-template <bool FILL, int G>
-__global__ void __launch_bounds__(256) k_nl_search(int N, const NlStruct *__restrict__ S, const int32_t *__restrict__ sid,
-                                                   const int32_t *__restrict__ cellid, const int32_t *__restrict__ cstart,
-                                                   const float4 *__restrict__ xs, const double *__restrict__ xw,
-                                                   const int32_t *__restrict__ mimg, double rc, float rc2f,
-                                                   int32_t *counts, const int32_t *__restrict__ row_ptr, int64_t cap,
-                                                   int32_t *col, char4 *shift, int32_t *status) {
-    // G lanes per centre atom (G = 8 or 32); the ballots below involve only the group
-    const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / G;
-    const int lane = threadIdx.x % G;
-    constexpr unsigned low_mask = (G == 32) ? 0xffffffffu : ((1u << (G % 32)) - 1u);
-    const int group_shift = (threadIdx.x & 31) & ~(G - 1);
-    const unsigned group_mask = low_mask << group_shift;
-    const int t = gid;
-    if (t >= N) return;
-    if (FILL) {
-        if ((int64_t)row_ptr[N] > cap) return;
-        if (status_bad(status)) return;
+__device__ __forceinline__ int structure_of_cell(const NlStruct *S, int B, int c) {
+    int lo = 0, hi = B - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (S[mid].cell0 <= c) lo = mid; else hi = mid - 1;
     }
-    const float4 me = xs[t];
+    return lo;
+}
+
+// Exact FP64 membership test of candidate j of centre i under the image (nx, ny, nz).
+__device__ __forceinline__ bool exact_inside(const double *__restrict__ xw, int j, double xi0, double xi1, double xi2,
+                                             int nx, int ny, int nz, const NlStruct &q, double rc2) {
+    const double d0 = __dadd_rn(__dsub_rn(xw[3 * j], xi0), __dmul_rn((double)nx, q.L[0]));
+    const double d1 = __dadd_rn(__dsub_rn(xw[3 * j + 1], xi1), __dmul_rn((double)ny, q.L[1]));
+    const double d2 = __dadd_rn(__dsub_rn(xw[3 * j + 2], xi2), __dmul_rn((double)nz, q.L[2]));
+    return __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2)) < rc2;
+}
+
+// Store pair (i, j) with its lattice shift relative to the caller's (unwrapped) positions:
+// image n of the wrapped positions minus the image counts of j, plus those of i.
+__device__ __forceinline__ void store_pair(const NlArgs &a, int pos, int j, int s0, int s1, int s2) {
+    if (s0 < -127 || s0 > 127 || s1 < -127 || s1 > 127 || s2 < -127 || s2 > 127) set_status(a.status, GM_ERR_UNSUPPORTED);
+    a.col[pos] = j;
+    a.shift[pos] = make_char4((signed char)s0, (signed char)s1, (signed char)s2, 0);
+}
+
+// Per-atom search over the full stencil (any K): one warp, 32 candidates of a cell per step.
+template <bool FILL>
+__device__ void search_atom_generic(const NlArgs &a, const NlStruct &q, int c_local, float4 me, int lane) {
     const int i = __float_as_int(me.w);
-    const NlStruct &q = S[sid[i]];
-    const int cid = cellid[i] - q.cell0;
-    const int ix = cid % q.nc[0], iy = (cid / q.nc[0]) % q.nc[1], iz = cid / (q.nc[0] * q.nc[1]);
-    const double rc2 = __dmul_rn(rc, rc);
-    const float lo = rc2f - q.eps2, hi = rc2f + q.eps2;
-    const int mi0 = mimg[3 * i], mi1 = mimg[3 * i + 1], mi2 = mimg[3 * i + 2];
-    const double xi0 = xw[3 * i], xi1 = xw[3 * i + 1], xi2 = xw[3 * i + 2];
+    const int ix = c_local % q.nc[0], iy = (c_local / q.nc[0]) % q.nc[1], iz = c_local / (q.nc[0] * q.nc[1]);
+    const double rc2 = __dmul_rn(a.rc, a.rc);
+    const float lo = a.rc2f - q.eps2, hi = a.rc2f + q.eps2;
+    const int mi0 = a.mimg[3 * i], mi1 = a.mimg[3 * i + 1], mi2 = a.mimg[3 * i + 2];
+    const double xi0 = a.xw[3 * i], xi1 = a.xw[3 * i + 1], xi2 = a.xw[3 * i + 2];
     const unsigned below = (1u << lane) - 1u;
-    int out = FILL ? row_ptr[i] : 0;
+    int out = FILL ? a.row_ptr[i] : 0;
     int cnt = 0;
     for (int dz = -q.K[2]; dz <= q.K[2]; ++dz) {
         const int vz = iz + dz, nz = floordiv(vz, q.nc[2]), cz = vz - nz * q.nc[2];
@@ -284,40 +477,29 @@ __global__ void __launch_bounds__(256) k_nl_search(int N, const NlStruct *__rest
                 const int c = q.cell0 + (cz * q.nc[1] + cy) * q.nc[0] + cx;
                 const float sx = (float)nx * q.Lf[0], sy = (float)ny * q.Lf[1], sz = (float)nz * q.Lf[2];
                 const bool zero_shift = (nx | ny | nz) == 0;
-                const int k0 = cstart[c], k1 = cstart[c + 1];
-                for (int base = k0; base < k1; base += G) {
+                const int k0 = a.cstart[c], k1 = a.cstart[c + 1];
+                for (int base = k0; base < k1; base += 32) {
                     const int k = base + lane;
-                    bool in = false;
+                    bool in = false, band = false;
                     int j = 0;
                     if (k < k1) {
-                        const float4 o = xs[k];
+                        const float4 o = a.xs[k];
                         j = __float_as_int(o.w);
                         if (!(zero_shift && j == i)) {
-                            const float fx = (o.x - me.x) + sx, fy = (o.y - me.y) + sy, fz = (o.z - me.z) + sz;
+                            const float fx = (o.x + sx) - me.x, fy = (o.y + sy) - me.y, fz = (o.z + sz) - me.z;
                             const float r2 = fx * fx + fy * fy + fz * fz;
-                            if (r2 < lo) in = true;
-                            else if (r2 <= hi) {
-                                const double d0 = __dadd_rn(__dsub_rn(xw[3 * j], xi0), __dmul_rn((double)nx, q.L[0]));
-                                const double d1 = __dadd_rn(__dsub_rn(xw[3 * j + 1], xi1), __dmul_rn((double)ny, q.L[1]));
-                                const double d2 = __dadd_rn(__dsub_rn(xw[3 * j + 2], xi2), __dmul_rn((double)nz, q.L[2]));
-                                const double r2d =
-                                    __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2));
-                                in = r2d < rc2;
-                            }
+                            in = r2 < lo;
+                            band = !in && r2 <= hi;
                         }
                     }
-                    const unsigned ball = (__ballot_sync(group_mask, in) >> group_shift) & low_mask;
+                    if (__any_sync(0xffffffffu, band)) {
+                        if (band) in = exact_inside(a.xw, j, xi0, xi1, xi2, nx, ny, nz, q, rc2);
+                    }
+                    const unsigned ball = __ballot_sync(0xffffffffu, in);
                     if (FILL) {
-                        if (in) {
-                            const int pos = out + __popc(ball & below);
-                            const int s0 = nx - mimg[3 * j] + mi0;
-                            const int s1 = ny - mimg[3 * j + 1] + mi1;
-                            const int s2 = nz - mimg[3 * j + 2] + mi2;
-                            if (s0 < -127 || s0 > 127 || s1 < -127 || s1 > 127 || s2 < -127 || s2 > 127)
-                                set_status(status, GM_ERR_UNSUPPORTED);
-                            col[pos] = j;
-                            shift[pos] = make_char4((signed char)s0, (signed char)s1, (signed char)s2, 0);
-                        }
+                        if (in)
+                            store_pair(a, out + __popc(ball & below), j, nx - a.mimg[3 * j] + mi0,
+                                       ny - a.mimg[3 * j + 1] + mi1, nz - a.mimg[3 * j + 2] + mi2);
                         out += __popc(ball);
                     } else {
                         cnt += __popc(ball);
@@ -326,19 +508,596 @@ __global__ void __launch_bounds__(256) k_nl_search(int N, const NlStruct *__rest
             }
         }
     }
-    if (!FILL && lane == 0) counts[i] = cnt;
+    if (!FILL && lane == 0) a.counts[i] = cnt;
 }
 
-__global__ void k_nl_total(const int32_t *__restrict__ rowN, int64_t cap, int64_t *n_pairs, int32_t *status) {
-    const int64_t P = *rowN;
-    *n_pairs = P;
-    if (P > cap) set_status(status, GM_ERR_CAPACITY);
+// Search passes.  SM_SLAB (the default) tests every candidate once and appends the accepted
+// ones, with their lattice shifts, to the home atom's slab row (up to maxn; the count is exact
+// either way); the compaction then copies the rows into the CSR list.  SM_COUNT and SM_FILL
+// are the two-pass alternative for a workspace without the slab (count, then write the CSR
+// rows directly once the offsets are known).
+//
+// One warp per work item = (cell, part): part p of `split` takes the home atoms p, p + split,
+// ... of the cell, up to 32 at a time (FP32 positions and indices in shared memory, broadcast
+// to the lanes).  Lane t < 27 holds stencil cell t (first sorted index, count, image).  The
+// warp stages up to NL_WIN candidates at a time in its own slice of shared memory -- every
+// lane issues its loads before storing, each candidate finding its stencil cell by a binary
+// search over the lanes' offsets -- and tests 32 staged candidates at a time against every
+// home atom.  Only chunks that hold candidates of the home cell itself check for the (i, i,
+// n = 0) self pair.  A candidate's info word holds its stencil cell (bits 0..4) and, for the
+// writing passes, its image minus its own image counts as bytes3 (bits 8..31, NL_FAR-style
+// flag in bit 5); the pair's shift adds the home atom's image counts.
+enum SearchMode { SM_COUNT, SM_FILL, SM_SLAB };
+constexpr int NL_WIN = 512;
+constexpr int NL_STAGE_UNROLL = 8;
+// dynamic shared memory of the search passes: staged candidates, their info words, and
+// each warp's home atoms
+constexpr size_t NL_SMEM = (size_t)NL_WARPS * NL_WIN * (sizeof(float4) + sizeof(unsigned)) + NL_WARPS * 32 * sizeof(float4);
+__device__ __forceinline__ float4 *nl_home_smem(float4 *smem) {
+    return reinterpret_cast<float4 *>(reinterpret_cast<unsigned *>(smem + NL_WARPS * NL_WIN) + NL_WARPS * NL_WIN);
+}
+
+// lattice shift of pair (i, j) with image (n0, n1, n2), from the full image counts
+__device__ __forceinline__ unsigned shift_slow(const NlArgs &a, int i, int j, int n0, int n1, int n2) {
+    const int s0 = n0 - a.mimg[3 * j] + a.mimg[3 * i];
+    const int s1 = n1 - a.mimg[3 * j + 1] + a.mimg[3 * i + 1];
+    const int s2 = n2 - a.mimg[3 * j + 2] + a.mimg[3 * i + 2];
+    return bytes3(s0, s1, s2);
+}
+
+// The tests of one chunk (32 staged candidates, one per lane) against the ng home atoms.
+// UNI: all home atoms of the group have the same image counts, so the staged info word
+// already holds the pair's complete shift.
+template <int MODE, bool SELF, bool UNI>
+__device__ __forceinline__ void test_chunk(const NlArgs &a, const float4 *home, int ng, float4 cv, bool valid, int j,
+                                           unsigned info, int n0, int n1, int n2, float lo2, float hi2,
+                                           const NlStruct &q, double rc2, int lane, int &hacc, unsigned hmb,
+                                           bool &hredo) {
+    const unsigned full = 0xffffffffu, below = (1u << lane) - 1u;
+    const int st = (int)(info & 31u);
+    const int selfj = (SELF && valid && st == NL_HOME_STENCIL) ? j : -1;
+    const unsigned vb = (info & 32u) ? NL_FAR : (info >> 8);
+    // slab entry of a uniform group (shift complete at staging)
+    const unsigned ucode = (MODE == SM_SLAB && UNI) ? shift_code(vb) : 0u;
+    const bool maybe_nocode = MODE == SM_SLAB && (!UNI || __any_sync(full, valid && ucode == NL_NOCODE));
+#pragma unroll 4
+    for (int h = 0; h < ng; ++h) {
+        const float4 hv = home[h];
+        const int hi = __float_as_int(hv.w);
+        const float fx = cv.x - hv.x, fy = cv.y - hv.y, fz = cv.z - hv.z;
+        const float r2 = fx * fx + fy * fy + fz * fz;
+        const bool other = SELF ? (valid && selfj != hi) : valid;
+        bool in = other && r2 < lo2;
+        if (other && !in && r2 <= hi2)                                   // inside the band: exact FP64 test
+            in = exact_inside(a.xw, j, a.xw[3 * hi], a.xw[3 * hi + 1], a.xw[3 * hi + 2], n0, n1, n2, q, rc2);
+        const unsigned ball = __ballot_sync(full, in);
+        if (MODE == SM_COUNT) {
+            if (lane == h) hacc += __popc(ball);
+        } else {
+            const int ob = __shfl_sync(full, hacc, h);
+            const unsigned mb = UNI ? 0u : __shfl_sync(full, hmb, h);
+            bool nocode = false;
+            if (in) {
+                const int pos = ob + __popc(ball & below);
+                if (MODE == SM_SLAB) {
+                    const unsigned code = UNI ? ucode : shift_code(bytes3_add(vb, mb));
+                    nocode = code == NL_NOCODE;
+                    if (pos < a.maxn) a.slab[(size_t)hi * a.maxn + pos] = (unsigned)j | (code << 27);
+                } else {
+                    unsigned sh = UNI ? vb : bytes3_add(vb, mb);
+                    if (sh & NL_FAR) sh = shift_slow(a, hi, j, n0, n1, n2);
+                    if (sh & NL_FAR) {
+                        set_status(a.status, GM_ERR_UNSUPPORTED);
+                        sh = 0;
+                    }
+                    a.col[pos] = j;
+                    reinterpret_cast<unsigned *>(a.shift)[pos] = sh;
+                }
+            }
+            if (maybe_nocode && __any_sync(full, nocode) && lane == h) hredo = true;
+            if (lane == h) hacc += __popc(ball);
+        }
+    }
+}
+
+// Mark row i for the per-atom search during the compaction.
+__device__ __forceinline__ void nl_redo(const NlArgs &a, int i) {
+    a.redo[i] = 1;
+    a.redo_list[atomicAdd(a.n_redo, 1)] = i;
+}
+
+template <int MODE>
+__device__ void ph_search(const NlArgs &a, int bid, int nb, float4 *smem) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float4 *s_home = nl_home_smem(smem) + 32 * warp;
+    float4 *wc = smem + warp * NL_WIN;
+    unsigned *wi = reinterpret_cast<unsigned *>(smem + NL_WARPS * NL_WIN) + warp * NL_WIN;
+    const unsigned full = 0xffffffffu;
+    if (MODE == SM_FILL && __shfl_sync(full, lane == 0 ? (int)status_bad(a.status) : 0, 0)) return;
+    const int items = *a.ncells * a.split;
+    const double rc2 = __dmul_rn(a.rc, a.rc);
+    for (int it = bid + nb * warp; it < items; it += nb * NL_WARPS) {
+        const int c = it / a.split, part = it - c * a.split;
+        const int h0 = a.cstart[c], nh = a.cstart[c + 1] - h0;
+        if (part >= nh) continue;                                  // uniform over the warp
+        const NlStruct &q = a.S[structure_of_cell(a.S, a.B, c)];
+        const int cl = c - q.cell0;
+        if (!(q.K[0] == 1 && q.K[1] == 1 && q.K[2] == 1)) {
+            // several images per stencil direction: per-atom search (with a slab, the
+            // compaction writes these rows with the same routine)
+            for (int h = part; h < nh; h += a.split) {
+                const float4 me = a.xs[h0 + h];
+                if (MODE == SM_FILL) {
+                    search_atom_generic<true>(a, q, cl, me, lane);
+                } else {
+                    search_atom_generic<false>(a, q, cl, me, lane);
+                    if (MODE == SM_SLAB && lane == 0) nl_redo(a, __float_as_int(me.w));
+                }
+            }
+            continue;
+        }
+        int k0 = 0, cnt = 0;
+        unsigned npk = 0;
+        float shx = 0.0f, shy = 0.0f, shz = 0.0f;
+        if (lane < 27) {
+            const int dz = lane / 9 - 1, dy = (lane / 3) % 3 - 1, dx = lane % 3 - 1;
+            const int ix = cl % q.nc[0], iy = (cl / q.nc[0]) % q.nc[1], iz = cl / (q.nc[0] * q.nc[1]);
+            const int vz = iz + dz, nz = floordiv(vz, q.nc[2]), cz = vz - nz * q.nc[2];
+            const int vy = iy + dy, ny = floordiv(vy, q.nc[1]), cy = vy - ny * q.nc[1];
+            const int vx = ix + dx, nx = floordiv(vx, q.nc[0]), cx = vx - nx * q.nc[0];
+            const int cc = q.cell0 + (cz * q.nc[1] + cy) * q.nc[0] + cx;
+            k0 = a.cstart[cc];
+            cnt = a.cstart[cc + 1] - k0;
+            npk = bytes3(nx, ny, nz);
+            shx = (float)nx * q.Lf[0];
+            shy = (float)ny * q.Lf[1];
+            shz = (float)nz * q.Lf[2];
+        }
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(full, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int off = incl - cnt;                                // first candidate of stencil cell `lane`
+        const int T = __shfl_sync(full, incl, 26);
+        const int home_lo = __shfl_sync(full, off, NL_HOME_STENCIL);
+        const int home_hi = home_lo + __shfl_sync(full, cnt, NL_HOME_STENCIL);
+        const float lo2 = a.rc2f - q.eps2, hi2 = a.rc2f + q.eps2;
+        const int nhp = (nh - part + a.split - 1) / a.split;       // home atoms of the item
+        for (int g0 = 0; g0 < nhp; g0 += 32) {
+            const int ng = min(32, nhp - g0);
+            int hidx = 0, hacc = 0;
+            unsigned hmb = 0;
+            bool hredo = false;
+            if (lane < ng) {
+                const int hk = h0 + part + a.split * (g0 + lane);
+                const float4 hv = a.xs[hk];
+                hidx = __float_as_int(hv.w);
+                s_home[lane] = hv;
+                if (MODE != SM_COUNT) hmb = a.xsm[hk];
+                if (MODE == SM_FILL) hacc = a.row_ptr[hidx];
+            }
+            // one image count for the whole group (the usual case): shifts complete at staging
+            const unsigned m_first = __shfl_sync(full, hmb, 0);
+            const bool uni = MODE == SM_COUNT ||
+                             (__all_sync(full, lane >= ng || hmb == m_first) && !(m_first & NL_FAR));
+            for (int w0 = 0; w0 < T; w0 += NL_WIN) {
+                const int wn = min(NL_WIN, T - w0);
+                __syncwarp();
+                // stage candidates w0 .. w0 + wn: loads first, then the stores
+                for (int u0 = 0; u0 < wn; u0 += 32 * NL_STAGE_UNROLL) {
+                    float4 o[NL_STAGE_UNROLL];
+                    unsigned pm[NL_STAGE_UNROLL];
+                    int sts[NL_STAGE_UNROLL];
+#pragma unroll
+                    for (int u = 0; u < NL_STAGE_UNROLL; ++u) {
+                        const int e = w0 + u0 + 32 * u + lane;
+                        int st = 0;
+#pragma unroll
+                        for (int step = 16; step > 0; step >>= 1) {
+                            const int t = st + step;
+                            const int ot = __shfl_sync(full, off, t & 31);
+                            if (t <= 26 && ot <= e) st = t;
+                        }
+                        const int kc = __shfl_sync(full, k0, st) + (e - __shfl_sync(full, off, st));
+                        sts[u] = st;
+                        o[u] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                        pm[u] = 0;
+                        if (e < w0 + wn) {
+                            o[u] = a.xs[kc];
+                            if (MODE != SM_COUNT) pm[u] = a.xsm[kc];
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < NL_STAGE_UNROLL; ++u) {
+                        const int el = u0 + 32 * u + lane;
+                        const int st = sts[u];
+                        const float sx = __shfl_sync(full, shx, st), sy = __shfl_sync(full, shy, st),
+                                    sz = __shfl_sync(full, shz, st);
+                        unsigned info = (unsigned)st;
+                        if (MODE != SM_COUNT) {
+                            // image minus the neighbour's image counts (plus the group's own, if uniform)
+                            const unsigned n = __shfl_sync(full, npk, st);
+                            const unsigned mh = uni ? m_first : 0u;
+                            const unsigned v = (pm[u] & NL_FAR)
+                                                   ? NL_FAR
+                                                   : bytes3(byte_at(n, 0) - byte_at(pm[u], 0) + byte_at(mh, 0),
+                                                            byte_at(n, 1) - byte_at(pm[u], 1) + byte_at(mh, 1),
+                                                            byte_at(n, 2) - byte_at(pm[u], 2) + byte_at(mh, 2));
+                            info |= (v & NL_FAR) ? 32u : (v << 8);
+                        }
+                        if (el < wn) {
+                            wc[el] = make_float4(o[u].x + sx, o[u].y + sy, o[u].z + sz, o[u].w);
+                            wi[el] = info;
+                        }
+                    }
+                }
+                __syncwarp();
+                for (int base = 0; base < wn; base += 32) {
+                    const int el = base + lane;
+                    const bool valid = el < wn;
+                    float4 cv = make_float4(3.0e30f, 3.0e30f, 3.0e30f, 0.0f);
+                    unsigned info = 0;
+                    if (valid) {
+                        cv = wc[el];
+                        info = wi[el];
+                    }
+                    const int j = __float_as_int(cv.w);
+                    const unsigned n = __shfl_sync(full, npk, (int)(info & 31u));
+                    const int n0 = byte_at(n, 0), n1 = byte_at(n, 1), n2 = byte_at(n, 2);
+                    // does the chunk overlap the home cell's candidates?
+                    const int e0 = w0 + base;
+                    const bool self = e0 < home_hi && e0 + 32 > home_lo;
+                    if (uni) {
+                        if (self)
+                            test_chunk<MODE, true, true>(a, s_home, ng, cv, valid, j, info, n0, n1, n2, lo2, hi2,
+                                                         q, rc2, lane, hacc, hmb, hredo);
+                        else
+                            test_chunk<MODE, false, true>(a, s_home, ng, cv, valid, j, info, n0, n1, n2, lo2, hi2,
+                                                          q, rc2, lane, hacc, hmb, hredo);
+                    } else if (MODE != SM_COUNT) {
+                        test_chunk<MODE, true, false>(a, s_home, ng, cv, valid, j, info, n0, n1, n2, lo2, hi2, q,
+                                                      rc2, lane, hacc, hmb, hredo);
+                    }
+                }
+            }
+            if (MODE != SM_FILL && lane < ng) {
+                a.counts[hidx] = hacc;
+                if (MODE == SM_SLAB) {
+                    const bool over = hacc > a.maxn || hredo;
+                    a.redo[hidx] = over ? 1 : 0;
+                    if (over) a.redo_list[atomicAdd(a.n_redo, 1)] = hidx;
+                }
+            }
+            __syncwarp();                                              // s_home is rewritten next
+        }
+    }
+}
+
+// Block-level variant of the search passes (small systems, where the warp-level one leaves
+// most of the GPU idle and restages the same candidates for every part of a cell): a work
+// item = (cell, part) per block; warp 0 builds the stencil, all 256 threads stage the item's
+// candidates (up to NL_BCAND) once, and warp w takes the home atoms part + split (w + 8 r).
+// The image counts are folded into the staged shifts when they agree over the item's home
+// atoms.  Items with more candidates than fit take the per-atom search.
+constexpr int NL_BCAND = NL_WARPS * NL_WIN;
+
+template <int MODE>
+__device__ void ph_search_block(const NlArgs &a, int bid, int nb, float4 *smem) {
+    __shared__ int s_k0[27], s_off[28];
+    __shared__ unsigned s_n[27];
+    __shared__ float s_sh[27][3];
+    __shared__ int s_skip;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float4 *s_home = nl_home_smem(smem) + 32 * warp;
+    float4 *cand = smem;
+    unsigned *cinfo = reinterpret_cast<unsigned *>(smem + NL_BCAND);
+    const unsigned full = 0xffffffffu;
+    if (threadIdx.x == 0) s_skip = MODE == SM_FILL && status_bad(a.status);
+    __syncthreads();
+    if (s_skip) return;                                            // uniform over the block
+    const int items = *a.ncells * a.split;
+    const double rc2 = __dmul_rn(a.rc, a.rc);
+    for (int it = bid; it < items; it += nb) {
+        const int c = it / a.split, part = it - c * a.split;
+        const int h0 = a.cstart[c], nh = a.cstart[c + 1] - h0;
+        if (part >= nh) continue;                                  // uniform over the block
+        const NlStruct &q = a.S[structure_of_cell(a.S, a.B, c)];
+        const int cl = c - q.cell0;
+        const bool tiled = q.K[0] == 1 && q.K[1] == 1 && q.K[2] == 1;
+        int T = 0;
+        if (tiled) {
+            if (warp == 0) {
+                int k0 = 0, cnt = 0;
+                if (lane < 27) {
+                    const int dz = lane / 9 - 1, dy = (lane / 3) % 3 - 1, dx = lane % 3 - 1;
+                    const int ix = cl % q.nc[0], iy = (cl / q.nc[0]) % q.nc[1], iz = cl / (q.nc[0] * q.nc[1]);
+                    const int vz = iz + dz, nz = floordiv(vz, q.nc[2]), cz = vz - nz * q.nc[2];
+                    const int vy = iy + dy, ny = floordiv(vy, q.nc[1]), cy = vy - ny * q.nc[1];
+                    const int vx = ix + dx, nx = floordiv(vx, q.nc[0]), cx = vx - nx * q.nc[0];
+                    const int cc = q.cell0 + (cz * q.nc[1] + cy) * q.nc[0] + cx;
+                    k0 = a.cstart[cc];
+                    cnt = a.cstart[cc + 1] - k0;
+                    s_k0[lane] = k0;
+                    s_n[lane] = bytes3(nx, ny, nz);
+                    s_sh[lane][0] = (float)nx * q.Lf[0];
+                    s_sh[lane][1] = (float)ny * q.Lf[1];
+                    s_sh[lane][2] = (float)nz * q.Lf[2];
+                }
+                int incl = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(full, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                if (lane < 27) s_off[lane + 1] = incl;
+                if (lane == 0) s_off[0] = 0;
+            }
+            __syncthreads();
+            T = s_off[27];
+        }
+        // image counts common to all home atoms of the item?
+        unsigned m_first = 0;
+        bool uni = true;
+        if (MODE != SM_COUNT) {
+            m_first = a.xsm[h0 + part];
+            bool same = true;
+            for (int h = part + a.split * threadIdx.x; h < nh; h += a.split * NL_THREADS) same &= a.xsm[h0 + h] == m_first;
+            uni = __syncthreads_and(same) && !(m_first & NL_FAR);
+        }
+        if (!tiled || T > NL_BCAND) {
+            for (int h = part + a.split * warp; h < nh; h += a.split * NL_WARPS) {
+                const float4 me = a.xs[h0 + h];
+                if (MODE == SM_FILL) {
+                    search_atom_generic<true>(a, q, cl, me, lane);
+                } else {
+                    search_atom_generic<false>(a, q, cl, me, lane);
+                    if (MODE == SM_SLAB && lane == 0) nl_redo(a, __float_as_int(me.w));
+                }
+            }
+            __syncthreads();
+            continue;
+        }
+        // stage all candidates of the item (loads before stores)
+        for (int e0 = threadIdx.x; e0 < T; e0 += NL_THREADS * 4) {
+            float4 o[4];
+            unsigned pm[4];
+            int sts[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = e0 + NL_THREADS * u;
+                int st = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int t = st + step;
+                    if (t <= 26 && s_off[t] <= e) st = t;
+                }
+                sts[u] = st;
+                o[u] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                pm[u] = 0;
+                if (e < T) {
+                    const int kc = s_k0[st] + (e - s_off[st]);
+                    o[u] = a.xs[kc];
+                    if (MODE != SM_COUNT) pm[u] = a.xsm[kc];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = e0 + NL_THREADS * u;
+                if (e < T) {
+                    const int st = sts[u];
+                    unsigned info = (unsigned)st;
+                    if (MODE != SM_COUNT) {
+                        const unsigned n = s_n[st], mh = uni ? m_first : 0u;
+                        const unsigned v = (pm[u] & NL_FAR) ? NL_FAR
+                                                            : bytes3(byte_at(n, 0) - byte_at(pm[u], 0) + byte_at(mh, 0),
+                                                                     byte_at(n, 1) - byte_at(pm[u], 1) + byte_at(mh, 1),
+                                                                     byte_at(n, 2) - byte_at(pm[u], 2) + byte_at(mh, 2));
+                        info |= (v & NL_FAR) ? 32u : (v << 8);
+                    }
+                    cand[e] = make_float4(o[u].x + s_sh[st][0], o[u].y + s_sh[st][1], o[u].z + s_sh[st][2], o[u].w);
+                    cinfo[e] = info;
+                }
+            }
+        }
+        __syncthreads();
+        const int home_lo = s_off[NL_HOME_STENCIL], home_hi = s_off[NL_HOME_STENCIL + 1];
+        const float lo2 = a.rc2f - q.eps2, hi2 = a.rc2f + q.eps2;
+        const int nhp = (nh - part + a.split - 1) / a.split;       // home atoms of the item
+        // warp w: home atoms r = w, w + 8, ... of the item, up to 32 at a time
+        for (int g0 = warp; g0 < nhp; g0 += NL_WARPS * 32) {
+            const int ng = min(32, (nhp - g0 + NL_WARPS - 1) / NL_WARPS);
+            int hidx = 0, hacc = 0;
+            unsigned hmb = 0;
+            bool hredo = false;
+            if (lane < ng) {
+                const int hk = h0 + part + a.split * (g0 + NL_WARPS * lane);
+                const float4 hv = a.xs[hk];
+                hidx = __float_as_int(hv.w);
+                s_home[lane] = hv;
+                if (MODE != SM_COUNT) hmb = a.xsm[hk];
+                if (MODE == SM_FILL) hacc = a.row_ptr[hidx];
+            }
+            __syncwarp();
+            for (int base = 0; base < T; base += 32) {
+                const int el = base + lane;
+                const bool valid = el < T;
+                float4 cv = make_float4(3.0e30f, 3.0e30f, 3.0e30f, 0.0f);
+                unsigned info = 0;
+                if (valid) {
+                    cv = cand[el];
+                    info = cinfo[el];
+                }
+                const int j = __float_as_int(cv.w);
+                const unsigned n = s_n[info & 31u];
+                const int n0 = byte_at(n, 0), n1 = byte_at(n, 1), n2 = byte_at(n, 2);
+                const bool self = base < home_hi && base + 32 > home_lo;
+                if (uni) {
+                    if (self)
+                        test_chunk<MODE, true, true>(a, s_home, ng, cv, valid, j, info, n0, n1, n2, lo2, hi2, q,
+                                                     rc2, lane, hacc, hmb, hredo);
+                    else
+                        test_chunk<MODE, false, true>(a, s_home, ng, cv, valid, j, info, n0, n1, n2, lo2, hi2, q,
+                                                      rc2, lane, hacc, hmb, hredo);
+                } else if (MODE != SM_COUNT) {
+                    test_chunk<MODE, true, false>(a, s_home, ng, cv, valid, j, info, n0, n1, n2, lo2, hi2, q,
+                                                  rc2, lane, hacc, hmb, hredo);
+                }
+            }
+            if (MODE != SM_FILL && lane < ng) {
+                a.counts[hidx] = hacc;
+                if (MODE == SM_SLAB) {
+                    const bool over = hacc > a.maxn || hredo;
+                    a.redo[hidx] = over ? 1 : 0;
+                    if (over) a.redo_list[atomicAdd(a.n_redo, 1)] = hidx;
+                }
+            }
+            __syncwarp();
+        }
+        __syncthreads();                                           // the staging is rewritten next
+    }
+}
+
+// Compaction after the slab pass: each warp copies NL_COPY_ROWS slab rows at a time into
+// their CSR rows (all loads of a step before its stores); rows marked for a redo -- longer
+// than the slab, or of structures that take the per-atom search -- are searched again
+// straight into the CSR row.
+constexpr int NL_COPY_ROWS = 4;
+
+__device__ void ph_compact(const NlArgs &a, int bid, int nb) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned full = 0xffffffffu;
+    if (__shfl_sync(full, lane == 0 ? (int)status_bad(a.status) : 0, 0)) return;
+    const int gw = bid + nb * warp, nw = nb * NL_WARPS;
+    for (int i0 = gw * NL_COPY_ROWS; i0 < a.N; i0 += nw * NL_COPY_ROWS) {
+        int r0[NL_COPY_ROWS], cnt[NL_COPY_ROWS], kmax = 0;
+#pragma unroll
+        for (int u = 0; u < NL_COPY_ROWS; ++u) {
+            const int i = i0 + u;
+            r0[u] = 0;
+            cnt[u] = 0;
+            if (i < a.N) {
+                r0[u] = a.row_ptr[i];
+                cnt[u] = a.redo[i] ? 0 : a.row_ptr[i + 1] - r0[u];
+            }
+            kmax = max(kmax, cnt[u]);
+        }
+        for (int k0 = 0; k0 < kmax; k0 += 64) {
+            unsigned e[NL_COPY_ROWS][2];
+#pragma unroll
+            for (int u = 0; u < NL_COPY_ROWS; ++u)
+#pragma unroll
+                for (int v = 0; v < 2; ++v) {
+                    const int k = k0 + 32 * v + lane;
+                    e[u][v] = k < cnt[u] ? a.slab[(size_t)(i0 + u) * a.maxn + k] : 0u;
+                }
+#pragma unroll
+            for (int u = 0; u < NL_COPY_ROWS; ++u)
+#pragma unroll
+                for (int v = 0; v < 2; ++v) {
+                    const int k = k0 + 32 * v + lane;
+                    const unsigned code = e[u][v] >> 27;                 // 0..26 in rows that are copied
+                    const int s0 = (int)(code % 3u) - 1, s1 = (int)((code / 3u) % 3u) - 1, s2 = (int)(code / 9u) - 1;
+                    if (k < cnt[u]) {
+                        a.col[r0[u] + k] = (int)(e[u][v] & 0x7FFFFFFu);
+                        a.shift[r0[u] + k] = make_char4((signed char)s0, (signed char)s1, (signed char)s2, 0);
+                    }
+                }
+        }
+    }
+    const int nredo = *a.n_redo;
+    for (int r = gw; r < nredo; r += nw) {
+        const int i = a.redo_list[r];
+        const int c = a.cellid[i];
+        const NlStruct &q = a.S[structure_of_cell(a.S, a.B, c)];
+        const float4 me = make_float4((float)a.xw[3 * i], (float)a.xw[3 * i + 1], (float)a.xw[3 * i + 2],
+                                      __int_as_float(i));
+        search_atom_generic<true>(a, q, c - q.cell0, me, lane);
+    }
+}
+
+// ------------------------------------------------------------------ kernels
+enum NlPhase { PH_SETUP, PH_BIN, PH_SCAN_CELLS_ONE, PH_SCAN1_CELLS, PH_SCAN2_CELLS, PH_SCATTER, PH_SORT, PH_COUNT,
+               PH_SCAN_ROWS_ONE, PH_SCAN1_ROWS, PH_SCAN2_ROWS, PH_FILL };
+// with a slab, PH_COUNT is the single search pass and PH_FILL the compaction
+
+__device__ __forceinline__ void run_phase(const NlArgs &a, int ph, int bid, int nb, float4 *smem) {
+    switch (ph) {
+    case PH_SETUP: ph_setup(a, bid, nb); break;
+    case PH_BIN: ph_bin(a, bid, nb); break;
+    case PH_SCAN_CELLS_ONE: ph_scan_one(a.ccount, a.cstart, *a.ncells, bid, 0, nullptr, a.status); break;
+    case PH_SCAN1_CELLS: ph_scan1(a.ccount, a.cstart, *a.ncells, a.bsum, bid, nb); break;
+    case PH_SCAN2_CELLS: ph_scan2(a.cstart, *a.ncells, a.bsum, bid, nb, 0, nullptr, a.status); break;
+    case PH_SCATTER: ph_scatter(a, bid, nb); break;
+    case PH_SORT: ph_sort(a, bid, nb); break;
+    case PH_COUNT:
+        if (a.block_items) {
+            if (a.maxn > 0) ph_search_block<SM_SLAB>(a, bid, nb, smem);
+            else ph_search_block<SM_COUNT>(a, bid, nb, smem);
+        } else {
+            if (a.maxn > 0) ph_search<SM_SLAB>(a, bid, nb, smem);
+            else ph_search<SM_COUNT>(a, bid, nb, smem);
+        }
+        break;
+    case PH_SCAN_ROWS_ONE: ph_scan_one(a.counts, a.row_ptr, a.N, bid, a.cap, a.n_pairs, a.status); break;
+    case PH_SCAN1_ROWS: ph_scan1(a.counts, a.row_ptr, a.N, a.bsum, bid, nb); break;
+    case PH_SCAN2_ROWS: ph_scan2(a.row_ptr, a.N, a.bsum, bid, nb, a.cap, a.n_pairs, a.status); break;
+    default:
+        if (a.maxn > 0) ph_compact(a, bid, nb);
+        else if (a.block_items) ph_search_block<SM_FILL>(a, bid, nb, smem);
+        else ph_search<SM_FILL>(a, bid, nb, smem);
+        break;
+    }
+}
+
+// All phases in one launch; the scans take one block when they are short (the decision is
+// the same in every block: it reads the same counts).
+__global__ void __launch_bounds__(NL_THREADS, 2) k_nl_coop(NlArgs a) {
+    extern __shared__ float4 nl_smem[];
+    const int bid = blockIdx.x, nb = gridDim.x;
+    run_phase(a, PH_SETUP, bid, nb, nl_smem);
+    if (!nl_grid_sync(a.bar, a.status)) return;
+    run_phase(a, PH_BIN, bid, nb, nl_smem);
+    if (!nl_grid_sync(a.bar, a.status)) return;
+    if (*a.ncells <= NL_SCAN_ONE_BLOCK) {
+        run_phase(a, PH_SCAN_CELLS_ONE, bid, nb, nl_smem);
+    } else {
+        run_phase(a, PH_SCAN1_CELLS, bid, nb, nl_smem);
+        if (!nl_grid_sync(a.bar, a.status)) return;
+        run_phase(a, PH_SCAN2_CELLS, bid, nb, nl_smem);
+    }
+    if (!nl_grid_sync(a.bar, a.status)) return;
+    run_phase(a, PH_SCATTER, bid, nb, nl_smem);
+    if (!nl_grid_sync(a.bar, a.status)) return;
+    run_phase(a, PH_SORT, bid, nb, nl_smem);
+    if (!nl_grid_sync(a.bar, a.status)) return;
+    run_phase(a, PH_COUNT, bid, nb, nl_smem);
+    if (!nl_grid_sync(a.bar, a.status)) return;
+    if (a.N <= NL_SCAN_ONE_BLOCK) {
+        run_phase(a, PH_SCAN_ROWS_ONE, bid, nb, nl_smem);
+    } else {
+        run_phase(a, PH_SCAN1_ROWS, bid, nb, nl_smem);
+        if (!nl_grid_sync(a.bar, a.status)) return;
+        run_phase(a, PH_SCAN2_ROWS, bid, nb, nl_smem);
+    }
+    if (!nl_grid_sync(a.bar, a.status)) return;
+    run_phase(a, PH_FILL, bid, nb, nl_smem);
+}
+
+__global__ void __launch_bounds__(NL_THREADS, 2) k_nl_phase(NlArgs a, int ph) {
+    extern __shared__ float4 nl_smem[];
+    run_phase(a, ph, blockIdx.x, gridDim.x, nl_smem);
 }
 
 // ------------------------------------------------------------------ host
 struct NlWs {
     NlStruct *S;
-    int32_t *sid, *mimg, *cellid, *ccount, *cstart, *cfill, *unsorted, *counts, *scan_tmp;
+    int32_t *ncells, *mimg, *cellid, *ccount, *cstart, *cfill, *unsorted, *counts, *bsum, *redo_list, *n_redo;
+    uint32_t *xsm, *mpk;
+    uint8_t *redo;
+    uint32_t *slab;
+    unsigned *bar;
     double *xw;
     float4 *xs;
 };
@@ -348,7 +1107,8 @@ static NlWs carve_nl(Carve &c, int B, int N) {
     const int ncmax = N + B;
     const size_t n1 = N > 0 ? (size_t)N : 1;
     w.S = c.take<NlStruct>(B);
-    w.sid = c.take<int32_t>(n1);
+    w.ncells = c.take<int32_t>(1);
+    w.bar = c.take<unsigned>(2);
     w.xw = c.take<double>(3 * n1);
     w.mimg = c.take<int32_t>(3 * n1);
     w.cellid = c.take<int32_t>(n1);
@@ -357,73 +1117,192 @@ static NlWs carve_nl(Carve &c, int B, int N) {
     w.cfill = c.take<int32_t>(ncmax);
     w.unsorted = c.take<int32_t>(n1);
     w.xs = c.take<float4>(n1);
+    w.xsm = c.take<uint32_t>(n1);
+    w.mpk = c.take<uint32_t>(n1);
+    w.redo = c.take<uint8_t>(n1);
+    w.redo_list = c.take<int32_t>(n1);
+    w.n_redo = c.take<int32_t>(1);
     w.counts = c.take<int32_t>(n1);
-    w.scan_tmp = c.take<int32_t>(scan_tmp_ints(ncmax + 1 > N ? ncmax + 1 : N));
+    w.bsum = c.take<int32_t>(NL_MAX_BLOCKS);
     return w;
 }
 
-size_t nl_workspace_bytes(int n_struct, int n_atoms) {
+// Slab row length for a list of `capacity` pairs: 1.25x the mean row plus a margin, in
+// multiples of 32 (rows longer than this are searched again during the compaction).
+static int nl_slab_row(int64_t capacity, int n_atoms) {
+    if (n_atoms <= 0 || n_atoms >= (1 << 27)) return 0;
+    int64_t m = (capacity * 5) / (4 * (int64_t)n_atoms) + 16;
+    m = (m + 31) / 32 * 32;
+    return (int)(m < 64 ? 64 : (m > 4096 ? 4096 : m));
+}
+
+size_t nl_workspace_min_bytes(int n_struct, int n_atoms) {
     Carve c(reinterpret_cast<void *>(256), ~size_t(0) >> 1);
     carve_nl(c, n_struct, n_atoms);
     return c.off + 256;
 }
 
+size_t nl_workspace_bytes(int n_struct, int n_atoms, int64_t capacity) {
+    const int maxn = nl_slab_row(capacity, n_atoms);
+    return nl_workspace_min_bytes(n_struct, n_atoms) + (maxn > 0 ? (size_t)n_atoms * maxn * sizeof(uint32_t) + 256 : 0);
+}
+
+struct NlDevice {
+    bool init = false;
+    int sms = 0, coop_blocks = 0;
+};
+
+static NlDevice &nl_device() {
+    static NlDevice d[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    NlDevice &x = d[dev & 63];
+    if (!x.init) {
+        cudaDeviceGetAttribute(&x.sms, cudaDevAttrMultiProcessorCount, dev);
+        int coop = 0;
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+        cudaFuncSetAttribute(k_nl_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)NL_SMEM);
+        cudaFuncSetAttribute(k_nl_phase, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)NL_SMEM);
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_nl_coop, NL_THREADS, NL_SMEM) != cudaSuccess)
+            per_sm = 0;
+        x.coop_blocks = coop ? per_sm * x.sms : 0;
+        x.init = true;
+    }
+    return x;
+}
+
+// parts per home cell: enough work items for the warps of a small system, few repeated
+// candidate reads for a large one
+static int nl_auto_split(int N, bool block_items) {
+    if (block_items) return N < 4096 ? 2 : 1;
+    return N < 65536 ? 2 : 1;
+}
+
 gm_status nl_build(const gm_system &sys, double r_cut, int n_species, gm_nlist &nl, void *ws, size_t ws_bytes,
-                   int32_t *status, cudaStream_t st) {
+                   int32_t *status, cudaStream_t st, const NlTuning &tune) {
     const int B = sys.n_structures, N = sys.n_atoms;
     Carve c(ws, ws_bytes);
     NlWs w = carve_nl(c, B, N);
     if (!c.ok) return GM_ERR_WORKSPACE;
+    // the single-pass search when the workspace also holds the slab, else the two-pass one
+    int maxn = tune.two_pass ? 0 : nl_slab_row(nl.capacity, N);
+    w.slab = nullptr;
+    if (maxn > 0) {
+        w.slab = c.take<uint32_t>((size_t)N * maxn);
+        if (!c.ok) { maxn = 0; w.slab = nullptr; }
+    }
+    NlArgs a;
+    a.N = N;
+    a.B = B;
+    a.n_species = n_species;
+    a.ncmax = N + B;
+    a.block_items = tune.items == 1 ? 1 : (tune.items == 2 ? 0 : (N < 16384 ? 1 : 0));
+    a.split = tune.split > 0 ? tune.split : nl_auto_split(N, a.block_items != 0);
+    a.atom_ptr = sys.atom_ptr;
+    a.pos = sys.pos;
+    a.species = sys.species;
+    a.cell = sys.cell;
+    a.pbc = sys.pbc;
+    a.rc = r_cut;
+    a.rc2f = (float)(r_cut * r_cut);
+    a.S = w.S;
+    a.ncells = w.ncells;
+    a.cellid = w.cellid;
+    a.ccount = w.ccount;
+    a.cstart = w.cstart;
+    a.cfill = w.cfill;
+    a.unsorted = w.unsorted;
+    a.counts = w.counts;
+    a.bsum = w.bsum;
+    a.mimg = w.mimg;
+    a.xw = w.xw;
+    a.xs = w.xs;
+    a.xsm = w.xsm;
+    a.mpk = w.mpk;
+    a.slab = w.slab;
+    a.maxn = maxn;
+    a.redo = w.redo;
+    a.redo_list = w.redo_list;
+    a.n_redo = w.n_redo;
+    a.row_ptr = nl.row_ptr;
+    a.col = nl.col;
+    a.shift = reinterpret_cast<char4 *>(nl.shift);
+    a.cap = nl.capacity;
+    a.n_pairs = nl.n_pairs;
+    a.bar = w.bar;
+    a.status = status;
+
+    NlDevice &dev = nl_device();
     const int ncmax = N + B;
-    std::optional<StageScope> scope;  // sub-stage events (profiling only)
+    auto clampi = [](long long v, long long lo, long long hi) { return (int)(v < lo ? lo : (v > hi ? hi : v)); };
+    if (tune.mode != GM_NL_MODE_PHASES && dev.coop_blocks > 0) {
+        // one cooperative launch, at most as many blocks as are co-resident
+        const long long want = tune.blocks > 0 ? tune.blocks : 2LL * dev.sms;
+        const int grid = clampi(want, 1, dev.coop_blocks < NL_MAX_BLOCKS ? dev.coop_blocks : NL_MAX_BLOCKS);
+        StageScope sc(ST_NL_COOP, st);
+        if (cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), st) != cudaSuccess) return GM_ERR_CUDA;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(NL_THREADS);
+        cfg.dynamicSmemBytes = NL_SMEM;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        if (cudaLaunchKernelEx(&cfg, k_nl_coop, a) != cudaSuccess) return GM_ERR_CUDA;
+        note_launches(1);
+        return cudaPeekAtLastError() == cudaSuccess ? GM_OK : GM_ERR_CUDA;
+    }
+    // one launch per phase
+    const int g_setup = clampi((ncmax + NL_THREADS - 1) / NL_THREADS, 1, NL_MAX_BLOCKS);
+    const int g_atoms = clampi((N + NL_THREADS - 1) / NL_THREADS, 1, NL_MAX_BLOCKS);
+    const int g_cells_scan = clampi((ncmax + NL_SCAN_SUB - 1) / NL_SCAN_SUB, 1, NL_MAX_BLOCKS);
+    const int g_rows_scan = clampi((N + NL_SCAN_SUB - 1) / NL_SCAN_SUB, 1, NL_MAX_BLOCKS);
+    const int g_sort = clampi((ncmax + NL_WARPS - 1) / NL_WARPS, 1, NL_MAX_BLOCKS);
+    const int g_search =
+        clampi(tune.blocks > 0 ? tune.blocks
+                               : (a.block_items ? (long long)ncmax * a.split
+                                                : ((long long)ncmax * a.split + NL_WARPS - 1) / NL_WARPS),
+               1, 8LL * dev.sms);
+    std::optional<StageScope> scope;
+    int launches = 0;
+    auto phase = [&](int grid, int ph) {
+        const bool search = ph == PH_COUNT || (ph == PH_FILL && maxn == 0);
+        k_nl_phase<<<grid, NL_THREADS, search ? NL_SMEM : 0, st>>>(a, ph);
+        ++launches;
+    };
     scope.emplace(ST_NL_BIN, st);
-    if (cudaMemsetAsync(w.ccount, 0, sizeof(int32_t) * ncmax, st) != cudaSuccess) return GM_ERR_CUDA;
-    if (cudaMemsetAsync(w.cfill, 0, sizeof(int32_t) * ncmax, st) != cudaSuccess) return GM_ERR_CUDA;
-    k_nl_setup<<<1, 1024, 0, st>>>(B, sys.atom_ptr, sys.cell, sys.pbc, r_cut, w.S, status);
-    note_launches(1);
-    const int tb = 256;
-    if (N > 0) {
-        k_nl_bin<<<(N + tb - 1) / tb, tb, 0, st>>>(N, B, sys.atom_ptr, sys.pos, sys.species, n_species, w.S, w.sid,
-                                                   w.xw, w.mimg, w.cellid, w.ccount, status);
-        note_launches(1);
-    }
-    exclusive_scan(w.ccount, w.cstart, ncmax, w.scan_tmp, st);
-    if (N > 0) {
-        k_nl_scatter<<<(N + tb - 1) / tb, tb, 0, st>>>(N, w.cellid, w.cstart, w.cfill, w.unsorted);
-        const int G = N >= 16384 ? 8 : 32;
-        const long long warps_cells = (long long)ncmax * 32, warps_atoms = (long long)N * G;
-        k_nl_sortcells<<<(int)((warps_cells + tb - 1) / tb), tb, 0, st>>>(ncmax, w.cstart, w.unsorted, w.xw, w.xs);
-        const float rc2f = (float)(r_cut * r_cut);
-        scope.reset();
-        scope.emplace(ST_NL_COUNT, st);
-        if (G == 8)
-            k_nl_search<false, 8><<<(int)((warps_atoms + tb - 1) / tb), tb, 0, st>>>(
-                N, w.S, w.sid, w.cellid, w.cstart, w.xs, w.xw, w.mimg, r_cut, rc2f, w.counts, nullptr, 0, nullptr,
-                nullptr, status);
-        else
-            k_nl_search<false, 32><<<(int)((warps_atoms + tb - 1) / tb), tb, 0, st>>>(
-                N, w.S, w.sid, w.cellid, w.cstart, w.xs, w.xw, w.mimg, r_cut, rc2f, w.counts, nullptr, 0, nullptr,
-                nullptr, status);
-        scope.reset();
-        scope.emplace(ST_NL_SCAN, st);
-        exclusive_scan(w.counts, nl.row_ptr, N, w.scan_tmp, st);
-        k_nl_total<<<1, 1, 0, st>>>(nl.row_ptr + N, nl.capacity, nl.n_pairs, status);
-        scope.reset();
-        scope.emplace(ST_NL_FILL, st);
-        if (G == 8)
-            k_nl_search<true, 8><<<(int)((warps_atoms + tb - 1) / tb), tb, 0, st>>>(
-                N, w.S, w.sid, w.cellid, w.cstart, w.xs, w.xw, w.mimg, r_cut, rc2f, nullptr, nl.row_ptr, nl.capacity,
-                nl.col, reinterpret_cast<char4 *>(nl.shift), status);
-        else
-            k_nl_search<true, 32><<<(int)((warps_atoms + tb - 1) / tb), tb, 0, st>>>(
-                N, w.S, w.sid, w.cellid, w.cstart, w.xs, w.xw, w.mimg, r_cut, rc2f, nullptr, nl.row_ptr, nl.capacity,
-                nl.col, reinterpret_cast<char4 *>(nl.shift), status);
-        note_launches(5);
+    phase(g_setup, PH_SETUP);
+    phase(g_atoms, PH_BIN);
+    if (ncmax <= NL_SCAN_ONE_BLOCK) {
+        phase(1, PH_SCAN_CELLS_ONE);
     } else {
-        exclusive_scan(w.counts, nl.row_ptr, 0, w.scan_tmp, st);
-        k_nl_total<<<1, 1, 0, st>>>(nl.row_ptr, nl.capacity, nl.n_pairs, status);
-        note_launches(1);
+        phase(g_cells_scan, PH_SCAN1_CELLS);
+        phase(g_cells_scan, PH_SCAN2_CELLS);
     }
+    phase(g_atoms, PH_SCATTER);
+    phase(g_sort, PH_SORT);
+    scope.reset();
+    scope.emplace(ST_NL_COUNT, st);
+    phase(g_search, PH_COUNT);
+    scope.reset();
+    scope.emplace(ST_NL_SCAN, st);
+    if (N <= NL_SCAN_ONE_BLOCK) {
+        phase(1, PH_SCAN_ROWS_ONE);
+    } else {
+        phase(g_rows_scan, PH_SCAN1_ROWS);
+        phase(g_rows_scan, PH_SCAN2_ROWS);
+    }
+    scope.reset();
+    scope.emplace(ST_NL_FILL, st);
+    phase(maxn > 0 ? clampi(((long long)N + NL_WARPS * NL_COPY_ROWS - 1) / (NL_WARPS * NL_COPY_ROWS), 1, 8LL * dev.sms)
+                   : g_search,
+          PH_FILL);
+    note_launches(launches);
+    scope.reset();
     return cudaPeekAtLastError() == cudaSuccess ? GM_OK : GM_ERR_CUDA;
 }
 

@@ -54,7 +54,7 @@ gm_status gm_build_neighbors_noalloc(const gm_model *m, const gm_system *sys, gm
         return set_last_error(GM_ERR_ARG, "bad system");
     if (!nl->row_ptr || !nl->n_pairs || nl->capacity < 0 || (nl->capacity > 0 && (!nl->col || !nl->shift)))
         return set_last_error(GM_ERR_ARG, "bad neighbour list");
-    const size_t need = gm::nl_workspace_bytes(sys->n_structures, sys->n_atoms);
+    const size_t need = gm::nl_workspace_min_bytes(sys->n_structures, sys->n_atoms);
     if (need > GM_NOALLOC_SCRATCH_BYTES)
         return set_last_error(GM_ERR_WORKSPACE,
                               "system too large for the fixed 8 MiB scratch of gm_build_neighbors_noalloc "
@@ -64,7 +64,7 @@ gm_status gm_build_neighbors_noalloc(const gm_model *m, const gm_system *sys, gm
         return set_last_error(GM_ERR_CUDA, "cudaGetSymbolAddress of the fixed scratch failed");
     const gm_model_desc *d = gm::model_desc(m);
     gm_status s = gm::nl_build(*sys, d->r_cut, d->n_species, *nl, scratch, GM_NOALLOC_SCRATCH_BYTES, status_dev,
-                               stream);
+                               stream, gm::nl_tuning(m));
     if (s != GM_OK) return set_last_error(s, "neighbour build launch failed");
     return cudaPeekAtLastError() == cudaSuccess ? GM_OK : set_last_error(GM_ERR_CUDA, "launch failed");
 }

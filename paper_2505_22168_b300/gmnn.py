@@ -101,6 +101,7 @@ class GMNN:
             self.handle = L.gm_model_create(self.cdesc)
         self.status = torch.zeros(1, dtype=torch.int32, device=self.device)
         self._ws = {}
+        self.tuning = {}
         self.theta = None
         if params is not None:
             self.set_params(pack_theta(params))
@@ -122,12 +123,19 @@ class GMNN:
         self.theta = th
         L.gm_model_set_params(self.handle, _ptr(th), _stream())
 
-    def set_tuning(self, pair_tpa=None, split_mask=None, gemm_bn=None):
-        """Speed knobs of the library (gm_model_set_tuning); None leaves a knob unchanged."""
-        for key, val in ((L.GM_TUNE_PAIR_TPA, pair_tpa), (L.GM_TUNE_SPLIT_MASK, split_mask),
-                         (L.GM_TUNE_GEMM_BN, gemm_bn)):
+    TUNING_KEYS = {"pair_tpa": L.GM_TUNE_PAIR_TPA, "split_mask": L.GM_TUNE_SPLIT_MASK, "gemm_bn": L.GM_TUNE_GEMM_BN,
+                   "nl_mode": L.GM_TUNE_NL_MODE, "nl_split": L.GM_TUNE_NL_SPLIT, "nl_blocks": L.GM_TUNE_NL_BLOCKS,
+                   "nl_two_pass": L.GM_TUNE_NL_TWO_PASS, "nl_items": L.GM_TUNE_NL_ITEMS}
+
+    def set_tuning(self, **knobs):
+        """Speed knobs of the library (gm_model_set_tuning): pair_tpa, split_mask, gemm_bn,
+        nl_mode, nl_split, nl_blocks, nl_two_pass, nl_items.  None leaves a knob unchanged."""
+        for name, val in knobs.items():
+            if name not in self.TUNING_KEYS:
+                raise ValueError(f"unknown tuning knob {name!r}")
             if val is not None:
-                L.gm_model_set_tuning(self.handle, key, int(val))
+                L.gm_model_set_tuning(self.handle, self.TUNING_KEYS[name], int(val))
+                self.tuning[name] = int(val)
 
     # -------------------------------------------------------------- buffers
     def workspace(self, op, sysd: DeviceSystem, capacity=0):

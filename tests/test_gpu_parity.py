@@ -4,6 +4,8 @@ Neighbour sets are compared bit for bit (as sorted (i, j, shift) triples).  Ener
 forces, virials and descriptors are compared element by element within the tolerance
 stated for the FP32 path (1e-5 relative on energy per atom and force RMS).
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -85,12 +87,7 @@ def test_neighbors_self_images(rc, count):
 def test_neighbors_outside_cell_ragged_and_empty():
     """Positions far outside the cell, structures of different sizes, and an empty one."""
     _, d, p = synth.config(1)
-    rng = np.random.default_rng(3)
-    structs = []
-    for L, n in ((4.0, 5), (7.0, 40), (9.0, 0), (5.5, 17), (12.0, 130)):
-        structs.append((rng.uniform(-2 * L, 3 * L, (n, 3)), rng.integers(0, 5, n), L * np.eye(3)))
-    b = make_batch(structs, 5)
-    _assert_same_pairs(b, dict(d, r_cut=3.3), p)
+    _assert_same_pairs(_ragged_batch(), dict(d, r_cut=3.3), p)
 
 
 def test_neighbors_exactly_at_cutoff():
@@ -98,6 +95,108 @@ def test_neighbors_exactly_at_cutoff():
     pos = np.array([[1.0, 1.0, 1.0], [1.0 + 2.5, 1.0, 1.0], [1.0, 1.0 + np.nextafter(2.5, 0.0), 1.0]])
     b = make_batch([(pos, np.array([0, 1, 2]), 20 * np.eye(3))], 5)
     _assert_same_pairs(b, dict(d, r_cut=2.5, r_min=0.2), p)
+
+
+# launch shapes of the neighbour build: one cooperative launch (default) or one launch per
+# phase; blocks per home cell; grid size.  None of them may change the list or its order.
+NL_TUNINGS = [dict(nl_mode=0), dict(nl_mode=1), dict(nl_mode=0, nl_split=1), dict(nl_mode=0, nl_split=3, nl_blocks=7),
+              dict(nl_mode=1, nl_split=2), dict(nl_mode=0, nl_blocks=1), dict(nl_mode=0, nl_two_pass=1),
+              dict(nl_mode=1, nl_two_pass=1, nl_split=5), dict(nl_items=1), dict(nl_items=2),
+              dict(nl_items=1, nl_split=3, nl_two_pass=1), dict(nl_items=2, nl_split=3, nl_mode=1)]
+
+
+def _ragged_batch():
+    rng = np.random.default_rng(3)
+    structs = []
+    for L, n in ((4.0, 5), (7.0, 40), (9.0, 0), (5.5, 17), (12.0, 130)):
+        structs.append((rng.uniform(-2 * L, 3 * L, (n, 3)), rng.integers(0, 5, n), L * np.eye(3)))
+    return make_batch(structs, 5)
+
+
+@pytest.mark.parametrize("case", ["config1", "li_small", "config2", "ragged", "shifted"])
+def test_neighbor_build_launch_shapes_give_identical_rows(case, li_small):
+    GMNN, DeviceSystem = _gm()
+    if case == "li_small":
+        b, d, p = li_small
+    elif case == "ragged":
+        _, d, p = synth.config(1)
+        b, d = _ragged_batch(), dict(d, r_cut=3.3)
+    elif case == "shifted":            # every atom two boxes up along x, one down along z
+        b, d, p = synth.config(2)
+        L = b.cell[0].diagonal()
+        b = dataclasses.replace(b, pos=b.pos + np.array([2.0 * L[0], 0.0, -L[2]]))
+    else:
+        b, d, p = synth.config(1 if case == "config1" else 2)
+    want = oracle.neighbors(b, d["r_cut"]).triples()
+    ref = None
+    for tune in NL_TUNINGS:
+        m = GMNN(d, p)
+        m.set_tuning(**tune)
+        nl = m.build_neighbors(DeviceSystem(b))
+        assert np.array_equal(nl.triples(), want), tune
+        P = int(nl.n_pairs.item())
+        rows = (nl.row_ptr.cpu().numpy(), nl.col[:P].cpu().numpy(), nl.shift[:P].cpu().numpy())
+        if ref is None:
+            ref = rows
+        else:
+            assert all(np.array_equal(x, y) for x, y in zip(rows, ref)), tune
+
+
+def test_neighbors_rows_longer_than_the_search_slab():
+    """A dense ball in a sparse box: the ball's rows are far longer than the mean row the
+    search slab is sized for, so the compaction searches them again."""
+    GMNN, DeviceSystem = _gm()
+    _, d, p = synth.config(1)
+    rng = np.random.default_rng(11)
+    L = 30.0
+    ball = 15.0 + rng.normal(0.0, 1.0, (120, 3))
+    sparse = rng.uniform(0.0, L, (600, 3))
+    pos = np.concatenate([sparse[:300], ball, sparse[300:]])
+    b = make_batch([(pos, rng.integers(0, 5, len(pos)), L * np.eye(3))], 5)
+    want = oracle.neighbors(b, d["r_cut"])
+    ref = None
+    for tune in (dict(), dict(nl_two_pass=1), dict(nl_mode=1), dict(nl_items=1), dict(nl_items=2)):
+        m = GMNN(d, p)
+        m.set_tuning(**tune)
+        nl = m.build_neighbors(DeviceSystem(b))
+        got = nl.triples()
+        assert np.array_equal(got, want.triples()), tune
+        P = int(nl.n_pairs.item())
+        cur = (nl.row_ptr.cpu().numpy(), nl.col[:P].cpu().numpy(), nl.shift[:P].cpu().numpy())
+        if ref is None:
+            ref = cur
+            slab_row = max(64, -(-(nl.capacity * 3 // (2 * b.n_atoms) + 16) // 32) * 32)
+            assert np.diff(cur[0]).max() > slab_row                   # some rows exceed the slab
+        else:
+            assert all(np.array_equal(x, y) for x, y in zip(cur, ref)), tune
+
+
+def test_neighbor_build_is_graph_capturable():
+    """The cooperative build replays inside a CUDA graph and follows moved positions."""
+    GMNN, DeviceSystem = _gm()
+    b, d, p = synth.config(2)
+    m = GMNN(d, p)
+    sysd = DeviceSystem(b)
+    nl = m.build_neighbors(sysd)
+    from paper_2505_22168_b300 import NeighborList
+    from paper_2505_22168_b300 import _lib
+    from paper_2505_22168_b300.gmnn import _ptr, _stream
+    nl2 = NeighborList(b.n_atoms, nl.capacity + 4096, m.device)
+    ws, wsb = m.workspace(_lib.GM_OP_NEIGHBORS, sysd, nl2.capacity)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        _lib.gm_build_neighbors(m.handle, sysd.c_struct(), nl2.c_struct(), ws, wsb, _ptr(m.status), _stream())
+    rng = np.random.default_rng(5)
+    for step in range(3):
+        moved = b.pos + rng.normal(0.0, 0.05, b.pos.shape)
+        sysd.pos.copy_(torch.as_tensor(moved))
+        m.clear_status()
+        g.replay()
+        torch.cuda.synchronize()
+        assert m.read_status() == 0
+        bm = dataclasses.replace(b, pos=moved)
+        assert np.array_equal(nl2.triples(), oracle.neighbors(bm, d["r_cut"]).triples()), step
 
 
 def test_neighbors_capacity_overflow_reports_required_count():
