@@ -42,8 +42,9 @@ def log(*a):
 # ----------------------------------------------------------------------------- workloads
 
 WORKLOADS = {
-    2: "emim-64pairs-1536 (configs[1]: EMIM+BF4-, 1536 atoms, L=25.43 A, r_cut 6 A, MLP 2x512, 0.01 A jitter/step)",
-    5: "li3po4-131072 (configs[4]: Li3PO4-like crystal, 131072 atoms, L=109.49 A, r_cut 6 A, MLP 2x512)",
+    2: "emim-64pairs-1536 (EMIM+BF4- box, 1536 atoms, L=25.43 A, r_cut 6 A, MLP 2x512, 0.01 A jitter/step)",
+    3: "li3po4-batch-256 (256 Li3PO4-like boxes of 32-512 atoms, 67768 atoms, r_cut 5 A, MLP 2x256)",
+    5: "li3po4-131072 (Li3PO4-like crystal, 131072 atoms, L=109.49 A, r_cut 6 A, MLP 2x512)",
 }
 
 
@@ -185,7 +186,7 @@ class ClockSampler:
 # ----------------------------------------------------------------------------- roofline
 
 def algorithmic_work(stage, n_atoms, n_pairs, H):
-    """(amount, unit) of algorithmic work of one launch of a stage; see the design doc."""
+    """(amount, unit) of algorithmic work of one launch of a stage."""
     F = 360
     if stage == "gemm_l1" or stage == "gemm_b0":
         return 2.0 * n_atoms * F * H, "flop"
@@ -282,6 +283,15 @@ def run_gpu(args, cfg, precision, steps, warmup, world, rank, measure_e2e, clock
 
     pos_buf = torch.empty_like(sysd.pos)
     sysd.pos = pos_buf
+    tuning = None
+    if args.tune:
+        # launch shapes picked by timing graph replays (untimed set-up; results are identical
+        # for every setting)
+        from paper_2505_22168_b300 import autotune
+        pos_buf.copy_(pos_dev[0])
+        t = autotune.tune(model, sysd, nl, out, reps=10 if n > 50000 else 20)
+        tuning = {"settings": t["settings"], "tuned_ms": round(t["ms"], 5), "default_ms": round(t["default_ms"], 5),
+                  "trials": len(t.get("trials", []))}
 
     def step(k):                       # stream launches
         pos_buf.copy_(pos_dev[k])
@@ -365,7 +375,7 @@ def run_gpu(args, cfg, precision, steps, warmup, world, rank, measure_e2e, clock
         dist.barrier()
     res = {"ms_total": ms, "ms_per_step": ms / steps, "n_atoms": n, "n_pairs": n_pairs, "stages": stages,
            "launches": launches, "H": desc["n_hidden"], "value": world * n * steps / (ms / 1e3),
-           "launch_mode": "cuda-graph replay" if graph is not None else "stream launches",
+           "launch_mode": "cuda-graph replay" if graph is not None else "stream launches", "tuning": tuning,
            "ms_per_step_stream_with_stage_events": ms_stream / steps}
 
     if measure_e2e:
@@ -398,7 +408,7 @@ def run_gpu(args, cfg, precision, steps, warmup, world, rank, measure_e2e, clock
 
 
 def run_train(args, steps, warmup):
-    """Training step on configs[3] (32 EMIM+BF4- boxes of 96-384 atoms, MLP 2x128): neighbour
+    """Training step on 32 EMIM+BF4- boxes of 96-384 atoms (MLP 2x128): neighbour
     rebuild, energies and forces, force-matching loss against teacher labels, and the
     parameter gradient.  Reference labels come from the FP64 oracle with the teacher's
     parameters (set-up, untimed)."""
@@ -450,7 +460,7 @@ def run_train(args, steps, warmup):
     if any(k.startswith("nl_") and v[1] > 0 for k, v in stages.items()):
         stages = {k: v for k, v in stages.items() if k != "neighbors"}
     total = sum(v[0] for v in stages.values() if v[1] > 0) or 1.0
-    return {"workload": "emim-train-32 (configs[3]: 32 EMIM+BF4- boxes, 7920 atoms, r_cut 5 A, MLP 2x128)",
+    return {"workload": "emim-train-32 (32 EMIM+BF4- boxes, 7920 atoms, r_cut 5 A, MLP 2x128)",
             "precision": "fp32", "step": "neighbours + energy/forces + loss + parameter gradient",
             "value": batch.n_atoms * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
             "steps": steps, "stage_share": {k: round(v[0] / total, 4) for k, v in stages.items() if v[1] > 0}}
@@ -495,7 +505,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["auto", "fp32", "mixed"], default="auto")
-    ap.add_argument("--config", type=int, choices=[2, 5], default=2)
+    ap.add_argument("--config", type=int, choices=[2, 3, 5], default=2)
+    ap.add_argument("--tune", type=int, default=1, help="autotune launch shapes before timing")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -552,17 +563,18 @@ def main():
 
     variants = []
     if not args.no_variants:
-        for cfg in (2, 5):
+        for cfg in (2, 3, 5):
             for prec in ("fp32", "mixed"):
                 if (cfg, prec) == (args.config, precision):
                     continue
                 if prec == "mixed" and not _mixed_available():
                     continue
-                steps = max(5, args.steps // (5 if cfg == 5 else 1))
+                steps = max(5, args.steps // {2: 1, 3: 2, 5: 5}[cfg])
                 r = run_gpu(args, cfg, prec, steps, args.warmup, world, rank, False)
                 rf, sh = roofline(r["stages"], r["n_atoms"], r["n_pairs"], r["H"], prec, peaks, sustained=False)
                 variants.append({"workload": WORKLOADS[cfg], "precision": prec, "value": r["value"], "unit": UNIT,
                                  "ms_per_step": r["ms_per_step"], "steps": steps, "n_pairs": r["n_pairs"],
+                                 "launch_mode": r["launch_mode"], "tuning": r["tuning"],
                                  "dominant": rf["kernel"] if rf else None, "roofline_frac": rf["frac"] if rf else None,
                                  "stage_share": sh})
 
@@ -584,7 +596,7 @@ def main():
         "config": {"workload": WORKLOADS[args.config], "precision": precision, "n_atoms": head["n_atoms"],
                    "n_pairs": head["n_pairs"], "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "256 MiB buffer written between timed steps (outside the step events)",
-                   "neighbour_rebuild": "every step", "launch_mode": head["launch_mode"],
+                   "neighbour_rebuild": "every step", "launch_mode": head["launch_mode"], "tuning": head["tuning"],
                    "stage_timing": "library stage events on a second pass of the same steps "
                                    + ("(a second graph with event-record nodes, "
                                       if head["launch_mode"] == "cuda-graph replay" else "(stream launches, ")

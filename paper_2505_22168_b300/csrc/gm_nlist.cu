@@ -1197,7 +1197,8 @@ gm_status nl_build(const gm_system &sys, double r_cut, int n_species, gm_nlist &
     a.B = B;
     a.n_species = n_species;
     a.ncmax = N + B;
-    a.block_items = tune.items == 1 ? 1 : (tune.items == 2 ? 0 : (N < 16384 ? 1 : 0));
+    // block items for small systems and for batches of small boxes (few cells per structure)
+    a.block_items = tune.items == 1 ? 1 : (tune.items == 2 ? 0 : ((N < 16384 || N < 2048 * B) ? 1 : 0));
     a.split = tune.split > 0 ? tune.split : nl_auto_split(N, a.block_items != 0);
     a.atom_ptr = sys.atom_ptr;
     a.pos = sys.pos;

@@ -291,6 +291,31 @@ def test_energy_forces_mixed_ragged_li3po4_batch(li_small):
     _ef_parity(b, d, p, precision="mixed")
 
 
+def test_autotuned_batched_model_matches_oracle(li_small):
+    """The autotuner's choice (over a reduced knob space) keeps energies and forces within the
+    parity tolerance of the oracle."""
+    from paper_2505_22168_b300 import autotune, NeighborList
+    GMNN, DeviceSystem = _gm()
+    b, d, p = li_small
+    for precision in ("fp32", "mixed"):
+        m = GMNN(d, p, precision=precision)
+        sysd = DeviceSystem(b)
+        nl0 = m.build_neighbors(sysd)
+        nl = NeighborList(b.n_atoms, nl0.capacity, m.device)
+        out = (torch.empty(b.n_structures, dtype=torch.float64, device=m.device),
+               torch.empty(b.n_atoms, 3, dtype=torch.float32, device=m.device), None)
+        space = {"nl_items": (0, 1, 2), "pair_tpa": (0, 8, 32), "gemm_bn": (0, 128)}
+        r = autotune.tune(m, sysd, nl, out, reps=3, space=space)
+        assert set(r["settings"]) <= set(space)
+        m.step(sysd, nl, out)
+        m.check_status()
+        ref = oracle.energy_forces(b, d, p, oracle.neighbors(b, d["r_cut"]))
+        tol = TOL[precision]
+        assert energy_error(out[0].cpu().numpy(), ref, b) <= tol
+        rms, worst = force_error(out[1].cpu().numpy().astype(np.float64), ref)
+        assert rms <= tol and worst <= ELEMENT_FACTOR * tol
+
+
 def test_descriptors_match_oracle():
     b, d, p = synth.config(1)
     m, sysd, nl = _nl_pair(b, d, p)
