@@ -407,7 +407,7 @@ def run_gpu(args, cfg, precision, steps, warmup, world, rank, measure_e2e, clock
     return res
 
 
-def run_train(args, steps, warmup):
+def run_train(args, steps, warmup, precision="fp32"):
     """Training step on 32 EMIM+BF4- boxes of 96-384 atoms (MLP 2x128): neighbour
     rebuild, energies and forces, force-matching loss against teacher labels, and the
     parameter gradient.  Reference labels come from the FP64 oracle with the teacher's
@@ -422,7 +422,7 @@ def run_train(args, steps, warmup):
     batch, desc, params = synth.config(4)
     onl = oracle.neighbors(batch, desc["r_cut"])
     teach = oracle.energy_forces(batch, desc, teacher_params(4), onl, virial=False)
-    model = GMNN(desc, params, precision="fp32")
+    model = GMNN(desc, params, precision=precision)
     sysd = DeviceSystem(batch)
     nl = model.build_neighbors(sysd)
     from paper_2505_22168_b300 import NeighborList
@@ -461,7 +461,7 @@ def run_train(args, steps, warmup):
         stages = {k: v for k, v in stages.items() if k != "neighbors"}
     total = sum(v[0] for v in stages.values() if v[1] > 0) or 1.0
     return {"workload": "emim-train-32 (32 EMIM+BF4- boxes, 7920 atoms, r_cut 5 A, MLP 2x128)",
-            "precision": "fp32", "step": "neighbours + energy/forces + loss + parameter gradient",
+            "precision": precision, "step": "neighbours + energy/forces + loss + parameter gradient",
             "value": batch.n_atoms * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
             "steps": steps, "stage_share": {k: round(v[0] / total, 4) for k, v in stages.items() if v[1] > 0}}
 
@@ -579,7 +579,10 @@ def main():
                                  "stage_share": sh})
 
     if not args.no_variants:
-        variants.append(run_train(args, max(5, args.steps // 5), args.warmup))
+        for prec in ("fp32", "mixed"):
+            if prec == "mixed" and not _mixed_available():
+                continue
+            variants.append(run_train(args, max(5, args.steps // 5), args.warmup, prec))
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

@@ -14,6 +14,7 @@
 #include <stdio.h>
 #include <stdlib.h>
 
+#include <algorithm>
 #include <atomic>
 #include <mutex>
 #include <string>
@@ -244,6 +245,7 @@ size_t ef_workspace_bytes(int B, int N, int H) {
 struct PgWs {
     float *psi, *psid, *psib, *psidb, *GG, *Gbs, *Z, *A1s, *P1, *Q1, *Zd1, *Zb2s, *Zb1s, *Y3, *t_sig, *t_c, *t_cs,
         *beta_part, *wg_part;
+    __nv_bfloat16 *hl;   // mixed path: hi/lo BF16 copy of the current GEMM's A operand [2 Mp][2 K]
 };
 
 PgWs carve_pg(Carve &c, int N, int H, int S) {
@@ -267,9 +269,13 @@ PgWs carve_pg(Carve &c, int N, int H, int S) {
     w.t_sig = c.take<float>(m1);
     w.t_c = c.take<float>(m1);
     w.t_cs = c.take<float>(m1);
-    w.beta_part = c.take<float>((size_t)(pg_beta_blocks(N) + 1) * S * S * NR * NB);
+    w.beta_part = c.take<float>((size_t)(pg_beta_blocks(N, S) + 1) * S * S * NR * NB);
+    w.hl = c.take<__nv_bfloat16>(2 * m1 * 2 * (size_t)(H > NFP ? H : NFP));
     const int ks = wgrad_ksplit(2 * Mp);
-    w.wg_part = c.take<float>((size_t)ks * NFP * (H > NFP ? H : NFP) + (size_t)ks * H * H);
+    size_t scratch = (size_t)ks * NFP * (H > NFP ? H : NFP) + (size_t)ks * H * H;   // weight-gradient slices,
+    scratch = std::max(scratch, colsum_part_floats(Mp, H));                           // later column sums
+    scratch = std::max(scratch, pg_tail_part_floats(N, S));                           // and species sums
+    w.wg_part = c.take<float>(scratch);
     return w;
 }
 
@@ -653,30 +659,46 @@ gm_status gm_param_grad(const gm_model *m, const gm_system *sys, const gm_nlist 
     {   // network forward (primal + tangent rows) and reverse
         StageScope sc(ST_PG_NETWORK, st);
         EpiArgs e{};
-        e.out0 = w.Z;
-        gemm_f32(EPI_STORE, 0, w.GG, m->W1t, 2 * Mp, H, NFP, e, st);
+        // the four stacked-row GEMMs: FFMA in the FP32 path; tcgen05 on hi/lo BF16 copies of
+        // the A operand in the mixed path (split passes as for the energy/force GEMMs)
+        const bool mixed = m->d.precision == GM_PREC_MIXED;
+        const int sp = m->split_mask;
+        auto mm = [&](int which, const float *A, const float *Bf, const __nv_bfloat16 *Bh, int N_, int K_,
+                      float *out) -> gm_status {
+            e.out0 = out;
+            if (!mixed) {
+                gemm_f32(EPI_STORE, 0, A, Bf, 2 * Mp, N_, K_, e, st);
+                return GM_OK;
+            }
+            split_bf16(A, 2 * Mp, K_, w.hl, st);
+            return gemm_bf16(EPI_STORE, 0, w.hl, Bh, 2 * Mp, N_, K_, ((sp >> which) & 1) != 0, e, status, st,
+                             m->gemm_bn);
+        };
+        gm_status gs;
+        if ((gs = mm(0, w.GG, m->W1t, m->W1t_h, H, NFP, w.Z)) != GM_OK) return fail(gs, "network GEMM 1 failed");
         pg_act1(act, Mp, H, w.Z, m->b1, w.A1s, w.P1, w.Q1, w.Zd1, st);
-        gemm_f32(EPI_STORE, 0, w.A1s, m->W2t, 2 * Mp, H, H, e, st);
+        if ((gs = mm(1, w.A1s, m->W2t, m->W2t_h, H, H, w.Z)) != GM_OK) return fail(gs, "network GEMM 2 failed");
         pg_act2(act, N, Mp, H, B, sys->atom_ptr, sys->species, S, dL_dE, m->sigma, m->w3, m->b2, m->b3, w.Z, w.Zb2s,
                 w.Y3, w.t_sig, w.t_c, w.t_cs, st);
-        gemm_f32(EPI_STORE, 0, w.Zb2s, m->W2, 2 * Mp, H, H, e, st);         // a1 adjoints (primal, tangent)
+        // a1 adjoints (primal, tangent)
+        if ((gs = mm(2, w.Zb2s, m->W2, m->W2_h, H, H, w.Z)) != GM_OK) return fail(gs, "network GEMM 3 failed");
         pg_act1b(Mp, H, w.Z, w.P1, w.Q1, w.Zd1, w.Zb1s, st);
-        e.out0 = w.Gbs;
-        gemm_f32(EPI_STORE, 0, w.Zb1s, m->W1p, 2 * Mp, NFP, H, e, st);     // feature adjoints
+        // feature adjoints
+        if ((gs = mm(3, w.Zb1s, m->W1p, m->W1p_h, NFP, H, w.Gbs)) != GM_OK) return fail(gs, "network GEMM 4 failed");
         // weight and bias gradients
         wgrad(w.GG, NFP, w.Zb1s, H, 2 * Mp, NFP, H, NF, w.wg_part, grad_theta + o.W1, st);
         wgrad(w.A1s, H, w.Zb2s, H, 2 * Mp, H, H, H, w.wg_part, grad_theta + o.W2, st);
-        colsum(Mp, H, w.Zb1s, grad_theta + o.b1, st);
-        colsum(Mp, H, w.Zb2s, grad_theta + o.b2, st);
-        colsum(Mp, H, w.Y3, grad_theta + o.w3, st);
-        pg_tail(N, sys->species, S, w.t_sig, w.t_c, w.t_cs, grad_theta + o.sigma, grad_theta + o.mu,
+        colsum(Mp, H, w.Zb1s, w.wg_part, grad_theta + o.b1, st);
+        colsum(Mp, H, w.Zb2s, w.wg_part, grad_theta + o.b2, st);
+        colsum(Mp, H, w.Y3, w.wg_part, grad_theta + o.w3, st);
+        pg_tail(N, sys->species, S, w.t_sig, w.t_c, w.t_cs, w.wg_part, grad_theta + o.sigma, grad_theta + o.mu,
                 grad_theta + o.b3, st);
     }
     {   // moment adjoints and the species-pair coefficient gradient
         StageScope sc(ST_PG_PAIR_BWD, st);
         launch_contract_bwd_dual(w.psi, w.psid, w.Gbs, N, Mp, w.psib, w.psidb, st);
         launch_pg_beta(a, dL_dF, w.psib, w.psidb, w.beta_part, st);
-        pg_beta_reduce(pg_beta_blocks(N), S * S * NR * NB, (float)(1.0 / sqrt((double)NB)), w.beta_part,
+        pg_beta_reduce(pg_beta_blocks(N, S), S * S * NR * NB, (float)(1.0 / sqrt((double)NB)), w.beta_part,
                        grad_theta + o.beta, st);
     }
     return launch_status();

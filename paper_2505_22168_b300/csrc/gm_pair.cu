@@ -341,25 +341,31 @@ __global__ void __launch_bounds__(256) k_moments_tangent(PairArgs a, const float
 //   P1_s = sum_c psib[s][c] m_c,  P2_s = sum_c psidb[s][c] m_c,
 //   P3_s = sum_c psidb[s][c] (D_c - L_c m_c w)
 // accumulated per block in shared memory, block partials written to part[block][S S 35].
-template <int TPA>
+// dJ/dbeta partials.  One warp per centre atom i (species zi); each lane accumulates its pairs'
+// NR x NB terms B_k alpha_s + dB_k gamma_s into its own slice of shared memory, indexed by the
+// neighbour's species (layout [z][s][k][lane]: lanes never share a bank, no atomics).  After
+// the row the lanes add up the 32 slices (lane l takes entries l, l + 32, ...) into the
+// block's [S][S][NR][NB] accumulator (one atomic per entry, distinct entries per lane) and
+// clear them.  Block partials are summed in a fixed order by k_pg_beta_reduce.
 __global__ void __launch_bounds__(256) k_pg_beta(PairArgs a, const float *__restrict__ vel,
                                                  const float *__restrict__ psib, const float *__restrict__ psidb,
                                                  float *__restrict__ part) {
     extern __shared__ float sm[];
-    const int nbeta = a.S * a.S * NR * NB;
-    float *acc = sm;
+    const int nbeta = a.S * a.S * NR * NB, nlane = a.S * NR * NB;     // per-lane slice: [S][NR][NB]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    float *acc = sm;                                                   // [nbeta]
+    float *pw = sm + nbeta + warp * 2 * NPSI;                          // this warp's psib, psidb
+    float *la = sm + nbeta + nwarps * 2 * NPSI + (size_t)warp * nlane * 32;
     for (int q = threadIdx.x; q < nbeta; q += blockDim.x) acc[q] = 0.0f;
+    for (int q = lane; q < nlane * 32; q += 32) la[q] = 0.0f;
     __syncthreads();
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    const int atom = g / TPA, sub = g % TPA;
-    const bool active = atom < a.N && !status_bad(a.status);
-    if (active) {
-        float pb[NPSI], pdb[NPSI];
-#pragma unroll
-        for (int q = 0; q < NPSI; ++q) {
-            pb[q] = psib[(size_t)atom * NPSI + q];
-            pdb[q] = psidb[(size_t)atom * NPSI + q];
+    const bool ok_status = !status_bad(a.status);
+    for (int atom = blockIdx.x * nwarps + warp; ok_status && atom < a.N; atom += gridDim.x * nwarps) {
+        for (int q = lane; q < NPSI; q += 32) {
+            pw[q] = psib[(size_t)atom * NPSI + q];
+            pw[NPSI + q] = psidb[(size_t)atom * NPSI + q];
         }
+        __syncwarp();
         const int b = structure_of(a.atom_ptr, a.B, atom);
         const double Lx = a.cell[9 * b], Ly = a.cell[9 * b + 4], Lz = a.cell[9 * b + 8];
         const double xi = a.pos[3 * atom], yi = a.pos[3 * atom + 1], zi = a.pos[3 * atom + 2];
@@ -367,10 +373,10 @@ __global__ void __launch_bounds__(256) k_pg_beta(PairArgs a, const float *__rest
         const int zsi = clamp_species(a.species[atom], a.S, a.status);
         const int p1 = a.row_ptr[atom + 1];
         NextPair nx;
-        nx.load(a, a.row_ptr[atom] + sub, p1);
-        for (int p = a.row_ptr[atom] + sub; p < p1; p += TPA) {
+        nx.load(a, a.row_ptr[atom] + lane, p1);
+        for (int p = a.row_ptr[atom] + lane; p < p1; p += 32) {
             const NextPair cur = nx;
-            nx.load(a, p + TPA, p1);
+            nx.load(a, p + 32, p1);
             if (!cur.ok) continue;
             const int j = cur.j;
             float fx, fy, fz;
@@ -390,21 +396,35 @@ __global__ void __launch_bounds__(256) k_pg_beta(PairArgs a, const float *__rest
                                  ddz * dmono(c, 2, ux, uy, uz);
                 ang[c] = Dc - (float)comp_rank(c) * m[c] * w;
             }
-            float *dst = acc + (zsi * a.S + clamp_species(a.species[j], a.S, a.status)) * (NR * NB);
+            float *dst = la + (size_t)clamp_species(a.species[j], a.S, a.status) * (NR * NB) * 32 + lane;
 #pragma unroll
             for (int s = 0; s < NR; ++s) {
                 float P1 = 0.0f, P2 = 0.0f, P3 = 0.0f;
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
-                    P1 = fmaf(pb[s * NC + c], m[c], P1);
-                    P2 = fmaf(pdb[s * NC + c], m[c], P2);
-                    P3 = fmaf(pdb[s * NC + c], ang[c], P3);
+                    P1 = fmaf(pw[s * NC + c], m[c], P1);
+                    P2 = fmaf(pw[NPSI + s * NC + c], m[c], P2);
+                    P3 = fmaf(pw[NPSI + s * NC + c], ang[c], P3);
                 }
                 const float alpha = fmaf(P3, rinv, P1), gam = w * P2;
 #pragma unroll
-                for (int k = 0; k < NB; ++k) atomicAdd(dst + s * NB + k, fmaf(B[k], alpha, dB[k] * gam));
+                for (int k = 0; k < NB; ++k) dst[(s * NB + k) * 32] += fmaf(B[k], alpha, dB[k] * gam);
             }
         }
+        __syncwarp();
+        // add the lanes' slices into the block accumulator for species row zi, and clear them
+        for (int e = lane; e < nlane; e += 32) {
+            float t = 0.0f;
+            float *row = la + (size_t)e * 32;
+#pragma unroll 8
+            for (int l = 0; l < 32; ++l) {                         // rotated: lanes read distinct banks
+                const int ll = (l + lane) & 31;
+                t += row[ll];
+                row[ll] = 0.0f;
+            }
+            if (t != 0.0f) atomicAdd(acc + zsi * nlane + e, t);
+        }
+        __syncwarp();
     }
     __syncthreads();
     for (int q = threadIdx.x; q < nbeta; q += blockDim.x) part[(size_t)blockIdx.x * nbeta + q] = acc[q];
@@ -471,15 +491,27 @@ void launch_moments_tangent(const PairArgs &a, const float *vel, float *psid, cu
     }
 }
 
-int pg_beta_blocks(int N) { return (N * 4 + 255) / 256; }
+// warps per block of k_pg_beta: the per-lane slices take S x NR x NB x 32 floats per warp
+static int pg_beta_warps(int S) {
+    const size_t per_warp = sizeof(float) * ((size_t)S * NR * NB * 32 + 2 * NPSI);
+    int w = (int)((96u << 10) / per_warp);
+    return w < 1 ? 1 : (w > 8 ? 8 : w);
+}
+
+int pg_beta_blocks(int N, int S) {
+    const int w = pg_beta_warps(S);
+    const int b = (N + w - 1) / w;
+    return b < 1 ? 1 : (b > 148 * 8 ? 148 * 8 : b);
+}
 
 void launch_pg_beta(const PairArgs &a, const float *vel, const float *psib, const float *psidb, float *part,
                     cudaStream_t st) {
-    const int threads = 256, TPA = 4;
-    const int blocks = pg_beta_blocks(a.N);
-    const size_t smem = sizeof(float) * a.S * a.S * NR * NB;
-    if (blocks > 0) {
-        k_pg_beta<TPA><<<blocks, threads, smem, st>>>(a, vel, psib, psidb, part);
+    const int w = pg_beta_warps(a.S);
+    const int blocks = pg_beta_blocks(a.N, a.S);
+    const size_t smem = sizeof(float) * ((size_t)a.S * a.S * NR * NB + (size_t)w * (2 * NPSI + a.S * NR * NB * 32));
+    if (a.N > 0) {
+        cudaFuncSetAttribute(k_pg_beta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_pg_beta<<<blocks, 32 * w, smem, st>>>(a, vel, psib, psidb, part);
         note_launches(1);
     }
 }

@@ -24,7 +24,7 @@ void launch_forces(const PairArgs &a, int tpa, const float *dpsi, float *F, floa
 
 // parameter gradient: tangent moments along vel (= dL/dF) and block partials of dJ/dbeta
 void launch_moments_tangent(const PairArgs &a, const float *vel, float *psid, cudaStream_t st);
-int pg_beta_blocks(int N);
+int pg_beta_blocks(int N, int S);
 void launch_pg_beta(const PairArgs &a, const float *vel, const float *psib, const float *psidb, float *part,
                     cudaStream_t st);
 

@@ -92,11 +92,34 @@ __global__ void __launch_bounds__(256) k_pg_act1b(int Mp, int H, const float *__
 }
 
 // out[h] = sum_{m < M} A[m][h], one thread per column (fixed order, FP64 accumulation)
-__global__ void __launch_bounds__(256) k_colsum(int M, int H, const float *__restrict__ A, float *__restrict__ out) {
+// Column sums of A [M][H]: block (column group of 32, chunk of CS_ROWS rows) writes
+// part[chunk][col]; k_colsum_final adds the chunks in FP64 in a fixed order.
+constexpr int CS_ROWS = 256;
+__global__ void __launch_bounds__(256) k_colsum_part(int M, int H, const float *__restrict__ A,
+                                                     float *__restrict__ part) {
+    __shared__ float sm[8][33];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int col = blockIdx.x * 32 + lane;
+    const int r0 = blockIdx.y * CS_ROWS, r1 = min(M, r0 + CS_ROWS);
+    float s = 0.0f;
+    if (col < H)
+        for (int m = r0 + warp; m < r1; m += 8) s += A[(size_t)m * H + col];
+    sm[warp][lane] = s;
+    __syncthreads();
+    if (warp == 0 && col < H) {
+        float t = 0.0f;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) t += sm[w][lane];
+        part[(size_t)blockIdx.y * H + col] = t;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_colsum_final(int chunks, int H, const float *__restrict__ part,
+                                                      float *__restrict__ out) {
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
     if (h >= H) return;
     double s = 0.0;
-    for (int m = 0; m < M; ++m) s += A[(size_t)m * H + h];
+    for (int r = 0; r < chunks; ++r) s += part[(size_t)r * H + h];
     out[h] = (float)s;
 }
 
@@ -149,43 +172,91 @@ __global__ void __launch_bounds__(256) k_wgrad_reduce(int ksplit, int Mo, int No
     out[e] = (float)s;
 }
 
-// per-species sums of the scale/shift gradients and the output bias (one block)
-__global__ void __launch_bounds__(256) k_pg_tail(int N, const int32_t *__restrict__ species, int S,
-                                                 const float *__restrict__ t_sig, const float *__restrict__ t_c,
-                                                 const float *__restrict__ t_cs, float *g_sigma, float *g_mu,
-                                                 float *g_b3) {
-    __shared__ double sh[256];
-    for (int z = -1; z < S; ++z) {
-        for (int which = 0; which < (z < 0 ? 1 : 2); ++which) {
-            double v = 0.0;
-            for (int i = threadIdx.x; i < N; i += blockDim.x) {
-                if (z < 0) v += t_cs[i];
-                else if (min(max(species[i], 0), S - 1) == z) v += which == 0 ? t_sig[i] : t_c[i];
-            }
-            sh[threadIdx.x] = v;
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                double s = 0.0;
-                for (int q = 0; q < (int)blockDim.x; ++q) s += sh[q];
-                if (z < 0) *g_b3 = (float)s;
-                else if (which == 0) g_sigma[z] = (float)s;
-                else g_mu[z] = (float)s;
-            }
-            __syncthreads();
+// Per-species sums of the scale/shift gradients and the output-bias sum: block b sums the
+// atoms [b * TAIL_ATOMS, ...) into part[b][q], q = 0 (b3), 1 + z (sigma_z), 1 + S + z (mu_z);
+// k_pg_tail_final adds the blocks in FP64 in a fixed order.
+constexpr int TAIL_ATOMS = 2048;
+__global__ void __launch_bounds__(256) k_pg_tail_part(int N, const int32_t *__restrict__ species, int S,
+                                                      const float *__restrict__ t_sig, const float *__restrict__ t_c,
+                                                      const float *__restrict__ t_cs, float *__restrict__ part) {
+    __shared__ float sm[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int a0 = blockIdx.x * TAIL_ATOMS, a1 = min(N, a0 + TAIL_ATOMS);
+    const int nq = 1 + 2 * S;
+    for (int q = 0; q < nq; ++q) {
+        const int z = q == 0 ? -1 : (q - 1) % S;
+        const bool mu = q > S;
+        float v = 0.0f;
+        for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
+            if (z < 0) v += t_cs[i];
+            else if (min(max(species[i], 0), S - 1) == z) v += mu ? t_c[i] : t_sig[i];
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) sm[warp] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float t = 0.0f;
+            for (int w = 0; w < 8; ++w) t += sm[w];
+            part[(size_t)blockIdx.x * nq + q] = t;
+        }
+        __syncthreads();
     }
 }
 
+__global__ void k_pg_tail_final(int nblocks, int S, const float *__restrict__ part, float *g_sigma, float *g_mu,
+                                float *g_b3) {
+    const int q = threadIdx.x, nq = 1 + 2 * S;
+    if (q >= nq) return;
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += part[(size_t)b * nq + q];
+    if (q == 0) *g_b3 = (float)s;
+    else if (q <= S) g_sigma[q - 1] = (float)s;
+    else g_mu[q - 1 - S] = (float)s;
+}
+
+// One warp per coefficient: lanes take every 32nd block partial (FP64), then a fixed
+// shuffle tree adds the lanes' sums.
 __global__ void __launch_bounds__(256) k_pg_beta_reduce(int nblocks, int nbeta, float scale,
                                                         const float *__restrict__ part, float *__restrict__ out) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (e >= nbeta) return;
     double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += part[(size_t)b * nbeta + e];
-    out[e] = (float)(s * scale);
+    for (int b = lane; b < nblocks; b += 32) s += part[(size_t)b * nbeta + e];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[e] = (float)(s * scale);
+}
+
+// hi/lo BF16 copy of an FP32 matrix [rows][K]: dst row = [hi(K) | lo(K)], lo = bf16(x - hi)
+__global__ void __launch_bounds__(256) k_split_bf16(const float *__restrict__ src, int rows, int K,
+                                                    __nv_bfloat16 *__restrict__ dst) {
+    const int kw = K / 8;
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)rows * kw) return;
+    const size_t r = idx / kw;
+    const int c = (int)(idx - r * kw) * 8;
+    const float4 v0 = *reinterpret_cast<const float4 *>(src + r * K + c);
+    const float4 v1 = *reinterpret_cast<const float4 *>(src + r * K + c + 4);
+    const float v[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+    __align__(16) __nv_bfloat16 hi[8], lo[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        hi[q] = __float2bfloat16_rn(v[q]);
+        lo[q] = __float2bfloat16_rn(v[q] - __bfloat162float(hi[q]));
+    }
+    *reinterpret_cast<uint4 *>(dst + r * 2 * K + c) = *reinterpret_cast<const uint4 *>(hi);
+    *reinterpret_cast<uint4 *>(dst + r * 2 * K + K + c) = *reinterpret_cast<const uint4 *>(lo);
 }
 
 // ------------------------------------------------------------------ launchers
+void split_bf16(const float *src, int rows, int K, __nv_bfloat16 *dst, cudaStream_t st) {
+    const size_t n = (size_t)rows * (K / 8);
+    if (n == 0) return;
+    k_split_bf16<<<(int)((n + 255) / 256), 256, 0, st>>>(src, rows, K, dst);
+    note_launches(1);
+}
+
 void pg_act1(int act, int Mp, int H, const float *Z, const float *b1, float *A1s, float *P1, float *Q1, float *Zd1,
              cudaStream_t st) {
     const int blocks = 148 * 8;
@@ -213,14 +284,19 @@ void pg_act1b(int Mp, int H, const float *Ab, const float *P1, const float *Q1, 
     note_launches(1);
 }
 
-void colsum(int M, int H, const float *A, float *out, cudaStream_t st) {
-    k_colsum<<<(H + 255) / 256, 256, 0, st>>>(M, H, A, out);
-    note_launches(1);
+void colsum(int M, int H, const float *A, float *part, float *out, cudaStream_t st) {
+    const int chunks = (M + CS_ROWS - 1) / CS_ROWS;
+    if (chunks > 0) k_colsum_part<<<dim3((H + 31) / 32, chunks), 256, 0, st>>>(M, H, A, part);
+    k_colsum_final<<<(H + 255) / 256, 256, 0, st>>>(chunks, H, part, out);
+    note_launches(chunks > 0 ? 2 : 1);
 }
 
+size_t colsum_part_floats(int M, int H) { return (size_t)((M + CS_ROWS - 1) / CS_ROWS) * H; }
+
+// K-slices of the weight gradient: about 256 rows each (enough blocks for the GPU), at most 128
 int wgrad_ksplit(int K) {
-    int ks = K / 1024;
-    return ks < 1 ? 1 : (ks > 64 ? 64 : ks);
+    int ks = K / 256;
+    return ks < 1 ? 1 : (ks > 128 ? 128 : ks);
 }
 
 void wgrad(const float *A, int lda, const float *B, int ldb, int K, int Mo, int No, int Mstore, float *part, float *out,
@@ -235,14 +311,18 @@ void wgrad(const float *A, int lda, const float *B, int ldb, int K, int Mo, int 
     note_launches(2);
 }
 
+size_t pg_tail_part_floats(int N, int S) { return (size_t)((N + TAIL_ATOMS - 1) / TAIL_ATOMS + 1) * (1 + 2 * S); }
+
 void pg_tail(int N, const int32_t *species, int S, const float *t_sig, const float *t_c, const float *t_cs,
-             float *g_sigma, float *g_mu, float *g_b3, cudaStream_t st) {
-    k_pg_tail<<<1, 256, 0, st>>>(N, species, S, t_sig, t_c, t_cs, g_sigma, g_mu, g_b3);
-    note_launches(1);
+             float *part, float *g_sigma, float *g_mu, float *g_b3, cudaStream_t st) {
+    const int nb = (N + TAIL_ATOMS - 1) / TAIL_ATOMS;
+    if (nb > 0) k_pg_tail_part<<<nb, 256, 0, st>>>(N, species, S, t_sig, t_c, t_cs, part);
+    k_pg_tail_final<<<1, ((1 + 2 * S + 31) / 32) * 32, 0, st>>>(nb, S, part, g_sigma, g_mu, g_b3);
+    note_launches(nb > 0 ? 2 : 1);
 }
 
 void pg_beta_reduce(int nblocks, int nbeta, float scale, const float *part, float *out, cudaStream_t st) {
-    k_pg_beta_reduce<<<(nbeta + 255) / 256, 256, 0, st>>>(nblocks, nbeta, scale, part, out);
+    k_pg_beta_reduce<<<(nbeta * 32 + 255) / 256, 256, 0, st>>>(nblocks, nbeta, scale, part, out);
     note_launches(1);
 }
 

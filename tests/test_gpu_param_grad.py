@@ -2,7 +2,9 @@
 oracle, through the C ABI and through the torch.autograd.Function.
 
 Tolerance (no figure is stated for the gradient): relative L2 error per parameter group
-<= 1e-4 for the FP32 kernels, and element-wise |error| <= 1e-3 x max|group|."""
+<= 1e-4 for the FP32 kernels, and element-wise |error| <= 1e-3 x max|group|.  The mixed path
+(network GEMMs on tcgen05 with BF16 operands, hi/lo split for the backward GEMMs, FP32
+accumulation) is held to 1e-2 relative L2 per group and 5e-2 element-wise."""
 import numpy as np
 import pytest
 
@@ -15,8 +17,8 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 GROUPS = ("beta", "W1", "b1", "W2", "b2", "w3", "b3", "sigma", "mu")
-TOL_L2 = 1e-4
-TOL_ELEM = 1e-3
+TOL_L2 = {"fp32": 1e-4, "mixed": 1e-2}
+TOL_ELEM = {"fp32": 1e-3, "mixed": 5e-2}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -40,21 +42,25 @@ def _setup(batch, desc, params, precision="fp32", seed=11):
     return m, sysd, nl, onl, ref, Eref, Fref
 
 
-def _compare(g_dev, go, n_species, n_hidden):
+def _compare(g_dev, go, n_species, n_hidden, precision="fp32"):
     from paper_2505_22168_b300 import unpack_theta
     g = unpack_theta(g_dev.cpu().numpy().astype(np.float64), n_species, n_hidden)
+    worst = {}
     for k in GROUPS:
         ref = go[k].reshape(-1)
         got = g[k].reshape(-1)
         scale = np.linalg.norm(ref)
         assert scale > 0, k
         rel = np.linalg.norm(got - ref) / scale
-        assert rel <= TOL_L2, (k, rel)
-        assert np.abs(got - ref).max() <= TOL_ELEM * np.abs(ref).max(), k
+        elem = np.abs(got - ref).max() / np.abs(ref).max()
+        worst[k] = (rel, elem)
+        assert rel <= TOL_L2[precision], (k, rel)
+        assert elem <= TOL_ELEM[precision], (k, elem)
+    return worst
 
 
-def _param_grad_case(batch, desc, params):
-    m, sysd, nl, onl, ref, Eref, Fref = _setup(batch, desc, params)
+def _param_grad_case(batch, desc, params, precision="fp32"):
+    m, sysd, nl, onl, ref, Eref, Fref = _setup(batch, desc, params, precision=precision)
     E, F, _ = m.energy_forces(sysd, nl)
     m.check_status()
     # the loss kernel, on the GPU's own energies and forces
@@ -72,7 +78,7 @@ def _param_grad_case(batch, desc, params):
                      torch.as_tensor(gF_o, dtype=torch.float32, device=m.device))
     m.check_status()
     go = oracle.param_grad(batch, desc, params, onl, gE_o, gF_o.astype(np.float32).astype(np.float64))
-    _compare(g, go, desc["n_species"], desc["n_hidden"])
+    return _compare(g, go, desc["n_species"], desc["n_hidden"], precision)
 
 
 @pytest.mark.parametrize("act", ["tanh", "silu"])
@@ -85,6 +91,14 @@ def test_param_grad_emim_batch():
     """Several EMIM boxes of different sizes (the training workload's structure)."""
     b4, d, p = synth.config(4)
     _param_grad_case(subset(b4, [0, 1, 2, 5]), d, p)
+
+
+@pytest.mark.parametrize("act", ["tanh", "silu"])
+def test_param_grad_mixed_precision(act):
+    """BF16 network GEMMs on tcgen05 in the parameter gradient (training with a BF16 MLP)."""
+    b4, d, p = synth.config(4, activation=act)
+    worst = _param_grad_case(subset(b4, [0, 1, 2, 5]), d, p, precision="mixed")
+    print("mixed param-grad errors (rel L2, elementwise):", {k: tuple(round(x, 6) for x in v) for k, v in worst.items()})
 
 
 def test_param_grad_small_li3po4_boxes_multi_image():
