@@ -110,10 +110,12 @@ typedef struct {
     int64_t *n_pairs;   /* device scalar: number of pairs found (also set on overflow) */
 } gm_nlist;
 
-/* Workspace kinds for gm_workspace_size.  For GM_OP_NEIGHBORS the size includes a search
- * slab of about 1.5 x capacity / n_atoms entries per atom, which lets the build test every
- * candidate pair once; gm_build_neighbors also accepts a workspace without room for the slab
- * (then it tests the candidates twice: count, then fill). */
+/* Workspace kinds for gm_workspace_size.  For GM_OP_NEIGHBORS and nl_capacity > 0 the size
+ * includes a search slab of 4 x (1.25 x capacity / n_atoms + 16, rounded up to 32) bytes per
+ * atom, which lets the build test every candidate pair once; with nl_capacity = 0 it is the
+ * minimum, without the slab.  gm_build_neighbors accepts any workspace of at least the
+ * minimum and uses the slab when it fits (else it tests the candidates twice: count, then
+ * fill). */
 enum { GM_OP_NEIGHBORS = 0, GM_OP_ENERGY_FORCES = 1, GM_OP_PARAM_GRAD = 2 };
 
 /* Number of FP32 parameters.  Flat layout of theta, in this order:
@@ -186,8 +188,9 @@ GM_API gm_status gm_energy_forces(const gm_model *m, const gm_system *sys, const
  * implicit synchronisation would stall the other streams mid-step.
  * Scratch is a fixed 8 MiB array in the library's own device memory (a file-scope
  * __device__ variable that every GPU loading the library holds until the process exits),
- * which fits systems of up to about 100,000 atoms: exactly, those whose
- * gm_workspace_size(..., GM_OP_NEIGHBORS) is at most 8 MiB.  Larger systems return
+ * which fits systems of up to about 100,000 atoms: exactly, those whose minimum neighbour
+ * workspace, gm_workspace_size(..., nl_capacity = 0, GM_OP_NEIGHBORS), is at most 8 MiB (the
+ * single-pass search is used when its slab fits too).  Larger systems return
  * GM_ERR_WORKSPACE (gm_last_error says why) without launching anything.
  * The first call on a device, with that device current, looks up the array's device
  * address (cudaGetSymbolAddress) and caches it; make that first call before any stream

@@ -1130,7 +1130,7 @@ static NlWs carve_nl(Carve &c, int B, int N) {
 // Slab row length for a list of `capacity` pairs: 1.25x the mean row plus a margin, in
 // multiples of 32 (rows longer than this are searched again during the compaction).
 static int nl_slab_row(int64_t capacity, int n_atoms) {
-    if (n_atoms <= 0 || n_atoms >= (1 << 27)) return 0;
+    if (n_atoms <= 0 || n_atoms >= (1 << 27) || capacity <= 0) return 0;
     int64_t m = (capacity * 5) / (4 * (int64_t)n_atoms) + 16;
     m = (m + 31) / 32 * 32;
     return (int)(m < 64 ? 64 : (m > 4096 ? 4096 : m));
