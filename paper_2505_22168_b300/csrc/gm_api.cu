@@ -501,7 +501,8 @@ static gm_status forward_to_features(const gm_model *m, const gm_system *sys, co
     {
         StageScope sc(ST_CONTRACT_FWD, st);
         if (m->d.precision == GM_PREC_MIXED && features_out == nullptr)
-            launch_contract_fwd_bf16(psi, N, Mp, reinterpret_cast<__nv_bfloat16 *>(w.G), nullptr, st);
+            launch_contract_fwd_bf16(psi, N, Mp, reinterpret_cast<__nv_bfloat16 *>(w.G), nullptr,
+                                     (m->split_mask & 1) != 0, st);
         else
             launch_contract_fwd_f32(psi, N, Mp, w.G, features_out, st);
     }
@@ -530,6 +531,7 @@ static gm_status network_fwd_bwd(const gm_model *m, const gm_system *sys, EfWs &
         e.bias = m->b1;
         e.out0 = A1;
         e.out1 = D1;
+        e.lo_out = (sp & 2) != 0;   // lo halves only where the consuming GEMM runs split
         {
             StageScope sc(ST_GEMM_L1, st);
             if ((s = gemm_bf16(EPI_L1, m->d.activation, G, m->W1t_h, Mp, H, NFP, (sp & 1) != 0, e, status, st, m->gemm_bn)) != GM_OK)
@@ -538,6 +540,7 @@ static gm_status network_fwd_bwd(const gm_model *m, const gm_system *sys, EfWs &
         e.bias = m->b2;
         e.out0 = dZ2;
         e.out1 = nullptr;
+        e.lo_out = (sp & 4) != 0;
         {
             StageScope sc(ST_GEMM_L2, st);
             if ((s = gemm_bf16(EPI_L2, m->d.activation, A1, m->W2t_h, Mp, H, H, (sp & 2) != 0, e, status, st, m->gemm_bn)) != GM_OK)
@@ -545,6 +548,7 @@ static gm_status network_fwd_bwd(const gm_model *m, const gm_system *sys, EfWs &
         }
         e.out0 = dZ1;
         e.aux = D1;
+        e.lo_out = (sp & 8) != 0;
         {
             StageScope sc(ST_GEMM_B1, st);
             if ((s = gemm_bf16(EPI_B1, 0, dZ2, m->W2_h, Mp, H, H, (sp & 4) != 0, e, status, st, m->gemm_bn)) != GM_OK)

@@ -217,7 +217,8 @@ __device__ __forceinline__ void fwd_group(const T (&P)[NPSI], const FeatOut &gt)
 
 template <typename OutT>
 __global__ void __launch_bounds__(CT_THREADS, 1) k_contract_fwd(const float *__restrict__ psi, int N, int Mp,
-                                                                OutT *__restrict__ G, float *__restrict__ G32) {
+                                                                OutT *__restrict__ G, float *__restrict__ G32,
+                                                                int lo_out) {
     extern __shared__ float tile[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * CT_ATOMS;
@@ -252,7 +253,7 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_contract_fwd(const float *__r
             }
             __nv_bfloat16 *row = reinterpret_cast<__nv_bfloat16 *>(G) + (size_t)m * 2 * NFP + c * 8;
             *reinterpret_cast<uint4 *>(row) = *reinterpret_cast<const uint4 *>(hi);
-            *reinterpret_cast<uint4 *>(row + NFP) = *reinterpret_cast<const uint4 *>(lo);
+            if (lo_out) *reinterpret_cast<uint4 *>(row + NFP) = *reinterpret_cast<const uint4 *>(lo);
         } else {
             *reinterpret_cast<float4 *>(G + (size_t)m * NFP + c * 4) = make_float4(v[0], v[1], v[2], v[3]);
         }
@@ -651,17 +652,17 @@ void launch_contract_fwd_f32(const float *psi, int N, int Mp, float *G, float *f
     const int blocks = (Mp + CT_ATOMS - 1) / CT_ATOMS;
     const size_t smem = sizeof(float) * CT_ATOMS * GT_STRIDE;
     if (blocks > 0) {
-        k_contract_fwd<float><<<blocks, CT_THREADS, smem, st>>>(psi, N, Mp, G, features_out);
+        k_contract_fwd<float><<<blocks, CT_THREADS, smem, st>>>(psi, N, Mp, G, features_out, 0);
         note_launches(1);
     }
 }
 
-void launch_contract_fwd_bf16(const float *psi, int N, int Mp, __nv_bfloat16 *G, float *features_out,
+void launch_contract_fwd_bf16(const float *psi, int N, int Mp, __nv_bfloat16 *G, float *features_out, bool lo_out,
                               cudaStream_t st) {
     const int blocks = (Mp + CT_ATOMS - 1) / CT_ATOMS;
     const size_t smem = sizeof(float) * CT_ATOMS * GT_STRIDE;
     if (blocks > 0) {
-        k_contract_fwd<__nv_bfloat16><<<blocks, CT_THREADS, smem, st>>>(psi, N, Mp, G, features_out);
+        k_contract_fwd<__nv_bfloat16><<<blocks, CT_THREADS, smem, st>>>(psi, N, Mp, G, features_out, lo_out ? 1 : 0);
         note_launches(1);
     }
 }

@@ -9,7 +9,9 @@ namespace gm {
 // feature columns >= 360 zero).
 // features_out [N][360] FP32 (optional copy for diagnostics, may be NULL).
 void launch_contract_fwd_f32(const float *psi, int N, int Mp, float *G, float *features_out, cudaStream_t st);
-void launch_contract_fwd_bf16(const float *psi, int N, int Mp, __nv_bfloat16 *G, float *features_out,
+// lo_out: also write the lo halves of the hi/lo BF16 rows (needed when the first network
+// GEMM runs with the split passes)
+void launch_contract_fwd_bf16(const float *psi, int N, int Mp, __nv_bfloat16 *G, float *features_out, bool lo_out,
                               cudaStream_t st);
 // dE/dG [Mp][384] FP32 and psi -> dE/dpsi [N][100] FP32 (unique components)
 void launch_contract_bwd(const float *psi, const float *dG, int N, float *dpsi, cudaStream_t st);

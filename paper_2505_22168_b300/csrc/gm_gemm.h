@@ -26,6 +26,7 @@ struct EpiArgs {
     void *out1;              // D1 (L1)
     const void *aux;         // D1 (B1)
     float *nn_part;          // [M][N/32] (L2): partial output-layer sums per 32 columns
+    int lo_out;              // BF16 outputs: also write the lo half (the consumer runs split)
 };
 // BF16 operands of the tcgen05 path are stored as hi/lo pairs, [rows][2K]: columns [0, K)
 // hold hi = bf16(x), columns [K, 2K) hold lo = bf16(x - hi).  A GEMM run with split = 0

@@ -28,6 +28,7 @@ constexpr uint64_t WAIT_NS = 1000000000ull; // bound of every wait
 
 __host__ __device__ constexpr int stages_for(int bn) { return bn >= 256 ? 4 : 6; }
 __host__ __device__ constexpr int tmem_cols_for(int bn) { return bn <= 32 ? 32 : (bn <= 64 ? 64 : (bn <= 128 ? 128 : 256)); }
+__host__ __device__ constexpr size_t ring_bytes_for(int bn) { return (size_t)stages_for(bn) * (A_STAGE_BYTES + bn * BK * 2); }
 __host__ __device__ constexpr size_t smem_bytes_for(int bn) {
     return (size_t)stages_for(bn) * (A_STAGE_BYTES + bn * BK * 2) + 1024 + 256;
 }
@@ -178,58 +179,112 @@ __device__ __forceinline__ float act_fast(float z, float &d1) {
     return z * s;
 }
 
-// Epilogue of one row segment of 32 columns starting at column n (multiple of 32).
-// BF16 outputs go to [m][n] (hi) and [m][N + n] (lo) of a [M][2N] array.
-template <int EPI, int ACT>
-__device__ __forceinline__ void epilogue32(const EpiArgs &e, int m, int n, int N, float (&v)[32], float &part) {
-    if (EPI == EPI_STORE) {
-        float4 *o = reinterpret_cast<float4 *>(static_cast<float *>(e.out0) + (size_t)m * N + n);
+// Per-warp staging of a 32-row x 32-column tile in the (then idle) stage ring, so that rows
+// held one per thread leave and arrive as whole 64- or 128-byte row segments: rows padded to
+// 80 and 144 bytes keep the 16-byte accesses of a warp on distinct banks.
+struct EpiStage {
+    uint4 hi[32][5];
+    uint4 lo[32][5];
+    float4 d[32][9];
+};
+constexpr size_t EPI_STAGE_BYTES = sizeof(EpiStage);
+
+// 32 rows x 32 BF16 (64 B a row) from the staging rows to out[row0 + r][col0 ..]
+__device__ __forceinline__ void warp_store_bf16(const uint4 (*st)[5], __nv_bfloat16 *out, int row0, size_t ld,
+                                                int col0, int lane) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-        return;
-    }
-    __nv_bfloat16 *ob = static_cast<__nv_bfloat16 *>(e.out0) + (size_t)m * 2 * N + n;
-    uint4 *ohi = reinterpret_cast<uint4 *>(ob), *olo = reinterpret_cast<uint4 *>(ob + N);
-    if (EPI == EPI_B1) {
-        const float4 *d = reinterpret_cast<const float4 *>(static_cast<const float *>(e.aux) + (size_t)m * N + n);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const float4 g0 = d[2 * q], g1 = d[2 * q + 1];
-            const float g[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
-            float y[8];
-#pragma unroll
-            for (int t = 0; t < 8; ++t) y[t] = v[8 * q + t] * g[t];
-            pack8_split(y, ohi[q], olo[q]);
-        }
-    } else if (EPI == EPI_L1) {
-        float4 *od = reinterpret_cast<float4 *>(static_cast<float *>(e.out1) + (size_t)m * N + n);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            float a[8], d[8];
-#pragma unroll
-            for (int t = 0; t < 8; ++t) a[t] = act_fast<ACT>(v[8 * q + t] + __ldg(e.bias + n + 8 * q + t), d[t]);
-            pack8_split(a, ohi[q], olo[q]);
-            od[2 * q] = make_float4(d[0], d[1], d[2], d[3]);
-            od[2 * q + 1] = make_float4(d[4], d[5], d[6], d[7]);
-        }
-    } else {  // EPI_L2
-        const float sg = m < e.n_atoms ? e.sigma[min(max(e.species[m], 0), e.n_species - 1)] : 0.0f;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            float dz[8];
-#pragma unroll
-            for (int t = 0; t < 8; ++t) {
-                float d;
-                const int c = n + 8 * q + t;
-                const float a = act_fast<ACT>(v[8 * q + t] + __ldg(e.bias + c), d);
-                const float w = __ldg(e.w3 + c);
-                part = fmaf(a, w, part);
-                dz[t] = sg * w * d;
-            }
-            pack8_split(dz, ohi[q], olo[q]);
-        }
+    for (int i = 0; i < 4; ++i) {
+        const int idx = i * 32 + lane, r = idx >> 2, q = idx & 3;
+        *reinterpret_cast<uint4 *>(out + (size_t)(row0 + r) * ld + col0 + q * 8) = st[r][q];
     }
 }
+// 32 rows x 32 FP32 (128 B a row), staging to global and global to staging
+__device__ __forceinline__ void warp_store_f32(const float4 (*st)[9], float *out, int row0, size_t ld, int col0,
+                                               int lane) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int idx = i * 32 + lane, r = idx >> 3, q = idx & 7;
+        *reinterpret_cast<float4 *>(out + (size_t)(row0 + r) * ld + col0 + q * 4) = st[r][q];
+    }
+}
+__device__ __forceinline__ void warp_load_f32(float4 (*st)[9], const float *in, int row0, size_t ld, int col0,
+                                              int lane) {
+    float4 t[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int idx = i * 32 + lane, r = idx >> 3, q = idx & 7;
+        t[i] = __ldg(reinterpret_cast<const float4 *>(in + (size_t)(row0 + r) * ld + col0 + q * 4));
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int idx = i * 32 + lane, r = idx >> 3, q = idx & 7;
+        st[r][q] = t[i];
+    }
+}
+
+// Epilogue of one row segment of 32 columns starting at column n (multiple of 32); the warp's
+// 32 rows start at row0 and this thread holds row row0 + lane.  BF16 outputs go to [m][n]
+// (hi) and, when e.lo_out, [m][N + n] (lo) of a [M][2N] array.
+template <int EPI, int ACT>
+__device__ __forceinline__ void epilogue32(const EpiArgs &e, int row0, int n, int N, float (&v)[32], float &part,
+                                           EpiStage &sg, int lane) {
+    const int m = row0 + lane;
+    if (EPI == EPI_STORE) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) sg.d[lane][q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        __syncwarp();
+        warp_store_f32(sg.d, static_cast<float *>(e.out0), row0, N, n, lane);
+        __syncwarp();
+        return;
+    }
+    float y[32];
+    if (EPI == EPI_B1) {
+        warp_load_f32(sg.d, static_cast<const float *>(e.aux), row0, N, n, lane);
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const float4 g = sg.d[lane][q];
+            y[4 * q] = v[4 * q] * g.x;
+            y[4 * q + 1] = v[4 * q + 1] * g.y;
+            y[4 * q + 2] = v[4 * q + 2] * g.z;
+            y[4 * q + 3] = v[4 * q + 3] * g.w;
+        }
+    } else if (EPI == EPI_L1) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            float d[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) y[4 * q + t] = act_fast<ACT>(v[4 * q + t] + __ldg(e.bias + n + 4 * q + t), d[t]);
+            sg.d[lane][q] = make_float4(d[0], d[1], d[2], d[3]);
+        }
+    } else {  // EPI_L2
+        const float sg_m = m < e.n_atoms ? e.sigma[min(max(e.species[m], 0), e.n_species - 1)] : 0.0f;
+#pragma unroll
+        for (int t = 0; t < 32; ++t) {
+            float d;
+            const int c = n + t;
+            const float a = act_fast<ACT>(v[t] + __ldg(e.bias + c), d);
+            const float w = __ldg(e.w3 + c);
+            part = fmaf(a, w, part);
+            y[t] = sg_m * w * d;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        uint4 hi, lo;
+        pack8_split(y + 8 * q, hi, lo);
+        sg.hi[lane][q] = hi;
+        sg.lo[lane][q] = lo;
+    }
+    __syncwarp();
+    __nv_bfloat16 *ob = static_cast<__nv_bfloat16 *>(e.out0);
+    warp_store_bf16(sg.hi, ob, row0, 2 * (size_t)N, n, lane);
+    if (e.lo_out) warp_store_bf16(sg.lo, ob + N, row0, 2 * (size_t)N, n, lane);
+    if (EPI == EPI_L1) warp_store_f32(sg.d, static_cast<float *>(e.out1), row0, N, n, lane);
+    __syncwarp();
+}
+
+static_assert(8 * sizeof(EpiStage) <= ring_bytes_for(64), "epilogue staging must fit in the stage ring");
 
 template <int BN, int EPI, int ACT>
 __global__ void __launch_bounds__(256, 1)
@@ -323,14 +378,17 @@ __global__ void __launch_bounds__(256, 1)
     const bool ready = __all_sync(0xffffffffu, mbar_wait(done, 0, abort_flag));
     tc_fence_after();
     if (ready) {
+        // every MMA has completed, so the stage ring is free for the epilogue's staging
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         const int quad = warp & 3, half = warp >> 2;
-        const int m = m0 + quad * 32 + lane;
+        const int row0 = m0 + quad * 32, m = row0 + lane;
+        EpiStage &sg = *reinterpret_cast<EpiStage *>(smem + (size_t)warp * EPI_STAGE_BYTES);
         constexpr int CH = BN / 64;  // 32-column chunks per half
 #pragma unroll 1
         for (int c = half * CH; c < (half + 1) * CH; ++c) {
             float v[32], part = 0.0f;
             tmem_ld_32cols(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(c * 32), v);
-            epilogue32<EPI, ACT>(e, m, n0 + c * 32, N, v, part);
+            epilogue32<EPI, ACT>(e, row0, n0 + c * 32, N, v, part, sg, lane);
             if (EPI == EPI_L2) e.nn_part[(size_t)m * (N / 32) + (n0 + c * 32) / 32] = part;
         }
     } else if (threadIdx.x == 0) {

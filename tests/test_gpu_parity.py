@@ -286,6 +286,23 @@ def test_energy_forces_mixed_precision(cfg, act):
     _ef_parity(b, d, p, precision="mixed")
 
 
+@pytest.mark.parametrize("mask", [14, 15])
+def test_energy_forces_mixed_split_masks(mask):
+    """Other choices of the GEMMs that run the hi/lo split passes (the lo halves of the
+    features and activations are written only where a split GEMM reads them)."""
+    b, d, p = synth.config(1)
+    m, sysd, nl = _nl_pair(b, d, p)
+    mm = _model(d, p, "mixed")
+    mm.set_tuning(split_mask=mask)
+    E, F, _ = mm.energy_forces(sysd, nl)
+    mm.check_status()
+    ref = oracle.energy_forces(b, d, p, oracle.neighbors(b, d["r_cut"]))
+    e = energy_error(E.cpu().numpy(), ref, b)
+    f_rms, f_max = force_error(F.cpu().numpy().astype(np.float64), ref)
+    tol = 2e-4 if mask == 15 else TOL["mixed"]       # all four GEMMs split: close to FP32
+    assert e <= tol and f_rms <= tol and f_max <= ELEMENT_FACTOR * tol, (e, f_rms, f_max)
+
+
 def test_energy_forces_mixed_ragged_li3po4_batch(li_small):
     b, d, p = li_small
     _ef_parity(b, d, p, precision="mixed")
