@@ -12,7 +12,11 @@
 //   #8 (Psi1_s1)_a (Psi3_s2)_abc (Psi2_s3)_bc  all         125  (printed in Eq. contraction)
 //
 // Layout: a block holds 32 atoms (one per lane) and 8 warps; warp w evaluates feature
-// group w for all 32 atoms, so every warp runs one code path.  Groups: 0 = #1-#4,
+// group w for all 32 atoms, so every warp runs one code path.  The forward and backward
+// kernels are capped at 128 registers so that two blocks share an SM: the latency-bound
+// group code gains more from the second block than it loses to the few spills (measured on
+// B300 at 16,384 atoms: backward 105 -> 63 us, forward 39 -> 28 us; three blocks spill too
+// much).  Groups: 0 = #1-#4,
 // 1 = #5, 2 = #6, 3-5 = #7 split by s1 ({0}, {1,4}, {2,3}), 6-7 = #8 split by s2
 // ({0,1}, {2,3,4}).  The 360 features of the 32 atoms are staged in shared memory and
 // written as coalesced rows of the [M][384] GEMM operand (columns 360..383 are zero).
@@ -216,7 +220,7 @@ __device__ __forceinline__ void fwd_group(const T (&P)[NPSI], const FeatOut &gt)
 }
 
 template <typename OutT>
-__global__ void __launch_bounds__(CT_THREADS, 1) k_contract_fwd(const float *__restrict__ psi, int N, int Mp,
+__global__ void __launch_bounds__(CT_THREADS, 2) k_contract_fwd(const float *__restrict__ psi, int N, int Mp,
                                                                 OutT *__restrict__ G, float *__restrict__ G32,
                                                                 int lo_out) {
     extern __shared__ float tile[];
@@ -267,9 +271,11 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_contract_fwd(const float *__r
 }
 
 // ------------------------------------------------------------------ backward groups
-template <int PART, typename T>
-__device__ __forceinline__ void bwd_group(const T (&P)[NPSI], const float *gb, T (&A)[NPSI]) {
-    if (PART == 0) {
+// Backward units: FAM 0 = families #1-#4; FAM 5, 6, 7, 8 = that family restricted by MASK
+// (a bit set per radial index: s1 for #5 and #7, s2 for #6 and #8).
+template <int FAM, int MASK, typename T>
+__device__ __forceinline__ void bwd_unit(const T (&P)[NPSI], const float *gb, T (&A)[NPSI]) {
+    if (FAM == 0) {
 #pragma unroll
         for (int s = 0; s < NR; ++s) A[s * NC] += gb[FAM_OFF1 + s];
 #pragma unroll
@@ -294,11 +300,12 @@ __device__ __forceinline__ void bwd_group(const T (&P)[NPSI], const float *gb, T
                     }
                 }
             }
-    } else if (PART == 1) {
+    } else if (FAM == 5) {
 #pragma unroll
         for (int s1 = 0; s1 < NR; ++s1)
 #pragma unroll
             for (int s2 = s1; s2 < NR; ++s2)
+                if ((MASK >> s1) & 1)
 #pragma unroll
                 for (int s3 = s2; s3 < NR; ++s3) {
                     const float g = gb[FAM_OFF5 + f5_index(s1, s2, s3)];
@@ -318,11 +325,12 @@ __device__ __forceinline__ void bwd_group(const T (&P)[NPSI], const float *gb, T
                             AM(s3, b, a) = mad(g, v3, AM(s3, b, a));
                         }
                 }
-    } else if (PART == 2) {
+    } else if (FAM == 6) {
 #pragma unroll
         for (int s1 = 0; s1 < NR; ++s1)
 #pragma unroll
             for (int s2 = 0; s2 < NR; ++s2)
+                if ((MASK >> s2) & 1)
 #pragma unroll
                 for (int s3 = s1; s3 < NR; ++s3) {
                     const float g = gb[FAM_OFF6 + f6_index(s1, s2, s3)];
@@ -339,10 +347,10 @@ __device__ __forceinline__ void bwd_group(const T (&P)[NPSI], const float *gb, T
                         AV(s3, a) = mad(g, w31, AV(s3, a));
                     }
                 }
-    } else if (PART >= 3 && PART <= 5) {
+    } else if (FAM == 7) {
 #pragma unroll
         for (int s1 = 0; s1 < NR; ++s1) {
-            if (!f7_group_has(PART, s1)) continue;
+            if (!((MASK >> s1) & 1)) continue;
 #pragma unroll
             for (int s2 = s1; s2 < NR; ++s2) {
                 T Mw[3][3], Q[3][3];
@@ -388,7 +396,7 @@ __device__ __forceinline__ void bwd_group(const T (&P)[NPSI], const float *gb, T
     } else {
 #pragma unroll
         for (int s2 = 0; s2 < NR; ++s2) {
-            if (!f8_group_has(PART, s2)) continue;
+            if (!((MASK >> s2) & 1)) continue;
 #pragma unroll
             for (int s3 = 0; s3 < NR; ++s3) {
                 T U[3], Vw[3];
@@ -424,22 +432,56 @@ __device__ __forceinline__ void bwd_group(const T (&P)[NPSI], const float *gb, T
     }
 }
 
+// The eight backward groups of the dual kernel (one warp each), as units.
+template <int PART, typename T>
+__device__ __forceinline__ void bwd_group(const T (&P)[NPSI], const float *gb, T (&A)[NPSI]) {
+    if (PART == 0) bwd_unit<0, 0x1F>(P, gb, A);
+    else if (PART == 1) bwd_unit<5, 0x1F>(P, gb, A);
+    else if (PART == 2) bwd_unit<6, 0x1F>(P, gb, A);
+    else if (PART == 3) bwd_unit<7, 0x01>(P, gb, A);
+    else if (PART == 4) bwd_unit<7, 0x12>(P, gb, A);
+    else if (PART == 5) bwd_unit<7, 0x0C>(P, gb, A);
+    else if (PART == 6) bwd_unit<8, 0x03>(P, gb, A);
+    else bwd_unit<8, 0x1C>(P, gb, A);
+}
+
+// Eight backward warps of balanced work (estimated FMAs per atom in brackets):
+//   #1-#4 + #8 s2=0 [1.7k]; #5 s1 in {0,4} [1.7k]; #5 s1 in {1,2,3} [2.1k]; #6 s2 in {0..3} [2.0k];
+//   #7 s1 in {0,4} [2.0k]; #7 s1=1 + #6 s2=4 [1.8k]; #7 s1 in {2,3} + #8 s2=1 [2.2k]; #8 s2 in {2,3,4} [1.7k]
+// (eight groups by family alone put 3.8k on the #5 warp).  Nine warps do not fit: at this
+// register count one SM sub-partition cannot hold three warps.
+constexpr int CT_BWD_WARPS = 8;
+template <typename T>
+__device__ __forceinline__ void bwd_warp(int warp, const T (&P)[NPSI], const float *gb, T (&A)[NPSI]) {
+    switch (warp) {
+    case 0: bwd_unit<0, 0x1F>(P, gb, A); bwd_unit<8, 0x01>(P, gb, A); break;
+    case 1: bwd_unit<5, 0x11>(P, gb, A); break;
+    case 2: bwd_unit<5, 0x0E>(P, gb, A); break;
+    case 3: bwd_unit<6, 0x0F>(P, gb, A); break;
+    case 4: bwd_unit<7, 0x11>(P, gb, A); break;
+    case 5: bwd_unit<7, 0x02>(P, gb, A); bwd_unit<6, 0x10>(P, gb, A); break;
+    case 6: bwd_unit<7, 0x0C>(P, gb, A); bwd_unit<8, 0x02>(P, gb, A); break;
+    default: bwd_unit<8, 0x1C>(P, gb, A); break;
+    }
+}
+
 // Stage the 360 leading columns of 32 rows of a [.][384] FP32 matrix into shared memory
 // (row stride GT_STRIDE, rows past N zero).  Every thread issues all of its 16-byte loads
 // before the first store, so the block waits for one memory latency instead of one per row.
+template <int NT>
 __device__ __forceinline__ void stage_rows(const float *__restrict__ src, int m0, int N, float *tile) {
-    constexpr int V4 = NF / 4, TOT = CT_ATOMS * V4, PER = (TOT + CT_THREADS - 1) / CT_THREADS;
+    constexpr int V4 = NF / 4, TOT = CT_ATOMS * V4, PER = (TOT + NT - 1) / NT;
     float4 v[PER];
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
-        const int idx = threadIdx.x + u * CT_THREADS;
+        const int idx = threadIdx.x + u * NT;
         const int r = idx / V4, q = idx - r * V4;
         v[u] = (idx < TOT && m0 + r < N) ? __ldg(reinterpret_cast<const float4 *>(src + (size_t)(m0 + r) * NFP) + q)
                                          : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
-        const int idx = threadIdx.x + u * CT_THREADS;
+        const int idx = threadIdx.x + u * NT;
         if (idx < TOT) {
             const int r = idx / V4, q = idx - r * V4;
             float *d = tile + r * GT_STRIDE + 4 * q;
@@ -449,7 +491,7 @@ __device__ __forceinline__ void stage_rows(const float *__restrict__ src, int m0
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(CT_THREADS, 1) k_contract_bwd(const float *__restrict__ psi,
+__global__ void __launch_bounds__(CT_BWD_WARPS * 32, 2) k_contract_bwd(const float *__restrict__ psi,
                                                                 const float *__restrict__ dG, int N,
                                                                 float *__restrict__ dpsi) {
     extern __shared__ float sm[];
@@ -457,31 +499,22 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_contract_bwd(const float *__r
     float *acc = sm + CT_ATOMS * GT_STRIDE;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * CT_ATOMS;
-    stage_rows(dG, m0, N, gtile);
+    stage_rows<CT_BWD_WARPS * 32>(dG, m0, N, gtile);
     float P[NPSI], A[NPSI];
     load_psi(psi, m0 + lane, N, P);
 #pragma unroll
     for (int q = 0; q < NPSI; ++q) A[q] = 0.0f;
     const float *gb = gtile + lane * GT_STRIDE;
-    switch (warp) {
-    case 0: bwd_group<0>(P, gb, A); break;
-    case 1: bwd_group<1>(P, gb, A); break;
-    case 2: bwd_group<2>(P, gb, A); break;
-    case 3: bwd_group<3>(P, gb, A); break;
-    case 4: bwd_group<4>(P, gb, A); break;
-    case 5: bwd_group<5>(P, gb, A); break;
-    case 6: bwd_group<6>(P, gb, A); break;
-    default: bwd_group<7>(P, gb, A); break;
-    }
+    bwd_warp(warp, P, gb, A);
     float *arow = acc + lane * AC_STRIDE;
-    for (int w = 0; w < CT_THREADS / 32; ++w) {
+    for (int w = 0; w < CT_BWD_WARPS; ++w) {
         if (warp == w) {
 #pragma unroll
             for (int q = 0; q < NPSI; ++q) arow[q] = (w == 0 ? 0.0f : arow[q]) + A[q];
         }
         __syncthreads();
     }
-    for (int idx = threadIdx.x; idx < CT_ATOMS * NPSI; idx += CT_THREADS) {
+    for (int idx = threadIdx.x; idx < CT_ATOMS * NPSI; idx += blockDim.x) {
         const int r = idx / NPSI, q = idx - r * NPSI, m = m0 + r;
         if (m < N) dpsi[(size_t)m * NPSI + q] = acc[r * AC_STRIDE + q];
     }
@@ -549,8 +582,8 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_contract_bwd_dual(const float
     float *acc2 = acc1 + CT_ATOMS * AC_STRIDE;         // psidb
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * CT_ATOMS;
-    stage_rows(Gbs, m0, N, gtile);
-    stage_rows(Gbs + (size_t)Mp * NFP, m0, N, gdtile);
+    stage_rows<CT_THREADS>(Gbs, m0, N, gtile);
+    stage_rows<CT_THREADS>(Gbs + (size_t)Mp * NFP, m0, N, gdtile);
     float *arow1 = acc1 + lane * AC_STRIDE, *arow2 = acc2 + lane * AC_STRIDE;
     {   // J^T Gb
         float P[NPSI], A[NPSI];
@@ -676,7 +709,7 @@ void launch_contract_bwd(const float *psi, const float *dG, int N, float *dpsi, 
         attr = true;
     }
     if (blocks > 0) {
-        k_contract_bwd<<<blocks, CT_THREADS, smem, st>>>(psi, dG, N, dpsi);
+        k_contract_bwd<<<blocks, CT_BWD_WARPS * 32, smem, st>>>(psi, dG, N, dpsi);
         note_launches(1);
     }
 }
