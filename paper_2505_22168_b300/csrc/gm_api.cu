@@ -216,6 +216,7 @@ int round_up(int x, int m) { return (x + m - 1) / m * m; }
 struct EfWs {
     float *psi, *dpsi, *G, *A1, *D1, *dZ2, *dZ1, *dG, *nn_part, *vir_atom;
     double *red_part;
+    float4 *pos_hi, *pos_lo;   // hi/lo FP32 split of the positions (pair displacements)
 };
 
 EfWs carve_ef(Carve &c, int B, int N, int H) {
@@ -224,6 +225,8 @@ EfWs carve_ef(Carve &c, int B, int N, int H) {
     const size_t n1 = N > 0 ? (size_t)N : 1, m1 = Mp > 0 ? (size_t)Mp : 1;
     w.psi = c.take<float>(n1 * NPSI);
     w.dpsi = c.take<float>(n1 * NPSI);
+    w.pos_hi = c.take<float4>(n1);
+    w.pos_lo = c.take<float4>(n1);
     w.G = c.take<float>(m1 * NFP);
     w.A1 = c.take<float>(m1 * H);
     w.D1 = c.take<float>(m1 * H);
@@ -245,6 +248,7 @@ size_t ef_workspace_bytes(int B, int N, int H) {
 struct PgWs {
     float *psi, *psid, *psib, *psidb, *GG, *Gbs, *Z, *A1s, *P1, *Q1, *Zd1, *Zb2s, *Zb1s, *Y3, *t_sig, *t_c, *t_cs,
         *beta_part, *wg_part;
+    float4 *pos_hi, *pos_lo;
     __nv_bfloat16 *hl;   // mixed path: hi/lo BF16 copy of the current GEMM's A operand [2 Mp][2 K]
 };
 
@@ -254,6 +258,8 @@ PgWs carve_pg(Carve &c, int N, int H, int S) {
     const size_t n1 = N > 0 ? (size_t)N : 1, m1 = Mp > 0 ? (size_t)Mp : 1;
     w.psi = c.take<float>(n1 * NPSI);
     w.psid = c.take<float>(n1 * NPSI);
+    w.pos_hi = c.take<float4>(n1);
+    w.pos_lo = c.take<float4>(n1);
     w.psib = c.take<float>(n1 * NPSI);
     w.psidb = c.take<float>(n1 * NPSI);
     w.GG = c.take<float>(2 * m1 * NFP);
@@ -308,13 +314,16 @@ gm_status check_nlist(const gm_system *s, const gm_nlist *nl, bool need_pairs) {
     return GM_OK;
 }
 
-PairArgs pair_args(const gm_model *m, const gm_system *s, const gm_nlist *nl, int32_t *status) {
+PairArgs pair_args(const gm_model *m, const gm_system *s, const gm_nlist *nl, const float4 *pos_hi,
+                   const float4 *pos_lo, int32_t *status) {
     PairArgs a;
     a.N = s->n_atoms;
     a.B = s->n_structures;
     a.S = m->S;
     a.atom_ptr = s->atom_ptr;
     a.pos = s->pos;
+    a.pos_hi = pos_hi;
+    a.pos_lo = pos_lo;
     a.species = s->species;
     a.cell = s->cell;
     a.row_ptr = nl->row_ptr;
@@ -492,10 +501,11 @@ static gm_status forward_to_features(const gm_model *m, const gm_system *sys, co
                                      float *psi_out, float *features_out, int32_t *status, cudaStream_t st) {
     const int N = sys->n_atoms;
     const int Mp = round_up(N, TILE_M);
-    PairArgs a = pair_args(m, sys, nl, status);
+    PairArgs a = pair_args(m, sys, nl, w.pos_hi, w.pos_lo, status);
     float *psi = psi_out ? psi_out : w.psi;
     {
         StageScope sc(ST_MOMENTS, st);
+        launch_split_pos(N, sys->pos, w.pos_hi, w.pos_lo, st);
         launch_moments(a, choose_tpa(m, N), psi, st);
     }
     {
@@ -611,7 +621,7 @@ gm_status gm_energy_forces(const gm_model *m, const gm_system *sys, const gm_nli
         }
         if (cudaMemsetAsync(forces, 0, sizeof(float) * 3 * (size_t)N, st) != cudaSuccess)
             return fail(GM_ERR_CUDA, "memset of forces failed");
-        PairArgs a = pair_args(m, sys, nl, status);
+        PairArgs a = pair_args(m, sys, nl, w.pos_hi, w.pos_lo, status);
         StageScope sc(ST_FORCES, st);
         launch_forces(a, choose_tpa(m, N), w.dpsi, forces, virial ? w.vir_atom : nullptr, st);
     }
@@ -653,9 +663,10 @@ gm_status gm_param_grad(const gm_model *m, const gm_system *sys, const gm_nlist 
     if (N == 0) return launch_status();
     const int Mp = round_up(N, TILE_M);
     const int act = m->d.activation;
-    PairArgs a = pair_args(m, sys, nl, status);
+    PairArgs a = pair_args(m, sys, nl, w.pos_hi, w.pos_lo, status);
     {   // primal and tangent moments, features and their tangents
         StageScope sc(ST_PG_PAIR_FWD, st);
+        launch_split_pos(N, sys->pos, w.pos_hi, w.pos_lo, st);
         launch_moments(a, choose_tpa(m, N), w.psi, st);
         launch_moments_tangent(a, dL_dF, w.psid, st);
         launch_contract_fwd_dual(w.psi, w.psid, N, Mp, w.GG, st);

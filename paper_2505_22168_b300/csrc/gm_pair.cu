@@ -2,8 +2,9 @@
 //
 // One group of TPA lanes per centre atom i walks i's CSR row; lanes take every TPA-th
 // neighbour, so a warp covers 32/TPA atoms.  Per pair: the minimum-image displacement
-// d = (r_j - r_i) + n.L is formed in FP64 and rounded to FP32; everything after that
-// (r, rhat, basis, radial functions, monomials) is FP32.
+// d = (r_j - r_i) + n.L is formed to FP64 accuracy (error-free FP32 transforms of hi/lo
+// position splits, see disp_axis) and rounded to FP32; everything after that (r, rhat,
+// basis, radial functions, monomials) is FP32.
 //
 // Moments:  Psi_i[s][c] = sum_j R_s(r_ij) m_c(rhat_ij)  (unique components m_c, see
 //           gm_common.cuh), reduced across the TPA lanes with warp shuffles.
@@ -26,20 +27,31 @@ __device__ __forceinline__ int clamp_species(int z, int S, int32_t *status) {
     return z;
 }
 
-__device__ __forceinline__ void pair_displacement(double xj, double yj, double zj, double xi, double yi, double zi,
-                                                  char4 sh, double Lx, double Ly, double Lz, float &fx, float &fy,
-                                                  float &fz) {
-    fx = (float)((xj - xi) + (double)sh.x * Lx);
-    fy = (float)((yj - yi) + (double)sh.y * Ly);
-    fz = (float)((zj - zi) + (double)sh.z * Lz);
+// One axis of d = (x_j - x_i) + s L from hi/lo FP32 splits of the FP64 operands
+// (x = x_h + x_l, L = L_h + L_l): the large terms are combined with error-free transforms
+// (TwoSum of the hi difference, TwoProduct of s L_h, TwoSum of the two), the small terms are
+// added in FP32, and the sum is rounded once.  The result is the FP32 rounding of the FP64
+// displacement to within one ulp (rounded twice there), at FP32 cost: B300 issues FP64
+// arithmetic at a small fraction of the FP32 rate.
+__device__ __forceinline__ float disp_axis(float xjh, float xjl, float xih, float xil, float s, float Lh, float Ll) {
+    const float h1 = xjh - xih;                       // TwoSum(xjh, -xih)
+    const float b1 = h1 - xjh;
+    const float l1 = (xjh - (h1 - b1)) + (-xih - b1);
+    const float h2 = s * Lh;                          // TwoProduct(s, Lh)
+    const float l2 = fmaf(s, Lh, -h2);
+    const float h3 = h1 + h2;                         // TwoSum(h1, h2)
+    const float b3 = h3 - h1;
+    const float l3 = (h1 - (h3 - b3)) + (h2 - b3);
+    const float lo = ((l1 + l2) + l3) + ((xjl - xil) + s * Ll);
+    return h3 + lo;
 }
 
-// The next neighbour of a row, loaded one iteration ahead (index, shift, FP64 position).
+// The next neighbour of a row, loaded one iteration ahead (index, shift, hi/lo position).
 struct NextPair {
     int j;
     bool ok;
     char4 sh;
-    double x, y, z;
+    float4 ph, pl;
     __device__ __forceinline__ void load(const PairArgs &a, int p, int p1) {
         ok = false;
         if (p < p1) {
@@ -47,15 +59,57 @@ struct NextPair {
             sh = a.shift[p];
             ok = (unsigned)j < (unsigned)a.N;
             if (ok) {
-                x = a.pos[3 * j];
-                y = a.pos[3 * j + 1];
-                z = a.pos[3 * j + 2];
+                ph = a.pos_hi[j];
+                pl = a.pos_lo[j];
             } else {
                 set_status(a.status, GM_ERR_ARG);
             }
         }
     }
 };
+
+// The centre atom's position and its box edges as hi/lo FP32 pairs.
+struct Centre {
+    float4 ph, pl;
+    float Lh[3], Ll[3];
+    __device__ __forceinline__ Centre(const PairArgs &a, int atom, int b) {
+        ph = a.pos_hi[atom];
+        pl = a.pos_lo[atom];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const double L = a.cell[9 * b + 4 * d];
+            Lh[d] = (float)L;
+            Ll[d] = (float)(L - (double)Lh[d]);
+        }
+    }
+    __device__ __forceinline__ void displacement(const NextPair &c, float &fx, float &fy, float &fz) const {
+        fx = disp_axis(c.ph.x, c.pl.x, ph.x, pl.x, (float)c.sh.x, Lh[0], Ll[0]);
+        fy = disp_axis(c.ph.y, c.pl.y, ph.y, pl.y, (float)c.sh.y, Lh[1], Ll[1]);
+        fz = disp_axis(c.ph.z, c.pl.z, ph.z, pl.z, (float)c.sh.z, Lh[2], Ll[2]);
+    }
+};
+
+// hi/lo FP32 split of the FP64 positions (once per atom)
+__global__ void __launch_bounds__(256) k_split_pos(int N, const double *__restrict__ pos, float4 *__restrict__ hi,
+                                                   float4 *__restrict__ lo) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    float h[3], l[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const double x = pos[3 * i + d];
+        h[d] = (float)x;
+        l[d] = (float)(x - (double)h[d]);
+    }
+    hi[i] = make_float4(h[0], h[1], h[2], 0.0f);
+    lo[i] = make_float4(l[0], l[1], l[2], 0.0f);
+}
+
+void launch_split_pos(int N, const double *pos, float4 *hi, float4 *lo, cudaStream_t st) {
+    if (N <= 0) return;
+    k_split_pos<<<(N + 255) / 256, 256, 0, st>>>(N, pos, hi, lo);
+    note_launches(1);
+}
 
 template <int TPA>
 __global__ void __launch_bounds__(256) k_moments(PairArgs a, float *__restrict__ psi) {
@@ -71,8 +125,7 @@ __global__ void __launch_bounds__(256) k_moments(PairArgs a, float *__restrict__
     for (int q = 0; q < NPSI; ++q) acc[q] = 0.0f;
     if (active) {
         const int b = structure_of(a.atom_ptr, a.B, atom);
-        const double Lx = a.cell[9 * b], Ly = a.cell[9 * b + 4], Lz = a.cell[9 * b + 8];
-        const double xi = a.pos[3 * atom], yi = a.pos[3 * atom + 1], zi = a.pos[3 * atom + 2];
+        const Centre ce(a, atom, b);
         const int zsi = clamp_species(a.species[atom], a.S, a.status);
         const float *brow = sbeta + zsi * a.S * (NR * NB);
         const int p1 = a.row_ptr[atom + 1];
@@ -84,7 +137,7 @@ __global__ void __launch_bounds__(256) k_moments(PairArgs a, float *__restrict__
             if (!cur.ok) continue;
             const int j = cur.j;
             float fx, fy, fz;
-            pair_displacement(cur.x, cur.y, cur.z, xi, yi, zi, cur.sh, Lx, Ly, Lz, fx, fy, fz);
+            ce.displacement(cur, fx, fy, fz);
             const float r = sqrtf(fx * fx + fy * fy + fz * fz);
             const float rinv = 1.0f / r;
             float B[NB], dB[NB];
@@ -174,8 +227,7 @@ __global__ void __launch_bounds__(256) k_forces(PairArgs a, const float *__restr
             g[4 * q] = v.x; g[4 * q + 1] = v.y; g[4 * q + 2] = v.z; g[4 * q + 3] = v.w;
         }
         const int b = structure_of(a.atom_ptr, a.B, atom);
-        const double Lx = a.cell[9 * b], Ly = a.cell[9 * b + 4], Lz = a.cell[9 * b + 8];
-        const double xi = a.pos[3 * atom], yi = a.pos[3 * atom + 1], zi = a.pos[3 * atom + 2];
+        const Centre ce(a, atom, b);
         const int zsi = clamp_species(a.species[atom], a.S, a.status);
         const float *brow = sbeta + zsi * a.S * (NR * NB);
         const int p1 = a.row_ptr[atom + 1];
@@ -187,7 +239,7 @@ __global__ void __launch_bounds__(256) k_forces(PairArgs a, const float *__restr
             if (!cur.ok) continue;
             const int j = cur.j;
             float fx, fy, fz;
-            pair_displacement(cur.x, cur.y, cur.z, xi, yi, zi, cur.sh, Lx, Ly, Lz, fx, fy, fz);
+            ce.displacement(cur, fx, fy, fz);
             const float r = sqrtf(fx * fx + fy * fy + fz * fz);
             const float rinv = 1.0f / r;
             const float ux = fx * rinv, uy = fy * rinv, uz = fz * rinv;
@@ -275,8 +327,7 @@ __global__ void __launch_bounds__(256) k_moments_tangent(PairArgs a, const float
     for (int q = 0; q < NPSI; ++q) acc[q] = 0.0f;
     if (active) {
         const int b = structure_of(a.atom_ptr, a.B, atom);
-        const double Lx = a.cell[9 * b], Ly = a.cell[9 * b + 4], Lz = a.cell[9 * b + 8];
-        const double xi = a.pos[3 * atom], yi = a.pos[3 * atom + 1], zi = a.pos[3 * atom + 2];
+        const Centre ce(a, atom, b);
         const float vix = vel[3 * atom], viy = vel[3 * atom + 1], viz = vel[3 * atom + 2];
         const int zsi = clamp_species(a.species[atom], a.S, a.status);
         const float *brow = sbeta + zsi * a.S * (NR * NB);
@@ -289,7 +340,7 @@ __global__ void __launch_bounds__(256) k_moments_tangent(PairArgs a, const float
             if (!cur.ok) continue;
             const int j = cur.j;
             float fx, fy, fz;
-            pair_displacement(cur.x, cur.y, cur.z, xi, yi, zi, cur.sh, Lx, Ly, Lz, fx, fy, fz);
+            ce.displacement(cur, fx, fy, fz);
             const float r = sqrtf(fx * fx + fy * fy + fz * fz);
             const float rinv = 1.0f / r;
             const float ux = fx * rinv, uy = fy * rinv, uz = fz * rinv;
@@ -367,8 +418,7 @@ __global__ void __launch_bounds__(256) k_pg_beta(PairArgs a, const float *__rest
         }
         __syncwarp();
         const int b = structure_of(a.atom_ptr, a.B, atom);
-        const double Lx = a.cell[9 * b], Ly = a.cell[9 * b + 4], Lz = a.cell[9 * b + 8];
-        const double xi = a.pos[3 * atom], yi = a.pos[3 * atom + 1], zi = a.pos[3 * atom + 2];
+        const Centre ce(a, atom, b);
         const float vix = vel[3 * atom], viy = vel[3 * atom + 1], viz = vel[3 * atom + 2];
         const int zsi = clamp_species(a.species[atom], a.S, a.status);
         const int p1 = a.row_ptr[atom + 1];
@@ -380,7 +430,7 @@ __global__ void __launch_bounds__(256) k_pg_beta(PairArgs a, const float *__rest
             if (!cur.ok) continue;
             const int j = cur.j;
             float fx, fy, fz;
-            pair_displacement(cur.x, cur.y, cur.z, xi, yi, zi, cur.sh, Lx, Ly, Lz, fx, fy, fz);
+            ce.displacement(cur, fx, fy, fz);
             const float r = sqrtf(fx * fx + fy * fy + fz * fz);
             const float rinv = 1.0f / r;
             const float ux = fx * rinv, uy = fy * rinv, uz = fz * rinv;

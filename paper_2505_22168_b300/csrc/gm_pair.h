@@ -9,6 +9,7 @@ struct PairArgs {
     int N, B, S;
     const int32_t *atom_ptr;
     const double *pos;
+    const float4 *pos_hi, *pos_lo;   // hi/lo FP32 splits of pos (launch_split_pos)
     const int32_t *species;
     const double *cell;
     const int32_t *row_ptr;
@@ -19,6 +20,8 @@ struct PairArgs {
     int32_t *status;
 };
 
+// pos_hi[i] = (float)pos[i], pos_lo[i] = (float)(pos[i] - pos_hi[i]) per axis (w = 0)
+void launch_split_pos(int N, const double *pos, float4 *hi, float4 *lo, cudaStream_t st);
 void launch_moments(const PairArgs &a, int tpa, float *psi, cudaStream_t st);
 void launch_forces(const PairArgs &a, int tpa, const float *dpsi, float *F, float *vir_atom, cudaStream_t st);
 
