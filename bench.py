@@ -468,32 +468,69 @@ def run_train(args, steps, warmup, precision="fp32"):
 
 # ----------------------------------------------------------------------------- CPU (oracle)
 
-def oracle_step_seconds(cfg, budget_s, max_evals=None):
+def oracle_step_seconds(cfg, budget_s, max_evals=None, keep=False):
     """Time the FP64 oracle (brute-force neighbours + energy/forces) on the workload's
-    structure; repeats until budget_s of CPU time or max_evals evaluations."""
+    structure; repeats until budget_s of CPU time or max_evals evaluations.  With keep, also
+    returns the last evaluation's result."""
     import oracle
     import synth
 
     batch, desc, params = synth.config(cfg)
     oracle.build()
     times = []
+    ref = None
     t_start = time.perf_counter()
     while True:
         t0 = time.perf_counter()
         nl = oracle.neighbors(batch, desc["r_cut"])
-        oracle.energy_forces(batch, desc, params, nl, virial=True)
+        ref = oracle.energy_forces(batch, desc, params, nl, virial=True)
         times.append(time.perf_counter() - t0)
         if time.perf_counter() - t_start >= budget_s or (max_evals and len(times) >= max_evals):
             break
+    if keep:
+        return batch.n_atoms, times, oracle.num_threads(), ref
     return batch.n_atoms, times, oracle.num_threads()
 
 
+def accuracy_vs_oracle(cfg, ref):
+    """Errors of both GPU paths against the oracle's result for the same positions (the
+    metrics of the parity tests: energy per atom relative to the rms atomic energy, force
+    RMS and largest element relative to the rms reference force)."""
+    import torch
+
+    import synth
+    from paper_2505_22168_b300 import GMNN, DeviceSystem
+
+    batch, desc, params = synth.config(cfg)
+    out = {"reference": "FP64 oracle at the workload's base positions"}
+    for prec in ("fp32", "mixed"):
+        if prec == "mixed" and not _mixed_available():
+            continue
+        m = GMNN(desc, params, precision=prec)
+        sysd = DeviceSystem(batch)
+        nl = m.build_neighbors(sysd)
+        E, F, _ = m.energy_forces(sysd, nl)
+        m.check_status()
+        E = E.cpu().numpy()
+        F = F.cpu().numpy().astype(np.float64)
+        ap = batch.atom_ptr
+        e_err = max(abs(E[b] - ref["E"][b]) / (ap[b + 1] - ap[b]) / np.sqrt((ref["E_atom"][ap[b]:ap[b + 1]] ** 2).mean())
+                    for b in range(batch.n_structures) if ap[b + 1] > ap[b])
+        rms = np.sqrt((ref["F"] ** 2).mean())
+        dF = F - ref["F"]
+        out[prec] = {"energy": float(e_err), "force_rms": float(np.sqrt((dF ** 2).mean()) / rms),
+                     "force_max": float(np.abs(dF).max() / rms)}
+        del m
+        torch.cuda.synchronize()
+    return out
+
+
 def cpu_baseline(cfg, budget_s):
-    n, times, threads = oracle_step_seconds(cfg, budget_s)
+    n, times, threads, ref = oracle_step_seconds(cfg, budget_s, keep=True)
     value = n * len(times) / sum(times)
     return {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{len(times)} full evaluations (brute-force neighbours + E/F/virial, FP64) of the "
-                      f"{n}-atom workload, {sum(times):.1f} s on {threads} OpenMP threads"}
+                      f"{n}-atom workload, {sum(times):.1f} s on {threads} OpenMP threads"}, ref
 
 
 # ----------------------------------------------------------------------------- main
@@ -585,8 +622,10 @@ def main():
             variants.append(run_train(args, max(5, args.steps // 5), args.warmup, prec))
 
     cpu = None
+    accuracy = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args.config, args.cpu_seconds)
+        cpu, ref = cpu_baseline(args.config, args.cpu_seconds)
+        accuracy = accuracy_vs_oracle(args.config, ref)
 
     if rank != 0:
         if world > 1:
@@ -604,7 +643,7 @@ def main():
                                    + ("(a second graph with event-record nodes, "
                                       if head["launch_mode"] == "cuda-graph replay" else "(stream launches, ")
                                    + f"{head['ms_per_step_stream_with_stage_events']:.4f} ms/step)"},
-        "roofline": roof, "stage_share": share, "cpu_baseline": cpu, "e2e": head.get("e2e"),
+        "roofline": roof, "stage_share": share, "cpu_baseline": cpu, "accuracy": accuracy, "e2e": head.get("e2e"),
         "gpu_launches": head["launches"], "clocks": clocks, "variants": variants,
     }
     print(json.dumps(line), flush=True)

@@ -498,14 +498,15 @@ gm_status gm_build_neighbors(const gm_model *m, const gm_system *sys, gm_nlist *
 }
 
 static gm_status forward_to_features(const gm_model *m, const gm_system *sys, const gm_nlist *nl, EfWs &w,
-                                     float *psi_out, float *features_out, int32_t *status, cudaStream_t st) {
+                                     float *psi_out, float *features_out, float *forces_to_clear, int32_t *status,
+                                     cudaStream_t st) {
     const int N = sys->n_atoms;
     const int Mp = round_up(N, TILE_M);
     PairArgs a = pair_args(m, sys, nl, w.pos_hi, w.pos_lo, status);
     float *psi = psi_out ? psi_out : w.psi;
     {
         StageScope sc(ST_MOMENTS, st);
-        launch_split_pos(N, sys->pos, w.pos_hi, w.pos_lo, st);
+        launch_split_pos(N, sys->pos, w.pos_hi, w.pos_lo, forces_to_clear, st);
         launch_moments(a, choose_tpa(m, N), psi, st);
     }
     {
@@ -613,14 +614,12 @@ gm_status gm_energy_forces(const gm_model *m, const gm_system *sys, const gm_nli
     cudaStream_t st = stream;
     const int Mp = round_up(N, TILE_M);
     if (N > 0) {
-        if ((s = forward_to_features(m, sys, nl, w, nullptr, nullptr, status, st)) != GM_OK) return s;
+        if ((s = forward_to_features(m, sys, nl, w, nullptr, nullptr, forces, status, st)) != GM_OK) return s;
         if ((s = network_fwd_bwd(m, sys, w, Mp, status, st)) != GM_OK) return s;
         {
             StageScope sc(ST_CONTRACT_BWD, st);
             launch_contract_bwd(w.psi, w.dG, N, w.dpsi, st);
         }
-        if (cudaMemsetAsync(forces, 0, sizeof(float) * 3 * (size_t)N, st) != cudaSuccess)
-            return fail(GM_ERR_CUDA, "memset of forces failed");
         PairArgs a = pair_args(m, sys, nl, w.pos_hi, w.pos_lo, status);
         StageScope sc(ST_FORCES, st);
         launch_forces(a, choose_tpa(m, N), w.dpsi, forces, virial ? w.vir_atom : nullptr, st);
@@ -642,7 +641,7 @@ gm_status gm_descriptors(const gm_model *m, const gm_system *sys, const gm_nlist
     EfWs w = carve_ef(c, sys->n_structures, sys->n_atoms, m->H);
     if (!c.ok) return fail(GM_ERR_WORKSPACE, "workspace too small");
     if (sys->n_atoms == 0) return GM_OK;
-    return forward_to_features(m, sys, nl, w, psi, features, status, stream);
+    return forward_to_features(m, sys, nl, w, psi, features, nullptr, status, stream);
 }
 
 gm_status gm_param_grad(const gm_model *m, const gm_system *sys, const gm_nlist *nl, const double *dL_dE,
@@ -666,7 +665,7 @@ gm_status gm_param_grad(const gm_model *m, const gm_system *sys, const gm_nlist 
     PairArgs a = pair_args(m, sys, nl, w.pos_hi, w.pos_lo, status);
     {   // primal and tangent moments, features and their tangents
         StageScope sc(ST_PG_PAIR_FWD, st);
-        launch_split_pos(N, sys->pos, w.pos_hi, w.pos_lo, st);
+        launch_split_pos(N, sys->pos, w.pos_hi, w.pos_lo, nullptr, st);
         launch_moments(a, choose_tpa(m, N), w.psi, st);
         launch_moments_tangent(a, dL_dF, w.psid, st);
         launch_contract_fwd_dual(w.psi, w.psid, N, Mp, w.GG, st);

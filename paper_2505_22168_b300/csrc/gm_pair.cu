@@ -89,11 +89,17 @@ struct Centre {
     }
 };
 
-// hi/lo FP32 split of the FP64 positions (once per atom)
+// hi/lo FP32 split of the FP64 positions (once per atom); also clears the force array
+// the force kernel accumulates into, when given
 __global__ void __launch_bounds__(256) k_split_pos(int N, const double *__restrict__ pos, float4 *__restrict__ hi,
-                                                   float4 *__restrict__ lo) {
+                                                   float4 *__restrict__ lo, float *__restrict__ zero_F) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
+    if (zero_F) {
+        zero_F[3 * i] = 0.0f;
+        zero_F[3 * i + 1] = 0.0f;
+        zero_F[3 * i + 2] = 0.0f;
+    }
     float h[3], l[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -105,9 +111,9 @@ __global__ void __launch_bounds__(256) k_split_pos(int N, const double *__restri
     lo[i] = make_float4(l[0], l[1], l[2], 0.0f);
 }
 
-void launch_split_pos(int N, const double *pos, float4 *hi, float4 *lo, cudaStream_t st) {
+void launch_split_pos(int N, const double *pos, float4 *hi, float4 *lo, float *zero_F, cudaStream_t st) {
     if (N <= 0) return;
-    k_split_pos<<<(N + 255) / 256, 256, 0, st>>>(N, pos, hi, lo);
+    k_split_pos<<<(N + 255) / 256, 256, 0, st>>>(N, pos, hi, lo, zero_F);
     note_launches(1);
 }
 
