@@ -103,6 +103,7 @@ struct NlArgs {
     uint32_t *slab;         // single-pass search: row i at i * maxn, entries j | shift code << 27
     int maxn;               // slab row length (0: two-pass search, no slab)
     int block_items;        // 1: block-level search items, 0: warp-level
+    int small;              // cooperative launch: grids and short scans computed by every block
     uint8_t *redo;          // 1: row searched again during the compaction
     int32_t *redo_list, *n_redo;
     double *xw;
@@ -247,7 +248,7 @@ __device__ int nl_struct_setup(const NlArgs &a, int b, NlStruct &q) {
 }
 
 // Block 0 builds the per-structure grids and the global cell numbering; every block
-// zeroes its share of the cell histograms.
+// zeroes its share of the scatter slots (the histogram is cleared before the launch).
 __device__ void ph_setup(const NlArgs &a, int bid, int nb) {
     if (bid == 0) {
         int carry = 0;
@@ -268,10 +269,71 @@ __device__ void ph_setup(const NlArgs &a, int bid, int nb) {
             *a.n_redo = 0;
         }
     }
-    for (int c = bid * NL_THREADS + threadIdx.x; c < a.ncmax; c += nb * NL_THREADS) {
-        a.ccount[c] = 0;
-        a.cfill[c] = 0;
+    for (int c = bid * NL_THREADS + threadIdx.x; c < a.ncmax; c += nb * NL_THREADS) a.cfill[c] = 0;
+}
+
+// Small systems: every block derives all per-structure grids itself (shared memory), so
+// binning needs no grid barrier after the setup; block 0 also publishes them.
+static_assert(256 * sizeof(NlStruct) <= NL_WARPS * 512 * (sizeof(float4) + sizeof(unsigned)),
+              "the structures of a small batch must fit in the search's shared memory");
+__device__ void ph_setup_local(const NlArgs &a, int bid, NlStruct *Ss) {
+    int carry = 0;
+    for (int chunk = 0; chunk < a.B; chunk += NL_THREADS) {
+        const int b = chunk + threadIdx.x;
+        NlStruct q;
+        const int ncell = b < a.B ? nl_struct_setup(a, b, q) : 0;
+        int tot;
+        const int pre = block_exclusive_scan(ncell, &tot);
+        if (b < a.B) {
+            q.cell0 = carry + pre;
+            Ss[b] = q;
+            if (bid == 0) a.S[b] = q;
+        }
+        carry += tot;
     }
+    if (bid == 0 && threadIdx.x == 0) {
+        *a.ncells = carry;
+        *a.n_redo = 0;
+    }
+    __syncthreads();
+}
+
+// Exclusive scan of src[0..n) (n <= NL_SCAN_ONE_BLOCK) into shared memory dst[0..n] by every
+// block; block 0 also publishes it (pub[0..n]; n_pairs and the capacity check when given).
+__device__ void ph_scan_local(const int32_t *src, int n, int32_t *dst, int bid, int32_t *pub, int64_t cap,
+                              int64_t *n_pairs, int32_t *status) {
+    int carry = 0;
+    for (int s = 0; s < n; s += NL_SCAN_SUB) {
+        const int base = s + threadIdx.x * 4;
+        int v[4], sum = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[k] = base + k < n ? src[base + k] : 0;
+            sum += v[k];
+        }
+        int tot;
+        int pre = carry + block_exclusive_scan(sum, &tot);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (base + k < n) {
+                dst[base + k] = pre;
+                if (bid == 0) pub[base + k] = pre;
+            }
+            pre += v[k];
+        }
+        carry += tot;
+    }
+    if (threadIdx.x == 0) {
+        dst[n] = carry;
+        if (bid == 0) {
+            pub[n] = carry;
+            if (n_pairs) {
+                *n_pairs = carry;
+                if ((int64_t)carry > cap) set_status(status, GM_ERR_CAPACITY);
+            }
+        }
+    }
+    __syncthreads();
 }
 
 // ------------------------------------------------------------------ bin
@@ -294,7 +356,7 @@ __device__ __forceinline__ double wrap_axis(double x, double L, double invL, int
 
 // Work spread over blocks first: warp w of block bid takes the 32-atom chunks
 // bid + nb (w + 8 k), so a small system occupies many SMs.
-__device__ void ph_bin(const NlArgs &a, int bid, int nb) {
+__device__ void ph_bin(const NlArgs &a, int bid, int nb, const NlStruct *S) {
     const int lane = threadIdx.x & 31;
     for (int ch = bid + nb * (threadIdx.x >> 5); ch * 32 < a.N; ch += nb * NL_WARPS) {
         const int i = ch * 32 + lane;
@@ -302,7 +364,7 @@ __device__ void ph_bin(const NlArgs &a, int bid, int nb) {
         const int b = structure_of(a.atom_ptr, a.B, i);
         const int z = a.species[i];
         if (z < 0 || z >= a.n_species) set_status(a.status, GM_ERR_SPECIES);
-        const NlStruct &q = a.S[b];
+        const NlStruct &q = S[b];
         int ic[3];
         for (int d = 0; d < 3; ++d) {
             const double x = a.pos[3 * i + d];
@@ -400,14 +462,14 @@ __device__ void ph_scan_one(const int32_t *src, int32_t *dst, int n, int bid, in
 }
 
 // ------------------------------------------------------------------ scatter and sort
-__device__ void ph_scatter(const NlArgs &a, int bid, int nb) {
+__device__ void ph_scatter(const NlArgs &a, int bid, int nb, const int32_t *cstart) {
     const int lane = threadIdx.x & 31;
     for (int ch = bid + nb * (threadIdx.x >> 5); ch * 32 < a.N; ch += nb * NL_WARPS) {
         const int i = ch * 32 + lane;
         if (i >= a.N) continue;
         const int c = a.cellid[i];
         const int slot = atomicAdd(a.cfill + c, 1);
-        a.unsorted[a.cstart[c] + slot] = i;
+        a.unsorted[cstart[c] + slot] = i;
     }
 }
 
@@ -458,7 +520,8 @@ __device__ __forceinline__ void store_pair(const NlArgs &a, int pos, int j, int 
 
 // Per-atom search over the full stencil (any K): one warp, 32 candidates of a cell per step.
 template <bool FILL>
-__device__ void search_atom_generic(const NlArgs &a, const NlStruct &q, int c_local, float4 me, int lane) {
+__device__ void search_atom_generic(const NlArgs &a, const NlStruct &q, int c_local, float4 me, int lane,
+                                    int row_start = 0) {
     const int i = __float_as_int(me.w);
     const int ix = c_local % q.nc[0], iy = (c_local / q.nc[0]) % q.nc[1], iz = c_local / (q.nc[0] * q.nc[1]);
     const double rc2 = __dmul_rn(a.rc, a.rc);
@@ -466,7 +529,7 @@ __device__ void search_atom_generic(const NlArgs &a, const NlStruct &q, int c_lo
     const int mi0 = a.mimg[3 * i], mi1 = a.mimg[3 * i + 1], mi2 = a.mimg[3 * i + 2];
     const double xi0 = a.xw[3 * i], xi1 = a.xw[3 * i + 1], xi2 = a.xw[3 * i + 2];
     const unsigned below = (1u << lane) - 1u;
-    int out = FILL ? a.row_ptr[i] : 0;
+    int out = FILL ? row_start : 0;
     int cnt = 0;
     for (int dz = -q.K[2]; dz <= q.K[2]; ++dz) {
         const int vz = iz + dz, nz = floordiv(vz, q.nc[2]), cz = vz - nz * q.nc[2];
@@ -603,7 +666,9 @@ __device__ __forceinline__ void test_chunk(const NlArgs &a, const float4 *home, 
 // Mark row i for the per-atom search during the compaction.
 __device__ __forceinline__ void nl_redo(const NlArgs &a, int i) {
     a.redo[i] = 1;
-    a.redo_list[atomicAdd(a.n_redo, 1)] = i;
+    const int r = atomicAdd(a.n_redo, 1);
+    if (r < a.N) a.redo_list[r] = i;
+    else set_status(a.status, GM_ERR_ARG);
 }
 
 template <int MODE>
@@ -628,7 +693,7 @@ __device__ void ph_search(const NlArgs &a, int bid, int nb, float4 *smem) {
             for (int h = part; h < nh; h += a.split) {
                 const float4 me = a.xs[h0 + h];
                 if (MODE == SM_FILL) {
-                    search_atom_generic<true>(a, q, cl, me, lane);
+                    search_atom_generic<true>(a, q, cl, me, lane, a.row_ptr[__float_as_int(me.w)]);
                 } else {
                     search_atom_generic<false>(a, q, cl, me, lane);
                     if (MODE == SM_SLAB && lane == 0) nl_redo(a, __float_as_int(me.w));
@@ -767,7 +832,7 @@ __device__ void ph_search(const NlArgs &a, int bid, int nb, float4 *smem) {
                 if (MODE == SM_SLAB) {
                     const bool over = hacc > a.maxn || hredo;
                     a.redo[hidx] = over ? 1 : 0;
-                    if (over) a.redo_list[atomicAdd(a.n_redo, 1)] = hidx;
+                    if (over) nl_redo(a, hidx);
                 }
             }
             __syncwarp();                                              // s_home is rewritten next
@@ -850,7 +915,7 @@ __device__ void ph_search_block(const NlArgs &a, int bid, int nb, float4 *smem) 
             for (int h = part + a.split * warp; h < nh; h += a.split * NL_WARPS) {
                 const float4 me = a.xs[h0 + h];
                 if (MODE == SM_FILL) {
-                    search_atom_generic<true>(a, q, cl, me, lane);
+                    search_atom_generic<true>(a, q, cl, me, lane, a.row_ptr[__float_as_int(me.w)]);
                 } else {
                     search_atom_generic<false>(a, q, cl, me, lane);
                     if (MODE == SM_SLAB && lane == 0) nl_redo(a, __float_as_int(me.w));
@@ -950,7 +1015,7 @@ __device__ void ph_search_block(const NlArgs &a, int bid, int nb, float4 *smem) 
                 if (MODE == SM_SLAB) {
                     const bool over = hacc > a.maxn || hredo;
                     a.redo[hidx] = over ? 1 : 0;
-                    if (over) a.redo_list[atomicAdd(a.n_redo, 1)] = hidx;
+                    if (over) nl_redo(a, hidx);
                 }
             }
             __syncwarp();
@@ -965,7 +1030,7 @@ __device__ void ph_search_block(const NlArgs &a, int bid, int nb, float4 *smem) 
 // straight into the CSR row.
 constexpr int NL_COPY_ROWS = 4;
 
-__device__ void ph_compact(const NlArgs &a, int bid, int nb) {
+__device__ void ph_compact(const NlArgs &a, int bid, int nb, const int32_t *row_ptr) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned full = 0xffffffffu;
     if (__shfl_sync(full, lane == 0 ? (int)status_bad(a.status) : 0, 0)) return;
@@ -978,8 +1043,8 @@ __device__ void ph_compact(const NlArgs &a, int bid, int nb) {
             r0[u] = 0;
             cnt[u] = 0;
             if (i < a.N) {
-                r0[u] = a.row_ptr[i];
-                cnt[u] = a.redo[i] ? 0 : a.row_ptr[i + 1] - r0[u];
+                r0[u] = row_ptr[i];
+                cnt[u] = a.redo[i] ? 0 : row_ptr[i + 1] - r0[u];
             }
             kmax = max(kmax, cnt[u]);
         }
@@ -1006,14 +1071,14 @@ __device__ void ph_compact(const NlArgs &a, int bid, int nb) {
                 }
         }
     }
-    const int nredo = *a.n_redo;
+    const int nredo = min(*a.n_redo, a.N);
     for (int r = gw; r < nredo; r += nw) {
         const int i = a.redo_list[r];
         const int c = a.cellid[i];
         const NlStruct &q = a.S[structure_of_cell(a.S, a.B, c)];
         const float4 me = make_float4((float)a.xw[3 * i], (float)a.xw[3 * i + 1], (float)a.xw[3 * i + 2],
                                       __int_as_float(i));
-        search_atom_generic<true>(a, q, c - q.cell0, me, lane);
+        search_atom_generic<true>(a, q, c - q.cell0, me, lane, row_ptr[i]);
     }
 }
 
@@ -1025,11 +1090,11 @@ enum NlPhase { PH_SETUP, PH_BIN, PH_SCAN_CELLS_ONE, PH_SCAN1_CELLS, PH_SCAN2_CEL
 __device__ __forceinline__ void run_phase(const NlArgs &a, int ph, int bid, int nb, float4 *smem) {
     switch (ph) {
     case PH_SETUP: ph_setup(a, bid, nb); break;
-    case PH_BIN: ph_bin(a, bid, nb); break;
+    case PH_BIN: ph_bin(a, bid, nb, a.S); break;
     case PH_SCAN_CELLS_ONE: ph_scan_one(a.ccount, a.cstart, *a.ncells, bid, 0, nullptr, a.status); break;
     case PH_SCAN1_CELLS: ph_scan1(a.ccount, a.cstart, *a.ncells, a.bsum, bid, nb); break;
     case PH_SCAN2_CELLS: ph_scan2(a.cstart, *a.ncells, a.bsum, bid, nb, 0, nullptr, a.status); break;
-    case PH_SCATTER: ph_scatter(a, bid, nb); break;
+    case PH_SCATTER: ph_scatter(a, bid, nb, a.cstart); break;
     case PH_SORT: ph_sort(a, bid, nb); break;
     case PH_COUNT:
         if (a.block_items) {
@@ -1044,7 +1109,7 @@ __device__ __forceinline__ void run_phase(const NlArgs &a, int ph, int bid, int 
     case PH_SCAN1_ROWS: ph_scan1(a.counts, a.row_ptr, a.N, a.bsum, bid, nb); break;
     case PH_SCAN2_ROWS: ph_scan2(a.row_ptr, a.N, a.bsum, bid, nb, a.cap, a.n_pairs, a.status); break;
     default:
-        if (a.maxn > 0) ph_compact(a, bid, nb);
+        if (a.maxn > 0) ph_compact(a, bid, nb, a.row_ptr);
         else if (a.block_items) ph_search_block<SM_FILL>(a, bid, nb, smem);
         else ph_search<SM_FILL>(a, bid, nb, smem);
         break;
@@ -1056,6 +1121,32 @@ __device__ __forceinline__ void run_phase(const NlArgs &a, int ph, int bid, int 
 __global__ void __launch_bounds__(NL_THREADS, 2) k_nl_coop(NlArgs a) {
     extern __shared__ float4 nl_smem[];
     const int bid = blockIdx.x, nb = gridDim.x;
+    if (a.small) {
+        // four barriers: every block sets up the grids and scans the short arrays itself
+        NlStruct *Ss = reinterpret_cast<NlStruct *>(nl_smem);
+        int32_t *si = reinterpret_cast<int32_t *>(nl_smem);
+        ph_setup_local(a, bid, Ss);
+        for (int c = bid * NL_THREADS + threadIdx.x; c < a.ncmax; c += nb * NL_THREADS) a.cfill[c] = 0;
+        ph_bin(a, bid, nb, Ss);
+        if (!nl_grid_sync(a.bar, a.status)) return;
+        const int ncells = *a.ncells;
+        ph_scan_local(a.ccount, ncells, si, bid, a.cstart, 0, nullptr, a.status);
+        ph_scatter(a, bid, nb, si);
+        if (!nl_grid_sync(a.bar, a.status)) return;
+        run_phase(a, PH_SORT, bid, nb, nl_smem);
+        if (!nl_grid_sync(a.bar, a.status)) return;
+        run_phase(a, PH_COUNT, bid, nb, nl_smem);
+        if (!nl_grid_sync(a.bar, a.status)) return;
+        ph_scan_local(a.counts, a.N, si, bid, a.row_ptr, a.cap, a.n_pairs, a.status);
+        if ((int64_t)si[a.N] > a.cap) return;
+        if (a.maxn > 0) {
+            ph_compact(a, bid, nb, si);
+        } else {
+            if (!nl_grid_sync(a.bar, a.status)) return;        // the fill reads the published rows
+            ph_search<SM_FILL>(a, bid, nb, nl_smem);
+        }
+        return;
+    }
     run_phase(a, PH_SETUP, bid, nb, nl_smem);
     if (!nl_grid_sync(a.bar, a.status)) return;
     run_phase(a, PH_BIN, bid, nb, nl_smem);
@@ -1108,11 +1199,12 @@ static NlWs carve_nl(Carve &c, int B, int N) {
     const size_t n1 = N > 0 ? (size_t)N : 1;
     w.S = c.take<NlStruct>(B);
     w.ncells = c.take<int32_t>(1);
-    w.bar = c.take<unsigned>(2);
+
     w.xw = c.take<double>(3 * n1);
     w.mimg = c.take<int32_t>(3 * n1);
     w.cellid = c.take<int32_t>(n1);
-    w.ccount = c.take<int32_t>(ncmax);
+    w.ccount = c.take<int32_t>(ncmax + 64);                        // histogram, then the barrier words
+    w.bar = reinterpret_cast<unsigned *>(w.ccount + ncmax + 32);
     w.cstart = c.take<int32_t>(ncmax + 1);
     w.cfill = c.take<int32_t>(ncmax);
     w.unsorted = c.take<int32_t>(n1);
@@ -1236,13 +1328,16 @@ gm_status nl_build(const gm_system &sys, double r_cut, int n_species, gm_nlist &
 
     NlDevice &dev = nl_device();
     const int ncmax = N + B;
+    // cell histogram and barrier words start at zero
+    if (cudaMemsetAsync(w.ccount, 0, sizeof(int32_t) * ((size_t)ncmax + 64), st) != cudaSuccess) return GM_ERR_CUDA;
+    a.small = (N + B <= NL_SCAN_ONE_BLOCK && B <= 256) ? 1 : 0;
     auto clampi = [](long long v, long long lo, long long hi) { return (int)(v < lo ? lo : (v > hi ? hi : v)); };
     if (tune.mode != GM_NL_MODE_PHASES && dev.coop_blocks > 0) {
         // one cooperative launch, at most as many blocks as are co-resident
         const long long want = tune.blocks > 0 ? tune.blocks : 2LL * dev.sms;
         const int grid = clampi(want, 1, dev.coop_blocks < NL_MAX_BLOCKS ? dev.coop_blocks : NL_MAX_BLOCKS);
         StageScope sc(ST_NL_COOP, st);
-        if (cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), st) != cudaSuccess) return GM_ERR_CUDA;
+
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(grid);
         cfg.blockDim = dim3(NL_THREADS);
