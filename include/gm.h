@@ -142,6 +142,9 @@ GM_API void gm_model_destroy(gm_model *m);
  *                       4 and 8 the two backward GEMMs; default 12 (backward GEMMs), which
  *                       keeps forces within 2e-3 of the FP64 result
  *   GM_TUNE_GEMM_BN     mixed path: tensor-core tile width 64, 128 or 256 (0 = by size)
+ *   GM_TUNE_GEMM_CPS    mixed path: tensor-core GEMM blocks resident per SM, 1 or 2 (two halve
+ *                       the operand ring and overlap one block's epilogue with the other's
+ *                       main loop; 0 = two when the tiles fill the GPU twice)
  *   GM_TUNE_NL_MODE     neighbour build as one cooperative launch (GM_NL_MODE_AUTO, the
  *                       default when the device supports it) or one launch per phase
  *                       (GM_NL_MODE_PHASES)
@@ -154,7 +157,7 @@ GM_API void gm_model_destroy(gm_model *m);
  *                       block with shared staging, 2 = one per warp
  * Errors: GM_ERR_ARG for an unknown key or value. */
 enum { GM_TUNE_PAIR_TPA = 0, GM_TUNE_SPLIT_MASK = 1, GM_TUNE_GEMM_BN = 2, GM_TUNE_NL_MODE = 3, GM_TUNE_NL_SPLIT = 4,
-       GM_TUNE_NL_BLOCKS = 5, GM_TUNE_NL_TWO_PASS = 6, GM_TUNE_NL_ITEMS = 7 };
+       GM_TUNE_NL_BLOCKS = 5, GM_TUNE_NL_TWO_PASS = 6, GM_TUNE_NL_ITEMS = 7, GM_TUNE_GEMM_CPS = 8 };
 enum { GM_NL_MODE_AUTO = 0, GM_NL_MODE_PHASES = 1 };
 GM_API gm_status gm_model_set_tuning(gm_model *m, int32_t key, int32_t value);
 

@@ -22,6 +22,7 @@ SPACE = {
     "nl_split": (0, 1, 2, 4, 8, 16),
     "pair_tpa": (0, 4, 8, 16, 32),
     "gemm_bn": (0, 64, 128, 256),
+    "gemm_cps": (0, 1, 2),
 }
 
 
@@ -60,6 +61,7 @@ def tune(model, sysd, nl, out, reps=20, cache: str | os.PathLike | None = None, 
     space = dict(SPACE if space is None else space)
     if model.precision != "mixed":
         space.pop("gemm_bn", None)            # the FP32 path has no tensor-core tiles
+        space.pop("gemm_cps", None)
     if timer is None:
         def timer(m):
             return time_step(m, sysd, nl, out, reps)

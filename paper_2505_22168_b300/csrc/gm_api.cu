@@ -112,6 +112,7 @@ struct gm_model {
     __nv_bfloat16 *W1t_h, *W1p_h, *W2t_h, *W2_h;   // BF16 hi/lo pairs, rows [hi(K) | lo(K)]
     int split_mask;        // GEMMs run with three hi/lo passes: 1 L1, 2 L2, 4 B1, 8 B0
     int gemm_bn;           // tensor-core tile width (0 = by size)
+    int gemm_cps;          // tensor-core GEMM blocks per SM (0 = by tile count)
     NlTuning nl;           // neighbour build launch shape
     float *b1, *b2, *w3, *b3, *sigma, *mu;
 };
@@ -387,6 +388,7 @@ gm_status gm_model_create(const gm_model_desc *d, gm_model **out) {
     m->pair_tpa = 0;
     m->split_mask = 12;
     m->gemm_bn = 0;
+    m->gemm_cps = 0;
     m->nl = NlTuning();
     Layout L = model_layout(m->S, m->H);
     m->buf_bytes = L.total;
@@ -439,6 +441,10 @@ gm_status gm_model_set_tuning(gm_model *m, int32_t key, int32_t value) {
     case GM_TUNE_GEMM_BN:
         if (value != 0 && value != 64 && value != 128 && value != 256) return fail(GM_ERR_ARG, "bad GEMM tile width");
         m->gemm_bn = value;
+        return GM_OK;
+    case GM_TUNE_GEMM_CPS:
+        if (value < 0 || value > 2) return fail(GM_ERR_ARG, "GEMM blocks per SM must be 0, 1 or 2");
+        m->gemm_cps = value;
         return GM_OK;
     case GM_TUNE_NL_MODE:
         if (value != GM_NL_MODE_AUTO && value != GM_NL_MODE_PHASES) return fail(GM_ERR_ARG, "bad neighbour mode");
@@ -545,7 +551,7 @@ static gm_status network_fwd_bwd(const gm_model *m, const gm_system *sys, EfWs &
         e.lo_out = (sp & 2) != 0;   // lo halves only where the consuming GEMM runs split
         {
             StageScope sc(ST_GEMM_L1, st);
-            if ((s = gemm_bf16(EPI_L1, m->d.activation, G, m->W1t_h, Mp, H, NFP, (sp & 1) != 0, e, status, st, m->gemm_bn)) != GM_OK)
+            if ((s = gemm_bf16(EPI_L1, m->d.activation, G, m->W1t_h, Mp, H, NFP, (sp & 1) != 0, e, status, st, m->gemm_bn, m->gemm_cps)) != GM_OK)
                 return fail(s, "tcgen05 GEMM L1 failed");
         }
         e.bias = m->b2;
@@ -554,7 +560,7 @@ static gm_status network_fwd_bwd(const gm_model *m, const gm_system *sys, EfWs &
         e.lo_out = (sp & 4) != 0;
         {
             StageScope sc(ST_GEMM_L2, st);
-            if ((s = gemm_bf16(EPI_L2, m->d.activation, A1, m->W2t_h, Mp, H, H, (sp & 2) != 0, e, status, st, m->gemm_bn)) != GM_OK)
+            if ((s = gemm_bf16(EPI_L2, m->d.activation, A1, m->W2t_h, Mp, H, H, (sp & 2) != 0, e, status, st, m->gemm_bn, m->gemm_cps)) != GM_OK)
                 return fail(s, "tcgen05 GEMM L2 failed");
         }
         e.out0 = dZ1;
@@ -562,13 +568,13 @@ static gm_status network_fwd_bwd(const gm_model *m, const gm_system *sys, EfWs &
         e.lo_out = (sp & 8) != 0;
         {
             StageScope sc(ST_GEMM_B1, st);
-            if ((s = gemm_bf16(EPI_B1, 0, dZ2, m->W2_h, Mp, H, H, (sp & 4) != 0, e, status, st, m->gemm_bn)) != GM_OK)
+            if ((s = gemm_bf16(EPI_B1, 0, dZ2, m->W2_h, Mp, H, H, (sp & 4) != 0, e, status, st, m->gemm_bn, m->gemm_cps)) != GM_OK)
                 return fail(s, "tcgen05 GEMM B1 failed");
         }
         e.out0 = w.dG;
         {
             StageScope sc(ST_GEMM_B0, st);
-            if ((s = gemm_bf16(EPI_STORE, 0, dZ1, m->W1p_h, Mp, NFP, H, (sp & 8) != 0, e, status, st, m->gemm_bn)) != GM_OK)
+            if ((s = gemm_bf16(EPI_STORE, 0, dZ1, m->W1p_h, Mp, NFP, H, (sp & 8) != 0, e, status, st, m->gemm_bn, m->gemm_cps)) != GM_OK)
                 return fail(s, "tcgen05 GEMM B0 failed");
         }
         return GM_OK;
@@ -686,7 +692,7 @@ gm_status gm_param_grad(const gm_model *m, const gm_system *sys, const gm_nlist 
             }
             split_bf16(A, 2 * Mp, K_, w.hl, st);
             return gemm_bf16(EPI_STORE, 0, w.hl, Bh, 2 * Mp, N_, K_, ((sp >> which) & 1) != 0, e, status, st,
-                             m->gemm_bn);
+                             m->gemm_bn, m->gemm_cps);
         };
         gm_status gs;
         if ((gs = mm(0, w.GG, m->W1t, m->W1t_h, H, NFP, w.Z)) != GM_OK) return fail(gs, "network GEMM 1 failed");

@@ -42,8 +42,10 @@ void gemm_f32(int epi, int act, const float *A, const float *B, int M, int N, in
 // B [N][2K] BF16 hi/lo pairs with 16-byte aligned rows.  L1/L2/B1 outputs are BF16 hi/lo
 // pairs [M][2N] (D1 FP32 [M][N]), STORE is FP32 [M][N].
 // forced_bn = 0 picks the tile width from the problem size (64, 128 or 256 columns).
+// forced_cps = 0 picks one or two CTAs per SM from the tile count (two halve the stage ring
+// and overlap one CTA's epilogue with the other's main loop).
 gm_status gemm_bf16(int epi, int act, const __nv_bfloat16 *A, const __nv_bfloat16 *B, int M, int N, int K, int split,
-                    const EpiArgs &e, int32_t *status, cudaStream_t st, int forced_bn = 0);
+                    const EpiArgs &e, int32_t *status, cudaStream_t st, int forced_bn = 0, int forced_cps = 0);
 int tc_choose_bn(int M, int N, int forced);
 
 }  // namespace gm

@@ -55,35 +55,42 @@ bool tensor_map(const void *base, int inner, int rows, int box_rows, CUtensorMap
     return true;
 }
 
-template <int BN, int EPI, int ACT>
+template <int BN, int EPI, int ACT, int CPS>
 cudaError_t launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, int M, int N, int K, int split,
                       const EpiArgs &e, int32_t *status, cudaStream_t st) {
     static bool attr_set = false;
-    const size_t smem = tc::smem_bytes_for(BN);
+    const size_t smem = tc::smem_bytes_for(BN, CPS);
     if (!attr_set) {
-        cudaError_t err = cudaFuncSetAttribute(tc::k_gemm_tc<BN, EPI, ACT>,
+        cudaError_t err = cudaFuncSetAttribute(tc::k_gemm_tc<BN, EPI, ACT, CPS>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return err;
         attr_set = true;
     }
     dim3 grid(M / tc::BM, N / BN);
-    tc::k_gemm_tc<BN, EPI, ACT><<<grid, 256, smem, st>>>(ma, mb, M, N, K, split, e, status);
+    tc::k_gemm_tc<BN, EPI, ACT, CPS><<<grid, 256, smem, st>>>(ma, mb, M, N, K, split, e, status);
     return cudaPeekAtLastError();
 }
 
-template <int BN>
+template <int BN, int CPS>
 cudaError_t dispatch_epi(int epi, int act, const CUtensorMap &ma, const CUtensorMap &mb, int M, int N, int K,
                          int split, const EpiArgs &e, int32_t *status, cudaStream_t st) {
     switch (epi) {
     case EPI_L1:
-        return act == 0 ? launch_tc<BN, EPI_L1, 0>(ma, mb, M, N, K, split, e, status, st)
-                        : launch_tc<BN, EPI_L1, 1>(ma, mb, M, N, K, split, e, status, st);
+        return act == 0 ? launch_tc<BN, EPI_L1, 0, CPS>(ma, mb, M, N, K, split, e, status, st)
+                        : launch_tc<BN, EPI_L1, 1, CPS>(ma, mb, M, N, K, split, e, status, st);
     case EPI_L2:
-        return act == 0 ? launch_tc<BN, EPI_L2, 0>(ma, mb, M, N, K, split, e, status, st)
-                        : launch_tc<BN, EPI_L2, 1>(ma, mb, M, N, K, split, e, status, st);
-    case EPI_B1: return launch_tc<BN, EPI_B1, 0>(ma, mb, M, N, K, split, e, status, st);
-    default: return launch_tc<BN, EPI_STORE, 0>(ma, mb, M, N, K, split, e, status, st);
+        return act == 0 ? launch_tc<BN, EPI_L2, 0, CPS>(ma, mb, M, N, K, split, e, status, st)
+                        : launch_tc<BN, EPI_L2, 1, CPS>(ma, mb, M, N, K, split, e, status, st);
+    case EPI_B1: return launch_tc<BN, EPI_B1, 0, CPS>(ma, mb, M, N, K, split, e, status, st);
+    default: return launch_tc<BN, EPI_STORE, 0, CPS>(ma, mb, M, N, K, split, e, status, st);
     }
+}
+
+template <int BN>
+cudaError_t dispatch_cps(int cps, int epi, int act, const CUtensorMap &ma, const CUtensorMap &mb, int M, int N,
+                         int K, int split, const EpiArgs &e, int32_t *status, cudaStream_t st) {
+    return cps == 2 ? dispatch_epi<BN, 2>(epi, act, ma, mb, M, N, K, split, e, status, st)
+                    : dispatch_epi<BN, 1>(epi, act, ma, mb, M, N, K, split, e, status, st);
 }
 
 }  // namespace
@@ -97,19 +104,27 @@ int tc_choose_bn(int M, int N, int forced) {
     return 64;
 }
 
+// CTAs per SM: two (halved stage ring) once there are enough tiles to fill the GPU twice
+int tc_choose_cps(int M, int N, int bn, int forced) {
+    if (forced == 1 || forced == 2) return forced;
+    const long long tiles = (long long)(M / tc::BM) * (N / bn);
+    return tiles >= 2 * 148 ? 2 : 1;
+}
+
 gm_status gemm_bf16(int epi, int act, const __nv_bfloat16 *A, const __nv_bfloat16 *B, int M, int N, int K, int split,
-                    const EpiArgs &e, int32_t *status, cudaStream_t st, int forced_bn) {
+                    const EpiArgs &e, int32_t *status, cudaStream_t st, int forced_bn, int forced_cps) {
     if (M <= 0) return GM_OK;
     if (M % tc::BM || K % tc::BK || N % 64) return GM_ERR_UNSUPPORTED;
     const int bn = tc_choose_bn(M, N, forced_bn);
+    const int cps = tc_choose_cps(M, N, bn, forced_cps);
     CUtensorMap ma, mb;
     // operands are [rows][2K] hi/lo pairs
     if (!tensor_map(A, 2 * K, M, tc::BM, &ma) || !tensor_map(B, 2 * K, N, bn, &mb)) return GM_ERR_CUDA;
     cudaError_t err;
     switch (bn) {
-    case 256: err = dispatch_epi<256>(epi, act, ma, mb, M, N, K, split, e, status, st); break;
-    case 128: err = dispatch_epi<128>(epi, act, ma, mb, M, N, K, split, e, status, st); break;
-    default: err = dispatch_epi<64>(epi, act, ma, mb, M, N, K, split, e, status, st); break;
+    case 256: err = dispatch_cps<256>(cps, epi, act, ma, mb, M, N, K, split, e, status, st); break;
+    case 128: err = dispatch_cps<128>(cps, epi, act, ma, mb, M, N, K, split, e, status, st); break;
+    default: err = dispatch_cps<64>(cps, epi, act, ma, mb, M, N, K, split, e, status, st); break;
     }
     note_launches(1);
     return err == cudaSuccess ? GM_OK : GM_ERR_CUDA;

@@ -26,11 +26,17 @@ constexpr int BK = 64;                      // BF16 elements per 128-byte swizzl
 constexpr int A_STAGE_BYTES = BM * BK * 2;  // 16 KiB
 constexpr uint64_t WAIT_NS = 1000000000ull; // bound of every wait
 
-__host__ __device__ constexpr int stages_for(int bn) { return bn >= 256 ? 4 : 6; }
+// stage ring: about 192 KB for one CTA per SM, about 96 KB when two CTAs share an SM (one
+// CTA's epilogue then overlaps the other's main loop)
+__host__ __device__ constexpr int stages_for(int bn, int cps = 1) {
+    return cps == 1 ? (bn >= 256 ? 4 : 6) : (bn >= 256 ? 2 : (bn >= 128 ? 3 : 4));
+}
 __host__ __device__ constexpr int tmem_cols_for(int bn) { return bn <= 32 ? 32 : (bn <= 64 ? 64 : (bn <= 128 ? 128 : 256)); }
-__host__ __device__ constexpr size_t ring_bytes_for(int bn) { return (size_t)stages_for(bn) * (A_STAGE_BYTES + bn * BK * 2); }
-__host__ __device__ constexpr size_t smem_bytes_for(int bn) {
-    return (size_t)stages_for(bn) * (A_STAGE_BYTES + bn * BK * 2) + 1024 + 256;
+__host__ __device__ constexpr size_t ring_bytes_for(int bn, int cps = 1) {
+    return (size_t)stages_for(bn, cps) * (A_STAGE_BYTES + bn * BK * 2);
+}
+__host__ __device__ constexpr size_t smem_bytes_for(int bn, int cps = 1) {
+    return ring_bytes_for(bn, cps) + 1024 + 256;
 }
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -284,13 +290,14 @@ __device__ __forceinline__ void epilogue32(const EpiArgs &e, int row0, int n, in
     __syncwarp();
 }
 
-static_assert(8 * sizeof(EpiStage) <= ring_bytes_for(64), "epilogue staging must fit in the stage ring");
+static_assert(8 * sizeof(EpiStage) <= ring_bytes_for(64, 2) && 8 * sizeof(EpiStage) <= ring_bytes_for(256, 2),
+              "epilogue staging must fit in the stage ring");
 
-template <int BN, int EPI, int ACT>
-__global__ void __launch_bounds__(256, 1)
+template <int BN, int EPI, int ACT, int CPS>
+__global__ void __launch_bounds__(256, CPS)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N, int K,
               int split, EpiArgs e, int32_t *status) {
-    constexpr int STAGES = stages_for(BN);
+    constexpr int STAGES = stages_for(BN, CPS);
     constexpr int B_STAGE_BYTES = BN * BK * 2;
     constexpr int STAGE_BYTES = A_STAGE_BYTES + B_STAGE_BYTES;
     constexpr uint32_t TMEM_COLS = tmem_cols_for(BN);

@@ -303,6 +303,29 @@ def test_energy_forces_mixed_split_masks(mask):
     assert e <= tol and f_rms <= tol and f_max <= ELEMENT_FACTOR * tol, (e, f_rms, f_max)
 
 
+@pytest.mark.parametrize("bn", [64, 128, 256])
+def test_mixed_gemm_blocks_per_sm_give_identical_results(bn):
+    """One or two tensor-core GEMM blocks per SM (a full or a halved operand ring) compute each
+    output tile the same way: energies agree bit for bit, forces up to the order of their FP32
+    atomic sums, and both are within the mixed tolerance of the oracle."""
+    b, d, p = synth.config(2)
+    _, sysd, nl = _nl_pair(b, d, p)
+    ref = oracle.energy_forces(b, d, p, oracle.neighbors(b, d["r_cut"]))
+    outs = []
+    for cps in (1, 2):
+        mm = _model(d, p, "mixed")
+        mm.set_tuning(gemm_bn=bn, gemm_cps=cps)
+        E, F, _ = mm.energy_forces(sysd, nl)
+        mm.check_status()
+        outs.append((E.cpu().numpy(), F.cpu().numpy()))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.abs(outs[0][1] - outs[1][1]).max() <= 1e-5 * np.abs(outs[0][1]).max()
+    e = energy_error(outs[1][0], ref, b)
+    f_rms, f_max = force_error(outs[1][1].astype(np.float64), ref)
+    tol = TOL["mixed"]
+    assert e <= tol and f_rms <= tol and f_max <= ELEMENT_FACTOR * tol, (e, f_rms, f_max)
+
+
 def test_energy_forces_mixed_ragged_li3po4_batch(li_small):
     b, d, p = li_small
     _ef_parity(b, d, p, precision="mixed")
