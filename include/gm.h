@@ -75,6 +75,11 @@ typedef enum {
                           accumulation; everything else as GM_PREC_FP32 */
 } gm_precision;
 
+/* Largest system (all structures of a batch together) one call takes: the network GEMMs of
+ * the parameter gradient stack two rows per atom in tiles of 128 rows, and a launch grid
+ * has at most 65535 rows of tiles. */
+#define GM_MAX_ATOMS 4000000
+
 typedef struct {
     int32_t n_species;  /* S, 1..16 */
     int32_t n_basis;    /* radial basis functions (7) */
@@ -91,7 +96,7 @@ typedef struct gm_model gm_model; /* opaque */
 /* A batch of B periodic structures, N atoms in total (ragged, no padding). */
 typedef struct {
     int32_t n_structures;     /* B >= 1 */
-    int32_t n_atoms;          /* N >= 0 */
+    int32_t n_atoms;          /* 0 <= N <= GM_MAX_ATOMS, else GM_ERR_UNSUPPORTED */
     const int32_t *atom_ptr;  /* device [B+1]; structure b owns atoms atom_ptr[b]..atom_ptr[b+1]-1 */
     const double *pos;        /* device [N][3] Cartesian positions (any image) */
     const int32_t *species;   /* device [N], 0 <= species < n_species */

@@ -16,6 +16,7 @@ GM_OK, GM_ERR_ARG, GM_ERR_CAPACITY, GM_ERR_UNSUPPORTED, GM_ERR_CUDA, GM_ERR_TIME
 GM_ACT_TANH, GM_ACT_SILU = 0, 1
 GM_PREC_FP32, GM_PREC_MIXED = 0, 1
 GM_OP_NEIGHBORS, GM_OP_ENERGY_FORCES, GM_OP_PARAM_GRAD = 0, 1, 2
+GM_MAX_ATOMS = 4_000_000
 MIXED_AVAILABLE = True   # GM_PREC_MIXED: BF16 network GEMMs on tcgen05
 
 STATUS_NAMES = {0: "GM_OK", 1: "GM_ERR_ARG", 2: "GM_ERR_CAPACITY", 3: "GM_ERR_UNSUPPORTED", 4: "GM_ERR_CUDA",

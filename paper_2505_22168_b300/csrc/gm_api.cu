@@ -297,6 +297,7 @@ bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) %
 gm_status check_system(const gm_model *m, const gm_system *s) {
     if (!m || !s) return fail(GM_ERR_ARG, "null model or system");
     if (s->n_structures < 1 || s->n_atoms < 0) return fail(GM_ERR_ARG, "n_structures must be >= 1 and n_atoms >= 0");
+    if (s->n_atoms > GM_MAX_ATOMS) return fail(GM_ERR_UNSUPPORTED, "more than GM_MAX_ATOMS atoms");
     if (!s->atom_ptr || !s->cell || !s->pbc) return fail(GM_ERR_ARG, "atom_ptr, cell and pbc must be non-null");
     if (s->n_atoms > 0 && (!s->pos || !s->species)) return fail(GM_ERR_ARG, "pos and species must be non-null");
     if (!aligned(s->pos, 8) || !aligned(s->cell, 8) || !aligned(s->atom_ptr, 4) || !aligned(s->species, 4))

@@ -15,7 +15,8 @@ __global__ void __launch_bounds__(256) k_gemm_f32(const float *__restrict__ A, c
     __shared__ __align__(16) float As[2][SB_K][SB_M + 4];
     __shared__ __align__(16) float Bs[2][SB_K][SB_N + 4];
     const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-    const int m0 = blockIdx.x * SB_M, n0 = blockIdx.y * SB_N;
+    // the N tiles of one row block are consecutive blocks, so the A rows come from DRAM once
+    const int m0 = blockIdx.y * SB_M, n0 = blockIdx.x * SB_N;
     float acc[8][4];
 #pragma unroll
     for (int i = 0; i < 8; ++i)
@@ -112,7 +113,7 @@ static void launch_act(int act, dim3 g, const float *A, const float *B, int M, i
 void gemm_f32(int epi, int act, const float *A, const float *B, int M, int N, int K, const EpiArgs &e,
               cudaStream_t st) {
     if (M <= 0) return;
-    dim3 g(M / SB_M, N / SB_N);
+    dim3 g(N / SB_N, M / SB_M);
     note_launches(1);
     switch (epi) {
     case EPI_L1: launch_act<EPI_L1>(act, g, A, B, M, N, K, e, st); break;

@@ -66,7 +66,7 @@ cudaError_t launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, int M, int N
         if (err != cudaSuccess) return err;
         attr_set = true;
     }
-    dim3 grid(M / tc::BM, N / BN);
+    dim3 grid(N / BN, M / tc::BM);
     tc::k_gemm_tc<BN, EPI, ACT, CPS><<<grid, 256, smem, st>>>(ma, mb, M, N, K, split, e, status);
     return cudaPeekAtLastError();
 }
@@ -114,7 +114,7 @@ int tc_choose_cps(int M, int N, int bn, int forced) {
 gm_status gemm_bf16(int epi, int act, const __nv_bfloat16 *A, const __nv_bfloat16 *B, int M, int N, int K, int split,
                     const EpiArgs &e, int32_t *status, cudaStream_t st, int forced_bn, int forced_cps) {
     if (M <= 0) return GM_OK;
-    if (M % tc::BM || K % tc::BK || N % 64) return GM_ERR_UNSUPPORTED;
+    if (M % tc::BM || K % tc::BK || N % 64 || M / tc::BM > 65535) return GM_ERR_UNSUPPORTED;
     const int bn = tc_choose_bn(M, N, forced_bn);
     const int cps = tc_choose_cps(M, N, bn, forced_cps);
     CUtensorMap ma, mb;

@@ -310,7 +310,8 @@ __global__ void __launch_bounds__(256, CPS)
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    // the N tiles of one row block are consecutive blocks, so the A rows come from DRAM once
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const int KB1 = K / BK;                 // K blocks of one pass
     const int KB = split ? 3 * KB1 : KB1;   // passes: hi*hi (+ lo*hi + hi*lo)
 

@@ -69,17 +69,31 @@ __global__ void __launch_bounds__(REDUCE_CHUNK) k_reduce_partial(int B, int N, c
     }
 }
 
-__global__ void __launch_bounds__(256) k_reduce_final(int B, const int32_t *__restrict__ atom_ptr,
-                                                      const double *__restrict__ part, double *energy,
-                                                      double *virial) {
-    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (b >= B) return;
+// Phase 2: one block per structure.  Lane l < 30 of warp w reads component l % 10 of chunks
+// k0 + 3w + l / 10, k0 + 3w + l / 10 + 24, ...; the 24 running sums per component are then
+// added in a fixed order (deterministic for a given structure size).
+constexpr int RF_THREADS = 256, RF_LANES = 24;
+__global__ void __launch_bounds__(RF_THREADS) k_reduce_final(int B, const int32_t *__restrict__ atom_ptr,
+                                                             const double *__restrict__ part, double *energy,
+                                                             double *virial) {
+    __shared__ double sh[RF_LANES][10];
+    const int b = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int a0 = atom_ptr[b], a1 = atom_ptr[b + 1];
-    double s = 0.0;
-    if (a1 > a0 && lane < 10)
-        for (int k = a0 / REDUCE_CHUNK; k <= (a1 - 1) / REDUCE_CHUNK; ++k) s += part[(size_t)(b + k) * 10 + lane];
-    if (lane == 0) energy[b] = s;
-    else if (lane < 10 && virial) virial[9 * b + lane - 1] = s;
+    const int sub = warp * 3 + lane / 10, q = lane % 10;
+    if (lane < 30) {
+        double s = 0.0;
+        if (a1 > a0)
+            for (int k = a0 / REDUCE_CHUNK + sub; k <= (a1 - 1) / REDUCE_CHUNK; k += RF_LANES)
+                s += part[(size_t)(b + k) * 10 + q];
+        sh[sub][q] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < 10) {
+        double s = 0.0;
+        for (int t = 0; t < RF_LANES; ++t) s += sh[t][threadIdx.x];
+        if (threadIdx.x == 0) energy[b] = s;
+        else if (virial) virial[9 * b + threadIdx.x - 1] = s;
+    }
 }
 
 size_t reduce_partial_doubles(int B, int N) { return (size_t)(B + (N + REDUCE_CHUNK - 1) / REDUCE_CHUNK + 1) * 10; }
@@ -94,7 +108,7 @@ void launch_struct_reduce(int B, int N, const int32_t *atom_ptr, const int32_t *
         note_launches(1);
     }
     if (B > 0) {
-        k_reduce_final<<<(B * 32 + 255) / 256, 256, 0, st>>>(B, atom_ptr, part, energy, virial);
+        k_reduce_final<<<B, RF_THREADS, 0, st>>>(B, atom_ptr, part, energy, virial);
         note_launches(1);
     }
 }

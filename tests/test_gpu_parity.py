@@ -221,6 +221,20 @@ def test_non_orthorhombic_cell_is_unsupported():
     assert m.read_status() == _lib.GM_ERR_UNSUPPORTED
 
 
+def test_more_than_max_atoms_is_unsupported():
+    """Checked on the host before anything touches the (much smaller) buffers."""
+    from paper_2505_22168_b300 import _lib
+    from paper_2505_22168_b300.gmnn import _ptr, _stream
+    b, d, p = synth.config(1)
+    m, sysd, nl = _nl_pair(b, d, p)
+    c = sysd.c_struct()
+    c.n_atoms = _lib.GM_MAX_ATOMS + 1
+    ws, wsb = m.workspace(_lib.GM_OP_NEIGHBORS, sysd, nl.capacity)
+    with pytest.raises(_lib.GmError) as err:
+        _lib.gm_build_neighbors(m.handle, c, nl.c_struct(), ws, wsb, _ptr(m.status), _stream())
+    assert err.value.code == _lib.GM_ERR_UNSUPPORTED
+
+
 def test_bad_species_is_reported():
     from paper_2505_22168_b300 import _lib
     b, d, p = synth.config(1)

@@ -69,3 +69,10 @@ def test_null_arguments_rejected_on_host(lib):
     assert L.gm_build_neighbors(None, None, None, None, 0, None, None) == lib.GM_ERR_ARG
     assert L.gm_energy_forces(None, None, None, None, None, None, None, 0, None, None) == lib.GM_ERR_ARG
     assert L.gm_status_clear(None, None) == lib.GM_ERR_ARG
+
+
+def test_header_constants_match_binding(lib):
+    text = (ROOT / "include" / "gm.h").read_text()
+    assert int(re.search(r"#define GM_MAX_ATOMS (\d+)", text).group(1)) == lib.GM_MAX_ATOMS
+    tune = dict(re.findall(r"(GM_TUNE_\w+) = (\d+)", text))
+    assert tune and all(int(v) == getattr(lib, k) for k, v in tune.items())
