@@ -219,57 +219,6 @@ __device__ __forceinline__ void fwd_group(const T (&P)[NPSI], const FeatOut &gt)
     }
 }
 
-template <typename OutT>
-__global__ void __launch_bounds__(CT_THREADS, 2) k_contract_fwd(const float *__restrict__ psi, int N, int Mp,
-                                                                OutT *__restrict__ G, float *__restrict__ G32,
-                                                                int lo_out) {
-    extern __shared__ float tile[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * CT_ATOMS;
-    float P[NPSI];
-    load_psi(psi, m0 + lane, N, P);
-    const FeatOut gt{tile + lane * GT_STRIDE, nullptr};
-    switch (warp) {
-    case 0: fwd_group<0>(P, gt); break;
-    case 1: fwd_group<1>(P, gt); break;
-    case 2: fwd_group<2>(P, gt); break;
-    case 3: fwd_group<3>(P, gt); break;
-    case 4: fwd_group<4>(P, gt); break;
-    case 5: fwd_group<5>(P, gt); break;
-    case 6: fwd_group<6>(P, gt); break;
-    default: fwd_group<7>(P, gt); break;
-    }
-    __syncthreads();
-    // 16-byte stores of 8 columns (BF16: a hi/lo row pair [hi(384) | lo(384)]) or 4 columns
-    constexpr int CW = sizeof(OutT) == 2 ? 8 : 4, NCW = NFP / CW;
-    for (int idx = threadIdx.x; idx < CT_ATOMS * NCW; idx += CT_THREADS) {
-        const int r = idx / NCW, c = idx - r * NCW, m = m0 + r;
-        if (m >= Mp) continue;
-        float v[CW];
-#pragma unroll
-        for (int j = 0; j < CW; ++j) v[j] = c * CW + j < NF ? tile[r * GT_STRIDE + c * CW + j] : 0.0f;
-        if constexpr (sizeof(OutT) == 2) {
-            __align__(16) __nv_bfloat16 hi[8], lo[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                hi[j] = __float2bfloat16_rn(v[j]);
-                lo[j] = __float2bfloat16_rn(v[j] - __bfloat162float(hi[j]));
-            }
-            __nv_bfloat16 *row = reinterpret_cast<__nv_bfloat16 *>(G) + (size_t)m * 2 * NFP + c * 8;
-            *reinterpret_cast<uint4 *>(row) = *reinterpret_cast<const uint4 *>(hi);
-            if (lo_out) *reinterpret_cast<uint4 *>(row + NFP) = *reinterpret_cast<const uint4 *>(lo);
-        } else {
-            *reinterpret_cast<float4 *>(G + (size_t)m * NFP + c * 4) = make_float4(v[0], v[1], v[2], v[3]);
-        }
-    }
-    if (G32 != nullptr) {
-        for (int idx = threadIdx.x; idx < CT_ATOMS * NF; idx += CT_THREADS) {
-            const int r = idx / NF, f = idx - r * NF, m = m0 + r;
-            if (m < N) G32[(size_t)m * NF + f] = tile[r * GT_STRIDE + f];
-        }
-    }
-}
-
 // ------------------------------------------------------------------ backward groups
 // Backward units: FAM 0 = families #1-#4; FAM 5, 6, 7, 8 = that family restricted by MASK
 // (a bit set per radial index: s1 for #5 and #7, s2 for #6 and #8).
@@ -445,26 +394,6 @@ __device__ __forceinline__ void bwd_group(const T (&P)[NPSI], const float *gb, T
     else bwd_unit<8, 0x1C>(P, gb, A);
 }
 
-// Eight backward warps of balanced work (estimated FMAs per atom in brackets):
-//   #1-#4 + #8 s2=0 [1.7k]; #5 s1 in {0,4} [1.7k]; #5 s1 in {1,2,3} [2.1k]; #6 s2 in {0..3} [2.0k];
-//   #7 s1 in {0,4} [2.0k]; #7 s1=1 + #6 s2=4 [1.8k]; #7 s1 in {2,3} + #8 s2=1 [2.2k]; #8 s2 in {2,3,4} [1.7k]
-// (eight groups by family alone put 3.8k on the #5 warp).  Nine warps do not fit: at this
-// register count one SM sub-partition cannot hold three warps.
-constexpr int CT_BWD_WARPS = 8;
-template <typename T>
-__device__ __forceinline__ void bwd_warp(int warp, const T (&P)[NPSI], const float *gb, T (&A)[NPSI]) {
-    switch (warp) {
-    case 0: bwd_unit<0, 0x1F>(P, gb, A); bwd_unit<8, 0x01>(P, gb, A); break;
-    case 1: bwd_unit<5, 0x11>(P, gb, A); break;
-    case 2: bwd_unit<5, 0x0E>(P, gb, A); break;
-    case 3: bwd_unit<6, 0x0F>(P, gb, A); break;
-    case 4: bwd_unit<7, 0x11>(P, gb, A); break;
-    case 5: bwd_unit<7, 0x02>(P, gb, A); bwd_unit<6, 0x10>(P, gb, A); break;
-    case 6: bwd_unit<7, 0x0C>(P, gb, A); bwd_unit<8, 0x02>(P, gb, A); break;
-    default: bwd_unit<8, 0x1C>(P, gb, A); break;
-    }
-}
-
 // Stage the 360 leading columns of 32 rows of a [.][384] FP32 matrix into shared memory
 // (row stride GT_STRIDE, rows past N zero).  Every thread issues all of its 16-byte loads
 // before the first store, so the block waits for one memory latency instead of one per row.
@@ -491,32 +420,549 @@ __device__ __forceinline__ void stage_rows(const float *__restrict__ src, int m0
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(CT_BWD_WARPS * 32, 2) k_contract_bwd(const float *__restrict__ psi,
-                                                                const float *__restrict__ dG, int N,
-                                                                float *__restrict__ dpsi) {
-    extern __shared__ float sm[];
-    float *gtile = sm;
-    float *acc = sm + CT_ATOMS * GT_STRIDE;
+// ------------------------------------------------------------------ item kernels (FP32 path)
+// The forward and backward kernels of the energy/force step stage the moments of 32 atoms
+// in shared memory ([32][100], one row per atom; the 400-byte rows keep 16-byte accesses
+// free of bank conflicts), lane = atom.  Every thread keeps the vectors and matrices of its
+// atom (v_s, M_s: 45 values) in registers for the whole kernel; the rank-3 tensors T_s, and
+// the one matrix an item selects at run time, are read from the shared tile.  The warps
+// walk a list of 31 work items, each one family restricted to one radial index (or index
+// pair) chosen at run time, with the other indices unrolled over the register tensors:
+//   D(s1<=s2)  #7 and #4   15 items      E(s2)  #8   5 items      B(s1)  #5   5 items
+//   C(s2)      #6          5 items       F      #1-#3  1 item
+// Every item kind is one short loop body shared by all warps, so the instruction stream
+// stays in the instruction cache (fully unrolled per-warp code, 15k FMAs per atom in the
+// backward, starved the warps of instructions), and the shared-memory traffic is a few
+// 16-byte accesses per item.  Items are dealt to the warps heaviest first in snake order.
+// Backward: gradients with respect to v_s, M_s and Psi0_s accumulate in registers; those
+// with respect to an item's run-time tensor (T_s1, T_s2; M_s1 in #5, M_s2 in #6) are added
+// into the warp's private [32][100] shared slot (warp-private read-modify-write, no
+// atomics), and the register sums join them at the end.  The slots are summed in warp order
+// (deterministic).
+constexpr int IT_COUNT = 31;
+enum { IK_B = 0, IK_E = 1, IK_F = 2, IK_D = 3, IK_C = 4 };
+
+#define LM(m, a, b) m[idx2(a, b) - 4]
+#define LT(t, a, b, c) t[idx3(a, b, c) - 10]
+
+__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
+
+// Components of one radial channel (ch = row + s * 20, 16-byte aligned): 0 scalar, 1-3
+// vector, 4-9 rank 2, 10-19 rank 3.
+__device__ __forceinline__ void ld_v(const float *ch, float (&v)[3]) {
+    const float4 q = ld4(ch);
+    v[0] = q.y; v[1] = q.z; v[2] = q.w;
+}
+__device__ __forceinline__ void ld_m(const float *ch, float (&m)[6]) {
+    const float4 a = ld4(ch + 4), b = ld4(ch + 8);
+    m[0] = a.x; m[1] = a.y; m[2] = a.z; m[3] = a.w; m[4] = b.x; m[5] = b.y;
+}
+__device__ __forceinline__ void ld_t(const float *ch, float (&t)[10]) {
+    const float4 a = ld4(ch + 8), b = ld4(ch + 12), c = ld4(ch + 16);
+    t[0] = a.z; t[1] = a.w; t[2] = b.x; t[3] = b.y; t[4] = b.z; t[5] = b.w; t[6] = c.x; t[7] = c.y; t[8] = c.z;
+    t[9] = c.w;
+}
+__device__ __forceinline__ void add_v(float *ch, const float (&v)[3], float c0) {
+    float4 q = ld4(ch);
+    q.x += c0; q.y += v[0]; q.z += v[1]; q.w += v[2];
+    st4(ch, q);
+}
+__device__ __forceinline__ void add_m(float *ch, const float (&m)[6]) {
+    float4 a = ld4(ch + 4), b = ld4(ch + 8);
+    a.x += m[0]; a.y += m[1]; a.z += m[2]; a.w += m[3]; b.x += m[4]; b.y += m[5];
+    st4(ch + 4, a);
+    st4(ch + 8, b);
+}
+__device__ __forceinline__ void add_t(float *ch, const float (&t)[10]) {
+    float4 a = ld4(ch + 8), b = ld4(ch + 12), c = ld4(ch + 16);
+    a.z += t[0]; a.w += t[1]; b.x += t[2]; b.y += t[3]; b.z += t[4]; b.w += t[5]; c.x += t[6]; c.y += t[7];
+    c.z += t[8]; c.w += t[9];
+    st4(ch + 8, a);
+    st4(ch + 12, b);
+    st4(ch + 16, c);
+}
+template <int K> __device__ __forceinline__ void zero_arr(float (&x)[K]) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) x[q] = 0.0f;
+}
+
+// pair index q in [0, 15) -> (s1 <= s2), lexicographic (the order of pair_le_index)
+__device__ __forceinline__ void pair_of(int q, int &s1, int &s2) {
+    s1 = 0;
+    while (q >= NR - s1) {
+        q -= NR - s1;
+        ++s1;
+    }
+    s2 = s1 + q;
+}
+
+// position k of the item list (heaviest first) -> kind and run-time index
+__device__ __forceinline__ void item_of(int k, int &kind, int &arg) {
+    if (k == 0) { kind = IK_B; arg = 0; }
+    else if (k <= 5) { kind = IK_E; arg = k - 1; }
+    else if (k == 6) { kind = IK_B; arg = 1; }
+    else if (k == 7) { kind = IK_F; arg = 0; }
+    else if (k < 23) { kind = IK_D; arg = k - 8; }
+    else if (k == 23) { kind = IK_B; arg = 2; }
+    else if (k < 29) { kind = IK_C; arg = k - 24; }
+    else { kind = IK_B; arg = k - 26; }          // 29 -> 3, 30 -> 4
+}
+// the r-th item of warp w of W (snake order: w, 2W-1-w, 2W+w, ...)
+__device__ __forceinline__ int item_pos(int r, int w, int W) { return r * W + ((r & 1) ? W - 1 - w : w); }
+
+// register copy of an atom's vectors and matrices
+struct RegVM {
+    float v[NR][3], m[NR][6];
+};
+__device__ __forceinline__ void load_vm(const float *row, RegVM &p) {
+#pragma unroll
+    for (int s = 0; s < NR; ++s) {
+        ld_v(row + s * NC, p.v[s]);
+        ld_m(row + s * NC, p.m[s]);
+    }
+}
+
+// Features of item (kind, arg) for this lane's atom (row = its moments) into out[0..360).
+__device__ __forceinline__ void fwd_item(int kind, int arg, const float *row, const RegVM &P, float *out) {
+    if (kind == IK_D) {                            // #7: Q_cd = T1_abc T2_abd, f = Q : M3;  #4: T1 : T2
+        int s1, s2;
+        pair_of(arg, s1, s2);
+        float T1[10], T2[10];
+        ld_t(row + s1 * NC, T1);
+        ld_t(row + s2 * NC, T2);
+        float f4 = 0.0f, Q[3][3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                float v = 0.0f;
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) v = fmaf(LT(T1, a, b, c), LT(T2, a, b, d), v);
+                Q[c][d] = v;
+                if (c == d) f4 += v;
+            }
+        out[FAM_OFF4 + arg] = f4;
+        const int f0 = FAM_OFF7 + f7_index(s1, s2, 0);
+#pragma unroll
+        for (int s3 = 0; s3 < NR; ++s3) {
+            float f = 0.0f;
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int d = 0; d < 3; ++d) f = fmaf(Q[c][d], LM(P.m[s3], c, d), f);
+            out[f0 + s3] = f;
+        }
+    } else if (kind == IK_E) {                     // #8: U_a = T2_abc M3_bc, f = v1 . U
+        const int t2 = arg;
+        float T2[10];
+        ld_t(row + t2 * NC, T2);
+#pragma unroll
+        for (int s3 = 0; s3 < NR; ++s3) {
+            float U[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                float v = 0.0f;
+#pragma unroll
+                for (int b = 0; b < 3; ++b)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) v = fmaf(LT(T2, a, b, c), LM(P.m[s3], b, c), v);
+                U[a] = v;
+            }
+#pragma unroll
+            for (int s1 = 0; s1 < NR; ++s1) {
+                float f = 0.0f;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) f = fmaf(P.v[s1][a], U[a], f);
+                out[FAM_OFF8 + f8_index(s1, t2, s3)] = f;
+            }
+        }
+    } else if (kind == IK_B) {                     // #5: tr(M1 M2 M3), s1 <= s2 <= s3
+        const int s1 = arg;
+        float M1[6];
+        ld_m(row + s1 * NC, M1);
+#pragma unroll
+        for (int s2 = 0; s2 < NR; ++s2) {
+            if (s2 < s1) continue;
+            float Nm[3][3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    float v = 0.0f;
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) v = fmaf(LM(M1, a, b), LM(P.m[s2], b, c), v);
+                    Nm[a][c] = v;
+                }
+#pragma unroll
+            for (int s3 = s2; s3 < NR; ++s3) {
+                float f = 0.0f;
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) f = fmaf(Nm[a][c], LM(P.m[s3], c, a), f);
+                out[FAM_OFF5 + f5_index(s1, s2, s3)] = f;
+            }
+        }
+    } else if (kind == IK_C) {                     // #6: w = M2 v3, f = v1 . w, s1 <= s3
+        const int t2 = arg;
+        float M2[6];
+        ld_m(row + t2 * NC, M2);
+#pragma unroll
+        for (int s3 = 0; s3 < NR; ++s3) {
+            float w[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                float v = 0.0f;
+#pragma unroll
+                for (int b = 0; b < 3; ++b) v = fmaf(LM(M2, a, b), P.v[s3][b], v);
+                w[a] = v;
+            }
+#pragma unroll
+            for (int s1 = 0; s1 <= s3; ++s1) {
+                float f = 0.0f;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) f = fmaf(P.v[s1][a], w[a], f);
+                out[FAM_OFF6 + f6_index(s1, t2, s3)] = f;
+            }
+        }
+    } else {                                       // #1, #2, #3
+#pragma unroll
+        for (int s = 0; s < NR; ++s) out[FAM_OFF1 + s] = row[s * NC];
+#pragma unroll
+        for (int s1 = 0; s1 < NR; ++s1)
+#pragma unroll
+            for (int s2 = s1; s2 < NR; ++s2) {
+                float f2 = 0.0f, f3 = 0.0f;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    f2 = fmaf(P.v[s1][a], P.v[s2][a], f2);
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) f3 = fmaf(LM(P.m[s1], a, b), LM(P.m[s2], a, b), f3);
+                }
+                const int q = pair_le_index(s1, s2);
+                out[FAM_OFF2 + q] = f2;
+                out[FAM_OFF3 + q] = f3;
+            }
+    }
+}
+
+// register gradient accumulators of one atom: dE/dv_s, dE/dM_s, dE/dPsi0_s
+struct RegGrad {
+    float v[NR][3], m[NR][6], c0[NR];
+};
+
+// dE/dPsi contributions of item (kind, arg) for this lane's atom (gb = its dE/dG): into
+// the registers A, and into the slot row acc for the item's run-time tensor.  Full-tensor
+// index loops write into unique accumulators, which sums all index permutations (the
+// gradient with respect to the unique component).  Run-time targets that coincide
+// (s1 == s2) are updated one after the other, so both contributions land.
+__device__ __forceinline__ void bwd_item(int kind, int arg, const float *row, const RegVM &P, const float *gb,
+                                         RegGrad &A, float *acc) {
+    if (kind == IK_D) {                            // #7 and #4
+        int s1, s2;
+        pair_of(arg, s1, s2);
+        float T1[10], T2[10];
+        ld_t(row + s1 * NC, T1);
+        ld_t(row + s2 * NC, T2);
+        const int f0 = FAM_OFF7 + f7_index(s1, s2, 0);
+        const float g4 = gb[FAM_OFF4 + arg];
+        float g[NR], Mw[6];                        // Mw = sum_s3 g M3 (symmetric)
+        zero_arr(Mw);
+#pragma unroll
+        for (int s3 = 0; s3 < NR; ++s3) {
+            g[s3] = gb[f0 + s3];
+#pragma unroll
+            for (int u = 0; u < 6; ++u) Mw[u] = fmaf(g[s3], P.m[s3][u], Mw[u]);
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {          // Q_cd; d/dM3_cd = Q_cd
+                float v = 0.0f;
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) v = fmaf(LT(T1, a, b, c), LT(T2, a, b, d), v);
+#pragma unroll
+                for (int s3 = 0; s3 < NR; ++s3) LM(A.m[s3], c, d) = fmaf(g[s3], v, LM(A.m[s3], c, d));
+            }
+        float t1[10], t2[10];                      // d/dT1_abc = g4 T2_abc + T2_abd Mw_cd, and T1 <-> T2
+        zero_arr(t1);
+        zero_arr(t2);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    float x1 = g4 * LT(T2, a, b, c), x2 = g4 * LT(T1, a, b, c);
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        x1 = fmaf(LT(T2, a, b, d), LM(Mw, c, d), x1);
+                        x2 = fmaf(LT(T1, a, b, d), LM(Mw, d, c), x2);
+                    }
+                    LT(t1, a, b, c) += x1;
+                    LT(t2, a, b, c) += x2;
+                }
+        add_t(acc + s1 * NC, t1);
+        add_t(acc + s2 * NC, t2);
+    } else if (kind == IK_E) {                     // #8
+        const int t2 = arg;
+        float T2[10], at[10];
+        ld_t(row + t2 * NC, T2);
+        zero_arr(at);
+#pragma unroll
+        for (int s3 = 0; s3 < NR; ++s3) {
+            float U[3], Vw[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                float v = 0.0f;
+#pragma unroll
+                for (int b = 0; b < 3; ++b)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) v = fmaf(LT(T2, a, b, c), LM(P.m[s3], b, c), v);
+                U[a] = v;
+            }
+#pragma unroll
+            for (int s1 = 0; s1 < NR; ++s1) {      // d/dv1 = g U; Vw = sum_s1 g v1
+                const float g = gb[FAM_OFF8 + f8_index(s1, t2, s3)];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    A.v[s1][a] = fmaf(g, U[a], A.v[s1][a]);
+                    Vw[a] = fmaf(g, P.v[s1][a], Vw[a]);
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < 3; ++a)            // d/dT2_abc = Vw_a M3_bc, d/dM3_bc = Vw_a T2_abc
+#pragma unroll
+                for (int b = 0; b < 3; ++b)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        LT(at, a, b, c) = fmaf(Vw[a], LM(P.m[s3], b, c), LT(at, a, b, c));
+                        LM(A.m[s3], b, c) = fmaf(Vw[a], LT(T2, a, b, c), LM(A.m[s3], b, c));
+                    }
+        }
+        add_t(acc + t2 * NC, at);
+    } else if (kind == IK_B) {                     // #5: s1 <= s2 <= s3
+        const int s1 = arg;
+        float M1[6], a1[6];
+        ld_m(row + s1 * NC, M1);
+        zero_arr(a1);
+#pragma unroll
+        for (int s2 = 0; s2 < NR; ++s2) {
+            if (s2 < s1) continue;
+            float Nm[3][3], Mg[6];                 // Nm = M1 M2, Mg = sum_s3 g M3
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    float v = 0.0f;
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) v = fmaf(LM(M1, a, b), LM(P.m[s2], b, c), v);
+                    Nm[a][c] = v;
+                }
+            zero_arr(Mg);
+#pragma unroll
+            for (int s3 = s2; s3 < NR; ++s3) {     // d/d(M3)_ba = (M1 M2)_ab
+                const float g = gb[FAM_OFF5 + f5_index(s1, s2, s3)];
+#pragma unroll
+                for (int u = 0; u < 6; ++u) Mg[u] = fmaf(g, P.m[s3][u], Mg[u]);
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) LM(A.m[s3], b, a) = fmaf(g, Nm[a][b], LM(A.m[s3], b, a));
+            }
+#pragma unroll
+            for (int a = 0; a < 3; ++a)            // d/d(M1)_ba = (M2 Mg)_ab, d/d(M2)_ba = (Mg M1)_ab
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    float x1 = 0.0f, x2 = 0.0f;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        x1 = fmaf(LM(P.m[s2], a, c), LM(Mg, c, b), x1);
+                        x2 = fmaf(LM(Mg, a, c), LM(M1, c, b), x2);
+                    }
+                    LM(a1, b, a) += x1;
+                    LM(A.m[s2], b, a) += x2;
+                }
+        }
+        add_m(acc + s1 * NC, a1);
+    } else if (kind == IK_C) {                     // #6: s1 <= s3
+        const int t2 = arg;
+        float M2[6], am[6];
+        ld_m(row + t2 * NC, M2);
+        zero_arr(am);
+#pragma unroll
+        for (int s3 = 0; s3 < NR; ++s3) {
+            float w[3], vg[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                float v = 0.0f;
+#pragma unroll
+                for (int b = 0; b < 3; ++b) v = fmaf(LM(M2, a, b), P.v[s3][b], v);
+                w[a] = v;
+            }
+#pragma unroll
+            for (int s1 = 0; s1 <= s3; ++s1) {     // d/dv1 = g M2 v3; vg = sum_s1 g v1
+                const float g = gb[FAM_OFF6 + f6_index(s1, t2, s3)];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    A.v[s1][a] = fmaf(g, w[a], A.v[s1][a]);
+                    vg[a] = fmaf(g, P.v[s1][a], vg[a]);
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {          // d/dM2_ab = vg_a v3_b, d/dv3 = M2 vg
+                float v = 0.0f;
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    LM(am, a, b) = fmaf(vg[a], P.v[s3][b], LM(am, a, b));
+                    v = fmaf(LM(M2, a, b), vg[b], v);
+                }
+                A.v[s3][a] += v;
+            }
+        }
+        add_m(acc + t2 * NC, am);
+    } else {                                       // #1, #2, #3
+#pragma unroll
+        for (int s = 0; s < NR; ++s) A.c0[s] += gb[FAM_OFF1 + s];
+#pragma unroll
+        for (int s1 = 0; s1 < NR; ++s1)
+#pragma unroll
+            for (int s2 = s1; s2 < NR; ++s2) {
+                const int q = pair_le_index(s1, s2);
+                const float g2 = gb[FAM_OFF2 + q], g3 = gb[FAM_OFF3 + q];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    A.v[s1][a] = fmaf(g2, P.v[s2][a], A.v[s1][a]);
+                    A.v[s2][a] = fmaf(g2, P.v[s1][a], A.v[s2][a]);
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) {
+                        LM(A.m[s1], a, b) = fmaf(g3, LM(P.m[s2], a, b), LM(A.m[s1], a, b));
+                        LM(A.m[s2], a, b) = fmaf(g3, LM(P.m[s1], a, b), LM(A.m[s2], a, b));
+                    }
+                }
+            }
+    }
+}
+
+// psi rows m0..m0+31 (zero past N) into the shared tile [32][100]
+template <int NT>
+__device__ __forceinline__ void stage_psi(const float *__restrict__ psi, int m0, int N, float *ptile) {
+    constexpr int V4 = NPSI / 4;
+    const float4 *src = reinterpret_cast<const float4 *>(psi + (size_t)m0 * NPSI);
+    float4 *dst = reinterpret_cast<float4 *>(ptile);
+    for (int idx = threadIdx.x; idx < CT_ATOMS * V4; idx += NT)
+        dst[idx] = m0 + idx / V4 < N ? __ldg(src + idx) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+}
+
+template <typename OutT, int W>
+__global__ void __launch_bounds__(W * 32) k_contract_fwd(const float *__restrict__ psi, int N, int Mp,
+                                                         OutT *__restrict__ G, float *__restrict__ G32, int lo_out) {
+    extern __shared__ __align__(16) float smf[];
+    float *ptile = smf;                            // [32][100]
+    float *tile = smf + CT_ATOMS * NPSI;           // [32][GT_STRIDE] features
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * CT_ATOMS;
-    stage_rows<CT_BWD_WARPS * 32>(dG, m0, N, gtile);
-    float P[NPSI], A[NPSI];
-    load_psi(psi, m0 + lane, N, P);
-#pragma unroll
-    for (int q = 0; q < NPSI; ++q) A[q] = 0.0f;
-    const float *gb = gtile + lane * GT_STRIDE;
-    bwd_warp(warp, P, gb, A);
-    float *arow = acc + lane * AC_STRIDE;
-    for (int w = 0; w < CT_BWD_WARPS; ++w) {
-        if (warp == w) {
-#pragma unroll
-            for (int q = 0; q < NPSI; ++q) arow[q] = (w == 0 ? 0.0f : arow[q]) + A[q];
-        }
-        __syncthreads();
+    stage_psi<W * 32>(psi, m0, N, ptile);
+    __syncthreads();
+    const float *row = ptile + lane * NPSI;
+    float *out = tile + lane * GT_STRIDE;
+    RegVM P;
+    load_vm(row, P);
+    for (int r = 0;; ++r) {
+        const int k = item_pos(r, warp, W);
+        if (k >= IT_COUNT) break;
+        int kind, arg;
+        item_of(k, kind, arg);
+        fwd_item(kind, arg, row, P, out);
     }
-    for (int idx = threadIdx.x; idx < CT_ATOMS * NPSI; idx += blockDim.x) {
-        const int r = idx / NPSI, q = idx - r * NPSI, m = m0 + r;
-        if (m < N) dpsi[(size_t)m * NPSI + q] = acc[r * AC_STRIDE + q];
+    __syncthreads();
+    // 16-byte stores of 8 columns (BF16: a hi/lo row pair [hi(384) | lo(384)]) or 4 columns
+    constexpr int CW = sizeof(OutT) == 2 ? 8 : 4, NCW = NFP / CW;
+    for (int idx = threadIdx.x; idx < CT_ATOMS * NCW; idx += W * 32) {
+        const int r = idx / NCW, c = idx - r * NCW, m = m0 + r;
+        if (m >= Mp) continue;
+        float v[CW];
+#pragma unroll
+        for (int j = 0; j < CW; ++j) v[j] = c * CW + j < NF ? tile[r * GT_STRIDE + c * CW + j] : 0.0f;
+        if constexpr (sizeof(OutT) == 2) {
+            __align__(16) __nv_bfloat16 hi[8], lo[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                hi[j] = __float2bfloat16_rn(v[j]);
+                lo[j] = __float2bfloat16_rn(v[j] - __bfloat162float(hi[j]));
+            }
+            __nv_bfloat16 *orow = reinterpret_cast<__nv_bfloat16 *>(G) + (size_t)m * 2 * NFP + c * 8;
+            *reinterpret_cast<uint4 *>(orow) = *reinterpret_cast<const uint4 *>(hi);
+            if (lo_out) *reinterpret_cast<uint4 *>(orow + NFP) = *reinterpret_cast<const uint4 *>(lo);
+        } else {
+            *reinterpret_cast<float4 *>(G + (size_t)m * NFP + c * 4) = make_float4(v[0], v[1], v[2], v[3]);
+        }
+    }
+    if (G32 != nullptr) {
+        for (int idx = threadIdx.x; idx < CT_ATOMS * NF; idx += W * 32) {
+            const int r = idx / NF, f = idx - r * NF, m = m0 + r;
+            if (m < N) G32[(size_t)m * NF + f] = tile[r * GT_STRIDE + f];
+        }
+    }
+}
+
+template <int W>
+__global__ void __launch_bounds__(W * 32) k_contract_bwd(const float *__restrict__ psi, const float *__restrict__ dG,
+                                                         int N, float *__restrict__ dpsi) {
+    extern __shared__ __align__(16) float smb[];
+    float *ptile = smb;                                    // [32][100] moments
+    float *slots = ptile + CT_ATOMS * NPSI;                // W x [32][100] partial dE/dPsi
+    float *gtile = slots + W * CT_ATOMS * NPSI;            // [32][GT_STRIDE] dE/dG
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * CT_ATOMS;
+    stage_psi<W * 32>(psi, m0, N, ptile);
+    {
+        float4 *mine = reinterpret_cast<float4 *>(slots + warp * CT_ATOMS * NPSI);
+        for (int q = lane; q < CT_ATOMS * NPSI / 4; q += 32) mine[q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+    stage_rows<W * 32>(dG, m0, N, gtile);                   // ends with __syncthreads()
+    const float *row = ptile + lane * NPSI;
+    const float *gb = gtile + lane * GT_STRIDE;
+    float *acc = slots + warp * CT_ATOMS * NPSI + lane * NPSI;
+    RegVM P;
+    load_vm(row, P);
+    RegGrad A;
+#pragma unroll
+    for (int s = 0; s < NR; ++s) {
+        zero_arr(A.v[s]);
+        zero_arr(A.m[s]);
+        A.c0[s] = 0.0f;
+    }
+    for (int r = 0;; ++r) {
+        const int k = item_pos(r, warp, W);
+        if (k >= IT_COUNT) break;
+        int kind, arg;
+        item_of(k, kind, arg);
+        bwd_item(kind, arg, row, P, gb, A, acc);
+    }
+#pragma unroll
+    for (int s = 0; s < NR; ++s) {
+        add_v(acc + s * NC, A.v[s], A.c0[s]);
+        add_m(acc + s * NC, A.m[s]);
+    }
+    __syncthreads();
+    const float4 *s4 = reinterpret_cast<const float4 *>(slots);
+    constexpr int V4 = NPSI / 4, SLOT4 = CT_ATOMS * V4;
+    float4 *d4 = reinterpret_cast<float4 *>(dpsi + (size_t)m0 * NPSI);
+    for (int idx = threadIdx.x; idx < SLOT4; idx += W * 32) {
+        if (m0 + idx / V4 >= N) break;
+        float4 v = s4[idx];
+#pragma unroll
+        for (int w = 1; w < W; ++w) {
+            const float4 x = s4[w * SLOT4 + idx];
+            v.x += x.x; v.y += x.y; v.z += x.z; v.w += x.w;
+        }
+        d4[idx] = v;
     }
 }
 
@@ -681,35 +1127,49 @@ void launch_contract_bwd_dual(const float *psi, const float *psid, const float *
         note_launches(1);
     }
 }
-void launch_contract_fwd_f32(const float *psi, int N, int Mp, float *G, float *features_out, cudaStream_t st) {
+// Warps per block of the item kernels: the forward uses 8 (its 59 KB of shared memory let
+// three blocks share an SM); the backward uses 4 (110 KB with the four private slots, two
+// blocks per SM).
+constexpr int CT_FWD_W = 8, CT_BWD_W = 4;
+constexpr size_t ct_fwd_smem() { return sizeof(float) * (CT_ATOMS * NPSI + CT_ATOMS * GT_STRIDE); }
+constexpr size_t ct_bwd_smem() { return sizeof(float) * ((CT_BWD_W + 1) * CT_ATOMS * NPSI + CT_ATOMS * GT_STRIDE); }
+
+template <typename OutT>
+static void launch_fwd_items(const float *psi, int N, int Mp, OutT *G, float *features_out, int lo_out,
+                             cudaStream_t st) {
     const int blocks = (Mp + CT_ATOMS - 1) / CT_ATOMS;
-    const size_t smem = sizeof(float) * CT_ATOMS * GT_STRIDE;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_contract_fwd<OutT, CT_FWD_W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)ct_fwd_smem());
+        attr = true;
+    }
     if (blocks > 0) {
-        k_contract_fwd<float><<<blocks, CT_THREADS, smem, st>>>(psi, N, Mp, G, features_out, 0);
+        k_contract_fwd<OutT, CT_FWD_W><<<blocks, CT_FWD_W * 32, ct_fwd_smem(), st>>>(psi, N, Mp, G, features_out,
+                                                                                     lo_out);
         note_launches(1);
     }
+}
+
+void launch_contract_fwd_f32(const float *psi, int N, int Mp, float *G, float *features_out, cudaStream_t st) {
+    launch_fwd_items<float>(psi, N, Mp, G, features_out, 0, st);
 }
 
 void launch_contract_fwd_bf16(const float *psi, int N, int Mp, __nv_bfloat16 *G, float *features_out, bool lo_out,
                               cudaStream_t st) {
-    const int blocks = (Mp + CT_ATOMS - 1) / CT_ATOMS;
-    const size_t smem = sizeof(float) * CT_ATOMS * GT_STRIDE;
-    if (blocks > 0) {
-        k_contract_fwd<__nv_bfloat16><<<blocks, CT_THREADS, smem, st>>>(psi, N, Mp, G, features_out, lo_out ? 1 : 0);
-        note_launches(1);
-    }
+    launch_fwd_items<__nv_bfloat16>(psi, N, Mp, G, features_out, lo_out ? 1 : 0, st);
 }
 
 void launch_contract_bwd(const float *psi, const float *dG, int N, float *dpsi, cudaStream_t st) {
     const int blocks = (N + CT_ATOMS - 1) / CT_ATOMS;
-    const size_t smem = sizeof(float) * (CT_ATOMS * GT_STRIDE + CT_ATOMS * AC_STRIDE);
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_contract_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_contract_bwd<CT_BWD_W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)ct_bwd_smem());
         attr = true;
     }
     if (blocks > 0) {
-        k_contract_bwd<<<blocks, CT_BWD_WARPS * 32, smem, st>>>(psi, dG, N, dpsi);
+        k_contract_bwd<CT_BWD_W><<<blocks, CT_BWD_W * 32, ct_bwd_smem(), st>>>(psi, dG, N, dpsi);
         note_launches(1);
     }
 }
