@@ -881,10 +881,14 @@ __global__ void __launch_bounds__(W * 32) k_contract_fwd(const float *__restrict
         fwd_item(kind, arg, row, P, out);
     }
     __syncthreads();
-    // 16-byte stores of 8 columns (BF16: a hi/lo row pair [hi(384) | lo(384)]) or 4 columns
+    // 16-byte stores of 8 columns (BF16: a hi/lo row pair [hi(384) | lo(384)]) or 4 columns.
+    // A warp takes 8 rows x 4 column groups: with the odd row stride the scalar tile reads
+    // are free of bank conflicts, and each row gets 64 contiguous bytes.
     constexpr int CW = sizeof(OutT) == 2 ? 8 : 4, NCW = NFP / CW;
+    static_assert(NCW % 4 == 0, "column groups per row");
     for (int idx = threadIdx.x; idx < CT_ATOMS * NCW; idx += W * 32) {
-        const int r = idx / NCW, c = idx - r * NCW, m = m0 + r;
+        const int chunk = idx >> 5, l = idx & 31;
+        const int r = 8 * (chunk & 3) + (l >> 2), c = 4 * (chunk >> 2) + (l & 3), m = m0 + r;
         if (m >= Mp) continue;
         float v[CW];
 #pragma unroll
