@@ -513,7 +513,7 @@ static gm_status forward_to_features(const gm_model *m, const gm_system *sys, co
     float *psi = psi_out ? psi_out : w.psi;
     {
         StageScope sc(ST_MOMENTS, st);
-        launch_split_pos(N, sys->pos, w.pos_hi, w.pos_lo, forces_to_clear, st);
+        launch_split_pos(N, sys->pos, sys->species, w.pos_hi, w.pos_lo, forces_to_clear, st);
         launch_moments(a, choose_tpa(m, N), psi, st);
     }
     {
@@ -672,7 +672,7 @@ gm_status gm_param_grad(const gm_model *m, const gm_system *sys, const gm_nlist 
     PairArgs a = pair_args(m, sys, nl, w.pos_hi, w.pos_lo, status);
     {   // primal and tangent moments, features and their tangents
         StageScope sc(ST_PG_PAIR_FWD, st);
-        launch_split_pos(N, sys->pos, w.pos_hi, w.pos_lo, nullptr, st);
+        launch_split_pos(N, sys->pos, sys->species, w.pos_hi, w.pos_lo, nullptr, st);
         launch_moments(a, choose_tpa(m, N), w.psi, st);
         launch_moments_tangent(a, dL_dF, w.psid, st);
         launch_contract_fwd_dual(w.psi, w.psid, N, Mp, w.GG, st);

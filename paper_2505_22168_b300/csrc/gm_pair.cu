@@ -46,25 +46,54 @@ __device__ __forceinline__ float disp_axis(float xjh, float xjl, float xih, floa
     return h3 + lo;
 }
 
-// The next neighbour of a row, loaded one iteration ahead (index, shift, hi/lo position).
+// One neighbour of a row: index, shift, hi/lo position (species in ph.w).
 struct NextPair {
     int j;
     bool ok;
     char4 sh;
     float4 ph, pl;
-    __device__ __forceinline__ void load(const PairArgs &a, int p, int p1) {
+};
+
+// Gather pipeline over the pairs p0, p0 + step, ... < p1 of a row: while pair i is computed,
+// the position of pair i + 1 and the index of pair i + 2 are in flight, so the dependent
+// index -> position gather costs no latency inside the loop.
+struct PairPipe {
+    int p1, step, q;          // q: pair whose index is loaded next
+    int jn;                   // index, shift and flag of pair i + 2
+    char4 shn;
+    bool okn;
+    NextPair nx;              // pair i + 1 (position loads issued)
+    __device__ __forceinline__ void index(const PairArgs &a, int p, int &j, char4 &sh, bool &ok) const {
         ok = false;
         if (p < p1) {
             j = a.col[p];
             sh = a.shift[p];
             ok = (unsigned)j < (unsigned)a.N;
-            if (ok) {
-                ph = a.pos_hi[j];
-                pl = a.pos_lo[j];
-            } else {
-                set_status(a.status, GM_ERR_ARG);
-            }
+            if (!ok) set_status(a.status, GM_ERR_ARG);
         }
+    }
+    __device__ __forceinline__ void gather(const PairArgs &a) {
+        if (nx.ok) {
+            nx.ph = a.pos_hi[nx.j];
+            nx.pl = a.pos_lo[nx.j];
+        }
+    }
+    __device__ __forceinline__ PairPipe(const PairArgs &a, int p0, int p1_, int step_) : p1(p1_), step(step_) {
+        index(a, p0, nx.j, nx.sh, nx.ok);
+        index(a, p0 + step, jn, shn, okn);
+        gather(a);
+        q = p0 + 2 * step;
+    }
+    // the current pair; the pipeline advances by one
+    __device__ __forceinline__ NextPair next(const PairArgs &a) {
+        const NextPair cur = nx;
+        nx.j = jn;
+        nx.sh = shn;
+        nx.ok = okn;
+        gather(a);
+        index(a, q, jn, shn, okn);
+        q += step;
+        return cur;
     }
 };
 
@@ -89,9 +118,11 @@ struct Centre {
     }
 };
 
-// hi/lo FP32 split of the FP64 positions (once per atom); also clears the force array
+// hi/lo FP32 split of the FP64 positions (once per atom), the species index carried in the
+// hi word's w lane (so the neighbour gather brings it along); also clears the force array
 // the force kernel accumulates into, when given
-__global__ void __launch_bounds__(256) k_split_pos(int N, const double *__restrict__ pos, float4 *__restrict__ hi,
+__global__ void __launch_bounds__(256) k_split_pos(int N, const double *__restrict__ pos,
+                                                   const int32_t *__restrict__ species, float4 *__restrict__ hi,
                                                    float4 *__restrict__ lo, float *__restrict__ zero_F) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
@@ -107,13 +138,14 @@ __global__ void __launch_bounds__(256) k_split_pos(int N, const double *__restri
         h[d] = (float)x;
         l[d] = (float)(x - (double)h[d]);
     }
-    hi[i] = make_float4(h[0], h[1], h[2], 0.0f);
+    hi[i] = make_float4(h[0], h[1], h[2], __int_as_float(species[i]));
     lo[i] = make_float4(l[0], l[1], l[2], 0.0f);
 }
 
-void launch_split_pos(int N, const double *pos, float4 *hi, float4 *lo, float *zero_F, cudaStream_t st) {
+void launch_split_pos(int N, const double *pos, const int32_t *species, float4 *hi, float4 *lo, float *zero_F,
+                      cudaStream_t st) {
     if (N <= 0) return;
-    k_split_pos<<<(N + 255) / 256, 256, 0, st>>>(N, pos, hi, lo, zero_F);
+    k_split_pos<<<(N + 255) / 256, 256, 0, st>>>(N, pos, species, hi, lo, zero_F);
     note_launches(1);
 }
 
@@ -135,11 +167,9 @@ __global__ void __launch_bounds__(256) k_moments(PairArgs a, float *__restrict__
         const int zsi = clamp_species(a.species[atom], a.S, a.status);
         const float *brow = sbeta + zsi * a.S * (NR * NB);
         const int p1 = a.row_ptr[atom + 1];
-        NextPair nx;
-        nx.load(a, a.row_ptr[atom] + sub, p1);
+        PairPipe pp(a, a.row_ptr[atom] + sub, p1, TPA);
         for (int p = a.row_ptr[atom] + sub; p < p1; p += TPA) {
-            const NextPair cur = nx;
-            nx.load(a, p + TPA, p1);
+            const NextPair cur = pp.next(a);
             if (!cur.ok) continue;
             const int j = cur.j;
             float fx, fy, fz;
@@ -148,7 +178,7 @@ __global__ void __launch_bounds__(256) k_moments(PairArgs a, float *__restrict__
             const float rinv = 1.0f / r;
             float B[NB], dB[NB];
             radial_basis<false>(a.rc, r, B, dB);
-            const float *bt = brow + clamp_species(a.species[j], a.S, a.status) * (NR * NB);
+            const float *bt = brow + clamp_species(__float_as_int(cur.ph.w), a.S, a.status) * (NR * NB);
             float R[NR];
 #pragma unroll
             for (int s = 0; s < NR; ++s) {
@@ -237,11 +267,9 @@ __global__ void __launch_bounds__(256) k_forces(PairArgs a, const float *__restr
         const int zsi = clamp_species(a.species[atom], a.S, a.status);
         const float *brow = sbeta + zsi * a.S * (NR * NB);
         const int p1 = a.row_ptr[atom + 1];
-        NextPair nx;
-        nx.load(a, a.row_ptr[atom] + sub, p1);
+        PairPipe pp(a, a.row_ptr[atom] + sub, p1, TPA);
         for (int p = a.row_ptr[atom] + sub; p < p1; p += TPA) {
-            const NextPair cur = nx;
-            nx.load(a, p + TPA, p1);
+            const NextPair cur = pp.next(a);
             if (!cur.ok) continue;
             const int j = cur.j;
             float fx, fy, fz;
@@ -251,7 +279,7 @@ __global__ void __launch_bounds__(256) k_forces(PairArgs a, const float *__restr
             const float ux = fx * rinv, uy = fy * rinv, uz = fz * rinv;
             float B[NB], dB[NB];
             radial_basis<true>(a.rc, r, B, dB);
-            const float *bt = brow + clamp_species(a.species[j], a.S, a.status) * (NR * NB);
+            const float *bt = brow + clamp_species(__float_as_int(cur.ph.w), a.S, a.status) * (NR * NB);
             float R[NR], Rp[NR];
 #pragma unroll
             for (int s = 0; s < NR; ++s) {
@@ -338,11 +366,9 @@ __global__ void __launch_bounds__(256) k_moments_tangent(PairArgs a, const float
         const int zsi = clamp_species(a.species[atom], a.S, a.status);
         const float *brow = sbeta + zsi * a.S * (NR * NB);
         const int p1 = a.row_ptr[atom + 1];
-        NextPair nx;
-        nx.load(a, a.row_ptr[atom] + sub, p1);
+        PairPipe pp(a, a.row_ptr[atom] + sub, p1, TPA);
         for (int p = a.row_ptr[atom] + sub; p < p1; p += TPA) {
-            const NextPair cur = nx;
-            nx.load(a, p + TPA, p1);
+            const NextPair cur = pp.next(a);
             if (!cur.ok) continue;
             const int j = cur.j;
             float fx, fy, fz;
@@ -354,7 +380,7 @@ __global__ void __launch_bounds__(256) k_moments_tangent(PairArgs a, const float
             const float w = ux * ddx + uy * ddy + uz * ddz;
             float B[NB], dB[NB];
             radial_basis<true>(a.rc, r, B, dB);
-            const float *bt = brow + clamp_species(a.species[j], a.S, a.status) * (NR * NB);
+            const float *bt = brow + clamp_species(__float_as_int(cur.ph.w), a.S, a.status) * (NR * NB);
             float R[NR], Rp[NR];
 #pragma unroll
             for (int s = 0; s < NR; ++s) {
@@ -428,11 +454,9 @@ __global__ void __launch_bounds__(256) k_pg_beta(PairArgs a, const float *__rest
         const float vix = vel[3 * atom], viy = vel[3 * atom + 1], viz = vel[3 * atom + 2];
         const int zsi = clamp_species(a.species[atom], a.S, a.status);
         const int p1 = a.row_ptr[atom + 1];
-        NextPair nx;
-        nx.load(a, a.row_ptr[atom] + lane, p1);
+        PairPipe pp(a, a.row_ptr[atom] + lane, p1, 32);
         for (int p = a.row_ptr[atom] + lane; p < p1; p += 32) {
-            const NextPair cur = nx;
-            nx.load(a, p + 32, p1);
+            const NextPair cur = pp.next(a);
             if (!cur.ok) continue;
             const int j = cur.j;
             float fx, fy, fz;
@@ -452,7 +476,7 @@ __global__ void __launch_bounds__(256) k_pg_beta(PairArgs a, const float *__rest
                                  ddz * dmono(c, 2, ux, uy, uz);
                 ang[c] = Dc - (float)comp_rank(c) * m[c] * w;
             }
-            float *dst = la + (size_t)clamp_species(a.species[j], a.S, a.status) * (NR * NB) * 32 + lane;
+            float *dst = la + (size_t)clamp_species(__float_as_int(cur.ph.w), a.S, a.status) * (NR * NB) * 32 + lane;
 #pragma unroll
             for (int s = 0; s < NR; ++s) {
                 float P1 = 0.0f, P2 = 0.0f, P3 = 0.0f;

@@ -20,9 +20,11 @@ struct PairArgs {
     int32_t *status;
 };
 
-// pos_hi[i] = (float)pos[i], pos_lo[i] = (float)(pos[i] - pos_hi[i]) per axis (w = 0);
-// zero_F [N][3], if not null, is cleared for the force kernel's accumulation
-void launch_split_pos(int N, const double *pos, float4 *hi, float4 *lo, float *zero_F, cudaStream_t st);
+// pos_hi[i] = (float)pos[i], pos_lo[i] = (float)(pos[i] - pos_hi[i]) per axis; pos_hi[i].w
+// holds the bits of species[i] (lo w = 0).  zero_F [N][3], if not null, is cleared for the
+// force kernel's accumulation.
+void launch_split_pos(int N, const double *pos, const int32_t *species, float4 *hi, float4 *lo, float *zero_F,
+                      cudaStream_t st);
 void launch_moments(const PairArgs &a, int tpa, float *psi, cudaStream_t st);
 void launch_forces(const PairArgs &a, int tpa, const float *dpsi, float *F, float *vir_atom, cudaStream_t st);
 
