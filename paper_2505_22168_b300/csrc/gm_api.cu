@@ -384,7 +384,9 @@ gm_status gm_model_create(const gm_model_desc *d, gm_model **out) {
     m->n_param = theta_offsets(m->S, m->H).total;
     m->rc.r_cut = (float)d->r_cut;
     m->rc.inv_r_cut = (float)(1.0 / d->r_cut);
+    m->rc.pi_inv_r_cut = (float)(3.14159265358979323846 / d->r_cut);
     m->rc.gamma = (float)((double)(NB * NB) / (d->r_cut * d->r_cut));
+    m->rc.gamma_l2 = (float)((double)(NB * NB) / (d->r_cut * d->r_cut) * 1.44269504088896340736);
     for (int k = 0; k < NB; ++k) m->rc.mu[k] = (float)(d->r_min + k * (d->r_cut - d->r_min) / (NB - 1));
     m->pair_tpa = 0;
     m->split_mask = 12;

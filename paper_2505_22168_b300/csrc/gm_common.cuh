@@ -132,25 +132,62 @@ __device__ __forceinline__ float act_fwd2(float z, float &d1, float &d2) {
 
 // ---------------------------------------------------------------- radial part
 // Model constants the pair kernels need (beta is pre-scaled by n_basis^{-1/2}).
+// gamma_l2 = gamma log2(e) (rounded once from FP64), so Phi_k = 2^(-gamma_l2 t^2): the
+// result carries the same argument-rounding error as exp(-gamma t^2), which dominates
+// either way for the wide arguments (up to ~60) of the outer Gaussians.
 struct RadialConst {
-    float r_cut, inv_r_cut, gamma;
+    float r_cut, inv_r_cut, pi_inv_r_cut, gamma, gamma_l2;
     float mu[NB];
 };
 
-// f_c Phi_k (B) and optionally its r-derivative (dB) for the 7 Gaussians.
+// f_c Phi_k (B) and optionally its r-derivative (dB) for the 7 Gaussians.  The cutoff's
+// cosine and sine take the hardware approximation on [0, pi] (absolute error below 4e-7,
+// against f_c and Phi of order one).
 template <bool DERIV>
 __device__ __forceinline__ void radial_basis(const RadialConst &rc, float r, float (&B)[NB], float (&dB)[NB]) {
     float sp, cp;
-    sincospif(r * rc.inv_r_cut, &sp, &cp);
+    __sincosf(r * rc.pi_inv_r_cut, &sp, &cp);
     const bool inside = r < rc.r_cut;
     const float fc = inside ? 0.5f * (cp + 1.0f) : 0.0f;
-    const float dfc = inside ? -0.5f * 3.14159265358979323846f * rc.inv_r_cut * sp : 0.0f;
+    const float dfc = inside ? -0.5f * rc.pi_inv_r_cut * sp : 0.0f;
 #pragma unroll
     for (int k = 0; k < NB; ++k) {
         const float t = r - rc.mu[k];
-        const float ph = expf(-rc.gamma * t * t);
+        const float ph = exp2f(-rc.gamma_l2 * (t * t));
         B[k] = fc * ph;
-        if (DERIV) dB[k] = dfc * ph - 2.0f * rc.gamma * t * ph * fc;
+        if (DERIV) dB[k] = ph * fmaf(-2.0f * rc.gamma * t, fc, dfc);
+    }
+}
+
+// Coefficient rows beta[zi][zj][s][0..6] staged in shared memory with a stride of BETA_ROW
+// floats (16-byte aligned, two 16-byte loads per row; the stride of 12 spreads the rows
+// over all bank groups).
+constexpr int BETA_ROW = 12;
+__device__ __forceinline__ void stage_beta(const float *__restrict__ beta, int S, float *sb) {
+    const int n = S * S * NR * BETA_ROW;
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+        const int row = q / BETA_ROW, k = q - row * BETA_ROW;
+        sb[q] = k < NB ? beta[row * NB + k] : 0.0f;
+    }
+}
+// R_s = sum_k beta[s][k] B_k (and R'_s from dB) for the five radial functions, from the
+// staged rows of one species pair (bt = sb + (zi S + zj) NR BETA_ROW)
+template <bool DERIV>
+__device__ __forceinline__ void radial_combine(const float *bt, const float (&B)[NB], const float (&dB)[NB],
+                                               float (&R)[NR], float (&Rp)[NR]) {
+#pragma unroll
+    for (int s = 0; s < NR; ++s) {
+        const float4 c0 = *reinterpret_cast<const float4 *>(bt + s * BETA_ROW);
+        const float4 c1 = *reinterpret_cast<const float4 *>(bt + s * BETA_ROW + 4);
+        const float c[NB] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z};
+        float v = 0.0f, w = 0.0f;
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+            v = fmaf(c[k], B[k], v);
+            if (DERIV) w = fmaf(c[k], dB[k], w);
+        }
+        R[s] = v;
+        if (DERIV) Rp[s] = w;
     }
 }
 

@@ -54,15 +54,17 @@ struct NextPair {
     float4 ph, pl;
 };
 
-// Gather pipeline over the pairs p0, p0 + step, ... < p1 of a row: while pair i is computed,
-// the position of pair i + 1 and the index of pair i + 2 are in flight, so the dependent
-// index -> position gather costs no latency inside the loop.
+// Gather pipeline over the pairs p0, p0 + step, ... < p1 of a row, U pairs per call: while
+// pairs i .. i+U-1 are computed, the positions of the next U pairs and the indices of the U
+// after those are in flight, so the dependent index -> position gather costs no latency
+// inside the loop.
+template <int U>
 struct PairPipe {
-    int p1, step, q;          // q: pair whose index is loaded next
-    int jn;                   // index, shift and flag of pair i + 2
-    char4 shn;
-    bool okn;
-    NextPair nx;              // pair i + 1 (position loads issued)
+    int p1, step, q;          // q: first pair whose index is loaded next
+    int jn[U];                // indices, shifts and flags two groups ahead
+    char4 shn[U];
+    bool okn[U];
+    NextPair nx[U];           // the next group (position loads issued)
     __device__ __forceinline__ void index(const PairArgs &a, int p, int &j, char4 &sh, bool &ok) const {
         ok = false;
         if (p < p1) {
@@ -73,27 +75,40 @@ struct PairPipe {
         }
     }
     __device__ __forceinline__ void gather(const PairArgs &a) {
-        if (nx.ok) {
-            nx.ph = a.pos_hi[nx.j];
-            nx.pl = a.pos_lo[nx.j];
-        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (nx[u].ok) {
+                nx[u].ph = a.pos_hi[nx[u].j];
+                nx[u].pl = a.pos_lo[nx[u].j];
+            }
     }
     __device__ __forceinline__ PairPipe(const PairArgs &a, int p0, int p1_, int step_) : p1(p1_), step(step_) {
-        index(a, p0, nx.j, nx.sh, nx.ok);
-        index(a, p0 + step, jn, shn, okn);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            index(a, p0 + u * step, nx[u].j, nx[u].sh, nx[u].ok);
+            index(a, p0 + (U + u) * step, jn[u], shn[u], okn[u]);
+        }
         gather(a);
-        q = p0 + 2 * step;
+        q = p0 + 2 * U * step;
     }
-    // the current pair; the pipeline advances by one
-    __device__ __forceinline__ NextPair next(const PairArgs &a) {
-        const NextPair cur = nx;
-        nx.j = jn;
-        nx.sh = shn;
-        nx.ok = okn;
+    // the current group; the pipeline advances by U pairs
+    __device__ __forceinline__ void next(const PairArgs &a, NextPair (&cur)[U]) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            cur[u] = nx[u];
+            nx[u].j = jn[u];
+            nx[u].sh = shn[u];
+            nx[u].ok = okn[u];
+        }
         gather(a);
-        index(a, q, jn, shn, okn);
-        q += step;
-        return cur;
+#pragma unroll
+        for (int u = 0; u < U; ++u) index(a, q + u * step, jn[u], shn[u], okn[u]);
+        q += U * step;
+    }
+    __device__ __forceinline__ NextPair next(const PairArgs &a) {
+        NextPair cur[U];
+        next(a, cur);
+        return cur[0];
     }
 };
 
@@ -151,9 +166,8 @@ void launch_split_pos(int N, const double *pos, const int32_t *species, float4 *
 
 template <int TPA>
 __global__ void __launch_bounds__(256) k_moments(PairArgs a, float *__restrict__ psi) {
-    extern __shared__ float sbeta[];
-    const int nbeta = a.S * a.S * NR * NB;
-    for (int q = threadIdx.x; q < nbeta; q += blockDim.x) sbeta[q] = a.beta[q];
+    extern __shared__ __align__(16) float sbeta[];
+    stage_beta(a.beta, a.S, sbeta);
     __syncthreads();
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int atom = g / TPA, sub = g % TPA;
@@ -165,34 +179,40 @@ __global__ void __launch_bounds__(256) k_moments(PairArgs a, float *__restrict__
         const int b = structure_of(a.atom_ptr, a.B, atom);
         const Centre ce(a, atom, b);
         const int zsi = clamp_species(a.species[atom], a.S, a.status);
-        const float *brow = sbeta + zsi * a.S * (NR * NB);
+        const float *brow = sbeta + zsi * a.S * (NR * BETA_ROW);
         const int p1 = a.row_ptr[atom + 1];
-        PairPipe pp(a, a.row_ptr[atom] + sub, p1, TPA);
-        for (int p = a.row_ptr[atom] + sub; p < p1; p += TPA) {
-            const NextPair cur = pp.next(a);
-            if (!cur.ok) continue;
-            const int j = cur.j;
-            float fx, fy, fz;
-            ce.displacement(cur, fx, fy, fz);
-            const float r = sqrtf(fx * fx + fy * fy + fz * fz);
-            const float rinv = 1.0f / r;
-            float B[NB], dB[NB];
-            radial_basis<false>(a.rc, r, B, dB);
-            const float *bt = brow + clamp_species(__float_as_int(cur.ph.w), a.S, a.status) * (NR * NB);
-            float R[NR];
+        // two pairs per iteration (independent work for the latency-bound pair math); a
+        // missing second pair contributes exact zeros, so the sums are those of one pair at
+        // a time in row order
+        PairPipe<2> pp(a, a.row_ptr[atom] + sub, p1, TPA);
+        for (int p = a.row_ptr[atom] + sub; p < p1; p += 2 * TPA) {
+            NextPair cur[2];
+            pp.next(a, cur);
+            float R[2][NR], m[2][NC];
 #pragma unroll
-            for (int s = 0; s < NR; ++s) {
-                float v = 0.0f;
+            for (int u = 0; u < 2; ++u) {
+                float fx = 1.0f, fy = 0.0f, fz = 0.0f;
+                int zj = 0;
+                if (cur[u].ok) {
+                    ce.displacement(cur[u], fx, fy, fz);
+                    zj = clamp_species(__float_as_int(cur[u].ph.w), a.S, a.status);
+                }
+                const float r = sqrtf(fx * fx + fy * fy + fz * fz);
+                const float rinv = 1.0f / r;
+                float B[NB], dB[NB];
+                radial_basis<false>(a.rc, r, B, dB);
+                const float w = cur[u].ok ? 1.0f : 0.0f;
+                float Rp[NR];
+                radial_combine<false>(brow + zj * (NR * BETA_ROW), B, dB, R[u], Rp);
 #pragma unroll
-                for (int k = 0; k < NB; ++k) v = fmaf(bt[s * NB + k], B[k], v);
-                R[s] = v;
+                for (int s = 0; s < NR; ++s) R[u][s] *= w;
+                monomials(fx * rinv, fy * rinv, fz * rinv, m[u]);
             }
-            float m[NC];
-            monomials(fx * rinv, fy * rinv, fz * rinv, m);
 #pragma unroll
             for (int s = 0; s < NR; ++s)
 #pragma unroll
-                for (int c = 0; c < NC; ++c) acc[s * NC + c] = fmaf(R[s], m[c], acc[s * NC + c]);
+                for (int c = 0; c < NC; ++c)
+                    acc[s * NC + c] = fmaf(R[1][s], m[1][c], fmaf(R[0][s], m[0][c], acc[s * NC + c]));
         }
     }
     if (TPA >= 8) {
@@ -243,9 +263,8 @@ __global__ void __launch_bounds__(256) k_moments(PairArgs a, float *__restrict__
 template <int TPA>
 __global__ void __launch_bounds__(256) k_forces(PairArgs a, const float *__restrict__ dpsi, float *__restrict__ F,
                                                 float *__restrict__ vir_atom) {
-    extern __shared__ float sbeta[];
-    const int nbeta = a.S * a.S * NR * NB;
-    for (int q = threadIdx.x; q < nbeta; q += blockDim.x) sbeta[q] = a.beta[q];
+    extern __shared__ __align__(16) float sbeta[];
+    stage_beta(a.beta, a.S, sbeta);
     __syncthreads();
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
     const int atom = gt / TPA, sub = gt % TPA;
@@ -265,9 +284,9 @@ __global__ void __launch_bounds__(256) k_forces(PairArgs a, const float *__restr
         const int b = structure_of(a.atom_ptr, a.B, atom);
         const Centre ce(a, atom, b);
         const int zsi = clamp_species(a.species[atom], a.S, a.status);
-        const float *brow = sbeta + zsi * a.S * (NR * NB);
+        const float *brow = sbeta + zsi * a.S * (NR * BETA_ROW);
         const int p1 = a.row_ptr[atom + 1];
-        PairPipe pp(a, a.row_ptr[atom] + sub, p1, TPA);
+        PairPipe<1> pp(a, a.row_ptr[atom] + sub, p1, TPA);
         for (int p = a.row_ptr[atom] + sub; p < p1; p += TPA) {
             const NextPair cur = pp.next(a);
             if (!cur.ok) continue;
@@ -279,19 +298,9 @@ __global__ void __launch_bounds__(256) k_forces(PairArgs a, const float *__restr
             const float ux = fx * rinv, uy = fy * rinv, uz = fz * rinv;
             float B[NB], dB[NB];
             radial_basis<true>(a.rc, r, B, dB);
-            const float *bt = brow + clamp_species(__float_as_int(cur.ph.w), a.S, a.status) * (NR * NB);
             float R[NR], Rp[NR];
-#pragma unroll
-            for (int s = 0; s < NR; ++s) {
-                float v = 0.0f, w = 0.0f;
-#pragma unroll
-                for (int k = 0; k < NB; ++k) {
-                    v = fmaf(bt[s * NB + k], B[k], v);
-                    w = fmaf(bt[s * NB + k], dB[k], w);
-                }
-                R[s] = v;
-                Rp[s] = w;
-            }
+            radial_combine<true>(brow + clamp_species(__float_as_int(cur.ph.w), a.S, a.status) * (NR * BETA_ROW), B,
+                                 dB, R, Rp);
             float m[NC];
             monomials(ux, uy, uz, m);
             float S1 = 0.0f, S2 = 0.0f, Q0 = 0.0f, Q1 = 0.0f, Q2 = 0.0f;
@@ -349,9 +358,8 @@ __global__ void __launch_bounds__(256) k_forces(PairArgs a, const float *__restr
 template <int TPA>
 __global__ void __launch_bounds__(256) k_moments_tangent(PairArgs a, const float *__restrict__ vel,
                                                          float *__restrict__ psid) {
-    extern __shared__ float sbeta[];
-    const int nbeta = a.S * a.S * NR * NB;
-    for (int q = threadIdx.x; q < nbeta; q += blockDim.x) sbeta[q] = a.beta[q];
+    extern __shared__ __align__(16) float sbeta[];
+    stage_beta(a.beta, a.S, sbeta);
     __syncthreads();
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int atom = g / TPA, sub = g % TPA;
@@ -364,9 +372,9 @@ __global__ void __launch_bounds__(256) k_moments_tangent(PairArgs a, const float
         const Centre ce(a, atom, b);
         const float vix = vel[3 * atom], viy = vel[3 * atom + 1], viz = vel[3 * atom + 2];
         const int zsi = clamp_species(a.species[atom], a.S, a.status);
-        const float *brow = sbeta + zsi * a.S * (NR * NB);
+        const float *brow = sbeta + zsi * a.S * (NR * BETA_ROW);
         const int p1 = a.row_ptr[atom + 1];
-        PairPipe pp(a, a.row_ptr[atom] + sub, p1, TPA);
+        PairPipe<1> pp(a, a.row_ptr[atom] + sub, p1, TPA);
         for (int p = a.row_ptr[atom] + sub; p < p1; p += TPA) {
             const NextPair cur = pp.next(a);
             if (!cur.ok) continue;
@@ -380,19 +388,11 @@ __global__ void __launch_bounds__(256) k_moments_tangent(PairArgs a, const float
             const float w = ux * ddx + uy * ddy + uz * ddz;
             float B[NB], dB[NB];
             radial_basis<true>(a.rc, r, B, dB);
-            const float *bt = brow + clamp_species(__float_as_int(cur.ph.w), a.S, a.status) * (NR * NB);
             float R[NR], Rp[NR];
+            radial_combine<true>(brow + clamp_species(__float_as_int(cur.ph.w), a.S, a.status) * (NR * BETA_ROW), B,
+                                 dB, R, Rp);
 #pragma unroll
-            for (int s = 0; s < NR; ++s) {
-                float x = 0.0f, y = 0.0f;
-#pragma unroll
-                for (int k = 0; k < NB; ++k) {
-                    x = fmaf(bt[s * NB + k], B[k], x);
-                    y = fmaf(bt[s * NB + k], dB[k], y);
-                }
-                R[s] = x;
-                Rp[s] = y * w;
-            }
+            for (int s = 0; s < NR; ++s) Rp[s] *= w;
             float m[NC];
             monomials(ux, uy, uz, m);
 #pragma unroll
@@ -454,7 +454,7 @@ __global__ void __launch_bounds__(256) k_pg_beta(PairArgs a, const float *__rest
         const float vix = vel[3 * atom], viy = vel[3 * atom + 1], viz = vel[3 * atom + 2];
         const int zsi = clamp_species(a.species[atom], a.S, a.status);
         const int p1 = a.row_ptr[atom + 1];
-        PairPipe pp(a, a.row_ptr[atom] + lane, p1, 32);
+        PairPipe<1> pp(a, a.row_ptr[atom] + lane, p1, 32);
         for (int p = a.row_ptr[atom] + lane; p < p1; p += 32) {
             const NextPair cur = pp.next(a);
             if (!cur.ok) continue;
@@ -510,12 +510,25 @@ __global__ void __launch_bounds__(256) k_pg_beta(PairArgs a, const float *__rest
     for (int q = threadIdx.x; q < nbeta; q += blockDim.x) part[(size_t)blockIdx.x * nbeta + q] = acc[q];
 }
 
+// shared memory of the staged coefficient rows (61 KB for 16 species: above the default
+// 48 KB, so the kernels opt in once)
+static size_t beta_smem_bytes(int S) { return sizeof(float) * (size_t)S * S * NR * BETA_ROW; }
+template <typename Kern>
+static void allow_beta_smem(Kern kernel) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)beta_smem_bytes(MAX_S));
+}
+
 template <int TPA>
 static void launch_moments_t(const PairArgs &a, float *psi, cudaStream_t st) {
     const int threads = 256;
     const long long total = (long long)a.N * TPA;
     const int blocks = (int)((total + threads - 1) / threads);
-    const size_t smem = sizeof(float) * a.S * a.S * NR * NB;
+    const size_t smem = beta_smem_bytes(a.S);
+    static bool attr = false;
+    if (!attr) {
+        allow_beta_smem(k_moments<TPA>);
+        attr = true;
+    }
     if (blocks > 0) {
         k_moments<TPA><<<blocks, threads, smem, st>>>(a, psi);
         note_launches(1);
@@ -527,7 +540,12 @@ static void launch_forces_t(const PairArgs &a, const float *dpsi, float *F, floa
     const int threads = 256;
     const long long total = (long long)a.N * TPA;
     const int blocks = (int)((total + threads - 1) / threads);
-    const size_t smem = sizeof(float) * a.S * a.S * NR * NB;
+    const size_t smem = beta_smem_bytes(a.S);
+    static bool attr = false;
+    if (!attr) {
+        allow_beta_smem(k_forces<TPA>);
+        attr = true;
+    }
     if (blocks > 0) {
         k_forces<TPA><<<blocks, threads, smem, st>>>(a, dpsi, F, vir);
         note_launches(1);
@@ -564,7 +582,12 @@ void launch_moments_tangent(const PairArgs &a, const float *vel, float *psid, cu
     const int threads = 256, TPA = 4;
     const long long total = (long long)a.N * TPA;
     const int blocks = (int)((total + threads - 1) / threads);
-    const size_t smem = sizeof(float) * a.S * a.S * NR * NB;
+    const size_t smem = beta_smem_bytes(a.S);
+    static bool attr = false;
+    if (!attr) {
+        allow_beta_smem(k_moments_tangent<TPA>);
+        attr = true;
+    }
     if (blocks > 0) {
         k_moments_tangent<TPA><<<blocks, threads, smem, st>>>(a, vel, psid);
         note_launches(1);
