@@ -216,7 +216,8 @@ int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
 struct EfWs {
     float *psi, *dpsi, *G, *A1, *D1, *dZ2, *dZ1, *dG, *nn_part, *vir_atom;
-    double *red_part;
+    unsigned long long *red_acc;   // fixed-point structure sums (cleared by the position split)
+    int n_red_acc;
     float4 *pos_hi, *pos_lo;   // hi/lo FP32 split of the positions (pair displacements)
 };
 
@@ -236,7 +237,8 @@ EfWs carve_ef(Carve &c, int B, int N, int H) {
     w.dG = c.take<float>(m1 * NFP);
     w.nn_part = c.take<float>(m1 * (H / 32));
     w.vir_atom = c.take<float>(n1 * 9);
-    w.red_part = c.take<double>(reduce_partial_doubles(B, N));
+    w.red_acc = c.take<unsigned long long>(reduce_acc_words(B));
+    w.n_red_acc = (int)reduce_acc_words(B);
     return w;
 }
 
@@ -506,6 +508,8 @@ gm_status gm_build_neighbors(const gm_model *m, const gm_system *sys, gm_nlist *
     return launch_status();
 }
 
+// forces_to_clear (the step's force output) and, with it, the structure-sum accumulators are
+// cleared by the position-split kernel
 static gm_status forward_to_features(const gm_model *m, const gm_system *sys, const gm_nlist *nl, EfWs &w,
                                      float *psi_out, float *features_out, float *forces_to_clear, int32_t *status,
                                      cudaStream_t st) {
@@ -515,7 +519,8 @@ static gm_status forward_to_features(const gm_model *m, const gm_system *sys, co
     float *psi = psi_out ? psi_out : w.psi;
     {
         StageScope sc(ST_MOMENTS, st);
-        launch_split_pos(N, sys->pos, sys->species, w.pos_hi, w.pos_lo, forces_to_clear, st);
+        launch_split_pos(N, sys->pos, sys->species, w.pos_hi, w.pos_lo, forces_to_clear,
+                         forces_to_clear ? w.red_acc : nullptr, w.n_red_acc, st);
         launch_moments(a, choose_tpa(m, N), psi, st);
     }
     {
@@ -635,7 +640,7 @@ gm_status gm_energy_forces(const gm_model *m, const gm_system *sys, const gm_nli
     }
     StageScope sc(ST_REDUCE, st);
     launch_struct_reduce(B, N, sys->atom_ptr, sys->species, m->S, m->sigma, m->mu, m->b3, w.nn_part, H / 32,
-                         virial ? w.vir_atom : nullptr, w.red_part, energy, virial, st);
+                         virial ? w.vir_atom : nullptr, w.red_acc, energy, virial, st);
     return launch_status();
 }
 
@@ -674,7 +679,7 @@ gm_status gm_param_grad(const gm_model *m, const gm_system *sys, const gm_nlist 
     PairArgs a = pair_args(m, sys, nl, w.pos_hi, w.pos_lo, status);
     {   // primal and tangent moments, features and their tangents
         StageScope sc(ST_PG_PAIR_FWD, st);
-        launch_split_pos(N, sys->pos, sys->species, w.pos_hi, w.pos_lo, nullptr, st);
+        launch_split_pos(N, sys->pos, sys->species, w.pos_hi, w.pos_lo, nullptr, nullptr, 0, st);
         launch_moments(a, choose_tpa(m, N), w.psi, st);
         launch_moments_tangent(a, dL_dF, w.psid, st);
         launch_contract_fwd_dual(w.psi, w.psid, N, Mp, w.GG, st);

@@ -138,8 +138,11 @@ struct Centre {
 // the force kernel accumulates into, when given
 __global__ void __launch_bounds__(256) k_split_pos(int N, const double *__restrict__ pos,
                                                    const int32_t *__restrict__ species, float4 *__restrict__ hi,
-                                                   float4 *__restrict__ lo, float *__restrict__ zero_F) {
+                                                   float4 *__restrict__ lo, float *__restrict__ zero_F,
+                                                   unsigned long long *__restrict__ zero_acc, int n_acc) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (zero_acc)
+        for (int q = i; q < n_acc; q += gridDim.x * blockDim.x) zero_acc[q] = 0ull;
     if (i >= N) return;
     if (zero_F) {
         zero_F[3 * i] = 0.0f;
@@ -158,9 +161,9 @@ __global__ void __launch_bounds__(256) k_split_pos(int N, const double *__restri
 }
 
 void launch_split_pos(int N, const double *pos, const int32_t *species, float4 *hi, float4 *lo, float *zero_F,
-                      cudaStream_t st) {
+                      unsigned long long *zero_acc, int n_acc, cudaStream_t st) {
     if (N <= 0) return;
-    k_split_pos<<<(N + 255) / 256, 256, 0, st>>>(N, pos, species, hi, lo, zero_F);
+    k_split_pos<<<(N + 255) / 256, 256, 0, st>>>(N, pos, species, hi, lo, zero_F, zero_acc, n_acc);
     note_launches(1);
 }
 

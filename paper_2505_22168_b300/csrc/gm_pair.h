@@ -21,10 +21,10 @@ struct PairArgs {
 };
 
 // pos_hi[i] = (float)pos[i], pos_lo[i] = (float)(pos[i] - pos_hi[i]) per axis; pos_hi[i].w
-// holds the bits of species[i] (lo w = 0).  zero_F [N][3], if not null, is cleared for the
-// force kernel's accumulation.
+// holds the bits of species[i] (lo w = 0).  zero_F [N][3] and zero_acc [n_acc], if not null,
+// are cleared (the force kernel's and the structure reduction's accumulators).
 void launch_split_pos(int N, const double *pos, const int32_t *species, float4 *hi, float4 *lo, float *zero_F,
-                      cudaStream_t st);
+                      unsigned long long *zero_acc, int n_acc, cudaStream_t st);
 void launch_moments(const PairArgs &a, int tpa, float *psi, cudaStream_t st);
 void launch_forces(const PairArgs &a, int tpa, const float *dpsi, float *F, float *vir_atom, cudaStream_t st);
 

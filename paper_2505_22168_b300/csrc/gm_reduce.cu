@@ -1,9 +1,9 @@
-// gm_reduce.cu -- per-structure FP64 reductions and the force-matching loss.
+// gm_reduce.cu -- per-structure reductions and the force-matching loss.
 //
 //   E_i = sigma_Z (sum of output-layer partials + b3) + mu_Z      (Eq. scale_shift)
-//   E_b = sum_{i in b} E_i in FP64                               (Eq. energy_sum)
-//   W_b = sum_{i in b} W_i in FP64 (per-atom virials from the force kernel)
-// Sums run over fixed chunks of atoms and then over chunks in order (deterministic).
+//   E_b = sum_{i in b} E_i                                       (Eq. energy_sum)
+//   W_b = sum_{i in b} W_i (per-atom virials from the force kernel)
+// Sums in 64-bit fixed point (exact, deterministic), returned as FP64.
 //   loss (section "Training": energy and force terms, per-atom division of the energy term)
 // One block per structure, fixed summation order (deterministic).
 #include "gm_internal.h"
@@ -24,93 +24,106 @@ __device__ __forceinline__ double block_sum_double(double v, double *sh) {
     return r;  // valid in thread 0
 }
 
-// Phase 1: block k takes atoms [k*CH, (k+1)*CH), one atom per thread: E_i (and the
-// per-atom virial) go to shared memory, then one warp per structure overlapping the chunk
-// sums its run and stores the partial at slot (b + k).  Consecutive chunks share at most
-// one structure, so these slots never collide and structure b finds its partials at
-// b + k for the chunks k it spans.  Phase 2 adds them in chunk order (deterministic).
-__global__ void __launch_bounds__(REDUCE_CHUNK) k_reduce_partial(int B, int N, const int32_t *__restrict__ atom_ptr,
-                                                                 const int32_t *__restrict__ species, int S,
-                                                                 const float *__restrict__ sigma,
-                                                                 const float *__restrict__ mu,
-                                                                 const float *__restrict__ b3,
-                                                                 const float *__restrict__ nn_part, int nparts,
-                                                                 const float *__restrict__ vir_atom, double *part) {
-    __shared__ float vals[10][REDUCE_CHUNK];
-    const int k = blockIdx.x;
-    const int c0 = k * REDUCE_CHUNK, c1 = min(N, c0 + REDUCE_CHUNK);
-    const int i = c0 + threadIdx.x;
-    if (i < c1) {
+// One pass over the atoms.  Thread i forms E_i (and takes the per-atom virial) in FP32 and
+// converts each value to a 64-bit fixed-point integer in units of 2^-24 (the scaling by a
+// power of two is exact; the rounding to the unit is below 3e-8 eV per atom).  Lanes of a
+// warp that belong to the same structure add their integers with shuffles and one lane adds
+// the result to the structure's accumulator with a 64-bit atomic.  Integer sums are exact,
+// so the totals do not depend on the order of the atomics (deterministic), and they equal
+// the FP64 sum of the per-atom values to within the unit.  The block that finishes last
+// (ticket counter after a device-scope fence, no waiting) converts the totals to FP64,
+// writes energy and virial, and resets the accumulators and the counter.  The accumulators
+// start from zero: the position-split kernel of the same step clears them.  A value that is
+// not finite or exceeds 1e9 in magnitude (a diverged model) is counted in an eleventh word
+// per structure instead, and that structure's results come out as NaN, as an FP64 sum would.
+constexpr float FIX_ONE = 16777216.0f;        // 2^24
+constexpr double FIX_INV = 1.0 / 16777216.0;
+constexpr int RW = 11;                         // accumulator words per structure
+__device__ __forceinline__ long long to_fixed(float x, bool &bad) {
+    if (!(fabsf(x) < 1e9f)) {
+        bad = true;
+        return 0;
+    }
+    return __float2ll_rn(x * FIX_ONE);
+}
+
+__global__ void __launch_bounds__(REDUCE_CHUNK) k_reduce(int B, int N, const int32_t *__restrict__ atom_ptr,
+                                                         const int32_t *__restrict__ species, int S,
+                                                         const float *__restrict__ sigma, const float *__restrict__ mu,
+                                                         const float *__restrict__ b3,
+                                                         const float *__restrict__ nn_part, int nparts,
+                                                         const float *__restrict__ vir_atom,
+                                                         unsigned long long *acc, double *energy, double *virial) {
+    __shared__ bool last;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31;
+    const int nv = vir_atom ? 10 : 1;
+    long long v[10];
+#pragma unroll
+    for (int q = 0; q < 10; ++q) v[q] = 0;
+    int b = -1;
+    bool bad = false;
+    if (i < N) {
         float nn = b3[0];
         for (int t = 0; t < nparts; ++t) nn += nn_part[(size_t)i * nparts + t];
         const int z = min(max(species[i], 0), S - 1);
-        vals[0][threadIdx.x] = fmaf(sigma[z], nn, mu[z]);
+        v[0] = to_fixed(fmaf(sigma[z], nn, mu[z]), bad);
+        if (vir_atom)
 #pragma unroll
-        for (int q = 0; q < 9; ++q) vals[1 + q][threadIdx.x] = vir_atom ? vir_atom[(size_t)i * 9 + q] : 0.0f;
+            for (int q = 0; q < 9; ++q) v[1 + q] = to_fixed(vir_atom[(size_t)i * 9 + q], bad);
+        b = structure_of(atom_ptr, B, i);
+    }
+    unsigned todo = __ballot_sync(0xffffffffu, b >= 0);
+    while (todo) {                                   // one round per structure present in the warp
+        const int lead = __ffs(todo) - 1;
+        const int bl = __shfl_sync(0xffffffffu, b, lead);
+        const bool mine = b == bl;
+        todo &= ~__ballot_sync(0xffffffffu, mine);
+        for (int q = 0; q < nv; ++q) {
+            long long x = mine ? v[q] : 0;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+            if (lane == lead) atomicAdd(acc + (size_t)bl * RW + q, (unsigned long long)x);
+        }
+        if (__any_sync(0xffffffffu, mine && bad) && lane == lead) atomicAdd(acc + (size_t)bl * RW + 10, 1ull);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned long long ticket = atomicAdd(acc + (size_t)B * RW, 1ull);
+        last = ticket == (unsigned long long)(gridDim.x - 1);
     }
     __syncthreads();
-    const int bf = structure_of(atom_ptr, B, c0), bl = structure_of(atom_ptr, B, c1 - 1);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int b = bf + warp; b <= bl; b += REDUCE_CHUNK / 32) {
-        const int lo = max(atom_ptr[b], c0) - c0, hi = min(atom_ptr[b + 1], c1) - c0;
-        double acc[10];
-#pragma unroll
-        for (int q = 0; q < 10; ++q) acc[q] = 0.0;
-        for (int t = lo + lane; t < hi; t += 32)
-#pragma unroll
-            for (int q = 0; q < 10; ++q) acc[q] += (double)vals[q][t];
-#pragma unroll
-        for (int q = 0; q < 10; ++q)
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) acc[q] += __shfl_down_sync(0xffffffffu, acc[q], off);
-        if (lane == 0)
-#pragma unroll
-            for (int q = 0; q < 10; ++q) part[(size_t)(b + k) * 10 + q] = acc[q];
-    }
-}
-
-// Phase 2: one block per structure.  Lane l < 30 of warp w reads component l % 10 of chunks
-// k0 + 3w + l / 10, k0 + 3w + l / 10 + 24, ...; the 24 running sums per component are then
-// added in a fixed order (deterministic for a given structure size).
-constexpr int RF_THREADS = 256, RF_LANES = 24;
-__global__ void __launch_bounds__(RF_THREADS) k_reduce_final(int B, const int32_t *__restrict__ atom_ptr,
-                                                             const double *__restrict__ part, double *energy,
-                                                             double *virial) {
-    __shared__ double sh[RF_LANES][10];
-    const int b = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int a0 = atom_ptr[b], a1 = atom_ptr[b + 1];
-    const int sub = warp * 3 + lane / 10, q = lane % 10;
-    if (lane < 30) {
-        double s = 0.0;
-        if (a1 > a0)
-            for (int k = a0 / REDUCE_CHUNK + sub; k <= (a1 - 1) / REDUCE_CHUNK; k += RF_LANES)
-                s += part[(size_t)(b + k) * 10 + q];
-        sh[sub][q] = s;
+    if (!last) return;
+    __threadfence();
+    for (int q = threadIdx.x; q < B * 10; q += blockDim.x) {
+        const int s = q / 10, c = q - s * 10;
+        if (c >= nv) continue;
+        const long long x = (long long)atomicExch(acc + (size_t)s * RW + c, 0ull);
+        const bool nan = atomicAdd(acc + (size_t)s * RW + 10, 0ull) != 0ull;
+        const double val = nan ? __longlong_as_double(0x7ff8000000000000ll) : (double)x * FIX_INV;
+        if (c == 0) energy[s] = val;
+        else virial[9 * s + c - 1] = val;
     }
     __syncthreads();
-    if (threadIdx.x < 10) {
-        double s = 0.0;
-        for (int t = 0; t < RF_LANES; ++t) s += sh[t][threadIdx.x];
-        if (threadIdx.x == 0) energy[b] = s;
-        else if (virial) virial[9 * b + threadIdx.x - 1] = s;
-    }
+    for (int s = threadIdx.x; s < B; s += blockDim.x) atomicExch(acc + (size_t)s * RW + 10, 0ull);
+    if (threadIdx.x == 0) atomicExch(acc + (size_t)B * RW, 0ull);
 }
 
-size_t reduce_partial_doubles(int B, int N) { return (size_t)(B + (N + REDUCE_CHUNK - 1) / REDUCE_CHUNK + 1) * 10; }
+size_t reduce_acc_words(int B) { return (size_t)B * RW + 1; }
 
 void launch_struct_reduce(int B, int N, const int32_t *atom_ptr, const int32_t *species, int S, const float *sigma,
                           const float *mu, const float *b3, const float *nn_part, int nparts, const float *vir_atom,
-                          double *part, double *energy, double *virial, cudaStream_t st) {
-    const int chunks = (N + REDUCE_CHUNK - 1) / REDUCE_CHUNK;
-    if (chunks > 0) {
-        k_reduce_partial<<<chunks, REDUCE_CHUNK, 0, st>>>(B, N, atom_ptr, species, S, sigma, mu, b3, nn_part, nparts, vir_atom,
-                                                 part);
-        note_launches(1);
+                          unsigned long long *acc, double *energy, double *virial, cudaStream_t st) {
+    if (B <= 0) return;
+    if (N <= 0) {                                    // no atoms: every structure sums to zero
+        cudaMemsetAsync(energy, 0, sizeof(double) * B, st);
+        if (virial) cudaMemsetAsync(virial, 0, sizeof(double) * 9 * B, st);
+        return;
     }
-    if (B > 0) {
-        k_reduce_final<<<B, RF_THREADS, 0, st>>>(B, atom_ptr, part, energy, virial);
-        note_launches(1);
-    }
+    k_reduce<<<(N + REDUCE_CHUNK - 1) / REDUCE_CHUNK, REDUCE_CHUNK, 0, st>>>(B, N, atom_ptr, species, S, sigma, mu, b3,
+                                                                            nn_part, nparts, vir_atom, acc, energy,
+                                                                            virial);
+    note_launches(1);
 }
 
 // Force-matching loss: one block; FP64 accumulation in a fixed order.

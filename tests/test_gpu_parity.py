@@ -391,6 +391,36 @@ def test_energy_forces_deterministic_energy():
     assert float(E1.item()) == float(E2.item())
 
 
+def test_batched_energies_and_virials_are_deterministic(li_small):
+    """Structure sums are exact integer sums (fixed point): repeated steps on a ragged batch
+    give identical energies and virials although the order of the block atomics varies."""
+    b, d, p = li_small
+    m, sysd, nl = _nl_pair(b, d, p)
+    runs = [m.energy_forces(sysd, nl, virial=True) for _ in range(3)]
+    for E, _, W in runs[1:]:
+        assert torch.equal(E, runs[0][0]) and torch.equal(W, runs[0][2])
+
+
+def test_diverged_energy_comes_out_nan():
+    """A per-atom energy beyond the fixed-point range (here an energy shift of 2e9 for one
+    species) makes the structures holding that species NaN instead of wrapping around."""
+    b1, d, p = synth.config(1)
+    spec1 = np.ones_like(b1.species)                     # a copy of the box without species 0
+    b = make_batch([(b1.pos, b1.species, b1.cell[0]), (b1.pos, spec1, b1.cell[0]),
+                    (b1.pos, b1.species, b1.cell[0])], d["n_species"])
+    p = dict(p)
+    p["mu"] = np.array(p["mu"], dtype=np.float64).copy()
+    p["mu"][0] = 2e9
+    m, sysd, nl = _nl_pair(b, d, p)
+    E, _, W = m.energy_forces(sysd, nl, virial=True)
+    m.check_status()
+    has0 = [bool((b.species[b.atom_ptr[k]:b.atom_ptr[k + 1]] == 0).any()) for k in range(b.n_structures)]
+    E = E.cpu().numpy()
+    assert any(has0)
+    for k in range(b.n_structures):
+        assert np.isnan(E[k]) == has0[k]
+
+
 # ------------------------------------------------------------------ full size
 
 def test_full_size_li3po4_sampled_rows_and_properties():
