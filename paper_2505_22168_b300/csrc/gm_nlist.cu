@@ -98,6 +98,8 @@ struct NlArgs {
     NlStruct *S;
     int32_t *ncells;        // device scalar: cells of all structures
     int32_t *cellid, *ccount, *cstart, *cfill, *unsorted, *counts, *bsum, *mimg;
+    int32_t *cstruct;       // structure of each cell (filled while binning)
+    int32_t *item_ctr;      // [2] work-item counters of the block-level search passes (zeroed per build)
     uint32_t *xsm;          // image counts of the sorted atoms (bytes3 of mimg)
     uint32_t *mpk;          // image counts by atom index (bytes3 of mimg)
     uint32_t *slab;         // single-pass search: row i at i * maxn, entries j | shift code << 27
@@ -382,6 +384,12 @@ __device__ void ph_bin(const NlArgs &a, int bid, int nb, const NlStruct *S) {
         a.mpk[i] = bytes3(a.mimg[3 * i], a.mimg[3 * i + 1], a.mimg[3 * i + 2]);
         atomicAdd(a.ccount + cid, 1);
     }
+    // cell -> structure table for the search passes
+    for (int b = bid; b < a.B; b += nb) {
+        const NlStruct &q = S[b];
+        const int ncb = q.nc[0] * q.nc[1] * q.nc[2];
+        for (int c = threadIdx.x; c < ncb; c += NL_THREADS) a.cstruct[q.cell0 + c] = b;
+    }
 }
 
 // ------------------------------------------------------------------ scan
@@ -492,17 +500,11 @@ __device__ void ph_sort(const NlArgs &a, int bid, int nb) {
 }
 
 // ------------------------------------------------------------------ search
-__device__ __forceinline__ int structure_of_cell(const NlStruct *S, int B, int c) {
-    int lo = 0, hi = B - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (S[mid].cell0 <= c) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
-// Exact FP64 membership test of candidate j of centre i under the image (nx, ny, nz).
-__device__ __forceinline__ bool exact_inside(const double *__restrict__ xw, int j, double xi0, double xi1, double xi2,
+// Exact FP64 membership test of candidate j of centre i under the image (nx, ny, nz).  Kept
+// out of line and reached through a warp vote, so that the rare test is a real branch and
+// not predicated FP64 code issued with every candidate test (B300 issues FP64 at a small
+// fraction of the FP32 rate).
+__device__ __noinline__ bool exact_inside(const double *__restrict__ xw, int j, double xi0, double xi1, double xi2,
                                              int nx, int ny, int nz, const NlStruct &q, double rc2) {
     const double d0 = __dadd_rn(__dsub_rn(xw[3 * j], xi0), __dmul_rn((double)nx, q.L[0]));
     const double d1 = __dadd_rn(__dsub_rn(xw[3 * j + 1], xi1), __dmul_rn((double)ny, q.L[1]));
@@ -631,8 +633,10 @@ __device__ __forceinline__ void test_chunk(const NlArgs &a, const float4 *home, 
         const float r2 = fx * fx + fy * fy + fz * fz;
         const bool other = SELF ? (valid && selfj != hi) : valid;
         bool in = other && r2 < lo2;
-        if (other && !in && r2 <= hi2)                                   // inside the band: exact FP64 test
-            in = exact_inside(a.xw, j, a.xw[3 * hi], a.xw[3 * hi + 1], a.xw[3 * hi + 2], n0, n1, n2, q, rc2);
+        const bool band = other && !in && r2 <= hi2;                     // inside the band: exact FP64 test
+        if (__any_sync(full, band)) {
+            if (band) in = exact_inside(a.xw, j, a.xw[3 * hi], a.xw[3 * hi + 1], a.xw[3 * hi + 2], n0, n1, n2, q, rc2);
+        }
         const unsigned ball = __ballot_sync(full, in);
         if (MODE == SM_COUNT) {
             if (lane == h) hacc += __popc(ball);
@@ -685,7 +689,7 @@ __device__ void ph_search(const NlArgs &a, int bid, int nb, float4 *smem) {
         const int c = it / a.split, part = it - c * a.split;
         const int h0 = a.cstart[c], nh = a.cstart[c + 1] - h0;
         if (part >= nh) continue;                                  // uniform over the warp
-        const NlStruct &q = a.S[structure_of_cell(a.S, a.B, c)];
+        const NlStruct &q = a.S[a.cstruct[c]];
         const int cl = c - q.cell0;
         if (!(q.K[0] == 1 && q.K[1] == 1 && q.K[2] == 1)) {
             // several images per stencil direction: per-atom search (with a slab, the
@@ -848,12 +852,16 @@ __device__ void ph_search(const NlArgs &a, int bid, int nb, float4 *smem) {
 // atoms.  Items with more candidates than fit take the per-atom search.
 constexpr int NL_BCAND = NL_WARPS * NL_WIN;
 
+// Items are claimed from a counter (one per pass) rather than dealt in a fixed order: item
+// costs vary by an order of magnitude over a batch of boxes of different sizes, and a fixed
+// deal left the slowest block at twice the mean.  Thread 0 claims the next item while the
+// block works on the current one.
 template <int MODE>
 __device__ void ph_search_block(const NlArgs &a, int bid, int nb, float4 *smem) {
     __shared__ int s_k0[27], s_off[28];
     __shared__ unsigned s_n[27];
     __shared__ float s_sh[27][3];
-    __shared__ int s_skip;
+    __shared__ int s_skip, s_item;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float4 *s_home = nl_home_smem(smem) + 32 * warp;
     float4 *cand = smem;
@@ -864,13 +872,23 @@ __device__ void ph_search_block(const NlArgs &a, int bid, int nb, float4 *smem) 
     if (s_skip) return;                                            // uniform over the block
     const int items = *a.ncells * a.split;
     const double rc2 = __dmul_rn(a.rc, a.rc);
-    for (int it = bid; it < items; it += nb) {
+    int32_t *ctr = a.item_ctr + (MODE == SM_FILL ? 1 : 0);
+    if (threadIdx.x == 0) s_item = atomicAdd(ctr, 1);
+    __syncthreads();
+    for (int it = s_item; it < items; it = s_item) {
+        int next = 0;
+        if (threadIdx.x == 0) next = atomicAdd(ctr, 1);           // consumed at the end of the item
         const int c = it / a.split, part = it - c * a.split;
         const int h0 = a.cstart[c], nh = a.cstart[c + 1] - h0;
-        if (part >= nh) continue;                                  // uniform over the block
-        const NlStruct &q = a.S[structure_of_cell(a.S, a.B, c)];
+        const NlStruct &q = a.S[a.cstruct[c]];
         const int cl = c - q.cell0;
         const bool tiled = q.K[0] == 1 && q.K[1] == 1 && q.K[2] == 1;
+        if (part >= nh) {                                          // uniform over the block
+            __syncthreads();
+            if (threadIdx.x == 0) s_item = next;
+            __syncthreads();
+            continue;
+        }
         int T = 0;
         if (tiled) {
             if (warp == 0) {
@@ -921,6 +939,8 @@ __device__ void ph_search_block(const NlArgs &a, int bid, int nb, float4 *smem) 
                     if (MODE == SM_SLAB && lane == 0) nl_redo(a, __float_as_int(me.w));
                 }
             }
+            __syncthreads();
+            if (threadIdx.x == 0) s_item = next;
             __syncthreads();
             continue;
         }
@@ -1021,6 +1041,8 @@ __device__ void ph_search_block(const NlArgs &a, int bid, int nb, float4 *smem) 
             __syncwarp();
         }
         __syncthreads();                                           // the staging is rewritten next
+        if (threadIdx.x == 0) s_item = next;
+        __syncthreads();
     }
 }
 
@@ -1075,7 +1097,7 @@ __device__ void ph_compact(const NlArgs &a, int bid, int nb, const int32_t *row_
     for (int r = gw; r < nredo; r += nw) {
         const int i = a.redo_list[r];
         const int c = a.cellid[i];
-        const NlStruct &q = a.S[structure_of_cell(a.S, a.B, c)];
+        const NlStruct &q = a.S[a.cstruct[c]];
         const float4 me = make_float4((float)a.xw[3 * i], (float)a.xw[3 * i + 1], (float)a.xw[3 * i + 2],
                                       __int_as_float(i));
         search_atom_generic<true>(a, q, c - q.cell0, me, lane, row_ptr[i]);
@@ -1185,6 +1207,7 @@ __global__ void __launch_bounds__(NL_THREADS, 2) k_nl_phase(NlArgs a, int ph) {
 struct NlWs {
     NlStruct *S;
     int32_t *ncells, *mimg, *cellid, *ccount, *cstart, *cfill, *unsorted, *counts, *bsum, *redo_list, *n_redo;
+    int32_t *cstruct, *item_ctr;
     uint32_t *xsm, *mpk;
     uint8_t *redo;
     uint32_t *slab;
@@ -1205,6 +1228,8 @@ static NlWs carve_nl(Carve &c, int B, int N) {
     w.cellid = c.take<int32_t>(n1);
     w.ccount = c.take<int32_t>(ncmax + 64);                        // histogram, then the barrier words
     w.bar = reinterpret_cast<unsigned *>(w.ccount + ncmax + 32);
+    w.item_ctr = w.ccount + ncmax + 40;                            // search item counters (same memset)
+    w.cstruct = c.take<int32_t>(ncmax);
     w.cstart = c.take<int32_t>(ncmax + 1);
     w.cfill = c.take<int32_t>(ncmax);
     w.unsorted = c.take<int32_t>(n1);
@@ -1302,6 +1327,8 @@ gm_status nl_build(const gm_system &sys, double r_cut, int n_species, gm_nlist &
     a.S = w.S;
     a.ncells = w.ncells;
     a.cellid = w.cellid;
+    a.cstruct = w.cstruct;
+    a.item_ctr = w.item_ctr;
     a.ccount = w.ccount;
     a.cstart = w.cstart;
     a.cfill = w.cfill;
