@@ -112,16 +112,19 @@ nv = _Nvml()
 h = nv.handle(sys.argv[1], int(sys.argv[2]))
 print("max", nv.max_clock(h), flush=True)
 while True:
-    print("s", nv.clock(h), nv.reasons(h), nv.power_w(h), flush=True)
-    r, _, _ = select.select([sys.stdin], [], [], 0.01)
+    print("s", time.monotonic(), nv.clock(h), nv.reasons(h), nv.power_w(h), flush=True)
+    r, _, _ = select.select([sys.stdin], [], [], 0.005)
     if r:
         break
 """
 
 
 class ClockSampler:
-    """SM clock, power and clock-event reasons sampled every 10 ms through NVML (read only)
-    by a child process while the timed region runs (no contention with the launch loop)."""
+    """SM clock, power and clock-event reasons sampled about every 5 ms through NVML (read
+    only) by a child process while the timed region runs (no contention with the launch
+    loop).  The region starts once the child has taken its first sample; samples carry the
+    child's monotonic time and the summary keeps those inside the region, plus the first one
+    after it when the region is shorter than the sampling interval."""
 
     REASONS = {"hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40,
                "sw_power_cap": 0x4}
@@ -130,6 +133,7 @@ class ClockSampler:
         self.proc = None
         self.lines = []
         self.error = None
+        self.t0 = self.t1 = None
         self.uuid, self.index = "", torch_device
         try:
             import torch
@@ -143,8 +147,14 @@ class ClockSampler:
             self.proc = subprocess.Popen([sys.executable, "-c", _SAMPLER_CHILD, self.uuid, str(self.index), str(ROOT)],
                                          stdin=subprocess.PIPE, stdout=subprocess.PIPE, stderr=subprocess.PIPE,
                                          text=True)
-            first = self.proc.stdout.readline()      # wait until sampling has started
-            self.lines.append(first)
+            while True:                               # wait until sampling has started
+                line = self.proc.stdout.readline()
+                if not line:
+                    break
+                self.lines.append(line)
+                if line.startswith("s "):
+                    break
+            self.t0 = time.monotonic()
         except Exception as exc:
             self.error = f"{type(exc).__name__}: {exc}"
             self.proc = None
@@ -153,6 +163,8 @@ class ClockSampler:
     def __exit__(self, *exc):
         if self.proc is None:
             return
+        self.t1 = time.monotonic()
+        time.sleep(0.03)                              # let a sample after the region land
         try:
             out, err = self.proc.communicate(input="stop\n", timeout=10)
             self.lines += out.splitlines()
@@ -170,12 +182,20 @@ class ClockSampler:
                 continue
             if p[0] == "max" and len(p) > 1 and p[1] != "None":
                 max_mhz = int(p[1])
-            elif p[0] == "s" and len(p) >= 4 and p[1] != "None":
-                clks.append(int(p[1]))
-                r = int(p[2])
-                reasons |= {name for name, bit in self.REASONS.items() if r & bit}
-                if p[3] != "None":
-                    powers.append(float(p[3]))
+        samples = []
+        for line in self.lines:
+            p = line.split()
+            if len(p) >= 5 and p[0] == "s" and p[2] != "None":
+                samples.append((float(p[1]), int(p[2]), int(p[3]), None if p[4] == "None" else float(p[4])))
+        if self.t0 is not None and self.t1 is not None:
+            inside = [s for s in samples if self.t0 <= s[0] <= self.t1]
+            after = [s for s in samples if s[0] > self.t1][:1]
+            samples = inside if len(inside) >= 2 else inside + after
+        for _, clk, r, pw in samples:
+            clks.append(clk)
+            reasons |= {name for name, bit in self.REASONS.items() if r & bit}
+            if pw is not None:
+                powers.append(pw)
         if not clks:
             return {"sm_mhz": None, "sm_max_mhz": max_mhz, "reasons": ["unavailable"], "samples": 0,
                     "error": self.error}
