@@ -844,6 +844,17 @@ __device__ void ph_search(const NlArgs &a, int bid, int nb, float4 *smem) {
     }
 }
 
+// stencil cell (0..26) of staged candidate e, from the cells' exclusive offsets off[0..27]
+__device__ __forceinline__ int stencil_of(int e, const int *off) {
+    int st = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+        const int t = st + step;
+        if (t <= 26 && off[t] <= e) st = t;
+    }
+    return st;
+}
+
 // Block-level variant of the search passes (small systems, where the warp-level one leaves
 // most of the GPU idle and restages the same candidates for every part of a cell): a work
 // item = (cell, part) per block; warp 0 builds the stencil, all 256 threads stage the item's
@@ -863,10 +874,9 @@ __device__ void ph_search_block(const NlArgs &a, int bid, int nb, float4 *smem) 
     __shared__ float s_sh[27][3];
     __shared__ int s_skip, s_item;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float4 *s_home = nl_home_smem(smem) + 32 * warp;
     float4 *cand = smem;
     unsigned *cinfo = reinterpret_cast<unsigned *>(smem + NL_BCAND);
-    const unsigned full = 0xffffffffu;
+    const unsigned full = 0xffffffffu, below = (1u << lane) - 1u;
     if (threadIdx.x == 0) s_skip = MODE == SM_FILL && status_bad(a.status);
     __syncthreads();
     if (s_skip) return;                                            // uniform over the block
@@ -982,6 +992,9 @@ __device__ void ph_search_block(const NlArgs &a, int bid, int nb, float4 *smem) 
                         info |= (v & NL_FAR) ? 32u : (v << 8);
                     }
                     cand[e] = make_float4(o[u].x + s_sh[st][0], o[u].y + s_sh[st][1], o[u].z + s_sh[st][2], o[u].w);
+                    // uniform single-pass items stage the complete slab entry (index | shift code)
+                    if (MODE == SM_SLAB && uni)
+                        info = (unsigned)__float_as_int(o[u].w) | (shift_code((info & 32u) ? NL_FAR : (info >> 8)) << 27);
                     cinfo[e] = info;
                 }
             }
@@ -990,55 +1003,74 @@ __device__ void ph_search_block(const NlArgs &a, int bid, int nb, float4 *smem) 
         const int home_lo = s_off[NL_HOME_STENCIL], home_hi = s_off[NL_HOME_STENCIL + 1];
         const float lo2 = a.rc2f - q.eps2, hi2 = a.rc2f + q.eps2;
         const int nhp = (nh - part + a.split - 1) / a.split;       // home atoms of the item
-        // warp w: home atoms r = w, w + 8, ... of the item, up to 32 at a time
-        for (int g0 = warp; g0 < nhp; g0 += NL_WARPS * 32) {
-            const int ng = min(32, (nhp - g0 + NL_WARPS - 1) / NL_WARPS);
-            int hidx = 0, hacc = 0;
-            unsigned hmb = 0;
+        // Warp w takes home atoms r = w, w + 8, ... of the item, one at a time against all T
+        // candidates in chunks of 32: the row offset is a warp-uniform register and the home
+        // position is the staged copy from the home stencil cell (shift 0), so the chunk loop
+        // has no shuffles and no global loads.
+        for (int r = warp; r < nhp; r += NL_WARPS) {
+            const int hl = part + a.split * r;                     // index within the home cell
+            const float4 hv = cand[home_lo + hl];
+            const int hi = __float_as_int(hv.w);
+            const unsigned hmb = (MODE != SM_COUNT && !uni) ? a.xsm[h0 + hl] : 0u;
+            const int rb = MODE == SM_FILL ? a.row_ptr[hi] : 0;
+            int cnt = 0;
             bool hredo = false;
-            if (lane < ng) {
-                const int hk = h0 + part + a.split * (g0 + NL_WARPS * lane);
-                const float4 hv = a.xs[hk];
-                hidx = __float_as_int(hv.w);
-                s_home[lane] = hv;
-                if (MODE != SM_COUNT) hmb = a.xsm[hk];
-                if (MODE == SM_FILL) hacc = a.row_ptr[hidx];
-            }
-            __syncwarp();
             for (int base = 0; base < T; base += 32) {
-                const int el = base + lane;
-                const bool valid = el < T;
+                const int e = base + lane;
+                const bool valid = e < T;
                 float4 cv = make_float4(3.0e30f, 3.0e30f, 3.0e30f, 0.0f);
-                unsigned info = 0;
+                unsigned w = 0;
                 if (valid) {
-                    cv = cand[el];
-                    info = cinfo[el];
+                    cv = cand[e];
+                    w = cinfo[e];
                 }
                 const int j = __float_as_int(cv.w);
-                const unsigned n = s_n[info & 31u];
-                const int n0 = byte_at(n, 0), n1 = byte_at(n, 1), n2 = byte_at(n, 2);
-                const bool self = base < home_hi && base + 32 > home_lo;
-                if (uni) {
-                    if (self)
-                        test_chunk<MODE, true, true>(a, s_home, ng, cv, valid, j, info, n0, n1, n2, lo2, hi2, q,
-                                                     rc2, lane, hacc, hmb, hredo);
-                    else
-                        test_chunk<MODE, false, true>(a, s_home, ng, cv, valid, j, info, n0, n1, n2, lo2, hi2, q,
-                                                      rc2, lane, hacc, hmb, hredo);
-                } else if (MODE != SM_COUNT) {
-                    test_chunk<MODE, true, false>(a, s_home, ng, cv, valid, j, info, n0, n1, n2, lo2, hi2, q,
-                                                  rc2, lane, hacc, hmb, hredo);
+                const float fx = cv.x - hv.x, fy = cv.y - hv.y, fz = cv.z - hv.z;
+                const float r2 = fx * fx + fy * fy + fz * fz;
+                const bool other = valid && !(j == hi && e >= home_lo && e < home_hi);
+                bool in = other && r2 < lo2;
+                const bool band = other && !in && r2 <= hi2;          // inside the band: exact FP64 test
+                if (__any_sync(full, band)) {
+                    if (band) {
+                        const unsigned n = s_n[stencil_of(e, s_off)];
+                        in = exact_inside(a.xw, j, a.xw[3 * hi], a.xw[3 * hi + 1], a.xw[3 * hi + 2], byte_at(n, 0),
+                                          byte_at(n, 1), byte_at(n, 2), q, rc2);
+                    }
                 }
+                const unsigned ball = __ballot_sync(full, in);
+                if (MODE != SM_COUNT && in) {
+                    const int pos = cnt + __popc(ball & below);
+                    const unsigned vb = (w & 32u) ? NL_FAR : (w >> 8);
+                    if (MODE == SM_SLAB) {
+                        const unsigned ent =
+                            uni ? w : ((unsigned)j | (shift_code(bytes3_add(vb, hmb)) << 27));
+                        hredo |= (ent >> 27) == NL_NOCODE;
+                        if (pos < a.maxn) a.slab[(size_t)hi * a.maxn + pos] = ent;
+                    } else {
+                        unsigned sh = uni ? vb : bytes3_add(vb, hmb);
+                        if (sh & NL_FAR) {
+                            const unsigned n = s_n[stencil_of(e, s_off)];
+                            sh = shift_slow(a, hi, j, byte_at(n, 0), byte_at(n, 1), byte_at(n, 2));
+                        }
+                        if (sh & NL_FAR) {
+                            set_status(a.status, GM_ERR_UNSUPPORTED);
+                            sh = 0;
+                        }
+                        a.col[rb + pos] = j;
+                        reinterpret_cast<unsigned *>(a.shift)[rb + pos] = sh;
+                    }
+                }
+                cnt += __popc(ball);
             }
-            if (MODE != SM_FILL && lane < ng) {
-                a.counts[hidx] = hacc;
+            hredo = __any_sync(full, hredo);
+            if (MODE != SM_FILL && lane == 0) {
+                a.counts[hi] = cnt;
                 if (MODE == SM_SLAB) {
-                    const bool over = hacc > a.maxn || hredo;
-                    a.redo[hidx] = over ? 1 : 0;
-                    if (over) nl_redo(a, hidx);
+                    const bool over = cnt > a.maxn || hredo;
+                    a.redo[hi] = over ? 1 : 0;
+                    if (over) nl_redo(a, hi);
                 }
             }
-            __syncwarp();
         }
         __syncthreads();                                           // the staging is rewritten next
         if (threadIdx.x == 0) s_item = next;
