@@ -954,7 +954,9 @@ __device__ void ph_search_block(const NlArgs &a, int bid, int nb, float4 *smem) 
             __syncthreads();
             continue;
         }
-        // stage all candidates of the item (loads before stores)
+        // stage all candidates of the item (loads before stores), then pad to a multiple of
+        // 32 with far-away dummies (no bounds test in the chunk loop)
+        bool nocode_seen = false;
         for (int e0 = threadIdx.x; e0 < T; e0 += NL_THREADS * 4) {
             float4 o[4];
             unsigned pm[4];
@@ -993,14 +995,24 @@ __device__ void ph_search_block(const NlArgs &a, int bid, int nb, float4 *smem) 
                     }
                     cand[e] = make_float4(o[u].x + s_sh[st][0], o[u].y + s_sh[st][1], o[u].z + s_sh[st][2], o[u].w);
                     // uniform single-pass items stage the complete slab entry (index | shift code)
-                    if (MODE == SM_SLAB && uni)
-                        info = (unsigned)__float_as_int(o[u].w) | (shift_code((info & 32u) ? NL_FAR : (info >> 8)) << 27);
+                    if (MODE == SM_SLAB && uni) {
+                        const unsigned code = shift_code((info & 32u) ? NL_FAR : (info >> 8));
+                        nocode_seen |= code == NL_NOCODE;
+                        info = (unsigned)__float_as_int(o[u].w) | (code << 27);
+                    }
                     cinfo[e] = info;
                 }
             }
         }
+        const int Tp = (T + 31) & ~31;
+        if (threadIdx.x < Tp - T) {
+            cand[T + threadIdx.x] = make_float4(3.0e30f, 3.0e30f, 3.0e30f, 0.0f);
+            cinfo[T + threadIdx.x] = 0u;
+        }
+        // rows that meet a shift outside {-1, 0, 1}^3 need the redo; uniform items know it here
+        const bool check_codes = MODE == SM_SLAB && (!uni || __syncthreads_or(nocode_seen));
         __syncthreads();
-        const int home_lo = s_off[NL_HOME_STENCIL], home_hi = s_off[NL_HOME_STENCIL + 1];
+        const int home_lo = s_off[NL_HOME_STENCIL];
         const float lo2 = a.rc2f - q.eps2, hi2 = a.rc2f + q.eps2;
         const int nhp = (nh - part + a.split - 1) / a.split;       // home atoms of the item
         // Warp w takes home atoms r = w, w + 8, ... of the item, one at a time against all T
@@ -1009,25 +1021,22 @@ __device__ void ph_search_block(const NlArgs &a, int bid, int nb, float4 *smem) 
         // has no shuffles and no global loads.
         for (int r = warp; r < nhp; r += NL_WARPS) {
             const int hl = part + a.split * r;                     // index within the home cell
-            const float4 hv = cand[home_lo + hl];
+            const int self_e = home_lo + hl;                       // the home atom's own staged copy
+            const float4 hv = cand[self_e];
             const int hi = __float_as_int(hv.w);
             const unsigned hmb = (MODE != SM_COUNT && !uni) ? a.xsm[h0 + hl] : 0u;
             const int rb = MODE == SM_FILL ? a.row_ptr[hi] : 0;
+            uint32_t *srow = MODE == SM_SLAB ? a.slab + (size_t)hi * a.maxn : nullptr;
             int cnt = 0;
             bool hredo = false;
-            for (int base = 0; base < T; base += 32) {
+            for (int base = 0; base < Tp; base += 32) {
                 const int e = base + lane;
-                const bool valid = e < T;
-                float4 cv = make_float4(3.0e30f, 3.0e30f, 3.0e30f, 0.0f);
-                unsigned w = 0;
-                if (valid) {
-                    cv = cand[e];
-                    w = cinfo[e];
-                }
+                const float4 cv = cand[e];
+                const unsigned w = cinfo[e];
                 const int j = __float_as_int(cv.w);
                 const float fx = cv.x - hv.x, fy = cv.y - hv.y, fz = cv.z - hv.z;
                 const float r2 = fx * fx + fy * fy + fz * fz;
-                const bool other = valid && !(j == hi && e >= home_lo && e < home_hi);
+                const bool other = e != self_e;
                 bool in = other && r2 < lo2;
                 const bool band = other && !in && r2 <= hi2;          // inside the band: exact FP64 test
                 if (__any_sync(full, band)) {
@@ -1044,8 +1053,8 @@ __device__ void ph_search_block(const NlArgs &a, int bid, int nb, float4 *smem) 
                     if (MODE == SM_SLAB) {
                         const unsigned ent =
                             uni ? w : ((unsigned)j | (shift_code(bytes3_add(vb, hmb)) << 27));
-                        hredo |= (ent >> 27) == NL_NOCODE;
-                        if (pos < a.maxn) a.slab[(size_t)hi * a.maxn + pos] = ent;
+                        if (check_codes) hredo |= (ent >> 27) == NL_NOCODE;
+                        if (pos < a.maxn) srow[pos] = ent;
                     } else {
                         unsigned sh = uni ? vb : bytes3_add(vb, hmb);
                         if (sh & NL_FAR) {
@@ -1062,7 +1071,7 @@ __device__ void ph_search_block(const NlArgs &a, int bid, int nb, float4 *smem) 
                 }
                 cnt += __popc(ball);
             }
-            hredo = __any_sync(full, hredo);
+            if (check_codes) hredo = __any_sync(full, hredo);
             if (MODE != SM_FILL && lane == 0) {
                 a.counts[hi] = cnt;
                 if (MODE == SM_SLAB) {
