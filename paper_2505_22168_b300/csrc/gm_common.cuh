@@ -82,6 +82,13 @@ __host__ __device__ constexpr int f7_index(int s1, int s2, int s3) {  // s1 <= s
 }
 __host__ __device__ constexpr int f8_index(int s1, int s2, int s3) { return (s1 * NR + s2) * NR + s3; }
 
+// ---------------------------------------------------------------- dependent launch
+// Wait for the predecessor kernels of a programmatic dependent launch (no-op otherwise).
+// The next kernel is released implicitly as this grid's blocks exit: releasing it early
+// (griddepcontrol.launch_dependents at the start) helped the 1536-atom step by 2 us but slowed
+// multi-wave grids by up to 20 % on B300.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // ---------------------------------------------------------------- status word
 __device__ __forceinline__ void set_status(int32_t *st, int32_t code) {
     if (st) atomicCAS(st, 0, code);

@@ -867,6 +867,7 @@ __global__ void __launch_bounds__(W * 32) k_contract_fwd(const float *__restrict
     float *tile = smf + CT_ATOMS * NPSI;           // [32][GT_STRIDE] features
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * CT_ATOMS;
+    griddep_wait();
     stage_psi<W * 32>(psi, m0, N, ptile);
     __syncthreads();
     const float *row = ptile + lane * NPSI;
@@ -924,6 +925,7 @@ __global__ void __launch_bounds__(W * 32) k_contract_bwd(const float *__restrict
     float *gtile = slots + W * CT_ATOMS * NPSI;            // [32][GT_STRIDE] dE/dG
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * CT_ATOMS;
+    griddep_wait();
     stage_psi<W * 32>(psi, m0, N, ptile);
     {
         float4 *mine = reinterpret_cast<float4 *>(slots + warp * CT_ATOMS * NPSI);
@@ -1149,8 +1151,8 @@ static void launch_fwd_items(const float *psi, int N, int Mp, OutT *G, float *fe
         attr = true;
     }
     if (blocks > 0) {
-        k_contract_fwd<OutT, CT_FWD_W><<<blocks, CT_FWD_W * 32, ct_fwd_smem(), st>>>(psi, N, Mp, G, features_out,
-                                                                                     lo_out);
+        launch_pdl(k_contract_fwd<OutT, CT_FWD_W>, dim3(blocks), dim3(CT_FWD_W * 32), ct_fwd_smem(), st, psi, N, Mp, G,
+                   features_out, lo_out);
         note_launches(1);
     }
 }
@@ -1173,7 +1175,7 @@ void launch_contract_bwd(const float *psi, const float *dG, int N, float *dpsi, 
         attr = true;
     }
     if (blocks > 0) {
-        k_contract_bwd<CT_BWD_W><<<blocks, CT_BWD_W * 32, ct_bwd_smem(), st>>>(psi, dG, N, dpsi);
+        launch_pdl(k_contract_bwd<CT_BWD_W>, dim3(blocks), dim3(CT_BWD_W * 32), ct_bwd_smem(), st, psi, dG, N, dpsi);
         note_launches(1);
     }
 }

@@ -12,6 +12,7 @@ constexpr int SB_M = 128, SB_N = 64, SB_K = 16;
 template <int EPI, int ACT>
 __global__ void __launch_bounds__(256) k_gemm_f32(const float *__restrict__ A, const float *__restrict__ B, int M,
                                                   int N, int K, EpiArgs e) {
+    griddep_wait();
     __shared__ __align__(16) float As[2][SB_K][SB_M + 4];
     __shared__ __align__(16) float Bs[2][SB_K][SB_N + 4];
     const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
@@ -106,8 +107,8 @@ __global__ void __launch_bounds__(256) k_gemm_f32(const float *__restrict__ A, c
 template <int EPI>
 static void launch_act(int act, dim3 g, const float *A, const float *B, int M, int N, int K, const EpiArgs &e,
                        cudaStream_t st) {
-    if (act == 0) k_gemm_f32<EPI, 0><<<g, 256, 0, st>>>(A, B, M, N, K, e);
-    else k_gemm_f32<EPI, 1><<<g, 256, 0, st>>>(A, B, M, N, K, e);
+    if (act == 0) launch_pdl(k_gemm_f32<EPI, 0>, g, dim3(256), 0, st, A, B, M, N, K, e);
+    else launch_pdl(k_gemm_f32<EPI, 1>, g, dim3(256), 0, st, A, B, M, N, K, e);
 }
 
 void gemm_f32(int epi, int act, const float *A, const float *B, int M, int N, int K, const EpiArgs &e,
@@ -118,8 +119,8 @@ void gemm_f32(int epi, int act, const float *A, const float *B, int M, int N, in
     switch (epi) {
     case EPI_L1: launch_act<EPI_L1>(act, g, A, B, M, N, K, e, st); break;
     case EPI_L2: launch_act<EPI_L2>(act, g, A, B, M, N, K, e, st); break;
-    case EPI_B1: k_gemm_f32<EPI_B1, 0><<<g, 256, 0, st>>>(A, B, M, N, K, e); break;
-    default: k_gemm_f32<EPI_STORE, 0><<<g, 256, 0, st>>>(A, B, M, N, K, e); break;
+    case EPI_B1: launch_pdl(k_gemm_f32<EPI_B1, 0>, g, dim3(256), 0, st, A, B, M, N, K, e); break;
+    default: launch_pdl(k_gemm_f32<EPI_STORE, 0>, g, dim3(256), 0, st, A, B, M, N, K, e); break;
     }
 }
 

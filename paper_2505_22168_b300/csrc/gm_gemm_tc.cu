@@ -67,7 +67,7 @@ cudaError_t launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, int M, int N
         attr_set = true;
     }
     dim3 grid(N / BN, M / tc::BM);
-    tc::k_gemm_tc<BN, EPI, ACT, CPS><<<grid, 256, smem, st>>>(ma, mb, M, N, K, split, e, status);
+    launch_pdl(tc::k_gemm_tc<BN, EPI, ACT, CPS>, grid, dim3(256), smem, st, ma, mb, M, N, K, split, e, status);
     return cudaPeekAtLastError();
 }
 

@@ -333,6 +333,7 @@ __global__ void __launch_bounds__(256, CPS)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    griddep_wait();                         // operands and epilogue inputs come from earlier kernels
 
     if (warp == 0 && lane == 0) {
         // ---------------- TMA producer

@@ -35,6 +35,28 @@ enum Stage {
     ST_NL_SCAN, ST_NL_FILL, ST_NL_COOP, N_STAGES
 };
 void note_launches(int n);
+
+// Programmatic dependent launch: the kernel may be scheduled while its predecessor on the
+// stream drains (its launch latency and any independent prologue overlap the predecessor's
+// tail).  Every kernel launched this way calls griddep_wait() before it reads or writes
+// global memory that earlier kernels of the stream use; the wait returns once those kernels
+// have completed and their writes are visible (and at once when there is no predecessor).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 struct StageScope {
     int stage;
     cudaStream_t st;

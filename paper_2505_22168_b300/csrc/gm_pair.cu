@@ -140,6 +140,7 @@ __global__ void __launch_bounds__(256) k_split_pos(int N, const double *__restri
                                                    const int32_t *__restrict__ species, float4 *__restrict__ hi,
                                                    float4 *__restrict__ lo, float *__restrict__ zero_F,
                                                    unsigned long long *__restrict__ zero_acc, int n_acc) {
+    griddep_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (zero_acc)
         for (int q = i; q < n_acc; q += gridDim.x * blockDim.x) zero_acc[q] = 0ull;
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(256) k_split_pos(int N, const double *__restri
 void launch_split_pos(int N, const double *pos, const int32_t *species, float4 *hi, float4 *lo, float *zero_F,
                       unsigned long long *zero_acc, int n_acc, cudaStream_t st) {
     if (N <= 0) return;
-    k_split_pos<<<(N + 255) / 256, 256, 0, st>>>(N, pos, species, hi, lo, zero_F, zero_acc, n_acc);
+    launch_pdl(k_split_pos, dim3((N + 255) / 256), dim3(256), 0, st, N, pos, species, hi, lo, zero_F, zero_acc, n_acc);
     note_launches(1);
 }
 
@@ -171,6 +172,7 @@ template <int TPA>
 __global__ void __launch_bounds__(256) k_moments(PairArgs a, float *__restrict__ psi) {
     extern __shared__ __align__(16) float sbeta[];
     stage_beta(a.beta, a.S, sbeta);
+    griddep_wait();
     __syncthreads();
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int atom = g / TPA, sub = g % TPA;
@@ -268,6 +270,7 @@ __global__ void __launch_bounds__(256) k_forces(PairArgs a, const float *__restr
                                                 float *__restrict__ vir_atom) {
     extern __shared__ __align__(16) float sbeta[];
     stage_beta(a.beta, a.S, sbeta);
+    griddep_wait();
     __syncthreads();
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
     const int atom = gt / TPA, sub = gt % TPA;
@@ -363,6 +366,7 @@ __global__ void __launch_bounds__(256) k_moments_tangent(PairArgs a, const float
                                                          float *__restrict__ psid) {
     extern __shared__ __align__(16) float sbeta[];
     stage_beta(a.beta, a.S, sbeta);
+    griddep_wait();
     __syncthreads();
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int atom = g / TPA, sub = g % TPA;
@@ -533,7 +537,7 @@ static void launch_moments_t(const PairArgs &a, float *psi, cudaStream_t st) {
         attr = true;
     }
     if (blocks > 0) {
-        k_moments<TPA><<<blocks, threads, smem, st>>>(a, psi);
+        launch_pdl(k_moments<TPA>, dim3(blocks), dim3(threads), smem, st, a, psi);
         note_launches(1);
     }
 }
@@ -550,7 +554,7 @@ static void launch_forces_t(const PairArgs &a, const float *dpsi, float *F, floa
         attr = true;
     }
     if (blocks > 0) {
-        k_forces<TPA><<<blocks, threads, smem, st>>>(a, dpsi, F, vir);
+        launch_pdl(k_forces<TPA>, dim3(blocks), dim3(threads), smem, st, a, dpsi, F, vir);
         note_launches(1);
     }
 }

@@ -55,6 +55,7 @@ __global__ void __launch_bounds__(REDUCE_CHUNK) k_reduce(int B, int N, const int
                                                          const float *__restrict__ vir_atom,
                                                          unsigned long long *acc, double *energy, double *virial) {
     __shared__ bool last;
+    griddep_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31;
     const int nv = vir_atom ? 10 : 1;
     long long v[10];
@@ -120,9 +121,8 @@ void launch_struct_reduce(int B, int N, const int32_t *atom_ptr, const int32_t *
         if (virial) cudaMemsetAsync(virial, 0, sizeof(double) * 9 * B, st);
         return;
     }
-    k_reduce<<<(N + REDUCE_CHUNK - 1) / REDUCE_CHUNK, REDUCE_CHUNK, 0, st>>>(B, N, atom_ptr, species, S, sigma, mu, b3,
-                                                                            nn_part, nparts, vir_atom, acc, energy,
-                                                                            virial);
+    launch_pdl(k_reduce, dim3((N + REDUCE_CHUNK - 1) / REDUCE_CHUNK), dim3(REDUCE_CHUNK), 0, st, B, N, atom_ptr, species,
+               S, sigma, mu, b3, nn_part, nparts, vir_atom, acc, energy, virial);
     note_launches(1);
 }
 
