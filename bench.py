@@ -238,7 +238,8 @@ def algorithmic_work(stage, n_atoms, n_pairs, H):
         # positions in, sorted copies, CSR out (col 4 B + shift 4 B per pair)
         return 24.0 * n_atoms * 3 + 8.0 * n_pairs + 4.0 * n_atoms, "byte"
     if stage == "reduce":
-        return 4.0 * n_atoms * (H // 64 + 2), "byte"
+        # output-layer partials (H / 32 per atom) and the species index in
+        return 4.0 * n_atoms * (H // 32 + 1), "byte"
     return 0.0, "flop"
 
 
