@@ -11,38 +11,23 @@
 //   #7 (Psi3_s1)_abc (Psi3_s2)_abd (Psi2_s3)_cd s1<=s2     75
 //   #8 (Psi1_s1)_a (Psi3_s2)_abc (Psi2_s3)_bc  all         125  (printed in Eq. contraction)
 //
-// Layout: a block holds 32 atoms (one per lane) and 8 warps; warp w evaluates feature
-// group w for all 32 atoms, so every warp runs one code path.  The forward and backward
-// kernels are capped at 128 registers so that two blocks share an SM: the latency-bound
-// group code gains more from the second block than it loses to the few spills (measured on
-// B300 at 16,384 atoms: backward 105 -> 63 us, forward 39 -> 28 us; three blocks spill too
-// much).  Groups: 0 = #1-#4,
-// 1 = #5, 2 = #6, 3-5 = #7 split by s1 ({0}, {1,4}, {2,3}), 6-7 = #8 split by s2
-// ({0,1}, {2,3,4}).  The 360 features of the 32 atoms are staged in shared memory and
-// written as coalesced rows of the [M][384] GEMM operand (columns 360..383 are zero).
-//
-// Backward: each group accumulates its contribution to dE/dPsi (unique components, 100
-// per atom) in registers, using full-tensor index loops whose writes land in the unique
-// accumulators (this sums all index permutations, i.e. the gradient with respect to
-// the unique component); the 8 partial gradients are added in a fixed group order.
+// Layout: a block holds 32 atoms (lane = atom) whose moments are staged in shared memory;
+// its warps walk a list of work items (one family restricted to one radial index or index
+// pair, see the item kernels below).  The 360 features of the 32 atoms are staged in shared
+// memory and written as coalesced rows of the [M][384] GEMM operand (columns 360..383 are
+// zero).  Backward: dE/dPsi over the unique components (100 per atom), with full-tensor
+// index loops whose writes land in unique accumulators (this sums all index permutations,
+// i.e. the gradient with respect to the unique component); per-warp partial gradients are
+// added in warp order.  The parameter gradient runs the same items on dual numbers.
 #include "gm_contract.h"
 
 namespace gm {
 
 constexpr int CT_ATOMS = 32;
-constexpr int CT_THREADS = 256;
 constexpr int GT_STRIDE = NF + 1;
-constexpr int AC_STRIDE = NPSI + 1;
-
-#define PV(s, a) P[(s) * NC + idx1(a)]
-#define PM(s, a, b) P[(s) * NC + idx2(a, b)]
-#define PT(s, a, b, c) P[(s) * NC + idx3(a, b, c)]
-#define AV(s, a) A[(s) * NC + idx1(a)]
-#define AM(s, a, b) A[(s) * NC + idx2(a, b)]
-#define AT(s, a, b, c) A[(s) * NC + idx3(a, b, c)]
 
 // Forward-mode dual number (value, derivative along a tangent direction).  The features
-// are polynomials of the moments, so running the same group code on duals gives exact
+// are polynomials of the moments, so running the same item code on duals gives exact
 // tangents (parameter gradient: dG along dPsi, and the second-order term of the adjoint).
 struct Dual {
     float v, d;
@@ -66,333 +51,6 @@ struct FeatOut {
     __device__ __forceinline__ void put(int f, float x) const { v[f] = x; }
     __device__ __forceinline__ void put(int f, Dual x) const { v[f] = x.v; d[f] = x.d; }
 };
-
-__host__ __device__ constexpr bool f7_group_has(int part, int s1) {
-    return part == 3 ? s1 == 0 : (part == 4 ? (s1 == 1 || s1 == 4) : (s1 == 2 || s1 == 3));
-}
-__host__ __device__ constexpr bool f8_group_has(int part, int s2) { return part == 6 ? s2 <= 1 : s2 >= 2; }
-
-__device__ __forceinline__ void load_psi(const float *__restrict__ psi, int m, int N, float (&P)[NPSI]) {
-    if (m < N) {
-        const float4 *p4 = reinterpret_cast<const float4 *>(psi + (size_t)m * NPSI);
-#pragma unroll
-        for (int q = 0; q < NPSI / 4; ++q) {
-            const float4 v = p4[q];
-            P[4 * q] = v.x; P[4 * q + 1] = v.y; P[4 * q + 2] = v.z; P[4 * q + 3] = v.w;
-        }
-    } else {
-#pragma unroll
-        for (int q = 0; q < NPSI; ++q) P[q] = 0.0f;
-    }
-}
-
-// ------------------------------------------------------------------ forward groups
-template <int PART, typename T>
-__device__ __forceinline__ void fwd_group(const T (&P)[NPSI], const FeatOut &gt) {
-    if (PART == 0) {
-#pragma unroll
-        for (int s = 0; s < NR; ++s) gt.put(FAM_OFF1 + s, P[s * NC]);
-#pragma unroll
-        for (int s1 = 0; s1 < NR; ++s1)
-#pragma unroll
-            for (int s2 = s1; s2 < NR; ++s2) {
-                T f2 = zero<T>(), f3 = zero<T>(), f4 = zero<T>();
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    f2 = mad(PV(s1, a), PV(s2, a), f2);
-#pragma unroll
-                    for (int b = 0; b < 3; ++b) {
-                        f3 = mad(PM(s1, a, b), PM(s2, a, b), f3);
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) f4 = mad(PT(s1, a, b, c), PT(s2, a, b, c), f4);
-                    }
-                }
-                const int q = pair_le_index(s1, s2);
-                gt.put(FAM_OFF2 + q, f2);
-                gt.put(FAM_OFF3 + q, f3);
-                gt.put(FAM_OFF4 + q, f4);
-            }
-    } else if (PART == 1) {
-        // fixed trip counts with guards: triangular bounds left the loops rolled and the
-        // moments in local memory
-#pragma unroll
-        for (int s1 = 0; s1 < NR; ++s1)
-#pragma unroll
-            for (int s2 = 0; s2 < NR; ++s2) {
-                if (s2 < s1) continue;
-                T Nm[3][3];
-#pragma unroll
-                for (int a = 0; a < 3; ++a)
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        T v = zero<T>();
-#pragma unroll
-                        for (int b = 0; b < 3; ++b) v = mad(PM(s1, a, b), PM(s2, b, c), v);
-                        Nm[a][c] = v;
-                    }
-#pragma unroll
-                for (int s3 = 0; s3 < NR; ++s3) {
-                    if (s3 < s2) continue;
-                    T f = zero<T>();
-#pragma unroll
-                    for (int a = 0; a < 3; ++a)
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) f = mad(Nm[a][c], PM(s3, c, a), f);
-                    gt.put(FAM_OFF5 + f5_index(s1, s2, s3), f);
-                }
-            }
-    } else if (PART == 2) {
-#pragma unroll
-        for (int s2 = 0; s2 < NR; ++s2)
-#pragma unroll
-            for (int s3 = 0; s3 < NR; ++s3) {
-                T w[3];
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    T v = zero<T>();
-#pragma unroll
-                    for (int b = 0; b < 3; ++b) v = mad(PM(s2, a, b), PV(s3, b), v);
-                    w[a] = v;
-                }
-#pragma unroll
-                for (int s1 = 0; s1 <= s3; ++s1) {
-                    T f = zero<T>();
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) f = mad(PV(s1, a), w[a], f);
-                    gt.put(FAM_OFF6 + f6_index(s1, s2, s3), f);
-                }
-            }
-    } else if (PART >= 3 && PART <= 5) {
-#pragma unroll
-        for (int s1 = 0; s1 < NR; ++s1) {
-            if (!f7_group_has(PART, s1)) continue;
-#pragma unroll
-            for (int s2 = s1; s2 < NR; ++s2) {
-                T Q[3][3];
-#pragma unroll
-                for (int c = 0; c < 3; ++c)
-#pragma unroll
-                    for (int d = 0; d < 3; ++d) {
-                        T v = zero<T>();
-#pragma unroll
-                        for (int a = 0; a < 3; ++a)
-#pragma unroll
-                            for (int b = 0; b < 3; ++b) v = mad(PT(s1, a, b, c), PT(s2, a, b, d), v);
-                        Q[c][d] = v;
-                    }
-#pragma unroll
-                for (int s3 = 0; s3 < NR; ++s3) {
-                    T f = zero<T>();
-#pragma unroll
-                    for (int c = 0; c < 3; ++c)
-#pragma unroll
-                        for (int d = 0; d < 3; ++d) f = mad(Q[c][d], PM(s3, c, d), f);
-                    gt.put(FAM_OFF7 + f7_index(s1, s2, s3), f);
-                }
-            }
-        }
-    } else {
-#pragma unroll
-        for (int s2 = 0; s2 < NR; ++s2) {
-            if (!f8_group_has(PART, s2)) continue;
-#pragma unroll
-            for (int s3 = 0; s3 < NR; ++s3) {
-                T U[3];
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    T v = zero<T>();
-#pragma unroll
-                    for (int b = 0; b < 3; ++b)
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) v = mad(PT(s2, a, b, c), PM(s3, b, c), v);
-                    U[a] = v;
-                }
-#pragma unroll
-                for (int s1 = 0; s1 < NR; ++s1) {
-                    T f = zero<T>();
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) f = mad(PV(s1, a), U[a], f);
-                    gt.put(FAM_OFF8 + f8_index(s1, s2, s3), f);
-                }
-            }
-        }
-    }
-}
-
-// ------------------------------------------------------------------ backward groups
-// Backward units: FAM 0 = families #1-#4; FAM 5, 6, 7, 8 = that family restricted by MASK
-// (a bit set per radial index: s1 for #5 and #7, s2 for #6 and #8).
-template <int FAM, int MASK, typename T>
-__device__ __forceinline__ void bwd_unit(const T (&P)[NPSI], const float *gb, T (&A)[NPSI]) {
-    if (FAM == 0) {
-#pragma unroll
-        for (int s = 0; s < NR; ++s) A[s * NC] += gb[FAM_OFF1 + s];
-#pragma unroll
-        for (int s1 = 0; s1 < NR; ++s1)
-#pragma unroll
-            for (int s2 = s1; s2 < NR; ++s2) {
-                const int q = pair_le_index(s1, s2);
-                const float g2 = gb[FAM_OFF2 + q], g3 = gb[FAM_OFF3 + q], g4 = gb[FAM_OFF4 + q];
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    AV(s1, a) = mad(g2, PV(s2, a), AV(s1, a));
-                    AV(s2, a) = mad(g2, PV(s1, a), AV(s2, a));
-#pragma unroll
-                    for (int b = 0; b < 3; ++b) {
-                        AM(s1, a, b) = mad(g3, PM(s2, a, b), AM(s1, a, b));
-                        AM(s2, a, b) = mad(g3, PM(s1, a, b), AM(s2, a, b));
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            AT(s1, a, b, c) = mad(g4, PT(s2, a, b, c), AT(s1, a, b, c));
-                            AT(s2, a, b, c) = mad(g4, PT(s1, a, b, c), AT(s2, a, b, c));
-                        }
-                    }
-                }
-            }
-    } else if (FAM == 5) {
-#pragma unroll
-        for (int s1 = 0; s1 < NR; ++s1)
-#pragma unroll
-            for (int s2 = s1; s2 < NR; ++s2)
-                if ((MASK >> s1) & 1)
-#pragma unroll
-                for (int s3 = s2; s3 < NR; ++s3) {
-                    const float g = gb[FAM_OFF5 + f5_index(s1, s2, s3)];
-#pragma unroll
-                    for (int a = 0; a < 3; ++a)
-#pragma unroll
-                        for (int b = 0; b < 3; ++b) {
-                            T v1 = zero<T>(), v2 = zero<T>(), v3 = zero<T>();
-#pragma unroll
-                            for (int c = 0; c < 3; ++c) {
-                                v1 = mad(PM(s2, a, c), PM(s3, c, b), v1);   // d/d(M1)_ba -> (M2 M3)_ab
-                                v2 = mad(PM(s3, a, c), PM(s1, c, b), v2);   // d/d(M2)_ba -> (M3 M1)_ab
-                                v3 = mad(PM(s1, a, c), PM(s2, c, b), v3);   // d/d(M3)_ba -> (M1 M2)_ab
-                            }
-                            AM(s1, b, a) = mad(g, v1, AM(s1, b, a));
-                            AM(s2, b, a) = mad(g, v2, AM(s2, b, a));
-                            AM(s3, b, a) = mad(g, v3, AM(s3, b, a));
-                        }
-                }
-    } else if (FAM == 6) {
-#pragma unroll
-        for (int s1 = 0; s1 < NR; ++s1)
-#pragma unroll
-            for (int s2 = 0; s2 < NR; ++s2)
-                if ((MASK >> s2) & 1)
-#pragma unroll
-                for (int s3 = s1; s3 < NR; ++s3) {
-                    const float g = gb[FAM_OFF6 + f6_index(s1, s2, s3)];
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        T w13 = zero<T>(), w31 = zero<T>();
-#pragma unroll
-                        for (int b = 0; b < 3; ++b) {
-                            w13 = mad(PM(s2, a, b), PV(s3, b), w13);
-                            w31 = mad(PM(s2, a, b), PV(s1, b), w31);
-                            AM(s2, a, b) = mad(g * PV(s1, a), PV(s3, b), AM(s2, a, b));
-                        }
-                        AV(s1, a) = mad(g, w13, AV(s1, a));
-                        AV(s3, a) = mad(g, w31, AV(s3, a));
-                    }
-                }
-    } else if (FAM == 7) {
-#pragma unroll
-        for (int s1 = 0; s1 < NR; ++s1) {
-            if (!((MASK >> s1) & 1)) continue;
-#pragma unroll
-            for (int s2 = s1; s2 < NR; ++s2) {
-                T Mw[3][3], Q[3][3];
-#pragma unroll
-                for (int c = 0; c < 3; ++c)
-#pragma unroll
-                    for (int d = 0; d < 3; ++d) {
-                        T v = zero<T>(), w = zero<T>();
-#pragma unroll
-                        for (int s3 = 0; s3 < NR; ++s3) w = mad(gb[FAM_OFF7 + f7_index(s1, s2, s3)], PM(s3, c, d), w);
-#pragma unroll
-                        for (int a = 0; a < 3; ++a)
-#pragma unroll
-                            for (int b = 0; b < 3; ++b) v = mad(PT(s1, a, b, c), PT(s2, a, b, d), v);
-                        Mw[c][d] = w;
-                        Q[c][d] = v;
-                    }
-#pragma unroll
-                for (int s3 = 0; s3 < NR; ++s3) {
-                    const float g = gb[FAM_OFF7 + f7_index(s1, s2, s3)];
-#pragma unroll
-                    for (int c = 0; c < 3; ++c)
-#pragma unroll
-                        for (int d = 0; d < 3; ++d) AM(s3, c, d) = mad(g, Q[c][d], AM(s3, c, d));
-                }
-#pragma unroll
-                for (int a = 0; a < 3; ++a)
-#pragma unroll
-                    for (int b = 0; b < 3; ++b)
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            T t1 = zero<T>(), t2 = zero<T>();
-#pragma unroll
-                            for (int d = 0; d < 3; ++d) {
-                                t1 = mad(PT(s2, a, b, d), Mw[c][d], t1);   // d/d(T1)_abc
-                                t2 = mad(PT(s1, a, b, d), Mw[d][c], t2);   // d/d(T2)_abc
-                            }
-                            AT(s1, a, b, c) += t1;
-                            AT(s2, a, b, c) += t2;
-                        }
-            }
-        }
-    } else {
-#pragma unroll
-        for (int s2 = 0; s2 < NR; ++s2) {
-            if (!((MASK >> s2) & 1)) continue;
-#pragma unroll
-            for (int s3 = 0; s3 < NR; ++s3) {
-                T U[3], Vw[3];
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    T v = zero<T>(), w = zero<T>();
-#pragma unroll
-                    for (int b = 0; b < 3; ++b)
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) v = mad(PT(s2, a, b, c), PM(s3, b, c), v);
-#pragma unroll
-                    for (int s1 = 0; s1 < NR; ++s1) w = mad(gb[FAM_OFF8 + f8_index(s1, s2, s3)], PV(s1, a), w);
-                    U[a] = v;
-                    Vw[a] = w;
-                }
-#pragma unroll
-                for (int s1 = 0; s1 < NR; ++s1) {
-                    const float g = gb[FAM_OFF8 + f8_index(s1, s2, s3)];
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) AV(s1, a) = mad(g, U[a], AV(s1, a));
-                }
-#pragma unroll
-                for (int a = 0; a < 3; ++a)
-#pragma unroll
-                    for (int b = 0; b < 3; ++b)
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            AT(s2, a, b, c) = mad(Vw[a], PM(s3, b, c), AT(s2, a, b, c));
-                            AM(s3, b, c) = mad(Vw[a], PT(s2, a, b, c), AM(s3, b, c));
-                        }
-            }
-        }
-    }
-}
-
-// The eight backward groups of the dual kernel (one warp each), as units.
-template <int PART, typename T>
-__device__ __forceinline__ void bwd_group(const T (&P)[NPSI], const float *gb, T (&A)[NPSI]) {
-    if (PART == 0) bwd_unit<0, 0x1F>(P, gb, A);
-    else if (PART == 1) bwd_unit<5, 0x1F>(P, gb, A);
-    else if (PART == 2) bwd_unit<6, 0x1F>(P, gb, A);
-    else if (PART == 3) bwd_unit<7, 0x01>(P, gb, A);
-    else if (PART == 4) bwd_unit<7, 0x12>(P, gb, A);
-    else if (PART == 5) bwd_unit<7, 0x0C>(P, gb, A);
-    else if (PART == 6) bwd_unit<8, 0x03>(P, gb, A);
-    else bwd_unit<8, 0x1C>(P, gb, A);
-}
 
 // Stage the 360 leading columns of 32 rows of a [.][384] FP32 matrix into shared memory
 // (row stride GT_STRIDE, rows past N zero).  Every thread issues all of its 16-byte loads
@@ -511,147 +169,242 @@ __device__ __forceinline__ void item_of(int k, int &kind, int &arg) {
 // the r-th item of warp w of W (snake order: w, 2W-1-w, 2W+w, ...)
 __device__ __forceinline__ int item_pos(int r, int w, int W) { return r * W + ((r & 1) ? W - 1 - w : w); }
 
-// register copy of an atom's vectors and matrices
-struct RegVM {
-    float v[NR][3], m[NR][6];
+// Item code is generic in the scalar T: float (features and dE/dPsi) or Dual (values with
+// their tangents, for the parameter gradient).  Sources and sinks per lane:
+//   MomSrc<T>  the atom's moments in the shared tile (Dual: moments and tangent moments)
+//   GradIn<T>  dE/dG of the atom (Dual: two gradient rows, see k_contract_bwd_dual)
+//   SlotAcc<T> the warp's slot row(s) for run-time gradient targets
+template <typename T> struct MomSrc;
+template <> struct MomSrc<float> {
+    const float *r;
+    __device__ __forceinline__ void v(int s, float (&x)[3]) const { ld_v(r + s * NC, x); }
+    __device__ __forceinline__ void m(int s, float (&x)[6]) const { ld_m(r + s * NC, x); }
+    __device__ __forceinline__ void t(int s, float (&x)[10]) const { ld_t(r + s * NC, x); }
+    __device__ __forceinline__ float c0(int s) const { return r[s * NC]; }
 };
-__device__ __forceinline__ void load_vm(const float *row, RegVM &p) {
+template <> struct MomSrc<Dual> {
+    const float *r, *d;
+    template <int K>
+    __device__ __forceinline__ static void zip(const float (&a)[K], const float (&b)[K], Dual (&x)[K]) {
+#pragma unroll
+        for (int q = 0; q < K; ++q) x[q] = {a[q], b[q]};
+    }
+    __device__ __forceinline__ void v(int s, Dual (&x)[3]) const {
+        float a[3], b[3];
+        ld_v(r + s * NC, a);
+        ld_v(d + s * NC, b);
+        zip(a, b, x);
+    }
+    __device__ __forceinline__ void m(int s, Dual (&x)[6]) const {
+        float a[6], b[6];
+        ld_m(r + s * NC, a);
+        ld_m(d + s * NC, b);
+        zip(a, b, x);
+    }
+    __device__ __forceinline__ void t(int s, Dual (&x)[10]) const {
+        float a[10], b[10];
+        ld_t(r + s * NC, a);
+        ld_t(d + s * NC, b);
+        zip(a, b, x);
+    }
+    __device__ __forceinline__ Dual c0(int s) const { return {r[s * NC], d[s * NC]}; }
+};
+template <typename T> struct GradIn;
+template <> struct GradIn<float> {
+    const float *g;
+    __device__ __forceinline__ float operator()(int f) const { return g[f]; }
+};
+template <> struct GradIn<Dual> {
+    const float *g, *gd;
+    __device__ __forceinline__ Dual operator()(int f) const { return {g[f], gd[f]}; }
+};
+template <typename T> struct SlotAcc;
+template <> struct SlotAcc<float> {
+    float *a;
+    __device__ __forceinline__ void v(int s, const float (&x)[3], float c0) const { add_v(a + s * NC, x, c0); }
+    __device__ __forceinline__ void m(int s, const float (&x)[6]) const { add_m(a + s * NC, x); }
+    __device__ __forceinline__ void t(int s, const float (&x)[10]) const { add_t(a + s * NC, x); }
+};
+template <> struct SlotAcc<Dual> {
+    float *a, *ad;
+    template <int K>
+    __device__ __forceinline__ static void unzip(const Dual (&x)[K], float (&a)[K], float (&b)[K]) {
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            a[q] = x[q].v;
+            b[q] = x[q].d;
+        }
+    }
+    __device__ __forceinline__ void v(int s, const Dual (&x)[3], Dual c0) const {
+        float p[3], q[3];
+        unzip(x, p, q);
+        add_v(a + s * NC, p, c0.v);
+        add_v(ad + s * NC, q, c0.d);
+    }
+    __device__ __forceinline__ void m(int s, const Dual (&x)[6]) const {
+        float p[6], q[6];
+        unzip(x, p, q);
+        add_m(a + s * NC, p);
+        add_m(ad + s * NC, q);
+    }
+    __device__ __forceinline__ void t(int s, const Dual (&x)[10]) const {
+        float p[10], q[10];
+        unzip(x, p, q);
+        add_t(a + s * NC, p);
+        add_t(ad + s * NC, q);
+    }
+};
+template <typename T, int K> __device__ __forceinline__ void zero_t(T (&x)[K]) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) x[q] = zero<T>();
+}
+
+// register copy of an atom's vectors and matrices
+template <typename T>
+struct RegVM {
+    T v[NR][3], m[NR][6];
+};
+template <typename T>
+__device__ __forceinline__ void load_vm(const MomSrc<T> &src, RegVM<T> &p) {
 #pragma unroll
     for (int s = 0; s < NR; ++s) {
-        ld_v(row + s * NC, p.v[s]);
-        ld_m(row + s * NC, p.m[s]);
+        src.v(s, p.v[s]);
+        src.m(s, p.m[s]);
     }
 }
 
-// Features of item (kind, arg) for this lane's atom (row = its moments) into out[0..360).
-__device__ __forceinline__ void fwd_item(int kind, int arg, const float *row, const RegVM &P, float *out) {
+// Features of item (kind, arg) for this lane's atom (src = its moments) into out[0..360).
+template <typename T>
+__device__ __forceinline__ void fwd_item(int kind, int arg, const MomSrc<T> &src, const RegVM<T> &P,
+                                         const FeatOut &out) {
     if (kind == IK_D) {                            // #7: Q_cd = T1_abc T2_abd, f = Q : M3;  #4: T1 : T2
         int s1, s2;
         pair_of(arg, s1, s2);
-        float T1[10], T2[10];
-        ld_t(row + s1 * NC, T1);
-        ld_t(row + s2 * NC, T2);
-        float f4 = 0.0f, Q[3][3];
+        T T1[10], T2[10];
+        src.t(s1, T1);
+        src.t(s2, T2);
+        T f4 = zero<T>(), Q[3][3];
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                float v = 0.0f;
+                T v = zero<T>();
 #pragma unroll
                 for (int a = 0; a < 3; ++a)
 #pragma unroll
-                    for (int b = 0; b < 3; ++b) v = fmaf(LT(T1, a, b, c), LT(T2, a, b, d), v);
+                    for (int b = 0; b < 3; ++b) v = mad(LT(T1, a, b, c), LT(T2, a, b, d), v);
                 Q[c][d] = v;
                 if (c == d) f4 += v;
             }
-        out[FAM_OFF4 + arg] = f4;
+        out.put(FAM_OFF4 + arg, f4);
         const int f0 = FAM_OFF7 + f7_index(s1, s2, 0);
 #pragma unroll
         for (int s3 = 0; s3 < NR; ++s3) {
-            float f = 0.0f;
+            T f = zero<T>();
 #pragma unroll
             for (int c = 0; c < 3; ++c)
 #pragma unroll
-                for (int d = 0; d < 3; ++d) f = fmaf(Q[c][d], LM(P.m[s3], c, d), f);
-            out[f0 + s3] = f;
+                for (int d = 0; d < 3; ++d) f = mad(Q[c][d], LM(P.m[s3], c, d), f);
+            out.put(f0 + s3, f);
         }
     } else if (kind == IK_E) {                     // #8: U_a = T2_abc M3_bc, f = v1 . U
         const int t2 = arg;
-        float T2[10];
-        ld_t(row + t2 * NC, T2);
+        T T2[10];
+        src.t(t2, T2);
 #pragma unroll
         for (int s3 = 0; s3 < NR; ++s3) {
-            float U[3];
+            T U[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                float v = 0.0f;
+                T v = zero<T>();
 #pragma unroll
                 for (int b = 0; b < 3; ++b)
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) v = fmaf(LT(T2, a, b, c), LM(P.m[s3], b, c), v);
+                    for (int c = 0; c < 3; ++c) v = mad(LT(T2, a, b, c), LM(P.m[s3], b, c), v);
                 U[a] = v;
             }
 #pragma unroll
             for (int s1 = 0; s1 < NR; ++s1) {
-                float f = 0.0f;
+                T f = zero<T>();
 #pragma unroll
-                for (int a = 0; a < 3; ++a) f = fmaf(P.v[s1][a], U[a], f);
-                out[FAM_OFF8 + f8_index(s1, t2, s3)] = f;
+                for (int a = 0; a < 3; ++a) f = mad(P.v[s1][a], U[a], f);
+                out.put(FAM_OFF8 + f8_index(s1, t2, s3), f);
             }
         }
     } else if (kind == IK_B) {                     // #5: tr(M1 M2 M3), s1 <= s2 <= s3
         const int s1 = arg;
-        float M1[6];
-        ld_m(row + s1 * NC, M1);
+        T M1[6];
+        src.m(s1, M1);
 #pragma unroll
         for (int s2 = 0; s2 < NR; ++s2) {
             if (s2 < s1) continue;
-            float Nm[3][3];
+            T Nm[3][3];
 #pragma unroll
             for (int a = 0; a < 3; ++a)
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    float v = 0.0f;
+                    T v = zero<T>();
 #pragma unroll
-                    for (int b = 0; b < 3; ++b) v = fmaf(LM(M1, a, b), LM(P.m[s2], b, c), v);
+                    for (int b = 0; b < 3; ++b) v = mad(LM(M1, a, b), LM(P.m[s2], b, c), v);
                     Nm[a][c] = v;
                 }
 #pragma unroll
             for (int s3 = s2; s3 < NR; ++s3) {
-                float f = 0.0f;
+                T f = zero<T>();
 #pragma unroll
                 for (int a = 0; a < 3; ++a)
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) f = fmaf(Nm[a][c], LM(P.m[s3], c, a), f);
-                out[FAM_OFF5 + f5_index(s1, s2, s3)] = f;
+                    for (int c = 0; c < 3; ++c) f = mad(Nm[a][c], LM(P.m[s3], c, a), f);
+                out.put(FAM_OFF5 + f5_index(s1, s2, s3), f);
             }
         }
     } else if (kind == IK_C) {                     // #6: w = M2 v3, f = v1 . w, s1 <= s3
         const int t2 = arg;
-        float M2[6];
-        ld_m(row + t2 * NC, M2);
+        T M2[6];
+        src.m(t2, M2);
 #pragma unroll
         for (int s3 = 0; s3 < NR; ++s3) {
-            float w[3];
+            T w[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                float v = 0.0f;
+                T v = zero<T>();
 #pragma unroll
-                for (int b = 0; b < 3; ++b) v = fmaf(LM(M2, a, b), P.v[s3][b], v);
+                for (int b = 0; b < 3; ++b) v = mad(LM(M2, a, b), P.v[s3][b], v);
                 w[a] = v;
             }
 #pragma unroll
             for (int s1 = 0; s1 <= s3; ++s1) {
-                float f = 0.0f;
+                T f = zero<T>();
 #pragma unroll
-                for (int a = 0; a < 3; ++a) f = fmaf(P.v[s1][a], w[a], f);
-                out[FAM_OFF6 + f6_index(s1, t2, s3)] = f;
+                for (int a = 0; a < 3; ++a) f = mad(P.v[s1][a], w[a], f);
+                out.put(FAM_OFF6 + f6_index(s1, t2, s3), f);
             }
         }
     } else {                                       // #1, #2, #3
 #pragma unroll
-        for (int s = 0; s < NR; ++s) out[FAM_OFF1 + s] = row[s * NC];
+        for (int s = 0; s < NR; ++s) out.put(FAM_OFF1 + s, src.c0(s));
 #pragma unroll
         for (int s1 = 0; s1 < NR; ++s1)
 #pragma unroll
             for (int s2 = s1; s2 < NR; ++s2) {
-                float f2 = 0.0f, f3 = 0.0f;
+                T f2 = zero<T>(), f3 = zero<T>();
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    f2 = fmaf(P.v[s1][a], P.v[s2][a], f2);
+                    f2 = mad(P.v[s1][a], P.v[s2][a], f2);
 #pragma unroll
-                    for (int b = 0; b < 3; ++b) f3 = fmaf(LM(P.m[s1], a, b), LM(P.m[s2], a, b), f3);
+                    for (int b = 0; b < 3; ++b) f3 = mad(LM(P.m[s1], a, b), LM(P.m[s2], a, b), f3);
                 }
                 const int q = pair_le_index(s1, s2);
-                out[FAM_OFF2 + q] = f2;
-                out[FAM_OFF3 + q] = f3;
+                out.put(FAM_OFF2 + q, f2);
+                out.put(FAM_OFF3 + q, f3);
             }
     }
 }
 
 // register gradient accumulators of one atom: dE/dv_s, dE/dM_s, dE/dPsi0_s
+template <typename T>
 struct RegGrad {
-    float v[NR][3], m[NR][6], c0[NR];
+    T v[NR][3], m[NR][6], c0[NR];
 };
 
 // dE/dPsi contributions of item (kind, arg) for this lane's atom (gb = its dE/dG): into
@@ -659,80 +412,82 @@ struct RegGrad {
 // index loops write into unique accumulators, which sums all index permutations (the
 // gradient with respect to the unique component).  Run-time targets that coincide
 // (s1 == s2) are updated one after the other, so both contributions land.
-__device__ __forceinline__ void bwd_item(int kind, int arg, const float *row, const RegVM &P, const float *gb,
-                                         RegGrad &A, float *acc) {
+template <typename T>
+__device__ __forceinline__ void bwd_item(int kind, int arg, const MomSrc<T> &src, const RegVM<T> &P,
+                                         const GradIn<T> &gb, RegGrad<T> &A, const SlotAcc<T> &acc) {
     if (kind == IK_D) {                            // #7 and #4
         int s1, s2;
         pair_of(arg, s1, s2);
-        float T1[10], T2[10];
-        ld_t(row + s1 * NC, T1);
-        ld_t(row + s2 * NC, T2);
+        T T1[10], T2[10];
+        src.t(s1, T1);
+        src.t(s2, T2);
         const int f0 = FAM_OFF7 + f7_index(s1, s2, 0);
-        const float g4 = gb[FAM_OFF4 + arg];
-        float g[NR], Mw[6];                        // Mw = sum_s3 g M3 (symmetric)
-        zero_arr(Mw);
+        const T g4 = gb(FAM_OFF4 + arg);
+        T g[NR], Mw[6];                        // Mw = sum_s3 g M3 (symmetric)
+        zero_t(Mw);
 #pragma unroll
         for (int s3 = 0; s3 < NR; ++s3) {
-            g[s3] = gb[f0 + s3];
+            g[s3] = gb(f0 + s3);
 #pragma unroll
-            for (int u = 0; u < 6; ++u) Mw[u] = fmaf(g[s3], P.m[s3][u], Mw[u]);
+            for (int u = 0; u < 6; ++u) Mw[u] = mad(g[s3], P.m[s3][u], Mw[u]);
         }
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
             for (int d = 0; d < 3; ++d) {          // Q_cd; d/dM3_cd = Q_cd
-                float v = 0.0f;
+                T v = zero<T>();
 #pragma unroll
                 for (int a = 0; a < 3; ++a)
 #pragma unroll
-                    for (int b = 0; b < 3; ++b) v = fmaf(LT(T1, a, b, c), LT(T2, a, b, d), v);
+                    for (int b = 0; b < 3; ++b) v = mad(LT(T1, a, b, c), LT(T2, a, b, d), v);
 #pragma unroll
-                for (int s3 = 0; s3 < NR; ++s3) LM(A.m[s3], c, d) = fmaf(g[s3], v, LM(A.m[s3], c, d));
+                for (int s3 = 0; s3 < NR; ++s3) LM(A.m[s3], c, d) = mad(g[s3], v, LM(A.m[s3], c, d));
             }
-        float t1[10], t2[10];                      // d/dT1_abc = g4 T2_abc + T2_abd Mw_cd, and T1 <-> T2
-        zero_arr(t1);
-        zero_arr(t2);
+        T t1[10], t2[10];                      // d/dT1_abc = g4 T2_abc + T2_abd Mw_cd, and T1 <-> T2
+        zero_t(t1);
+        zero_t(t2);
 #pragma unroll
         for (int a = 0; a < 3; ++a)
 #pragma unroll
             for (int b = 0; b < 3; ++b)
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    float x1 = g4 * LT(T2, a, b, c), x2 = g4 * LT(T1, a, b, c);
+                    T x1 = g4 * LT(T2, a, b, c), x2 = g4 * LT(T1, a, b, c);
 #pragma unroll
                     for (int d = 0; d < 3; ++d) {
-                        x1 = fmaf(LT(T2, a, b, d), LM(Mw, c, d), x1);
-                        x2 = fmaf(LT(T1, a, b, d), LM(Mw, d, c), x2);
+                        x1 = mad(LT(T2, a, b, d), LM(Mw, c, d), x1);
+                        x2 = mad(LT(T1, a, b, d), LM(Mw, d, c), x2);
                     }
                     LT(t1, a, b, c) += x1;
                     LT(t2, a, b, c) += x2;
                 }
-        add_t(acc + s1 * NC, t1);
-        add_t(acc + s2 * NC, t2);
+        acc.t(s1, t1);
+        acc.t(s2, t2);
     } else if (kind == IK_E) {                     // #8
         const int t2 = arg;
-        float T2[10], at[10];
-        ld_t(row + t2 * NC, T2);
-        zero_arr(at);
+        T T2[10], at[10];
+        src.t(t2, T2);
+        zero_t(at);
 #pragma unroll
         for (int s3 = 0; s3 < NR; ++s3) {
-            float U[3], Vw[3] = {0.0f, 0.0f, 0.0f};
+            T U[3], Vw[3];
+            zero_t(Vw);
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                float v = 0.0f;
+                T v = zero<T>();
 #pragma unroll
                 for (int b = 0; b < 3; ++b)
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) v = fmaf(LT(T2, a, b, c), LM(P.m[s3], b, c), v);
+                    for (int c = 0; c < 3; ++c) v = mad(LT(T2, a, b, c), LM(P.m[s3], b, c), v);
                 U[a] = v;
             }
 #pragma unroll
             for (int s1 = 0; s1 < NR; ++s1) {      // d/dv1 = g U; Vw = sum_s1 g v1
-                const float g = gb[FAM_OFF8 + f8_index(s1, t2, s3)];
+                const T g = gb(FAM_OFF8 + f8_index(s1, t2, s3));
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    A.v[s1][a] = fmaf(g, U[a], A.v[s1][a]);
-                    Vw[a] = fmaf(g, P.v[s1][a], Vw[a]);
+                    A.v[s1][a] = mad(g, U[a], A.v[s1][a]);
+                    Vw[a] = mad(g, P.v[s1][a], Vw[a]);
                 }
             }
 #pragma unroll
@@ -741,108 +496,109 @@ __device__ __forceinline__ void bwd_item(int kind, int arg, const float *row, co
                 for (int b = 0; b < 3; ++b)
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        LT(at, a, b, c) = fmaf(Vw[a], LM(P.m[s3], b, c), LT(at, a, b, c));
-                        LM(A.m[s3], b, c) = fmaf(Vw[a], LT(T2, a, b, c), LM(A.m[s3], b, c));
+                        LT(at, a, b, c) = mad(Vw[a], LM(P.m[s3], b, c), LT(at, a, b, c));
+                        LM(A.m[s3], b, c) = mad(Vw[a], LT(T2, a, b, c), LM(A.m[s3], b, c));
                     }
         }
-        add_t(acc + t2 * NC, at);
+        acc.t(t2, at);
     } else if (kind == IK_B) {                     // #5: s1 <= s2 <= s3
         const int s1 = arg;
-        float M1[6], a1[6];
-        ld_m(row + s1 * NC, M1);
-        zero_arr(a1);
+        T M1[6], a1[6];
+        src.m(s1, M1);
+        zero_t(a1);
 #pragma unroll
         for (int s2 = 0; s2 < NR; ++s2) {
             if (s2 < s1) continue;
-            float Nm[3][3], Mg[6];                 // Nm = M1 M2, Mg = sum_s3 g M3
+            T Nm[3][3], Mg[6];                 // Nm = M1 M2, Mg = sum_s3 g M3
 #pragma unroll
             for (int a = 0; a < 3; ++a)
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    float v = 0.0f;
+                    T v = zero<T>();
 #pragma unroll
-                    for (int b = 0; b < 3; ++b) v = fmaf(LM(M1, a, b), LM(P.m[s2], b, c), v);
+                    for (int b = 0; b < 3; ++b) v = mad(LM(M1, a, b), LM(P.m[s2], b, c), v);
                     Nm[a][c] = v;
                 }
-            zero_arr(Mg);
+            zero_t(Mg);
 #pragma unroll
             for (int s3 = s2; s3 < NR; ++s3) {     // d/d(M3)_ba = (M1 M2)_ab
-                const float g = gb[FAM_OFF5 + f5_index(s1, s2, s3)];
+                const T g = gb(FAM_OFF5 + f5_index(s1, s2, s3));
 #pragma unroll
-                for (int u = 0; u < 6; ++u) Mg[u] = fmaf(g, P.m[s3][u], Mg[u]);
+                for (int u = 0; u < 6; ++u) Mg[u] = mad(g, P.m[s3][u], Mg[u]);
 #pragma unroll
                 for (int a = 0; a < 3; ++a)
 #pragma unroll
-                    for (int b = 0; b < 3; ++b) LM(A.m[s3], b, a) = fmaf(g, Nm[a][b], LM(A.m[s3], b, a));
+                    for (int b = 0; b < 3; ++b) LM(A.m[s3], b, a) = mad(g, Nm[a][b], LM(A.m[s3], b, a));
             }
 #pragma unroll
             for (int a = 0; a < 3; ++a)            // d/d(M1)_ba = (M2 Mg)_ab, d/d(M2)_ba = (Mg M1)_ab
 #pragma unroll
                 for (int b = 0; b < 3; ++b) {
-                    float x1 = 0.0f, x2 = 0.0f;
+                    T x1 = zero<T>(), x2 = zero<T>();
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        x1 = fmaf(LM(P.m[s2], a, c), LM(Mg, c, b), x1);
-                        x2 = fmaf(LM(Mg, a, c), LM(M1, c, b), x2);
+                        x1 = mad(LM(P.m[s2], a, c), LM(Mg, c, b), x1);
+                        x2 = mad(LM(Mg, a, c), LM(M1, c, b), x2);
                     }
                     LM(a1, b, a) += x1;
                     LM(A.m[s2], b, a) += x2;
                 }
         }
-        add_m(acc + s1 * NC, a1);
+        acc.m(s1, a1);
     } else if (kind == IK_C) {                     // #6: s1 <= s3
         const int t2 = arg;
-        float M2[6], am[6];
-        ld_m(row + t2 * NC, M2);
-        zero_arr(am);
+        T M2[6], am[6];
+        src.m(t2, M2);
+        zero_t(am);
 #pragma unroll
         for (int s3 = 0; s3 < NR; ++s3) {
-            float w[3], vg[3] = {0.0f, 0.0f, 0.0f};
+            T w[3], vg[3];
+            zero_t(vg);
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                float v = 0.0f;
+                T v = zero<T>();
 #pragma unroll
-                for (int b = 0; b < 3; ++b) v = fmaf(LM(M2, a, b), P.v[s3][b], v);
+                for (int b = 0; b < 3; ++b) v = mad(LM(M2, a, b), P.v[s3][b], v);
                 w[a] = v;
             }
 #pragma unroll
             for (int s1 = 0; s1 <= s3; ++s1) {     // d/dv1 = g M2 v3; vg = sum_s1 g v1
-                const float g = gb[FAM_OFF6 + f6_index(s1, t2, s3)];
+                const T g = gb(FAM_OFF6 + f6_index(s1, t2, s3));
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    A.v[s1][a] = fmaf(g, w[a], A.v[s1][a]);
-                    vg[a] = fmaf(g, P.v[s1][a], vg[a]);
+                    A.v[s1][a] = mad(g, w[a], A.v[s1][a]);
+                    vg[a] = mad(g, P.v[s1][a], vg[a]);
                 }
             }
 #pragma unroll
             for (int a = 0; a < 3; ++a) {          // d/dM2_ab = vg_a v3_b, d/dv3 = M2 vg
-                float v = 0.0f;
+                T v = zero<T>();
 #pragma unroll
                 for (int b = 0; b < 3; ++b) {
-                    LM(am, a, b) = fmaf(vg[a], P.v[s3][b], LM(am, a, b));
-                    v = fmaf(LM(M2, a, b), vg[b], v);
+                    LM(am, a, b) = mad(vg[a], P.v[s3][b], LM(am, a, b));
+                    v = mad(LM(M2, a, b), vg[b], v);
                 }
                 A.v[s3][a] += v;
             }
         }
-        add_m(acc + t2 * NC, am);
+        acc.m(t2, am);
     } else {                                       // #1, #2, #3
 #pragma unroll
-        for (int s = 0; s < NR; ++s) A.c0[s] += gb[FAM_OFF1 + s];
+        for (int s = 0; s < NR; ++s) A.c0[s] += gb(FAM_OFF1 + s);
 #pragma unroll
         for (int s1 = 0; s1 < NR; ++s1)
 #pragma unroll
             for (int s2 = s1; s2 < NR; ++s2) {
                 const int q = pair_le_index(s1, s2);
-                const float g2 = gb[FAM_OFF2 + q], g3 = gb[FAM_OFF3 + q];
+                const T g2 = gb(FAM_OFF2 + q), g3 = gb(FAM_OFF3 + q);
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    A.v[s1][a] = fmaf(g2, P.v[s2][a], A.v[s1][a]);
-                    A.v[s2][a] = fmaf(g2, P.v[s1][a], A.v[s2][a]);
+                    A.v[s1][a] = mad(g2, P.v[s2][a], A.v[s1][a]);
+                    A.v[s2][a] = mad(g2, P.v[s1][a], A.v[s2][a]);
 #pragma unroll
                     for (int b = 0; b < 3; ++b) {
-                        LM(A.m[s1], a, b) = fmaf(g3, LM(P.m[s2], a, b), LM(A.m[s1], a, b));
-                        LM(A.m[s2], a, b) = fmaf(g3, LM(P.m[s1], a, b), LM(A.m[s2], a, b));
+                        LM(A.m[s1], a, b) = mad(g3, LM(P.m[s2], a, b), LM(A.m[s1], a, b));
+                        LM(A.m[s2], a, b) = mad(g3, LM(P.m[s1], a, b), LM(A.m[s2], a, b));
                     }
                 }
             }
@@ -870,16 +626,16 @@ __global__ void __launch_bounds__(W * 32) k_contract_fwd(const float *__restrict
     griddep_wait();
     stage_psi<W * 32>(psi, m0, N, ptile);
     __syncthreads();
-    const float *row = ptile + lane * NPSI;
-    float *out = tile + lane * GT_STRIDE;
-    RegVM P;
-    load_vm(row, P);
+    const MomSrc<float> src{ptile + lane * NPSI};
+    const FeatOut out{tile + lane * GT_STRIDE, nullptr};
+    RegVM<float> P;
+    load_vm(src, P);
     for (int r = 0;; ++r) {
         const int k = item_pos(r, warp, W);
         if (k >= IT_COUNT) break;
         int kind, arg;
         item_of(k, kind, arg);
-        fwd_item(kind, arg, row, P, out);
+        fwd_item(kind, arg, src, P, out);
     }
     __syncthreads();
     // 16-byte stores of 8 columns (BF16: a hi/lo row pair [hi(384) | lo(384)]) or 4 columns.
@@ -932,16 +688,16 @@ __global__ void __launch_bounds__(W * 32) k_contract_bwd(const float *__restrict
         for (int q = lane; q < CT_ATOMS * NPSI / 4; q += 32) mine[q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
     stage_rows<W * 32>(dG, m0, N, gtile);                   // ends with __syncthreads()
-    const float *row = ptile + lane * NPSI;
-    const float *gb = gtile + lane * GT_STRIDE;
-    float *acc = slots + warp * CT_ATOMS * NPSI + lane * NPSI;
-    RegVM P;
-    load_vm(row, P);
-    RegGrad A;
+    const MomSrc<float> src{ptile + lane * NPSI};
+    const GradIn<float> gb{gtile + lane * GT_STRIDE};
+    const SlotAcc<float> acc{slots + warp * CT_ATOMS * NPSI + lane * NPSI};
+    RegVM<float> P;
+    load_vm(src, P);
+    RegGrad<float> A;
 #pragma unroll
     for (int s = 0; s < NR; ++s) {
-        zero_arr(A.v[s]);
-        zero_arr(A.m[s]);
+        zero_t(A.v[s]);
+        zero_t(A.m[s]);
         A.c0[s] = 0.0f;
     }
     for (int r = 0;; ++r) {
@@ -949,12 +705,12 @@ __global__ void __launch_bounds__(W * 32) k_contract_bwd(const float *__restrict
         if (k >= IT_COUNT) break;
         int kind, arg;
         item_of(k, kind, arg);
-        bwd_item(kind, arg, row, P, gb, A, acc);
+        bwd_item(kind, arg, src, P, gb, A, acc);
     }
 #pragma unroll
     for (int s = 0; s < NR; ++s) {
-        add_v(acc + s * NC, A.v[s], A.c0[s]);
-        add_m(acc + s * NC, A.m[s]);
+        acc.v(s, A.v[s], A.c0[s]);
+        acc.m(s, A.m[s]);
     }
     __syncthreads();
     const float4 *s4 = reinterpret_cast<const float4 *>(slots);
@@ -973,38 +729,39 @@ __global__ void __launch_bounds__(W * 32) k_contract_bwd(const float *__restrict
 }
 
 // ------------------------------------------------------------------ parameter-gradient variants
-// Dual forward: features G and their tangents Gd = dG/dPsi . Psid, written as the stacked
-// GEMM operand GG [2 Mp][384] (rows m: G, rows Mp + m: Gd; FP32).
-__global__ void __launch_bounds__(CT_THREADS, 1) k_contract_fwd_dual(const float *__restrict__ psi,
-                                                                     const float *__restrict__ psid, int N, int Mp,
-                                                                     float *__restrict__ GG) {
-    extern __shared__ float tiles[];
-    float *tv = tiles, *td = tiles + CT_ATOMS * GT_STRIDE;
+// The same work items on dual numbers (value, tangent along Psid).
+//
+// Forward: features G and their tangents Gd = dG/dPsi . Psid, written as the stacked GEMM
+// operand GG [2 Mp][384] (rows m: G, rows Mp + m: Gd; FP32).
+template <int W>
+__global__ void __launch_bounds__(W * 32) k_contract_fwd_dual(const float *__restrict__ psi,
+                                                              const float *__restrict__ psid, int N, int Mp,
+                                                              float *__restrict__ GG) {
+    extern __shared__ __align__(16) float smd[];
+    float *ptile = smd, *pdtile = smd + CT_ATOMS * NPSI;          // [32][100] each
+    float *tv = pdtile + CT_ATOMS * NPSI, *td = tv + CT_ATOMS * GT_STRIDE;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * CT_ATOMS;
-    Dual P[NPSI];
-    {
-        float a[NPSI], b[NPSI];
-        load_psi(psi, m0 + lane, N, a);
-        load_psi(psid, m0 + lane, N, b);
-#pragma unroll
-        for (int q = 0; q < NPSI; ++q) P[q] = {a[q], b[q]};
-    }
-    const FeatOut gt{tv + lane * GT_STRIDE, td + lane * GT_STRIDE};
-    switch (warp) {
-    case 0: fwd_group<0>(P, gt); break;
-    case 1: fwd_group<1>(P, gt); break;
-    case 2: fwd_group<2>(P, gt); break;
-    case 3: fwd_group<3>(P, gt); break;
-    case 4: fwd_group<4>(P, gt); break;
-    case 5: fwd_group<5>(P, gt); break;
-    case 6: fwd_group<6>(P, gt); break;
-    default: fwd_group<7>(P, gt); break;
+    griddep_wait();
+    stage_psi<W * 32>(psi, m0, N, ptile);
+    stage_psi<W * 32>(psid, m0, N, pdtile);
+    __syncthreads();
+    const MomSrc<Dual> src{ptile + lane * NPSI, pdtile + lane * NPSI};
+    const FeatOut out{tv + lane * GT_STRIDE, td + lane * GT_STRIDE};
+    RegVM<Dual> P;
+    load_vm(src, P);
+    for (int r = 0;; ++r) {
+        const int k = item_pos(r, warp, W);
+        if (k >= IT_COUNT) break;
+        int kind, arg;
+        item_of(k, kind, arg);
+        fwd_item(kind, arg, src, P, out);
     }
     __syncthreads();
-    constexpr int NC4 = NFP / 4;
-    for (int idx = threadIdx.x; idx < CT_ATOMS * NC4; idx += CT_THREADS) {
-        const int r = idx / NC4, c = idx - r * NC4, m = m0 + r;
+    constexpr int NCW = NFP / 4;                                  // 8 rows x 4 column groups per warp
+    for (int idx = threadIdx.x; idx < CT_ATOMS * NCW; idx += W * 32) {
+        const int chunk = idx >> 5, l = idx & 31;
+        const int r = 8 * (chunk & 3) + (l >> 2), c = 4 * (chunk >> 2) + (l & 3), m = m0 + r;
         if (m >= Mp) continue;
         float v[4], d[4];
 #pragma unroll
@@ -1018,103 +775,101 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_contract_fwd_dual(const float
     }
 }
 
-// Dual backward.  With Gb = dJ/dG and Gdb = dJ/dGd (stacked in Gbs [2 Mp][384]):
-//   psib  = J^T Gb + (dJ^T/dPsi . Psid) Gdb   (adjoint of the moments)
-//   psidb = J^T Gdb                            (adjoint of the tangent moments)
-// where J = dG/dPsi.  The second term is the tangent part of J^T Gdb evaluated on duals.
-__global__ void __launch_bounds__(CT_THREADS, 1) k_contract_bwd_dual(const float *__restrict__ psi,
-                                                                     const float *__restrict__ psid,
-                                                                     const float *__restrict__ Gbs, int N, int Mp,
-                                                                     float *__restrict__ psib,
-                                                                     float *__restrict__ psidb) {
-    extern __shared__ float sm[];
-    float *gtile = sm;                                // Gb
-    float *gdtile = sm + CT_ATOMS * GT_STRIDE;         // Gdb
-    float *acc1 = gdtile + CT_ATOMS * GT_STRIDE;       // psib
-    float *acc2 = acc1 + CT_ATOMS * AC_STRIDE;         // psidb
+// Backward.  With Gb = dJ/dG and Gdb = dJ/dGd (stacked in Gbs [2 Mp][384]) the moment
+// adjoints are
+//   psidb = J^T Gdb,   psib = J^T Gb + (dJ^T/dPsi . Psid) Gdb,   J = dG/dPsi.
+// J^T g is linear in g, so one evaluation of the backward items on duals with moments
+// Psi + e Psid and gradient rows Gdb + e Gb gives psidb as the value and psib as the
+// tangent.  Each warp has a value slot and a tangent slot; the slots are summed in warp
+// order (deterministic).
+template <int W>
+__global__ void __launch_bounds__(W * 32) k_contract_bwd_dual(const float *__restrict__ psi,
+                                                              const float *__restrict__ psid,
+                                                              const float *__restrict__ Gbs, int N, int Mp,
+                                                              float *__restrict__ psib, float *__restrict__ psidb) {
+    extern __shared__ __align__(16) float smd[];
+    float *ptile = smd, *pdtile = smd + CT_ATOMS * NPSI;          // [32][100] each
+    float *slots = pdtile + CT_ATOMS * NPSI;                      // W x (value, tangent) x [32][100]
+    float *gtile = slots + 2 * W * CT_ATOMS * NPSI;               // Gb rows [32][GT_STRIDE]
+    float *gdtile = gtile + CT_ATOMS * GT_STRIDE;                 // Gdb rows
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * CT_ATOMS;
-    stage_rows<CT_THREADS>(Gbs, m0, N, gtile);
-    stage_rows<CT_THREADS>(Gbs + (size_t)Mp * NFP, m0, N, gdtile);
-    float *arow1 = acc1 + lane * AC_STRIDE, *arow2 = acc2 + lane * AC_STRIDE;
-    {   // J^T Gb
-        float P[NPSI], A[NPSI];
-        load_psi(psi, m0 + lane, N, P);
-#pragma unroll
-        for (int q = 0; q < NPSI; ++q) A[q] = 0.0f;
-        const float *gb = gtile + lane * GT_STRIDE;
-        switch (warp) {
-        case 0: bwd_group<0>(P, gb, A); break;
-        case 1: bwd_group<1>(P, gb, A); break;
-        case 2: bwd_group<2>(P, gb, A); break;
-        case 3: bwd_group<3>(P, gb, A); break;
-        case 4: bwd_group<4>(P, gb, A); break;
-        case 5: bwd_group<5>(P, gb, A); break;
-        case 6: bwd_group<6>(P, gb, A); break;
-        default: bwd_group<7>(P, gb, A); break;
-        }
-        for (int w = 0; w < CT_THREADS / 32; ++w) {
-            if (warp == w) {
-#pragma unroll
-                for (int q = 0; q < NPSI; ++q) arow1[q] = (w == 0 ? 0.0f : arow1[q]) + A[q];
-            }
-            __syncthreads();
-        }
+    griddep_wait();
+    stage_psi<W * 32>(psi, m0, N, ptile);
+    stage_psi<W * 32>(psid, m0, N, pdtile);
+    {
+        float4 *mine = reinterpret_cast<float4 *>(slots + 2 * warp * CT_ATOMS * NPSI);
+        for (int q = lane; q < 2 * CT_ATOMS * NPSI / 4; q += 32) mine[q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
-    {   // J^T Gdb on duals: value -> psidb, tangent -> second-order part of psib
-        Dual P[NPSI], A[NPSI];
-        {
-            float a[NPSI], b[NPSI];
-            load_psi(psi, m0 + lane, N, a);
-            load_psi(psid, m0 + lane, N, b);
+    stage_rows<W * 32>(Gbs, m0, N, gtile);                        // each ends with __syncthreads()
+    stage_rows<W * 32>(Gbs + (size_t)Mp * NFP, m0, N, gdtile);
+    const MomSrc<Dual> src{ptile + lane * NPSI, pdtile + lane * NPSI};
+    const GradIn<Dual> gb{gdtile + lane * GT_STRIDE, gtile + lane * GT_STRIDE};
+    float *mine = slots + 2 * warp * CT_ATOMS * NPSI;
+    const SlotAcc<Dual> acc{mine + lane * NPSI, mine + CT_ATOMS * NPSI + lane * NPSI};
+    RegVM<Dual> P;
+    load_vm(src, P);
+    RegGrad<Dual> A;
 #pragma unroll
-            for (int q = 0; q < NPSI; ++q) {
-                P[q] = {a[q], b[q]};
-                A[q] = {0.0f, 0.0f};
-            }
-        }
-        const float *gb = gdtile + lane * GT_STRIDE;
-        switch (warp) {
-        case 0: bwd_group<0>(P, gb, A); break;
-        case 1: bwd_group<1>(P, gb, A); break;
-        case 2: bwd_group<2>(P, gb, A); break;
-        case 3: bwd_group<3>(P, gb, A); break;
-        case 4: bwd_group<4>(P, gb, A); break;
-        case 5: bwd_group<5>(P, gb, A); break;
-        case 6: bwd_group<6>(P, gb, A); break;
-        default: bwd_group<7>(P, gb, A); break;
-        }
-        for (int w = 0; w < CT_THREADS / 32; ++w) {
-            if (warp == w) {
-#pragma unroll
-                for (int q = 0; q < NPSI; ++q) {
-                    arow1[q] += A[q].d;
-                    arow2[q] = (w == 0 ? 0.0f : arow2[q]) + A[q].v;
-                }
-            }
-            __syncthreads();
-        }
+    for (int s = 0; s < NR; ++s) {
+        zero_t(A.v[s]);
+        zero_t(A.m[s]);
+        A.c0[s] = zero<Dual>();
     }
-    for (int idx = threadIdx.x; idx < CT_ATOMS * NPSI; idx += CT_THREADS) {
-        const int r = idx / NPSI, q = idx - r * NPSI, m = m0 + r;
-        if (m < N) {
-            psib[(size_t)m * NPSI + q] = acc1[r * AC_STRIDE + q];
-            psidb[(size_t)m * NPSI + q] = acc2[r * AC_STRIDE + q];
+    for (int r = 0;; ++r) {
+        const int k = item_pos(r, warp, W);
+        if (k >= IT_COUNT) break;
+        int kind, arg;
+        item_of(k, kind, arg);
+        bwd_item(kind, arg, src, P, gb, A, acc);
+    }
+#pragma unroll
+    for (int s = 0; s < NR; ++s) {
+        acc.v(s, A.v[s], A.c0[s]);
+        acc.m(s, A.m[s]);
+    }
+    __syncthreads();
+    const float4 *s4 = reinterpret_cast<const float4 *>(slots);
+    constexpr int V4 = NPSI / 4, SLOT4 = CT_ATOMS * V4;
+    float4 *dv = reinterpret_cast<float4 *>(psidb + (size_t)m0 * NPSI);
+    float4 *dd = reinterpret_cast<float4 *>(psib + (size_t)m0 * NPSI);
+    for (int idx = threadIdx.x; idx < SLOT4; idx += W * 32) {
+        if (m0 + idx / V4 >= N) break;
+        float4 v = s4[idx], d = s4[SLOT4 + idx];
+#pragma unroll
+        for (int w = 1; w < W; ++w) {
+            const float4 x = s4[2 * w * SLOT4 + idx], y = s4[(2 * w + 1) * SLOT4 + idx];
+            v.x += x.x; v.y += x.y; v.z += x.z; v.w += x.w;
+            d.x += y.x; d.y += y.y; d.z += y.z; d.w += y.w;
         }
+        dv[idx] = v;
+        dd[idx] = d;
     }
 }
 
 // ------------------------------------------------------------------ launchers
+// Warps per block of the dual kernels: the forward stages 118 KB (moments, tangents and two
+// feature tiles) with 8 warps; the backward 220 KB (two moment tiles, two gradient tiles and
+// value/tangent slots for 4 warps).
+constexpr int CT_FWD_DUAL_W = 8, CT_BWD_DUAL_W = 4;
+constexpr size_t ct_fwd_dual_smem() { return sizeof(float) * (2 * CT_ATOMS * NPSI + 2 * CT_ATOMS * GT_STRIDE); }
+constexpr size_t ct_bwd_dual_smem() {
+    return sizeof(float) * ((2 + 2 * CT_BWD_DUAL_W) * CT_ATOMS * NPSI + 2 * CT_ATOMS * GT_STRIDE);
+}
+static_assert(ct_fwd_dual_smem() <= 227 * 1024 && ct_bwd_dual_smem() <= 227 * 1024,
+              "dual contraction tiles exceed the shared memory of a block");
+
 void launch_contract_fwd_dual(const float *psi, const float *psid, int N, int Mp, float *GG, cudaStream_t st) {
     const int blocks = (Mp + CT_ATOMS - 1) / CT_ATOMS;
-    const size_t smem = sizeof(float) * 2 * CT_ATOMS * GT_STRIDE;
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_contract_fwd_dual, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_contract_fwd_dual<CT_FWD_DUAL_W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)ct_fwd_dual_smem());
         attr = true;
     }
     if (blocks > 0) {
-        k_contract_fwd_dual<<<blocks, CT_THREADS, smem, st>>>(psi, psid, N, Mp, GG);
+        launch_pdl(k_contract_fwd_dual<CT_FWD_DUAL_W>, dim3(blocks), dim3(CT_FWD_DUAL_W * 32), ct_fwd_dual_smem(), st,
+                   psi, psid, N, Mp, GG);
         note_launches(1);
     }
 }
@@ -1122,17 +877,19 @@ void launch_contract_fwd_dual(const float *psi, const float *psid, int N, int Mp
 void launch_contract_bwd_dual(const float *psi, const float *psid, const float *Gbs, int N, int Mp, float *psib,
                               float *psidb, cudaStream_t st) {
     const int blocks = (N + CT_ATOMS - 1) / CT_ATOMS;
-    const size_t smem = sizeof(float) * (2 * CT_ATOMS * GT_STRIDE + 2 * CT_ATOMS * AC_STRIDE);
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_contract_bwd_dual, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_contract_bwd_dual<CT_BWD_DUAL_W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)ct_bwd_dual_smem());
         attr = true;
     }
     if (blocks > 0) {
-        k_contract_bwd_dual<<<blocks, CT_THREADS, smem, st>>>(psi, psid, Gbs, N, Mp, psib, psidb);
+        launch_pdl(k_contract_bwd_dual<CT_BWD_DUAL_W>, dim3(blocks), dim3(CT_BWD_DUAL_W * 32), ct_bwd_dual_smem(), st,
+                   psi, psid, Gbs, N, Mp, psib, psidb);
         note_launches(1);
     }
 }
+
 // Warps per block of the item kernels: the forward uses 8 (its 59 KB of shared memory let
 // three blocks share an SM); the backward uses 4 (110 KB with the four private slots, two
 // blocks per SM).
