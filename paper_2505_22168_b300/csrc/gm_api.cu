@@ -280,8 +280,8 @@ PgWs carve_pg(Carve &c, int N, int H, int S) {
     w.t_cs = c.take<float>(m1);
     w.beta_part = c.take<float>((size_t)(pg_beta_blocks(N, S) + 1) * S * S * NR * NB);
     w.hl = c.take<__nv_bfloat16>(2 * m1 * 2 * (size_t)(H > NFP ? H : NFP));
-    const int ks = wgrad_ksplit(2 * Mp);
-    size_t scratch = (size_t)ks * NFP * (H > NFP ? H : NFP) + (size_t)ks * H * H;   // weight-gradient slices,
+    size_t scratch = std::max((size_t)wgrad_ksplit(2 * Mp, NFP, H) * NFP * H,         // weight-gradient slices
+                              (size_t)wgrad_ksplit(2 * Mp, H, H) * H * H);            // (W1, then W2),
     scratch = std::max(scratch, colsum_part_floats(Mp, H));                           // later column sums
     scratch = std::max(scratch, pg_tail_part_floats(N, S));                           // and species sums
     w.wg_part = c.take<float>(scratch);

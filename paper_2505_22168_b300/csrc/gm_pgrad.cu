@@ -16,6 +16,17 @@
 
 namespace gm {
 
+// Fixed-order compensated FP32 summation (Kahan): a few ulps of error whatever the number of
+// terms, at FP32 speed (B300 issues FP64 adds at a small fraction of the FP32 rate).
+struct KahanSum {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float x) {
+        const float y = x - c, t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+};
+
 template <int ACT>
 __global__ void __launch_bounds__(256) k_pg_act1(int Mp, int H, const float *__restrict__ Z,
                                                  const float *__restrict__ b1, float *__restrict__ A1s,
@@ -91,9 +102,9 @@ __global__ void __launch_bounds__(256) k_pg_act1b(int Mp, int H, const float *__
     }
 }
 
-// out[h] = sum_{m < M} A[m][h], one thread per column (fixed order, FP64 accumulation)
-// Column sums of A [M][H]: block (column group of 32, chunk of CS_ROWS rows) writes
-// part[chunk][col]; k_colsum_final adds the chunks in FP64 in a fixed order.
+// Column sums out[h] = sum_{m < M} A[m][h] of A [M][H]: block (column group of 32, chunk of
+// CS_ROWS rows) writes part[chunk][col]; k_colsum_final adds the chunks in a fixed order
+// (compensated).
 constexpr int CS_ROWS = 256;
 __global__ void __launch_bounds__(256) k_colsum_part(int M, int H, const float *__restrict__ A,
                                                      float *__restrict__ part) {
@@ -118,63 +129,87 @@ __global__ void __launch_bounds__(256) k_colsum_final(int chunks, int H, const f
                                                       float *__restrict__ out) {
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
     if (h >= H) return;
-    double s = 0.0;
-    for (int r = 0; r < chunks; ++r) s += part[(size_t)r * H + h];
-    out[h] = (float)s;
+    KahanSum k;
+#pragma unroll 8
+    for (int r = 0; r < chunks; ++r) k.add(part[(size_t)r * H + h]);
+    out[h] = k.s;
 }
 
-// C_part[z][i][j] = sum_{k in slice z} A[k][i] B[k][j]; 64 x 64 tiles, 4 x 4 per thread
-constexpr int WG_T = 64, WG_K = 16;
+// C_part[z][i][j] = sum_{k in slice z} A[k][i] B[k][j] (A [K][lda], B [K][ldb], row-major):
+// 128 x 128 tiles, 8 x 8 per thread (rows 4 ty + {0..3} and 64 + 4 ty + {0..3}, columns
+// likewise), 8 rows of K per step staged in shared memory; the next step's 16-byte global
+// loads are in flight while the current step is multiplied.  Mo and No are multiples of 4.
+constexpr int WG_T = 128, WG_K = 8;
 __global__ void __launch_bounds__(256) k_wgrad(const float *__restrict__ A, int lda, const float *__restrict__ Bm,
                                                int ldb, int K, int Mo, int No, int kchunk, float *__restrict__ part) {
-    __shared__ float As[WG_K][WG_T], Bs[WG_K][WG_T];
+    __shared__ __align__(16) float As[2][WG_K][WG_T], Bs[2][WG_K][WG_T];
     const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
     const int i0 = blockIdx.x * WG_T, j0 = blockIdx.y * WG_T, z = blockIdx.z;
     const int kb = z * kchunk, ke = min(K, kb + kchunk);
-    float acc[4][4] = {};
+    const int lr = tid >> 5, lc = (tid & 31) * 4;                 // this thread's 16-byte load in a step
+    const float4 zero4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    float4 av = zero4, bv = zero4;
+    auto fetch = [&](int k0) {
+        const int k = k0 + lr;
+        av = (k < ke && i0 + lc < Mo) ? __ldg(reinterpret_cast<const float4 *>(A + (size_t)k * lda + i0 + lc)) : zero4;
+        bv = (k < ke && j0 + lc < No) ? __ldg(reinterpret_cast<const float4 *>(Bm + (size_t)k * ldb + j0 + lc)) : zero4;
+    };
+    float acc[8][8];
+#pragma unroll
+    for (int p = 0; p < 8; ++p)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[p][q] = 0.0f;
+    fetch(kb);
+    int buf = 0;
     for (int k0 = kb; k0 < ke; k0 += WG_K) {
-        for (int e = tid; e < WG_K * WG_T; e += 256) {
-            const int kk = e / WG_T, ii = e % WG_T, k = k0 + kk;
-            As[kk][ii] = (k < ke && i0 + ii < Mo) ? A[(size_t)k * lda + i0 + ii] : 0.0f;
-            Bs[kk][ii] = (k < ke && j0 + ii < No) ? Bm[(size_t)k * ldb + j0 + ii] : 0.0f;
-        }
+        *reinterpret_cast<float4 *>(&As[buf][lr][lc]) = av;
+        *reinterpret_cast<float4 *>(&Bs[buf][lr][lc]) = bv;
         __syncthreads();
+        if (k0 + WG_K < ke) fetch(k0 + WG_K);
 #pragma unroll
         for (int kk = 0; kk < WG_K; ++kk) {
-            float a[4], b[4];
+            const float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][kk][4 * ty]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][kk][64 + 4 * ty]);
+            const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][4 * tx]);
+            const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][64 + 4 * tx]);
+            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                a[q] = As[kk][ty * 4 + q];
-                b[q] = Bs[kk][tx * 4 + q];
-            }
+            for (int p = 0; p < 8; ++p)
 #pragma unroll
-            for (int p = 0; p < 4; ++p)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(a[p], b[q], acc[p][q]);
+                for (int q = 0; q < 8; ++q) acc[p][q] = fmaf(a[p], b[q], acc[p][q]);
         }
-        __syncthreads();
+        buf ^= 1;
     }
 #pragma unroll
-    for (int p = 0; p < 4; ++p)
+    for (int p = 0; p < 8; ++p) {
+        const int i = i0 + (p < 4 ? 4 * ty + p : 64 + 4 * ty + p - 4);
+        if (i >= Mo) continue;
+        float *row = part + ((size_t)z * Mo + i) * No;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int i = i0 + ty * 4 + p, j = j0 + tx * 4 + q;
-            if (i < Mo && j < No) part[((size_t)z * Mo + i) * No + j] = acc[p][q];
+        for (int h = 0; h < 2; ++h) {
+            const int j = j0 + h * 64 + 4 * tx;
+            if (j < No)
+                *reinterpret_cast<float4 *>(row + j) =
+                    make_float4(acc[p][4 * h], acc[p][4 * h + 1], acc[p][4 * h + 2], acc[p][4 * h + 3]);
         }
+    }
 }
 
+// The K slices in a fixed order, compensated (KahanSum).
 __global__ void __launch_bounds__(256) k_wgrad_reduce(int ksplit, int Mo, int No, int Mstore,
                                                       const float *__restrict__ part, float *__restrict__ out) {
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (size_t)Mstore * No) return;
-    double s = 0.0;
-    for (int z = 0; z < ksplit; ++z) s += part[(size_t)z * Mo * No + e];
-    out[e] = (float)s;
+    KahanSum k;
+#pragma unroll 8
+    for (int z = 0; z < ksplit; ++z) k.add(part[(size_t)z * Mo * No + e]);
+    out[e] = k.s;
 }
 
 // Per-species sums of the scale/shift gradients and the output-bias sum: block b sums the
 // atoms [b * TAIL_ATOMS, ...) into part[b][q], q = 0 (b3), 1 + z (sigma_z), 1 + S + z (mu_z);
-// k_pg_tail_final adds the blocks in FP64 in a fixed order.
+// k_pg_tail_final adds the blocks in a fixed order (compensated).
 constexpr int TAIL_ATOMS = 2048;
 __global__ void __launch_bounds__(256) k_pg_tail_part(int N, const int32_t *__restrict__ species, int S,
                                                       const float *__restrict__ t_sig, const float *__restrict__ t_c,
@@ -208,24 +243,27 @@ __global__ void k_pg_tail_final(int nblocks, int S, const float *__restrict__ pa
                                 float *g_b3) {
     const int q = threadIdx.x, nq = 1 + 2 * S;
     if (q >= nq) return;
-    double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += part[(size_t)b * nq + q];
-    if (q == 0) *g_b3 = (float)s;
-    else if (q <= S) g_sigma[q - 1] = (float)s;
-    else g_mu[q - 1 - S] = (float)s;
+    KahanSum k;
+#pragma unroll 8
+    for (int b = 0; b < nblocks; ++b) k.add(part[(size_t)b * nq + q]);
+    if (q == 0) *g_b3 = k.s;
+    else if (q <= S) g_sigma[q - 1] = k.s;
+    else g_mu[q - 1 - S] = k.s;
 }
 
-// One warp per coefficient: lanes take every 32nd block partial (FP64), then a fixed
+// One warp per coefficient: lanes take every 32nd block partial (compensated), then a fixed
 // shuffle tree adds the lanes' sums.
 __global__ void __launch_bounds__(256) k_pg_beta_reduce(int nblocks, int nbeta, float scale,
                                                         const float *__restrict__ part, float *__restrict__ out) {
     const int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (e >= nbeta) return;
-    double s = 0.0;
-    for (int b = lane; b < nblocks; b += 32) s += part[(size_t)b * nbeta + e];
+    KahanSum k;
+#pragma unroll 4
+    for (int b = lane; b < nblocks; b += 32) k.add(part[(size_t)b * nbeta + e]);
+    float s = k.s;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) out[e] = (float)(s * scale);
+    if (lane == 0) out[e] = s * scale;
 }
 
 // hi/lo BF16 copy of an FP32 matrix [rows][K]: dst row = [hi(K) | lo(K)], lo = bf16(x - hi)
@@ -293,15 +331,19 @@ void colsum(int M, int H, const float *A, float *part, float *out, cudaStream_t 
 
 size_t colsum_part_floats(int M, int H) { return (size_t)((M + CS_ROWS - 1) / CS_ROWS) * H; }
 
-// K-slices of the weight gradient: about 256 rows each (enough blocks for the GPU), at most 128
-int wgrad_ksplit(int K) {
-    int ks = K / 256;
+// K slices of the weight gradient: enough 128 x 128 tile-slices for two blocks per SM, slices
+// of at least 128 rows, at most 128 slices
+int wgrad_ksplit(int K, int Mo, int No) {
+    const int tiles = ((Mo + WG_T - 1) / WG_T) * ((No + WG_T - 1) / WG_T);
+    int ks = (2 * 148 + tiles - 1) / tiles;
+    const int kmax = K / 128;
+    ks = ks > kmax ? kmax : ks;
     return ks < 1 ? 1 : (ks > 128 ? 128 : ks);
 }
 
 void wgrad(const float *A, int lda, const float *B, int ldb, int K, int Mo, int No, int Mstore, float *part, float *out,
            cudaStream_t st) {
-    const int ks = wgrad_ksplit(K);
+    const int ks = wgrad_ksplit(K, Mo, No);
     int kchunk = (K + ks - 1) / ks;
     kchunk = (kchunk + WG_K - 1) / WG_K * WG_K;
     dim3 grid((Mo + WG_T - 1) / WG_T, (No + WG_T - 1) / WG_T, ks);

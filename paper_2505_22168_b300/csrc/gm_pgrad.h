@@ -15,7 +15,7 @@ void pg_act1b(int Mp, int H, const float *Ab, const float *P1, const float *Q1, 
 // out[h] = sum_{m < M} A[m][h]; part holds colsum_part_floats(M, H) floats
 void colsum(int M, int H, const float *A, float *part, float *out, cudaStream_t st);
 size_t colsum_part_floats(int M, int H);
-int wgrad_ksplit(int K);
+int wgrad_ksplit(int K, int Mo, int No);
 // out[i][j] (i < Mstore) = sum_k A[k][i] B[k][j], A [K][lda], B [K][ldb]; part holds ksplit x Mo x No
 void wgrad(const float *A, int lda, const float *B, int ldb, int K, int Mo, int No, int Mstore, float *part, float *out,
            cudaStream_t st);
