@@ -681,7 +681,9 @@ gm_status gm_param_grad(const gm_model *m, const gm_system *sys, const gm_nlist 
         StageScope sc(ST_PG_PAIR_FWD, st);
         launch_split_pos(N, sys->pos, sys->species, w.pos_hi, w.pos_lo, nullptr, nullptr, 0, st);
         launch_moments(a, choose_tpa(m, N), w.psi, st);
-        launch_moments_tangent(a, dL_dF, w.psid, st);
+        // at most 4 lanes per atom: the tangent kernel sums its 100 accumulators over the lanes
+        // with a plain all-reduce (8 lanes took 101 us against 57 us for 4 at 7920 atoms)
+        launch_moments_tangent(a, std::min(choose_tpa(m, N), 4), dL_dF, w.psid, st);
         launch_contract_fwd_dual(w.psi, w.psid, N, Mp, w.GG, st);
     }
     {   // network forward (primal + tangent rows) and reverse

@@ -46,12 +46,14 @@ __device__ __forceinline__ float disp_axis(float xjh, float xjl, float xih, floa
     return h3 + lo;
 }
 
-// One neighbour of a row: index, shift, hi/lo position (species in ph.w).
+// One neighbour of a row: index, shift, hi/lo position (species in ph.w) and, for the
+// tangent kernels, its velocity (the direction the positions move along).
 struct NextPair {
     int j;
     bool ok;
     char4 sh;
     float4 ph, pl;
+    float vx, vy, vz;
 };
 
 // Gather pipeline over the pairs p0, p0 + step, ... < p1 of a row, U pairs per call: while
@@ -60,6 +62,7 @@ struct NextPair {
 // inside the loop.
 template <int U>
 struct PairPipe {
+    const float *vel;         // per-atom velocities [N][3] gathered with the positions (or null)
     int p1, step, q;          // q: first pair whose index is loaded next
     int jn[U];                // indices, shifts and flags two groups ahead
     char4 shn[U];
@@ -80,9 +83,15 @@ struct PairPipe {
             if (nx[u].ok) {
                 nx[u].ph = a.pos_hi[nx[u].j];
                 nx[u].pl = a.pos_lo[nx[u].j];
+                if (vel) {
+                    nx[u].vx = vel[3 * nx[u].j];
+                    nx[u].vy = vel[3 * nx[u].j + 1];
+                    nx[u].vz = vel[3 * nx[u].j + 2];
+                }
             }
     }
-    __device__ __forceinline__ PairPipe(const PairArgs &a, int p0, int p1_, int step_) : p1(p1_), step(step_) {
+    __device__ __forceinline__ PairPipe(const PairArgs &a, int p0, int p1_, int step_, const float *vel_ = nullptr)
+        : vel(vel_), p1(p1_), step(step_) {
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             index(a, p0 + u * step, nx[u].j, nx[u].sh, nx[u].ok);
@@ -381,17 +390,16 @@ __global__ void __launch_bounds__(256) k_moments_tangent(PairArgs a, const float
         const int zsi = clamp_species(a.species[atom], a.S, a.status);
         const float *brow = sbeta + zsi * a.S * (NR * BETA_ROW);
         const int p1 = a.row_ptr[atom + 1];
-        PairPipe<1> pp(a, a.row_ptr[atom] + sub, p1, TPA);
+        PairPipe<1> pp(a, a.row_ptr[atom] + sub, p1, TPA, vel);
         for (int p = a.row_ptr[atom] + sub; p < p1; p += TPA) {
             const NextPair cur = pp.next(a);
             if (!cur.ok) continue;
-            const int j = cur.j;
             float fx, fy, fz;
             ce.displacement(cur, fx, fy, fz);
             const float r = sqrtf(fx * fx + fy * fy + fz * fz);
             const float rinv = 1.0f / r;
             const float ux = fx * rinv, uy = fy * rinv, uz = fz * rinv;
-            const float ddx = vel[3 * j] - vix, ddy = vel[3 * j + 1] - viy, ddz = vel[3 * j + 2] - viz;
+            const float ddx = cur.vx - vix, ddy = cur.vy - viy, ddz = cur.vz - viz;
             const float w = ux * ddx + uy * ddy + uz * ddz;
             float B[NB], dB[NB];
             radial_basis<true>(a.rc, r, B, dB);
@@ -461,17 +469,16 @@ __global__ void __launch_bounds__(256) k_pg_beta(PairArgs a, const float *__rest
         const float vix = vel[3 * atom], viy = vel[3 * atom + 1], viz = vel[3 * atom + 2];
         const int zsi = clamp_species(a.species[atom], a.S, a.status);
         const int p1 = a.row_ptr[atom + 1];
-        PairPipe<1> pp(a, a.row_ptr[atom] + lane, p1, 32);
+        PairPipe<1> pp(a, a.row_ptr[atom] + lane, p1, 32, vel);
         for (int p = a.row_ptr[atom] + lane; p < p1; p += 32) {
             const NextPair cur = pp.next(a);
             if (!cur.ok) continue;
-            const int j = cur.j;
             float fx, fy, fz;
             ce.displacement(cur, fx, fy, fz);
             const float r = sqrtf(fx * fx + fy * fy + fz * fz);
             const float rinv = 1.0f / r;
             const float ux = fx * rinv, uy = fy * rinv, uz = fz * rinv;
-            const float ddx = vel[3 * j] - vix, ddy = vel[3 * j + 1] - viy, ddz = vel[3 * j + 2] - viz;
+            const float ddx = cur.vx - vix, ddy = cur.vy - viy, ddz = cur.vz - viz;
             const float w = ux * ddx + uy * ddy + uz * ddz;
             float B[NB], dB[NB];
             radial_basis<true>(a.rc, r, B, dB);
@@ -585,8 +592,9 @@ void launch_forces(const PairArgs &a, int tpa, const float *dpsi, float *F, floa
 
 namespace gm {
 
-void launch_moments_tangent(const PairArgs &a, const float *vel, float *psid, cudaStream_t st) {
-    const int threads = 256, TPA = 4;
+template <int TPA>
+static void launch_tangent_t(const PairArgs &a, const float *vel, float *psid, cudaStream_t st) {
+    const int threads = 256;
     const long long total = (long long)a.N * TPA;
     const int blocks = (int)((total + threads - 1) / threads);
     const size_t smem = beta_smem_bytes(a.S);
@@ -596,8 +604,19 @@ void launch_moments_tangent(const PairArgs &a, const float *vel, float *psid, cu
         attr = true;
     }
     if (blocks > 0) {
-        k_moments_tangent<TPA><<<blocks, threads, smem, st>>>(a, vel, psid);
+        launch_pdl(k_moments_tangent<TPA>, dim3(blocks), dim3(threads), smem, st, a, vel, psid);
         note_launches(1);
+    }
+}
+
+void launch_moments_tangent(const PairArgs &a, int tpa, const float *vel, float *psid, cudaStream_t st) {
+    switch (tpa) {
+    case 1: launch_tangent_t<1>(a, vel, psid, st); break;
+    case 2: launch_tangent_t<2>(a, vel, psid, st); break;
+    case 4: launch_tangent_t<4>(a, vel, psid, st); break;
+    case 8: launch_tangent_t<8>(a, vel, psid, st); break;
+    case 16: launch_tangent_t<16>(a, vel, psid, st); break;
+    default: launch_tangent_t<32>(a, vel, psid, st); break;
     }
 }
 

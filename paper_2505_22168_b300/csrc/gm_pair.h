@@ -29,7 +29,8 @@ void launch_moments(const PairArgs &a, int tpa, float *psi, cudaStream_t st);
 void launch_forces(const PairArgs &a, int tpa, const float *dpsi, float *F, float *vir_atom, cudaStream_t st);
 
 // parameter gradient: tangent moments along vel (= dL/dF) and block partials of dJ/dbeta
-void launch_moments_tangent(const PairArgs &a, const float *vel, float *psid, cudaStream_t st);
+// tpa: lanes per atom as for launch_moments
+void launch_moments_tangent(const PairArgs &a, int tpa, const float *vel, float *psid, cudaStream_t st);
 int pg_beta_blocks(int N, int S);
 void launch_pg_beta(const PairArgs &a, const float *vel, const float *psib, const float *psidb, float *part,
                     cudaStream_t st);
