@@ -177,8 +177,13 @@ void launch_split_pos(int N, const double *pos, const int32_t *species, float4 *
     note_launches(1);
 }
 
+// Block shape of the moments kernel: with 8 or more lanes per atom (small systems) 128-thread
+// blocks at up to 170 registers, so that three blocks (12 warps) share an SM and a 1536-atom
+// system runs in one wave; with fewer lanes 256-thread blocks and two pairs per iteration.
+template <int TPA> constexpr int moments_threads() { return TPA >= 8 ? 128 : 256; }
 template <int TPA>
-__global__ void __launch_bounds__(256) k_moments(PairArgs a, float *__restrict__ psi) {
+__global__ void __launch_bounds__(moments_threads<TPA>(), TPA >= 8 ? 3 : 1) k_moments(PairArgs a,
+                                                                                   float *__restrict__ psi) {
     extern __shared__ __align__(16) float sbeta[];
     stage_beta(a.beta, a.S, sbeta);
     griddep_wait();
@@ -195,16 +200,17 @@ __global__ void __launch_bounds__(256) k_moments(PairArgs a, float *__restrict__
         const int zsi = clamp_species(a.species[atom], a.S, a.status);
         const float *brow = sbeta + zsi * a.S * (NR * BETA_ROW);
         const int p1 = a.row_ptr[atom + 1];
-        // two pairs per iteration (independent work for the latency-bound pair math); a
-        // missing second pair contributes exact zeros, so the sums are those of one pair at
-        // a time in row order
-        PairPipe<2> pp(a, a.row_ptr[atom] + sub, p1, TPA);
-        for (int p = a.row_ptr[atom] + sub; p < p1; p += 2 * TPA) {
-            NextPair cur[2];
+        // U pairs per iteration (independent work for the latency-bound pair math); a missing
+        // second pair contributes exact zeros, so the sums are those of one pair at a time in
+        // row order
+        constexpr int U = TPA >= 8 ? 1 : 2;
+        PairPipe<U> pp(a, a.row_ptr[atom] + sub, p1, TPA);
+        for (int p = a.row_ptr[atom] + sub; p < p1; p += U * TPA) {
+            NextPair cur[U];
             pp.next(a, cur);
-            float R[2][NR], m[2][NC];
+            float R[U][NR], m[U][NC];
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
+            for (int u = 0; u < U; ++u) {
                 float fx = 1.0f, fy = 0.0f, fz = 0.0f;
                 int zj = 0;
                 if (cur[u].ok) {
@@ -225,8 +231,12 @@ __global__ void __launch_bounds__(256) k_moments(PairArgs a, float *__restrict__
 #pragma unroll
             for (int s = 0; s < NR; ++s)
 #pragma unroll
-                for (int c = 0; c < NC; ++c)
-                    acc[s * NC + c] = fmaf(R[1][s], m[1][c], fmaf(R[0][s], m[0][c], acc[s * NC + c]));
+                for (int c = 0; c < NC; ++c) {
+                    float t = acc[s * NC + c];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) t = fmaf(R[u][s], m[u][c], t);
+                    acc[s * NC + c] = t;
+                }
         }
     }
     if (TPA >= 8) {
@@ -534,7 +544,7 @@ static void allow_beta_smem(Kern kernel) {
 
 template <int TPA>
 static void launch_moments_t(const PairArgs &a, float *psi, cudaStream_t st) {
-    const int threads = 256;
+    const int threads = moments_threads<TPA>();
     const long long total = (long long)a.N * TPA;
     const int blocks = (int)((total + threads - 1) / threads);
     const size_t smem = beta_smem_bytes(a.S);
