@@ -180,7 +180,7 @@ void launch_split_pos(int N, const double *pos, const int32_t *species, float4 *
 // Block shape of the moments kernel: with 8 or more lanes per atom (small systems) 128-thread
 // blocks at up to 170 registers, so that three blocks (12 warps) share an SM and a 1536-atom
 // system runs in one wave; with fewer lanes 256-thread blocks and two pairs per iteration.
-template <int TPA> constexpr int moments_threads() { return TPA >= 8 ? 128 : 256; }
+template <int TPA> __host__ __device__ constexpr int moments_threads() { return TPA >= 8 ? 128 : 256; }
 template <int TPA>
 __global__ void __launch_bounds__(moments_threads<TPA>(), TPA >= 8 ? 3 : 1) k_moments(PairArgs a,
                                                                                    float *__restrict__ psi) {
@@ -284,12 +284,30 @@ __global__ void __launch_bounds__(moments_threads<TPA>(), TPA >= 8 ? 3 : 1) k_mo
     }
 }
 
+// Block shape and gradient storage of the force kernel.  With 8 or more lanes per atom the
+// atom's dE/dPsi (identical for its lanes) sits once in shared memory, transposed to
+// [component][radial function] rows of 8 (one 16-byte and one 4-byte broadcast load per
+// component; atoms 168 floats apart, so the atoms of a warp hit distinct banks), and
+// 128-thread blocks run four per SM; with fewer lanes each lane keeps it in registers.
+template <int TPA> __host__ __device__ constexpr bool forces_gsmem() { return TPA >= 8; }
+template <int TPA> __host__ __device__ constexpr int forces_threads() { return TPA >= 8 ? 128 : 256; }
+constexpr int FG_ROW = 168;
 template <int TPA>
-__global__ void __launch_bounds__(256) k_forces(PairArgs a, const float *__restrict__ dpsi, float *__restrict__ F,
-                                                float *__restrict__ vir_atom) {
+__global__ void __launch_bounds__(forces_threads<TPA>(), TPA >= 8 ? 4 : 1)
+    k_forces(PairArgs a, const float *__restrict__ dpsi, float *__restrict__ F, float *__restrict__ vir_atom) {
+    constexpr bool GS = forces_gsmem<TPA>();
     extern __shared__ __align__(16) float sbeta[];
+    float *gsm = sbeta + a.S * a.S * NR * BETA_ROW;              // [atoms of the block][FG_ROW]
     stage_beta(a.beta, a.S, sbeta);
     griddep_wait();
+    if (GS) {
+        constexpr int APB = forces_threads<TPA>() / TPA;
+        const int a_first = blockIdx.x * APB;
+        for (int q = threadIdx.x; q < APB * NPSI; q += blockDim.x) {
+            const int al = q / NPSI, e = q - al * NPSI, s = e / NC, c = e - s * NC, m = a_first + al;
+            gsm[al * FG_ROW + c * 8 + s] = m < a.N ? dpsi[(size_t)m * NPSI + e] : 0.0f;
+        }
+    }
     __syncthreads();
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
     const int atom = gt / TPA, sub = gt % TPA;
@@ -299,12 +317,15 @@ __global__ void __launch_bounds__(256) k_forces(PairArgs a, const float *__restr
 #pragma unroll
     for (int q = 0; q < 9; ++q) V[q] = 0.0f;
     if (active) {
-        float g[NPSI];
-        const float4 *g4 = reinterpret_cast<const float4 *>(dpsi + (size_t)atom * NPSI);
+        float g[GS ? 1 : NPSI];
+        const float *gs = gsm + (threadIdx.x / TPA) * FG_ROW;
+        if (!GS) {
+            const float4 *g4 = reinterpret_cast<const float4 *>(dpsi + (size_t)atom * NPSI);
 #pragma unroll
-        for (int q = 0; q < NPSI / 4; ++q) {
-            const float4 v = g4[q];
-            g[4 * q] = v.x; g[4 * q + 1] = v.y; g[4 * q + 2] = v.z; g[4 * q + 3] = v.w;
+            for (int q = 0; q < NPSI / 4; ++q) {
+                const float4 v = g4[q];
+                g[4 * q] = v.x; g[4 * q + 1] = v.y; g[4 * q + 2] = v.z; g[4 * q + 3] = v.w;
+            }
         }
         const int b = structure_of(a.atom_ptr, a.B, atom);
         const Centre ce(a, atom, b);
@@ -331,11 +352,20 @@ __global__ void __launch_bounds__(256) k_forces(PairArgs a, const float *__restr
             float S1 = 0.0f, S2 = 0.0f, Q0 = 0.0f, Q1 = 0.0f, Q2 = 0.0f;
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
+                float gc[NR];
+                if (GS) {
+                    const float4 q4 = *reinterpret_cast<const float4 *>(gs + c * 8);
+                    gc[0] = q4.x; gc[1] = q4.y; gc[2] = q4.z; gc[3] = q4.w;
+                    gc[4] = gs[c * 8 + 4];
+                } else {
+#pragma unroll
+                    for (int s = 0; s < NR; ++s) gc[s] = g[(GS ? 0 : s * NC + c)];
+                }
                 float Ac = 0.0f, Apc = 0.0f;
 #pragma unroll
                 for (int s = 0; s < NR; ++s) {
-                    Ac = fmaf(g[s * NC + c], R[s], Ac);
-                    Apc = fmaf(g[s * NC + c], Rp[s], Apc);
+                    Ac = fmaf(gc[s], R[s], Ac);
+                    Apc = fmaf(gc[s], Rp[s], Apc);
                 }
                 S1 = fmaf(Apc, m[c], S1);
                 if (comp_rank(c) > 0) {
@@ -538,8 +568,8 @@ __global__ void __launch_bounds__(256) k_pg_beta(PairArgs a, const float *__rest
 // 48 KB, so the kernels opt in once)
 static size_t beta_smem_bytes(int S) { return sizeof(float) * (size_t)S * S * NR * BETA_ROW; }
 template <typename Kern>
-static void allow_beta_smem(Kern kernel) {
-    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)beta_smem_bytes(MAX_S));
+static void allow_beta_smem(Kern kernel, size_t extra = 0) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(beta_smem_bytes(MAX_S) + extra));
 }
 
 template <int TPA>
@@ -561,13 +591,14 @@ static void launch_moments_t(const PairArgs &a, float *psi, cudaStream_t st) {
 
 template <int TPA>
 static void launch_forces_t(const PairArgs &a, const float *dpsi, float *F, float *vir, cudaStream_t st) {
-    const int threads = 256;
+    const int threads = forces_threads<TPA>();
     const long long total = (long long)a.N * TPA;
     const int blocks = (int)((total + threads - 1) / threads);
-    const size_t smem = beta_smem_bytes(a.S);
+    const size_t smem = beta_smem_bytes(a.S) +
+                        (forces_gsmem<TPA>() ? sizeof(float) * (threads / TPA) * FG_ROW : 0);
     static bool attr = false;
     if (!attr) {
-        allow_beta_smem(k_forces<TPA>);
+        allow_beta_smem(k_forces<TPA>, forces_gsmem<TPA>() ? sizeof(float) * (threads / TPA) * FG_ROW : 0);
         attr = true;
     }
     if (blocks > 0) {
