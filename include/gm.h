@@ -158,8 +158,10 @@ GM_API void gm_model_destroy(gm_model *m);
  *                       (capped at what the device keeps resident)
  *   GM_TUNE_NL_TWO_PASS 1: count-then-fill neighbour search even when the workspace holds the
  *                       search slab (0, the default: one search pass and a compaction)
- *   GM_TUNE_NL_ITEMS    neighbour search work items: 0 = by size, 1 = one home cell (part) per
- *                       block with shared staging, 2 = one per warp
+ *   GM_TUNE_NL_ITEMS    neighbour search work items: 0 = by size (small systems whose boxes are
+ *                       all at least 2 r_cut long: brute force over each structure's atoms,
+ *                       same rows), 1 = one home cell (part) per block with shared staging,
+ *                       2 = one per warp, 3 = brute force where possible, else as 0
  * Errors: GM_ERR_ARG for an unknown key or value. */
 enum { GM_TUNE_PAIR_TPA = 0, GM_TUNE_SPLIT_MASK = 1, GM_TUNE_GEMM_BN = 2, GM_TUNE_NL_MODE = 3, GM_TUNE_NL_SPLIT = 4,
        GM_TUNE_NL_BLOCKS = 5, GM_TUNE_NL_TWO_PASS = 6, GM_TUNE_NL_ITEMS = 7, GM_TUNE_GEMM_CPS = 8 };

@@ -464,7 +464,7 @@ gm_status gm_model_set_tuning(gm_model *m, int32_t key, int32_t value) {
         m->nl.blocks = value;
         return GM_OK;
     case GM_TUNE_NL_ITEMS:
-        if (value < 0 || value > 2) return fail(GM_ERR_ARG, "neighbour item mode must be 0, 1 or 2");
+        if (value < 0 || value > 3) return fail(GM_ERR_ARG, "neighbour item mode must be 0, 1, 2 or 3");
         m->nl.items = value;
         return GM_OK;
     case GM_TUNE_NL_TWO_PASS:

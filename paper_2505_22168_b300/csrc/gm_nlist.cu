@@ -106,6 +106,8 @@ struct NlArgs {
     int maxn;               // slab row length (0: two-pass search, no slab)
     int block_items;        // 1: block-level search items, 0: warp-level
     int small;              // cooperative launch: grids and short scans computed by every block
+    int try_brute;          // small systems: brute-force search when every box is single-image
+    int *brute_over;        // set when a brute-force row exceeds BR_CAP (zeroed per build)
     uint8_t *redo;          // 1: row searched again during the compaction
     int32_t *redo_list, *n_redo;
     double *xw;
@@ -1087,13 +1089,185 @@ __device__ void ph_search_block(const NlArgs &a, int bid, int nb, float4 *smem) 
     }
 }
 
+// ------------------------------------------------------------------ brute-force search
+// Small systems whose boxes are all at least 2.001 r_cut long on every axis: each neighbour
+// has exactly one image within r_cut (the minimum image), so a warp can test its atom
+// against every atom of its structure -- no histogram, scatter or sort phases.  The row
+// comes out in the cell-list order all the same: with the cell grid of the setup, the
+// stencil cell of pair (i, j, n) is d = c_j + n nc - c_i per axis (in {-1, 0, 1}, cells
+// being at least r_cut long), and the accepted pairs, found in ascending j, are placed by a
+// stable counting sort on that stencil index.  A row longer than BR_CAP (shared memory)
+// sends the whole build back to the cell-list path.
+constexpr int BR_CAP = 512;
+struct BrBuf {
+    unsigned key[BR_CAP];   // stencil << 27 | j
+    unsigned img[BR_CAP];   // bytes3 of the image n (each component in {-1, 0, 1})
+    int hist[32], run[32];
+};
+
+// shared-memory layout of the small-system brute-force path: the per-structure grids (at most
+// 256) and the row scan (at most 4097 ints) first, then one buffer per warp
+constexpr size_t NL_BR_OFF = ((256 * sizeof(NlStruct) > 4097 * sizeof(int32_t) ? 256 * sizeof(NlStruct)
+                                                                               : 4097 * sizeof(int32_t)) + 127) / 128 * 128;
+static_assert(NL_BR_OFF + NL_WARPS * sizeof(BrBuf) <= NL_SMEM, "brute-force buffers exceed the search's shared memory");
+
+__device__ bool nl_brute_eligible(const NlArgs &a, const NlStruct *Ss) {
+    bool ok = true;
+    for (int b = threadIdx.x; b < a.B; b += blockDim.x) {
+        const NlStruct &q = Ss[b];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) ok = ok && q.K[d] == 1 && q.L[d] >= 2.001 * a.rc;
+    }
+    return __syncthreads_and(ok);
+}
+
+// wrap (as ph_bin) without the histogram; xs[i] = FP32 wrapped position with the packed cell
+// coordinates (cx | cy << 10 | cz << 20) in w, indexed by atom
+__device__ void ph_wrap_brute(const NlArgs &a, int bid, int nb, const NlStruct *S) {
+    const int lane = threadIdx.x & 31;
+    for (int ch = bid + nb * (threadIdx.x >> 5); ch * 32 < a.N; ch += nb * NL_WARPS) {
+        const int i = ch * 32 + lane;
+        if (i >= a.N) continue;
+        const int b = structure_of(a.atom_ptr, a.B, i);
+        const int z = a.species[i];
+        if (z < 0 || z >= a.n_species) set_status(a.status, GM_ERR_SPECIES);
+        const NlStruct &q = S[b];
+        int ic[3];
+        float wf[3];
+        for (int d = 0; d < 3; ++d) {
+            const double x = a.pos[3 * i + d];
+            int m;
+            const double w = wrap_axis(x, q.L[d], q.invL[d], m);
+            if (!(fabs(x) < 1.0e6 * q.L[d])) set_status(a.status, GM_ERR_UNSUPPORTED);
+            a.xw[3 * i + d] = w;
+            a.mimg[3 * i + d] = m;
+            int c = (int)floor(w * q.inv_cs[d]);
+            c = c < 0 ? 0 : (c >= q.nc[d] ? q.nc[d] - 1 : c);
+            ic[d] = c;
+            wf[d] = (float)w;
+        }
+        a.xs[i] = make_float4(wf[0], wf[1], wf[2], __int_as_float(ic[0] | (ic[1] << 10) | (ic[2] << 20)));
+    }
+}
+
+// Accepted pairs of atom i (structure q) into the warp's buffer, in ascending j; returns the
+// row length (entries beyond BR_CAP are counted, not stored)
+__device__ int brute_row(const NlArgs &a, const NlStruct &q, int i, int lane, BrBuf &bb) {
+    const unsigned full = 0xffffffffu, below = (1u << lane) - 1u;
+    const float4 xi = a.xs[i];
+    const double xi0 = a.xw[3 * i], xi1 = a.xw[3 * i + 1], xi2 = a.xw[3 * i + 2];
+    const int ci = __float_as_int(xi.w), cix = ci & 1023, ciy = (ci >> 10) & 1023, ciz = ci >> 20;
+    const float iL0 = 1.0f / q.Lf[0], iL1 = 1.0f / q.Lf[1], iL2 = 1.0f / q.Lf[2];
+    const float lo2 = a.rc2f - q.eps2, hi2 = a.rc2f + q.eps2;
+    const double rc2 = __dmul_rn(a.rc, a.rc);
+    int cnt = 0;
+    for (int base = q.a0; base < q.a0 + q.n; base += 32) {
+        const int j = base + lane;
+        const bool valid = j < q.a0 + q.n;
+        const float4 xj = valid ? a.xs[j] : make_float4(3.0e30f, 3.0e30f, 3.0e30f, 0.0f);
+        // minimum image n = -rint(d / L) per axis; d + n L
+        const float f0 = xj.x - xi.x, f1 = xj.y - xi.y, f2 = xj.z - xi.z;
+        const float n0 = -rintf(f0 * iL0), n1 = -rintf(f1 * iL1), n2 = -rintf(f2 * iL2);
+        const float dx = fmaf(n0, q.Lf[0], f0), dy = fmaf(n1, q.Lf[1], f1), dz = fmaf(n2, q.Lf[2], f2);
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        const bool other = valid && !(j == i && n0 == 0.0f && n1 == 0.0f && n2 == 0.0f);
+        bool in = other && r2 < lo2;
+        const bool band = other && !in && r2 <= hi2;               // inside the band: exact FP64 test
+        if (__any_sync(full, band)) {
+            if (band) in = exact_inside(a.xw, j, xi0, xi1, xi2, (int)n0, (int)n1, (int)n2, q, rc2);
+        }
+        const unsigned ball = __ballot_sync(full, in);
+        if (in) {
+            const int pos = cnt + __popc(ball & below);
+            const int cj = __float_as_int(xj.w);
+            const int sx = (cj & 1023) + (int)n0 * q.nc[0] - cix;
+            const int sy = ((cj >> 10) & 1023) + (int)n1 * q.nc[1] - ciy;
+            const int sz = (cj >> 20) + (int)n2 * q.nc[2] - ciz;
+            const unsigned st = (unsigned)((sz + 1) * 9 + (sy + 1) * 3 + (sx + 1));
+            if (pos < BR_CAP) {
+                bb.key[pos] = (st << 27) | (unsigned)j;
+                bb.img[pos] = bytes3((int)n0, (int)n1, (int)n2);
+            }
+        }
+        cnt += __popc(ball);
+    }
+    return cnt;
+}
+
+// The buffered row (cnt <= BR_CAP entries) in stencil order, stable in j: into slab row i
+// (codes; returns false when a shift has no code) or, with csr >= 0, into the CSR list at csr
+__device__ bool brute_emit(const NlArgs &a, int i, int cnt, int lane, BrBuf &bb, int csr) {
+    const unsigned full = 0xffffffffu, below = (1u << lane) - 1u;
+    if (lane < 32) bb.hist[lane] = 0;
+    __syncwarp();
+    for (int e = lane; e < cnt; e += 32) atomicAdd(&bb.hist[bb.key[e] >> 27], 1);
+    __syncwarp();
+    int h = lane < 27 ? bb.hist[lane] : 0, incl = h;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(full, incl, o);
+        if (lane >= o) incl += y;
+    }
+    bb.run[lane] = incl - h;                                    // exclusive offsets per stencil cell
+    __syncwarp();
+    const int mi0 = a.mimg[3 * i], mi1 = a.mimg[3 * i + 1], mi2 = a.mimg[3 * i + 2];
+    bool coded = true;
+    for (int e0 = 0; e0 < cnt; e0 += 32) {
+        const int e = e0 + lane;
+        const bool v = e < cnt;
+        const unsigned k = v ? bb.key[e] : 0u;
+        const unsigned st = v ? k >> 27 : 31u;
+        const unsigned m = __match_any_sync(full, st);
+        const int pos = bb.run[st] + __popc(m & below);
+        __syncwarp();
+        if (v) {
+            const int j = (int)(k & 0x7FFFFFFu);
+            const unsigned n = bb.img[e];
+            const int s0 = byte_at(n, 0) - a.mimg[3 * j] + mi0;
+            const int s1 = byte_at(n, 1) - a.mimg[3 * j + 1] + mi1;
+            const int s2 = byte_at(n, 2) - a.mimg[3 * j + 2] + mi2;
+            if (csr >= 0) {
+                store_pair(a, csr + pos, j, s0, s1, s2);
+            } else {
+                const unsigned code = shift_code(bytes3(s0, s1, s2));
+                coded = coded && code != NL_NOCODE;
+                a.slab[(size_t)i * a.maxn + pos] = (unsigned)j | (code << 27);
+            }
+            if (lane == __ffs(m) - 1) bb.run[st] += __popc(m);
+        }
+        __syncwarp();
+    }
+    return __all_sync(full, coded);
+}
+
+// One atom per warp: rows into the slab (counts, redo marks as the cell-list search)
+__device__ void ph_search_brute(const NlArgs &a, int bid, int nb, const NlStruct *Ss, BrBuf *bufs) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    BrBuf &bb = bufs[warp];
+    for (int i = bid * NL_WARPS + warp; i < a.N; i += nb * NL_WARPS) {
+        const NlStruct &q = Ss[structure_of(a.atom_ptr, a.B, i)];
+        const int cnt = brute_row(a, q, i, lane, bb);
+        if (cnt > BR_CAP) {
+            if (lane == 0) atomicExch(a.brute_over, 1);
+            continue;
+        }
+        bool over = cnt > a.maxn;
+        if (!over) over = !brute_emit(a, i, cnt, lane, bb, -1);
+        if (lane == 0) {
+            a.counts[i] = cnt;
+            a.redo[i] = over ? 1 : 0;
+            if (over) nl_redo(a, i);
+        }
+    }
+}
+
 // Compaction after the slab pass: each warp copies NL_COPY_ROWS slab rows at a time into
 // their CSR rows (all loads of a step before its stores); rows marked for a redo -- longer
 // than the slab, or of structures that take the per-atom search -- are searched again
 // straight into the CSR row.
 constexpr int NL_COPY_ROWS = 4;
 
-__device__ void ph_compact(const NlArgs &a, int bid, int nb, const int32_t *row_ptr) {
+__device__ void ph_compact(const NlArgs &a, int bid, int nb, const int32_t *row_ptr, BrBuf *brute = nullptr) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned full = 0xffffffffu;
     if (__shfl_sync(full, lane == 0 ? (int)status_bad(a.status) : 0, 0)) return;
@@ -1137,6 +1311,12 @@ __device__ void ph_compact(const NlArgs &a, int bid, int nb, const int32_t *row_
     const int nredo = min(*a.n_redo, a.N);
     for (int r = gw; r < nredo; r += nw) {
         const int i = a.redo_list[r];
+        if (brute) {                                   // rows of the brute-force search (<= BR_CAP)
+            BrBuf &bb = brute[warp];
+            const int cnt = brute_row(a, a.S[structure_of(a.atom_ptr, a.B, i)], i, lane, bb);
+            brute_emit(a, i, min(cnt, BR_CAP), lane, bb, row_ptr[i]);
+            continue;
+        }
         const int c = a.cellid[i];
         const NlStruct &q = a.S[a.cstruct[c]];
         const float4 me = make_float4((float)a.xw[3 * i], (float)a.xw[3 * i + 1], (float)a.xw[3 * i + 2],
@@ -1189,6 +1369,21 @@ __global__ void __launch_bounds__(NL_THREADS, 2) k_nl_coop(NlArgs a) {
         NlStruct *Ss = reinterpret_cast<NlStruct *>(nl_smem);
         int32_t *si = reinterpret_cast<int32_t *>(nl_smem);
         ph_setup_local(a, bid, Ss);
+        if (a.try_brute && nl_brute_eligible(a, Ss)) {
+            BrBuf *bufs = reinterpret_cast<BrBuf *>(reinterpret_cast<char *>(nl_smem) + NL_BR_OFF);
+            ph_wrap_brute(a, bid, nb, Ss);
+            if (!nl_grid_sync(a.bar, a.status)) return;
+            ph_search_brute(a, bid, nb, Ss, bufs);
+            if (!nl_grid_sync(a.bar, a.status)) return;
+            if (*reinterpret_cast<volatile int *>(a.brute_over) == 0) {
+                ph_scan_local(a.counts, a.N, si, bid, a.row_ptr, a.cap, a.n_pairs, a.status);
+                if ((int64_t)si[a.N] > a.cap) return;
+                ph_compact(a, bid, nb, si, bufs);
+                return;
+            }
+            // a row longer than BR_CAP: the cell-list path below builds the list instead
+            if (bid == 0 && threadIdx.x == 0) *a.n_redo = 0;
+        }
         for (int c = bid * NL_THREADS + threadIdx.x; c < a.ncmax; c += nb * NL_THREADS) a.cfill[c] = 0;
         ph_bin(a, bid, nb, Ss);
         if (!nl_grid_sync(a.bar, a.status)) return;
@@ -1248,7 +1443,7 @@ __global__ void __launch_bounds__(NL_THREADS, 2) k_nl_phase(NlArgs a, int ph) {
 struct NlWs {
     NlStruct *S;
     int32_t *ncells, *mimg, *cellid, *ccount, *cstart, *cfill, *unsorted, *counts, *bsum, *redo_list, *n_redo;
-    int32_t *cstruct, *item_ctr;
+    int32_t *cstruct, *item_ctr, *brute_over;
     uint32_t *xsm, *mpk;
     uint8_t *redo;
     uint32_t *slab;
@@ -1270,6 +1465,7 @@ static NlWs carve_nl(Carve &c, int B, int N) {
     w.ccount = c.take<int32_t>(ncmax + 64);                        // histogram, then the barrier words
     w.bar = reinterpret_cast<unsigned *>(w.ccount + ncmax + 32);
     w.item_ctr = w.ccount + ncmax + 40;                            // search item counters (same memset)
+    w.brute_over = w.ccount + ncmax + 44;                          // brute-force overflow flag (same memset)
     w.cstruct = c.take<int32_t>(ncmax);
     w.cstart = c.take<int32_t>(ncmax + 1);
     w.cfill = c.take<int32_t>(ncmax);
@@ -1399,6 +1595,10 @@ gm_status nl_build(const gm_system &sys, double r_cut, int n_species, gm_nlist &
     // cell histogram and barrier words start at zero
     if (cudaMemsetAsync(w.ccount, 0, sizeof(int32_t) * ((size_t)ncmax + 64), st) != cudaSuccess) return GM_ERR_CUDA;
     a.small = (N + B <= NL_SCAN_ONE_BLOCK && B <= 256) ? 1 : 0;
+    // brute-force search (small systems, single-image boxes; decided on the device) unless the
+    // work items are set to cells, or there is no slab
+    a.try_brute = (tune.items == 0 || tune.items == 3) && a.maxn > 0 ? 1 : 0;
+    a.brute_over = w.brute_over;
     auto clampi = [](long long v, long long lo, long long hi) { return (int)(v < lo ? lo : (v > hi ? hi : v)); };
     if (tune.mode != GM_NL_MODE_PHASES && dev.coop_blocks > 0) {
         // one cooperative launch, at most as many blocks as are co-resident

@@ -102,7 +102,7 @@ def test_neighbors_exactly_at_cutoff():
 NL_TUNINGS = [dict(nl_mode=0), dict(nl_mode=1), dict(nl_mode=0, nl_split=1), dict(nl_mode=0, nl_split=3, nl_blocks=7),
               dict(nl_mode=1, nl_split=2), dict(nl_mode=0, nl_blocks=1), dict(nl_mode=0, nl_two_pass=1),
               dict(nl_mode=1, nl_two_pass=1, nl_split=5), dict(nl_items=1), dict(nl_items=2),
-              dict(nl_items=1, nl_split=3, nl_two_pass=1), dict(nl_items=2, nl_split=3, nl_mode=1)]
+              dict(nl_items=1, nl_split=3, nl_two_pass=1), dict(nl_items=2, nl_split=3, nl_mode=1), dict(nl_items=3)]
 
 
 def _ragged_batch():
@@ -169,6 +169,31 @@ def test_neighbors_rows_longer_than_the_search_slab():
             assert np.diff(cur[0]).max() > slab_row                   # some rows exceed the slab
         else:
             assert all(np.array_equal(x, y) for x, y in zip(cur, ref)), tune
+
+
+def test_brute_force_rows_beyond_the_buffer_fall_back_to_cells():
+    """A single-image box whose dense ball gives rows longer than the brute-force search's
+    shared-memory buffer: the build switches to the cell list and still returns the oracle's
+    pairs, in the same rows as an explicit cell-list build."""
+    GMNN, DeviceSystem = _gm()
+    _, d, p = synth.config(1)
+    rng = np.random.default_rng(17)
+    L = 40.0
+    ball = 20.0 + rng.normal(0.0, 1.2, (700, 3))
+    sparse = rng.uniform(0.0, L, (300, 3))
+    pos = np.concatenate([sparse[:150], ball, sparse[150:]])
+    b = make_batch([(pos, rng.integers(0, 5, len(pos)), L * np.eye(3))], 5)
+    want = oracle.neighbors(b, d["r_cut"])
+    assert np.diff(want.row_ptr).max() > 512
+    rows = []
+    for tune in (dict(), dict(nl_items=1)):
+        m = GMNN(d, p)
+        m.set_tuning(**tune)
+        nl = m.build_neighbors(DeviceSystem(b))
+        assert np.array_equal(nl.triples(), want.triples()), tune
+        P = int(nl.n_pairs.item())
+        rows.append((nl.row_ptr.cpu().numpy(), nl.col[:P].cpu().numpy(), nl.shift[:P].cpu().numpy()))
+    assert all(np.array_equal(x, y) for x, y in zip(rows[0], rows[1]))
 
 
 def test_neighbor_build_is_graph_capturable():
