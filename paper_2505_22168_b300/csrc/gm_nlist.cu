@@ -214,12 +214,16 @@ __device__ int nl_struct_setup(const NlArgs &a, int b, NlStruct &q) {
     q.n = a.atom_ptr[b + 1] - q.a0;
     bool ok = ortho && periodic && positive;
     long long nc[3];
-    const double cells_per_len = 1.0 / (a.rc * (1.0 + 1e-5));   // cell edge >= r_cut (1 + 1e-5)
+    // Only L and 1/L (the FP64 wrap) need FP64; the grid (cells per axis, cells per length,
+    // stencil widths) and the filter band need to be consistent and conservative, and FP32
+    // keeps B300's slow FP64 unit off this per-build latency chain.  Cells stay at least
+    // r_cut (1 + 1e-5) long, a margin far above the FP32 rounding.
+    const float cells_per_len = 1.0f / ((float)a.rc * (1.0f + 1e-5f));
     for (int d = 0; d < 3; ++d) {
         q.L[d] = ok ? C[4 * d] : 1.0;
         q.invL[d] = 1.0 / q.L[d];
-        const double f = floor(q.L[d] * cells_per_len);
-        nc[d] = f < 1.0 ? 1 : (f > 1024.0 ? 1024 : (long long)f);
+        const float f = floorf((float)q.L[d] * cells_per_len * (1.0f - 1e-6f));
+        nc[d] = f < 1.0f ? 1 : (f > 1024.0f ? 1024 : (long long)f);
     }
     const long long limit = q.n > 1 ? q.n : 1;
     while (nc[0] * nc[1] * nc[2] > limit) {
@@ -229,25 +233,27 @@ __device__ int nl_struct_setup(const NlArgs &a, int b, NlStruct &q) {
         nc[am] -= 1;
     }
     int Kmax = 0;
-    double Lmax = 0.0;
+    float Lmax = 0.0f;
+    const float rcf = (float)a.rc;
     for (int d = 0; d < 3; ++d) {
         q.nc[d] = (int)nc[d];
-        q.inv_cs[d] = (double)nc[d] * q.invL[d];
-        int K = (int)ceil(a.rc * q.inv_cs[d] + 1e-6);
+        q.Lf[d] = (float)q.L[d];
+        const float ics = (float)nc[d] / q.Lf[d];
+        q.inv_cs[d] = (double)ics;
+        int K = (int)ceilf(rcf * ics * (1.0f + 1e-6f) + 1e-6f);
         if (K > 100) { ok = false; K = 0; }
         q.K[d] = ok ? K : 0;
-        q.Lf[d] = (float)q.L[d];
         Kmax = K > Kmax ? K : Kmax;
-        Lmax = q.L[d] > Lmax ? q.L[d] : Lmax;
+        Lmax = q.Lf[d] > Lmax ? q.Lf[d] : Lmax;
     }
     if (!ok) set_status(a.status, GM_ERR_UNSUPPORTED);
     // FP32 filter error per axis: the roundings of the two wrapped coordinates and of the
     // image offset (each <= 2^-24 L), of the shifted coordinate (<= 2^-24 2L) and of the
     // difference (<= 2^-24 r_cut near the cutoff) stay below 2^-24 L (8 + 4K); the band
-    // bounds the resulting r^2 error near r_cut
-    const double u = 5.9604644775390625e-8;  // 2^-24
-    const double e = u * Lmax * (8.0 + 4.0 * Kmax);
-    q.eps2 = (float)(4.0 * (2.0 * 1.7320508075688772 * e * a.rc + 3.0 * e * e + 4.0 * u * a.rc * a.rc) + 1e-30);
+    // bounds the resulting r^2 error near r_cut (x 4, and x 1.01 over the FP32 evaluation)
+    const float u = 5.9604644775390625e-8f;  // 2^-24
+    const float e = u * Lmax * (8.0f + 4.0f * (float)Kmax);
+    q.eps2 = 1.01f * (4.0f * (2.0f * 1.7320508f * e * rcf + 3.0f * e * e + 4.0f * u * rcf * rcf)) + 1e-30f;
     return q.nc[0] * q.nc[1] * q.nc[2];
 }
 
