@@ -1167,10 +1167,22 @@ __device__ int brute_row(const NlArgs &a, const NlStruct &q, int i, int lane, Br
     const float lo2 = a.rc2f - q.eps2, hi2 = a.rc2f + q.eps2;
     const double rc2 = __dmul_rn(a.rc, a.rc);
     int cnt = 0;
-    for (int base = q.a0; base < q.a0 + q.n; base += 32) {
+    constexpr int BU = 8;                                       // chunks loaded together
+    const int aend = q.a0 + q.n;
+    for (int b0 = q.a0; b0 < aend; b0 += 32 * BU) {
+      float4 xb[BU];
+#pragma unroll
+      for (int u = 0; u < BU; ++u) {
+        const int j = b0 + 32 * u + lane;
+        xb[u] = j < aend ? a.xs[j] : make_float4(3.0e30f, 3.0e30f, 3.0e30f, 0.0f);
+      }
+#pragma unroll
+      for (int u = 0; u < BU; ++u) {
+        const int base = b0 + 32 * u;
+        if (base >= aend) break;                                // uniform over the warp
         const int j = base + lane;
-        const bool valid = j < q.a0 + q.n;
-        const float4 xj = valid ? a.xs[j] : make_float4(3.0e30f, 3.0e30f, 3.0e30f, 0.0f);
+        const bool valid = j < aend;
+        const float4 xj = xb[u];
         // minimum image n = -rint(d / L) per axis; d + n L
         const float f0 = xj.x - xi.x, f1 = xj.y - xi.y, f2 = xj.z - xi.z;
         const float n0 = -rintf(f0 * iL0), n1 = -rintf(f1 * iL1), n2 = -rintf(f2 * iL2);
@@ -1196,6 +1208,7 @@ __device__ int brute_row(const NlArgs &a, const NlStruct &q, int i, int lane, Br
             }
         }
         cnt += __popc(ball);
+      }
     }
     return cnt;
 }
