@@ -204,15 +204,28 @@ __device__ __forceinline__ int block_sum(int v) {
 }
 
 // ------------------------------------------------------------------ setup
-// Cell grid of structure b (FP64, fixed operation order).  Returns its number of cells.
-__device__ int nl_struct_setup(const NlArgs &a, int b, NlStruct &q) {
+// Box checks on the bit patterns (integer compares keep them off the FP64 unit): an entry is
+// zero (+0 or -0), or positive (above +0, at most +inf: NaN fails as in a comparison).
+__device__ __forceinline__ bool dzero(double v) { return (__double_as_longlong(v) << 1) == 0; }
+__device__ __forceinline__ bool dpositive(double v) {
+    const long long b = __double_as_longlong(v);
+    return b > 0 && b <= 0x7FF0000000000000ll;
+}
+// Orthorhombic, periodic on every axis, positive edges
+__device__ __forceinline__ bool box_supported(const NlArgs &a, int b) {
     const double *C = a.cell + 9 * b;
-    const bool ortho = C[1] == 0.0 && C[2] == 0.0 && C[3] == 0.0 && C[5] == 0.0 && C[6] == 0.0 && C[7] == 0.0;
+    const bool ortho = dzero(C[1]) && dzero(C[2]) && dzero(C[3]) && dzero(C[5]) && dzero(C[6]) && dzero(C[7]);
     const bool periodic = a.pbc[3 * b] && a.pbc[3 * b + 1] && a.pbc[3 * b + 2];
-    const bool positive = C[0] > 0.0 && C[4] > 0.0 && C[8] > 0.0;
+    return ortho && periodic && dpositive(C[0]) && dpositive(C[4]) && dpositive(C[8]);
+}
+
+// Cell grid of structure b (FP64, fixed operation order).  Returns its number of cells.
+// inv3, when given, holds the three reciprocals 1 / L already (computed one per thread).
+__device__ int nl_struct_setup(const NlArgs &a, int b, NlStruct &q, const double *inv3 = nullptr) {
+    const double *C = a.cell + 9 * b;
     q.a0 = a.atom_ptr[b];
     q.n = a.atom_ptr[b + 1] - q.a0;
-    bool ok = ortho && periodic && positive;
+    bool ok = box_supported(a, b);
     long long nc[3];
     // Only L and 1/L (the FP64 wrap) need FP64; the grid (cells per axis, cells per length,
     // stencil widths) and the filter band need to be consistent and conservative, and FP32
@@ -221,7 +234,7 @@ __device__ int nl_struct_setup(const NlArgs &a, int b, NlStruct &q) {
     const float cells_per_len = 1.0f / ((float)a.rc * (1.0f + 1e-5f));
     for (int d = 0; d < 3; ++d) {
         q.L[d] = ok ? C[4 * d] : 1.0;
-        q.invL[d] = 1.0 / q.L[d];
+        q.invL[d] = inv3 ? inv3[d] : 1.0 / q.L[d];
         const float f = floorf((float)q.L[d] * cells_per_len * (1.0f - 1e-6f));
         nc[d] = f < 1.0f ? 1 : (f > 1024.0f ? 1024 : (long long)f);
     }
@@ -287,11 +300,24 @@ __device__ void ph_setup(const NlArgs &a, int bid, int nb) {
 static_assert(256 * sizeof(NlStruct) <= NL_WARPS * 512 * (sizeof(float4) + sizeof(unsigned)),
               "the structures of a small batch must fit in the search's shared memory");
 __device__ void ph_setup_local(const NlArgs &a, int bid, NlStruct *Ss) {
+    // the 3 B reciprocals 1 / L first, one per thread (FP64 divisions in parallel), into the
+    // structures' own slots
+    for (int t = threadIdx.x; t < 3 * a.B; t += NL_THREADS) {
+        const int b = t / 3, d = t - 3 * b;
+        Ss[b].invL[d] = 1.0 / (box_supported(a, b) ? a.cell[9 * b + 4 * d] : 1.0);
+    }
+    __syncthreads();
     int carry = 0;
     for (int chunk = 0; chunk < a.B; chunk += NL_THREADS) {
         const int b = chunk + threadIdx.x;
         NlStruct q;
-        const int ncell = b < a.B ? nl_struct_setup(a, b, q) : 0;
+        double inv3[3];
+        if (b < a.B) {
+            inv3[0] = Ss[b].invL[0];
+            inv3[1] = Ss[b].invL[1];
+            inv3[2] = Ss[b].invL[2];
+        }
+        const int ncell = b < a.B ? nl_struct_setup(a, b, q, inv3) : 0;
         int tot;
         const int pre = block_exclusive_scan(ncell, &tot);
         if (b < a.B) {
@@ -1104,10 +1130,15 @@ __device__ void ph_search_block(const NlArgs &a, int bid, int nb, float4 *smem) 
 // being at least r_cut long), and the accepted pairs, found in ascending j, are placed by a
 // stable counting sort on that stencil index.  A row longer than BR_CAP (shared memory)
 // sends the whole build back to the cell-list path.
+//
+// A buffered pair is one word: stencil << 27 | image << 22 | j, the image n coded as
+// (n_x + 1) + 3 (n_y + 1) + 9 (n_z + 1) and j < 2^22.  The per-atom cell word of the wrap,
+// w = c_x + 3 c_y + 9 c_z (an exact small integer in FP32), gives the stencil index
+// (s_x + 1) + 3 (s_y + 1) + 9 (s_z + 1) as 13 + w_j - w_i + n . (nc_x, 3 nc_y, 9 nc_z).
 constexpr int BR_CAP = 512;
+static_assert(GM_MAX_ATOMS <= (1 << 22), "brute-force keys hold the neighbour index in 22 bits");
 struct BrBuf {
-    unsigned key[BR_CAP];   // stencil << 27 | j
-    unsigned img[BR_CAP];   // bytes3 of the image n (each component in {-1, 0, 1})
+    unsigned key[BR_CAP];
     int hist[32], run[32];
 };
 
@@ -1122,37 +1153,43 @@ __device__ bool nl_brute_eligible(const NlArgs &a, const NlStruct *Ss) {
     for (int b = threadIdx.x; b < a.B; b += blockDim.x) {
         const NlStruct &q = Ss[b];
 #pragma unroll
-        for (int d = 0; d < 3; ++d) ok = ok && q.K[d] == 1 && q.L[d] >= 2.001 * a.rc;
+        for (int d = 0; d < 3; ++d) ok = ok && q.K[d] == 1 && q.Lf[d] >= 2.001f * (float)a.rc;
     }
     return __syncthreads_and(ok);
 }
 
-// wrap (as ph_bin) without the histogram; xs[i] = FP32 wrapped position with the packed cell
-// coordinates (cx | cy << 10 | cz << 20) in w, indexed by atom
+// wrap (as ph_bin) without the histogram; xs[i] = FP32 wrapped position with the cell word
+// c_x + 3 c_y + 9 c_z (as a float) in w, indexed by atom.  One lane per axis (ten atoms per
+// warp, lanes 30 and 31 idle): the FP64 wrap of an atom runs on three lanes at once, and its
+// axis-0 lane gathers the other two by shuffles.
 __device__ void ph_wrap_brute(const NlArgs &a, int bid, int nb, const NlStruct *S) {
-    const int lane = threadIdx.x & 31;
-    for (int ch = bid + nb * (threadIdx.x >> 5); ch * 32 < a.N; ch += nb * NL_WARPS) {
-        const int i = ch * 32 + lane;
-        if (i >= a.N) continue;
-        const int b = structure_of(a.atom_ptr, a.B, i);
-        const int z = a.species[i];
-        if (z < 0 || z >= a.n_species) set_status(a.status, GM_ERR_SPECIES);
-        const NlStruct &q = S[b];
-        int ic[3];
-        float wf[3];
-        for (int d = 0; d < 3; ++d) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, ga = lane / 3, d = lane - 3 * ga;
+    const int l1 = min(3 * ga + 1, 31), l2 = min(3 * ga + 2, 31);
+    for (int g = bid + nb * (threadIdx.x >> 5); g * 10 < a.N; g += nb * NL_WARPS) {
+        const int i = g * 10 + ga;
+        const bool act = lane < 30 && i < a.N;
+        float wf = 0.0f;
+        int c = 0;
+        if (act) {
+            const NlStruct &q = S[structure_of(a.atom_ptr, a.B, i)];
+            if (d == 0) {
+                const int z = a.species[i];
+                if (z < 0 || z >= a.n_species) set_status(a.status, GM_ERR_SPECIES);
+            }
             const double x = a.pos[3 * i + d];
             int m;
             const double w = wrap_axis(x, q.L[d], q.invL[d], m);
             if (!(fabs(x) < 1.0e6 * q.L[d])) set_status(a.status, GM_ERR_UNSUPPORTED);
             a.xw[3 * i + d] = w;
             a.mimg[3 * i + d] = m;
-            int c = (int)floor(w * q.inv_cs[d]);
+            c = (int)floor(w * q.inv_cs[d]);
             c = c < 0 ? 0 : (c >= q.nc[d] ? q.nc[d] - 1 : c);
-            ic[d] = c;
-            wf[d] = (float)w;
+            wf = (float)w;
         }
-        a.xs[i] = make_float4(wf[0], wf[1], wf[2], __int_as_float(ic[0] | (ic[1] << 10) | (ic[2] << 20)));
+        const float w1 = __shfl_sync(full, wf, l1), w2 = __shfl_sync(full, wf, l2);
+        const int c1 = __shfl_sync(full, c, l1), c2 = __shfl_sync(full, c, l2);
+        if (act && d == 0) a.xs[i] = make_float4(wf, w1, w2, (float)(c + 3 * c1 + 9 * c2));
     }
 }
 
@@ -1161,54 +1198,63 @@ __device__ void ph_wrap_brute(const NlArgs &a, int bid, int nb, const NlStruct *
 __device__ int brute_row(const NlArgs &a, const NlStruct &q, int i, int lane, BrBuf &bb) {
     const unsigned full = 0xffffffffu, below = (1u << lane) - 1u;
     const float4 xi = a.xs[i];
-    const double xi0 = a.xw[3 * i], xi1 = a.xw[3 * i + 1], xi2 = a.xw[3 * i + 2];
-    const int ci = __float_as_int(xi.w), cix = ci & 1023, ciy = (ci >> 10) & 1023, ciz = ci >> 20;
-    const float iL0 = 1.0f / q.Lf[0], iL1 = 1.0f / q.Lf[1], iL2 = 1.0f / q.Lf[2];
+    const float L0 = q.Lf[0], L1 = q.Lf[1], L2 = q.Lf[2];
+    const float iL0 = 1.0f / L0, iL1 = 1.0f / L1, iL2 = 1.0f / L2;
     const float lo2 = a.rc2f - q.eps2, hi2 = a.rc2f + q.eps2;
-    const double rc2 = __dmul_rn(a.rc, a.rc);
+    const float sc0 = (float)q.nc[0], sc1 = 3.0f * (float)q.nc[1], sc2 = 9.0f * (float)q.nc[2];
+    const float soff = 13.0f - xi.w;
     int cnt = 0;
-    constexpr int BU = 8;                                       // chunks loaded together
+    // batches of BU chunks of 32 candidates: the tests of a batch are independent (one
+    // vote for its band pairs), the ballots and stores follow in candidate order
+    constexpr int BU = 8;
     const int aend = q.a0 + q.n;
     for (int b0 = q.a0; b0 < aend; b0 += 32 * BU) {
-      float4 xb[BU];
+        float4 xb[BU];
 #pragma unroll
-      for (int u = 0; u < BU; ++u) {
-        const int j = b0 + 32 * u + lane;
-        xb[u] = j < aend ? a.xs[j] : make_float4(3.0e30f, 3.0e30f, 3.0e30f, 0.0f);
-      }
-#pragma unroll
-      for (int u = 0; u < BU; ++u) {
-        const int base = b0 + 32 * u;
-        if (base >= aend) break;                                // uniform over the warp
-        const int j = base + lane;
-        const bool valid = j < aend;
-        const float4 xj = xb[u];
-        // minimum image n = -rint(d / L) per axis; d + n L
-        const float f0 = xj.x - xi.x, f1 = xj.y - xi.y, f2 = xj.z - xi.z;
-        const float n0 = -rintf(f0 * iL0), n1 = -rintf(f1 * iL1), n2 = -rintf(f2 * iL2);
-        const float dx = fmaf(n0, q.Lf[0], f0), dy = fmaf(n1, q.Lf[1], f1), dz = fmaf(n2, q.Lf[2], f2);
-        const float r2 = dx * dx + dy * dy + dz * dz;
-        const bool other = valid && !(j == i && n0 == 0.0f && n1 == 0.0f && n2 == 0.0f);
-        bool in = other && r2 < lo2;
-        const bool band = other && !in && r2 <= hi2;               // inside the band: exact FP64 test
-        if (__any_sync(full, band)) {
-            if (band) in = exact_inside(a.xw, j, xi0, xi1, xi2, (int)n0, (int)n1, (int)n2, q, rc2);
+        for (int u = 0; u < BU; ++u) {
+            const int j = b0 + 32 * u + lane;
+            xb[u] = j < aend ? a.xs[j] : make_float4(3.0e30f, 3.0e30f, 3.0e30f, 0.0f);
         }
-        const unsigned ball = __ballot_sync(full, in);
-        if (in) {
-            const int pos = cnt + __popc(ball & below);
-            const int cj = __float_as_int(xj.w);
-            const int sx = (cj & 1023) + (int)n0 * q.nc[0] - cix;
-            const int sy = ((cj >> 10) & 1023) + (int)n1 * q.nc[1] - ciy;
-            const int sz = (cj >> 20) + (int)n2 * q.nc[2] - ciz;
-            const unsigned st = (unsigned)((sz + 1) * 9 + (sy + 1) * 3 + (sx + 1));
-            if (pos < BR_CAP) {
-                bb.key[pos] = (st << 27) | (unsigned)j;
-                bb.img[pos] = bytes3((int)n0, (int)n1, (int)n2);
+        unsigned key[BU], inm = 0u, bandm = 0u;
+#pragma unroll
+        for (int u = 0; u < BU; ++u) {
+            const int j = b0 + 32 * u + lane;
+            // minimum image n = -rint(d / L) per axis (boxes of at least 2 r_cut: the one
+            // image that can be within r_cut; atom i's own images cannot)
+            const float f0 = xb[u].x - xi.x, f1 = xb[u].y - xi.y, f2 = xb[u].z - xi.z;
+            const float n0 = -rintf(f0 * iL0), n1 = -rintf(f1 * iL1), n2 = -rintf(f2 * iL2);
+            const float dx = fmaf(n0, L0, f0), dy = fmaf(n1, L1, f1), dz = fmaf(n2, L2, f2);
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            const bool other = j < aend && j != i;
+            inm |= (other && r2 < lo2) ? 1u << u : 0u;
+            bandm |= (other && r2 >= lo2 && r2 <= hi2) ? 1u << u : 0u;  // band: exact FP64 test
+            const float st = fmaf(n2, sc2, fmaf(n1, sc1, fmaf(n0, sc0, xb[u].w + soff)));
+            const float img = fmaf(n2, 9.0f, fmaf(n1, 3.0f, n0 + 13.0f));
+            // st 32 + img < 2^10 for a pair within r_cut, an integer: the low mantissa bits of
+            // its sum with 2^23
+            const unsigned v = (unsigned)__float_as_int(fmaf(st, 32.0f, img) + 8388608.0f);
+            key[u] = (v << 22) | (unsigned)j;
+        }
+        if (__any_sync(full, bandm != 0u)) {
+#pragma unroll
+            for (int u = 0; u < BU; ++u) {
+                if (!((bandm >> u) & 1u)) continue;
+                const int j = b0 + 32 * u + lane;
+                const float n0 = -rintf((xb[u].x - xi.x) * iL0), n1 = -rintf((xb[u].y - xi.y) * iL1),
+                            n2 = -rintf((xb[u].z - xi.z) * iL2);
+                if (exact_inside(a.xw, j, a.xw[3 * i], a.xw[3 * i + 1], a.xw[3 * i + 2], (int)n0, (int)n1, (int)n2,
+                                 q, __dmul_rn(a.rc, a.rc)))
+                    inm |= 1u << u;
             }
         }
-        cnt += __popc(ball);
-      }
+#pragma unroll
+        for (int u = 0; u < BU; ++u) {
+            const bool in = (inm >> u) & 1u;
+            const unsigned ball = __ballot_sync(full, in);
+            const int pos = cnt + __popc(ball & below);
+            if (in && pos < BR_CAP) bb.key[pos] = key[u];
+            cnt += __popc(ball);
+        }
     }
     return cnt;
 }
@@ -1240,11 +1286,11 @@ __device__ bool brute_emit(const NlArgs &a, int i, int cnt, int lane, BrBuf &bb,
         const int pos = bb.run[st] + __popc(m & below);
         __syncwarp();
         if (v) {
-            const int j = (int)(k & 0x7FFFFFFu);
-            const unsigned n = bb.img[e];
-            const int s0 = byte_at(n, 0) - a.mimg[3 * j] + mi0;
-            const int s1 = byte_at(n, 1) - a.mimg[3 * j + 1] + mi1;
-            const int s2 = byte_at(n, 2) - a.mimg[3 * j + 2] + mi2;
+            const int j = (int)(k & 0x3FFFFFu);
+            const int img = (int)((k >> 22) & 31u);
+            const int s0 = img % 3 - 1 - a.mimg[3 * j] + mi0;
+            const int s1 = (img / 3) % 3 - 1 - a.mimg[3 * j + 1] + mi1;
+            const int s2 = img / 9 - 1 - a.mimg[3 * j + 2] + mi2;
             if (csr >= 0) {
                 store_pair(a, csr + pos, j, s0, s1, s2);
             } else {
@@ -1259,11 +1305,16 @@ __device__ bool brute_emit(const NlArgs &a, int i, int cnt, int lane, BrBuf &bb,
     return __all_sync(full, coded);
 }
 
-// One atom per warp: rows into the slab (counts, redo marks as the cell-list search)
+// One atom per warp: rows into the slab (counts, redo marks as the cell-list search).  Row
+// i = s nb + bid goes to warp (s + rot) mod NL_WARPS of block bid: rows spread over all
+// blocks first, and the second half of the grid (the second block of each SM when the
+// blocks fill the SMs in order) starts a quarter of the block further on, so that two
+// blocks on one SM keep their busy warps on different schedulers.
 __device__ void ph_search_brute(const NlArgs &a, int bid, int nb, const NlStruct *Ss, BrBuf *bufs) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     BrBuf &bb = bufs[warp];
-    for (int i = bid * NL_WARPS + warp; i < a.N; i += nb * NL_WARPS) {
+    const int rot = bid >= (nb >> 1) ? NL_WARPS / 4 : 0;
+    for (int i = ((warp - rot + NL_WARPS) % NL_WARPS) * nb + bid; i < a.N; i += NL_WARPS * nb) {
         const NlStruct &q = Ss[structure_of(a.atom_ptr, a.B, i)];
         const int cnt = brute_row(a, q, i, lane, bb);
         if (cnt > BR_CAP) {
