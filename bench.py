@@ -113,14 +113,14 @@ h = nv.handle(sys.argv[1], int(sys.argv[2]))
 print("max", nv.max_clock(h), flush=True)
 while True:
     print("s", time.monotonic(), nv.clock(h), nv.reasons(h), nv.power_w(h), flush=True)
-    r, _, _ = select.select([sys.stdin], [], [], 0.005)
+    r, _, _ = select.select([sys.stdin], [], [], 0.001)
     if r:
         break
 """
 
 
 class ClockSampler:
-    """SM clock, power and clock-event reasons sampled about every 5 ms through NVML (read
+    """SM clock, power and clock-event reasons sampled about every 1 ms through NVML (read
     only) by a child process while the timed region runs (no contention with the launch
     loop).  The region starts once the child has taken its first sample; samples carry the
     child's monotonic time and the summary keeps those inside the region, plus the first one
