@@ -64,8 +64,20 @@ __global__ void __launch_bounds__(REDUCE_CHUNK) k_reduce(int B, int N, const int
     int b = -1;
     bool bad = false;
     if (i < N) {
+        // the atom's partials (an even count, at most 16: H in 64..512) loaded together as
+        // float2, then added in order
+        float2 pt[8];
+        const float2 *row = reinterpret_cast<const float2 *>(nn_part + (size_t)i * nparts);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) pt[t] = 2 * t < nparts ? row[t] : make_float2(0.0f, 0.0f);
         float nn = b3[0];
-        for (int t = 0; t < nparts; ++t) nn += nn_part[(size_t)i * nparts + t];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            if (2 * t < nparts) {
+                nn += pt[t].x;
+                nn += pt[t].y;
+            }
+        }
         const int z = min(max(species[i], 0), S - 1);
         v[0] = to_fixed(fmaf(sigma[z], nn, mu[z]), bad);
         if (vir_atom)
@@ -79,7 +91,9 @@ __global__ void __launch_bounds__(REDUCE_CHUNK) k_reduce(int B, int N, const int
         const int bl = __shfl_sync(0xffffffffu, b, lead);
         const bool mine = b == bl;
         todo &= ~__ballot_sync(0xffffffffu, mine);
-        for (int q = 0; q < nv; ++q) {
+#pragma unroll
+        for (int q = 0; q < 10; ++q) {
+            if (q >= nv) break;
             long long x = mine ? v[q] : 0;
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
@@ -116,6 +130,11 @@ void launch_struct_reduce(int B, int N, const int32_t *atom_ptr, const int32_t *
                           const float *mu, const float *b3, const float *nn_part, int nparts, const float *vir_atom,
                           unsigned long long *acc, double *energy, double *virial, cudaStream_t st) {
     if (B <= 0) return;
+    if (nparts < 2 || nparts > 16 || nparts % 2 != 0) {     // H in 64..512, a multiple of 64
+        cudaMemsetAsync(energy, 0xff, sizeof(double) * B, st);   // NaN: not a supported width
+        if (virial) cudaMemsetAsync(virial, 0xff, sizeof(double) * 9 * B, st);
+        return;
+    }
     if (N <= 0) {                                    // no atoms: every structure sums to zero
         cudaMemsetAsync(energy, 0, sizeof(double) * B, st);
         if (virial) cudaMemsetAsync(virial, 0, sizeof(double) * 9 * B, st);
