@@ -890,28 +890,51 @@ void launch_contract_bwd_dual(const float *psi, const float *psid, const float *
     }
 }
 
-// Warps per block of the item kernels: the forward uses 8 (its 59 KB of shared memory let
+// Warps per block of the item kernels.  The forward uses 8 (its 59 KB of shared memory let
 // three blocks share an SM); the backward uses 4 (110 KB with the four private slots, two
-// blocks per SM).
+// blocks per SM).  A grid of fewer blocks than SMs (systems under 32 x #SMs atoms) leaves
+// SMs idle, so there the 31 items of a block are shared by twice the warps instead: 16 in
+// the forward (same shared memory, 128 registers), 8 in the backward (161 KB, one block per
+// SM).  The forward's features do not depend on the split; the backward sums its warps'
+// slots in warp order, so its last bits depend on the warp count (fixed for a given size).
 constexpr int CT_FWD_W = 8, CT_BWD_W = 4;
 constexpr size_t ct_fwd_smem() { return sizeof(float) * (CT_ATOMS * NPSI + CT_ATOMS * GT_STRIDE); }
-constexpr size_t ct_bwd_smem() { return sizeof(float) * ((CT_BWD_W + 1) * CT_ATOMS * NPSI + CT_ATOMS * GT_STRIDE); }
+template <int W> constexpr size_t ct_bwd_smem() {
+    return sizeof(float) * ((W + 1) * CT_ATOMS * NPSI + CT_ATOMS * GT_STRIDE);
+}
+static_assert(ct_bwd_smem<2 * CT_BWD_W>() <= 227 * 1024, "backward with doubled warps fits in shared memory");
+
+static int sm_count() {
+    static int cnt[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int &c = cnt[dev & 63];
+    if (c <= 0) cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
+    return c > 0 ? c : 1;
+}
+
+template <typename OutT, int W>
+static void launch_fwd_w(int blocks, const float *psi, int N, int Mp, OutT *G, float *features_out, int lo_out,
+                         cudaStream_t st) {
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_contract_fwd<OutT, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ct_fwd_smem());
+        attr = true;
+    }
+    launch_pdl(k_contract_fwd<OutT, W>, dim3(blocks), dim3(W * 32), ct_fwd_smem(), st, psi, N, Mp, G, features_out,
+               lo_out);
+    note_launches(1);
+}
 
 template <typename OutT>
 static void launch_fwd_items(const float *psi, int N, int Mp, OutT *G, float *features_out, int lo_out,
                              cudaStream_t st) {
     const int blocks = (Mp + CT_ATOMS - 1) / CT_ATOMS;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_contract_fwd<OutT, CT_FWD_W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)ct_fwd_smem());
-        attr = true;
-    }
-    if (blocks > 0) {
-        launch_pdl(k_contract_fwd<OutT, CT_FWD_W>, dim3(blocks), dim3(CT_FWD_W * 32), ct_fwd_smem(), st, psi, N, Mp, G,
-                   features_out, lo_out);
-        note_launches(1);
-    }
+    if (blocks <= 0) return;
+    if (blocks < sm_count())
+        launch_fwd_w<OutT, 2 * CT_FWD_W>(blocks, psi, N, Mp, G, features_out, lo_out, st);
+    else
+        launch_fwd_w<OutT, CT_FWD_W>(blocks, psi, N, Mp, G, features_out, lo_out, st);
 }
 
 void launch_contract_fwd_f32(const float *psi, int N, int Mp, float *G, float *features_out, cudaStream_t st) {
@@ -923,18 +946,24 @@ void launch_contract_fwd_bf16(const float *psi, int N, int Mp, __nv_bfloat16 *G,
     launch_fwd_items<__nv_bfloat16>(psi, N, Mp, G, features_out, lo_out ? 1 : 0, st);
 }
 
-void launch_contract_bwd(const float *psi, const float *dG, int N, float *dpsi, cudaStream_t st) {
-    const int blocks = (N + CT_ATOMS - 1) / CT_ATOMS;
+template <int W>
+static void launch_bwd_w(int blocks, const float *psi, const float *dG, int N, float *dpsi, cudaStream_t st) {
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_contract_bwd<CT_BWD_W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)ct_bwd_smem());
+        cudaFuncSetAttribute(k_contract_bwd<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ct_bwd_smem<W>());
         attr = true;
     }
-    if (blocks > 0) {
-        launch_pdl(k_contract_bwd<CT_BWD_W>, dim3(blocks), dim3(CT_BWD_W * 32), ct_bwd_smem(), st, psi, dG, N, dpsi);
-        note_launches(1);
-    }
+    launch_pdl(k_contract_bwd<W>, dim3(blocks), dim3(W * 32), ct_bwd_smem<W>(), st, psi, dG, N, dpsi);
+    note_launches(1);
+}
+
+void launch_contract_bwd(const float *psi, const float *dG, int N, float *dpsi, cudaStream_t st) {
+    const int blocks = (N + CT_ATOMS - 1) / CT_ATOMS;
+    if (blocks <= 0) return;
+    if (blocks < sm_count())
+        launch_bwd_w<2 * CT_BWD_W>(blocks, psi, dG, N, dpsi, st);
+    else
+        launch_bwd_w<CT_BWD_W>(blocks, psi, dG, N, dpsi, st);
 }
 
 }  // namespace gm
