@@ -313,7 +313,14 @@ __global__ void __launch_bounds__(256, CPS)
     // the N tiles of one row block are consecutive blocks, so the A rows come from DRAM once
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const int KB1 = K / BK;                 // K blocks of one pass
-    const int KB = split ? 3 * KB1 : KB1;   // passes: hi*hi (+ lo*hi + hi*lo)
+    // Split operands (hi | lo halves along K): with a ring of at least four stages, stage
+    // pairs hold the four tiles of one K block (A hi, B hi, A lo, B lo) and the three products
+    // hi*hi, lo*hi, hi*lo run on them (each tile loaded once); otherwise three passes over K
+    // (hi*hi, lo*hi, hi*lo), the hi tiles loaded twice.
+    constexpr bool FUSED_OK = STAGES >= 4;
+    const bool fused = split && FUSED_OK;
+    constexpr int FST = STAGES / 2;         // fused stages (pairs of ring stages)
+    const int KB = split ? (fused ? KB1 : 3 * KB1) : KB1;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -335,7 +342,54 @@ __global__ void __launch_bounds__(256, CPS)
     const uint32_t tmem = *tmem_slot;
     griddep_wait();                         // operands and epilogue inputs come from earlier kernels
 
-    if (warp == 0 && lane == 0) {
+    if (warp == 0 && lane == 0 && fused) {
+        // ---------------- TMA producer, fused split: one stage pair per K block
+        int issued = 0;
+        for (int kb = 0; kb < KB; ++kb) {
+            const int s = kb % FST;
+            if (kb >= FST && !mbar_wait(empty + s, ((kb / FST) - 1) & 1, abort_flag)) {
+                *abort_flag = 1;
+                break;
+            }
+            uint8_t *hi_dst = smem + (2 * s) * STAGE_BYTES;
+            uint8_t *lo_dst = hi_dst + STAGE_BYTES;
+            mbar_expect_tx(full + s, 2 * STAGE_BYTES);
+            tma_load_2d(hi_dst, &tmA, full + s, kb * BK, m0);
+            tma_load_2d(hi_dst + A_STAGE_BYTES, &tmB, full + s, kb * BK, n0);
+            tma_load_2d(lo_dst, &tmA, full + s, K + kb * BK, m0);
+            tma_load_2d(lo_dst + A_STAGE_BYTES, &tmB, full + s, K + kb * BK, n0);
+            ++issued;
+        }
+        if (*abort_flag) {
+            for (int kb = (issued > FST ? issued - FST : 0); kb < issued; ++kb) {
+                volatile int never = 0;
+                mbar_wait(full + (kb % FST), (kb / FST) & 1, &never);
+            }
+        }
+    } else if (warp == 1 && lane == 0 && fused) {
+        // ---------------- MMA issuer, fused split
+        constexpr uint32_t idesc = instr_desc(BN);
+        bool ok = true;
+        for (int kb = 0; kb < KB; ++kb) {
+            const int s = kb % FST;
+            if (!mbar_wait(full + s, (kb / FST) & 1, abort_flag)) {
+                *abort_flag = 1;
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t ah = su32(smem + (2 * s) * STAGE_BYTES), bh = ah + A_STAGE_BYTES;
+            const uint32_t al = ah + STAGE_BYTES, bl = al + A_STAGE_BYTES;
+#pragma unroll
+            for (int k = 0; k < BK / 16; ++k) {
+                umma_bf16(tmem, smem_desc(ah + 32 * k), smem_desc(bh + 32 * k), idesc, (kb | k) != 0);
+                umma_bf16(tmem, smem_desc(al + 32 * k), smem_desc(bh + 32 * k), idesc, true);
+                umma_bf16(tmem, smem_desc(ah + 32 * k), smem_desc(bl + 32 * k), idesc, true);
+            }
+            umma_commit(empty + s);
+        }
+        if (ok) umma_commit(done);
+    } else if (warp == 0 && lane == 0) {
         // ---------------- TMA producer
         int issued = 0;
         for (int kb = 0; kb < KB; ++kb) {
