@@ -535,9 +535,10 @@ static gm_status forward_to_features(const gm_model *m, const gm_system *sys, co
     return launch_status();
 }
 
-// The four network GEMMs: features -> energies (partial sums) and dE/dG.
+// The four network GEMMs: features -> energies (partial sums) and dE/dG.  energy (mixed
+// path only): the structure energies are summed inside the B1 GEMM and written there.
 static gm_status network_fwd_bwd(const gm_model *m, const gm_system *sys, EfWs &w, int Mp, int32_t *status,
-                                 cudaStream_t st) {
+                                 cudaStream_t st, double *energy = nullptr) {
     const int H = m->H;
     EpiArgs e{};
     e.n_atoms = sys->n_atoms;
@@ -574,12 +575,21 @@ static gm_status network_fwd_bwd(const gm_model *m, const gm_system *sys, EfWs &
         e.out0 = dZ1;
         e.aux = D1;
         e.lo_out = (sp & 8) != 0;
+        if (energy) {
+            e.atom_ptr = sys->atom_ptr;
+            e.n_structures = sys->n_structures;
+            e.mu = m->mu;
+            e.b3 = m->b3;
+            e.red_acc = w.red_acc;
+            e.energy = energy;
+        }
         {
             StageScope sc(ST_GEMM_B1, st);
             if ((s = gemm_bf16(EPI_B1, 0, dZ2, m->W2_h, Mp, H, H, (sp & 4) != 0, e, status, st, m->gemm_bn, m->gemm_cps)) != GM_OK)
                 return fail(s, "tcgen05 GEMM B1 failed");
         }
         e.out0 = w.dG;
+        e.energy = nullptr;
         {
             StageScope sc(ST_GEMM_B0, st);
             if ((s = gemm_bf16(EPI_STORE, 0, dZ1, m->W1p_h, Mp, NFP, H, (sp & 8) != 0, e, status, st, m->gemm_bn, m->gemm_cps)) != GM_OK)
@@ -627,9 +637,11 @@ gm_status gm_energy_forces(const gm_model *m, const gm_system *sys, const gm_nli
     if (!c.ok) return fail(GM_ERR_WORKSPACE, "workspace too small");
     cudaStream_t st = stream;
     const int Mp = round_up(N, TILE_M);
+    // without the virial, the mixed path sums the energies inside its B1 GEMM
+    const bool fused_energy = N > 0 && virial == nullptr && m->d.precision == GM_PREC_MIXED;
     if (N > 0) {
         if ((s = forward_to_features(m, sys, nl, w, nullptr, nullptr, forces, status, st)) != GM_OK) return s;
-        if ((s = network_fwd_bwd(m, sys, w, Mp, status, st)) != GM_OK) return s;
+        if ((s = network_fwd_bwd(m, sys, w, Mp, status, st, fused_energy ? energy : nullptr)) != GM_OK) return s;
         {
             StageScope sc(ST_CONTRACT_BWD, st);
             launch_contract_bwd(w.psi, w.dG, N, w.dpsi, st);
@@ -638,9 +650,11 @@ gm_status gm_energy_forces(const gm_model *m, const gm_system *sys, const gm_nli
         StageScope sc(ST_FORCES, st);
         launch_forces(a, choose_tpa(m, N), w.dpsi, forces, virial ? w.vir_atom : nullptr, st);
     }
-    StageScope sc(ST_REDUCE, st);
-    launch_struct_reduce(B, N, sys->atom_ptr, sys->species, m->S, m->sigma, m->mu, m->b3, w.nn_part, H / 32,
-                         virial ? w.vir_atom : nullptr, w.red_acc, energy, virial, st);
+    if (!fused_energy) {
+        StageScope sc(ST_REDUCE, st);
+        launch_struct_reduce(B, N, sys->atom_ptr, sys->species, m->S, m->sigma, m->mu, m->b3, w.nn_part, H / 32,
+                             virial ? w.vir_atom : nullptr, w.red_acc, energy, virial, st);
+    }
     return launch_status();
 }
 

@@ -27,6 +27,15 @@ struct EpiArgs {
     const void *aux;         // D1 (B1)
     float *nn_part;          // [M][N/32] (L2): partial output-layer sums per 32 columns
     int lo_out;              // BF16 outputs: also write the lo half (the consumer runs split)
+    // Structure energies fused into the tcgen05 B1 GEMM (energy non-null; no virial): while
+    // the first N tile of each row block runs its main loop, its four idle warps add E_i of
+    // the block's rows (from nn_part, N/32 partials each) to the per-structure fixed-point
+    // accumulators, and the last such block writes energy[] (gm_fixed.cuh)
+    const int32_t *atom_ptr; // [n_structures + 1]
+    int n_structures;
+    const float *mu, *b3;    // [S], [1]
+    unsigned long long *red_acc;
+    double *energy;          // [n_structures]
 };
 // BF16 operands of the tcgen05 path are stored as hi/lo pairs, [rows][2K]: columns [0, K)
 // hold hi = bf16(x), columns [K, 2K) hold lo = bf16(x - hi).  A GEMM run with split = 0

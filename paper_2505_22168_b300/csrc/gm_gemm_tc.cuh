@@ -16,6 +16,7 @@
 
 #include <cuda.h>
 
+#include "gm_fixed.cuh"
 #include "gm_gemm.h"
 
 namespace gm {
@@ -435,6 +436,32 @@ __global__ void __launch_bounds__(256, CPS)
         if (ok) umma_commit(done);
     }
     __syncwarp();
+
+    // ---------------- structure energies (B1, first N tile of each row block): warps 4..7,
+    // idle during the main loop, one row per thread (gm_fixed.cuh); the block holds a ticket
+    // and the last of the gridDim.y blocks writes energy[]
+    if (EPI == EPI_B1 && e.energy != nullptr && blockIdx.x == 0 && warp >= 4) {
+        const int m = m0 + (warp - 4) * 32 + lane;
+        long long v[1] = {0};
+        int b = -1;
+        bool bad = false;
+        if (m < e.n_atoms) {
+            v[0] = to_fixed(atom_energy(m, e.species, e.n_species, e.sigma, e.mu, e.b3, e.nn_part, N / 32), bad);
+            b = structure_of(e.atom_ptr, e.n_structures, m);
+        }
+        __shared__ int energy_last;
+        warp_add_fixed<1>(b, v, 1, bad, e.red_acc, lane);
+        __threadfence();
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        if (warp == 4 && lane == 0) {
+            const unsigned long long ticket = atomicAdd(e.red_acc + (size_t)e.n_structures * RW, 1ull);
+            energy_last = ticket == (unsigned long long)(gridDim.y - 1) ? 1 : 0;
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        if (energy_last)
+            finalize_fixed(e.n_structures, 1, e.red_acc, e.energy, nullptr, threadIdx.x - 128, 128,
+                           [] { asm volatile("bar.sync 1, 128;" ::: "memory"); });
+    }
 
     // ---------------- epilogue: 8 warps; warp w reads TMEM lanes 32 (w % 4) .. +31 (rows)
     // and column half w / 4; thread = row m0 + 32 (w % 4) + lane

@@ -8,6 +8,7 @@
 // One block per structure, fixed summation order (deterministic).
 #include "gm_internal.h"
 #include "gm_reduce.h"
+#include "gm_fixed.cuh"
 
 namespace gm {
 
@@ -24,29 +25,11 @@ __device__ __forceinline__ double block_sum_double(double v, double *sh) {
     return r;  // valid in thread 0
 }
 
-// One pass over the atoms.  Thread i forms E_i (and takes the per-atom virial) in FP32 and
-// converts each value to a 64-bit fixed-point integer in units of 2^-24 (the scaling by a
-// power of two is exact; the rounding to the unit is below 3e-8 eV per atom).  Lanes of a
-// warp that belong to the same structure add their integers with shuffles and one lane adds
-// the result to the structure's accumulator with a 64-bit atomic.  Integer sums are exact,
-// so the totals do not depend on the order of the atomics (deterministic), and they equal
-// the FP64 sum of the per-atom values to within the unit.  The block that finishes last
-// (ticket counter after a device-scope fence, no waiting) converts the totals to FP64,
-// writes energy and virial, and resets the accumulators and the counter.  The accumulators
-// start from zero: the position-split kernel of the same step clears them.  A value that is
-// not finite or exceeds 1e9 in magnitude (a diverged model) is counted in an eleventh word
-// per structure instead, and that structure's results come out as NaN, as an FP64 sum would.
-constexpr float FIX_ONE = 16777216.0f;        // 2^24
-constexpr double FIX_INV = 1.0 / 16777216.0;
-constexpr int RW = 11;                         // accumulator words per structure
-__device__ __forceinline__ long long to_fixed(float x, bool &bad) {
-    if (!(fabsf(x) < 1e9f)) {
-        bad = true;
-        return 0;
-    }
-    return __float2ll_rn(x * FIX_ONE);
-}
-
+// One pass over the atoms: thread i forms E_i (and takes the per-atom virial) in FP32 and
+// adds it to its structure's fixed-point accumulators (gm_fixed.cuh).  The block that
+// finishes last (ticket counter after a device-scope fence, no waiting) converts the totals
+// to FP64, writes energy and virial, and resets the accumulators and the counter.  The
+// accumulators start from zero: the position-split kernel of the same step clears them.
 __global__ void __launch_bounds__(REDUCE_CHUNK) k_reduce(int B, int N, const int32_t *__restrict__ atom_ptr,
                                                          const int32_t *__restrict__ species, int S,
                                                          const float *__restrict__ sigma, const float *__restrict__ mu,
@@ -64,43 +47,13 @@ __global__ void __launch_bounds__(REDUCE_CHUNK) k_reduce(int B, int N, const int
     int b = -1;
     bool bad = false;
     if (i < N) {
-        // the atom's partials (an even count, at most 16: H in 64..512) loaded together as
-        // float2, then added in order
-        float2 pt[8];
-        const float2 *row = reinterpret_cast<const float2 *>(nn_part + (size_t)i * nparts);
-#pragma unroll
-        for (int t = 0; t < 8; ++t) pt[t] = 2 * t < nparts ? row[t] : make_float2(0.0f, 0.0f);
-        float nn = b3[0];
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            if (2 * t < nparts) {
-                nn += pt[t].x;
-                nn += pt[t].y;
-            }
-        }
-        const int z = min(max(species[i], 0), S - 1);
-        v[0] = to_fixed(fmaf(sigma[z], nn, mu[z]), bad);
+        v[0] = to_fixed(atom_energy(i, species, S, sigma, mu, b3, nn_part, nparts), bad);
         if (vir_atom)
 #pragma unroll
             for (int q = 0; q < 9; ++q) v[1 + q] = to_fixed(vir_atom[(size_t)i * 9 + q], bad);
         b = structure_of(atom_ptr, B, i);
     }
-    unsigned todo = __ballot_sync(0xffffffffu, b >= 0);
-    while (todo) {                                   // one round per structure present in the warp
-        const int lead = __ffs(todo) - 1;
-        const int bl = __shfl_sync(0xffffffffu, b, lead);
-        const bool mine = b == bl;
-        todo &= ~__ballot_sync(0xffffffffu, mine);
-#pragma unroll
-        for (int q = 0; q < 10; ++q) {
-            if (q >= nv) break;
-            long long x = mine ? v[q] : 0;
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-            if (lane == lead) atomicAdd(acc + (size_t)bl * RW + q, (unsigned long long)x);
-        }
-        if (__any_sync(0xffffffffu, mine && bad) && lane == lead) atomicAdd(acc + (size_t)bl * RW + 10, 1ull);
-    }
+    warp_add_fixed<10>(b, v, nv, bad, acc, lane);
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -109,19 +62,7 @@ __global__ void __launch_bounds__(REDUCE_CHUNK) k_reduce(int B, int N, const int
     }
     __syncthreads();
     if (!last) return;
-    __threadfence();
-    for (int q = threadIdx.x; q < B * 10; q += blockDim.x) {
-        const int s = q / 10, c = q - s * 10;
-        if (c >= nv) continue;
-        const long long x = (long long)atomicExch(acc + (size_t)s * RW + c, 0ull);
-        const bool nan = atomicAdd(acc + (size_t)s * RW + 10, 0ull) != 0ull;
-        const double val = nan ? __longlong_as_double(0x7ff8000000000000ll) : (double)x * FIX_INV;
-        if (c == 0) energy[s] = val;
-        else virial[9 * s + c - 1] = val;
-    }
-    __syncthreads();
-    for (int s = threadIdx.x; s < B; s += blockDim.x) atomicExch(acc + (size_t)s * RW + 10, 0ull);
-    if (threadIdx.x == 0) atomicExch(acc + (size_t)B * RW, 0ull);
+    finalize_fixed(B, nv, acc, energy, virial, threadIdx.x, blockDim.x, [] { __syncthreads(); });
 }
 
 size_t reduce_acc_words(int B) { return (size_t)B * RW + 1; }

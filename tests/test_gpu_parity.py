@@ -426,6 +426,60 @@ def test_batched_energies_and_virials_are_deterministic(li_small):
         assert torch.equal(E, runs[0][0]) and torch.equal(W, runs[0][2])
 
 
+def _with_empty_structure():
+    b4, d, p = synth.config(4)
+    b = subset(b4, [0, 3, 5])
+    empty = (np.zeros((0, 3)), np.zeros(0, np.int32), 12.0 * np.eye(3))
+    structs = [(b.pos[b.atom_ptr[k]:b.atom_ptr[k + 1]], b.species[b.atom_ptr[k]:b.atom_ptr[k + 1]], b.cell[k])
+               for k in range(b.n_structures)]
+    return make_batch(structs[:1] + [empty] + structs[1:], 5), d, p
+
+
+@pytest.mark.parametrize("which", ["emim1536", "li3po4_batch", "with_empty"])
+def test_mixed_energies_summed_in_gemm_equal_reduction_kernel(which, li_small):
+    """Without the virial the mixed path sums the structure energies inside its first
+    backward GEMM; with it, the reduction kernel does.  Both add the same per-atom FP32
+    energies as exact fixed-point integers, so the energies agree bit for bit, and they are
+    within the mixed tolerance of the oracle.  (The forces take neighbour contributions by
+    float atomics, so they agree to rounding.)"""
+    if which == "emim1536":
+        b, d, p = synth.config(2)
+    elif which == "li3po4_batch":
+        b, d, p = li_small
+    else:
+        b, d, p = _with_empty_structure()
+    _ef_parity(b, d, p, precision="mixed", virial=False)
+    _, sysd, nl = _nl_pair(b, d, p)
+    mm = _model(d, p, "mixed")
+    E0, F0, _ = mm.energy_forces(sysd, nl, virial=False)
+    E1, F1, _ = mm.energy_forces(sysd, nl, virial=True)
+    mm.check_status()
+    assert np.array_equal(E0.cpu().numpy(), E1.cpu().numpy(), equal_nan=True)
+    f0, f1 = F0.cpu().numpy(), F1.cpu().numpy()    # float atomics: summation order varies
+    assert np.abs(f0 - f1).max() <= 1e-5 * max(np.abs(f1).max(), 1e-30)
+
+
+def test_diverged_energy_comes_out_nan_mixed_without_virial():
+    """The NaN rule of the structure sums holds where the mixed path sums the energies
+    inside its GEMM (no virial)."""
+    b1, d, p = synth.config(1)
+    spec1 = np.ones_like(b1.species)
+    b = make_batch([(b1.pos, b1.species, b1.cell[0]), (b1.pos, spec1, b1.cell[0]),
+                    (b1.pos, b1.species, b1.cell[0])], d["n_species"])
+    p = dict(p)
+    p["mu"] = np.array(p["mu"], dtype=np.float64).copy()
+    p["mu"][0] = 2e9
+    _, sysd, nl = _nl_pair(b, d, p)
+    mm = _model(d, p, "mixed")
+    E, _, _ = mm.energy_forces(sysd, nl, virial=False)
+    mm.check_status()
+    has0 = [bool((b.species[b.atom_ptr[k]:b.atom_ptr[k + 1]] == 0).any()) for k in range(b.n_structures)]
+    E = E.cpu().numpy()
+    assert any(has0) and not all(has0)
+    for k in range(b.n_structures):
+        assert np.isnan(E[k]) == has0[k]
+
+
 def test_diverged_energy_comes_out_nan():
     """A per-atom energy beyond the fixed-point range (here an energy shift of 2e9 for one
     species) makes the structures holding that species NaN instead of wrapping around."""
