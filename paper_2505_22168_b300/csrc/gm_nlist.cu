@@ -1139,7 +1139,9 @@ constexpr int BR_CAP = 512;
 static_assert(GM_MAX_ATOMS <= (1 << 22), "brute-force keys hold the neighbour index in 22 bits");
 struct BrBuf {
     unsigned key[BR_CAP];
+    unsigned row[BR_CAP];   // the placed row (j | shift code << 27), kept for the direct write
     int hist[32], run[32];
+    int rowi, rowcnt;       // the warp's placed row (rowi -1: none)
 };
 
 // shared-memory layout of the small-system brute-force path: the per-structure grids (at most
@@ -1261,7 +1263,8 @@ __device__ int brute_row(const NlArgs &a, const NlStruct &q, int i, int lane, Br
 
 // The buffered row (cnt <= BR_CAP entries) in stencil order, stable in j: into slab row i
 // (codes; returns false when a shift has no code) or, with csr >= 0, into the CSR list at csr
-__device__ bool brute_emit(const NlArgs &a, int i, int cnt, int lane, BrBuf &bb, int csr) {
+// (slab rows go to dst: the slab row of i, or the warp buffer's row for the direct write)
+__device__ bool brute_emit(const NlArgs &a, int i, int cnt, int lane, BrBuf &bb, int csr, unsigned *dst = nullptr) {
     const unsigned full = 0xffffffffu, below = (1u << lane) - 1u;
     if (lane < 32) bb.hist[lane] = 0;
     __syncwarp();
@@ -1296,7 +1299,7 @@ __device__ bool brute_emit(const NlArgs &a, int i, int cnt, int lane, BrBuf &bb,
             } else {
                 const unsigned code = shift_code(bytes3(s0, s1, s2));
                 coded = coded && code != NL_NOCODE;
-                a.slab[(size_t)i * a.maxn + pos] = (unsigned)j | (code << 27);
+                (dst ? dst : a.slab + (size_t)i * a.maxn)[pos] = (unsigned)j | (code << 27);
             }
             if (lane == __ffs(m) - 1) bb.run[st] += __popc(m);
         }
@@ -1310,9 +1313,17 @@ __device__ bool brute_emit(const NlArgs &a, int i, int cnt, int lane, BrBuf &bb,
 // blocks first, and the second half of the grid (the second block of each SM when the
 // blocks fill the SMs in order) starts a quarter of the block further on, so that two
 // blocks on one SM keep their busy warps on different schedulers.
+//
+// With at most one row per warp (N <= blocks x warps) the placed row stays in the warp's
+// buffer (any length up to BR_CAP) and the compaction writes it into the CSR list from
+// there (brute_direct); otherwise it goes to the slab.
+__device__ __forceinline__ bool brute_direct(const NlArgs &a, int nb) { return a.N <= nb * NL_WARPS; }
+
 __device__ void ph_search_brute(const NlArgs &a, int bid, int nb, const NlStruct *Ss, BrBuf *bufs) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     BrBuf &bb = bufs[warp];
+    const bool direct = brute_direct(a, nb);
+    if (lane == 0) bb.rowi = -1;
     const int rot = bid >= (nb >> 1) ? NL_WARPS / 4 : 0;
     for (int i = ((warp - rot + NL_WARPS) % NL_WARPS) * nb + bid; i < a.N; i += NL_WARPS * nb) {
         const NlStruct &q = Ss[structure_of(a.atom_ptr, a.B, i)];
@@ -1321,12 +1332,16 @@ __device__ void ph_search_brute(const NlArgs &a, int bid, int nb, const NlStruct
             if (lane == 0) atomicExch(a.brute_over, 1);
             continue;
         }
-        bool over = cnt > a.maxn;
-        if (!over) over = !brute_emit(a, i, cnt, lane, bb, -1);
+        bool over = !direct && cnt > a.maxn;
+        if (!over) over = !brute_emit(a, i, cnt, lane, bb, -1, direct ? bb.row : nullptr);
         if (lane == 0) {
             a.counts[i] = cnt;
             a.redo[i] = over ? 1 : 0;
             if (over) nl_redo(a, i);
+            if (direct && !over) {
+                bb.rowi = i;
+                bb.rowcnt = cnt;
+            }
         }
     }
 }
@@ -1342,7 +1357,20 @@ __device__ void ph_compact(const NlArgs &a, int bid, int nb, const int32_t *row_
     const unsigned full = 0xffffffffu;
     if (__shfl_sync(full, lane == 0 ? (int)status_bad(a.status) : 0, 0)) return;
     const int gw = bid + nb * warp, nw = nb * NL_WARPS;
-    for (int i0 = gw * NL_COPY_ROWS; i0 < a.N; i0 += nw * NL_COPY_ROWS) {
+    if (brute && brute_direct(a, nb)) {                // the warp's own placed row, from its buffer
+        const BrBuf &bb = brute[warp];
+        const int i = bb.rowi;
+        if (i >= 0) {
+            const int r0 = row_ptr[i], cnt = bb.rowcnt;
+            for (int k = lane; k < cnt; k += 32) {
+                const unsigned e = bb.row[k], code = e >> 27;
+                a.col[r0 + k] = (int)(e & 0x7FFFFFFu);
+                a.shift[r0 + k] = make_char4((signed char)((int)(code % 3u) - 1), (signed char)((int)((code / 3u) % 3u) - 1),
+                                             (signed char)((int)(code / 9u) - 1), 0);
+            }
+        }
+    }
+    for (int i0 = gw * NL_COPY_ROWS; !(brute && brute_direct(a, nb)) && i0 < a.N; i0 += nw * NL_COPY_ROWS) {
         int r0[NL_COPY_ROWS], cnt[NL_COPY_ROWS], kmax = 0;
 #pragma unroll
         for (int u = 0; u < NL_COPY_ROWS; ++u) {
