@@ -106,6 +106,8 @@ struct NlArgs {
     int maxn;               // slab row length (0: two-pass search, no slab)
     int block_items;        // 1: block-level search items, 0: warp-level
     int small;              // cooperative launch: grids and short scans computed by every block
+    int mid;                // cooperative launch, N + B up to 8192 (not small): the brute-force search
+                            // if the boxes allow it, else the phases of large systems
     int try_brute;          // small systems: brute-force search when every box is single-image
     int *brute_over;        // set when a brute-force row exceeds BR_CAP (zeroed per build)
     uint8_t *redo;          // 1: row searched again during the compaction
@@ -1148,6 +1150,8 @@ struct BrBuf {
 // 256) and the row scan (at most 4097 ints) first, then one buffer per warp
 constexpr size_t NL_BR_OFF = ((256 * sizeof(NlStruct) > 4097 * sizeof(int32_t) ? 256 * sizeof(NlStruct)
                                                                                : 4097 * sizeof(int32_t)) + 127) / 128 * 128;
+// the row scan of the mid-size brute-force path: N + 1 <= 2 NL_SCAN_ONE_BLOCK entries
+static_assert(NL_BR_OFF >= 2 * NL_SCAN_ONE_BLOCK * sizeof(int32_t), "row scan of the mid-size path");
 static_assert(NL_BR_OFF + NL_WARPS * sizeof(BrBuf) <= NL_SMEM, "brute-force buffers exceed the search's shared memory");
 
 __device__ bool nl_brute_eligible(const NlArgs &a, const NlStruct *Ss) {
@@ -1459,29 +1463,46 @@ __device__ __forceinline__ void run_phase(const NlArgs &a, int ph, int bid, int 
 
 // All phases in one launch; the scans take one block when they are short (the decision is
 // the same in every block: it reads the same counts).
+// The brute-force search (grids already in Ss): true when it built the list (or gave up on
+// an error), false when a row was longer than BR_CAP and the cell list must be built instead.
+__device__ bool nl_brute_build(const NlArgs &a, int bid, int nb, NlStruct *Ss, int32_t *si, float4 *smem) {
+    BrBuf *bufs = reinterpret_cast<BrBuf *>(reinterpret_cast<char *>(smem) + NL_BR_OFF);
+    ph_wrap_brute(a, bid, nb, Ss);
+    if (!nl_grid_sync(a.bar, a.status)) return true;
+    ph_search_brute(a, bid, nb, Ss, bufs);
+    if (!nl_grid_sync(a.bar, a.status)) return true;
+    if (*reinterpret_cast<volatile int *>(a.brute_over) != 0) {
+        if (bid == 0 && threadIdx.x == 0) *a.n_redo = 0;
+        return false;
+    }
+    ph_scan_local(a.counts, a.N, si, bid, a.row_ptr, a.cap, a.n_pairs, a.status);
+    if ((int64_t)si[a.N] > a.cap) return true;
+    ph_compact(a, bid, nb, si, bufs);
+    return true;
+}
+
 __global__ void __launch_bounds__(NL_THREADS, 2) k_nl_coop(NlArgs a) {
     extern __shared__ float4 nl_smem[];
     const int bid = blockIdx.x, nb = gridDim.x;
+    if (a.mid) {
+        // every block sets up the grids; the brute-force search when the boxes allow it, else
+        // (or after a row longer than BR_CAP) the phases below from the binning on -- the
+        // setup published the grids, the cell count and the redo count as the setup phase does
+        NlStruct *Ss = reinterpret_cast<NlStruct *>(nl_smem);
+        ph_setup_local(a, bid, Ss);
+        if (a.try_brute && nl_brute_eligible(a, Ss) &&
+            nl_brute_build(a, bid, nb, Ss, reinterpret_cast<int32_t *>(nl_smem), nl_smem))
+            return;
+        for (int c = bid * NL_THREADS + threadIdx.x; c < a.ncmax; c += nb * NL_THREADS) a.cfill[c] = 0;
+        if (!nl_grid_sync(a.bar, a.status)) return;
+    }
     if (a.small) {
         // four barriers: every block sets up the grids and scans the short arrays itself
         NlStruct *Ss = reinterpret_cast<NlStruct *>(nl_smem);
         int32_t *si = reinterpret_cast<int32_t *>(nl_smem);
         ph_setup_local(a, bid, Ss);
-        if (a.try_brute && nl_brute_eligible(a, Ss)) {
-            BrBuf *bufs = reinterpret_cast<BrBuf *>(reinterpret_cast<char *>(nl_smem) + NL_BR_OFF);
-            ph_wrap_brute(a, bid, nb, Ss);
-            if (!nl_grid_sync(a.bar, a.status)) return;
-            ph_search_brute(a, bid, nb, Ss, bufs);
-            if (!nl_grid_sync(a.bar, a.status)) return;
-            if (*reinterpret_cast<volatile int *>(a.brute_over) == 0) {
-                ph_scan_local(a.counts, a.N, si, bid, a.row_ptr, a.cap, a.n_pairs, a.status);
-                if ((int64_t)si[a.N] > a.cap) return;
-                ph_compact(a, bid, nb, si, bufs);
-                return;
-            }
-            // a row longer than BR_CAP: the cell-list path below builds the list instead
-            if (bid == 0 && threadIdx.x == 0) *a.n_redo = 0;
-        }
+        // a row longer than BR_CAP: the cell-list path below builds the list instead
+        if (a.try_brute && nl_brute_eligible(a, Ss) && nl_brute_build(a, bid, nb, Ss, si, nl_smem)) return;
         for (int c = bid * NL_THREADS + threadIdx.x; c < a.ncmax; c += nb * NL_THREADS) a.cfill[c] = 0;
         ph_bin(a, bid, nb, Ss);
         if (!nl_grid_sync(a.bar, a.status)) return;
@@ -1503,8 +1524,10 @@ __global__ void __launch_bounds__(NL_THREADS, 2) k_nl_coop(NlArgs a) {
         }
         return;
     }
-    run_phase(a, PH_SETUP, bid, nb, nl_smem);
-    if (!nl_grid_sync(a.bar, a.status)) return;
+    if (!a.mid) {
+        run_phase(a, PH_SETUP, bid, nb, nl_smem);
+        if (!nl_grid_sync(a.bar, a.status)) return;
+    }
     run_phase(a, PH_BIN, bid, nb, nl_smem);
     if (!nl_grid_sync(a.bar, a.status)) return;
     if (*a.ncells <= NL_SCAN_ONE_BLOCK) {
@@ -1696,6 +1719,7 @@ gm_status nl_build(const gm_system &sys, double r_cut, int n_species, gm_nlist &
     // brute-force search (small systems, single-image boxes; decided on the device) unless the
     // work items are set to cells, or there is no slab
     a.try_brute = (tune.items == 0 || tune.items == 3) && a.maxn > 0 ? 1 : 0;
+    a.mid = (!a.small && a.try_brute && N + B <= 2 * NL_SCAN_ONE_BLOCK && B <= 256) ? 1 : 0;
     a.brute_over = w.brute_over;
     auto clampi = [](long long v, long long lo, long long hi) { return (int)(v < lo ? lo : (v > hi ? hi : v)); };
     if (tune.mode != GM_NL_MODE_PHASES && dev.coop_blocks > 0) {

@@ -113,11 +113,34 @@ def _ragged_batch():
     return make_batch(structs, 5)
 
 
-@pytest.mark.parametrize("case", ["config1", "li_small", "config2", "ragged", "shifted"])
+def _mid_size_li3po4():
+    """Li3PO4-like boxes, some shorter than 2 r_cut, with 4096 < atoms + boxes <= 8192: the
+    mid-size cooperative path, whose boxes rule out the brute-force search."""
+    b3, d, p = synth.config(3)
+    k, n = 0, 0
+    while n + k + 1 + (b3.atom_ptr[k + 1] - b3.atom_ptr[k]) <= 8000:
+        n += b3.atom_ptr[k + 1] - b3.atom_ptr[k]
+        k += 1
+    b = subset(b3, range(k))
+    assert 4096 < b.n_atoms + b.n_structures <= 8192
+    assert (b.cell[:, 0, 0] < 2.001 * d["r_cut"]).any()
+    return b, d, p
+
+
+@pytest.mark.parametrize("case", ["config1", "li_small", "config2", "ragged", "shifted", "train_batch",
+                                  "mid_multi_image"])
 def test_neighbor_build_launch_shapes_give_identical_rows(case, li_small):
+    """(train_batch: 32 EMIM boxes, 7920 atoms -- the mid-size path's brute-force search;
+    mid_multi_image: the same path falling back to the cell list.)"""
     GMNN, DeviceSystem = _gm()
     if case == "li_small":
         b, d, p = li_small
+    elif case == "train_batch":
+        b, d, p = synth.config(4)
+        assert 4096 < b.n_atoms + b.n_structures <= 8192
+        assert (b.cell[:, 0, 0] >= 2.001 * d["r_cut"]).all()
+    elif case == "mid_multi_image":
+        b, d, p = _mid_size_li3po4()
     elif case == "ragged":
         _, d, p = synth.config(1)
         b, d = _ragged_batch(), dict(d, r_cut=3.3)
