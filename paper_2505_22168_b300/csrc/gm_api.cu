@@ -341,10 +341,11 @@ PairArgs pair_args(const gm_model *m, const gm_system *s, const gm_nlist *nl, co
 
 int choose_tpa(const gm_model *m, int N) {
     if (m->pair_tpa > 0) return m->pair_tpa;
-    // measured on B300 (EMIM 1536 atoms: 32; Li3PO4 67k and 131k atoms: 1)
+    // measured on B300 (EMIM 1536 atoms and the 7920-atom training batch: 32; Li3PO4 67k and
+    // 131k atoms: 1)
     if (N >= 49152) return 1;
     if (N >= 16384) return 2;
-    if (N >= 4096) return 8;
+    if (N >= 8192) return 8;
     return 32;
 }
 
