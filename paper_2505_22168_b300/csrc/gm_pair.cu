@@ -671,7 +671,7 @@ static int pg_beta_warps(int S) {
 int pg_beta_blocks(int N, int S) {
     const int w = pg_beta_warps(S);
     const int b = (N + w - 1) / w;
-    return b < 1 ? 1 : (b > 148 * 8 ? 148 * 8 : b);
+    return b < 1 ? 1 : (b > 148 * 2 ? 148 * 2 : b);
 }
 
 void launch_pg_beta(const PairArgs &a, const float *vel, const float *psib, const float *psidb, float *part,
