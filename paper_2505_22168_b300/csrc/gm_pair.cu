@@ -481,10 +481,11 @@ __global__ void __launch_bounds__(256) k_moments_tangent(PairArgs a, const float
 // accumulated per block in shared memory, block partials written to part[block][S S 35].
 // dJ/dbeta partials.  One warp per centre atom i (species zi); each lane accumulates its pairs'
 // NR x NB terms B_k alpha_s + dB_k gamma_s into its own slice of shared memory, indexed by the
-// neighbour's species (layout [z][s][k][lane]: lanes never share a bank, no atomics).  After
-// the row the lanes add up the 32 slices (lane l takes entries l, l + 32, ...) into the
-// block's [S][S][NR][NB] accumulator (one atomic per entry, distinct entries per lane) and
-// clear them.  Block partials are summed in a fixed order by k_pg_beta_reduce.
+// neighbour's species (layout [z][s][k][lane]: lanes never share a bank, no atomics).  A warp
+// takes its atoms 32 at a time, species by species: after the rows of one centre species the
+// lanes add up the 32 slices (lane l takes entries l, l + 32, ...) into the block's
+// [S][S][NR][NB] accumulator (one atomic per entry, distinct entries per lane) and clear
+// them.  Block partials are summed in a fixed order by k_pg_beta_reduce.
 __global__ void __launch_bounds__(256) k_pg_beta(PairArgs a, const float *__restrict__ vel,
                                                  const float *__restrict__ psib, const float *__restrict__ psidb,
                                                  float *__restrict__ part) {
@@ -498,7 +499,17 @@ __global__ void __launch_bounds__(256) k_pg_beta(PairArgs a, const float *__rest
     for (int q = lane; q < nlane * 32; q += 32) la[q] = 0.0f;
     __syncthreads();
     const bool ok_status = !status_bad(a.status);
-    for (int atom = blockIdx.x * nwarps + warp; ok_status && atom < a.N; atom += gridDim.x * nwarps) {
+    const unsigned full = 0xffffffffu;
+    const int gw = blockIdx.x * nwarps + warp, nwt = gridDim.x * nwarps;
+    for (int g0 = gw; ok_status && g0 < a.N; g0 += 32 * nwt) {
+      const int mine = g0 + lane * nwt;                          // this lane's atom of the group
+      const int zmine = mine < a.N ? clamp_species(a.species[mine], a.S, a.status) : -1;
+      for (int zsi = 0; zsi < a.S; ++zsi) {
+        unsigned todo = __ballot_sync(full, zmine == zsi);
+        if (!todo) continue;
+        while (todo) {
+        const int atom = g0 + (__ffs(todo) - 1) * nwt;
+        todo &= todo - 1u;
         for (int q = lane; q < NPSI; q += 32) {
             pw[q] = psib[(size_t)atom * NPSI + q];
             pw[NPSI + q] = psidb[(size_t)atom * NPSI + q];
@@ -507,7 +518,6 @@ __global__ void __launch_bounds__(256) k_pg_beta(PairArgs a, const float *__rest
         const int b = structure_of(a.atom_ptr, a.B, atom);
         const Centre ce(a, atom, b);
         const float vix = vel[3 * atom], viy = vel[3 * atom + 1], viz = vel[3 * atom + 2];
-        const int zsi = clamp_species(a.species[atom], a.S, a.status);
         const int p1 = a.row_ptr[atom + 1];
         PairPipe<1> pp(a, a.row_ptr[atom] + lane, p1, 32, vel);
         for (int p = a.row_ptr[atom] + lane; p < p1; p += 32) {
@@ -546,6 +556,7 @@ __global__ void __launch_bounds__(256) k_pg_beta(PairArgs a, const float *__rest
             }
         }
         __syncwarp();
+        }
         // add the lanes' slices into the block accumulator for species row zi, and clear them
         for (int e = lane; e < nlane; e += 32) {
             float t = 0.0f;
@@ -559,6 +570,7 @@ __global__ void __launch_bounds__(256) k_pg_beta(PairArgs a, const float *__rest
             if (t != 0.0f) atomicAdd(acc + zsi * nlane + e, t);
         }
         __syncwarp();
+      }
     }
     __syncthreads();
     for (int q = threadIdx.x; q < nbeta; q += blockDim.x) part[(size_t)blockIdx.x * nbeta + q] = acc[q];
