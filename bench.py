@@ -119,6 +119,11 @@ while True:
 """
 
 
+# end-to-end steps (host copies and a synchronisation each): enough wall time (~30 ms) that
+# host jitter averages out
+E2E_STEPS = 200
+
+
 class ClockSampler:
     """SM clock, power and clock-event reasons sampled about every 1 ms through NVML (read
     only) by a child process while the timed region runs (no contention with the launch
@@ -287,7 +292,7 @@ def run_gpu(args, cfg, precision, steps, warmup, world, rank, measure_e2e, clock
     model = GMNN(desc, params, precision=precision)
     sysd = DeviceSystem(batch)
     nl = model.build_neighbors(sysd)
-    path = jitter_path(batch, 7000 + cfg, warmup + steps) if cfg == 2 else None
+    path = jitter_path(batch, 7000 + cfg, warmup + max(steps, E2E_STEPS)) if cfg == 2 else None
     n = batch.n_atoms
     if path is not None:
         pos_dev = [torch.as_tensor(path[k], device=model.device) for k in range(warmup + steps)]
@@ -402,7 +407,7 @@ def run_gpu(args, cfg, precision, steps, warmup, world, rank, measure_e2e, clock
     if measure_e2e:
         # end to end through the public API with host buffers: pinned positions in,
         # energies and forces out, copies inside the timed region
-        e2e_steps = min(steps, 30)
+        e2e_steps = E2E_STEPS
         host_pos = [torch.as_tensor(path[warmup + k] if path is not None else batch.pos).pin_memory()
                     for k in range(e2e_steps)]
         E_host = torch.empty(batch.n_structures, dtype=torch.float64).pin_memory()
@@ -424,10 +429,12 @@ def run_gpu(args, cfg, precision, steps, warmup, world, rank, measure_e2e, clock
                 F_host.copy_(out[1], non_blocking=True)
             g_e2e.replay()
         torch.cuda.synchronize()
+        pin_np = pin_in.numpy()                       # the pinned input as the host program sees it
+        host_np = [h.numpy() for h in host_pos]
         t0 = time.perf_counter()
         for k in range(e2e_steps):
             if g_e2e is not None:
-                pin_in.copy_(host_pos[k])
+                np.copyto(pin_np, host_np[k])
                 g_e2e.replay()
             else:
                 pos_buf.copy_(host_pos[k], non_blocking=True)
