@@ -64,6 +64,8 @@ def lib():
         _lib.or_loss.restype = ctypes.c_double
         _lib.or_feature_table.restype = ctypes.c_int
         _lib.or_num_threads.restype = ctypes.c_int
+        _lib.or_radial_basis.restype = ctypes.c_int
+        _lib.or_radial_fns.restype = ctypes.c_int
     return _lib
 
 
@@ -241,6 +243,32 @@ def param_grad(batch, desc, params, nl: NeighborList, gE, gF):
     if rc != 0:
         raise RuntimeError(f"or_param_grad failed ({rc})")
     return grads
+
+
+def radial_basis(desc, params, r):
+    """(B, dB): f_c(r) Phi_k(r) and its r-derivative for k < n_basis, at one distance."""
+    L = lib()
+    keep = []
+    m = _model(desc, params, keep)
+    nb = int(desc.get("n_basis", 7))
+    B, dB = np.zeros(nb), np.zeros(nb)
+    rc = L.or_radial_basis(ctypes.byref(m), ctypes.c_double(r), _p(B), _p(dB))
+    if rc != 0:
+        raise RuntimeError(f"or_radial_basis failed ({rc})")
+    return B, dB
+
+
+def radial_fns(desc, params, zi, zj, r):
+    """(R, dR): the radial functions R_s(r) of the ordered species pair (zi, zj) and dR_s/dr."""
+    L = lib()
+    keep = []
+    m = _model(desc, params, keep)
+    nr = int(desc.get("n_radial", 5))
+    R, dR = np.zeros(nr), np.zeros(nr)
+    rc = L.or_radial_fns(ctypes.byref(m), ctypes.c_int(zi), ctypes.c_int(zj), ctypes.c_double(r), _p(R), _p(dR))
+    if rc != 0:
+        raise RuntimeError(f"or_radial_fns failed ({rc})")
+    return R, dR
 
 
 def feature_table(n_radial=5):

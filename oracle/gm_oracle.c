@@ -446,6 +446,30 @@ static int struct_of(int n_struct, const int *atom_ptr, int i) {
     return lo;
 }
 
+/* Test hooks for the pins of the radial part (section "Machine Learning Interatomic
+ * Potentials": basis functions combined by species-pair coefficients into R).
+ * or_radial_basis: B[k] = f_c(r) Phi_k(r) and dB[k] = d/dr of it, k < n_basis.
+ * or_radial_fns:   R[s] and dR[s]/dr of the ordered species pair (zi, zj), s < n_radial. */
+int or_radial_basis(const or_model *M, double r, double *B, double *dB) {
+    if (M->n_basis > 16) return 2;
+    pair_basis pb;
+    basis_eval(M, r, &pb);
+    for (int k = 0; k < M->n_basis; ++k) {
+        B[k] = pb.B[k];
+        dB[k] = pb.dB[k];
+    }
+    return 0;
+}
+
+int or_radial_fns(const or_model *M, int zi, int zj, double r, double *R, double *dR) {
+    if (M->n_basis > 16 || M->n_radial > OR_MAXR) return 2;
+    if (zi < 0 || zj < 0 || zi >= M->n_species || zj >= M->n_species) return 3;
+    pair_basis pb;
+    basis_eval(M, r, &pb);
+    radial(M, zi, zj, &pb, R, dR);
+    return 0;
+}
+
 /* ------------------------------------------------------------------ energy + forces */
 
 /*
