@@ -33,6 +33,11 @@ METRIC = "energy+force atom-steps/s at 1.5k & 131k atoms; mixed vs plain FP32 pa
 UNIT = "atom-steps/s"
 FP32_ALU_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # 148 SMs x 128 FP32 lanes x FMA x 2.032 GHz
 FLUSH_BYTES = 256 << 20
+# algorithmic work per unit (the measurement section of the scope table): the neighbour build
+# moves 56 B per atom and 7 B per pair; the moments pass is ~160 FMA per pair, the force pass
+# ~350 FMA per pair (2 flop each)
+NL_BYTES_PER_ATOM, NL_BYTES_PER_PAIR = 56.0, 7.0
+MOMENTS_FLOP_PER_PAIR, FORCES_FLOP_PER_PAIR = 320.0, 700.0
 
 
 def log(*a):
@@ -218,9 +223,9 @@ def algorithmic_work(stage, n_atoms, n_pairs, H):
     if stage == "gemm_l2" or stage == "gemm_b1":
         return 2.0 * n_atoms * H * H, "flop"
     if stage == "moments":
-        return 330.0 * n_pairs, "flop"
+        return MOMENTS_FLOP_PER_PAIR * n_pairs, "flop"
     if stage == "forces":
-        return 800.0 * n_pairs, "flop"
+        return FORCES_FLOP_PER_PAIR * n_pairs, "flop"
     if stage == "contract_fwd":
         return 8.8e3 * n_atoms, "flop"
     if stage == "contract_bwd":
@@ -235,20 +240,76 @@ def algorithmic_work(stage, n_atoms, n_pairs, H):
         return 8.0 * n_atoms, "byte"
     if stage == "nl_fill":
         return 16.0 * n_atoms + 4.0 * n_atoms + 8.0 * n_pairs, "byte"
-    if stage == "nl_coop":
-        # the whole cooperative build: positions and species in, binned copies, counts and
-        # the CSR list out (col 4 B + shift 4 B per pair)
-        return (28.0 + 48.0 + 8.0 + 44.0 + 20.0 + 8.0 + 20.0) * n_atoms + 8.0 * n_pairs, "byte"
-    if stage == "neighbors":
-        # positions in, sorted copies, CSR out (col 4 B + shift 4 B per pair)
-        return 24.0 * n_atoms * 3 + 8.0 * n_pairs + 4.0 * n_atoms, "byte"
+    if stage in ("nl_coop", "neighbors"):
+        # what the build must move: positions in (24 B), sorted coordinates out (24 B),
+        # permutation / cell index (8 B) per atom; column index (4 B) and image shift (3 B)
+        # per pair
+        return NL_BYTES_PER_ATOM * n_atoms + NL_BYTES_PER_PAIR * n_pairs, "byte"
     if stage == "reduce":
         # output-layer partials (H / 32 per atom) and the species index in
         return 4.0 * n_atoms * (H // 32 + 1), "byte"
     return 0.0, "flop"
 
 
-def roofline(stages, n_atoms, n_pairs, H, precision, peaks, sustained):
+# source files whose kernels each stage runs (a traffic figure is void once they change)
+STAGE_SOURCES = {
+    "nl_coop": ("gm_nlist.cu",), "neighbors": ("gm_nlist.cu",), "moments": ("gm_pair.cu", "gm_common.cuh"),
+    "forces": ("gm_pair.cu", "gm_common.cuh"), "contract_fwd": ("gm_contract.cu",),
+    "contract_bwd": ("gm_contract.cu",), "gemm_l1": ("gm_gemm_tc.cuh", "gm_gemm_tc.cu"),
+    "gemm_l2": ("gm_gemm_tc.cuh", "gm_gemm_tc.cu"), "gemm_b1": ("gm_gemm_tc.cuh", "gm_gemm_tc.cu"),
+    "gemm_b0": ("gm_gemm_tc.cuh", "gm_gemm_tc.cu"),
+}
+
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
+# of the stage's kernel on the named workload, with the hash of its sources at that time
+# (the capture commands and figures are under profiles/)
+TRAFFIC = {
+    ("nl_coop", WORKLOADS[2]): {"bytes_per_launch": 140032, "source_sha16": "2022f003a55f031a",
+                                "capture": "profiles/nl_coop_emim1536.md"},
+}
+
+
+def source_sha16(stage):
+    import hashlib
+    h = hashlib.sha256()
+    for f in STAGE_SOURCES.get(stage, ()):
+        h.update((ROOT / "paper_2505_22168_b300" / "csrc" / f).read_bytes())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(stage, workload):
+    t = TRAFFIC.get((stage, workload))
+    if t is None or t["source_sha16"] != source_sha16(stage):
+        return None
+    return t["bytes_per_launch"]
+
+
+def measure_alu_peaks():
+    """FP32 FMA and special-function-unit (ex2) throughput of this GPU, measured with the
+    library's probe kernels (gm_probe_alu): best of five timed launches after one warm-up."""
+    import torch
+
+    from paper_2505_22168_b300 import _lib
+    from paper_2505_22168_b300.gmnn import _ptr, _stream
+    sink = torch.zeros(8192, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    out = {}
+    for kind, name, iters, scale in ((0, "fp32_fma_tflops", 16384, 1e12), (1, "mufu_ex2_gops", 2048, 1e9)):
+        best = 0.0
+        for rep in range(6):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ops = _lib.gm_probe_alu(kind, iters, _ptr(sink), _stream())
+            e1.record(stream)
+            e1.synchronize()
+            if rep > 0:
+                best = max(best, ops / (e0.elapsed_time(e1) * 1e-3))
+        out[name] = round(best / scale, 2)
+    out["how"] = "gm_probe_alu: independent FMA / ex2.approx chains on every SM, CUDA events, best of 5"
+    return out
+
+
+def roofline(stages, n_atoms, n_pairs, H, precision, peaks, sustained, workload=None):
     busy = {k: v for k, v in stages.items() if v[1] > 0}
     if any(k.startswith("nl_") for k in busy):
         busy.pop("neighbors", None)   # its sub-stages are timed on their own
@@ -271,24 +332,31 @@ def roofline(stages, n_atoms, n_pairs, H, precision, peaks, sustained):
         out = {"bound": "tensor", "unit": "TFLOP/s", "peak_source": f"measured {key}" if key in peaks else "fallback"}
     else:
         achieved = work / sec / 1e12
-        peak = FP32_ALU_PEAK_TFLOPS
-        out = {"bound": "alu", "unit": "TFLOP/s",
-               "peak_source": "derived: 148 SMs x 128 FP32 FMA/clk x 2 flop x 2032 MHz"}
+        if "fp32_fma_tflops" in peaks:
+            peak = peaks["fp32_fma_tflops"]
+            src = "measured fp32_fma_tflops (gm_probe_alu, this run)"
+        else:
+            peak = FP32_ALU_PEAK_TFLOPS
+            src = "derived: 148 SMs x 128 FP32 FMA/clk x 2 flop x 2032 MHz"
+        out = {"bound": "alu", "unit": "TFLOP/s", "peak_source": src}
     out.update({"kernel": top, "achieved": round(achieved, 3), "peak": round(peak, 2),
-                "frac": round(achieved / peak, 4), "traffic": None, "ms_per_launch": round(per[top], 5),
-                "algorithmic_work_per_launch": work, "work_unit": unit})
+                "frac": round(achieved / peak, 4), "traffic": traffic_for(top, workload),
+                "ms_per_launch": round(per[top], 5), "algorithmic_work_per_launch": work, "work_unit": unit})
     return out, share
 
 
 # ----------------------------------------------------------------------------- GPU arm
 
-def run_gpu(args, cfg, precision, steps, warmup, world, rank, measure_e2e, clock_sampler=None):
+def run_gpu(args, cfg, precision, steps, warmup, world, rank, measure_e2e, clock_sampler=None,
+            measure_accuracy=False):
     import torch
 
     import synth
     from paper_2505_22168_b300 import GMNN, DeviceSystem, _lib
 
     batch, desc, params = synth.config(cfg)
+    torch.cuda.synchronize()
+    torch.cuda.reset_peak_memory_stats()
     model = GMNN(desc, params, precision=precision)
     sysd = DeviceSystem(batch)
     nl = model.build_neighbors(sysd)
@@ -399,7 +467,23 @@ def run_gpu(args, cfg, precision, steps, warmup, world, rank, measure_e2e, clock
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
         dist.barrier()
+    # device memory of the step: torch's peak (inputs, outputs, neighbour list, workspaces, the
+    # captured graphs' pools) without the benchmark's own buffers, plus the model's weights
+    bench_bytes = FLUSH_BYTES + (len(pos_dev) * sysd.pos.numel() * 8 if path is not None else 0)
+    peak_torch = torch.cuda.max_memory_allocated()
+    memory = {"peak_bytes": int(peak_torch - bench_bytes + _lib.gm_model_device_bytes(model.handle)),
+              "torch_max_allocated_bytes": int(peak_torch), "benchmark_buffers_bytes": int(bench_bytes),
+              "model_weights_bytes": int(_lib.gm_model_device_bytes(model.handle)),
+              "workspace_bytes": {"neighbors": int(model.workspace(_lib.GM_OP_NEIGHBORS, sysd, nl.capacity)[1]),
+                                  "energy_forces": int(model.workspace(_lib.GM_OP_ENERGY_FORCES, sysd, nl.capacity)[1])},
+              "neighbour_list_bytes": int(nl.capacity * 8 + (n + 1) * 4)}
+    accuracy = None
+    if measure_accuracy and cfg == 3:
+        accuracy = batch_accuracy(batch, desc, params, out[0].cpu().numpy(), out[1].cpu().numpy(), range(0, 256, 16))
+    elif measure_accuracy and cfg == 5:
+        accuracy = sampled_accuracy(batch, desc, params, out[1].cpu().numpy(), 12)
     res = {"ms_total": ms, "ms_per_step": ms / steps, "n_atoms": n, "n_pairs": n_pairs, "stages": stages,
+           "memory": memory, "accuracy": accuracy,
            "launches": launches, "H": desc["n_hidden"], "value": world * n * steps / (ms / 1e3),
            "launch_mode": "cuda-graph replay" if graph is not None else "stream launches", "tuning": tuning,
            "ms_per_step_stream_with_stage_events": ms_stream / steps}
@@ -478,12 +562,16 @@ def run_train(args, steps, warmup, precision="fp32"):
     out = (torch.empty(batch.n_structures, dtype=torch.float64, device=model.device),
            torch.empty(batch.n_atoms, 3, dtype=torch.float32, device=model.device), None)
 
+    last = {}
+
     def step():
         model.clear_status()
         model.build_neighbors(sysd, nl, check=False)
         model.energy_forces(sysd, nl, out=out, clear=False)
         loss, gE, gF = model.force_matching_loss(sysd, out[0], Eref, out[1], Fref)
-        return model.param_grad(sysd, nl, gE, gF, clear=False)
+        last["loss"] = loss
+        last["grad"] = model.param_grad(sysd, nl, gE, gF, clear=False)
+        return last["grad"]
 
     for _ in range(warmup):
         step()
@@ -505,7 +593,20 @@ def run_train(args, steps, warmup, precision="fp32"):
     if any(k.startswith("nl_") and v[1] > 0 for k, v in stages.items()):
         stages = {k: v for k, v in stages.items() if k != "neighbors"}
     total = sum(v[0] for v in stages.values() if v[1] > 0) or 1.0
+    # accuracy of the whole training step: the oracle's loss and parameter gradient at the same
+    # parameters and labels (FP64 energies and forces, then the hand-derived gradient)
+    from paper_2505_22168_b300 import unpack_theta
+    ref = oracle.energy_forces(batch, desc, params, onl, virial=False)
+    L_o, gE_o, gF_o = oracle.loss(batch, ref["E"], teach["E"], ref["F"], teach["F"].astype(np.float32).astype(np.float64))
+    go = oracle.param_grad(batch, desc, params, onl, gE_o, gF_o)
+    g = unpack_theta(last["grad"].cpu().numpy().astype(np.float64), desc["n_species"], desc["n_hidden"])
+    rel = {k: float(np.linalg.norm(g[k].ravel() - go[k].ravel()) / np.linalg.norm(go[k].ravel())) for k in go}
+    accuracy = {"loss": float(abs(float(last["loss"].item()) - L_o) / abs(L_o)),
+                "param_grad_rel_l2_worst_group": max(rel.values()),
+                "param_grad_worst_group": max(rel, key=rel.get),
+                "reference": "FP64 oracle loss and parameter gradient on the same batch, parameters and labels"}
     return {"workload": "emim-train-32 (32 EMIM+BF4- boxes, 7920 atoms, r_cut 5 A, MLP 2x128)",
+            "accuracy": accuracy,
             "precision": precision, "step": "neighbours + energy/forces + loss + parameter gradient",
             "value": batch.n_atoms * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
             "steps": steps, "stage_share": {k: round(v[0] / total, 4) for k, v in stages.items() if v[1] > 0}}
@@ -570,6 +671,52 @@ def accuracy_vs_oracle(cfg, ref):
     return out
 
 
+def _errors(E, F, Eref, Fref, E_atom_ref, atom_ptr):
+    """Parity metrics: energy per atom over the rms atomic energy (worst structure), force
+    RMS and largest element over the rms reference force."""
+    out = {}
+    if E is not None:
+        e = 0.0
+        for b in range(len(atom_ptr) - 1):
+            a0, a1 = atom_ptr[b], atom_ptr[b + 1]
+            if a1 > a0:
+                e = max(e, abs(E[b] - Eref[b]) / (a1 - a0) / np.sqrt((E_atom_ref[a0:a1] ** 2).mean()))
+        out["energy"] = float(e)
+    rms = np.sqrt((Fref ** 2).mean())
+    dF = F.astype(np.float64) - Fref
+    out["force_rms"] = float(np.sqrt((dF ** 2).mean()) / rms)
+    out["force_max"] = float(np.abs(dF).max() / rms)
+    return out
+
+
+def batch_accuracy(batch, desc, params, E, F, idx):
+    """Errors of a batched run on a subset of its structures, against the FP64 oracle on those
+    structures alone (structures are independent, so this is exact for them)."""
+    import oracle
+    from synth.systems import make_batch
+    idx = list(idx)
+    ap = batch.atom_ptr
+    sub = make_batch([(batch.pos[ap[b]:ap[b + 1]], batch.species[ap[b]:ap[b + 1]], batch.cell[b]) for b in idx],
+                     batch.n_species)
+    ref = oracle.energy_forces(sub, desc, params, oracle.neighbors(sub, desc["r_cut"]), virial=False)
+    rows = np.concatenate([np.arange(ap[b], ap[b + 1]) for b in idx])
+    out = _errors(E[idx], F[rows], ref["E"], ref["F"], ref["E_atom"], sub.atom_ptr)
+    out["reference"] = f"FP64 oracle on {len(idx)} of the {batch.n_structures} structures ({sub.n_atoms} atoms)"
+    return out
+
+
+def sampled_accuracy(batch, desc, params, F, n_rows):
+    """Force errors of a large system on sampled atoms, against an exact oracle evaluation of
+    those atoms (oracle.sampled_forces)."""
+    import oracle
+    rows = np.sort(np.random.default_rng(31).choice(batch.n_atoms, n_rows, replace=False))
+    ref = oracle.sampled_forces(batch, desc, params, rows)
+    out = _errors(None, F[ref["rows"]], None, ref["F"], None, None)
+    out["reference"] = (f"FP64 oracle forces of {n_rows} sampled atoms (exact sub-evaluation over "
+                        f"{ref['n_sub_atoms']} atoms); energies not compared at this size")
+    return out
+
+
 def cpu_baseline(cfg, budget_s):
     n, times, threads, ref = oracle_step_seconds(cfg, budget_s, keep=True)
     value = n * len(times) / sum(times)
@@ -591,6 +738,7 @@ def main():
     ap.add_argument("--tune", type=int, default=1, help="autotune launch shapes before timing")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the oracle checks of the variants")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--stage-timing", type=int, default=1)
     ap.add_argument("--graph", type=int, default=1, help="replay the step as a CUDA graph")
@@ -637,11 +785,23 @@ def main():
     if pk.exists():
         peaks = json.loads(pk.read_text())
 
+    alu_peaks = measure_alu_peaks()
+    peaks = dict(peaks, **{k: v for k, v in alu_peaks.items() if k != "how"})
     sampler = ClockSampler(local_rank)
     head = run_gpu(args, args.config, precision, args.steps, args.warmup, world, rank, True, sampler)
     clocks = sampler.summary()
     roof, share = roofline(head["stages"], head["n_atoms"], head["n_pairs"], head["H"], precision, peaks,
-                           sustained=False)
+                           sustained=False, workload=WORKLOADS[args.config])
+
+    # errors of both paths at the headline workload's base positions (the oracle run doubles
+    # as the CPU baseline's sample)
+    cpu = None
+    accuracy = None
+    accuracy_by_prec = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu, ref = cpu_baseline(args.config, args.cpu_seconds)
+        accuracy = accuracy_vs_oracle(args.config, ref)
+        accuracy_by_prec = {k: v for k, v in accuracy.items() if k in ("fp32", "mixed")}
 
     variants = []
     if not args.no_variants:
@@ -652,25 +812,24 @@ def main():
                 if prec == "mixed" and not _mixed_available():
                     continue
                 steps = max(5, args.steps // {2: 1, 3: 2, 5: 5}[cfg])
-                r = run_gpu(args, cfg, prec, steps, args.warmup, world, rank, False)
-                rf, sh = roofline(r["stages"], r["n_atoms"], r["n_pairs"], r["H"], prec, peaks, sustained=False)
-                variants.append({"workload": WORKLOADS[cfg], "precision": prec, "value": r["value"], "unit": UNIT,
-                                 "ms_per_step": r["ms_per_step"], "steps": steps, "n_pairs": r["n_pairs"],
-                                 "launch_mode": r["launch_mode"], "tuning": r["tuning"],
-                                 "dominant": rf["kernel"] if rf else None, "roofline_frac": rf["frac"] if rf else None,
-                                 "stage_share": sh})
+                r = run_gpu(args, cfg, prec, steps, args.warmup, world, rank, False,
+                            measure_accuracy=rank == 0 and not args.no_accuracy)
+                rf, sh = roofline(r["stages"], r["n_atoms"], r["n_pairs"], r["H"], prec, peaks, sustained=False,
+                                  workload=WORKLOADS[cfg])
+                v = {"workload": WORKLOADS[cfg], "precision": prec, "value": r["value"], "unit": UNIT,
+                     "ms_per_step": r["ms_per_step"], "steps": steps, "n_pairs": r["n_pairs"],
+                     "launch_mode": r["launch_mode"], "tuning": r["tuning"],
+                     "dominant": rf["kernel"] if rf else None, "roofline_frac": rf["frac"] if rf else None,
+                     "roofline": rf, "stage_share": sh, "memory": r["memory"], "accuracy": r["accuracy"]}
+                if cfg == 2 and accuracy_by_prec is not None:
+                    v["accuracy"] = accuracy_by_prec.get(prec)
+                variants.append(v)
 
     if not args.no_variants:
         for prec in ("fp32", "mixed"):
             if prec == "mixed" and not _mixed_available():
                 continue
             variants.append(run_train(args, max(5, args.steps // 5), args.warmup, prec))
-
-    cpu = None
-    accuracy = None
-    if rank == 0 and not args.no_cpu_baseline:
-        cpu, ref = cpu_baseline(args.config, args.cpu_seconds)
-        accuracy = accuracy_vs_oracle(args.config, ref)
 
     if rank != 0:
         if world > 1:
@@ -689,11 +848,34 @@ def main():
                                       if head["launch_mode"] == "cuda-graph replay" else "(stream launches, ")
                                    + f"{head['ms_per_step_stream_with_stage_events']:.4f} ms/step)"},
         "roofline": roof, "stage_share": share, "cpu_baseline": cpu, "accuracy": accuracy, "e2e": head.get("e2e"),
-        "gpu_launches": head["launches"], "clocks": clocks, "variants": variants,
+        "gpu_launches": head["launches"], "clocks": clocks, "memory": head["memory"], "alu_peaks": alu_peaks,
+        "variants": variants,
     }
+    print_summary(line)
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def _short(x):
+    return "-" if x is None else f"{x:.2e}"
+
+
+def print_summary(line):
+    """One short line per measured workload on stderr (the JSON line on stdout has it all)."""
+    acc = line.get("accuracy") or {}
+    rows = [("headline", line["config"]["workload"].split(" ")[0], line["config"]["precision"], line["value"],
+             line["ms_per_step"], acc.get(line["config"]["precision"]), (line.get("roofline") or {}).get("frac"),
+             (line.get("memory") or {}).get("peak_bytes"))]
+    for v in line.get("variants", []):
+        rows.append(("variant", v["workload"].split(" ")[0], v.get("precision"), v["value"], v["ms_per_step"],
+                     v.get("accuracy"), v.get("roofline_frac"), (v.get("memory") or {}).get("peak_bytes")))
+    for kind, wl, prec, val, ms, a, frac, mem in rows:
+        a = a or {}
+        err = a.get("force_rms", a.get("param_grad_rel_l2_worst_group"))
+        log(f"{kind:8s} {wl:22s} {prec:5s} {val / 1e6:8.2f} M atom-steps/s {ms:8.4f} ms  "
+            f"F/grad err {_short(err)}  E err {_short(a.get('energy'))}  roof {frac}  "
+            f"mem {'-' if mem is None else f'{mem / 2**20:.0f} MiB'}")
 
 
 def _mixed_available():

@@ -28,8 +28,8 @@
  *   - The caller owns every buffer.  Entry points never allocate or free memory, except
  *     gm_model_create / gm_model_destroy, which own the model's repacked weight copies.
  *   - Device pointers are CUDA global memory of the current device.  All work is
- *     enqueued on `stream` (a cudaStream_t, passed as struct CUstream_st*); calls do not
- *     synchronise the host.
+ *     enqueued on `stream` (a cudaStream_t, passed as struct CUstream_st*), which must
+ *     belong to the current device; calls do not synchronise the host.
  *   - The synchronous return value reports argument, shape and launch errors only.
  *     Conditions found on the device are written to *status_dev (an int32 the caller
  *     zeroes before a step): the first error wins; later kernels of the same step see a
@@ -146,6 +146,11 @@ GM_API void gm_model_destroy(gm_model *m);
  *                       (three tensor-core passes) -- bit 1 first layer, 2 second layer,
  *                       4 and 8 the two backward GEMMs; default 12 (backward GEMMs), which
  *                       keeps forces within 2e-3 of the FP64 result
+ *   GM_TUNE_PG_SPLIT_MASK  mixed path: the same bits for the four network GEMMs of
+ *                       gm_param_grad (forward, forward, backward, backward on the stacked
+ *                       primal and tangent rows); default 15 (all split), which keeps every
+ *                       parameter group's gradient within 1e-5 relative L2 of the FP64 result
+ *                       (12 gave 7e-3 on the scale parameters)
  *   GM_TUNE_GEMM_BN     mixed path: tensor-core tile width 64, 128 or 256 (0 = by size)
  *   GM_TUNE_GEMM_CPS    mixed path: tensor-core GEMM blocks resident per SM, 1 or 2 (two halve
  *                       the operand ring and overlap one block's epilogue with the other's
@@ -164,9 +169,20 @@ GM_API void gm_model_destroy(gm_model *m);
  *                       2 = one per warp, 3 = brute force where possible, else as 0
  * Errors: GM_ERR_ARG for an unknown key or value. */
 enum { GM_TUNE_PAIR_TPA = 0, GM_TUNE_SPLIT_MASK = 1, GM_TUNE_GEMM_BN = 2, GM_TUNE_NL_MODE = 3, GM_TUNE_NL_SPLIT = 4,
-       GM_TUNE_NL_BLOCKS = 5, GM_TUNE_NL_TWO_PASS = 6, GM_TUNE_NL_ITEMS = 7, GM_TUNE_GEMM_CPS = 8 };
+       GM_TUNE_NL_BLOCKS = 5, GM_TUNE_NL_TWO_PASS = 6, GM_TUNE_NL_ITEMS = 7, GM_TUNE_GEMM_CPS = 8,
+       GM_TUNE_PG_SPLIT_MASK = 9 };
 enum { GM_NL_MODE_AUTO = 0, GM_NL_MODE_PHASES = 1 };
 GM_API gm_status gm_model_set_tuning(gm_model *m, int32_t key, int32_t value);
+
+/* Lanes per atom the pair kernels use for a system of n_atoms atoms: the GM_TUNE_PAIR_TPA
+ * setting, or (when it is 0) the library's choice by size.  -1 for a null model or a
+ * negative n_atoms. */
+GM_API int32_t gm_model_pair_lanes(const gm_model *m, int32_t n_atoms);
+
+/* Bytes of device memory the model handle itself holds (its repacked weight copies);
+ * 0 for a null model.  With gm_workspace_size this gives a step's whole device footprint
+ * besides the caller's inputs and outputs. */
+GM_API size_t gm_model_device_bytes(const gm_model *m);
 
 /* Bytes of workspace an operation needs (op = GM_OP_*).  nl_capacity is the neighbour
  * list capacity the caller will pass.  Errors: GM_ERR_ARG. */
@@ -198,10 +214,13 @@ GM_API gm_status gm_energy_forces(const gm_model *m, const gm_system *sys, const
  * implicit synchronisation would stall the other streams mid-step.
  * Scratch is a fixed 8 MiB array in the library's own device memory (a file-scope
  * __device__ variable that every GPU loading the library holds until the process exits),
- * which fits systems of up to about 100,000 atoms: exactly, those whose minimum neighbour
- * workspace, gm_workspace_size(..., nl_capacity = 0, GM_OP_NEIGHBORS), is at most 8 MiB (the
- * single-pass search is used when its slab fits too).  Larger systems return
- * GM_ERR_WORKSPACE (gm_last_error says why) without launching anything.
+ * which fits systems whose minimum neighbour workspace, gm_workspace_size(..., nl_capacity
+ * = 0, GM_OP_NEIGHBORS), is at most 8 MiB (about 90,000 atoms in one structure; the
+ * single-pass search is used when its slab fits too, else the two-pass one).  Larger
+ * systems return GM_ERR_WORKSPACE (gm_last_error says why) without launching anything.
+ * The arguments are checked as for gm_build_neighbors (GM_ERR_ARG for a null or misaligned
+ * pointer), and `stream` must belong to the current device (else GM_ERR_ARG): the cached
+ * scratch address is the current device's.
  * The first call on a device, with that device current, looks up the array's device
  * address (cudaGetSymbolAddress) and caches it; make that first call before any stream
  * capture.  All calls share the array and it keeps the last call's contents (the build
@@ -252,6 +271,15 @@ GM_API gm_status gm_profile_collect(double *stage_ms, int64_t *stage_count, int 
  * gm_profile_forget_graphs stops reading them (the events themselves stay allocated, since
  * a graph may still record them). */
 GM_API void gm_profile_forget_graphs(void);
+
+/* Throughput probe (no counterpart in the paper; it measures the denominators of the FP32
+ * rooflines): launches one kernel of independent chains of a single operation on every SM --
+ * kind 0: FP32 fused multiply-add, kind 1: the special-function unit's base-2 exponential --
+ * with `iters` iterations of 64 operations per thread, and writes the number of operations
+ * launched to *ops (an FMA counts as 2 flop).  Time the launch with CUDA events on `stream`.
+ * sink: device float buffer of at least (SMs x 8) entries (never written in practice).
+ * Errors: GM_ERR_ARG, GM_ERR_CUDA. */
+GM_API gm_status gm_probe_alu(int32_t kind, int64_t iters, float *sink, double *ops, struct CUstream_st *stream);
 
 /* Zero the device status word (cudaMemsetAsync on `stream`); call before each step. */
 GM_API gm_status gm_status_clear(int32_t *status_dev, struct CUstream_st *stream);

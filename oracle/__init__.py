@@ -209,6 +209,47 @@ def energy_forces(batch, desc, params, nl: NeighborList, virial=True, psi=False,
     return out
 
 
+class _SubBatch:
+    """The attributes of a batch the oracle reads (positions, species, cells, atom ranges)."""
+
+    def __init__(self, pos, species, atom_ptr, cell, pbc):
+        self.pos, self.species, self.atom_ptr, self.cell, self.pbc = pos, species, atom_ptr, cell, pbc
+        self.n_atoms = int(atom_ptr[-1])
+        self.n_structures = int(len(atom_ptr) - 1)
+
+
+def sampled_forces(batch, desc, params, rows):
+    """Exact forces F[rows] and atomic energies E_atom[rows] of a few atoms of a large system.
+
+    F_i = -d/dr_i sum_k E_k involves only the atoms k whose environment holds i, i.e. i itself
+    and its neighbours (the neighbour relation is symmetric), and E_k needs k's full neighbour
+    row.  So the model is evaluated on the sub-system of those atoms K and their neighbours,
+    with complete rows for K and empty rows for the rest (same positions and cells, so the
+    image shifts stay valid).  Nothing is approximated: F[rows] and E_atom[rows] equal the
+    full evaluation's up to summation order."""
+    r_cut = float(desc["r_cut"])
+    rows = np.unique(np.asarray(rows, np.int64))
+    first = neighbor_rows(batch, r_cut, rows)
+    K = np.unique(np.concatenate([rows, first.col.astype(np.int64)]))
+    nlK = neighbor_rows(batch, r_cut, K)
+    U = np.unique(np.concatenate([K, nlK.col.astype(np.int64)]))
+    remap = np.full(batch.n_atoms, -1, np.int64)
+    remap[U] = np.arange(len(U))
+    counts = np.diff(nlK.row_ptr)[U]
+    row_ptr = np.zeros(len(U) + 1, np.int64)
+    row_ptr[1:] = np.cumsum(counts)
+    # nlK's rows are contiguous in global atom order and U is ascending, so the pairs keep
+    # their order; only the column indices are renumbered
+    col = remap[nlK.col.astype(np.int64)].astype(np.int32)
+    ap = np.asarray(batch.atom_ptr, np.int64)
+    sub_ap = np.searchsorted(U, ap).astype(np.int32)
+    sub = _SubBatch(np.ascontiguousarray(np.asarray(batch.pos)[U]), np.ascontiguousarray(np.asarray(batch.species)[U]),
+                    sub_ap, np.asarray(batch.cell), np.asarray(batch.pbc))
+    out = energy_forces(sub, desc, params, NeighborList(row_ptr, col, nlK.shift), virial=False)
+    return {"rows": rows, "F": out["F"][remap[rows]], "E_atom": out["E_atom"][remap[rows]],
+            "n_sub_atoms": len(U), "n_complete_rows": len(K)}
+
+
 def loss(batch, E, E_ref, F, F_ref, wE=1.0, wF=1.0):
     """Force-matching loss and its gradients (gE [B], gF [N, 3])."""
     L = lib()

@@ -149,6 +149,44 @@ int or_neighbor_rows(int n_struct, const int *atom_ptr, const double *pos, const
     return rc;
 }
 
+/* All pairs (i, j, n) of centre atom i (local index within its structure) by brute force
+ * over every atom j and every image n within the range nmax.  With out_j == NULL only
+ * counts; else writes the pairs in the order j, then n0, n1, n2. */
+static int64_t row_pairs(int i, int n, const double *xw, const int *m, const double *C, int ortho,
+                         const int *nmax, double rc2, int a0, int *out_i, int *out_j, int *out_shift) {
+    int64_t np = 0;
+    for (int j = 0; j < n; ++j)
+        for (int n0 = -nmax[0]; n0 <= nmax[0]; ++n0)
+            for (int n1 = -nmax[1]; n1 <= nmax[1]; ++n1)
+                for (int n2 = -nmax[2]; n2 <= nmax[2]; ++n2) {
+                    if (i == j && n0 == 0 && n1 == 0 && n2 == 0) continue;
+                    double d[3];
+                    if (ortho) {
+                        d[0] = (xw[3 * j] - xw[3 * i]) + (double)n0 * C[0];
+                        d[1] = (xw[3 * j + 1] - xw[3 * i + 1]) + (double)n1 * C[4];
+                        d[2] = (xw[3 * j + 2] - xw[3 * i + 2]) + (double)n2 * C[8];
+                    } else {
+                        for (int c = 0; c < 3; ++c)
+                            d[c] = (xw[3 * j + c] - xw[3 * i + c]) + (n0 * C[c] + n1 * C[3 + c] + n2 * C[6 + c]);
+                    }
+                    double r2 = d[0] * d[0] + d[1] * d[1];
+                    r2 = r2 + d[2] * d[2];
+                    if (!(r2 < rc2)) continue;
+                    if (out_j) {
+                        out_i[np] = a0 + i;
+                        out_j[np] = a0 + j;
+                        out_shift[3 * np + 0] = n0 - m[3 * j + 0] + m[3 * i + 0];
+                        out_shift[3 * np + 1] = n1 - m[3 * j + 1] + m[3 * i + 1];
+                        out_shift[3 * np + 2] = n2 - m[3 * j + 2] + m[3 * i + 2];
+                    }
+                    ++np;
+                }
+    return np;
+}
+
+/* The rows are independent, so they are searched in parallel over centre atoms: a counting
+ * pass, a prefix sum over the rows (in atom order), then a filling pass that writes every
+ * row at its offset.  The arithmetic of each pair test is the same in both passes. */
 static int neighbors_impl(int n_struct, const int *atom_ptr, const double *pos, const double *cell,
                           const unsigned char *pbc, double r_cut, const unsigned char *want_row, int64_t cap,
                           int *pi, int *pj, int *pshift, int64_t *n_pairs) {
@@ -160,6 +198,7 @@ static int neighbors_impl(int n_struct, const int *atom_ptr, const double *pos, 
         const unsigned char *pb = pbc + 3 * b;
         double *xw = (double *)malloc(sizeof(double) * 3 * (n ? n : 1));
         int *m = (int *)malloc(sizeof(int) * 3 * (n ? n : 1));
+        int64_t *cnt = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
         wrap_structure(n, pos + 3 * a0, C, pb, xw, m);
         /* image range: perpendicular widths w_a = V / |b x c| etc. */
         int nmax[3];
@@ -172,36 +211,22 @@ static int neighbors_impl(int n_struct, const int *atom_ptr, const double *pos, 
             nmax[a] = pb[a] ? (int)ceil(r_cut / w) + 1 : 0;
         }
         const int ortho = is_orthorhombic(C);
+#pragma omp parallel for schedule(dynamic, 16)
         for (int i = 0; i < n; ++i) {
             if (want_row && !want_row[a0 + i]) continue;
-            for (int j = 0; j < n; ++j)
-                for (int n0 = -nmax[0]; n0 <= nmax[0]; ++n0)
-                    for (int n1 = -nmax[1]; n1 <= nmax[1]; ++n1)
-                        for (int n2 = -nmax[2]; n2 <= nmax[2]; ++n2) {
-                            if (i == j && n0 == 0 && n1 == 0 && n2 == 0) continue;
-                            double d[3];
-                            if (ortho) {
-                                d[0] = (xw[3 * j] - xw[3 * i]) + (double)n0 * C[0];
-                                d[1] = (xw[3 * j + 1] - xw[3 * i + 1]) + (double)n1 * C[4];
-                                d[2] = (xw[3 * j + 2] - xw[3 * i + 2]) + (double)n2 * C[8];
-                            } else {
-                                for (int c = 0; c < 3; ++c)
-                                    d[c] = (xw[3 * j + c] - xw[3 * i + c]) +
-                                           (n0 * C[c] + n1 * C[3 + c] + n2 * C[6 + c]);
-                            }
-                            double r2 = d[0] * d[0] + d[1] * d[1];
-                            r2 = r2 + d[2] * d[2];
-                            if (!(r2 < rc2)) continue;
-                            if (np < cap) {
-                                pi[np] = a0 + i;
-                                pj[np] = a0 + j;
-                                pshift[3 * np + 0] = n0 - m[3 * j + 0] + m[3 * i + 0];
-                                pshift[3 * np + 1] = n1 - m[3 * j + 1] + m[3 * i + 1];
-                                pshift[3 * np + 2] = n2 - m[3 * j + 2] + m[3 * i + 2];
-                            }
-                            ++np;
-                        }
+            cnt[i + 1] = row_pairs(i, n, xw, m, C, ortho, nmax, rc2, a0, NULL, NULL, NULL);
         }
+        for (int i = 0; i < n; ++i) cnt[i + 1] += cnt[i];
+        if (np + cnt[n] <= cap) {
+#pragma omp parallel for schedule(dynamic, 16)
+            for (int i = 0; i < n; ++i) {
+                if (want_row && !want_row[a0 + i]) continue;
+                const int64_t o = np + cnt[i];
+                row_pairs(i, n, xw, m, C, ortho, nmax, rc2, a0, pi + o, pj + o, pshift + 3 * o);
+            }
+        }
+        np += cnt[n];
+        free(cnt);
         free(xw);
         free(m);
     }

@@ -27,7 +27,7 @@ EXPORTS = ("gm_param_count", "gm_model_create", "gm_model_set_params", "gm_model
            "gm_build_neighbors", "gm_energy_forces", "gm_param_grad", "gm_force_matching_loss", "gm_descriptors",
            "gm_status_clear", "gm_status_string", "gm_last_error", "gm_profile_enable", "gm_profile_reset",
            "gm_profile_n_stages", "gm_profile_stage_name", "gm_profile_collect", "gm_build_neighbors_noalloc", "gm_model_set_tuning",
-           "gm_profile_forget_graphs")
+           "gm_profile_forget_graphs", "gm_model_pair_lanes", "gm_model_device_bytes", "gm_probe_alu")
 
 
 class GmModelDesc(ctypes.Structure):
@@ -93,6 +93,9 @@ def load():
         "gm_build_neighbors_noalloc": (st, [_P, ctypes.POINTER(GmSystem), ctypes.POINTER(GmNlist), _P, _P]),
         "gm_model_set_tuning": (st, [_P, ctypes.c_int32, ctypes.c_int32]),
         "gm_profile_forget_graphs": (None, []),
+        "gm_model_pair_lanes": (ctypes.c_int32, [_P, ctypes.c_int32]),
+        "gm_model_device_bytes": (ctypes.c_size_t, [_P]),
+        "gm_probe_alu": (st, [ctypes.c_int32, ctypes.c_int64, _P, ctypes.POINTER(ctypes.c_double), _P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -128,11 +131,27 @@ def gm_model_set_params(model: int, theta_ptr: int, stream: int):
 GM_TUNE_PAIR_TPA, GM_TUNE_SPLIT_MASK, GM_TUNE_GEMM_BN = 0, 1, 2
 GM_TUNE_NL_MODE, GM_TUNE_NL_SPLIT, GM_TUNE_NL_BLOCKS, GM_TUNE_NL_TWO_PASS, GM_TUNE_NL_ITEMS = 3, 4, 5, 6, 7
 GM_TUNE_GEMM_CPS = 8
+GM_TUNE_PG_SPLIT_MASK = 9
 GM_NL_MODE_AUTO, GM_NL_MODE_PHASES = 0, 1
 
 
 def gm_model_set_tuning(model: int, key: int, value: int):
     check(load().gm_model_set_tuning(model, key, value), "gm_model_set_tuning")
+
+
+def gm_model_pair_lanes(model: int, n_atoms: int) -> int:
+    return int(load().gm_model_pair_lanes(model, n_atoms))
+
+
+def gm_model_device_bytes(model: int) -> int:
+    return int(load().gm_model_device_bytes(model))
+
+
+def gm_probe_alu(kind: int, iters: int, sink: int, stream: int) -> float:
+    """Launch the throughput probe; returns the operations launched (see gm.h)."""
+    ops = ctypes.c_double(0.0)
+    check(load().gm_probe_alu(kind, iters, sink, ctypes.byref(ops), stream), "gm_probe_alu")
+    return float(ops.value)
 
 
 def gm_model_destroy(model: int):

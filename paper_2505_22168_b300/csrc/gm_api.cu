@@ -111,6 +111,7 @@ struct gm_model {
     float *W2;             // [H][H]    backward (B[n][k] = W2[n][k])
     __nv_bfloat16 *W1t_h, *W1p_h, *W2t_h, *W2_h;   // BF16 hi/lo pairs, rows [hi(K) | lo(K)]
     int split_mask;        // GEMMs run with three hi/lo passes: 1 L1, 2 L2, 4 B1, 8 B0
+    int pg_split_mask;     // the same for the four network GEMMs of the parameter gradient
     int gemm_bn;           // tensor-core tile width (0 = by size)
     int gemm_cps;          // tensor-core GEMM blocks per SM (0 = by tile count)
     NlTuning nl;           // neighbour build launch shape
@@ -296,6 +297,13 @@ size_t pg_workspace_bytes(int N, int H, int S) {
 
 bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
+}  // namespace
+
+// Argument checks shared by every entry point that takes a system and a neighbour list
+// (declared in gm_internal.h): every pointer the kernels dereference is non-null where
+// needed and aligned for its element type, so a bad pointer is rejected on the host.
+namespace gm {
+
 gm_status check_system(const gm_model *m, const gm_system *s) {
     if (!m || !s) return fail(GM_ERR_ARG, "null model or system");
     if (s->n_structures < 1 || s->n_atoms < 0) return fail(GM_ERR_ARG, "n_structures must be >= 1 and n_atoms >= 0");
@@ -317,6 +325,24 @@ gm_status check_nlist(const gm_system *s, const gm_nlist *nl, bool need_pairs) {
     (void)need_pairs;
     return GM_OK;
 }
+
+gm_status launch_status() {
+    cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess) return fail(GM_ERR_CUDA, cudaGetErrorString(e));
+    return GM_OK;
+}
+
+gm_status check_stream_device(cudaStream_t stream) {
+    int cur = -1, sdev = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) return fail(GM_ERR_CUDA, "cudaGetDevice failed");
+    if (cudaStreamGetDevice(stream, &sdev) != cudaSuccess) return fail(GM_ERR_ARG, "invalid stream");
+    if (sdev != cur) return fail(GM_ERR_ARG, "the stream belongs to another device than the current one");
+    return GM_OK;
+}
+
+}  // namespace gm
+
+namespace {
 
 PairArgs pair_args(const gm_model *m, const gm_system *s, const gm_nlist *nl, const float4 *pos_hi,
                    const float4 *pos_lo, int32_t *status) {
@@ -349,11 +375,6 @@ int choose_tpa(const gm_model *m, int N) {
     return 32;
 }
 
-gm_status launch_status() {
-    cudaError_t e = cudaPeekAtLastError();
-    if (e != cudaSuccess) return fail(GM_ERR_CUDA, cudaGetErrorString(e));
-    return GM_OK;
-}
 
 }  // namespace
 
@@ -393,6 +414,7 @@ gm_status gm_model_create(const gm_model_desc *d, gm_model **out) {
     for (int k = 0; k < NB; ++k) m->rc.mu[k] = (float)(d->r_min + k * (d->r_cut - d->r_min) / (NB - 1));
     m->pair_tpa = 0;
     m->split_mask = 12;
+    m->pg_split_mask = 15;
     m->gemm_bn = 0;
     m->gemm_cps = 0;
     m->nl = NlTuning();
@@ -432,6 +454,13 @@ gm_status gm_model_set_params(gm_model *m, const float *theta, struct CUstream_s
     return launch_status();
 }
 
+size_t gm_model_device_bytes(const gm_model *m) { return m ? m->buf_bytes : 0; }
+
+int32_t gm_model_pair_lanes(const gm_model *m, int32_t n_atoms) {
+    if (!m || n_atoms < 0) return -1;
+    return choose_tpa(m, n_atoms);
+}
+
 gm_status gm_model_set_tuning(gm_model *m, int32_t key, int32_t value) {
     if (!m) return fail(GM_ERR_ARG, "null model");
     switch (key) {
@@ -443,6 +472,10 @@ gm_status gm_model_set_tuning(gm_model *m, int32_t key, int32_t value) {
     case GM_TUNE_SPLIT_MASK:
         if (value < 0 || value > 15) return fail(GM_ERR_ARG, "split mask must be in 0..15");
         m->split_mask = value;
+        return GM_OK;
+    case GM_TUNE_PG_SPLIT_MASK:
+        if (value < 0 || value > 15) return fail(GM_ERR_ARG, "split mask must be in 0..15");
+        m->pg_split_mask = value;
         return GM_OK;
     case GM_TUNE_GEMM_BN:
         if (value != 0 && value != 64 && value != 128 && value != 256) return fail(GM_ERR_ARG, "bad GEMM tile width");
@@ -707,7 +740,7 @@ gm_status gm_param_grad(const gm_model *m, const gm_system *sys, const gm_nlist 
         // the four stacked-row GEMMs: FFMA in the FP32 path; tcgen05 on hi/lo BF16 copies of
         // the A operand in the mixed path (split passes as for the energy/force GEMMs)
         const bool mixed = m->d.precision == GM_PREC_MIXED;
-        const int sp = m->split_mask;
+        const int sp = m->pg_split_mask;
         auto mm = [&](int which, const float *A, const float *Bf, const __nv_bfloat16 *Bh, int N_, int K_,
                       float *out) -> gm_status {
             e.out0 = out;

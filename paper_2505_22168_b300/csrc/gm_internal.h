@@ -66,9 +66,17 @@ struct StageScope {
     ~StageScope();
 };
 
-// ---- model and error accessors (gm_api.cu)
+// ---- model and error accessors, argument checks (gm_api.cu)
 const gm_model_desc *model_desc(const gm_model *m);
 gm_status set_last_error(gm_status s, const char *msg);
+// GM_ERR_ARG / GM_ERR_UNSUPPORTED (with gm_last_error set) for a system or neighbour list
+// that no kernel may be launched on: null or misaligned pointers, bad sizes
+gm_status check_system(const gm_model *m, const gm_system *s);
+gm_status check_nlist(const gm_system *s, const gm_nlist *nl, bool need_pairs);
+// GM_ERR_CUDA (with the runtime's message) if a launch of this thread failed, else GM_OK
+gm_status launch_status();
+// GM_ERR_ARG unless `stream` belongs to the current device
+gm_status check_stream_device(cudaStream_t stream);
 
 // ---- neighbour search (gm_nlist.cu)
 struct NlTuning {

@@ -48,25 +48,31 @@ extern "C" {
 gm_status gm_build_neighbors_noalloc(const gm_model *m, const gm_system *sys, gm_nlist *nl, int32_t *status_dev,
                                      struct CUstream_st *stream) {
     using gm::set_last_error;
-    if (!m || !sys || !nl || !status_dev) return set_last_error(GM_ERR_ARG, "null argument");
-    if (sys->n_structures < 1 || sys->n_atoms < 0 || !sys->atom_ptr || !sys->cell || !sys->pbc ||
-        (sys->n_atoms > 0 && (!sys->pos || !sys->species)))
-        return set_last_error(GM_ERR_ARG, "bad system");
-    if (!nl->row_ptr || !nl->n_pairs || nl->capacity < 0 || (nl->capacity > 0 && (!nl->col || !nl->shift)))
-        return set_last_error(GM_ERR_ARG, "bad neighbour list");
+    // the same argument checks as gm_build_neighbors: nothing is launched on a null or
+    // misaligned pointer
+    gm_status s = gm::check_system(m, sys);
+    if (s != GM_OK) return s;
+    if ((s = gm::check_nlist(sys, nl, false)) != GM_OK) return s;
+    if (!status_dev) return set_last_error(GM_ERR_ARG, "null status");
+    // the cached scratch address is the current device's, so the stream must be too
+    if ((s = gm::check_stream_device(stream)) != GM_OK) return s;
     const size_t need = gm::nl_workspace_min_bytes(sys->n_structures, sys->n_atoms);
     if (need > GM_NOALLOC_SCRATCH_BYTES)
         return set_last_error(GM_ERR_WORKSPACE,
                               "system too large for the fixed 8 MiB scratch of gm_build_neighbors_noalloc "
-                              "(about 100,000 atoms); use gm_build_neighbors with a workspace");
+                              "(its minimum neighbour workspace exceeds 8 MiB: about 90,000 atoms in one "
+                              "structure); use gm_build_neighbors with a workspace");
     void *scratch = nullptr;
     if (scratch_address(&scratch) != GM_OK)
         return set_last_error(GM_ERR_CUDA, "cudaGetSymbolAddress of the fixed scratch failed");
     const gm_model_desc *d = gm::model_desc(m);
-    gm_status s = gm::nl_build(*sys, d->r_cut, d->n_species, *nl, scratch, GM_NOALLOC_SCRATCH_BYTES, status_dev,
-                               stream, gm::nl_tuning(m));
+    {
+        gm::StageScope sc(gm::ST_NEIGHBORS, stream);
+        s = gm::nl_build(*sys, d->r_cut, d->n_species, *nl, scratch, GM_NOALLOC_SCRATCH_BYTES, status_dev, stream,
+                         gm::nl_tuning(m));
+    }
     if (s != GM_OK) return set_last_error(s, "neighbour build launch failed");
-    return cudaPeekAtLastError() == cudaSuccess ? GM_OK : set_last_error(GM_ERR_CUDA, "launch failed");
+    return gm::launch_status();
 }
 
 }  // extern "C"

@@ -126,11 +126,12 @@ class GMNN:
     TUNING_KEYS = {"pair_tpa": L.GM_TUNE_PAIR_TPA, "split_mask": L.GM_TUNE_SPLIT_MASK, "gemm_bn": L.GM_TUNE_GEMM_BN,
                    "nl_mode": L.GM_TUNE_NL_MODE, "nl_split": L.GM_TUNE_NL_SPLIT, "nl_blocks": L.GM_TUNE_NL_BLOCKS,
                    "nl_two_pass": L.GM_TUNE_NL_TWO_PASS, "nl_items": L.GM_TUNE_NL_ITEMS,
-                   "gemm_cps": L.GM_TUNE_GEMM_CPS}
+                   "gemm_cps": L.GM_TUNE_GEMM_CPS, "pg_split_mask": L.GM_TUNE_PG_SPLIT_MASK}
 
     def set_tuning(self, **knobs):
-        """Speed knobs of the library (gm_model_set_tuning): pair_tpa, split_mask, gemm_bn,
-        gemm_cps, nl_mode, nl_split, nl_blocks, nl_two_pass, nl_items.  None leaves a knob unchanged."""
+        """Speed knobs of the library (gm_model_set_tuning): pair_tpa, split_mask, pg_split_mask,
+        gemm_bn, gemm_cps, nl_mode, nl_split, nl_blocks, nl_two_pass, nl_items.  None leaves a
+        knob unchanged."""
         for name, val in knobs.items():
             if name not in self.TUNING_KEYS:
                 raise ValueError(f"unknown tuning knob {name!r}")
@@ -261,8 +262,9 @@ class GMNNFunction(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, theta, model: GMNN, sysd: DeviceSystem, nl: NeighborList):
-        if model.theta is None or model.theta.data_ptr() != theta.data_ptr():
-            model.set_params(theta.detach())
+        # repack on every call: an optimiser updates theta in place (same storage, new
+        # values), so the storage address says nothing about whether the weights changed
+        model.set_params(theta.detach())
         E, F, _ = model.energy_forces(sysd, nl)
         ctx.model, ctx.sysd, ctx.nl = model, sysd, nl
         return E, F

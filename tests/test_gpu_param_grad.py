@@ -1,24 +1,25 @@
 """GPU force-matching loss and parameter gradient (force double-backward) against the FP64
 oracle, through the C ABI and through the torch.autograd.Function.
 
-Tolerance (no figure is stated for the gradient): relative L2 error per parameter group
+Tolerance (the paper states none for the gradient): relative L2 error per parameter group
 <= 1e-4 for the FP32 kernels, and element-wise |error| <= 1e-3 x max|group|.  The mixed path
-(network GEMMs on tcgen05 with BF16 operands, hi/lo split for the backward GEMMs, FP32
-accumulation) is held to 1e-2 relative L2 per group and 5e-2 element-wise."""
+(network GEMMs on tcgen05 with BF16 operands and FP32 accumulation; by default all four GEMMs
+of the parameter gradient run with hi/lo split operands) is held to 5e-3 relative L2 per group
+and 5e-3 element-wise of the group's largest entry."""
 import numpy as np
 import pytest
 
 import oracle
 import synth
-from tests.parity import subset
+from tests.parity import energy_error, subset
 
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
 GROUPS = ("beta", "W1", "b1", "W2", "b2", "w3", "b3", "sigma", "mu")
-TOL_L2 = {"fp32": 1e-4, "mixed": 1e-2}
-TOL_ELEM = {"fp32": 1e-3, "mixed": 5e-2}
+TOL_L2 = {"fp32": 1e-4, "mixed": 5e-3}
+TOL_ELEM = {"fp32": 1e-3, "mixed": 5e-3}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -124,3 +125,56 @@ def test_autograd_function_backward_matches_oracle():
     _, gE_o, gF_o = oracle.loss(b, E.detach().cpu().numpy(), Eref, F.detach().cpu().numpy().astype(np.float64), Fref)
     go = oracle.param_grad(b, d, p, onl, gE_o, gF_o)
     _compare(theta.grad, go, d["n_species"], d["n_hidden"])
+
+
+@pytest.mark.parametrize("tpa", [1, 2, 4, 8, 16, 32])
+def test_param_grad_every_pair_lane_count(tpa):
+    """The parameter gradient's pair kernels (moments, tangent moments, the beta gradient) at
+    every lanes-per-atom setting, FP32, on the 96-atom box."""
+    b, d, p = synth.config(1, activation="tanh")
+    m, sysd, nl, onl, ref, Eref, Fref = _setup(b, d, p)
+    m.set_tuning(pair_tpa=tpa)
+    _, gE_o, gF_o = oracle.loss(b, ref["E"], Eref, ref["F"], Fref)
+    g = m.param_grad(sysd, nl, torch.as_tensor(gE_o, device=m.device),
+                     torch.as_tensor(gF_o, dtype=torch.float32, device=m.device))
+    m.check_status()
+    go = oracle.param_grad(b, d, p, onl, gE_o, gF_o.astype(np.float32).astype(np.float64))
+    _compare(g, go, d["n_species"], d["n_hidden"])
+
+
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+def test_autograd_training_steps_follow_the_updated_weights(precision):
+    """Three optimiser steps through GMNNFunction.  The optimiser updates theta in place, so
+    every forward must use the updated weights: after each step the energies, forces and
+    theta.grad equal the oracle's at the current theta."""
+    from paper_2505_22168_b300 import GMNNFunction, pack_theta, unpack_theta
+    b4, d, p = synth.config(4, activation="silu")
+    b = subset(b4, [0, 2])
+    m, sysd, nl, onl, ref, Eref, Fref = _setup(b, d, p, precision=precision)
+    theta = torch.as_tensor(pack_theta(p), device=m.device).requires_grad_(True)
+    opt = torch.optim.SGD([theta], lr=0.05)
+    nat = torch.as_tensor(np.diff(b.atom_ptr), dtype=torch.float64, device=m.device)
+    Eref_d = torch.as_tensor(Eref, device=m.device)
+    Fref_d = torch.as_tensor(Fref, device=m.device)
+    tol_f = {"fp32": 1e-5, "mixed": 2e-3}[precision]
+    last = None
+    for step in range(3):
+        opt.zero_grad()
+        E, F = GMNNFunction.apply(theta, m, sysd, nl)
+        L = (((E - Eref_d) / nat) ** 2).mean() + ((F.double() - Fref_d) ** 2).sum() / (3 * b.n_atoms)
+        L.backward()
+        m.check_status()
+        cur = unpack_theta(theta.detach().cpu().numpy().astype(np.float64), d["n_species"], d["n_hidden"])
+        r = oracle.energy_forces(b, d, cur, onl, virial=False)
+        Fg = F.detach().cpu().numpy().astype(np.float64)
+        rms = np.sqrt((r["F"] ** 2).mean())
+        assert np.sqrt(((Fg - r["F"]) ** 2).mean()) / rms <= tol_f, step
+        Eg = E.detach().cpu().numpy()
+        assert energy_error(Eg, r, b) <= tol_f, step
+        _, gE_o, gF_o = oracle.loss(b, Eg, Eref, Fg, Fref)
+        go = oracle.param_grad(b, d, cur, onl, gE_o, gF_o)
+        _compare(theta.grad, go, d["n_species"], d["n_hidden"], precision)
+        if last is not None:
+            assert not np.array_equal(Fg, last)          # the weights did change
+        last = Fg
+        opt.step()

@@ -311,7 +311,7 @@ def _ef_parity(batch, desc, params, precision="fp32", virial=True):
     assert f_rms <= tol, f_rms
     assert f_max <= ELEMENT_FACTOR * tol, f_max
     if virial:
-        assert virial_error(W.cpu().numpy(), ref) <= 10 * tol
+        assert virial_error(W.cpu().numpy(), ref) <= tol
     return e, f_rms
 
 
@@ -548,3 +548,104 @@ def test_full_size_li3po4_sampled_rows_and_properties():
     Fn = F.cpu().numpy().astype(np.float64)
     assert np.abs(Fn.sum(0)).max() <= 1e-4 * np.sqrt((Fn ** 2).mean()) * np.sqrt(b.n_atoms)
     assert np.isfinite(E.cpu().numpy()).all()
+
+
+# ------------------------------------------------------------------ lanes per atom
+
+_REFS = {}
+
+
+def _oracle_ref(key, batch, desc, params):
+    """Oracle energies, forces and virials, computed once per system of this module."""
+    if key not in _REFS:
+        _REFS[key] = oracle.energy_forces(batch, desc, params, oracle.neighbors(batch, desc["r_cut"]))
+    return _REFS[key]
+
+
+def _check_against(ref, batch, E, F, W, tol):
+    e = energy_error(E.cpu().numpy(), ref, batch)
+    f_rms, f_max = force_error(F.cpu().numpy().astype(np.float64), ref)
+    assert e <= tol and f_rms <= tol and f_max <= ELEMENT_FACTOR * tol, (e, f_rms, f_max)
+    if W is not None:
+        v = virial_error(W.cpu().numpy(), ref)
+        assert v <= tol, v
+    return e, f_rms, f_max
+
+
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+@pytest.mark.parametrize("tpa", [1, 2, 4, 8, 16, 32])
+@pytest.mark.parametrize("case", ["config1", "li_small"])
+def test_energy_forces_every_pair_lane_count(case, tpa, precision, li_small):
+    """Every lanes-per-atom shape of the pair kernels (moments and forces; 1, 2 and 4 lanes
+    use their own code without the shared-memory dE/dPsi rows) against the oracle, with the
+    virial, on the 96-atom box and on 24 Li3PO4 boxes (several with multiple images)."""
+    b, d, p = synth.config(1) if case == "config1" else li_small
+    ref = _oracle_ref(case, b, d, p)
+    GMNN, DeviceSystem = _gm()
+    m = GMNN(d, p, precision=precision)
+    m.set_tuning(pair_tpa=tpa)
+    from paper_2505_22168_b300 import _lib
+    assert _lib.gm_model_pair_lanes(m.handle, b.n_atoms) == tpa
+    sysd = DeviceSystem(b)
+    nl = m.build_neighbors(sysd)
+    E, F, W = m.energy_forces(sysd, nl, virial=True)
+    m.check_status()
+    _check_against(ref, b, E, F, W, TOL[precision])
+
+
+def _li_boxes(n_boxes):
+    """n_boxes Li3PO4-like crystals of 512 atoms each (17.2 A, single image at r_cut 6) with
+    the 131,072-atom workload's model (r_cut 6, 2x512): the library's own lanes-per-atom
+    choice depends on the total atom count only."""
+    from synth.systems import li3po4_crystal
+    _, d, p = synth.config(5)
+    b = make_batch([li3po4_crystal(64, 7100 + k, sigma=0.1) for k in range(n_boxes)], 3)
+    return b, d, p
+
+
+@pytest.mark.parametrize("n_boxes,lanes", [(16, 8), (32, 2), (96, 1)])
+def test_library_lane_choice_by_size_matches_oracle(n_boxes, lanes):
+    """8,192, 16,384 and 49,152 atoms: the pair-kernel shapes the library picks by size for
+    mid-size and large systems (8, 2 and 1 lanes per atom, as for the 131,072-atom crystal and
+    the batched Li3PO4 workload), with no forced knob, against the full oracle for both
+    precisions, energies, forces and virials."""
+    b, d, p = _li_boxes(n_boxes)
+    ref = _oracle_ref(("li_boxes", n_boxes), b, d, p)
+    GMNN, DeviceSystem = _gm()
+    from paper_2505_22168_b300 import _lib
+    for precision in ("fp32", "mixed"):
+        m = GMNN(d, p, precision=precision)
+        assert _lib.gm_model_pair_lanes(m.handle, b.n_atoms) == lanes
+        sysd = DeviceSystem(b)
+        nl = m.build_neighbors(sysd)
+        E, F, W = m.energy_forces(sysd, nl, virial=True)
+        m.check_status()
+        _check_against(ref, b, E, F, W, TOL[precision])
+        E2, F2, _ = m.energy_forces(sysd, nl, virial=False)       # the step the benchmark times
+        m.check_status()
+        _check_against(ref, b, E2, F2, None, TOL[precision])
+
+
+def test_full_size_li3po4_sampled_forces_match_oracle():
+    """131,072 atoms in the benchmark's launch configuration (one lane per atom): the forces
+    and the atomic energies of 12 sampled atoms equal an exact oracle evaluation of those atoms
+    (their neighbours' complete environments are evaluated; nothing is truncated), for both
+    precisions."""
+    b, d, p = synth.config(5)
+    rows = np.sort(np.random.default_rng(21).choice(b.n_atoms, 12, replace=False))
+    ref = oracle.sampled_forces(b, d, p, rows)
+    GMNN, DeviceSystem = _gm()
+    from paper_2505_22168_b300 import _lib
+    for precision in ("fp32", "mixed"):
+        m = GMNN(d, p, precision=precision)
+        assert _lib.gm_model_pair_lanes(m.handle, b.n_atoms) == 1
+        sysd = DeviceSystem(b)
+        nl = m.build_neighbors(sysd)
+        _, F, _ = m.energy_forces(sysd, nl, virial=False)
+        m.check_status()
+        Fs = F.cpu().numpy().astype(np.float64)[ref["rows"]]
+        rms = np.sqrt((ref["F"] ** 2).mean())
+        tol = TOL[precision]
+        f_rms = np.sqrt(((Fs - ref["F"]) ** 2).mean()) / rms
+        f_max = np.abs(Fs - ref["F"]).max() / rms
+        assert f_rms <= tol and f_max <= ELEMENT_FACTOR * tol, (precision, f_rms, f_max)

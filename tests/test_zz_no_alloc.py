@@ -36,10 +36,11 @@ def _host(nl):
     return (nl.row_ptr.cpu().numpy(), nl.col[:P].cpu().numpy(), nl.shift[:P].cpu().numpy(), P)
 
 
-def _compare_once(batch, desc, params):
+def _compare_once(batch, desc, params, **tuning):
     from paper_2505_22168_b300 import GMNN, DeviceSystem, _lib
     from paper_2505_22168_b300.gmnn import _ptr, _stream
     model = GMNN(desc, params)
+    model.set_tuning(**tuning)
     sysd = DeviceSystem(batch)
     cap = model.estimate_capacity(sysd)
     ref, got = _lists(model, sysd, cap)
@@ -64,6 +65,37 @@ def test_noalloc_matches_workspace_build_on_two_calls_in_a_row():
     _compare_once(b1, d1, p1)                          # first call (may set up the scratch address)
     _compare_once(subset(b3, range(40)), d3, p3)       # second call: other system, stale scratch
     _compare_once(b1, d1, p1)                          # and back
+
+
+def test_noalloc_two_pass_search_matches_workspace_build():
+    """Systems whose search slab does not fit beside the minimum workspace in the fixed
+    scratch take the two-pass search (count, then fill): a 32,768-atom Li3PO4-like crystal
+    at r_cut 6 (minimum workspace ~3 MB, slab ~17 MB), and the 96-atom box with the
+    two-pass search forced on both entry points."""
+    from synth.systems import li3po4_crystal, make_batch
+    b5, d5, p5 = synth.config(5)
+    big = make_batch([li3po4_crystal(4096, 2024, sigma=0.1)], b5.n_species)
+    _compare_once(big, d5, p5)
+    b1, d1, p1 = synth.config(1)
+    _compare_once(b1, d1, p1, nl_two_pass=1)
+
+
+def test_noalloc_rejects_a_misaligned_position_pointer():
+    """The same host-side argument checks as gm_build_neighbors: a position pointer that is
+    not 8-byte aligned returns GM_ERR_ARG before anything is launched."""
+    from paper_2505_22168_b300 import GMNN, DeviceSystem, NeighborList, _lib
+    from paper_2505_22168_b300.gmnn import _ptr, _stream
+    b, d, p = synth.config(1)
+    model = GMNN(d, p)
+    sysd = DeviceSystem(b)
+    sysc = sysd.c_struct()
+    sysc.pos = _ptr(sysd.pos) + 4
+    nl = NeighborList(b.n_atoms, 16, model.device)
+    with pytest.raises(_lib.GmError) as e:
+        _lib.gm_build_neighbors_noalloc(model.handle, sysc, nl.c_struct(), _ptr(model.status), _stream())
+    assert e.value.code == _lib.GM_ERR_ARG
+    torch.cuda.synchronize()
+    assert model.read_status() == _lib.GM_OK
 
 
 def test_noalloc_rejects_systems_beyond_its_fixed_scratch():
