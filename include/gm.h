@@ -69,6 +69,17 @@ typedef enum {
 
 typedef enum { GM_ACT_TANH = 0, GM_ACT_SILU = 1 } gm_activation;
 
+/* Radial basis (section "Machine Learning Interatomic Potentials" names both):
+ *   GM_BASIS_GAUSSIAN  equidistant Gaussians (the reading above)
+ *   GM_BASIS_BESSEL    Bessel-like functions of Kocer et al.,
+ *                      f_k(r) = a_k [j0((k+1) pi r/r_cut) + j0((k+2) pi r/r_cut)], j0(x) = sin(x)/x,
+ *                      a_k = (-1)^k sqrt(2) pi r_cut^(-3/2) (k+1)(k+2) / sqrt((k+1)^2 + (k+2)^2),
+ *                      with the same cutoff f_c and n_basis^(-1/2) normalisation; r_min unused */
+typedef enum { GM_BASIS_GAUSSIAN = 0, GM_BASIS_BESSEL = 1 } gm_basis;
+
+/* Most shallow-ensemble output heads a model may have. */
+#define GM_MAX_ENSEMBLE 32
+
 typedef enum {
     GM_PREC_FP32 = 0,  /* moments, contractions and network in FP32 (FFMA) */
     GM_PREC_MIXED = 1  /* network GEMMs in BF16 on tcgen05 tensor cores with FP32
@@ -89,6 +100,9 @@ typedef struct {
     int32_t precision;  /* gm_precision */
     double r_min;       /* first Gaussian centre (A) */
     double r_cut;       /* cutoff radius (A) */
+    int32_t basis;      /* gm_basis; 0 (zero-initialised) = GM_BASIS_GAUSSIAN */
+    int32_t n_ensemble; /* shallow-ensemble output heads N_ens (section "Uncertainty
+                           Quantification"): 0 or 1 = one head, up to GM_MAX_ENSEMBLE */
 } gm_model_desc;
 
 typedef struct gm_model gm_model; /* opaque */
@@ -124,8 +138,9 @@ typedef struct {
 enum { GM_OP_NEIGHBORS = 0, GM_OP_ENERGY_FORCES = 1, GM_OP_PARAM_GRAD = 2 };
 
 /* Number of FP32 parameters.  Flat layout of theta, in this order:
- *   beta[S][S][n_radial][n_basis], W1[360][H], b1[H], W2[H][H], b2[H], w3[H], b3[1],
- *   sigma[S], mu[S]   (row-major; W1 maps features to the first hidden layer). */
+ *   beta[S][S][n_radial][n_basis], W1[360][H], b1[H], W2[H][H], b2[H], w3[H][E], b3[E],
+ *   sigma[S], mu[S]   (row-major; W1 maps features to the first hidden layer; E = the
+ *   number of output heads, 1 unless desc.n_ensemble > 1). */
 GM_API int64_t gm_param_count(const gm_model_desc *desc);
 
 /* Create a model handle (allocates its device weight copies on the current device).
@@ -206,6 +221,35 @@ GM_API gm_status gm_energy_forces(const gm_model *m, const gm_system *sys, const
                            float *forces, double *virial, void *ws, size_t ws_bytes, int32_t *status_dev,
                            struct CUstream_st *stream);
 
+/* Force modes of a shallow ensemble (section "Uncertainty Quantification", Eq. jacobian). */
+enum { GM_ENS_MEAN_GRADIENT = 0, GM_ENS_JACOBIAN = 1 };
+
+/* Energies and forces of a shallow-ensemble model (desc.n_ensemble = E >= 2 output heads on
+ * the last hidden layer; section "Uncertainty Quantification").  Head k gives
+ * E_i^(k) = sigma_Zi (w3[:, k] . a2_i + b3[k]) + mu_Zi and E^(k) = sum_i E_i^(k).
+ *   energy        device [B] FP64: the mean over heads, Ebar = (1/E) sum_k E^(k)
+ *   forces        device [N][3] FP32: -dEbar/dr (Eq. jacobian, left: one backward pass with
+ *                 the heads' mean weights)
+ *   virial        device [B][9] FP64 of Ebar, or NULL
+ *   energy_heads  device [B][E] FP64, E^(k) per structure, or NULL
+ *   energy_std    device [B] FP64, sigma_E = sqrt((1/E) sum_k (E^(k) - Ebar)^2) (Eq.
+ *                 uncertainty), or NULL
+ *   mode          GM_ENS_MEAN_GRADIENT, or GM_ENS_JACOBIAN: also every head's forces
+ *                 F^(k) = -dE^(k)/dr (Eq. jacobian, right; E more backward passes), which
+ *                 give (with the implied sum over components of Eq. uncertainty)
+ *   forces_heads  device [E][N][3] FP32, F^(k), or NULL (GM_ENS_JACOBIAN only)
+ *   force_std     device [N] FP32, sigma_F,i = sqrt((1/E) sum_k |F^(k)_i - mean_k F^(k)_i|^2),
+ *                 or NULL (GM_ENS_JACOBIAN only)
+ * Workspace as GM_OP_ENERGY_FORCES.  gm_energy_forces on an ensemble model returns energy
+ * and forces of the mean as above (no per-head outputs).  Errors: GM_ERR_ARG (a model with
+ * one head, per-head forces requested in the mean-gradient mode, null or misaligned
+ * pointers), GM_ERR_WORKSPACE. */
+GM_API gm_status gm_energy_forces_ensemble(const gm_model *m, const gm_system *sys, const gm_nlist *nl,
+                                           double *energy, float *forces, double *virial, double *energy_heads,
+                                           double *energy_std, int32_t mode, float *forces_heads, float *force_std,
+                                           void *ws, size_t ws_bytes, int32_t *status_dev,
+                                           struct CUstream_st *stream);
+
 /* Neighbour search that allocates nothing and needs no workspace (the paper has no
  * counterpart; this is a convenience of this library).  Same inputs, outputs, rule and
  * status reporting as gm_build_neighbors, for callers that cannot hand the library
@@ -229,7 +273,8 @@ GM_API gm_status gm_energy_forces(const gm_model *m, const gm_system *sys, const
 GM_API gm_status gm_build_neighbors_noalloc(const gm_model *m, const gm_system *sys, gm_nlist *nl,
                                             int32_t *status_dev, struct CUstream_st *stream);
 
-/* Parameter gradient of a loss through energies and forces:
+/* Parameter gradient of a loss through energies and forces (models with one output head;
+ * a shallow-ensemble model returns GM_ERR_UNSUPPORTED):
  *   grad_theta = d/dtheta [ sum_b dL_dE[b] E_b + sum_i dL_dF[i] . F_i ]
  * (section "Training": loss terms on energies and forces).  dL_dE device [B] FP64,
  * dL_dF device [N][3] FP32, grad_theta device [gm_param_count] FP32, overwritten.

@@ -39,7 +39,7 @@ class _Model(ctypes.Structure):
                 ("n_hidden", ctypes.c_int), ("activation", ctypes.c_int),
                 ("r_min", ctypes.c_double), ("r_cut", ctypes.c_double)] + \
                [(k, ctypes.POINTER(ctypes.c_double)) for k in
-                ("beta", "W1", "b1", "W2", "b2", "w3", "b3", "sigma", "mu")]
+                ("beta", "W1", "b1", "W2", "b2", "w3", "b3", "sigma", "mu")] + [("basis", ctypes.c_int)]
 
 
 class _Grad(ctypes.Structure):
@@ -49,6 +49,7 @@ class _Grad(ctypes.Structure):
 
 PARAM_NAMES = ("beta", "W1", "b1", "W2", "b2", "w3", "b3", "sigma", "mu")
 ACTIVATIONS = {"tanh": 0, "silu": 1}
+BASES = {"gaussian": 0, "bessel": 1}
 
 
 def lib():
@@ -79,7 +80,7 @@ def _model(desc, params, keep):
     return _Model(int(desc["n_species"]), int(desc.get("n_basis", 7)), int(desc.get("n_radial", 5)),
                   int(desc["n_hidden"]), ACTIVATIONS[desc.get("activation", "silu")],
                   float(desc.get("r_min", 0.5)), float(desc["r_cut"]),
-                  *[_p(arrs[k]) for k in PARAM_NAMES])
+                  *[_p(arrs[k]) for k in PARAM_NAMES], BASES[desc.get("basis", "gaussian")])
 
 
 class NeighborList:
@@ -206,6 +207,32 @@ def energy_forces(batch, desc, params, nl: NeighborList, virial=True, psi=False,
                             _p(out["virial"]), _p(out["psi"]), _p(out["G"]))
     if rc != 0:
         raise RuntimeError(f"or_energy_forces failed ({rc})")
+    return out
+
+
+def energy_forces_ensemble(batch, desc, params, nl: NeighborList, virial=True):
+    """Shallow ensemble (section "Uncertainty Quantification"): output weights w3 [H, E] and
+    b3 [E] on one network.  Head k is the model with w3[:, k] and b3[k]; each head is evaluated
+    in full (energies, forces, virials), then the mean over heads gives the ensemble energy
+    and force (Eq. jacobian: the mean force is minus the gradient of the mean energy) and the
+    spread over heads with the 1/E normalisation of Eq. uncertainty: per structure for the
+    energy, per atom for the force with the sum over its three components.
+    Returns E [B], F [N,3], virial [B,3,3], E_heads [B,E], F_heads [E,N,3], E_std [B], F_std [N]."""
+    w3 = np.asarray(params["w3"], np.float64)
+    b3 = np.asarray(params["b3"], np.float64).reshape(-1)
+    if w3.ndim == 1:
+        w3 = w3[:, None]
+    n_heads = w3.shape[1]
+    heads = [energy_forces(batch, desc, dict(params, w3=np.ascontiguousarray(w3[:, k]), b3=b3[k:k + 1]), nl,
+                           virial=virial) for k in range(n_heads)]
+    Eh = np.stack([h["E"] for h in heads], 1)
+    Fh = np.stack([h["F"] for h in heads])
+    Em, Fm = Eh.mean(1), Fh.mean(0)
+    out = {"E_heads": Eh, "F_heads": Fh, "E": Em, "F": Fm,
+           "E_std": np.sqrt(((Eh - Em[:, None]) ** 2).mean(1)),
+           "F_std": np.sqrt(((Fh - Fm[None]) ** 2).sum(2).mean(0)),
+           "E_atom": np.mean([h["E_atom"] for h in heads], 0)}
+    out["virial"] = np.mean([h["virial"] for h in heads], 0) if virial else None
     return out
 
 

@@ -20,6 +20,8 @@
  * the complete contraction list):
  *   Phi_k(r) = exp(-gamma (r - mu_k)^2), mu_k = r_min + k (r_c - r_min)/(n_b - 1),
  *              gamma = n_b^2 / r_c^2                      ("equidistant Gaussians")
+ *   or, as the alternative basis, the Bessel-like functions of Kocer et al.
+ *   f_k(r)   = a_k [j0((k+1) pi r/r_c) + j0((k+2) pi r/r_c)]   (see basis_eval)
  *   f_c(r)   = (cos(pi r / r_c) + 1) / 2 for r < r_c, else 0
  *   R_s(r)   = f_c(r) n_b^{-1/2} sum_k beta[Zi][Zj][s][k] Phi_k(r)  (ordered pair)
  *   features = 8 families (#1 Psi0; #2 Psi1.Psi1; #3 Psi2:Psi2; #4 Psi3:Psi3;
@@ -60,6 +62,7 @@ typedef struct {
     const double *b3;    /* [1] */
     const double *sigma; /* [S] */
     const double *mu;    /* [S] */
+    int basis;           /* 0: equidistant Gaussians, 1: Bessel-like functions (Kocer et al.) */
 } or_model;
 
 typedef struct { /* parameter gradient, same shapes as or_model */
@@ -249,6 +252,28 @@ static void basis_eval(const or_model *M, double r, pair_basis *pb) {
     if (r < rc) {
         fc = 0.5 * (cos(M_PI * r / rc) + 1.0);
         dfc = -0.5 * M_PI / rc * sin(M_PI * r / rc);
+    }
+    if (M->basis == 1) {
+        /* Bessel-like functions of Kocer et al. (the second basis named in section "Machine
+         * Learning Interatomic Potentials"): sums of two consecutive zeroth-order spherical
+         * Bessel functions j0(x) = sin(x)/x whose zeros sit at r_cut,
+         *   f_k(r) = a_k [j0((k+1) pi r / r_c) + j0((k+2) pi r / r_c)],
+         *   a_k    = (-1)^k sqrt(2) pi r_c^(-3/2) (k+1)(k+2) / sqrt((k+1)^2 + (k+2)^2),
+         * so that f_k and f_k' vanish at r_c and int_0^rc f_k^2 r^2 dr = 1; read here with the
+         * same cosine cutoff and n_b^(-1/2) normalisation as the Gaussians.
+         * d/dr j0(c r) = (cos(c r) - j0(c r)) / r. */
+        for (int k = 0; k < nb; ++k) {
+            const double n1 = k + 1.0, n2 = k + 2.0;
+            const double a = ((k & 1) ? -1.0 : 1.0) * sqrt(2.0) * M_PI / pow(rc, 1.5) * n1 * n2 /
+                             sqrt(n1 * n1 + n2 * n2);
+            const double x1 = n1 * M_PI * r / rc, x2 = n2 * M_PI * r / rc;
+            const double j1 = sin(x1) / x1, j2 = sin(x2) / x2;
+            const double phi = a * (j1 + j2);
+            const double dphi = a * ((cos(x1) - j1) / r + (cos(x2) - j2) / r);
+            pb->B[k] = fc * phi;
+            pb->dB[k] = dfc * phi + fc * dphi;
+        }
+        return;
     }
     for (int k = 0; k < nb; ++k) {
         double muk = M->r_min + k * (rc - M->r_min) / (nb - 1);

@@ -76,9 +76,17 @@ def model_energy(pos, strain, params, desc, species, atom_ptr, cell, pairs):
     r = torch.sqrt((d * d).sum(1))
     u = d / r[:, None]
     nb, nr, rc, rmin = desc["n_basis"], desc["n_radial"], desc["r_cut"], desc["r_min"]
-    mu_k = torch.tensor([rmin + k * (rc - rmin) / (nb - 1) for k in range(nb)], dtype=torch.float64)
-    gamma = nb * nb / (rc * rc)
-    phi = torch.exp(-gamma * (r[:, None] - mu_k[None, :]) ** 2)
+    if desc.get("basis", "gaussian") == "bessel":
+        # Kocer et al.: a_k [j0((k+1) pi r / r_c) + j0((k+2) pi r / r_c)], j0(x) = sin x / x
+        k = torch.arange(nb, dtype=torch.float64)
+        a = (-1.0) ** k * math.sqrt(2.0) * math.pi / rc ** 1.5 * (k + 1) * (k + 2) / torch.sqrt((k + 1) ** 2 + (k + 2) ** 2)
+        x1 = (k[None, :] + 1) * math.pi * r[:, None] / rc
+        x2 = (k[None, :] + 2) * math.pi * r[:, None] / rc
+        phi = a[None, :] * (torch.sin(x1) / x1 + torch.sin(x2) / x2)
+    else:
+        mu_k = torch.tensor([rmin + k * (rc - rmin) / (nb - 1) for k in range(nb)], dtype=torch.float64)
+        gamma = nb * nb / (rc * rc)
+        phi = torch.exp(-gamma * (r[:, None] - mu_k[None, :]) ** 2)
     fc = torch.where(r < rc, 0.5 * (torch.cos(math.pi * r / rc) + 1.0), torch.zeros_like(r))
     beta = params["beta"][species[i], species[j]]          # [P, nr, nb]
     R = fc[:, None] * torch.einsum("psk,pk->ps", beta, phi) / math.sqrt(nb)

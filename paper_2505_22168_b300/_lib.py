@@ -15,6 +15,9 @@ GM_OK, GM_ERR_ARG, GM_ERR_CAPACITY, GM_ERR_UNSUPPORTED, GM_ERR_CUDA, GM_ERR_TIME
     GM_ERR_WORKSPACE = range(8)
 GM_ACT_TANH, GM_ACT_SILU = 0, 1
 GM_PREC_FP32, GM_PREC_MIXED = 0, 1
+GM_BASIS_GAUSSIAN, GM_BASIS_BESSEL = 0, 1
+GM_ENS_MEAN_GRADIENT, GM_ENS_JACOBIAN = 0, 1
+GM_MAX_ENSEMBLE = 32
 GM_OP_NEIGHBORS, GM_OP_ENERGY_FORCES, GM_OP_PARAM_GRAD = 0, 1, 2
 GM_MAX_ATOMS = 4_000_000
 MIXED_AVAILABLE = True   # GM_PREC_MIXED: BF16 network GEMMs on tcgen05
@@ -27,13 +30,15 @@ EXPORTS = ("gm_param_count", "gm_model_create", "gm_model_set_params", "gm_model
            "gm_build_neighbors", "gm_energy_forces", "gm_param_grad", "gm_force_matching_loss", "gm_descriptors",
            "gm_status_clear", "gm_status_string", "gm_last_error", "gm_profile_enable", "gm_profile_reset",
            "gm_profile_n_stages", "gm_profile_stage_name", "gm_profile_collect", "gm_build_neighbors_noalloc", "gm_model_set_tuning",
-           "gm_profile_forget_graphs", "gm_model_pair_lanes", "gm_model_device_bytes", "gm_probe_alu")
+           "gm_profile_forget_graphs", "gm_model_pair_lanes", "gm_model_device_bytes", "gm_probe_alu",
+           "gm_energy_forces_ensemble")
 
 
 class GmModelDesc(ctypes.Structure):
     _fields_ = [("n_species", ctypes.c_int32), ("n_basis", ctypes.c_int32), ("n_radial", ctypes.c_int32),
                 ("n_hidden", ctypes.c_int32), ("activation", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("r_min", ctypes.c_double), ("r_cut", ctypes.c_double)]
+                ("r_min", ctypes.c_double), ("r_cut", ctypes.c_double), ("basis", ctypes.c_int32),
+                ("n_ensemble", ctypes.c_int32)]
 
 
 class GmSystem(ctypes.Structure):
@@ -96,6 +101,8 @@ def load():
         "gm_model_pair_lanes": (ctypes.c_int32, [_P, ctypes.c_int32]),
         "gm_model_device_bytes": (ctypes.c_size_t, [_P]),
         "gm_probe_alu": (st, [ctypes.c_int32, ctypes.c_int64, _P, ctypes.POINTER(ctypes.c_double), _P]),
+        "gm_energy_forces_ensemble": (st, [_P, ctypes.POINTER(GmSystem), ctypes.POINTER(GmNlist), _P, _P, _P, _P, _P,
+                                           ctypes.c_int32, _P, _P, _P, ctypes.c_size_t, _P, _P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -179,6 +186,13 @@ def gm_build_neighbors_noalloc(model, sys: GmSystem, nl: GmNlist, status, stream
 def gm_energy_forces(model, sys: GmSystem, nl: GmNlist, energy, forces, virial, ws, ws_bytes, status, stream):
     check(load().gm_energy_forces(model, ctypes.byref(sys), ctypes.byref(nl), energy, forces, virial, ws, ws_bytes,
                                   status, stream), "gm_energy_forces")
+
+
+def gm_energy_forces_ensemble(model, sys: GmSystem, nl: GmNlist, energy, forces, virial, energy_heads, energy_std,
+                              mode, forces_heads, force_std, ws, ws_bytes, status, stream):
+    check(load().gm_energy_forces_ensemble(model, ctypes.byref(sys), ctypes.byref(nl), energy, forces, virial,
+                                           energy_heads, energy_std, mode, forces_heads, force_std, ws, ws_bytes,
+                                           status, stream), "gm_energy_forces_ensemble")
 
 
 def gm_param_grad(model, sys: GmSystem, nl: GmNlist, dL_dE, dL_dF, grad_theta, ws, ws_bytes, status, stream):

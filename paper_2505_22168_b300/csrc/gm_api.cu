@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "gm_contract.h"
+#include "gm_ensemble.h"
 #include "gm_gemm.h"
 #include "gm_internal.h"
 #include "gm_pair.h"
@@ -98,7 +99,7 @@ StageScope::~StageScope() {
 
 struct gm_model {
     gm_model_desc d;
-    int S, H;
+    int S, H, E;           // species, hidden width, shallow-ensemble heads (1 = plain model)
     int64_t n_param;
     RadialConst rc;
     int pair_tpa;          // lanes per atom in the pair kernels (0 = automatic)
@@ -116,15 +117,17 @@ struct gm_model {
     int gemm_cps;          // tensor-core GEMM blocks per SM (0 = by tile count)
     NlTuning nl;           // neighbour build launch shape
     float *b1, *b2, *w3, *b3, *sigma, *mu;
+    float *w3e, *b3e;      // ensemble heads: w3e [E][H] (member-major), b3e [E]; w3 and b3 hold
+                           // their mean (the head whose gradient is the mean force)
 };
 
 namespace {
 
 struct Layout {
-    size_t beta, W1t, W1p, W2t, W2, W1t_h, W1p_h, W2t_h, W2_h, b1, b2, w3, b3, sigma, mu, total;
+    size_t beta, W1t, W1p, W2t, W2, W1t_h, W1p_h, W2t_h, W2_h, b1, b2, w3, b3, sigma, mu, w3e, b3e, total;
 };
 
-Layout model_layout(int S, int H) {
+Layout model_layout(int S, int H, int E) {
     Layout L;
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -147,6 +150,8 @@ Layout model_layout(int S, int H) {
     L.b3 = take(sizeof(float) * 4);
     L.sigma = take(sizeof(float) * S);
     L.mu = take(sizeof(float) * S);
+    L.w3e = take(sizeof(float) * (size_t)E * H);
+    L.b3e = take(sizeof(float) * E);
     L.total = off;
     return L;
 }
@@ -155,7 +160,8 @@ struct ThetaOff {
     int64_t beta, W1, b1, W2, b2, w3, b3, sigma, mu, total;
 };
 
-ThetaOff theta_offsets(int S, int H) {
+// flat theta: ..., w3 [H][E], b3 [E], sigma, mu (E = 1: w3 [H], b3 [1])
+ThetaOff theta_offsets(int S, int H, int E = 1) {
     ThetaOff o;
     o.beta = 0;
     o.W1 = o.beta + (int64_t)S * S * NR * NB;
@@ -163,8 +169,8 @@ ThetaOff theta_offsets(int S, int H) {
     o.W2 = o.b1 + H;
     o.b2 = o.W2 + (int64_t)H * H;
     o.w3 = o.b2 + H;
-    o.b3 = o.w3 + H;
-    o.sigma = o.b3 + 1;
+    o.b3 = o.w3 + (int64_t)H * E;
+    o.sigma = o.b3 + E;
     o.mu = o.sigma + S;
     o.total = o.mu + S;
     return o;
@@ -177,7 +183,7 @@ __device__ __forceinline__ void put_split(__nv_bfloat16 *dst, int K, int r, int 
     dst[(size_t)r * 2 * K + K + k] = __float2bfloat16_rn(v - __bfloat162float(hi));
 }
 
-__global__ void k_repack(const float *__restrict__ th, ThetaOff o, int S, int H, float beta_scale, gm_model m) {
+__global__ void k_repack(const float *__restrict__ th, ThetaOff o, int S, int H, int E, float beta_scale, gm_model m) {
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t nbeta = (int64_t)S * S * NR * NB;
@@ -204,13 +210,26 @@ __global__ void k_repack(const float *__restrict__ th, ThetaOff o, int S, int H,
     for (int64_t q = tid; q < H; q += stride) {
         m.b1[q] = th[o.b1 + q];
         m.b2[q] = th[o.b2 + q];
-        m.w3[q] = th[o.w3 + q];
+        float sw = 0.0f;
+        for (int e = 0; e < E; ++e) {
+            const float w = th[o.w3 + q * E + e];
+            m.w3e[(int64_t)e * H + q] = w;
+            sw += w;
+        }
+        m.w3[q] = sw / (float)E;
     }
     for (int64_t q = tid; q < S; q += stride) {
         m.sigma[q] = th[o.sigma + q];
         m.mu[q] = th[o.mu + q];
     }
-    if (tid == 0) m.b3[0] = th[o.b3];
+    if (tid == 0) {
+        float sb = 0.0f;
+        for (int e = 0; e < E; ++e) {
+            m.b3e[e] = th[o.b3 + e];
+            sb += th[o.b3 + e];
+        }
+        m.b3[0] = sb / (float)E;
+    }
 }
 
 int round_up(int x, int m) { return (x + m - 1) / m * m; }
@@ -220,9 +239,12 @@ struct EfWs {
     unsigned long long *red_acc;   // fixed-point structure sums (cleared by the position split)
     int n_red_acc;
     float4 *pos_hi, *pos_lo;   // hi/lo FP32 split of the positions (pair displacements)
+    // shallow ensembles (E > 1): per-head partial sums, head-energy accumulators, per-head forces
+    float *nn_ens, *Fk;
+    unsigned long long *ens_acc;
 };
 
-EfWs carve_ef(Carve &c, int B, int N, int H) {
+EfWs carve_ef(Carve &c, int B, int N, int H, int E = 1) {
     EfWs w;
     const int Mp = round_up(N, TILE_M);
     const size_t n1 = N > 0 ? (size_t)N : 1, m1 = Mp > 0 ? (size_t)Mp : 1;
@@ -240,12 +262,19 @@ EfWs carve_ef(Carve &c, int B, int N, int H) {
     w.vir_atom = c.take<float>(n1 * 9);
     w.red_acc = c.take<unsigned long long>(reduce_acc_words(B));
     w.n_red_acc = (int)reduce_acc_words(B);
+    w.nn_ens = w.Fk = nullptr;
+    w.ens_acc = nullptr;
+    if (E > 1) {
+        w.nn_ens = c.take<float>(m1 * E * (H / 32));
+        w.Fk = c.take<float>((size_t)E * n1 * 3);
+        w.ens_acc = c.take<unsigned long long>(ens_acc_words(B, E));
+    }
     return w;
 }
 
-size_t ef_workspace_bytes(int B, int N, int H) {
+size_t ef_workspace_bytes(int B, int N, int H, int E) {
     Carve c(reinterpret_cast<void *>(256), ~size_t(0) >> 1);
-    carve_ef(c, B, N, H);
+    carve_ef(c, B, N, H, E);
     return c.off + 256;
 }
 
@@ -388,7 +417,7 @@ extern "C" {
 
 int64_t gm_param_count(const gm_model_desc *d) {
     if (!d || d->n_species < 1 || d->n_hidden < 1) return -1;
-    return theta_offsets(d->n_species, d->n_hidden).total;
+    return theta_offsets(d->n_species, d->n_hidden, d->n_ensemble > 1 ? d->n_ensemble : 1).total;
 }
 
 gm_status gm_model_create(const gm_model_desc *d, gm_model **out) {
@@ -401,24 +430,33 @@ gm_status gm_model_create(const gm_model_desc *d, gm_model **out) {
     if (d->activation != GM_ACT_TANH && d->activation != GM_ACT_SILU) return fail(GM_ERR_ARG, "bad activation");
     if (d->precision != GM_PREC_FP32 && d->precision != GM_PREC_MIXED) return fail(GM_ERR_ARG, "bad precision");
     if (!(d->r_cut > 0.0) || !(d->r_min >= 0.0) || !(d->r_min < d->r_cut)) return fail(GM_ERR_ARG, "bad radii");
+    if (d->basis != GM_BASIS_GAUSSIAN && d->basis != GM_BASIS_BESSEL) return fail(GM_ERR_ARG, "bad basis");
+    if (d->n_ensemble < 0 || d->n_ensemble > GM_MAX_ENSEMBLE) return fail(GM_ERR_UNSUPPORTED, "n_ensemble must be in 0..32");
     gm_model *m = new gm_model();
     m->d = *d;
     m->S = d->n_species;
     m->H = d->n_hidden;
-    m->n_param = theta_offsets(m->S, m->H).total;
+    m->E = d->n_ensemble > 1 ? d->n_ensemble : 1;
+    m->n_param = theta_offsets(m->S, m->H, m->E).total;
     m->rc.r_cut = (float)d->r_cut;
     m->rc.inv_r_cut = (float)(1.0 / d->r_cut);
     m->rc.pi_inv_r_cut = (float)(3.14159265358979323846 / d->r_cut);
     m->rc.gamma = (float)((double)(NB * NB) / (d->r_cut * d->r_cut));
     m->rc.gamma_l2 = (float)((double)(NB * NB) / (d->r_cut * d->r_cut) * 1.44269504088896340736);
     for (int k = 0; k < NB; ++k) m->rc.mu[k] = (float)(d->r_min + k * (d->r_cut - d->r_min) / (NB - 1));
+    m->rc.basis = d->basis;
+    for (int k = 0; k < NB; ++k) {
+        const double n1 = k + 1.0, n2 = k + 2.0;
+        m->rc.bes_a[k] = (float)(((k & 1) ? -1.0 : 1.0) * sqrt(2.0) * 3.14159265358979323846 / pow(d->r_cut, 1.5) *
+                                 n1 * n2 / sqrt(n1 * n1 + n2 * n2));
+    }
     m->pair_tpa = 0;
     m->split_mask = 12;
     m->pg_split_mask = 15;
     m->gemm_bn = 0;
     m->gemm_cps = 0;
     m->nl = NlTuning();
-    Layout L = model_layout(m->S, m->H);
+    Layout L = model_layout(m->S, m->H, m->E);
     m->buf_bytes = L.total;
     if (cudaMalloc(&m->buf, L.total) != cudaSuccess) {
         delete m;
@@ -440,6 +478,8 @@ gm_status gm_model_create(const gm_model_desc *d, gm_model **out) {
     m->b3 = reinterpret_cast<float *>(m->buf + L.b3);
     m->sigma = reinterpret_cast<float *>(m->buf + L.sigma);
     m->mu = reinterpret_cast<float *>(m->buf + L.mu);
+    m->w3e = reinterpret_cast<float *>(m->buf + L.w3e);
+    m->b3e = reinterpret_cast<float *>(m->buf + L.b3e);
     *out = m;
     return GM_OK;
 }
@@ -447,9 +487,9 @@ gm_status gm_model_create(const gm_model_desc *d, gm_model **out) {
 gm_status gm_model_set_params(gm_model *m, const float *theta, struct CUstream_st *stream) {
     if (!m || !theta) return fail(GM_ERR_ARG, "null argument");
     if (!aligned(theta, 4)) return fail(GM_ERR_ARG, "misaligned theta");
-    ThetaOff o = theta_offsets(m->S, m->H);
+    ThetaOff o = theta_offsets(m->S, m->H, m->E);
     const float scale = (float)(1.0 / sqrt((double)NB));
-    k_repack<<<296, 256, 0, stream>>>(theta, o, m->S, m->H, scale, *m);
+    k_repack<<<296, 256, 0, stream>>>(theta, o, m->S, m->H, m->E, scale, *m);
     note_launches(1);
     return launch_status();
 }
@@ -520,7 +560,7 @@ gm_status gm_workspace_size(const gm_model *m, int32_t n_structures, int32_t n_a
     if (!m || !bytes || n_structures < 1 || n_atoms < 0 || nl_capacity < 0) return fail(GM_ERR_ARG, "bad argument");
     switch (op) {
     case GM_OP_NEIGHBORS: *bytes = nl_workspace_bytes(n_structures, n_atoms, nl_capacity); return GM_OK;
-    case GM_OP_ENERGY_FORCES: *bytes = ef_workspace_bytes(n_structures, n_atoms, m->H); return GM_OK;
+    case GM_OP_ENERGY_FORCES: *bytes = ef_workspace_bytes(n_structures, n_atoms, m->H, m->E); return GM_OK;
     case GM_OP_PARAM_GRAD: *bytes = pg_workspace_bytes(n_atoms, m->H, m->S); return GM_OK;
     default: return fail(GM_ERR_ARG, "unknown op");
     }
@@ -571,16 +611,25 @@ static gm_status forward_to_features(const gm_model *m, const gm_system *sys, co
 
 // The four network GEMMs: features -> energies (partial sums) and dE/dG.  energy (mixed
 // path only): the structure energies are summed inside the B1 GEMM and written there.
+//   head:      output-layer weights whose gradient is taken (null: the model's w3, which for
+//              a shallow ensemble is the heads' mean)
+//   ens:       also write every ensemble head's partial sums (w.nn_ens) in the L2 epilogue
+//   from_l2:   skip L1 (its outputs A1, D1 are still in the workspace from an earlier pass)
 static gm_status network_fwd_bwd(const gm_model *m, const gm_system *sys, EfWs &w, int Mp, int32_t *status,
-                                 cudaStream_t st, double *energy = nullptr) {
+                                 cudaStream_t st, double *energy = nullptr, const float *head = nullptr,
+                                 bool ens = false, bool from_l2 = false) {
     const int H = m->H;
+    const int l2 = ens ? EPI_L2E : EPI_L2;
     EpiArgs e{};
     e.n_atoms = sys->n_atoms;
     e.n_species = m->S;
     e.species = sys->species;
-    e.w3 = m->w3;
+    e.w3 = head ? head : m->w3;
     e.sigma = m->sigma;
     e.nn_part = w.nn_part;
+    e.n_ens = ens ? m->E : 1;
+    e.w3e = m->w3e;
+    e.nn_ens = w.nn_ens;
     if (m->d.precision == GM_PREC_MIXED) {
         typedef __nv_bfloat16 bf;
         bf *G = reinterpret_cast<bf *>(w.G), *A1 = reinterpret_cast<bf *>(w.A1);
@@ -588,11 +637,11 @@ static gm_status network_fwd_bwd(const gm_model *m, const gm_system *sys, EfWs &
         const int sp = m->split_mask;
         bf *dZ2 = reinterpret_cast<bf *>(w.dZ2), *dZ1 = reinterpret_cast<bf *>(w.dZ1);
         gm_status s;
-        e.bias = m->b1;
-        e.out0 = A1;
-        e.out1 = D1;
-        e.lo_out = (sp & 2) != 0;   // lo halves only where the consuming GEMM runs split
-        {
+        if (!from_l2) {
+            e.bias = m->b1;
+            e.out0 = A1;
+            e.out1 = D1;
+            e.lo_out = (sp & 2) != 0;   // lo halves only where the consuming GEMM runs split
             StageScope sc(ST_GEMM_L1, st);
             if ((s = gemm_bf16(EPI_L1, m->d.activation, G, m->W1t_h, Mp, H, NFP, (sp & 1) != 0, e, status, st, m->gemm_bn, m->gemm_cps)) != GM_OK)
                 return fail(s, "tcgen05 GEMM L1 failed");
@@ -603,7 +652,7 @@ static gm_status network_fwd_bwd(const gm_model *m, const gm_system *sys, EfWs &
         e.lo_out = (sp & 4) != 0;
         {
             StageScope sc(ST_GEMM_L2, st);
-            if ((s = gemm_bf16(EPI_L2, m->d.activation, A1, m->W2t_h, Mp, H, H, (sp & 2) != 0, e, status, st, m->gemm_bn, m->gemm_cps)) != GM_OK)
+            if ((s = gemm_bf16(l2, m->d.activation, A1, m->W2t_h, Mp, H, H, (sp & 2) != 0, e, status, st, m->gemm_bn, m->gemm_cps)) != GM_OK)
                 return fail(s, "tcgen05 GEMM L2 failed");
         }
         e.out0 = dZ1;
@@ -631,10 +680,10 @@ static gm_status network_fwd_bwd(const gm_model *m, const gm_system *sys, EfWs &
         }
         return GM_OK;
     }
-    e.bias = m->b1;
-    e.out0 = w.A1;
-    e.out1 = w.D1;
-    {
+    if (!from_l2) {
+        e.bias = m->b1;
+        e.out0 = w.A1;
+        e.out1 = w.D1;
         StageScope sc(ST_GEMM_L1, st);
         gemm_f32(EPI_L1, m->d.activation, w.G, m->W1t, Mp, H, NFP, e, st);
     }
@@ -643,7 +692,7 @@ static gm_status network_fwd_bwd(const gm_model *m, const gm_system *sys, EfWs &
     e.out1 = nullptr;
     {
         StageScope sc(ST_GEMM_L2, st);
-        gemm_f32(EPI_L2, m->d.activation, w.A1, m->W2t, Mp, H, H, e, st);
+        gemm_f32(l2, m->d.activation, w.A1, m->W2t, Mp, H, H, e, st);
     }
     e.out0 = w.dZ1;
     e.aux = w.D1;
@@ -659,23 +708,20 @@ static gm_status network_fwd_bwd(const gm_model *m, const gm_system *sys, EfWs &
     return GM_OK;
 }
 
-gm_status gm_energy_forces(const gm_model *m, const gm_system *sys, const gm_nlist *nl, double *energy, float *forces,
-                           double *virial, void *ws, size_t ws_bytes, int32_t *status, struct CUstream_st *stream) {
-    gm_status s = check_system(m, sys);
-    if (s != GM_OK) return s;
-    if ((s = check_nlist(sys, nl, true)) != GM_OK) return s;
-    if (!energy || !status || (sys->n_atoms > 0 && !forces)) return fail(GM_ERR_ARG, "null output");
+// Energies, forces and virials of the model (the mean head for a shallow ensemble); with ens,
+// the L2 epilogue also leaves every head's partial sums in w.nn_ens.
+static gm_status energy_forces_pipeline(const gm_model *m, const gm_system *sys, const gm_nlist *nl, double *energy,
+                                        float *forces, double *virial, EfWs &w, bool ens, int32_t *status,
+                                        cudaStream_t st) {
     const int N = sys->n_atoms, B = sys->n_structures, H = m->H;
-    Carve c(ws, ws_bytes);
-    EfWs w = carve_ef(c, B, N, H);
-    if (!c.ok) return fail(GM_ERR_WORKSPACE, "workspace too small");
-    cudaStream_t st = stream;
     const int Mp = round_up(N, TILE_M);
+    gm_status s;
     // without the virial, the mixed path sums the energies inside its B1 GEMM
     const bool fused_energy = N > 0 && virial == nullptr && m->d.precision == GM_PREC_MIXED;
     if (N > 0) {
         if ((s = forward_to_features(m, sys, nl, w, nullptr, nullptr, forces, status, st)) != GM_OK) return s;
-        if ((s = network_fwd_bwd(m, sys, w, Mp, status, st, fused_energy ? energy : nullptr)) != GM_OK) return s;
+        if ((s = network_fwd_bwd(m, sys, w, Mp, status, st, fused_energy ? energy : nullptr, nullptr, ens)) != GM_OK)
+            return s;
         {
             StageScope sc(ST_CONTRACT_BWD, st);
             launch_contract_bwd(w.psi, w.dG, N, w.dpsi, st);
@@ -688,6 +734,71 @@ gm_status gm_energy_forces(const gm_model *m, const gm_system *sys, const gm_nli
         StageScope sc(ST_REDUCE, st);
         launch_struct_reduce(B, N, sys->atom_ptr, sys->species, m->S, m->sigma, m->mu, m->b3, w.nn_part, H / 32,
                              virial ? w.vir_atom : nullptr, w.red_acc, energy, virial, st);
+    }
+    return launch_status();
+}
+
+gm_status gm_energy_forces(const gm_model *m, const gm_system *sys, const gm_nlist *nl, double *energy, float *forces,
+                           double *virial, void *ws, size_t ws_bytes, int32_t *status, struct CUstream_st *stream) {
+    gm_status s = check_system(m, sys);
+    if (s != GM_OK) return s;
+    if ((s = check_nlist(sys, nl, true)) != GM_OK) return s;
+    if (!energy || !status || (sys->n_atoms > 0 && !forces)) return fail(GM_ERR_ARG, "null output");
+    Carve c(ws, ws_bytes);
+    EfWs w = carve_ef(c, sys->n_structures, sys->n_atoms, m->H);
+    if (!c.ok) return fail(GM_ERR_WORKSPACE, "workspace too small");
+    return energy_forces_pipeline(m, sys, nl, energy, forces, virial, w, false, status, stream);
+}
+
+gm_status gm_energy_forces_ensemble(const gm_model *m, const gm_system *sys, const gm_nlist *nl, double *energy,
+                                    float *forces, double *virial, double *energy_heads, double *energy_std,
+                                    int32_t mode, float *forces_heads, float *force_std, void *ws, size_t ws_bytes,
+                                    int32_t *status, struct CUstream_st *stream) {
+    gm_status s = check_system(m, sys);
+    if (s != GM_OK) return s;
+    if ((s = check_nlist(sys, nl, true)) != GM_OK) return s;
+    if (!energy || !status || (sys->n_atoms > 0 && !forces)) return fail(GM_ERR_ARG, "null output");
+    if (mode != GM_ENS_MEAN_GRADIENT && mode != GM_ENS_JACOBIAN) return fail(GM_ERR_ARG, "bad ensemble force mode");
+    if (mode == GM_ENS_MEAN_GRADIENT && (forces_heads || force_std))
+        return fail(GM_ERR_ARG, "per-head forces and their spread need GM_ENS_JACOBIAN");
+    if (!aligned(energy_heads, 8) || !aligned(energy_std, 8) || !aligned(forces_heads, 4) || !aligned(force_std, 4))
+        return fail(GM_ERR_ARG, "misaligned ensemble output");
+    const int N = sys->n_atoms, B = sys->n_structures, H = m->H, E = m->E;
+    if (E < 2) return fail(GM_ERR_ARG, "the model has a single output head (n_ensemble <= 1)");
+    Carve c(ws, ws_bytes);
+    EfWs w = carve_ef(c, B, N, H, E);
+    if (!c.ok) return fail(GM_ERR_WORKSPACE, "workspace too small");
+    cudaStream_t st = stream;
+    if (cudaMemsetAsync(w.ens_acc, 0, sizeof(unsigned long long) * ens_acc_words(B, E), st) != cudaSuccess)
+        return fail(GM_ERR_CUDA, "memset of the ensemble accumulators failed");
+    // the mean head: energies, forces (gradient of the mean energy) and virials, with every
+    // head's partial sums written in the L2 epilogue
+    if ((s = energy_forces_pipeline(m, sys, nl, energy, forces, virial, w, true, status, st)) != GM_OK) return s;
+    {
+        StageScope sc(ST_REDUCE, st);
+        launch_ens_energy(B, N, E, sys->atom_ptr, sys->species, m->S, m->sigma, m->mu, m->b3e, w.nn_ens, H / 32,
+                          w.ens_acc, energy_heads, energy_std, st);
+    }
+    if (mode == GM_ENS_JACOBIAN && N > 0) {
+        // every head's forces: the backward pass from L2 with that head's weights (the features,
+        // the first layer and the moments of the mean pass are reused)
+        const int Mp = round_up(N, TILE_M);
+        float *Fk = forces_heads ? forces_heads : w.Fk;
+        PairArgs a = pair_args(m, sys, nl, w.pos_hi, w.pos_lo, status);
+        for (int k = 0; k < E; ++k) {
+            float *Fh = Fk + (size_t)k * N * 3;
+            if (cudaMemsetAsync(Fh, 0, sizeof(float) * 3 * N, st) != cudaSuccess)
+                return fail(GM_ERR_CUDA, "memset of the head forces failed");
+            if ((s = network_fwd_bwd(m, sys, w, Mp, status, st, nullptr, m->w3e + (size_t)k * H, false, true)) != GM_OK)
+                return s;
+            {
+                StageScope sc(ST_CONTRACT_BWD, st);
+                launch_contract_bwd(w.psi, w.dG, N, w.dpsi, st);
+            }
+            StageScope sc(ST_FORCES, st);
+            launch_forces(a, choose_tpa(m, N), w.dpsi, Fh, nullptr, st);
+        }
+        if (force_std) launch_ens_force_std(N, E, Fk, force_std, st);
     }
     return launch_status();
 }
@@ -713,6 +824,8 @@ gm_status gm_param_grad(const gm_model *m, const gm_system *sys, const gm_nlist 
     if (s != GM_OK) return s;
     if ((s = check_nlist(sys, nl, true)) != GM_OK) return s;
     if (!dL_dE || !grad_theta || !status || (sys->n_atoms > 0 && !dL_dF)) return fail(GM_ERR_ARG, "null argument");
+    if (m->E > 1)
+        return fail(GM_ERR_UNSUPPORTED, "the parameter gradient of a shallow-ensemble model is not implemented");
     const int N = sys->n_atoms, B = sys->n_structures, H = m->H, S = m->S;
     Carve c(ws, ws_bytes);
     PgWs w = carve_pg(c, N, H, S);

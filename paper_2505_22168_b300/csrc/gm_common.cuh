@@ -143,16 +143,58 @@ __device__ __forceinline__ float act_fwd2(float z, float &d1, float &d2) {
 // gamma_l2 = gamma log2(e) (rounded once from FP64), so Phi_k = 2^(-gamma_l2 t^2): the
 // result carries the same argument-rounding error as exp(-gamma t^2), which dominates
 // either way for the wide arguments (up to ~60) of the outer Gaussians.
+enum { BASIS_GAUSSIAN = 0, BASIS_BESSEL = 1 };
 struct RadialConst {
     float r_cut, inv_r_cut, pi_inv_r_cut, gamma, gamma_l2;
     float mu[NB];
+    int basis;
+    float bes_a[NB];   // Bessel-like basis: a_k, rounded once from FP64
 };
+
+// Bessel-like basis of Kocer et al.: f_k = a_k [j0((k+1) t) + j0((k+2) t)], t = pi r / r_cut,
+// j0(x) = sin(x)/x, times the cosine cutoff.  One accurate sin/cos of t (sincospif), then
+// sin(q t) and cos(q t) for q = 2..NB+1 by the Chebyshev recurrence
+// sin((q+1) t) = 2 cos(t) sin(q t) - sin((q-1) t) (same for cos); d/dr j0(q t) = (cos(q t) - j0(q t)) / r.
+template <bool DERIV>
+__device__ __forceinline__ void bessel_basis(const RadialConst &rc, float r, float (&B)[NB], float (&dB)[NB]) {
+    float s1, c1;
+    sincospif(r * rc.inv_r_cut, &s1, &c1);
+    const bool inside = r < rc.r_cut;
+    const float fc = inside ? 0.5f * (c1 + 1.0f) : 0.0f;
+    const float dfc = inside ? -0.5f * rc.pi_inv_r_cut * s1 : 0.0f;
+    const float inv_t = 1.0f / (r * rc.pi_inv_r_cut);
+    const float inv_r = rc.pi_inv_r_cut * inv_t;
+    float j[NB + 1], dj[NB + 1];
+    float sp = 0.0f, cp = 1.0f, sq = s1, cq = c1;
+#pragma unroll
+    for (int q = 1; q <= NB + 1; ++q) {
+        j[q - 1] = sq * inv_t * (1.0f / (float)q);
+        if (DERIV) dj[q - 1] = (cq - j[q - 1]) * inv_r;
+        const float sn = fmaf(2.0f * c1, sq, -sp), cn = fmaf(2.0f * c1, cq, -cp);
+        sp = sq;
+        cp = cq;
+        sq = sn;
+        cq = cn;
+    }
+#pragma unroll
+    for (int k = 0; k < NB; ++k) {
+        const float ph = rc.bes_a[k] * (j[k] + j[k + 1]);
+        B[k] = fc * ph;
+        if (DERIV) dB[k] = fmaf(dfc, ph, fc * rc.bes_a[k] * (dj[k] + dj[k + 1]));
+    }
+}
 
 // f_c Phi_k (B) and optionally its r-derivative (dB) for the 7 Gaussians.  The cutoff's
 // cosine and sine take the hardware approximation on [0, pi] (absolute error below 4e-7,
 // against f_c and Phi of order one).
-template <bool DERIV>
+// BAS is the model's basis (a template parameter of the pair kernels, so each kernel holds
+// the code of one basis only and keeps its register budget)
+template <bool DERIV, int BAS>
 __device__ __forceinline__ void radial_basis(const RadialConst &rc, float r, float (&B)[NB], float (&dB)[NB]) {
+    if (BAS == BASIS_BESSEL) {
+        bessel_basis<DERIV>(rc, r, B, dB);
+        return;
+    }
     float sp, cp;
     __sincosf(r * rc.pi_inv_r_cut, &sp, &cp);
     const bool inside = r < rc.r_cut;

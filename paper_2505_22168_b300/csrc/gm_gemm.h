@@ -8,13 +8,16 @@
 //                         dZ2 = sigma_Z w3 phi'(Z2 + b2)          (dE_i/dZ2)
 //   B1  dA1 = dZ2 W2^T:   dZ1 = dA1 * D1
 //   B0  dG = dZ1 W1^T     (stored FP32)
+// A shallow ensemble (E output heads, section "Uncertainty Quantification") runs L2 as
+// EPI_L2E: w3 is the heads' mean (its gradient is the mean force) and the epilogue also
+// writes each head's partial sums of a2 . w3e[k] per 32 columns.
 #pragma once
 
 #include "gm_internal.h"
 
 namespace gm {
 
-enum { EPI_L1 = 0, EPI_L2 = 1, EPI_B1 = 2, EPI_STORE = 3 };
+enum { EPI_L1 = 0, EPI_L2 = 1, EPI_B1 = 2, EPI_STORE = 3, EPI_L2E = 4 };
 
 struct EpiArgs {
     const float *bias;       // [N] (L1, L2)
@@ -26,6 +29,9 @@ struct EpiArgs {
     void *out1;              // D1 (L1)
     const void *aux;         // D1 (B1)
     float *nn_part;          // [M][N/32] (L2): partial output-layer sums per 32 columns
+    int n_ens;               // EPI_L2E: ensemble heads E
+    const float *w3e;        // EPI_L2E: [E][N] head weights
+    float *nn_ens;           // EPI_L2E: [M][E][N/32] partial sums per head
     int lo_out;              // BF16 outputs: also write the lo half (the consumer runs split)
     // Structure energies fused into the tcgen05 B1 GEMM (energy non-null; no virial): while
     // the first N tile of each row block runs its main loop, its four idle warps add E_i of

@@ -85,9 +85,9 @@ __global__ void __launch_bounds__(256) k_gemm_f32(const float *__restrict__ A, c
             *reinterpret_cast<float4 *>(o0) = make_float4(a[0], a[1], a[2], a[3]);
             float *o1 = static_cast<float *>(e.out1) + (size_t)m * N + nb;
             *reinterpret_cast<float4 *>(o1) = make_float4(d[0], d[1], d[2], d[3]);
-        } else {  // EPI_L2
+        } else {  // EPI_L2, EPI_L2E
             const float sg = m < e.n_atoms ? e.sigma[min(max(e.species[m], 0), e.n_species - 1)] : 0.0f;
-            float part = 0.0f, dz[4];
+            float part = 0.0f, dz[4], av[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 float d;
@@ -95,11 +95,23 @@ __global__ void __launch_bounds__(256) k_gemm_f32(const float *__restrict__ A, c
                 const float w = e.w3[nb + j];
                 part = fmaf(a, w, part);
                 dz[j] = sg * w * d;
+                av[j] = a;
             }
             *reinterpret_cast<float4 *>(o0) = make_float4(dz[0], dz[1], dz[2], dz[3]);
 #pragma unroll
             for (int off = 4; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
             if ((tx & 7) == 0) e.nn_part[(size_t)m * (N / 32) + (n0 + tx * 4) / 32] = part;
+            if (EPI == EPI_L2E) {
+                for (int k = 0; k < e.n_ens; ++k) {
+                    const float *wk = e.w3e + (size_t)k * N + nb;
+                    float p = 0.0f;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) p = fmaf(av[j], wk[j], p);
+#pragma unroll
+                    for (int off = 4; off > 0; off >>= 1) p += __shfl_xor_sync(0xffffffffu, p, off);
+                    if ((tx & 7) == 0) e.nn_ens[((size_t)m * e.n_ens + k) * (N / 32) + (n0 + tx * 4) / 32] = p;
+                }
+            }
         }
     }
 }
@@ -119,6 +131,7 @@ void gemm_f32(int epi, int act, const float *A, const float *B, int M, int N, in
     switch (epi) {
     case EPI_L1: launch_act<EPI_L1>(act, g, A, B, M, N, K, e, st); break;
     case EPI_L2: launch_act<EPI_L2>(act, g, A, B, M, N, K, e, st); break;
+    case EPI_L2E: launch_act<EPI_L2E>(act, g, A, B, M, N, K, e, st); break;
     case EPI_B1: launch_pdl(k_gemm_f32<EPI_B1, 0>, g, dim3(256), 0, st, A, B, M, N, K, e); break;
     default: launch_pdl(k_gemm_f32<EPI_STORE, 0>, g, dim3(256), 0, st, A, B, M, N, K, e); break;
     }

@@ -264,8 +264,9 @@ __device__ __forceinline__ void epilogue32(const EpiArgs &e, int row0, int n, in
             for (int t = 0; t < 4; ++t) y[4 * q + t] = act_fast<ACT>(v[4 * q + t] + __ldg(e.bias + n + 4 * q + t), d[t]);
             sg.d[lane][q] = make_float4(d[0], d[1], d[2], d[3]);
         }
-    } else {  // EPI_L2
+    } else {  // EPI_L2, EPI_L2E
         const float sg_m = m < e.n_atoms ? e.sigma[min(max(e.species[m], 0), e.n_species - 1)] : 0.0f;
+        float av[32];
 #pragma unroll
         for (int t = 0; t < 32; ++t) {
             float d;
@@ -274,6 +275,16 @@ __device__ __forceinline__ void epilogue32(const EpiArgs &e, int row0, int n, in
             const float w = __ldg(e.w3 + c);
             part = fmaf(a, w, part);
             y[t] = sg_m * w * d;
+            av[t] = a;
+        }
+        if (EPI == EPI_L2E) {
+            for (int k = 0; k < e.n_ens; ++k) {
+                const float *wk = e.w3e + (size_t)k * N + n;
+                float p = 0.0f;
+#pragma unroll
+                for (int t = 0; t < 32; ++t) p = fmaf(av[t], __ldg(wk + t), p);
+                e.nn_ens[((size_t)m * e.n_ens + k) * (N / 32) + n / 32] = p;
+            }
         }
     }
 #pragma unroll
@@ -479,7 +490,7 @@ __global__ void __launch_bounds__(256, CPS)
             float v[32], part = 0.0f;
             tmem_ld_32cols(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(c * 32), v);
             epilogue32<EPI, ACT>(e, row0, n0 + c * 32, N, v, part, sg, lane);
-            if (EPI == EPI_L2) e.nn_part[(size_t)m * (N / 32) + (n0 + c * 32) / 32] = part;
+            if (EPI == EPI_L2 || EPI == EPI_L2E) e.nn_part[(size_t)m * (N / 32) + (n0 + c * 32) / 32] = part;
         }
     } else if (threadIdx.x == 0) {
         set_status(status, GM_ERR_TIMEOUT);

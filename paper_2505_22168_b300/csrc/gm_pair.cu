@@ -181,7 +181,7 @@ void launch_split_pos(int N, const double *pos, const int32_t *species, float4 *
 // blocks at up to 170 registers, so that three blocks (12 warps) share an SM and a 1536-atom
 // system runs in one wave; with fewer lanes 256-thread blocks and two pairs per iteration.
 template <int TPA> __host__ __device__ constexpr int moments_threads() { return TPA >= 8 ? 128 : 256; }
-template <int TPA>
+template <int TPA, int BAS>
 __global__ void __launch_bounds__(moments_threads<TPA>(), TPA >= 8 ? 3 : 1) k_moments(PairArgs a,
                                                                                    float *__restrict__ psi) {
     extern __shared__ __align__(16) float sbeta[];
@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(moments_threads<TPA>(), TPA >= 8 ? 3 : 1) k_mo
                 const float r = sqrtf(fx * fx + fy * fy + fz * fz);
                 const float rinv = 1.0f / r;
                 float B[NB], dB[NB];
-                radial_basis<false>(a.rc, r, B, dB);
+                radial_basis<false, BAS>(a.rc, r, B, dB);
                 const float w = cur[u].ok ? 1.0f : 0.0f;
                 float Rp[NR];
                 radial_combine<false>(brow + zj * (NR * BETA_ROW), B, dB, R[u], Rp);
@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(moments_threads<TPA>(), TPA >= 8 ? 3 : 1) k_mo
 template <int TPA> __host__ __device__ constexpr bool forces_gsmem() { return TPA >= 8; }
 template <int TPA> __host__ __device__ constexpr int forces_threads() { return TPA >= 8 ? 128 : 256; }
 constexpr int FG_ROW = 168;
-template <int TPA>
+template <int TPA, int BAS>
 __global__ void __launch_bounds__(forces_threads<TPA>(), TPA >= 8 ? 4 : 1)
     k_forces(PairArgs a, const float *__restrict__ dpsi, float *__restrict__ F, float *__restrict__ vir_atom) {
     constexpr bool GS = forces_gsmem<TPA>();
@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(forces_threads<TPA>(), TPA >= 8 ? 4 : 1)
             const float rinv = 1.0f / r;
             const float ux = fx * rinv, uy = fy * rinv, uz = fz * rinv;
             float B[NB], dB[NB];
-            radial_basis<true>(a.rc, r, B, dB);
+            radial_basis<true, BAS>(a.rc, r, B, dB);
             float R[NR], Rp[NR];
             radial_combine<true>(brow + clamp_species(__float_as_int(cur.ph.w), a.S, a.status) * (NR * BETA_ROW), B,
                                  dB, R, Rp);
@@ -410,7 +410,7 @@ __global__ void __launch_bounds__(forces_threads<TPA>(), TPA >= 8 ? 4 : 1)
 // Tangent moments for the parameter gradient: dPsi_i/dt when every position moves along
 // v (= dL/dF), i.e. d_ij changes by v_j - v_i.  Per pair and component c of rank L:
 //   d/dt [R_s m_c] = R'_s w m_c + R_s (D_c - L_c m_c w) / r,  w = u . dd,  D_c = dd . dm_c/du.
-template <int TPA>
+template <int TPA, int BAS>
 __global__ void __launch_bounds__(256) k_moments_tangent(PairArgs a, const float *__restrict__ vel,
                                                          float *__restrict__ psid) {
     extern __shared__ __align__(16) float sbeta[];
@@ -442,7 +442,7 @@ __global__ void __launch_bounds__(256) k_moments_tangent(PairArgs a, const float
             const float ddx = cur.vx - vix, ddy = cur.vy - viy, ddz = cur.vz - viz;
             const float w = ux * ddx + uy * ddy + uz * ddz;
             float B[NB], dB[NB];
-            radial_basis<true>(a.rc, r, B, dB);
+            radial_basis<true, BAS>(a.rc, r, B, dB);
             float R[NR], Rp[NR];
             radial_combine<true>(brow + clamp_species(__float_as_int(cur.ph.w), a.S, a.status) * (NR * BETA_ROW), B,
                                  dB, R, Rp);
@@ -486,6 +486,7 @@ __global__ void __launch_bounds__(256) k_moments_tangent(PairArgs a, const float
 // lanes add up the 32 slices (lane l takes entries l, l + 32, ...) into the block's
 // [S][S][NR][NB] accumulator (one atomic per entry, distinct entries per lane) and clear
 // them.  Block partials are summed in a fixed order by k_pg_beta_reduce.
+template <int BAS>
 __global__ void __launch_bounds__(256) k_pg_beta(PairArgs a, const float *__restrict__ vel,
                                                  const float *__restrict__ psib, const float *__restrict__ psidb,
                                                  float *__restrict__ part) {
@@ -531,7 +532,7 @@ __global__ void __launch_bounds__(256) k_pg_beta(PairArgs a, const float *__rest
             const float ddx = cur.vx - vix, ddy = cur.vy - viy, ddz = cur.vz - viz;
             const float w = ux * ddx + uy * ddy + uz * ddz;
             float B[NB], dB[NB];
-            radial_basis<true>(a.rc, r, B, dB);
+            radial_basis<true, BAS>(a.rc, r, B, dB);
             float m[NC], ang[NC];
             monomials(ux, uy, uz, m);
 #pragma unroll
@@ -584,7 +585,7 @@ static void allow_beta_smem(Kern kernel, size_t extra = 0) {
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(beta_smem_bytes(MAX_S) + extra));
 }
 
-template <int TPA>
+template <int TPA, int BAS>
 static void launch_moments_t(const PairArgs &a, float *psi, cudaStream_t st) {
     const int threads = moments_threads<TPA>();
     const long long total = (long long)a.N * TPA;
@@ -592,16 +593,16 @@ static void launch_moments_t(const PairArgs &a, float *psi, cudaStream_t st) {
     const size_t smem = beta_smem_bytes(a.S);
     static bool attr = false;
     if (!attr) {
-        allow_beta_smem(k_moments<TPA>);
+        allow_beta_smem(k_moments<TPA, BAS>);
         attr = true;
     }
     if (blocks > 0) {
-        launch_pdl(k_moments<TPA>, dim3(blocks), dim3(threads), smem, st, a, psi);
+        launch_pdl(k_moments<TPA, BAS>, dim3(blocks), dim3(threads), smem, st, a, psi);
         note_launches(1);
     }
 }
 
-template <int TPA>
+template <int TPA, int BAS>
 static void launch_forces_t(const PairArgs &a, const float *dpsi, float *F, float *vir, cudaStream_t st) {
     const int threads = forces_threads<TPA>();
     const long long total = (long long)a.N * TPA;
@@ -610,42 +611,54 @@ static void launch_forces_t(const PairArgs &a, const float *dpsi, float *F, floa
                         (forces_gsmem<TPA>() ? sizeof(float) * (threads / TPA) * FG_ROW : 0);
     static bool attr = false;
     if (!attr) {
-        allow_beta_smem(k_forces<TPA>, forces_gsmem<TPA>() ? sizeof(float) * (threads / TPA) * FG_ROW : 0);
+        allow_beta_smem(k_forces<TPA, BAS>, forces_gsmem<TPA>() ? sizeof(float) * (threads / TPA) * FG_ROW : 0);
         attr = true;
     }
     if (blocks > 0) {
-        launch_pdl(k_forces<TPA>, dim3(blocks), dim3(threads), smem, st, a, dpsi, F, vir);
+        launch_pdl(k_forces<TPA, BAS>, dim3(blocks), dim3(threads), smem, st, a, dpsi, F, vir);
         note_launches(1);
     }
 }
 
-void launch_moments(const PairArgs &a, int tpa, float *psi, cudaStream_t st) {
+template <int BAS>
+static void launch_moments_b(const PairArgs &a, int tpa, float *psi, cudaStream_t st) {
     switch (tpa) {
-    case 1: launch_moments_t<1>(a, psi, st); break;
-    case 2: launch_moments_t<2>(a, psi, st); break;
-    case 4: launch_moments_t<4>(a, psi, st); break;
-    case 8: launch_moments_t<8>(a, psi, st); break;
-    case 16: launch_moments_t<16>(a, psi, st); break;
-    default: launch_moments_t<32>(a, psi, st); break;
+    case 1: launch_moments_t<1, BAS>(a, psi, st); break;
+    case 2: launch_moments_t<2, BAS>(a, psi, st); break;
+    case 4: launch_moments_t<4, BAS>(a, psi, st); break;
+    case 8: launch_moments_t<8, BAS>(a, psi, st); break;
+    case 16: launch_moments_t<16, BAS>(a, psi, st); break;
+    default: launch_moments_t<32, BAS>(a, psi, st); break;
+    }
+}
+
+void launch_moments(const PairArgs &a, int tpa, float *psi, cudaStream_t st) {
+    if (a.rc.basis == BASIS_BESSEL) launch_moments_b<BASIS_BESSEL>(a, tpa, psi, st);
+    else launch_moments_b<BASIS_GAUSSIAN>(a, tpa, psi, st);
+}
+
+template <int BAS>
+static void launch_forces_b(const PairArgs &a, int tpa, const float *dpsi, float *F, float *vir, cudaStream_t st) {
+    switch (tpa) {
+    case 1: launch_forces_t<1, BAS>(a, dpsi, F, vir, st); break;
+    case 2: launch_forces_t<2, BAS>(a, dpsi, F, vir, st); break;
+    case 4: launch_forces_t<4, BAS>(a, dpsi, F, vir, st); break;
+    case 8: launch_forces_t<8, BAS>(a, dpsi, F, vir, st); break;
+    case 16: launch_forces_t<16, BAS>(a, dpsi, F, vir, st); break;
+    default: launch_forces_t<32, BAS>(a, dpsi, F, vir, st); break;
     }
 }
 
 void launch_forces(const PairArgs &a, int tpa, const float *dpsi, float *F, float *vir, cudaStream_t st) {
-    switch (tpa) {
-    case 1: launch_forces_t<1>(a, dpsi, F, vir, st); break;
-    case 2: launch_forces_t<2>(a, dpsi, F, vir, st); break;
-    case 4: launch_forces_t<4>(a, dpsi, F, vir, st); break;
-    case 8: launch_forces_t<8>(a, dpsi, F, vir, st); break;
-    case 16: launch_forces_t<16>(a, dpsi, F, vir, st); break;
-    default: launch_forces_t<32>(a, dpsi, F, vir, st); break;
-    }
+    if (a.rc.basis == BASIS_BESSEL) launch_forces_b<BASIS_BESSEL>(a, tpa, dpsi, F, vir, st);
+    else launch_forces_b<BASIS_GAUSSIAN>(a, tpa, dpsi, F, vir, st);
 }
 
 }  // namespace gm
 
 namespace gm {
 
-template <int TPA>
+template <int TPA, int BAS>
 static void launch_tangent_t(const PairArgs &a, const float *vel, float *psid, cudaStream_t st) {
     const int threads = 256;
     const long long total = (long long)a.N * TPA;
@@ -653,24 +666,30 @@ static void launch_tangent_t(const PairArgs &a, const float *vel, float *psid, c
     const size_t smem = beta_smem_bytes(a.S);
     static bool attr = false;
     if (!attr) {
-        allow_beta_smem(k_moments_tangent<TPA>);
+        allow_beta_smem(k_moments_tangent<TPA, BAS>);
         attr = true;
     }
     if (blocks > 0) {
-        launch_pdl(k_moments_tangent<TPA>, dim3(blocks), dim3(threads), smem, st, a, vel, psid);
+        launch_pdl(k_moments_tangent<TPA, BAS>, dim3(blocks), dim3(threads), smem, st, a, vel, psid);
         note_launches(1);
     }
 }
 
-void launch_moments_tangent(const PairArgs &a, int tpa, const float *vel, float *psid, cudaStream_t st) {
+template <int BAS>
+static void launch_tangent_b(const PairArgs &a, int tpa, const float *vel, float *psid, cudaStream_t st) {
     switch (tpa) {
-    case 1: launch_tangent_t<1>(a, vel, psid, st); break;
-    case 2: launch_tangent_t<2>(a, vel, psid, st); break;
-    case 4: launch_tangent_t<4>(a, vel, psid, st); break;
-    case 8: launch_tangent_t<8>(a, vel, psid, st); break;
-    case 16: launch_tangent_t<16>(a, vel, psid, st); break;
-    default: launch_tangent_t<32>(a, vel, psid, st); break;
+    case 1: launch_tangent_t<1, BAS>(a, vel, psid, st); break;
+    case 2: launch_tangent_t<2, BAS>(a, vel, psid, st); break;
+    case 4: launch_tangent_t<4, BAS>(a, vel, psid, st); break;
+    case 8: launch_tangent_t<8, BAS>(a, vel, psid, st); break;
+    case 16: launch_tangent_t<16, BAS>(a, vel, psid, st); break;
+    default: launch_tangent_t<32, BAS>(a, vel, psid, st); break;
     }
+}
+
+void launch_moments_tangent(const PairArgs &a, int tpa, const float *vel, float *psid, cudaStream_t st) {
+    if (a.rc.basis == BASIS_BESSEL) launch_tangent_b<BASIS_BESSEL>(a, tpa, vel, psid, st);
+    else launch_tangent_b<BASIS_GAUSSIAN>(a, tpa, vel, psid, st);
 }
 
 // warps per block of k_pg_beta: the per-lane slices take S x NR x NB x 32 floats per warp
@@ -692,8 +711,13 @@ void launch_pg_beta(const PairArgs &a, const float *vel, const float *psib, cons
     const int blocks = pg_beta_blocks(a.N, a.S);
     const size_t smem = sizeof(float) * ((size_t)a.S * a.S * NR * NB + (size_t)w * (2 * NPSI + a.S * NR * NB * 32));
     if (a.N > 0) {
-        cudaFuncSetAttribute(k_pg_beta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_pg_beta<<<blocks, 32 * w, smem, st>>>(a, vel, psib, psidb, part);
+        if (a.rc.basis == BASIS_BESSEL) {
+            cudaFuncSetAttribute(k_pg_beta<BASIS_BESSEL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_pg_beta<BASIS_BESSEL><<<blocks, 32 * w, smem, st>>>(a, vel, psib, psidb, part);
+        } else {
+            cudaFuncSetAttribute(k_pg_beta<BASIS_GAUSSIAN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_pg_beta<BASIS_GAUSSIAN><<<blocks, 32 * w, smem, st>>>(a, vel, psib, psidb, part);
+        }
         note_launches(1);
     }
 }

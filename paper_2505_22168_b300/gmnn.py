@@ -15,6 +15,7 @@ from . import _lib as L
 PARAM_ORDER = ("beta", "W1", "b1", "W2", "b2", "w3", "b3", "sigma", "mu")
 ACT = {"tanh": L.GM_ACT_TANH, "silu": L.GM_ACT_SILU}
 PREC = {"fp32": L.GM_PREC_FP32, "mixed": L.GM_PREC_MIXED}
+BASIS = {"gaussian": L.GM_BASIS_GAUSSIAN, "bessel": L.GM_BASIS_BESSEL}
 
 
 def pack_theta(params) -> np.ndarray:
@@ -22,12 +23,12 @@ def pack_theta(params) -> np.ndarray:
     return np.concatenate([np.asarray(params[k], np.float64).reshape(-1) for k in PARAM_ORDER]).astype(np.float32)
 
 
-def unpack_theta(theta, n_species, n_hidden, n_radial=5, n_basis=7):
+def unpack_theta(theta, n_species, n_hidden, n_radial=5, n_basis=7, n_ensemble=1):
     """Inverse of pack_theta: dict of named arrays (numpy)."""
     from synth.params import param_shapes  # shapes only
     th = np.asarray(theta)
     out, off = {}, 0
-    for k, shp in param_shapes(n_species, n_hidden, n_radial, n_basis).items():
+    for k, shp in param_shapes(n_species, n_hidden, n_radial, n_basis, n_ensemble=n_ensemble).items():
         n = int(np.prod(shp))
         out[k] = th[off:off + n].reshape(shp)
         off += n
@@ -93,9 +94,11 @@ class GMNN:
         self.device = torch.device(device)
         self.desc = dict(desc)
         self.precision = precision
+        self.n_ensemble = max(1, int(desc.get("n_ensemble", 1)))
         self.cdesc = L.GmModelDesc(int(desc["n_species"]), int(desc.get("n_basis", 7)), int(desc.get("n_radial", 5)),
                                    int(desc["n_hidden"]), ACT[desc.get("activation", "silu")], PREC[precision],
-                                   float(desc.get("r_min", 0.5)), float(desc["r_cut"]))
+                                   float(desc.get("r_min", 0.5)), float(desc["r_cut"]),
+                                   BASIS[desc.get("basis", "gaussian")], self.n_ensemble)
         self.n_param = L.gm_param_count(self.cdesc)
         with torch.cuda.device(self.device):
             self.handle = L.gm_model_create(self.cdesc)
@@ -202,6 +205,30 @@ class GMNN:
         L.gm_energy_forces(self.handle, sysd.c_struct(), nl.c_struct(), _ptr(E), _ptr(F), _ptr(W), ws, wsb,
                            _ptr(self.status), _stream())
         return E, F, W
+
+    def energy_forces_ensemble(self, sysd: DeviceSystem, nl: NeighborList, mode="mean", virial=False):
+        """Shallow ensemble (n_ensemble > 1): a dict with the mean energy "E" [B] and forces
+        "F" [N,3] (gradient of the mean energy), "E_heads" [B,E], "E_std" [B] and, in the
+        Jacobian mode, "F_heads" [E,N,3] and "F_std" [N]; "W" [B,3,3] with virial=True."""
+        E_ = self.n_ensemble
+        dev = self.device
+        B, N = sysd.n_structures, sysd.n_atoms
+        out = {"E": torch.empty(B, dtype=torch.float64, device=dev), "F": torch.empty(N, 3, dtype=torch.float32, device=dev),
+               "E_heads": torch.empty(B, E_, dtype=torch.float64, device=dev),
+               "E_std": torch.empty(B, dtype=torch.float64, device=dev),
+               "W": torch.empty(B, 3, 3, dtype=torch.float64, device=dev) if virial else None}
+        jac = mode == "jacobian"
+        if jac:
+            out["F_heads"] = torch.empty(E_, N, 3, dtype=torch.float32, device=dev)
+            out["F_std"] = torch.empty(N, dtype=torch.float32, device=dev)
+        ws, wsb = self.workspace(L.GM_OP_ENERGY_FORCES, sysd, nl.capacity)
+        self.clear_status()
+        L.gm_energy_forces_ensemble(self.handle, sysd.c_struct(), nl.c_struct(), _ptr(out["E"]), _ptr(out["F"]),
+                                    _ptr(out["W"]), _ptr(out["E_heads"]), _ptr(out["E_std"]),
+                                    L.GM_ENS_JACOBIAN if jac else L.GM_ENS_MEAN_GRADIENT,
+                                    _ptr(out.get("F_heads")), _ptr(out.get("F_std")), ws, wsb, _ptr(self.status),
+                                    _stream())
+        return out
 
     def step(self, sysd: DeviceSystem, nl: NeighborList, out):
         """One MD-style step on the current stream: clear the status word, rebuild the

@@ -39,9 +39,10 @@ def mean_neighbours(number_density, r_cut):
     return number_density * 4.0 / 3.0 * math.pi * r_cut ** 3
 
 
-def model_desc(n_species, n_hidden, r_cut, activation="silu", r_min=0.5, n_basis=7, n_radial=5):
+def model_desc(n_species, n_hidden, r_cut, activation="silu", r_min=0.5, n_basis=7, n_radial=5, basis="gaussian",
+               n_ensemble=1):
     return dict(n_species=n_species, n_hidden=n_hidden, r_cut=float(r_cut), r_min=float(r_min),
-                n_basis=n_basis, n_radial=n_radial, activation=activation)
+                n_basis=n_basis, n_radial=n_radial, activation=activation, basis=basis, n_ensemble=n_ensemble)
 
 
 @functools.lru_cache(maxsize=None)

@@ -11,8 +11,8 @@ binding) packs them its own way.
     b1    [H]                        ~ N(0, 0.1^2)
     W2    [H, H]                     Xavier normal
     b2    [H]                        ~ N(0, 0.1^2)
-    w3    [H]                        Xavier normal (fan_out 1)
-    b3    [1]                        ~ N(0, 0.1^2)
+    w3    [H] (or [H, E] for E heads) Xavier normal (fan_out 1 per head)
+    b3    [1] (or [E])               ~ N(0, 0.1^2)
     sigma [S]                        ~ U(0.5, 1.5)
     mu    [S]                        ~ N(0, 1)
 """
@@ -26,25 +26,26 @@ N_FEATURES = 360
 BETA_SCALE = 24.0
 
 
-def param_shapes(n_species: int, n_hidden: int, n_radial=5, n_basis=7, n_features=N_FEATURES):
-    S, H = n_species, n_hidden
+def param_shapes(n_species: int, n_hidden: int, n_radial=5, n_basis=7, n_features=N_FEATURES, n_ensemble=1):
+    """Parameter shapes; a shallow ensemble of E > 1 output heads has w3 [H, E] and b3 [E]."""
+    S, H, E = n_species, n_hidden, max(1, int(n_ensemble))
     return {
         "beta": (S, S, n_radial, n_basis),
         "W1": (n_features, H),
         "b1": (H,),
         "W2": (H, H),
         "b2": (H,),
-        "w3": (H,),
-        "b3": (1,),
+        "w3": (H,) if E == 1 else (H, E),
+        "b3": (E,),
         "sigma": (S,),
         "mu": (S,),
     }
 
 
 def make_params(n_species: int, n_hidden: int, seed: int, nbar: float,
-                n_radial=5, n_basis=7, n_features=N_FEATURES):
+                n_radial=5, n_basis=7, n_features=N_FEATURES, n_ensemble=1):
     rng = np.random.default_rng([seed, 41])
-    sh = param_shapes(n_species, n_hidden, n_radial, n_basis, n_features)
+    sh = param_shapes(n_species, n_hidden, n_radial, n_basis, n_features, n_ensemble)
 
     def xavier(fan_in, fan_out, shape):
         return rng.normal(0.0, math.sqrt(2.0 / (fan_in + fan_out)), shape)

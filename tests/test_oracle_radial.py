@@ -107,3 +107,82 @@ def test_dimer_rank0_moments_are_the_radial_functions(params, r, fc):
     assert np.allclose(psi0[1], _radial_by_hand(beta, 1, 0, r, fc), rtol=1e-12, atol=1e-15)
     swapped = _radial_by_hand(beta, 1, 0, r, fc)
     assert np.abs(psi0[0] - swapped).max() > 1e-3 * np.abs(psi0[0]).max()
+
+
+# ----------------------------------------------------------------- Bessel-like basis
+# The second basis the paper names (Kocer et al.): f_k = a_k [j0((k+1) pi r/r_c) +
+# j0((k+2) pi r/r_c)].  The zeroth-order spherical Bessel functions j0(n pi r / r_c) are
+# orthogonal on [0, r_c] with weight r^2 (norm r_c^3 / (2 n^2 pi^2)), so the f_k are unit
+# vectors, f_k and f_(k+1) share one term (overlap of sign -1), and f_k, f_l with |k - l| >= 2
+# are orthogonal.  Each f_k and its slope vanish at r_c.  These properties come from the
+# mathematics of j0, not from the formula typed again.
+
+BESSEL = dict(DESC, basis="bessel")
+
+
+def _bessel_only(params, r):
+    """f_k(r) without the cutoff: the oracle's f_c f_k divided by f_c (pinned above)."""
+    B, dB = oracle.radial_basis(BESSEL, params, r)
+    fc = 0.5 * (math.cos(math.pi * r / 5.0) + 1.0)
+    return B / fc
+
+
+def test_bessel_basis_is_orthonormal_with_weight_r_squared(params):
+    x, w = np.polynomial.legendre.leggauss(400)
+    r = 2.5 * (x + 1.0)                       # [0, 5]
+    w = 2.5 * w
+    F = np.array([_bessel_only(params, ri) for ri in r])          # [nodes, 7]
+    gram = (F * (w * r * r)[:, None]).T @ F
+    assert np.allclose(np.diag(gram), 1.0, atol=1e-9)
+    for k in range(7):
+        for l in range(7):
+            if abs(k - l) >= 2:
+                assert abs(gram[k, l]) <= 1e-9, (k, l)
+            elif abs(k - l) == 1:
+                assert gram[k, l] < -1e-3, (k, l)    # one shared term, opposite signs
+
+
+def test_bessel_basis_and_slope_vanish_at_r_cut(params):
+    B, dB = oracle.radial_basis(BESSEL, params, 5.0)
+    assert np.all(B == 0.0) and np.all(dB == 0.0)
+    f1 = np.abs(_bessel_only(params, 5.0 - 1e-2))
+    f2 = np.abs(_bessel_only(params, 5.0 - 1e-3))
+    # f_k(r_c - h) = O(h^2): ten times closer, about a hundred times smaller
+    assert np.all(f2 <= 0.02 * f1 + 1e-12) and np.all(f1 < 2e-2)
+
+
+def test_bessel_basis_derivative_matches_central_differences(params):
+    h = 1e-6
+    for r in (0.4, 1.3, 2.6, 3.9, 4.95):
+        _, dB = oracle.radial_basis(BESSEL, params, r)
+        Bp, _ = oracle.radial_basis(BESSEL, params, r + h)
+        Bm, _ = oracle.radial_basis(BESSEL, params, r - h)
+        assert np.allclose(dB, (Bp - Bm) / (2 * h), rtol=1e-7, atol=1e-9), r
+
+
+def test_bessel_model_forces_and_virial_match_autograd_and_differences():
+    import synth
+    from oracle import torch_ref
+    b, d, p = synth.config(1, activation="tanh")
+    d = dict(d, basis="bessel")
+    nl = oracle.neighbors(b, d["r_cut"])
+    out = oracle.energy_forces(b, d, p, nl)
+    t = torch_ref.energy_forces(b, d, p, nl)
+    assert abs(out["E"][0] - t["E"][0]) <= 1e-12 * np.abs(t["E_atom"]).sum()
+    assert np.abs(out["F"] - t["F"]).max() <= 1e-12 * np.abs(t["F"]).max()
+    assert np.abs(out["virial"] - t["virial"]).max() <= 1e-12 * np.abs(t["virial"]).max()
+    # central differences of the energy for a few atoms
+    h = 1e-5
+    for k in (0, 40, 95):
+        for c in range(3):
+            e = []
+            for sgn in (1, -1):
+                pos = b.pos.copy()
+                pos[k, c] += sgn * h
+                b2 = make_batch([(pos, b.species, b.cell[0])], b.n_species)
+                e.append(oracle.energy_forces(b2, d, p, nl, virial=False)["E"][0])
+            fd = -(e[0] - e[1]) / (2 * h)
+            assert abs(fd - out["F"][k, c]) <= 1e-6 * np.abs(out["F"]).max(), (k, c)
+    # the Bessel model is a different function of the positions than the Gaussian one
+    g = oracle.energy_forces(b, dict(d, basis="gaussian"), p, nl)
+    assert np.abs(g["F"] - out["F"]).max() > 1e-2 * np.abs(out["F"]).max()
