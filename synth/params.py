@@ -63,3 +63,18 @@ def make_params(n_species: int, n_hidden: int, seed: int, nbar: float,
         "mu": rng.normal(0.0, 1.0, sh["mu"]),
     }
     return {k: np.ascontiguousarray(v, dtype=np.float64) for k, v in p.items()}
+
+
+def maxwell_boltzmann(masses_amu, atom_ptr, temperature_k, seed):
+    """Seeded initial velocities (A/fs): each component ~ N(0, kT/m), then every structure's
+    centre-of-mass velocity removed.  Input generation only (the MD integrators on both sides
+    take these as given)."""
+    kb, conv = 8.617333262e-5, 103.642696562      # eV/K; amu A^2/fs^2 in eV
+    rng = np.random.default_rng([seed, 61])
+    m = np.asarray(masses_amu, np.float64)
+    v = rng.normal(0.0, 1.0, (len(m), 3)) * np.sqrt(kb * temperature_k / (m * conv))[:, None]
+    for b in range(len(atom_ptr) - 1):
+        a0, a1 = atom_ptr[b], atom_ptr[b + 1]
+        if a1 - a0 > 1:
+            v[a0:a1] -= (m[a0:a1, None] * v[a0:a1]).sum(0) / m[a0:a1].sum()
+    return v

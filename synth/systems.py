@@ -283,3 +283,12 @@ def dimer(r: float, direction=(0.0, 0.0, 1.0), species=(0, 1), box=100.0):
     c = np.full(3, box / 2)
     pos = np.stack([c - 0.5 * r * u, c + 0.5 * r * u])
     return pos, np.asarray(species, np.int32), np.eye(3) * box
+
+
+def species_masses(kind: str) -> np.ndarray:
+    """Atomic masses (amu) indexed by the species numbering of the generators."""
+    table = EMIM_SPECIES if kind == "emim" else LI3PO4_SPECIES
+    out = np.zeros(len(table))
+    for el, idx in table.items():
+        out[idx] = _MASS[el]
+    return out
