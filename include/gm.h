@@ -135,7 +135,7 @@ typedef struct {
  * minimum, without the slab.  gm_build_neighbors accepts any workspace of at least the
  * minimum and uses the slab when it fits (else it tests the candidates twice: count, then
  * fill). */
-enum { GM_OP_NEIGHBORS = 0, GM_OP_ENERGY_FORCES = 1, GM_OP_PARAM_GRAD = 2 };
+enum { GM_OP_NEIGHBORS = 0, GM_OP_ENERGY_FORCES = 1, GM_OP_PARAM_GRAD = 2, GM_OP_MD = 3 };
 
 /* Number of FP32 parameters.  Flat layout of theta, in this order:
  *   beta[S][S][n_radial][n_basis], W1[360][H], b1[H], W2[H][H], b2[H], w3[H][E], b3[E],
@@ -219,6 +219,62 @@ GM_API gm_status gm_build_neighbors(const gm_model *m, const gm_system *sys, gm_
  * The neighbour list must describe sys (as written by gm_build_neighbors or equivalent). */
 GM_API gm_status gm_energy_forces(const gm_model *m, const gm_system *sys, const gm_nlist *nl, double *energy,
                            float *forces, double *virial, void *ws, size_t ws_bytes, int32_t *status_dev,
+                           struct CUstream_st *stream);
+
+/* ---------------------------------------------------------------- molecular dynamics
+ * Section "Deployment": an MD engine whose whole loop runs on the device, with a neighbour
+ * list that has a skin and thermostats; the appendix's MD configuration: NVT, dt 0.5 fs, a
+ * Nose-Hoover chain (length 3, 2 chain steps, 3 Suzuki-Yoshida steps, tau), skin 0.5 A.
+ * Units: A, fs, amu, eV, K. */
+typedef enum { GM_MD_NVE = 0, GM_MD_NVT = 1 } gm_md_ensemble;
+#define GM_MD_MAX_CHAIN 8
+
+typedef struct {
+    double dt;            /* time step (fs) */
+    double skin;          /* neighbour-list skin (A): the list holds pairs within r_cut + skin and
+                             is rebuilt, on the device, after any atom has moved more than skin/2
+                             since the last build */
+    double temperature;   /* target temperature (K), NVT */
+    double tau;           /* thermostat time constant (fs), NVT: Q_1 = N_f kT tau^2, Q_j = kT tau^2 */
+    int32_t ensemble;     /* gm_md_ensemble */
+    int32_t chain_length; /* thermostats per chain, 1..GM_MD_MAX_CHAIN (NVT) */
+    int32_t chain_steps;  /* sub-steps of each thermostat half step, >= 1 (NVT) */
+    int32_t sy_steps;     /* Suzuki-Yoshida stages, 1, 3 or 5 (NVT) */
+} gm_md_params;
+
+/* MD state, all device memory owned by the caller (B structures, N atoms, S species). */
+typedef struct {
+    double *pos;          /* [N][3] positions (A), updated in place; must be sys->pos */
+    double *vel;          /* [N][3] velocities (A/fs), in/out */
+    const double *mass;   /* [S] masses (amu) */
+    float *forces;        /* [N][3] forces at pos (eV/A), written by gm_md_init and every step */
+    double *energy;       /* [B] potential energy at pos (eV) */
+    double *kinetic;      /* [B] kinetic energy (eV) */
+    double *pos_ref;      /* [N][3] positions at the last neighbour build (A) */
+    double *chain;        /* [B][2][GM_MD_MAX_CHAIN] thermostat positions xi and velocities v_xi
+                             of each structure's chain (NVT; zeroed by gm_md_init) */
+    int64_t *n_builds;    /* scalar: neighbour builds, incremented on the device (caller zeroes) */
+} gm_md_state;
+
+/* Start (or restart) a run: build the neighbour list at r_cut + skin from state->pos (nl must
+ * have room for it), record pos_ref, zero the chains, evaluate forces and energies, the
+ * kinetic energies, and count one build.  Workspace: GM_OP_MD with nl's capacity.  Errors:
+ * GM_ERR_ARG (null pointers, state->pos != sys->pos, bad parameters), GM_ERR_WORKSPACE. */
+GM_API gm_status gm_md_init(const gm_model *m, const gm_system *sys, gm_nlist *nl, const gm_md_params *params,
+                            gm_md_state *state, void *ws, size_t ws_bytes, int32_t *status_dev,
+                            struct CUstream_st *stream);
+
+/* n_steps steps of velocity Verlet (NVE) or with a Nose-Hoover chain per structure (NVT,
+ * integrated with the explicit reversible scheme of Martyna, Tuckerman, Tobias and Klein:
+ * a thermostat half step before the first and after the second velocity half kick), with
+ * N_f = 3 N_b - 3 degrees of freedom per structure.  Each step: thermostat, half kick and
+ * drift, the skin test, the neighbour build only when the test fails (decided on the device),
+ * energies and forces, half kick, kinetic energies, thermostat.  Everything is enqueued on
+ * `stream` without host synchronisation, so a run can be captured into a CUDA graph and
+ * replayed.  A neighbour-list overflow writes GM_ERR_CAPACITY to *status_dev and freezes the
+ * state (later kernels skip).  The workspace of gm_md_init; call gm_md_init first. */
+GM_API gm_status gm_md_run(const gm_model *m, const gm_system *sys, gm_nlist *nl, const gm_md_params *params,
+                           gm_md_state *state, int32_t n_steps, void *ws, size_t ws_bytes, int32_t *status_dev,
                            struct CUstream_st *stream);
 
 /* Force modes of a shallow ensemble (section "Uncertainty Quantification", Eq. jacobian). */

@@ -4,5 +4,5 @@ The compute path is libgm.so (CUDA kernels behind the C ABI of include/gm.h); th
 package only marshals PyTorch device buffers and streams into it.
 """
 from ._lib import GmError, load  # noqa: F401
-from .gmnn import (GMNN, DeviceSystem, GMNNFunction, NeighborList, pack_theta,  # noqa: F401
+from .gmnn import (GMNN, DeviceSystem, GMNNFunction, MDParams, MDState, NeighborList, pack_theta,  # noqa: F401
                    unpack_theta)

@@ -17,8 +17,10 @@ GM_ACT_TANH, GM_ACT_SILU = 0, 1
 GM_PREC_FP32, GM_PREC_MIXED = 0, 1
 GM_BASIS_GAUSSIAN, GM_BASIS_BESSEL = 0, 1
 GM_ENS_MEAN_GRADIENT, GM_ENS_JACOBIAN = 0, 1
+GM_MD_NVE, GM_MD_NVT = 0, 1
+GM_MD_MAX_CHAIN = 8
 GM_MAX_ENSEMBLE = 32
-GM_OP_NEIGHBORS, GM_OP_ENERGY_FORCES, GM_OP_PARAM_GRAD = 0, 1, 2
+GM_OP_NEIGHBORS, GM_OP_ENERGY_FORCES, GM_OP_PARAM_GRAD, GM_OP_MD = 0, 1, 2, 3
 GM_MAX_ATOMS = 4_000_000
 MIXED_AVAILABLE = True   # GM_PREC_MIXED: BF16 network GEMMs on tcgen05
 
@@ -31,7 +33,7 @@ EXPORTS = ("gm_param_count", "gm_model_create", "gm_model_set_params", "gm_model
            "gm_status_clear", "gm_status_string", "gm_last_error", "gm_profile_enable", "gm_profile_reset",
            "gm_profile_n_stages", "gm_profile_stage_name", "gm_profile_collect", "gm_build_neighbors_noalloc", "gm_model_set_tuning",
            "gm_profile_forget_graphs", "gm_model_pair_lanes", "gm_model_device_bytes", "gm_probe_alu",
-           "gm_energy_forces_ensemble")
+           "gm_energy_forces_ensemble", "gm_md_init", "gm_md_run")
 
 
 class GmModelDesc(ctypes.Structure):
@@ -50,6 +52,18 @@ class GmSystem(ctypes.Structure):
 class GmNlist(ctypes.Structure):
     _fields_ = [("capacity", ctypes.c_int64), ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p),
                 ("shift", ctypes.c_void_p), ("n_pairs", ctypes.c_void_p)]
+
+
+class GmMdParams(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("skin", ctypes.c_double), ("temperature", ctypes.c_double),
+                ("tau", ctypes.c_double), ("ensemble", ctypes.c_int32), ("chain_length", ctypes.c_int32),
+                ("chain_steps", ctypes.c_int32), ("sy_steps", ctypes.c_int32)]
+
+
+class GmMdState(ctypes.Structure):
+    _fields_ = [("pos", ctypes.c_void_p), ("vel", ctypes.c_void_p), ("mass", ctypes.c_void_p),
+                ("forces", ctypes.c_void_p), ("energy", ctypes.c_void_p), ("kinetic", ctypes.c_void_p),
+                ("pos_ref", ctypes.c_void_p), ("chain", ctypes.c_void_p), ("n_builds", ctypes.c_void_p)]
 
 
 class GmError(RuntimeError):
@@ -101,6 +115,10 @@ def load():
         "gm_model_pair_lanes": (ctypes.c_int32, [_P, ctypes.c_int32]),
         "gm_model_device_bytes": (ctypes.c_size_t, [_P]),
         "gm_probe_alu": (st, [ctypes.c_int32, ctypes.c_int64, _P, ctypes.POINTER(ctypes.c_double), _P]),
+        "gm_md_init": (st, [_P, ctypes.POINTER(GmSystem), ctypes.POINTER(GmNlist), ctypes.POINTER(GmMdParams),
+                            ctypes.POINTER(GmMdState), _P, ctypes.c_size_t, _P, _P]),
+        "gm_md_run": (st, [_P, ctypes.POINTER(GmSystem), ctypes.POINTER(GmNlist), ctypes.POINTER(GmMdParams),
+                           ctypes.POINTER(GmMdState), ctypes.c_int32, _P, ctypes.c_size_t, _P, _P]),
         "gm_energy_forces_ensemble": (st, [_P, ctypes.POINTER(GmSystem), ctypes.POINTER(GmNlist), _P, _P, _P, _P, _P,
                                            ctypes.c_int32, _P, _P, _P, ctypes.c_size_t, _P, _P]),
     }
@@ -193,6 +211,18 @@ def gm_energy_forces_ensemble(model, sys: GmSystem, nl: GmNlist, energy, forces,
     check(load().gm_energy_forces_ensemble(model, ctypes.byref(sys), ctypes.byref(nl), energy, forces, virial,
                                            energy_heads, energy_std, mode, forces_heads, force_std, ws, ws_bytes,
                                            status, stream), "gm_energy_forces_ensemble")
+
+
+def gm_md_init(model, sys: GmSystem, nl: GmNlist, params: GmMdParams, state: GmMdState, ws, ws_bytes, status,
+               stream):
+    check(load().gm_md_init(model, ctypes.byref(sys), ctypes.byref(nl), ctypes.byref(params), ctypes.byref(state),
+                            ws, ws_bytes, status, stream), "gm_md_init")
+
+
+def gm_md_run(model, sys: GmSystem, nl: GmNlist, params: GmMdParams, state: GmMdState, n_steps, ws, ws_bytes,
+              status, stream):
+    check(load().gm_md_run(model, ctypes.byref(sys), ctypes.byref(nl), ctypes.byref(params), ctypes.byref(state),
+                           n_steps, ws, ws_bytes, status, stream), "gm_md_run")
 
 
 def gm_param_grad(model, sys: GmSystem, nl: GmNlist, dL_dE, dL_dF, grad_theta, ws, ws_bytes, status, stream):

@@ -24,6 +24,7 @@
 #include "gm_ensemble.h"
 #include "gm_gemm.h"
 #include "gm_internal.h"
+#include "gm_md.h"
 #include "gm_pair.h"
 #include "gm_pgrad.h"
 #include "gm_reduce.h"
@@ -275,6 +276,36 @@ EfWs carve_ef(Carve &c, int B, int N, int H, int E = 1) {
 size_t ef_workspace_bytes(int B, int N, int H, int E) {
     Carve c(reinterpret_cast<void *>(256), ~size_t(0) >> 1);
     carve_ef(c, B, N, H, E);
+    return c.off + 256;
+}
+
+// MD: the neighbour build's workspace (with the search slab for the list's capacity), the
+// energy/force workspace, and the integrator's words (skin flag, kinetic-energy accumulators,
+// per-structure thermostat factors)
+struct MdWs {
+    void *nl;
+    size_t nl_bytes;
+    EfWs ef;
+    int32_t *flag;
+    unsigned long long *acc;
+    double *pending, *factor;
+};
+
+MdWs carve_md(Carve &c, int B, int N, int H, int64_t cap) {
+    MdWs w;
+    w.nl_bytes = nl_workspace_bytes(B, N, cap);
+    w.nl = c.take<char>(w.nl_bytes);
+    w.ef = carve_ef(c, B, N, H);
+    w.flag = c.take<int32_t>(64);
+    w.acc = c.take<unsigned long long>(reduce_acc_words(B));
+    w.pending = c.take<double>(B);
+    w.factor = c.take<double>(B);
+    return w;
+}
+
+size_t md_workspace_bytes(int B, int N, int H, int64_t cap) {
+    Carve c(reinterpret_cast<void *>(256), ~size_t(0) >> 1);
+    carve_md(c, B, N, H, cap);
     return c.off + 256;
 }
 
@@ -562,6 +593,7 @@ gm_status gm_workspace_size(const gm_model *m, int32_t n_structures, int32_t n_a
     case GM_OP_NEIGHBORS: *bytes = nl_workspace_bytes(n_structures, n_atoms, nl_capacity); return GM_OK;
     case GM_OP_ENERGY_FORCES: *bytes = ef_workspace_bytes(n_structures, n_atoms, m->H, m->E); return GM_OK;
     case GM_OP_PARAM_GRAD: *bytes = pg_workspace_bytes(n_atoms, m->H, m->S); return GM_OK;
+    case GM_OP_MD: *bytes = md_workspace_bytes(n_structures, n_atoms, m->H, nl_capacity); return GM_OK;
     default: return fail(GM_ERR_ARG, "unknown op");
     }
 }
@@ -803,6 +835,101 @@ gm_status gm_energy_forces_ensemble(const gm_model *m, const gm_system *sys, con
     return launch_status();
 }
 
+// ------------------------------------------------------------------ molecular dynamics
+
+static gm_status md_check(const gm_model *m, const gm_system *sys, const gm_nlist *nl, const gm_md_params *params,
+                          const gm_md_state *st, const int32_t *status) {
+    gm_status s = check_system(m, sys);
+    if (s != GM_OK) return s;
+    if ((s = check_nlist(sys, nl, false)) != GM_OK) return s;
+    if (!status || !st) return fail(GM_ERR_ARG, "null status or state");
+    if (md_check_params(params) != GM_OK) return fail(GM_ERR_ARG, "bad MD parameters");
+    if (m->E > 1) return fail(GM_ERR_UNSUPPORTED, "MD of a shallow-ensemble model uses its mean; not implemented");
+    if (!st->pos || !st->vel || !st->mass || !st->kinetic || !st->energy || !st->pos_ref || !st->chain ||
+        (sys->n_atoms > 0 && !st->forces))
+        return fail(GM_ERR_ARG, "null MD state field");
+    if (st->pos != sys->pos) return fail(GM_ERR_ARG, "state->pos must be the system's positions");
+    if (!aligned(st->vel, 8) || !aligned(st->mass, 8) || !aligned(st->forces, 4) || !aligned(st->energy, 8) ||
+        !aligned(st->kinetic, 8) || !aligned(st->pos_ref, 8) || !aligned(st->chain, 8) || !aligned(st->n_builds, 8))
+        return fail(GM_ERR_ARG, "misaligned MD state field");
+    return GM_OK;
+}
+
+gm_status gm_md_init(const gm_model *m, const gm_system *sys, gm_nlist *nl, const gm_md_params *params,
+                     gm_md_state *state, void *ws, size_t ws_bytes, int32_t *status, struct CUstream_st *stream) {
+    gm_status s = md_check(m, sys, nl, params, state, status);
+    if (s != GM_OK) return s;
+    const int N = sys->n_atoms, B = sys->n_structures;
+    Carve c(ws, ws_bytes);
+    MdWs w = carve_md(c, B, N, m->H, nl->capacity);
+    if (!c.ok) return fail(GM_ERR_WORKSPACE, "workspace too small");
+    cudaStream_t st = stream;
+    // chains at rest, accumulators at zero, and the skin flag set so that the kinetic pass
+    // below records pos_ref and counts this build
+    if (cudaMemsetAsync(state->chain, 0, sizeof(double) * 2 * GM_MD_MAX_CHAIN * B, st) != cudaSuccess ||
+        cudaMemsetAsync(w.acc, 0, sizeof(unsigned long long) * reduce_acc_words(B), st) != cudaSuccess ||
+        cudaMemsetAsync(w.flag, 0, sizeof(int32_t) * 64, st) != cudaSuccess ||
+        cudaMemsetAsync(w.flag, 1, 1, st) != cudaSuccess)
+        return fail(GM_ERR_CUDA, "memset of the MD state failed");
+    {
+        StageScope sc(ST_NEIGHBORS, st);
+        if ((s = nl_build(*sys, m->d.r_cut + params->skin, m->S, *nl, w.nl, w.nl_bytes, status, st, m->nl)) != GM_OK)
+            return fail(s, "neighbour build launch failed");
+    }
+    if ((s = energy_forces_pipeline(m, sys, nl, state->energy, state->forces, nullptr, w.ef, false, status, st)) != GM_OK)
+        return s;
+    gm_md_params nve = *params;
+    nve.ensemble = GM_MD_NVE;     // kinetic energies only: no thermostat step here
+    StageScope sc(ST_MD, st);
+    md_kick_ke(N, B, sys->atom_ptr, sys->species, state->mass, state->forces, nve, 0, state->vel, state->pos,
+               state->pos_ref, w.flag, w.acc, state->kinetic, state->chain, w.pending, state->n_builds, status, st);
+    return launch_status();
+}
+
+gm_status gm_md_run(const gm_model *m, const gm_system *sys, gm_nlist *nl, const gm_md_params *params,
+                    gm_md_state *state, int32_t n_steps, void *ws, size_t ws_bytes, int32_t *status,
+                    struct CUstream_st *stream) {
+    gm_status s = md_check(m, sys, nl, params, state, status);
+    if (s != GM_OK) return s;
+    if (n_steps < 0) return fail(GM_ERR_ARG, "negative step count");
+    const int N = sys->n_atoms, B = sys->n_structures;
+    Carve c(ws, ws_bytes);
+    MdWs w = carve_md(c, B, N, m->H, nl->capacity);
+    if (!c.ok) return fail(GM_ERR_WORKSPACE, "workspace too small");
+    cudaStream_t st = stream;
+    if (cudaMemsetAsync(w.acc, 0, sizeof(unsigned long long) * reduce_acc_words(B), st) != cudaSuccess ||
+        cudaMemsetAsync(w.flag, 0, sizeof(int32_t) * 64, st) != cudaSuccess)
+        return fail(GM_ERR_CUDA, "memset of the MD words failed");
+    const bool nvt = params->ensemble == GM_MD_NVT;
+    const double r_list = m->d.r_cut + params->skin;
+    for (int k = 0; k < n_steps; ++k) {
+        {
+            StageScope sc(ST_MD, st);
+            if (nvt) md_thermo(B, sys->atom_ptr, *params, state->chain, state->kinetic, w.pending, w.factor, k == 0,
+                               status, st);
+            md_kick_drift(N, B, sys->atom_ptr, sys->species, state->mass, state->forces, nvt ? w.factor : nullptr,
+                          *params, state->vel, state->pos, state->pos_ref, w.flag, status, st);
+        }
+        {
+            StageScope sc(ST_NEIGHBORS, st);
+            if ((s = nl_build(*sys, r_list, m->S, *nl, w.nl, w.nl_bytes, status, st, m->nl, w.flag)) != GM_OK)
+                return fail(s, "neighbour build launch failed");
+        }
+        if ((s = energy_forces_pipeline(m, sys, nl, state->energy, state->forces, nullptr, w.ef, false, status, st)) !=
+            GM_OK)
+            return s;
+        StageScope sc(ST_MD, st);
+        md_kick_ke(N, B, sys->atom_ptr, sys->species, state->mass, state->forces, *params, 1, state->vel, state->pos,
+                   state->pos_ref, w.flag, w.acc, state->kinetic, state->chain, w.pending, state->n_builds, status,
+                   st);
+    }
+    if (nvt && n_steps > 0) {
+        StageScope sc(ST_MD, st);
+        md_finish(N, B, sys->atom_ptr, w.pending, state->vel, status, st);
+    }
+    return launch_status();
+}
+
 gm_status gm_descriptors(const gm_model *m, const gm_system *sys, const gm_nlist *nl, float *psi, float *features,
                          void *ws, size_t ws_bytes, int32_t *status, struct CUstream_st *stream) {
     gm_status s = check_system(m, sys);
@@ -934,7 +1061,7 @@ const char *gm_profile_stage_name(int s) {
     static const char *names[N_STAGES] = {"neighbors", "moments", "contract_fwd", "gemm_l1", "gemm_l2",
                                           "gemm_b1", "gemm_b0", "contract_bwd", "forces", "reduce",
                                           "pg_pair_fwd", "pg_network", "pg_pair_bwd", "nl_bin", "nl_count",
-                                          "nl_scan", "nl_fill", "nl_coop"};
+                                          "nl_scan", "nl_fill", "nl_coop", "md_integrate"};
     return (s >= 0 && s < N_STAGES) ? names[s] : "";
 }
 

@@ -32,7 +32,7 @@ struct Carve {
 enum Stage {
     ST_NEIGHBORS = 0, ST_MOMENTS, ST_CONTRACT_FWD, ST_GEMM_L1, ST_GEMM_L2, ST_GEMM_B1, ST_GEMM_B0,
     ST_CONTRACT_BWD, ST_FORCES, ST_REDUCE, ST_PG_PAIR_FWD, ST_PG_NETWORK, ST_PG_PAIR_BWD, ST_NL_BIN, ST_NL_COUNT,
-    ST_NL_SCAN, ST_NL_FILL, ST_NL_COOP, N_STAGES
+    ST_NL_SCAN, ST_NL_FILL, ST_NL_COOP, ST_MD, N_STAGES
 };
 void note_launches(int n);
 
@@ -89,7 +89,9 @@ struct NlTuning {
 const NlTuning &nl_tuning(const gm_model *m);
 size_t nl_workspace_bytes(int n_struct, int n_atoms, int64_t capacity);   // with the search slab
 size_t nl_workspace_min_bytes(int n_struct, int n_atoms);                  // two-pass search
+// gate (device int32, may be null): build only when *gate != 0 at launch; the list is left as
+// it was otherwise (the memset of the build's own counters still runs)
 gm_status nl_build(const gm_system &sys, double r_cut, int n_species, gm_nlist &nl, void *ws, size_t ws_bytes,
-                   int32_t *status, cudaStream_t st, const NlTuning &tune);
+                   int32_t *status, cudaStream_t st, const NlTuning &tune, const int32_t *gate = nullptr);
 
 }  // namespace gm

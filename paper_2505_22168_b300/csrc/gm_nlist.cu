@@ -120,7 +120,14 @@ struct NlArgs {
     int64_t *n_pairs;
     unsigned *bar;          // grid barrier: [0] arrivals, [1] generation
     int32_t *status;
+    const int32_t *gate;    // if not null: build only when *gate != 0 (written by an earlier kernel)
 };
+
+// A gated build (the skin test of an MD step decides on the device whether the list is
+// rebuilt): every block reads the same word and returns before its first barrier.
+__device__ __forceinline__ bool nl_gated_off(const NlArgs &a) {
+    return a.gate != nullptr && *reinterpret_cast<const volatile int32_t *>(a.gate) == 0;
+}
 
 __device__ __forceinline__ unsigned long long nl_clock_ns() {
     unsigned long long t;
@@ -1484,6 +1491,7 @@ __device__ bool nl_brute_build(const NlArgs &a, int bid, int nb, NlStruct *Ss, i
 __global__ void __launch_bounds__(NL_THREADS, 2) k_nl_coop(NlArgs a) {
     extern __shared__ float4 nl_smem[];
     const int bid = blockIdx.x, nb = gridDim.x;
+    if (nl_gated_off(a)) return;
     if (a.mid) {
         // every block sets up the grids; the brute-force search when the boxes allow it, else
         // (or after a row longer than BR_CAP) the phases below from the binning on -- the
@@ -1557,6 +1565,7 @@ __global__ void __launch_bounds__(NL_THREADS, 2) k_nl_coop(NlArgs a) {
 
 __global__ void __launch_bounds__(NL_THREADS, 2) k_nl_phase(NlArgs a, int ph) {
     extern __shared__ float4 nl_smem[];
+    if (nl_gated_off(a)) return;
     run_phase(a, ph, blockIdx.x, gridDim.x, nl_smem);
 }
 
@@ -1655,7 +1664,7 @@ static int nl_auto_split(int N, bool block_items) {
 }
 
 gm_status nl_build(const gm_system &sys, double r_cut, int n_species, gm_nlist &nl, void *ws, size_t ws_bytes,
-                   int32_t *status, cudaStream_t st, const NlTuning &tune) {
+                   int32_t *status, cudaStream_t st, const NlTuning &tune, const int32_t *gate) {
     const int B = sys.n_structures, N = sys.n_atoms;
     Carve c(ws, ws_bytes);
     NlWs w = carve_nl(c, B, N);
@@ -1710,6 +1719,7 @@ gm_status nl_build(const gm_system &sys, double r_cut, int n_species, gm_nlist &
     a.n_pairs = nl.n_pairs;
     a.bar = w.bar;
     a.status = status;
+    a.gate = gate;
 
     NlDevice &dev = nl_device();
     const int ncmax = N + B;

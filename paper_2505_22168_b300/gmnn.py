@@ -87,6 +87,45 @@ class NeighborList:
         return t[np.lexsort(t.T[::-1])]
 
 
+class MDParams:
+    """Integration parameters (the gm_md_params of the C ABI).  Defaults: the paper's MD
+    configuration (NVT, 0.5 fs, chain of 3 with 2 chain steps and 3 Suzuki-Yoshida steps,
+    tau = 100 time steps, skin 0.5 A) at 600 K."""
+
+    def __init__(self, dt=0.5, skin=0.5, temperature=600.0, tau=None, ensemble="nvt", chain_length=3,
+                 chain_steps=2, sy_steps=3):
+        self.dt, self.skin, self.temperature = float(dt), float(skin), float(temperature)
+        self.tau = float(tau) if tau is not None else 100.0 * float(dt)
+        self.ensemble, self.chain_length, self.chain_steps, self.sy_steps = ensemble, chain_length, chain_steps, sy_steps
+
+    def c_struct(self) -> L.GmMdParams:
+        return L.GmMdParams(self.dt, self.skin, self.temperature, self.tau,
+                            L.GM_MD_NVT if self.ensemble == "nvt" else L.GM_MD_NVE, self.chain_length,
+                            self.chain_steps, self.sy_steps)
+
+
+class MDState:
+    """Device buffers of an MD run (the gm_md_state of the C ABI).  The positions are the
+    system's own (sysd.pos), integrated in place."""
+
+    def __init__(self, sysd, masses_by_species, vel):
+        dev = sysd.pos.device
+        N, B = sysd.n_atoms, sysd.n_structures
+        self.pos = sysd.pos
+        self.vel = torch.as_tensor(np.asarray(vel, np.float64), device=dev).contiguous()
+        self.mass = torch.as_tensor(np.asarray(masses_by_species, np.float64), device=dev).contiguous()
+        self.forces = torch.zeros(N, 3, dtype=torch.float32, device=dev)
+        self.energy = torch.zeros(B, dtype=torch.float64, device=dev)
+        self.kinetic = torch.zeros(B, dtype=torch.float64, device=dev)
+        self.pos_ref = torch.zeros_like(sysd.pos)
+        self.chain = torch.zeros(B, 2, L.GM_MD_MAX_CHAIN, dtype=torch.float64, device=dev)
+        self.n_builds = torch.zeros(1, dtype=torch.int64, device=dev)
+
+    def c_struct(self) -> L.GmMdState:
+        return L.GmMdState(_ptr(self.pos), _ptr(self.vel), _ptr(self.mass), _ptr(self.forces), _ptr(self.energy),
+                           _ptr(self.kinetic), _ptr(self.pos_ref), _ptr(self.chain), _ptr(self.n_builds))
+
+
 class GMNN:
     """A GMNN model on the GPU (handle to libgm's gm_model)."""
 
@@ -151,8 +190,8 @@ class GMNN:
             self._ws[op] = buf
         return _ptr(buf), int(buf.numel())
 
-    def estimate_capacity(self, sysd: DeviceSystem, margin=1.3):
-        rc = float(self.desc["r_cut"])
+    def estimate_capacity(self, sysd: DeviceSystem, margin=1.3, r_list=None):
+        rc = float(self.desc["r_cut"]) if r_list is None else float(r_list)
         vols = np.abs(np.linalg.det(sysd.host_cells))
         n = sysd.host_counts.astype(np.float64)
         est = np.sum(n * n / vols * 4.0 / 3.0 * math.pi * rc ** 3)
@@ -229,6 +268,34 @@ class GMNN:
                                     _ptr(out.get("F_heads")), _ptr(out.get("F_std")), ws, wsb, _ptr(self.status),
                                     _stream())
         return out
+
+    # -------------------------------------------------------------- molecular dynamics
+    def md_neighbor_list(self, sysd: DeviceSystem, params: MDParams, margin=1.5):
+        """An empty neighbour list with room for the skin list (pairs within r_cut + skin)."""
+        cap = self.estimate_capacity(sysd, margin, float(self.desc["r_cut"]) + params.skin)
+        return NeighborList(sysd.n_atoms, cap, self.device)
+
+    def md_init(self, sysd: DeviceSystem, nl: NeighborList, params: MDParams, state: MDState, clear=True):
+        ws, wsb = self.workspace(L.GM_OP_MD, sysd, nl.capacity)
+        if clear:
+            self.clear_status()
+        L.gm_md_init(self.handle, sysd.c_struct(), nl.c_struct(), params.c_struct(), state.c_struct(), ws, wsb,
+                     _ptr(self.status), _stream())
+
+    def md_run(self, sysd: DeviceSystem, nl: NeighborList, params: MDParams, state: MDState, n_steps: int):
+        """n_steps MD steps on the current stream (no host synchronisation)."""
+        ws, wsb = self.workspace(L.GM_OP_MD, sysd, nl.capacity)
+        L.gm_md_run(self.handle, sysd.c_struct(), nl.c_struct(), params.c_struct(), state.c_struct(), int(n_steps),
+                    ws, wsb, _ptr(self.status), _stream())
+
+    def capture_md(self, sysd: DeviceSystem, nl: NeighborList, params: MDParams, state: MDState, n_steps: int):
+        """CUDA graph of md_run(n_steps) on fixed buffers (the paper's compiled inner steps)."""
+        self.workspace(L.GM_OP_MD, sysd, nl.capacity)
+        torch.cuda.current_stream().synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            self.md_run(sysd, nl, params, state, n_steps)
+        return graph
 
     def step(self, sysd: DeviceSystem, nl: NeighborList, out):
         """One MD-style step on the current stream: clear the status word, rebuild the
