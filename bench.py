@@ -612,6 +612,83 @@ def run_train(args, steps, warmup, precision="fp32"):
             "steps": steps, "stage_share": {k: round(v[0] / total, 4) for k, v in stages.items() if v[1] > 0}}
 
 
+def md_system(n_atoms):
+    """The paper's Li3PO4 MD sizes (Table li3po4_perf): a 192-atom box and its 3x3x3 supercell of
+    5184 atoms (synthetic jittered crystal, 2.4 g/cm^3), the batch workload's model (r_cut 5 A,
+    MLP 2x256), Maxwell-Boltzmann velocities at 600 K."""
+    import synth
+    from synth.params import maxwell_boltzmann
+    from synth.systems import li3po4_crystal, make_batch, species_masses, supercell
+    _, desc, params = synth.config(3)
+    base = li3po4_crystal(24, 4242, sigma=0.05)
+    s = base if n_atoms == 192 else supercell(base, 3)
+    b = make_batch([s], 3)
+    masses = species_masses("li3po4")
+    vel = maxwell_boltzmann(masses[b.species], b.atom_ptr, 600.0, 4242)
+    return b, desc, params, masses, vel
+
+
+def run_md(args, n_atoms, precision, n_inner=100, replays=5):
+    """Whole MD steps on the device (section "Deployment"; the appendix's configuration: NVT at
+    600 K, 0.5 fs, Nose-Hoover chain 3/2/3, tau 100 steps, skin 0.5 A): half kick, drift, skin
+    test, neighbour rebuild when needed, energies and forces, half kick, thermostat.  A CUDA
+    graph of n_inner steps is replayed; each replay is timed with CUDA events (L2 not flushed:
+    the state of an MD run stays resident between steps, which is the workload)."""
+    import torch
+
+    from paper_2505_22168_b300 import GMNN, DeviceSystem, MDParams, MDState, _lib
+    b, desc, params, masses, vel = md_system(n_atoms)
+    m = GMNN(desc, params, precision=precision)
+    sysd = DeviceSystem(b)
+    mp = MDParams(dt=0.5, skin=0.5, temperature=600.0, ensemble="nvt")
+    nl = m.md_neighbor_list(sysd, mp)
+    st = MDState(sysd, masses, vel)
+    m.md_init(sysd, nl, mp, st)
+    g = m.capture_md(sysd, nl, mp, st, n_inner)
+    for _ in range(max(1, args.warmup // 2)):
+        g.replay()
+    stream = torch.cuda.current_stream()
+    stream.synchronize()
+    b0 = int(st.n_builds.item())
+    _lib.gm_profile_reset()
+    m.md_run(sysd, nl, mp, st, 1)                 # one uncaptured step: launches per step
+    stream.synchronize()
+    launches_per_step = _lib.gm_profile_collect()[1]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(replays)]
+    for e0, e1 in ev:
+        e0.record(stream)
+        g.replay()
+        e1.record(stream)
+    stream.synchronize()
+    if m.read_status() != 0:
+        raise RuntimeError(f"device status {m.read_status()} in the MD run")
+    ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
+    steps = n_inner * replays
+    builds = int(st.n_builds.item()) - b0
+    us_atom_step = ms * 1e3 / (steps * n_atoms)
+    # accuracy at the final configuration: the forces the integrator used against the oracle's
+    import oracle
+    pos = st.pos.cpu().numpy()
+    F = st.forces.cpu().numpy()
+    import dataclasses
+    bf = dataclasses.replace(b, pos=pos)
+    if n_atoms <= 1000:
+        ref = oracle.energy_forces(bf, desc, params, oracle.neighbors(bf, desc["r_cut"]), virial=False)
+        acc = _errors(st.energy.cpu().numpy(), F, ref["E"], ref["F"], ref["E_atom"], b.atom_ptr)
+        acc["reference"] = "FP64 oracle at the final configuration (full evaluation)"
+    else:
+        acc = sampled_accuracy(bf, desc, params, F, 12)
+    return {"workload": f"li3po4-md-{n_atoms} (Li3PO4-like crystal, {n_atoms} atoms, r_cut 5 A, MLP 2x256, "
+                        f"NVT 600 K, dt 0.5 fs, NHC 3/2/3, skin 0.5 A)",
+            "precision": precision, "step": "whole MD step (thermostat, Verlet, skin test, rebuilds, E/F)",
+            "value": n_atoms * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+            "us_per_atom_per_step": us_atom_step, "steps": steps, "n_inner": n_inner,
+            "neighbour_builds": builds, "launches_per_step": launches_per_step,
+            "launch_mode": "cuda-graph replay of n_inner steps", "accuracy": acc,
+            "paper_context": {"us_per_atom_per_step": {"192": 10.1, "5184": 2.3},
+                              "hardware": "V100, Apax JAX MD engine (Table li3po4_perf)"}}
+
+
 # ----------------------------------------------------------------------------- CPU (oracle)
 
 def oracle_step_seconds(cfg, budget_s, max_evals=None, keep=False):
@@ -830,6 +907,11 @@ def main():
             if prec == "mixed" and not _mixed_available():
                 continue
             variants.append(run_train(args, max(5, args.steps // 5), args.warmup, prec))
+        for n_md in (192, 5184):
+            for prec in ("fp32", "mixed"):
+                if prec == "mixed" and not _mixed_available():
+                    continue
+                variants.append(run_md(args, n_md, prec))
 
     if rank != 0:
         if world > 1:
@@ -870,6 +952,10 @@ def print_summary(line):
     for v in line.get("variants", []):
         rows.append(("variant", v["workload"].split(" ")[0], v.get("precision"), v["value"], v["ms_per_step"],
                      v.get("accuracy"), v.get("roofline_frac"), (v.get("memory") or {}).get("peak_bytes")))
+        if "us_per_atom_per_step" in v:
+            log(f"         {v['workload'].split(' ')[0]} {v['precision']}: {v['us_per_atom_per_step']:.4f} us/atom/step, "
+                f"{v['neighbour_builds']} builds in {v['steps']} steps (paper, V100: "
+                f"{v['paper_context']['us_per_atom_per_step']})")
     for kind, wl, prec, val, ms, a, frac, mem in rows:
         a = a or {}
         err = a.get("force_rms", a.get("param_grad_rel_l2_worst_group"))

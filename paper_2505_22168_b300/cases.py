@@ -3,13 +3,16 @@
     python -m paper_2505_22168_b300.cases neighbors --workload emim1536 --repeat 5
     python -m paper_2505_22168_b300.cases ef --workload li3po4 --units 2048 --precision mixed
     python -m paper_2505_22168_b300.cases param_grad --workload emim-train
+    python -m paper_2505_22168_b300.cases md --workload li3po4-md --units 24 --repeat 20
 
 Each case builds its seeded synthetic system, runs the operation once to warm up (buffers,
 kernel attributes, tensor maps) and then `--repeat` more times on the current stream, checks
 the device status word and prints one line.  Workloads: `emim1536` (64 EMIM+BF4- pairs,
 r_cut 6, MLP 2x512), `li3po4` (a jittered Li3PO4-like crystal of `--units` formula units,
 8 atoms each, r_cut 6, MLP 2x512), `li3po4-batch` (256 boxes of 32-512 atoms, r_cut 5,
-MLP 2x256), `emim-train` (32 EMIM boxes of 96-384 atoms, r_cut 5, MLP 2x128).
+MLP 2x256), `emim-train` (32 EMIM boxes of 96-384 atoms, r_cut 5, MLP 2x128), `li3po4-md` (a
+Li3PO4-like crystal of `--units` formula units with the batch model, r_cut 5, MLP 2x256; the
+`md` operation runs `--repeat` NVT steps at 600 K, dt 0.5 fs, skin 0.5 A after gm_md_init).
 """
 from __future__ import annotations
 
@@ -36,6 +39,10 @@ def workload(name: str, units: int):
         return synth.config(3)
     if name == "emim-train":
         return synth.config(4)
+    if name == "li3po4-md":
+        b = make_batch([li3po4_crystal(units, 4242, sigma=0.05)], 3)
+        _, d, p = synth.config(3)
+        return b, d, p
     if name == "li3po4":
         b = make_batch([li3po4_crystal(units, 77, sigma=0.1)], 3)
         d = model_desc(3, 512, 6.0, "silu")
@@ -46,7 +53,7 @@ def workload(name: str, units: int):
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("op", choices=["neighbors", "ef", "param_grad"])
+    ap.add_argument("op", choices=["neighbors", "ef", "param_grad", "md"])
     ap.add_argument("--workload", default="emim1536")
     ap.add_argument("--units", type=int, default=2048, help="Li3PO4 formula units (8 atoms each)")
     ap.add_argument("--precision", choices=["fp32", "mixed"], default="mixed")
@@ -60,6 +67,20 @@ def main(argv=None):
     if args.tune:
         m.set_tuning(**{k: int(v) for k, v in (t.split("=") for t in args.tune)})
     s = DeviceSystem(b)
+    if args.op == "md":
+        from synth.params import maxwell_boltzmann
+        from synth.systems import species_masses
+        from . import MDParams, MDState
+        masses = species_masses("li3po4")
+        mp = MDParams(dt=0.5, skin=0.5, temperature=600.0, ensemble="nvt")
+        nl = m.md_neighbor_list(s, mp)
+        st = MDState(s, masses, maxwell_boltzmann(masses[b.species], b.atom_ptr, 600.0, 4242))
+        m.md_init(s, nl, mp, st)
+        m.md_run(s, nl, mp, st, args.repeat)
+        m.check_status()
+        torch.cuda.synchronize()
+        print(f"ok md {args.workload} atoms={b.n_atoms} steps={args.repeat} builds={int(st.n_builds.item())}")
+        return
     nl = m.build_neighbors(s)
     if args.op == "neighbors":
         for _ in range(args.repeat):

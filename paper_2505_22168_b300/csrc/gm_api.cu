@@ -281,14 +281,14 @@ size_t ef_workspace_bytes(int B, int N, int H, int E) {
 
 // MD: the neighbour build's workspace (with the search slab for the list's capacity), the
 // energy/force workspace, and the integrator's words (skin flag, kinetic-energy accumulators,
-// per-structure thermostat factors)
+// per-structure thermostat velocity factors)
 struct MdWs {
     void *nl;
     size_t nl_bytes;
     EfWs ef;
     int32_t *flag;
     unsigned long long *acc;
-    double *pending, *factor;
+    double *pending;
 };
 
 MdWs carve_md(Carve &c, int B, int N, int H, int64_t cap) {
@@ -299,7 +299,6 @@ MdWs carve_md(Carve &c, int B, int N, int H, int64_t cap) {
     w.flag = c.take<int32_t>(64);
     w.acc = c.take<unsigned long long>(reduce_acc_words(B));
     w.pending = c.take<double>(B);
-    w.factor = c.take<double>(B);
     return w;
 }
 
@@ -882,7 +881,8 @@ gm_status gm_md_init(const gm_model *m, const gm_system *sys, gm_nlist *nl, cons
     nve.ensemble = GM_MD_NVE;     // kinetic energies only: no thermostat step here
     StageScope sc(ST_MD, st);
     md_kick_ke(N, B, sys->atom_ptr, sys->species, state->mass, state->forces, nve, 0, state->vel, state->pos,
-               state->pos_ref, w.flag, w.acc, state->kinetic, state->chain, w.pending, state->n_builds, status, st);
+               state->pos_ref, w.flag, w.acc, state->kinetic, state->chain, w.pending, state->n_builds, 1, status,
+               st);
     return launch_status();
 }
 
@@ -905,9 +905,8 @@ gm_status gm_md_run(const gm_model *m, const gm_system *sys, gm_nlist *nl, const
     for (int k = 0; k < n_steps; ++k) {
         {
             StageScope sc(ST_MD, st);
-            if (nvt) md_thermo(B, sys->atom_ptr, *params, state->chain, state->kinetic, w.pending, w.factor, k == 0,
-                               status, st);
-            md_kick_drift(N, B, sys->atom_ptr, sys->species, state->mass, state->forces, nvt ? w.factor : nullptr,
+            if (nvt && k == 0) md_thermo(B, sys->atom_ptr, *params, state->chain, state->kinetic, w.pending, status, st);
+            md_kick_drift(N, B, sys->atom_ptr, sys->species, state->mass, state->forces, nvt ? w.pending : nullptr,
                           *params, state->vel, state->pos, state->pos_ref, w.flag, status, st);
         }
         {
@@ -920,8 +919,8 @@ gm_status gm_md_run(const gm_model *m, const gm_system *sys, gm_nlist *nl, const
             return s;
         StageScope sc(ST_MD, st);
         md_kick_ke(N, B, sys->atom_ptr, sys->species, state->mass, state->forces, *params, 1, state->vel, state->pos,
-                   state->pos_ref, w.flag, w.acc, state->kinetic, state->chain, w.pending, state->n_builds, status,
-                   st);
+                   state->pos_ref, w.flag, w.acc, state->kinetic, state->chain, w.pending, state->n_builds,
+                   k == n_steps - 1, status, st);
     }
     if (nvt && n_steps > 0) {
         StageScope sc(ST_MD, st);

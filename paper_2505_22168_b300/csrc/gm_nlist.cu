@@ -1563,6 +1563,13 @@ __global__ void __launch_bounds__(NL_THREADS, 2) k_nl_coop(NlArgs a) {
     run_phase(a, PH_FILL, bid, nb, nl_smem);
 }
 
+// zero p[0..n) when *gate != 0 (the cleared words of a gated build)
+__global__ void __launch_bounds__(256) k_nl_zero_gated(int32_t *p, int n, const int32_t *gate) {
+    griddep_wait();
+    if (*reinterpret_cast<const volatile int32_t *>(gate) == 0) return;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) p[q] = 0;
+}
+
 __global__ void __launch_bounds__(NL_THREADS, 2) k_nl_phase(NlArgs a, int ph) {
     extern __shared__ float4 nl_smem[];
     if (nl_gated_off(a)) return;
@@ -1723,8 +1730,15 @@ gm_status nl_build(const gm_system &sys, double r_cut, int n_species, gm_nlist &
 
     NlDevice &dev = nl_device();
     const int ncmax = N + B;
-    // cell histogram and barrier words start at zero
-    if (cudaMemsetAsync(w.ccount, 0, sizeof(int32_t) * ((size_t)ncmax + 64), st) != cudaSuccess) return GM_ERR_CUDA;
+    // cell histogram and barrier words start at zero (a gated build clears them only when it
+    // will run: a kernel that reads the gate, in place of the memset)
+    if (gate) {
+        const int n0 = ncmax + 64;
+        launch_pdl(k_nl_zero_gated, dim3((n0 + 1023) / 1024), dim3(256), 0, st, w.ccount, n0, gate);
+        note_launches(1);
+    } else if (cudaMemsetAsync(w.ccount, 0, sizeof(int32_t) * ((size_t)ncmax + 64), st) != cudaSuccess) {
+        return GM_ERR_CUDA;
+    }
     a.small = (N + B <= NL_SCAN_ONE_BLOCK && B <= 256) ? 1 : 0;
     // brute-force search (small systems, single-image boxes; decided on the device) unless the
     // work items are set to cells, or there is no slab

@@ -292,3 +292,12 @@ def species_masses(kind: str) -> np.ndarray:
     for el, idx in table.items():
         out[idx] = _MASS[el]
     return out
+
+
+def supercell(structure, reps: int):
+    """(pos, species, cell) of a reps x reps x reps periodic supercell of one structure."""
+    pos, spec, cell = (np.asarray(x) for x in structure)
+    shifts = np.array([(i, j, k) for i in range(reps) for j in range(reps) for k in range(reps)], np.float64)
+    off = shifts @ cell
+    big = (pos[None, :, :] + off[:, None, :]).reshape(-1, 3)
+    return big, np.tile(spec, len(shifts)), cell * reps

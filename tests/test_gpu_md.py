@@ -64,8 +64,10 @@ def _oracle_md(b, d, p, masses, vel, params, n_steps):
 
 
 # bounds after the run: the FP32 path's forces are within ~1e-6 of the FP64 ones, the mixed
-# path's within ~1e-3; over tens of steps that moves atoms by ~1e-9 and ~1e-6 A
-BOUNDS = {"fp32": {"pos": 1e-6, "vel": 1e-7, "ke": 1e-6, "chain": 1e-5},
+# path's within ~1e-3; over tens of steps that moves atoms by ~1e-9 and ~1e-6 A.  The
+# thermostat chain itself runs in FP32 on both paths (its thermostat positions in FP64), so
+# its state carries FP32 rounding, amplified by a strongly coupled chain (tau = 10 steps).
+BOUNDS = {"fp32": {"pos": 1e-6, "vel": 1e-7, "ke": 1e-6, "chain": 1e-4},
           "mixed": {"pos": 1e-4, "vel": 1e-5, "ke": 1e-4, "chain": 1e-3}}
 
 
