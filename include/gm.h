@@ -182,10 +182,18 @@ GM_API void gm_model_destroy(gm_model *m);
  *                       all at least 2 r_cut long: brute force over each structure's atoms,
  *                       same rows), 1 = one home cell (part) per block with shared staging,
  *                       2 = one per warp, 3 = brute force where possible, else as 0
+ *   GM_TUNE_DEBUG_STALL 0 (default).  For tests of failure reporting only: 1 makes block 0 of
+ *                       the cooperative neighbour build return before the first grid barrier,
+ *                       so the other blocks' bounded waits run out; 2 makes the first network
+ *                       GEMM of gm_energy_forces (mixed path) issue no operand loads, so its MMA
+ *                       and epilogue waits run out.  Either way GM_ERR_TIMEOUT is written to
+ *                       *status_dev after about a second and every block returns; nothing
+ *                       asynchronous is in flight when a wait gives up, and the next call with
+ *                       the knob at 0 is unaffected.
  * Errors: GM_ERR_ARG for an unknown key or value. */
 enum { GM_TUNE_PAIR_TPA = 0, GM_TUNE_SPLIT_MASK = 1, GM_TUNE_GEMM_BN = 2, GM_TUNE_NL_MODE = 3, GM_TUNE_NL_SPLIT = 4,
        GM_TUNE_NL_BLOCKS = 5, GM_TUNE_NL_TWO_PASS = 6, GM_TUNE_NL_ITEMS = 7, GM_TUNE_GEMM_CPS = 8,
-       GM_TUNE_PG_SPLIT_MASK = 9 };
+       GM_TUNE_PG_SPLIT_MASK = 9, GM_TUNE_DEBUG_STALL = 10 };
 enum { GM_NL_MODE_AUTO = 0, GM_NL_MODE_PHASES = 1 };
 GM_API gm_status gm_model_set_tuning(gm_model *m, int32_t key, int32_t value);
 

@@ -157,6 +157,7 @@ GM_TUNE_PAIR_TPA, GM_TUNE_SPLIT_MASK, GM_TUNE_GEMM_BN = 0, 1, 2
 GM_TUNE_NL_MODE, GM_TUNE_NL_SPLIT, GM_TUNE_NL_BLOCKS, GM_TUNE_NL_TWO_PASS, GM_TUNE_NL_ITEMS = 3, 4, 5, 6, 7
 GM_TUNE_GEMM_CPS = 8
 GM_TUNE_PG_SPLIT_MASK = 9
+GM_TUNE_DEBUG_STALL = 10
 GM_NL_MODE_AUTO, GM_NL_MODE_PHASES = 0, 1
 
 

@@ -116,6 +116,7 @@ struct gm_model {
     int pg_split_mask;     // the same for the four network GEMMs of the parameter gradient
     int gemm_bn;           // tensor-core tile width (0 = by size)
     int gemm_cps;          // tensor-core GEMM blocks per SM (0 = by tile count)
+    int debug_stall;       // GM_TUNE_DEBUG_STALL (failure-reporting tests)
     NlTuning nl;           // neighbour build launch shape
     float *b1, *b2, *w3, *b3, *sigma, *mu;
     float *w3e, *b3e;      // ensemble heads: w3e [E][H] (member-major), b3e [E]; w3 and b3 hold
@@ -485,6 +486,7 @@ gm_status gm_model_create(const gm_model_desc *d, gm_model **out) {
     m->pg_split_mask = 15;
     m->gemm_bn = 0;
     m->gemm_cps = 0;
+    m->debug_stall = 0;
     m->nl = NlTuning();
     Layout L = model_layout(m->S, m->H, m->E);
     m->buf_bytes = L.total;
@@ -546,6 +548,11 @@ gm_status gm_model_set_tuning(gm_model *m, int32_t key, int32_t value) {
     case GM_TUNE_PG_SPLIT_MASK:
         if (value < 0 || value > 15) return fail(GM_ERR_ARG, "split mask must be in 0..15");
         m->pg_split_mask = value;
+        return GM_OK;
+    case GM_TUNE_DEBUG_STALL:
+        if (value < 0 || value > 2) return fail(GM_ERR_ARG, "debug stall must be 0, 1 or 2");
+        m->debug_stall = value;
+        m->nl.debug_stall = value == 1 ? 1 : 0;
         return GM_OK;
     case GM_TUNE_GEMM_BN:
         if (value != 0 && value != 64 && value != 128 && value != 256) return fail(GM_ERR_ARG, "bad GEMM tile width");
@@ -673,9 +680,11 @@ static gm_status network_fwd_bwd(const gm_model *m, const gm_system *sys, EfWs &
             e.out0 = A1;
             e.out1 = D1;
             e.lo_out = (sp & 2) != 0;   // lo halves only where the consuming GEMM runs split
+            e.debug_stall = m->debug_stall == 2 ? 1 : 0;
             StageScope sc(ST_GEMM_L1, st);
             if ((s = gemm_bf16(EPI_L1, m->d.activation, G, m->W1t_h, Mp, H, NFP, (sp & 1) != 0, e, status, st, m->gemm_bn, m->gemm_cps)) != GM_OK)
                 return fail(s, "tcgen05 GEMM L1 failed");
+            e.debug_stall = 0;
         }
         e.bias = m->b2;
         e.out0 = dZ2;

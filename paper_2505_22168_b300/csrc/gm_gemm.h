@@ -42,6 +42,8 @@ struct EpiArgs {
     const float *mu, *b3;    // [S], [1]
     unsigned long long *red_acc;
     double *energy;          // [n_structures]
+    int debug_stall;         // tcgen05 path, tests of failure reporting: the producer issues no
+                             // loads, so the MMA and epilogue waits run out (nothing in flight)
 };
 // BF16 operands of the tcgen05 path are stored as hi/lo pairs, [rows][2K]: columns [0, K)
 // hold hi = bf16(x), columns [K, 2K) hold lo = bf16(x - hi).  A GEMM run with split = 0

@@ -354,10 +354,12 @@ __global__ void __launch_bounds__(256, CPS)
     const uint32_t tmem = *tmem_slot;
     griddep_wait();                         // operands and epilogue inputs come from earlier kernels
 
+    // tests of failure reporting: a producer that issues nothing (no copy is ever in flight)
+    const int KB_LOAD = e.debug_stall ? 0 : KB;
     if (warp == 0 && lane == 0 && fused) {
         // ---------------- TMA producer, fused split: one stage pair per K block
         int issued = 0;
-        for (int kb = 0; kb < KB; ++kb) {
+        for (int kb = 0; kb < KB_LOAD; ++kb) {
             const int s = kb % FST;
             if (kb >= FST && !mbar_wait(empty + s, ((kb / FST) - 1) & 1, abort_flag)) {
                 *abort_flag = 1;
@@ -404,7 +406,7 @@ __global__ void __launch_bounds__(256, CPS)
     } else if (warp == 0 && lane == 0) {
         // ---------------- TMA producer
         int issued = 0;
-        for (int kb = 0; kb < KB; ++kb) {
+        for (int kb = 0; kb < KB_LOAD; ++kb) {
             const int s = kb % STAGES;
             if (kb >= STAGES && !mbar_wait(empty + s, ((kb / STAGES) - 1) & 1, abort_flag)) {
                 *abort_flag = 1;

@@ -85,6 +85,7 @@ struct NlTuning {
     int blocks = 0;               // blocks of the cooperative launch (0 = by size)
     int two_pass = 0;             // 1: count and fill passes even when the workspace holds the slab
     int items = 0;                // search work items: 0 = by size, 1 = per block, 2 = per warp, 3 = brute force
+    int debug_stall = 0;          // 1: block 0 of the cooperative build skips the grid barriers (tests)
 };
 const NlTuning &nl_tuning(const gm_model *m);
 size_t nl_workspace_bytes(int n_struct, int n_atoms, int64_t capacity);   // with the search slab

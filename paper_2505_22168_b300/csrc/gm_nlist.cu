@@ -121,6 +121,7 @@ struct NlArgs {
     unsigned *bar;          // grid barrier: [0] arrivals, [1] generation
     int32_t *status;
     const int32_t *gate;    // if not null: build only when *gate != 0 (written by an earlier kernel)
+    int debug_stall;        // tests of failure reporting: block 0 returns before the first barrier
 };
 
 // A gated build (the skin test of an MD step decides on the device whether the list is
@@ -1492,6 +1493,10 @@ __global__ void __launch_bounds__(NL_THREADS, 2) k_nl_coop(NlArgs a) {
     extern __shared__ float4 nl_smem[];
     const int bid = blockIdx.x, nb = gridDim.x;
     if (nl_gated_off(a)) return;
+    // failure-reporting tests: block 0 never arrives, so every other block's first (bounded)
+    // grid barrier runs out and it returns with GM_ERR_TIMEOUT; the next build's memset
+    // resets the barrier words
+    if (a.debug_stall && bid == 0 && nb > 1) return;
     if (a.mid) {
         // every block sets up the grids; the brute-force search when the boxes allow it, else
         // (or after a row longer than BR_CAP) the phases below from the binning on -- the
@@ -1727,6 +1732,7 @@ gm_status nl_build(const gm_system &sys, double r_cut, int n_species, gm_nlist &
     a.bar = w.bar;
     a.status = status;
     a.gate = gate;
+    a.debug_stall = tune.debug_stall;
 
     NlDevice &dev = nl_device();
     const int ncmax = N + B;
