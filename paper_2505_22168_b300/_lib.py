@@ -158,6 +158,7 @@ GM_TUNE_NL_MODE, GM_TUNE_NL_SPLIT, GM_TUNE_NL_BLOCKS, GM_TUNE_NL_TWO_PASS, GM_TU
 GM_TUNE_GEMM_CPS = 8
 GM_TUNE_PG_SPLIT_MASK = 9
 GM_TUNE_DEBUG_STALL = 10
+GM_TUNE_F16_BACKWARD = 11
 GM_NL_MODE_AUTO, GM_NL_MODE_PHASES = 0, 1
 
 

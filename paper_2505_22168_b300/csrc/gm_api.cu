@@ -112,7 +112,9 @@ struct gm_model {
     float *W2t;            // [H][H]    forward  (B[n][k] = W2[k][n])
     float *W2;             // [H][H]    backward (B[n][k] = W2[n][k])
     __nv_bfloat16 *W1t_h, *W1p_h, *W2t_h, *W2_h;   // BF16 hi/lo pairs, rows [hi(K) | lo(K)]
+    __half *W1p_f, *W2_f;  // FP16 copies of the backward weights, rows [fp16(K) | 0]
     int split_mask;        // GEMMs run with three hi/lo passes: 1 L1, 2 L2, 4 B1, 8 B0
+    int f16_backward;      // backward GEMMs B1, B0 on FP16 operands in one pass (else split BF16)
     int pg_split_mask;     // the same for the four network GEMMs of the parameter gradient
     int gemm_bn;           // tensor-core tile width (0 = by size)
     int gemm_cps;          // tensor-core GEMM blocks per SM (0 = by tile count)
@@ -126,7 +128,7 @@ struct gm_model {
 namespace {
 
 struct Layout {
-    size_t beta, W1t, W1p, W2t, W2, W1t_h, W1p_h, W2t_h, W2_h, b1, b2, w3, b3, sigma, mu, w3e, b3e, total;
+    size_t beta, W1t, W1p, W2t, W2, W1t_h, W1p_h, W2t_h, W2_h, W1p_f, W2_f, b1, b2, w3, b3, sigma, mu, w3e, b3e, total;
 };
 
 Layout model_layout(int S, int H, int E) {
@@ -146,6 +148,8 @@ Layout model_layout(int S, int H, int E) {
     L.W1p_h = take(4 * (size_t)NFP * H);
     L.W2t_h = take(4 * (size_t)H * H);
     L.W2_h = take(4 * (size_t)H * H);
+    L.W1p_f = take(4 * (size_t)NFP * H);
+    L.W2_f = take(4 * (size_t)H * H);
     L.b1 = take(sizeof(float) * H);
     L.b2 = take(sizeof(float) * H);
     L.w3 = take(sizeof(float) * H);
@@ -178,6 +182,11 @@ ThetaOff theta_offsets(int S, int H, int E = 1) {
     return o;
 }
 
+// FP16 weight copy in the hi slot of the same [rows][2K] layout (the lo slot stays zero).
+__device__ __forceinline__ void put_f16(__half *dst, int K, int r, int k, float v) {
+    dst[(size_t)r * 2 * K + k] = __float2half_rn(v);
+}
+
 // BF16 weight copy as a hi/lo pair: row r of a [rows][K] matrix becomes [hi(K) | lo(K)].
 __device__ __forceinline__ void put_split(__nv_bfloat16 *dst, int K, int r, int k, float v) {
     const __nv_bfloat16 hi = __float2bfloat16_rn(v);
@@ -199,12 +208,14 @@ __global__ void k_repack(const float *__restrict__ th, ThetaOff o, int S, int H,
         const int64_t qp = (int64_t)f * H + h;
         m.W1p[qp] = v;
         put_split(m.W1p_h, H, f, h, v);
+        put_f16(m.W1p_f, H, f, h, v);
     }
     for (int64_t q = tid; q < (int64_t)H * H; q += stride) {
         const int r = (int)(q / H), c = (int)(q % H);
         const float v = th[o.W2 + q];  // W2[r][c]
         m.W2[q] = v;
         put_split(m.W2_h, H, r, c, v);
+        put_f16(m.W2_f, H, r, c, v);
         const int64_t qt = (int64_t)c * H + r;  // W2t[c][r] = W2[r][c]
         m.W2t[qt] = v;
         put_split(m.W2t_h, H, c, r, v);
@@ -483,6 +494,7 @@ gm_status gm_model_create(const gm_model_desc *d, gm_model **out) {
     }
     m->pair_tpa = 0;
     m->split_mask = 12;
+    m->f16_backward = 1;
     m->pg_split_mask = 15;
     m->gemm_bn = 0;
     m->gemm_cps = 0;
@@ -504,6 +516,8 @@ gm_status gm_model_create(const gm_model_desc *d, gm_model **out) {
     m->W1p_h = reinterpret_cast<__nv_bfloat16 *>(m->buf + L.W1p_h);
     m->W2t_h = reinterpret_cast<__nv_bfloat16 *>(m->buf + L.W2t_h);
     m->W2_h = reinterpret_cast<__nv_bfloat16 *>(m->buf + L.W2_h);
+    m->W1p_f = reinterpret_cast<__half *>(m->buf + L.W1p_f);
+    m->W2_f = reinterpret_cast<__half *>(m->buf + L.W2_f);
     m->b1 = reinterpret_cast<float *>(m->buf + L.b1);
     m->b2 = reinterpret_cast<float *>(m->buf + L.b2);
     m->w3 = reinterpret_cast<float *>(m->buf + L.w3);
@@ -548,6 +562,10 @@ gm_status gm_model_set_tuning(gm_model *m, int32_t key, int32_t value) {
     case GM_TUNE_PG_SPLIT_MASK:
         if (value < 0 || value > 15) return fail(GM_ERR_ARG, "split mask must be in 0..15");
         m->pg_split_mask = value;
+        return GM_OK;
+    case GM_TUNE_F16_BACKWARD:
+        if (value != 0 && value != 1) return fail(GM_ERR_ARG, "FP16 backward flag must be 0 or 1");
+        m->f16_backward = value;
         return GM_OK;
     case GM_TUNE_DEBUG_STALL:
         if (value < 0 || value > 2) return fail(GM_ERR_ARG, "debug stall must be 0, 1 or 2");
@@ -686,10 +704,16 @@ static gm_status network_fwd_bwd(const gm_model *m, const gm_system *sys, EfWs &
                 return fail(s, "tcgen05 GEMM L1 failed");
             e.debug_stall = 0;
         }
+        // backward operands: FP16 in one pass (they are bounded: |dE/dz| <= |sigma w3| max phi'),
+        // or BF16 hi/lo split as the split mask says
+        const int f16 = m->f16_backward;
+        const bf *W2b = f16 ? reinterpret_cast<const bf *>(m->W2_f) : m->W2_h;
+        const bf *W1b = f16 ? reinterpret_cast<const bf *>(m->W1p_f) : m->W1p_h;
         e.bias = m->b2;
         e.out0 = dZ2;
         e.out1 = nullptr;
-        e.lo_out = (sp & 4) != 0;
+        e.lo_out = f16 ? 0 : (sp & 4) != 0;
+        e.out_f16 = f16;
         {
             StageScope sc(ST_GEMM_L2, st);
             if ((s = gemm_bf16(l2, m->d.activation, A1, m->W2t_h, Mp, H, H, (sp & 2) != 0, e, status, st, m->gemm_bn, m->gemm_cps)) != GM_OK)
@@ -697,7 +721,7 @@ static gm_status network_fwd_bwd(const gm_model *m, const gm_system *sys, EfWs &
         }
         e.out0 = dZ1;
         e.aux = D1;
-        e.lo_out = (sp & 8) != 0;
+        e.lo_out = f16 ? 0 : (sp & 8) != 0;
         if (energy) {
             e.atom_ptr = sys->atom_ptr;
             e.n_structures = sys->n_structures;
@@ -708,14 +732,17 @@ static gm_status network_fwd_bwd(const gm_model *m, const gm_system *sys, EfWs &
         }
         {
             StageScope sc(ST_GEMM_B1, st);
-            if ((s = gemm_bf16(EPI_B1, 0, dZ2, m->W2_h, Mp, H, H, (sp & 4) != 0, e, status, st, m->gemm_bn, m->gemm_cps)) != GM_OK)
+            if ((s = gemm_bf16(EPI_B1, 0, dZ2, W2b, Mp, H, H, f16 ? 0 : (sp & 4) != 0, e, status, st, m->gemm_bn,
+                               m->gemm_cps, f16)) != GM_OK)
                 return fail(s, "tcgen05 GEMM B1 failed");
         }
         e.out0 = w.dG;
         e.energy = nullptr;
+        e.out_f16 = 0;
         {
             StageScope sc(ST_GEMM_B0, st);
-            if ((s = gemm_bf16(EPI_STORE, 0, dZ1, m->W1p_h, Mp, NFP, H, (sp & 8) != 0, e, status, st, m->gemm_bn, m->gemm_cps)) != GM_OK)
+            if ((s = gemm_bf16(EPI_STORE, 0, dZ1, W1b, Mp, NFP, H, f16 ? 0 : (sp & 8) != 0, e, status, st, m->gemm_bn,
+                               m->gemm_cps, f16)) != GM_OK)
                 return fail(s, "tcgen05 GEMM B0 failed");
         }
         return GM_OK;

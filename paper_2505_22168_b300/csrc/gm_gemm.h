@@ -44,6 +44,8 @@ struct EpiArgs {
     double *energy;          // [n_structures]
     int debug_stall;         // tcgen05 path, tests of failure reporting: the producer issues no
                              // loads, so the MMA and epilogue waits run out (nothing in flight)
+    int out_f16;             // tcgen05 L2/L2E/B1: write the output as FP16 in the hi slot of the
+                             // [M][2N] layout (the FP16 backward GEMMs read it in one pass)
 };
 // BF16 operands of the tcgen05 path are stored as hi/lo pairs, [rows][2K]: columns [0, K)
 // hold hi = bf16(x), columns [K, 2K) hold lo = bf16(x - hi).  A GEMM run with split = 0
@@ -61,8 +63,11 @@ void gemm_f32(int epi, int act, const float *A, const float *B, int M, int N, in
 // forced_bn = 0 picks the tile width from the problem size (64, 128 or 256 columns).
 // forced_cps = 0 picks one or two CTAs per SM from the tile count (two halve the stage ring
 // and overlap one CTA's epilogue with the other's main loop).
+// f16 = 1: A and B hold FP16 (not BF16) in their hi slots, read in one pass (split must be 0;
+// one MMA always takes both operands in the same type)
 gm_status gemm_bf16(int epi, int act, const __nv_bfloat16 *A, const __nv_bfloat16 *B, int M, int N, int K, int split,
-                    const EpiArgs &e, int32_t *status, cudaStream_t st, int forced_bn = 0, int forced_cps = 0);
+                    const EpiArgs &e, int32_t *status, cudaStream_t st, int forced_bn = 0, int forced_cps = 0,
+                    int f16 = 0);
 int tc_choose_bn(int M, int N, int forced);
 
 }  // namespace gm

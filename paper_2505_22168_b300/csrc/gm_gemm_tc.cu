@@ -57,7 +57,7 @@ bool tensor_map(const void *base, int inner, int rows, int box_rows, CUtensorMap
 
 template <int BN, int EPI, int ACT, int CPS>
 cudaError_t launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, int M, int N, int K, int split,
-                      const EpiArgs &e, int32_t *status, cudaStream_t st) {
+                      const EpiArgs &e, int32_t *status, cudaStream_t st, int f16) {
     static bool attr_set = false;
     const size_t smem = tc::smem_bytes_for(BN, CPS);
     if (!attr_set) {
@@ -67,33 +67,33 @@ cudaError_t launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, int M, int N
         attr_set = true;
     }
     dim3 grid(N / BN, M / tc::BM);
-    launch_pdl(tc::k_gemm_tc<BN, EPI, ACT, CPS>, grid, dim3(256), smem, st, ma, mb, M, N, K, split, e, status);
+    launch_pdl(tc::k_gemm_tc<BN, EPI, ACT, CPS>, grid, dim3(256), smem, st, ma, mb, M, N, K, split, e, status, f16);
     return cudaPeekAtLastError();
 }
 
 template <int BN, int CPS>
 cudaError_t dispatch_epi(int epi, int act, const CUtensorMap &ma, const CUtensorMap &mb, int M, int N, int K,
-                         int split, const EpiArgs &e, int32_t *status, cudaStream_t st) {
+                         int split, const EpiArgs &e, int32_t *status, cudaStream_t st, int f16) {
     switch (epi) {
     case EPI_L1:
-        return act == 0 ? launch_tc<BN, EPI_L1, 0, CPS>(ma, mb, M, N, K, split, e, status, st)
-                        : launch_tc<BN, EPI_L1, 1, CPS>(ma, mb, M, N, K, split, e, status, st);
+        return act == 0 ? launch_tc<BN, EPI_L1, 0, CPS>(ma, mb, M, N, K, split, e, status, st, f16)
+                        : launch_tc<BN, EPI_L1, 1, CPS>(ma, mb, M, N, K, split, e, status, st, f16);
     case EPI_L2:
-        return act == 0 ? launch_tc<BN, EPI_L2, 0, CPS>(ma, mb, M, N, K, split, e, status, st)
-                        : launch_tc<BN, EPI_L2, 1, CPS>(ma, mb, M, N, K, split, e, status, st);
+        return act == 0 ? launch_tc<BN, EPI_L2, 0, CPS>(ma, mb, M, N, K, split, e, status, st, f16)
+                        : launch_tc<BN, EPI_L2, 1, CPS>(ma, mb, M, N, K, split, e, status, st, f16);
     case EPI_L2E:
-        return act == 0 ? launch_tc<BN, EPI_L2E, 0, CPS>(ma, mb, M, N, K, split, e, status, st)
-                        : launch_tc<BN, EPI_L2E, 1, CPS>(ma, mb, M, N, K, split, e, status, st);
-    case EPI_B1: return launch_tc<BN, EPI_B1, 0, CPS>(ma, mb, M, N, K, split, e, status, st);
-    default: return launch_tc<BN, EPI_STORE, 0, CPS>(ma, mb, M, N, K, split, e, status, st);
+        return act == 0 ? launch_tc<BN, EPI_L2E, 0, CPS>(ma, mb, M, N, K, split, e, status, st, f16)
+                        : launch_tc<BN, EPI_L2E, 1, CPS>(ma, mb, M, N, K, split, e, status, st, f16);
+    case EPI_B1: return launch_tc<BN, EPI_B1, 0, CPS>(ma, mb, M, N, K, split, e, status, st, f16);
+    default: return launch_tc<BN, EPI_STORE, 0, CPS>(ma, mb, M, N, K, split, e, status, st, f16);
     }
 }
 
 template <int BN>
 cudaError_t dispatch_cps(int cps, int epi, int act, const CUtensorMap &ma, const CUtensorMap &mb, int M, int N,
-                         int K, int split, const EpiArgs &e, int32_t *status, cudaStream_t st) {
-    return cps == 2 ? dispatch_epi<BN, 2>(epi, act, ma, mb, M, N, K, split, e, status, st)
-                    : dispatch_epi<BN, 1>(epi, act, ma, mb, M, N, K, split, e, status, st);
+                         int K, int split, const EpiArgs &e, int32_t *status, cudaStream_t st, int f16) {
+    return cps == 2 ? dispatch_epi<BN, 2>(epi, act, ma, mb, M, N, K, split, e, status, st, f16)
+                    : dispatch_epi<BN, 1>(epi, act, ma, mb, M, N, K, split, e, status, st, f16);
 }
 
 }  // namespace
@@ -115,9 +115,10 @@ int tc_choose_cps(int M, int N, int bn, int forced) {
 }
 
 gm_status gemm_bf16(int epi, int act, const __nv_bfloat16 *A, const __nv_bfloat16 *B, int M, int N, int K, int split,
-                    const EpiArgs &e, int32_t *status, cudaStream_t st, int forced_bn, int forced_cps) {
+                    const EpiArgs &e, int32_t *status, cudaStream_t st, int forced_bn, int forced_cps, int f16) {
     if (M <= 0) return GM_OK;
     if (M % tc::BM || K % tc::BK || N % 64 || M / tc::BM > 65535) return GM_ERR_UNSUPPORTED;
+    if (f16 && split) return GM_ERR_UNSUPPORTED;      // FP16 operands are read in one pass
     const int bn = tc_choose_bn(M, N, forced_bn);
     const int cps = tc_choose_cps(M, N, bn, forced_cps);
     CUtensorMap ma, mb;
@@ -125,9 +126,9 @@ gm_status gemm_bf16(int epi, int act, const __nv_bfloat16 *A, const __nv_bfloat1
     if (!tensor_map(A, 2 * K, M, tc::BM, &ma) || !tensor_map(B, 2 * K, N, bn, &mb)) return GM_ERR_CUDA;
     cudaError_t err;
     switch (bn) {
-    case 256: err = dispatch_cps<256>(cps, epi, act, ma, mb, M, N, K, split, e, status, st); break;
-    case 128: err = dispatch_cps<128>(cps, epi, act, ma, mb, M, N, K, split, e, status, st); break;
-    default: err = dispatch_cps<64>(cps, epi, act, ma, mb, M, N, K, split, e, status, st); break;
+    case 256: err = dispatch_cps<256>(cps, epi, act, ma, mb, M, N, K, split, e, status, st, f16); break;
+    case 128: err = dispatch_cps<128>(cps, epi, act, ma, mb, M, N, K, split, e, status, st, f16); break;
+    default: err = dispatch_cps<64>(cps, epi, act, ma, mb, M, N, K, split, e, status, st, f16); break;
     }
     note_launches(1);
     return err == cudaSuccess ? GM_OK : GM_ERR_CUDA;

@@ -110,6 +110,10 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
 __host__ __device__ constexpr uint32_t instr_desc(int bn) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
+// the same with A and B FP16 (format code 0 in both operand fields)
+__host__ __device__ constexpr uint32_t instr_desc_f16(int bn) {
+    return (1u << 4) | ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
 
 __device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                           uint32_t accumulate) {
@@ -164,6 +168,17 @@ __device__ __forceinline__ void pack8_split(const float *x, uint4 &hi, uint4 &lo
     }
     hi = pack8_bf16(h);
     lo = pack8_bf16(l);
+}
+
+__device__ __forceinline__ uint4 pack8_f16(const float *x) {
+    uint4 o;
+    __half2 h0 = __floats2half2_rn(x[0], x[1]), h1 = __floats2half2_rn(x[2], x[3]);
+    __half2 h2 = __floats2half2_rn(x[4], x[5]), h3 = __floats2half2_rn(x[6], x[7]);
+    o.x = *reinterpret_cast<uint32_t *>(&h0);
+    o.y = *reinterpret_cast<uint32_t *>(&h1);
+    o.z = *reinterpret_cast<uint32_t *>(&h2);
+    o.w = *reinterpret_cast<uint32_t *>(&h3);
+    return o;
 }
 
 __device__ __forceinline__ void unpack8_bf16(uint4 u, float *x) {
@@ -287,17 +302,22 @@ __device__ __forceinline__ void epilogue32(const EpiArgs &e, int row0, int n, in
             }
         }
     }
+    const bool f16 = EPI != EPI_L1 && e.out_f16;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        uint4 hi, lo;
-        pack8_split(y + 8 * q, hi, lo);
-        sg.hi[lane][q] = hi;
-        sg.lo[lane][q] = lo;
+        if (f16) {
+            sg.hi[lane][q] = pack8_f16(y + 8 * q);
+        } else {
+            uint4 hi, lo;
+            pack8_split(y + 8 * q, hi, lo);
+            sg.hi[lane][q] = hi;
+            sg.lo[lane][q] = lo;
+        }
     }
     __syncwarp();
     __nv_bfloat16 *ob = static_cast<__nv_bfloat16 *>(e.out0);
     warp_store_bf16(sg.hi, ob, row0, 2 * (size_t)N, n, lane);
-    if (e.lo_out) warp_store_bf16(sg.lo, ob + N, row0, 2 * (size_t)N, n, lane);
+    if (e.lo_out && !f16) warp_store_bf16(sg.lo, ob + N, row0, 2 * (size_t)N, n, lane);
     if (EPI == EPI_L1) warp_store_f32(sg.d, static_cast<float *>(e.out1), row0, N, n, lane);
     __syncwarp();
 }
@@ -308,7 +328,7 @@ static_assert(8 * sizeof(EpiStage) <= ring_bytes_for(64, 2) && 8 * sizeof(EpiSta
 template <int BN, int EPI, int ACT, int CPS>
 __global__ void __launch_bounds__(256, CPS)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N, int K,
-              int split, EpiArgs e, int32_t *status) {
+              int split, EpiArgs e, int32_t *status, int f16) {
     constexpr int STAGES = stages_for(BN, CPS);
     constexpr int B_STAGE_BYTES = BN * BK * 2;
     constexpr int STAGE_BYTES = A_STAGE_BYTES + B_STAGE_BYTES;
@@ -382,7 +402,7 @@ __global__ void __launch_bounds__(256, CPS)
         }
     } else if (warp == 1 && lane == 0 && fused) {
         // ---------------- MMA issuer, fused split
-        constexpr uint32_t idesc = instr_desc(BN);
+        const uint32_t idesc = f16 ? instr_desc_f16(BN) : instr_desc(BN);
         bool ok = true;
         for (int kb = 0; kb < KB; ++kb) {
             const int s = kb % FST;
@@ -429,7 +449,7 @@ __global__ void __launch_bounds__(256, CPS)
         }
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer
-        constexpr uint32_t idesc = instr_desc(BN);
+        const uint32_t idesc = f16 ? instr_desc_f16(BN) : instr_desc(BN);
         bool ok = true;
         for (int kb = 0; kb < KB; ++kb) {
             const int s = kb % STAGES;

@@ -355,7 +355,7 @@ def test_energy_forces_mixed_split_masks(mask):
     b, d, p = synth.config(1)
     m, sysd, nl = _nl_pair(b, d, p)
     mm = _model(d, p, "mixed")
-    mm.set_tuning(split_mask=mask)
+    mm.set_tuning(split_mask=mask, f16_backward=0)     # the BF16 backward GEMMs the mask splits
     E, F, _ = mm.energy_forces(sysd, nl)
     mm.check_status()
     ref = oracle.energy_forces(b, d, p, oracle.neighbors(b, d["r_cut"]))
@@ -363,6 +363,25 @@ def test_energy_forces_mixed_split_masks(mask):
     f_rms, f_max = force_error(F.cpu().numpy().astype(np.float64), ref)
     tol = 2e-4 if mask == 15 else TOL["mixed"]       # all four GEMMs split: close to FP32
     assert e <= tol and f_rms <= tol and f_max <= ELEMENT_FACTOR * tol, (e, f_rms, f_max)
+
+
+@pytest.mark.parametrize("f16", [0, 1])
+@pytest.mark.parametrize("cfg", [1, 2])
+def test_energy_forces_mixed_backward_operand_formats(cfg, f16):
+    """The two backward network GEMMs on FP16 operands in one pass (the default) or on BF16
+    hi/lo pairs in three passes: both within the mixed tolerance of the oracle."""
+    b, d, p = synth.config(cfg)
+    m, sysd, nl = _nl_pair(b, d, p)
+    mm = _model(d, p, "mixed")
+    mm.set_tuning(f16_backward=f16)
+    E, F, W = mm.energy_forces(sysd, nl, virial=True)
+    mm.check_status()
+    ref = oracle.energy_forces(b, d, p, oracle.neighbors(b, d["r_cut"]))
+    tol = TOL["mixed"]
+    e = energy_error(E.cpu().numpy(), ref, b)
+    f_rms, f_max = force_error(F.cpu().numpy().astype(np.float64), ref)
+    assert e <= tol and f_rms <= tol and f_max <= ELEMENT_FACTOR * tol, (e, f_rms, f_max)
+    assert virial_error(W.cpu().numpy(), ref) <= tol
 
 
 @pytest.mark.parametrize("bn", [64, 128, 256])
