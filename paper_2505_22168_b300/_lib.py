@@ -159,6 +159,7 @@ GM_TUNE_GEMM_CPS = 8
 GM_TUNE_PG_SPLIT_MASK = 9
 GM_TUNE_DEBUG_STALL = 10
 GM_TUNE_F16_BACKWARD = 11
+GM_TUNE_FUSED_MLP = 12
 GM_NL_MODE_AUTO, GM_NL_MODE_PHASES = 0, 1
 
 

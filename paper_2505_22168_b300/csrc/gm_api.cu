@@ -115,6 +115,7 @@ struct gm_model {
     __half *W1p_f, *W2_f;  // FP16 copies of the backward weights, rows [fp16(K) | 0]
     int split_mask;        // GEMMs run with three hi/lo passes: 1 L1, 2 L2, 4 B1, 8 B0
     int f16_backward;      // backward GEMMs B1, B0 on FP16 operands in one pass (else split BF16)
+    int fused_mlp;         // mixed path: the four network GEMMs as one kernel (where it applies)
     int pg_split_mask;     // the same for the four network GEMMs of the parameter gradient
     int gemm_bn;           // tensor-core tile width (0 = by size)
     int gemm_cps;          // tensor-core GEMM blocks per SM (0 = by tile count)
@@ -495,6 +496,7 @@ gm_status gm_model_create(const gm_model_desc *d, gm_model **out) {
     m->pair_tpa = 0;
     m->split_mask = 12;
     m->f16_backward = 1;
+    m->fused_mlp = 2;
     m->pg_split_mask = 15;
     m->gemm_bn = 0;
     m->gemm_cps = 0;
@@ -562,6 +564,10 @@ gm_status gm_model_set_tuning(gm_model *m, int32_t key, int32_t value) {
     case GM_TUNE_PG_SPLIT_MASK:
         if (value < 0 || value > 15) return fail(GM_ERR_ARG, "split mask must be in 0..15");
         m->pg_split_mask = value;
+        return GM_OK;
+    case GM_TUNE_FUSED_MLP:
+        if (value < 0 || value > 2) return fail(GM_ERR_ARG, "fused network mode must be 0, 1 or 2");
+        m->fused_mlp = value;
         return GM_OK;
     case GM_TUNE_F16_BACKWARD:
         if (value != 0 && value != 1) return fail(GM_ERR_ARG, "FP16 backward flag must be 0 or 1");
@@ -665,6 +671,19 @@ static gm_status forward_to_features(const gm_model *m, const gm_system *sys, co
     return launch_status();
 }
 
+// The mixed path's network runs as one fused kernel (gm_mlp_fused.cuh) when the model's width
+// allows it, the backward GEMMs take FP16 and the forward ones single-pass BF16, and no
+// ensemble partial sums or other output head are asked for.
+// GM_TUNE_FUSED_MLP: 0 never, 1 always, 2 (default) by size: one CTA per 128-atom tile runs its
+// four layers one after another, so the fused kernel pays off once the tiles fill the GPU twice
+// (131,072 atoms: 1.51 -> 1.45 ms per energy/force pass); at 1536 atoms (12 tiles) the four
+// separate GEMMs, spread over ~100 CTAs each, are faster (66 against 104 us)
+static bool use_fused_mlp(const gm_model *m, bool ens, bool from_l2, const float *head, int n_atoms) {
+    const bool want = m->fused_mlp == 1 || (m->fused_mlp == 2 && (n_atoms + TILE_M - 1) / TILE_M >= 2 * 148);
+    return m->d.precision == GM_PREC_MIXED && want && m->f16_backward && mlp_fused_supported(m->H) && !ens &&
+           !from_l2 && head == nullptr && (m->split_mask & 3) == 0 && m->debug_stall == 0;
+}
+
 // The four network GEMMs: features -> energies (partial sums) and dE/dG.  energy (mixed
 // path only): the structure energies are summed inside the B1 GEMM and written there.
 //   head:      output-layer weights whose gradient is taken (null: the model's w3, which for
@@ -686,6 +705,23 @@ static gm_status network_fwd_bwd(const gm_model *m, const gm_system *sys, EfWs &
     e.n_ens = ens ? m->E : 1;
     e.w3e = m->w3e;
     e.nn_ens = w.nn_ens;
+    if (use_fused_mlp(m, ens, from_l2, head, sys->n_atoms)) {
+        FusedMlpArgs fa;
+        fa.n_atoms = sys->n_atoms;
+        fa.n_species = m->S;
+        fa.species = sys->species;
+        fa.b1 = m->b1;
+        fa.b2 = m->b2;
+        fa.w3 = m->w3;
+        fa.sigma = m->sigma;
+        fa.D1 = reinterpret_cast<__half *>(w.D1);
+        fa.nn_part = w.nn_part;
+        fa.dG = w.dG;
+        StageScope sc(ST_GEMM_L1, st);
+        gm_status s = mlp_fused(m->d.activation, Mp, H, reinterpret_cast<const __nv_bfloat16 *>(w.G), m->W1t_h,
+                                m->W2t_h, m->W2_f, m->W1p_f, fa, status, st);
+        return s == GM_OK ? GM_OK : fail(s, "fused network kernel failed");
+    }
     if (m->d.precision == GM_PREC_MIXED) {
         typedef __nv_bfloat16 bf;
         bf *G = reinterpret_cast<bf *>(w.G), *A1 = reinterpret_cast<bf *>(w.A1);
@@ -783,8 +819,10 @@ static gm_status energy_forces_pipeline(const gm_model *m, const gm_system *sys,
     const int N = sys->n_atoms, B = sys->n_structures, H = m->H;
     const int Mp = round_up(N, TILE_M);
     gm_status s;
-    // without the virial, the mixed path sums the energies inside its B1 GEMM
-    const bool fused_energy = N > 0 && virial == nullptr && m->d.precision == GM_PREC_MIXED;
+    // without the virial, the mixed path sums the energies inside its B1 GEMM (not in the fused
+    // network kernel: the reduction kernel does)
+    const bool fused_energy = N > 0 && virial == nullptr && m->d.precision == GM_PREC_MIXED &&
+                              !use_fused_mlp(m, ens, false, nullptr, N);
     if (N > 0) {
         if ((s = forward_to_features(m, sys, nl, w, nullptr, nullptr, forces, status, st)) != GM_OK) return s;
         if ((s = network_fwd_bwd(m, sys, w, Mp, status, st, fused_energy ? energy : nullptr, nullptr, ens)) != GM_OK)

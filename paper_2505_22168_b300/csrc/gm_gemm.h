@@ -70,4 +70,20 @@ gm_status gemm_bf16(int epi, int act, const __nv_bfloat16 *A, const __nv_bfloat1
                     int f16 = 0);
 int tc_choose_bn(int M, int N, int forced);
 
+// The mixed path's whole network in one tcgen05 kernel per 128-row tile (gm_mlp_fused.cuh):
+// L1 and L2 on BF16 operands (single pass), B1 and B0 on FP16 operands; a1, dZ2 and dZ1 stay
+// in shared memory.  G [M][2 NFP] BF16 (hi slots), W1t [H][2 NFP], W2t [H][2H] BF16,
+// W2 [H][2H], W1p [NFP][2H] FP16 (hi slots).  Outputs: D1 [M][H] FP16 (phi'(z1)), nn_part
+// [M][H/32], dG [M][NFP] FP32.  H must be 128, 256 or 512.
+struct FusedMlpArgs {
+    int n_atoms, n_species;
+    const int32_t *species;
+    const float *b1, *b2, *w3, *sigma;
+    __half *D1;               // [M][H] FP16 phi'(z1) (scratch)
+    float *nn_part, *dG;
+};
+bool mlp_fused_supported(int H);
+gm_status mlp_fused(int act, int M, int H, const __nv_bfloat16 *G, const __nv_bfloat16 *W1t, const __nv_bfloat16 *W2t,
+                    const __half *W2, const __half *W1p, const FusedMlpArgs &a, int32_t *status, cudaStream_t st);
+
 }  // namespace gm

@@ -6,6 +6,7 @@
 #include <tuple>
 
 #include "gm_gemm_tc.cuh"
+#include "gm_mlp_fused.cuh"
 
 namespace gm {
 
@@ -129,6 +130,58 @@ gm_status gemm_bf16(int epi, int act, const __nv_bfloat16 *A, const __nv_bfloat1
     case 256: err = dispatch_cps<256>(cps, epi, act, ma, mb, M, N, K, split, e, status, st, f16); break;
     case 128: err = dispatch_cps<128>(cps, epi, act, ma, mb, M, N, K, split, e, status, st, f16); break;
     default: err = dispatch_cps<64>(cps, epi, act, ma, mb, M, N, K, split, e, status, st, f16); break;
+    }
+    note_launches(1);
+    return err == cudaSuccess ? GM_OK : GM_ERR_CUDA;
+}
+
+namespace {
+template <int H, int ACT>
+cudaError_t launch_fused(const CUtensorMap *maps, const tc::FusedArgs &f, int32_t *status, cudaStream_t st) {
+    using Sh = tc::FusedShape<H>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t err = cudaFuncSetAttribute(tc::k_mlp_fused<H, ACT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)Sh::SMEM);
+        if (err != cudaSuccess) return err;
+        attr_set = true;
+    }
+    launch_pdl(tc::k_mlp_fused<H, ACT>, dim3(f.M / tc::BM), dim3(320), Sh::SMEM, st, maps[0], maps[1], maps[2],
+               maps[3], maps[4], f, status);
+    return cudaPeekAtLastError();
+}
+}  // namespace
+
+bool mlp_fused_supported(int H) { return H == 128 || H == 256 || H == 512; }
+
+gm_status mlp_fused(int act, int M, int H, const __nv_bfloat16 *G, const __nv_bfloat16 *W1t, const __nv_bfloat16 *W2t,
+                    const __half *W2, const __half *W1p, const FusedMlpArgs &a, int32_t *status, cudaStream_t st) {
+    if (M <= 0) return GM_OK;
+    if (M % tc::BM || !mlp_fused_supported(H) || M / tc::BM > 65535) return GM_ERR_UNSUPPORTED;
+    const int chunk = H >= 256 ? 256 : H;
+    CUtensorMap maps[5];
+    // operands in the [rows][2K] layout of the split path (hi slots read)
+    if (!tensor_map(G, 2 * NFP, M, tc::BM, &maps[0]) || !tensor_map(W1t, 2 * NFP, H, chunk, &maps[1]) ||
+        !tensor_map(W2t, 2 * H, H, chunk, &maps[2]) || !tensor_map(W2, 2 * H, H, chunk, &maps[3]) ||
+        !tensor_map(W1p, 2 * H, NFP, 128, &maps[4]))
+        return GM_ERR_CUDA;
+    tc::FusedArgs f;
+    f.M = M;
+    f.n_atoms = a.n_atoms;
+    f.n_species = a.n_species;
+    f.species = a.species;
+    f.b1 = a.b1;
+    f.b2 = a.b2;
+    f.w3 = a.w3;
+    f.sigma = a.sigma;
+    f.D1 = a.D1;
+    f.nn_part = a.nn_part;
+    f.dG = a.dG;
+    cudaError_t err;
+    switch (H) {
+    case 128: err = act == 0 ? launch_fused<128, 0>(maps, f, status, st) : launch_fused<128, 1>(maps, f, status, st); break;
+    case 256: err = act == 0 ? launch_fused<256, 0>(maps, f, status, st) : launch_fused<256, 1>(maps, f, status, st); break;
+    default: err = act == 0 ? launch_fused<512, 0>(maps, f, status, st) : launch_fused<512, 1>(maps, f, status, st); break;
     }
     note_launches(1);
     return err == cudaSuccess ? GM_OK : GM_ERR_CUDA;

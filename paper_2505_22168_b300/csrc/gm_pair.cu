@@ -349,7 +349,18 @@ __global__ void __launch_bounds__(forces_threads<TPA>(), TPA >= 8 ? 4 : 1)
                                  dB, R, Rp);
             float m[NC];
             monomials(ux, uy, uz, m);
-            float S1 = 0.0f, S2 = 0.0f, Q0 = 0.0f, Q1 = 0.0f, Q2 = 0.0f;
+            // One pass over the components: A_c = sum_s g_sc R_s, and per rank L the sums
+            // P_L[s] = sum_(c of rank L) g_sc m_c.  Then
+            //   S1 = sum_c A'_c m_c     = sum_s R'_s (P_0 + P_1 + P_2 + P_3)[s]
+            //   S2 = sum_c L_c A_c m_c  = sum_s R_s (P_1 + 2 P_2 + 3 P_3)[s]
+            //   Q  = sum_c A_c dm_c/du  = grad_u of the polynomial sum_c A_c m_c(u), in closed
+            //        form for the rank-1, -2 and -3 monomials (~40 operations instead of 3 per
+            //        component and the monomial derivatives)
+            float A[NC], P[4][NR];
+#pragma unroll
+            for (int L = 0; L < 4; ++L)
+#pragma unroll
+                for (int s = 0; s < NR; ++s) P[L][s] = 0.0f;
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
                 float gc[NR];
@@ -361,20 +372,31 @@ __global__ void __launch_bounds__(forces_threads<TPA>(), TPA >= 8 ? 4 : 1)
 #pragma unroll
                     for (int s = 0; s < NR; ++s) gc[s] = g[(GS ? 0 : s * NC + c)];
                 }
-                float Ac = 0.0f, Apc = 0.0f;
+                float Ac = 0.0f;
 #pragma unroll
                 for (int s = 0; s < NR; ++s) {
                     Ac = fmaf(gc[s], R[s], Ac);
-                    Apc = fmaf(gc[s], Rp[s], Apc);
+                    P[comp_rank(c)][s] = fmaf(gc[s], m[c], P[comp_rank(c)][s]);
                 }
-                S1 = fmaf(Apc, m[c], S1);
-                if (comp_rank(c) > 0) {
-                    S2 = fmaf((float)comp_rank(c) * Ac, m[c], S2);
-                    Q0 = fmaf(Ac, dmono(c, 0, ux, uy, uz), Q0);
-                    Q1 = fmaf(Ac, dmono(c, 1, ux, uy, uz), Q1);
-                    Q2 = fmaf(Ac, dmono(c, 2, ux, uy, uz), Q2);
-                }
+                A[c] = Ac;
             }
+            float S1 = 0.0f, S2 = 0.0f;
+#pragma unroll
+            for (int s = 0; s < NR; ++s) {
+                S1 = fmaf(Rp[s], (P[0][s] + P[1][s]) + (P[2][s] + P[3][s]), S1);
+                S2 = fmaf(R[s], fmaf(3.0f, P[3][s], fmaf(2.0f, P[2][s], P[1][s])), S2);
+            }
+            // components 4..9: xx xy xz yy yz zz; 10..19: xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz
+            const float xx = m[4], xy = m[5], xz = m[6], yy = m[7], yz = m[8], zz = m[9];
+            float Q0 = A[1] + fmaf(2.0f * A[4], ux, fmaf(A[5], uy, A[6] * uz));
+            float Q1 = A[2] + fmaf(A[5], ux, fmaf(2.0f * A[7], uy, A[8] * uz));
+            float Q2 = A[3] + fmaf(A[6], ux, fmaf(A[8], uy, 2.0f * A[9] * uz));
+            Q0 += fmaf(3.0f * A[10], xx, fmaf(2.0f * A[11], xy, fmaf(2.0f * A[12], xz,
+                  fmaf(A[13], yy, fmaf(A[14], yz, A[15] * zz)))));
+            Q1 += fmaf(A[11], xx, fmaf(2.0f * A[13], xy, fmaf(A[14], xz,
+                  fmaf(3.0f * A[16], yy, fmaf(2.0f * A[17], yz, A[18] * zz)))));
+            Q2 += fmaf(A[12], xx, fmaf(A[14], xy, fmaf(2.0f * A[15], xz,
+                  fmaf(A[17], yy, fmaf(2.0f * A[18], yz, 3.0f * A[19] * zz)))));
             const float radial_term = S1 - S2 * rinv;
             const float gx = fmaf(ux, radial_term, Q0 * rinv);
             const float gy = fmaf(uy, radial_term, Q1 * rinv);

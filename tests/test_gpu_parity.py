@@ -384,6 +384,32 @@ def test_energy_forces_mixed_backward_operand_formats(cfg, f16):
     assert virial_error(W.cpu().numpy(), ref) <= tol
 
 
+@pytest.mark.parametrize("act", ["tanh", "silu"])
+@pytest.mark.parametrize("case", ["config1", "config2", "li_small"])
+def test_fused_network_kernel_matches_oracle_and_the_four_gemms(case, act, li_small):
+    """The mixed path's network as one tcgen05 kernel per 128-atom tile (widths 128, 512 and
+    256 in these cases), forced on: within the mixed tolerance of the oracle, with virials,
+    and within the same tolerance (RMS) of the four separate GEMMs, from which it differs by
+    FP32 summation order and the FP16 rounding of phi'(z1) it keeps between its layers."""
+    if case == "li_small":
+        b, d, p = li_small
+        d = dict(d, activation=act)
+    else:
+        b, d, p = synth.config(1 if case == "config1" else 2, activation=act)
+    _, sysd, nl = _nl_pair(b, d, p)
+    ref = oracle.energy_forces(b, d, p, oracle.neighbors(b, d["r_cut"]))
+    outs = []
+    for fused in (1, 0):
+        mm = _model(d, p, "mixed")
+        mm.set_tuning(fused_mlp=fused)
+        E, F, W = mm.energy_forces(sysd, nl, virial=True)
+        mm.check_status()
+        _check_against(ref, b, E, F, W, TOL["mixed"])
+        outs.append(F.cpu().numpy())
+    rms = np.sqrt((ref["F"] ** 2).mean())
+    assert np.sqrt(((outs[0] - outs[1]) ** 2).mean()) <= TOL["mixed"] * rms
+
+
 @pytest.mark.parametrize("bn", [64, 128, 256])
 def test_mixed_gemm_blocks_per_sm_give_identical_results(bn):
     """One or two tensor-core GEMM blocks per SM (a full or a halved operand ring) compute each
