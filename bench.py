@@ -222,6 +222,9 @@ def algorithmic_work(stage, n_atoms, n_pairs, H):
         return 2.0 * n_atoms * F * H, "flop"
     if stage == "gemm_l2" or stage == "gemm_b1":
         return 2.0 * n_atoms * H * H, "flop"
+    if stage == "mlp_fused":
+        # the four layers in one kernel: L1 and B0 (360 x H each), L2 and B1 (H x H each)
+        return 2.0 * n_atoms * (2 * F * H + 2 * H * H), "flop"
     if stage == "moments":
         return MOMENTS_FLOP_PER_PAIR * n_pairs, "flop"
     if stage == "forces":
@@ -257,7 +260,7 @@ STAGE_SOURCES = {
     "forces": ("gm_pair.cu", "gm_common.cuh"), "contract_fwd": ("gm_contract.cu",),
     "contract_bwd": ("gm_contract.cu",), "gemm_l1": ("gm_gemm_tc.cuh", "gm_gemm_tc.cu"),
     "gemm_l2": ("gm_gemm_tc.cuh", "gm_gemm_tc.cu"), "gemm_b1": ("gm_gemm_tc.cuh", "gm_gemm_tc.cu"),
-    "gemm_b0": ("gm_gemm_tc.cuh", "gm_gemm_tc.cu"),
+    "gemm_b0": ("gm_gemm_tc.cuh", "gm_gemm_tc.cu"), "mlp_fused": ("gm_mlp_fused.cuh", "gm_gemm_tc.cuh"),
 }
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
@@ -325,7 +328,7 @@ def roofline(stages, n_atoms, n_pairs, H, precision, peaks, sustained, workload=
         achieved = work / sec / 1e9
         peak = peaks.get("hbm_gbs", 6400.0)
         out = {"bound": "hbm", "unit": "GB/s", "peak_source": "measured hbm_gbs" if "hbm_gbs" in peaks else "fallback"}
-    elif top.startswith("gemm") and precision == "mixed":
+    elif (top.startswith("gemm") or top == "mlp_fused") and precision == "mixed":
         achieved = work / sec / 1e12
         key = "bf16_tflops_sustained" if sustained else "bf16_tflops"
         peak = peaks.get(key, 1400.0 if sustained else 1800.0)

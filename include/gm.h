@@ -157,6 +157,9 @@ GM_API void gm_model_destroy(gm_model *m);
 /* Tuning knobs of a model (they change speed, not results beyond rounding; the neighbour
  * knobs change nothing in the list):
  *   GM_TUNE_PAIR_TPA    lanes per atom in the pair kernels: 0 = by system size, or 1, 2, 4, 8, 16, 32
+ *                       (the force kernel too, unless GM_TUNE_FORCES_TPA is set)
+ *   GM_TUNE_FORCES_TPA  lanes per atom of the force kernel alone: 0 = as GM_TUNE_PAIR_TPA (or by
+ *                       size when that is 0), or 1, 2, 4, 8, 16, 32
  *   GM_TUNE_SPLIT_MASK  mixed path: network GEMMs that run with hi/lo split-BF16 operands
  *                       (three tensor-core passes) -- bit 1 first layer, 2 second layer,
  *                       4 and 8 the two backward GEMMs; default 12 (backward GEMMs), which
@@ -203,14 +206,16 @@ GM_API void gm_model_destroy(gm_model *m);
 enum { GM_TUNE_PAIR_TPA = 0, GM_TUNE_SPLIT_MASK = 1, GM_TUNE_GEMM_BN = 2, GM_TUNE_NL_MODE = 3, GM_TUNE_NL_SPLIT = 4,
        GM_TUNE_NL_BLOCKS = 5, GM_TUNE_NL_TWO_PASS = 6, GM_TUNE_NL_ITEMS = 7, GM_TUNE_GEMM_CPS = 8,
        GM_TUNE_PG_SPLIT_MASK = 9, GM_TUNE_DEBUG_STALL = 10, GM_TUNE_F16_BACKWARD = 11,
-       GM_TUNE_FUSED_MLP = 12 };
+       GM_TUNE_FUSED_MLP = 12, GM_TUNE_FORCES_TPA = 13 };
 enum { GM_NL_MODE_AUTO = 0, GM_NL_MODE_PHASES = 1 };
 GM_API gm_status gm_model_set_tuning(gm_model *m, int32_t key, int32_t value);
 
-/* Lanes per atom the pair kernels use for a system of n_atoms atoms: the GM_TUNE_PAIR_TPA
+/* Lanes per atom the moments kernels use for a system of n_atoms atoms: the GM_TUNE_PAIR_TPA
  * setting, or (when it is 0) the library's choice by size.  -1 for a null model or a
  * negative n_atoms. */
 GM_API int32_t gm_model_pair_lanes(const gm_model *m, int32_t n_atoms);
+/* The same for the force kernel (GM_TUNE_FORCES_TPA, else GM_TUNE_PAIR_TPA, else by size). */
+GM_API int32_t gm_model_force_lanes(const gm_model *m, int32_t n_atoms);
 
 /* Bytes of device memory the model handle itself holds (its repacked weight copies);
  * 0 for a null model.  With gm_workspace_size this gives a step's whole device footprint

@@ -33,7 +33,7 @@ EXPORTS = ("gm_param_count", "gm_model_create", "gm_model_set_params", "gm_model
            "gm_status_clear", "gm_status_string", "gm_last_error", "gm_profile_enable", "gm_profile_reset",
            "gm_profile_n_stages", "gm_profile_stage_name", "gm_profile_collect", "gm_build_neighbors_noalloc", "gm_model_set_tuning",
            "gm_profile_forget_graphs", "gm_model_pair_lanes", "gm_model_device_bytes", "gm_probe_alu",
-           "gm_energy_forces_ensemble", "gm_md_init", "gm_md_run")
+           "gm_energy_forces_ensemble", "gm_md_init", "gm_md_run", "gm_model_force_lanes")
 
 
 class GmModelDesc(ctypes.Structure):
@@ -113,6 +113,7 @@ def load():
         "gm_model_set_tuning": (st, [_P, ctypes.c_int32, ctypes.c_int32]),
         "gm_profile_forget_graphs": (None, []),
         "gm_model_pair_lanes": (ctypes.c_int32, [_P, ctypes.c_int32]),
+        "gm_model_force_lanes": (ctypes.c_int32, [_P, ctypes.c_int32]),
         "gm_model_device_bytes": (ctypes.c_size_t, [_P]),
         "gm_probe_alu": (st, [ctypes.c_int32, ctypes.c_int64, _P, ctypes.POINTER(ctypes.c_double), _P]),
         "gm_md_init": (st, [_P, ctypes.POINTER(GmSystem), ctypes.POINTER(GmNlist), ctypes.POINTER(GmMdParams),
@@ -160,6 +161,7 @@ GM_TUNE_PG_SPLIT_MASK = 9
 GM_TUNE_DEBUG_STALL = 10
 GM_TUNE_F16_BACKWARD = 11
 GM_TUNE_FUSED_MLP = 12
+GM_TUNE_FORCES_TPA = 13
 GM_NL_MODE_AUTO, GM_NL_MODE_PHASES = 0, 1
 
 
@@ -169,6 +171,10 @@ def gm_model_set_tuning(model: int, key: int, value: int):
 
 def gm_model_pair_lanes(model: int, n_atoms: int) -> int:
     return int(load().gm_model_pair_lanes(model, n_atoms))
+
+
+def gm_model_force_lanes(model: int, n_atoms: int) -> int:
+    return int(load().gm_model_force_lanes(model, n_atoms))
 
 
 def gm_model_device_bytes(model: int) -> int:

@@ -20,7 +20,8 @@ import torch
 SPACE = {
     "nl_items": (0, 1, 2),
     "nl_split": (0, 1, 2, 4, 8, 16),
-    "pair_tpa": (0, 4, 8, 16, 32),
+    "pair_tpa": (0, 1, 4, 8, 32),
+    "forces_tpa": (0, 8, 16, 32),
     "gemm_bn": (0, 64, 128, 256),
     "gemm_cps": (0, 1, 2),
 }

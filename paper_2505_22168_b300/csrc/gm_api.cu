@@ -104,6 +104,7 @@ struct gm_model {
     int64_t n_param;
     RadialConst rc;
     int pair_tpa;          // lanes per atom in the pair kernels (0 = automatic)
+    int forces_tpa;        // lanes per atom of the force kernel alone (0 = as pair_tpa / by size)
     char *buf;             // one device allocation holding everything below
     size_t buf_bytes;
     float *beta;           // [S][S][5][7] * n_basis^{-1/2}
@@ -437,14 +438,27 @@ PairArgs pair_args(const gm_model *m, const gm_system *s, const gm_nlist *nl, co
     return a;
 }
 
+// Lanes per atom of the moments kernel (and the tangent moments), measured on B300 over
+// Li3PO4-like crystals of 4k-131k atoms, the 1536-atom EMIM box and the 7920-atom training
+// batch: the best shape follows the waves of the 128-thread blocks (8 at 4096 atoms, 32 at
+// 8192, 4 at 16384, 8 at 32768), then one lane per atom (its 100 sums in registers) from ~49k
 int choose_tpa(const gm_model *m, int N) {
     if (m->pair_tpa > 0) return m->pair_tpa;
-    // measured on B300 (EMIM 1536 atoms and the 7920-atom training batch: 32; Li3PO4 67k and
-    // 131k atoms: 1)
     if (N >= 49152) return 1;
-    if (N >= 16384) return 2;
-    if (N >= 8192) return 8;
+    if (N >= 24576) return 8;
+    if (N >= 12288) return 4;
+    if (N >= 6144) return 32;
+    if (N >= 3072) return 8;
     return 32;
+}
+
+// Lanes per atom of the force kernel: with eight or more lanes an atom's dE/dPsi sits once in
+// shared memory (121 registers, four blocks per SM); 8 was fastest from 4k to 131k atoms
+// (131,072: 387 us against 424 us for one lane), 32 below
+int choose_forces_tpa(const gm_model *m, int N) {
+    if (m->forces_tpa > 0) return m->forces_tpa;
+    if (m->pair_tpa > 0) return m->pair_tpa;
+    return N >= 3072 ? 8 : 32;
 }
 
 
@@ -494,6 +508,7 @@ gm_status gm_model_create(const gm_model_desc *d, gm_model **out) {
                                  n1 * n2 / sqrt(n1 * n1 + n2 * n2));
     }
     m->pair_tpa = 0;
+    m->forces_tpa = 0;
     m->split_mask = 12;
     m->f16_backward = 1;
     m->fused_mlp = 2;
@@ -549,6 +564,11 @@ int32_t gm_model_pair_lanes(const gm_model *m, int32_t n_atoms) {
     return choose_tpa(m, n_atoms);
 }
 
+int32_t gm_model_force_lanes(const gm_model *m, int32_t n_atoms) {
+    if (!m || n_atoms < 0) return -1;
+    return choose_forces_tpa(m, n_atoms);
+}
+
 gm_status gm_model_set_tuning(gm_model *m, int32_t key, int32_t value) {
     if (!m) return fail(GM_ERR_ARG, "null model");
     switch (key) {
@@ -556,6 +576,11 @@ gm_status gm_model_set_tuning(gm_model *m, int32_t key, int32_t value) {
         if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8 && value != 16 && value != 32)
             return fail(GM_ERR_ARG, "pair TPA must be 0, 1, 2, 4, 8, 16 or 32");
         m->pair_tpa = value;
+        return GM_OK;
+    case GM_TUNE_FORCES_TPA:
+        if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8 && value != 16 && value != 32)
+            return fail(GM_ERR_ARG, "force TPA must be 0, 1, 2, 4, 8, 16 or 32");
+        m->forces_tpa = value;
         return GM_OK;
     case GM_TUNE_SPLIT_MASK:
         if (value < 0 || value > 15) return fail(GM_ERR_ARG, "split mask must be in 0..15");
@@ -717,7 +742,7 @@ static gm_status network_fwd_bwd(const gm_model *m, const gm_system *sys, EfWs &
         fa.D1 = reinterpret_cast<__half *>(w.D1);
         fa.nn_part = w.nn_part;
         fa.dG = w.dG;
-        StageScope sc(ST_GEMM_L1, st);
+        StageScope sc(ST_MLP_FUSED, st);
         gm_status s = mlp_fused(m->d.activation, Mp, H, reinterpret_cast<const __nv_bfloat16 *>(w.G), m->W1t_h,
                                 m->W2t_h, m->W2_f, m->W1p_f, fa, status, st);
         return s == GM_OK ? GM_OK : fail(s, "fused network kernel failed");
@@ -833,7 +858,7 @@ static gm_status energy_forces_pipeline(const gm_model *m, const gm_system *sys,
         }
         PairArgs a = pair_args(m, sys, nl, w.pos_hi, w.pos_lo, status);
         StageScope sc(ST_FORCES, st);
-        launch_forces(a, choose_tpa(m, N), w.dpsi, forces, virial ? w.vir_atom : nullptr, st);
+        launch_forces(a, choose_forces_tpa(m, N), w.dpsi, forces, virial ? w.vir_atom : nullptr, st);
     }
     if (!fused_energy) {
         StageScope sc(ST_REDUCE, st);
@@ -901,7 +926,7 @@ gm_status gm_energy_forces_ensemble(const gm_model *m, const gm_system *sys, con
                 launch_contract_bwd(w.psi, w.dG, N, w.dpsi, st);
             }
             StageScope sc(ST_FORCES, st);
-            launch_forces(a, choose_tpa(m, N), w.dpsi, Fh, nullptr, st);
+            launch_forces(a, choose_forces_tpa(m, N), w.dpsi, Fh, nullptr, st);
         }
         if (force_std) launch_ens_force_std(N, E, Fk, force_std, st);
     }
@@ -1134,7 +1159,7 @@ const char *gm_profile_stage_name(int s) {
     static const char *names[N_STAGES] = {"neighbors", "moments", "contract_fwd", "gemm_l1", "gemm_l2",
                                           "gemm_b1", "gemm_b0", "contract_bwd", "forces", "reduce",
                                           "pg_pair_fwd", "pg_network", "pg_pair_bwd", "nl_bin", "nl_count",
-                                          "nl_scan", "nl_fill", "nl_coop", "md_integrate"};
+                                          "nl_scan", "nl_fill", "nl_coop", "md_integrate", "mlp_fused"};
     return (s >= 0 && s < N_STAGES) ? names[s] : "";
 }
 

@@ -32,7 +32,7 @@ struct Carve {
 enum Stage {
     ST_NEIGHBORS = 0, ST_MOMENTS, ST_CONTRACT_FWD, ST_GEMM_L1, ST_GEMM_L2, ST_GEMM_B1, ST_GEMM_B0,
     ST_CONTRACT_BWD, ST_FORCES, ST_REDUCE, ST_PG_PAIR_FWD, ST_PG_NETWORK, ST_PG_PAIR_BWD, ST_NL_BIN, ST_NL_COUNT,
-    ST_NL_SCAN, ST_NL_FILL, ST_NL_COOP, ST_MD, N_STAGES
+    ST_NL_SCAN, ST_NL_FILL, ST_NL_COOP, ST_MD, ST_MLP_FUSED, N_STAGES
 };
 void note_launches(int n);
 

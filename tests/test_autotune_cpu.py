@@ -17,16 +17,18 @@ class FakeModel:
 
 def cost(m):
     t = m.tuning
-    # separable cost with its minimum at nl_items=1, nl_split=4, pair_tpa=16, gemm_bn=128, gemm_cps=2
+    # separable cost with its minimum at nl_items=1, nl_split=4, pair_tpa=8, forces_tpa=16,
+    # gemm_bn=128, gemm_cps=2
     return (1.0 + abs(t.get("nl_items", 0) - 1) + 0.1 * abs(t.get("nl_split", 0) - 4)
-            + 0.01 * abs(t.get("pair_tpa", 0) - 16) + 0.001 * abs(t.get("gemm_bn", 0) - 128)
-            + 0.0001 * abs(t.get("gemm_cps", 0) - 2))
+            + 0.01 * abs(t.get("pair_tpa", 0) - 8) + 0.005 * abs(t.get("forces_tpa", 0) - 16)
+            + 0.001 * abs(t.get("gemm_bn", 0) - 128) + 0.0001 * abs(t.get("gemm_cps", 0) - 2))
 
 
 def test_coordinate_descent_finds_the_separable_minimum():
     m = FakeModel()
     r = autotune.tune(m, None, None, None, timer=cost, key="k")
-    assert r["settings"] == {"nl_items": 1, "nl_split": 4, "pair_tpa": 16, "gemm_bn": 128, "gemm_cps": 2}
+    assert r["settings"] == {"nl_items": 1, "nl_split": 4, "pair_tpa": 8, "forces_tpa": 16, "gemm_bn": 128,
+                             "gemm_cps": 2}
     assert m.tuning == r["settings"]
     assert r["ms"] == min(ms for _, ms in r["trials"])
     assert r["default_ms"] == r["trials"][0][1]

@@ -451,7 +451,7 @@ def test_autotuned_batched_model_matches_oracle(li_small):
         nl = NeighborList(b.n_atoms, nl0.capacity, m.device)
         out = (torch.empty(b.n_structures, dtype=torch.float64, device=m.device),
                torch.empty(b.n_atoms, 3, dtype=torch.float32, device=m.device), None)
-        space = {"nl_items": (0, 1, 2), "pair_tpa": (0, 8, 32), "gemm_bn": (0, 128)}
+        space = {"nl_items": (0, 1, 2), "pair_tpa": (0, 8, 32), "forces_tpa": (0, 16), "gemm_bn": (0, 128)}
         r = autotune.tune(m, sysd, nl, out, reps=3, space=space)
         assert set(r["settings"]) <= set(space)
         m.step(sysd, nl, out)
@@ -631,6 +631,7 @@ def test_energy_forces_every_pair_lane_count(case, tpa, precision, li_small):
     m.set_tuning(pair_tpa=tpa)
     from paper_2505_22168_b300 import _lib
     assert _lib.gm_model_pair_lanes(m.handle, b.n_atoms) == tpa
+    assert _lib.gm_model_force_lanes(m.handle, b.n_atoms) == tpa
     sysd = DeviceSystem(b)
     nl = m.build_neighbors(sysd)
     E, F, W = m.energy_forces(sysd, nl, virial=True)
@@ -648,12 +649,12 @@ def _li_boxes(n_boxes):
     return b, d, p
 
 
-@pytest.mark.parametrize("n_boxes,lanes", [(16, 8), (32, 2), (96, 1)])
-def test_library_lane_choice_by_size_matches_oracle(n_boxes, lanes):
-    """8,192, 16,384 and 49,152 atoms: the pair-kernel shapes the library picks by size for
-    mid-size and large systems (8, 2 and 1 lanes per atom, as for the 131,072-atom crystal and
-    the batched Li3PO4 workload), with no forced knob, against the full oracle for both
-    precisions, energies, forces and virials."""
+@pytest.mark.parametrize("n_boxes,lanes,force_lanes", [(16, 32, 8), (32, 4, 8), (64, 8, 8), (96, 1, 8)])
+def test_library_lane_choice_by_size_matches_oracle(n_boxes, lanes, force_lanes):
+    """8,192, 16,384, 32,768 and 49,152 atoms: the pair-kernel shapes the library picks by size
+    for mid-size and large systems (moments 32, 4, 8 and 1 lanes per atom, forces 8, as for the
+    131,072-atom crystal and the batched Li3PO4 workload), with no forced knob, against the
+    full oracle for both precisions, energies, forces and virials."""
     b, d, p = _li_boxes(n_boxes)
     ref = _oracle_ref(("li_boxes", n_boxes), b, d, p)
     GMNN, DeviceSystem = _gm()
@@ -661,6 +662,7 @@ def test_library_lane_choice_by_size_matches_oracle(n_boxes, lanes):
     for precision in ("fp32", "mixed"):
         m = GMNN(d, p, precision=precision)
         assert _lib.gm_model_pair_lanes(m.handle, b.n_atoms) == lanes
+        assert _lib.gm_model_force_lanes(m.handle, b.n_atoms) == force_lanes
         sysd = DeviceSystem(b)
         nl = m.build_neighbors(sysd)
         E, F, W = m.energy_forces(sysd, nl, virial=True)
@@ -672,7 +674,8 @@ def test_library_lane_choice_by_size_matches_oracle(n_boxes, lanes):
 
 
 def test_full_size_li3po4_sampled_forces_match_oracle():
-    """131,072 atoms in the benchmark's launch configuration (one lane per atom): the forces
+    """131,072 atoms in the benchmark's launch configuration (moments one lane per atom, forces
+    eight, the fused network kernel): the forces
     and the atomic energies of 12 sampled atoms equal an exact oracle evaluation of those atoms
     (their neighbours' complete environments are evaluated; nothing is truncated), for both
     precisions."""
@@ -684,6 +687,7 @@ def test_full_size_li3po4_sampled_forces_match_oracle():
     for precision in ("fp32", "mixed"):
         m = GMNN(d, p, precision=precision)
         assert _lib.gm_model_pair_lanes(m.handle, b.n_atoms) == 1
+        assert _lib.gm_model_force_lanes(m.handle, b.n_atoms) == 8
         sysd = DeviceSystem(b)
         nl = m.build_neighbors(sysd)
         _, F, _ = m.energy_forces(sysd, nl, virial=False)
