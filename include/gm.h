@@ -171,8 +171,15 @@ GM_API void gm_model_destroy(gm_model *m);
  *   GM_TUNE_FUSED_MLP   mixed path: 1 runs the four network GEMMs of gm_energy_forces as one
  *                       tcgen05 kernel per 128-atom tile, the layer activations kept on chip
  *                       (widths 128, 256 and 512, with the FP16 backward and no split in the
- *                       forward layers); 0: four GEMM launches; 2 (default): fused when the
- *                       tiles fill the GPU at least twice (>= 296 tiles), else four launches
+ *                       forward layers); 0: four GEMM launches; 2 (default): by size -- four
+ *                       launches below 16 tiles, then a cluster per tile (GM_TUNE_MLP_CLUSTER,
+ *                       2 or 4 CTAs) while all its CTAs fit on the GPU at once, else one CTA
+ *                       per tile
+ *   GM_TUNE_MLP_CLUSTER mixed path, fused network: CTAs sharing one 128-atom tile along the
+ *                       hidden width (a thread-block cluster that all-gathers each layer's
+ *                       activations in shared memory): 0 = by size (default), 1 = one CTA per
+ *                       tile, 2, 4 or 8 (hidden width / CTAs at least 64); a size the device
+ *                       cannot launch falls back to the four GEMM launches
  *   GM_TUNE_PG_SPLIT_MASK  mixed path: the same bits for the four network GEMMs of
  *                       gm_param_grad (forward, forward, backward, backward on the stacked
  *                       primal and tangent rows); default 15 (all split), which keeps every
@@ -206,7 +213,7 @@ GM_API void gm_model_destroy(gm_model *m);
 enum { GM_TUNE_PAIR_TPA = 0, GM_TUNE_SPLIT_MASK = 1, GM_TUNE_GEMM_BN = 2, GM_TUNE_NL_MODE = 3, GM_TUNE_NL_SPLIT = 4,
        GM_TUNE_NL_BLOCKS = 5, GM_TUNE_NL_TWO_PASS = 6, GM_TUNE_NL_ITEMS = 7, GM_TUNE_GEMM_CPS = 8,
        GM_TUNE_PG_SPLIT_MASK = 9, GM_TUNE_DEBUG_STALL = 10, GM_TUNE_F16_BACKWARD = 11,
-       GM_TUNE_FUSED_MLP = 12, GM_TUNE_FORCES_TPA = 13 };
+       GM_TUNE_FUSED_MLP = 12, GM_TUNE_FORCES_TPA = 13, GM_TUNE_MLP_CLUSTER = 14 };
 enum { GM_NL_MODE_AUTO = 0, GM_NL_MODE_PHASES = 1 };
 GM_API gm_status gm_model_set_tuning(gm_model *m, int32_t key, int32_t value);
 

@@ -162,6 +162,7 @@ GM_TUNE_DEBUG_STALL = 10
 GM_TUNE_F16_BACKWARD = 11
 GM_TUNE_FUSED_MLP = 12
 GM_TUNE_FORCES_TPA = 13
+GM_TUNE_MLP_CLUSTER = 14
 GM_NL_MODE_AUTO, GM_NL_MODE_PHASES = 0, 1
 
 

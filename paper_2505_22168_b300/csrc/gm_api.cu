@@ -117,6 +117,7 @@ struct gm_model {
     int split_mask;        // GEMMs run with three hi/lo passes: 1 L1, 2 L2, 4 B1, 8 B0
     int f16_backward;      // backward GEMMs B1, B0 on FP16 operands in one pass (else split BF16)
     int fused_mlp;         // mixed path: the four network GEMMs as one kernel (where it applies)
+    int mlp_cluster;       // CTAs per tile of the fused network kernel (0 by size, 1 one, 2/4/8)
     int pg_split_mask;     // the same for the four network GEMMs of the parameter gradient
     int gemm_bn;           // tensor-core tile width (0 = by size)
     int gemm_cps;          // tensor-core GEMM blocks per SM (0 = by tile count)
@@ -512,6 +513,7 @@ gm_status gm_model_create(const gm_model_desc *d, gm_model **out) {
     m->split_mask = 12;
     m->f16_backward = 1;
     m->fused_mlp = 2;
+    m->mlp_cluster = 0;
     m->pg_split_mask = 15;
     m->gemm_bn = 0;
     m->gemm_cps = 0;
@@ -593,6 +595,11 @@ gm_status gm_model_set_tuning(gm_model *m, int32_t key, int32_t value) {
     case GM_TUNE_FUSED_MLP:
         if (value < 0 || value > 2) return fail(GM_ERR_ARG, "fused network mode must be 0, 1 or 2");
         m->fused_mlp = value;
+        return GM_OK;
+    case GM_TUNE_MLP_CLUSTER:
+        if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8)
+            return fail(GM_ERR_ARG, "network cluster size must be 0, 1, 2, 4 or 8");
+        m->mlp_cluster = value;
         return GM_OK;
     case GM_TUNE_F16_BACKWARD:
         if (value != 0 && value != 1) return fail(GM_ERR_ARG, "FP16 backward flag must be 0 or 1");
@@ -696,17 +703,45 @@ static gm_status forward_to_features(const gm_model *m, const gm_system *sys, co
     return launch_status();
 }
 
-// The mixed path's network runs as one fused kernel (gm_mlp_fused.cuh) when the model's width
-// allows it, the backward GEMMs take FP16 and the forward ones single-pass BF16, and no
-// ensemble partial sums or other output head are asked for.
-// GM_TUNE_FUSED_MLP: 0 never, 1 always, 2 (default) by size: one CTA per 128-atom tile runs its
-// four layers one after another, so the fused kernel pays off once the tiles fill the GPU twice
-// (131,072 atoms: 1.51 -> 1.45 ms per energy/force pass); at 1536 atoms (12 tiles) the four
-// separate GEMMs, spread over ~100 CTAs each, are faster (66 against 104 us)
-static bool use_fused_mlp(const gm_model *m, bool ens, bool from_l2, const float *head, int n_atoms) {
-    const bool want = m->fused_mlp == 1 || (m->fused_mlp == 2 && (n_atoms + TILE_M - 1) / TILE_M >= 2 * 148);
-    return m->d.precision == GM_PREC_MIXED && want && m->f16_backward && mlp_fused_supported(m->H) && !ens &&
-           !from_l2 && head == nullptr && (m->split_mask & 3) == 0 && m->debug_stall == 0;
+// The mixed path's network runs as one fused kernel when the model's width allows it, the
+// backward GEMMs take FP16 and the forward ones single-pass BF16, and no ensemble partial sums
+// or other output head are asked for.  Two forms:
+//   per tile   one CTA per 128-atom tile runs the four layers one after another
+//              (gm_mlp_fused.cuh); every CTA streams all the weights (1.8 MB at width 512)
+//   cluster    each tile split over a cluster of 2, 4 or 8 CTAs along the hidden width, the
+//              layer slices all-gathered between layers (gm_mlp_cluster.cuh); each CTA
+//              streams 1/CS of the weights but receives (CS - 1)/CS of every gathered layer
+// GM_TUNE_FUSED_MLP: 0 never (four GEMM launches), 1 always, 2 (default) by size;
+// GM_TUNE_MLP_CLUSTER: 0 (default) cluster size by size, 1 per tile, 2, 4 or 8.
+// By size (B300, whole energy/force step, width 512): below 16 tiles the four GEMM launches
+// (1536 atoms: 89 us against 93-97 with a cluster); a cluster while all its CTAs fit on the
+// GPU at once, at most 4 wide (4096 atoms: 141 us with 4 against 156 for the GEMMs; 5184
+// atoms, width 256: 166 with 2 against 175; 8192 atoms: 215 with 2 against 233); one CTA per
+// tile above that (16,384 atoms: 322 against 349).
+// Returns MLP_GEMMS, MLP_TILE or MLP_CLUSTER (with the cluster size in *cs).
+enum { MLP_GEMMS = 0, MLP_TILE = 1, MLP_CLUSTER = 2 };
+static int mlp_form(const gm_model *m, bool ens, bool from_l2, const float *head, int n_atoms, int *cs) {
+    *cs = 1;
+    if (m->d.precision != GM_PREC_MIXED || m->fused_mlp == 0 || !m->f16_backward || !mlp_fused_supported(m->H) ||
+        ens || from_l2 || head != nullptr || (m->split_mask & 3) != 0 || m->debug_stall != 0)
+        return MLP_GEMMS;
+    const int tiles = (n_atoms + TILE_M - 1) / TILE_M;
+    if (m->mlp_cluster >= 2) {
+        if (mlp_cluster_capacity(m->d.activation, m->H, m->mlp_cluster) <= 0) return MLP_GEMMS;
+        *cs = m->mlp_cluster;
+        return MLP_CLUSTER;
+    }
+    if (m->mlp_cluster == 0 && tiles >= 16) {
+        for (int c = 4; c >= 2; c /= 2) {
+            if (!mlp_cluster_supported(m->H, c) || tiles * c > 148) continue;
+            if (tiles <= mlp_cluster_capacity(m->d.activation, m->H, c)) {
+                *cs = c;
+                return MLP_CLUSTER;
+            }
+        }
+    }
+    if (m->fused_mlp == 1 || tiles >= 16) return MLP_TILE;
+    return MLP_GEMMS;
 }
 
 // The four network GEMMs: features -> energies (partial sums) and dE/dG.  energy (mixed
@@ -730,7 +765,9 @@ static gm_status network_fwd_bwd(const gm_model *m, const gm_system *sys, EfWs &
     e.n_ens = ens ? m->E : 1;
     e.w3e = m->w3e;
     e.nn_ens = w.nn_ens;
-    if (use_fused_mlp(m, ens, from_l2, head, sys->n_atoms)) {
+    int cs = 1;
+    const int form = mlp_form(m, ens, from_l2, head, sys->n_atoms, &cs);
+    if (form != MLP_GEMMS) {
         FusedMlpArgs fa;
         fa.n_atoms = sys->n_atoms;
         fa.n_species = m->S;
@@ -743,8 +780,25 @@ static gm_status network_fwd_bwd(const gm_model *m, const gm_system *sys, EfWs &
         fa.nn_part = w.nn_part;
         fa.dG = w.dG;
         StageScope sc(ST_MLP_FUSED, st);
-        gm_status s = mlp_fused(m->d.activation, Mp, H, reinterpret_cast<const __nv_bfloat16 *>(w.G), m->W1t_h,
-                                m->W2t_h, m->W2_f, m->W1p_f, fa, status, st);
+        gm_status s;
+        if (form == MLP_CLUSTER) {
+            fa.xa1 = reinterpret_cast<__nv_bfloat16 *>(w.A1);
+            fa.xdz2 = reinterpret_cast<__nv_bfloat16 *>(w.dZ2);
+            fa.xdz1 = reinterpret_cast<__nv_bfloat16 *>(w.dZ1);
+            if (energy) {
+                fa.atom_ptr = sys->atom_ptr;
+                fa.n_structures = sys->n_structures;
+                fa.mu = m->mu;
+                fa.b3 = m->b3;
+                fa.red_acc = w.red_acc;
+                fa.energy = energy;
+            }
+            s = mlp_cluster(m->d.activation, Mp, H, cs, reinterpret_cast<const __nv_bfloat16 *>(w.G), m->W1t_h,
+                            m->W2t_h, m->W2_f, m->W1p_f, fa, status, st);
+        } else {
+            s = mlp_fused(m->d.activation, Mp, H, reinterpret_cast<const __nv_bfloat16 *>(w.G), m->W1t_h, m->W2t_h,
+                          m->W2_f, m->W1p_f, fa, status, st);
+        }
         return s == GM_OK ? GM_OK : fail(s, "fused network kernel failed");
     }
     if (m->d.precision == GM_PREC_MIXED) {
@@ -844,10 +898,11 @@ static gm_status energy_forces_pipeline(const gm_model *m, const gm_system *sys,
     const int N = sys->n_atoms, B = sys->n_structures, H = m->H;
     const int Mp = round_up(N, TILE_M);
     gm_status s;
-    // without the virial, the mixed path sums the energies inside its B1 GEMM (not in the fused
-    // network kernel: the reduction kernel does)
+    // without the virial, the mixed path sums the energies inside its B1 GEMM or its cluster
+    // network kernel (after the per-tile fused kernel the reduction kernel does)
+    int cs = 1;
     const bool fused_energy = N > 0 && virial == nullptr && m->d.precision == GM_PREC_MIXED &&
-                              !use_fused_mlp(m, ens, false, nullptr, N);
+                              mlp_form(m, ens, false, nullptr, N, &cs) != MLP_TILE;
     if (N > 0) {
         if ((s = forward_to_features(m, sys, nl, w, nullptr, nullptr, forces, status, st)) != GM_OK) return s;
         if ((s = network_fwd_bwd(m, sys, w, Mp, status, st, fused_energy ? energy : nullptr, nullptr, ens)) != GM_OK)

@@ -81,9 +81,29 @@ struct FusedMlpArgs {
     const float *b1, *b2, *w3, *sigma;
     __half *D1;               // [M][H] FP16 phi'(z1) (scratch)
     float *nn_part, *dG;
+    // cluster kernel only: [M][2H] scratch arrays through which the cluster gathers a1, dZ2
+    // and dZ1 (first H columns), and the structure energies summed in the kernel (energy
+    // null: not summed)
+    __nv_bfloat16 *xa1 = nullptr, *xdz2 = nullptr, *xdz1 = nullptr;
+    const int32_t *atom_ptr = nullptr;
+    int n_structures = 0;
+    const float *mu = nullptr, *b3 = nullptr;
+    unsigned long long *red_acc = nullptr;
+    double *energy = nullptr;
 };
 bool mlp_fused_supported(int H);
 gm_status mlp_fused(int act, int M, int H, const __nv_bfloat16 *G, const __nv_bfloat16 *W1t, const __nv_bfloat16 *W2t,
                     const __half *W2, const __half *W1p, const FusedMlpArgs &a, int32_t *status, cudaStream_t st);
+
+// The same network with each 128-row tile split over a cluster of cs CTAs along the hidden
+// width (gm_mlp_cluster.cuh): cs in 2, 4, 8 with H / cs >= 64.  When a.energy is set the
+// structure energies are summed in the kernel (into a.red_acc, fixed point) and written to
+// a.energy.  mlp_cluster_capacity: clusters the device keeps resident at once (0: the
+// configuration cannot launch, or is not supported).
+bool mlp_cluster_supported(int H, int cs);
+int mlp_cluster_capacity(int act, int H, int cs);
+gm_status mlp_cluster(int act, int M, int H, int cs, const __nv_bfloat16 *G, const __nv_bfloat16 *W1t,
+                      const __nv_bfloat16 *W2t, const __half *W2, const __half *W1p, const FusedMlpArgs &a,
+                      int32_t *status, cudaStream_t st);
 
 }  // namespace gm

@@ -6,7 +6,7 @@
 #include <tuple>
 
 #include "gm_gemm_tc.cuh"
-#include "gm_mlp_fused.cuh"
+#include "gm_mlp_cluster.cuh"
 
 namespace gm {
 
@@ -152,7 +152,123 @@ cudaError_t launch_fused(const CUtensorMap *maps, const tc::FusedArgs &f, int32_
 }
 }  // namespace
 
+namespace {
+// launch configuration of the cluster kernel: CS CTAs per 128-row tile
+template <int H, int CS, int ACT>
+cudaLaunchConfig_t cluster_cfg(int M, cudaStream_t st, cudaLaunchAttribute *attr) {
+    using Sh = tc::ClusterShape<H, CS>;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(M / tc::BM * CS));
+    cfg.blockDim = dim3(320);
+    cfg.dynamicSmemBytes = Sh::SMEM;
+    cfg.stream = st;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
+    return cfg;
+}
+
+// clusters of the kernel the device keeps resident at once (0: it cannot launch); per device
+template <int H, int CS, int ACT>
+int cluster_capacity() {
+    static int cap[64];
+    static bool known[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    if (known[dev]) return cap[dev];
+    using Sh = tc::ClusterShape<H, CS>;
+    int n = 0;
+    if (cudaFuncSetAttribute(tc::k_mlp_cluster<H, CS, ACT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Sh::SMEM) == cudaSuccess) {
+        cudaLaunchAttribute attr[2];
+        cudaLaunchConfig_t cfg = cluster_cfg<H, CS, ACT>(tc::BM, nullptr, attr);
+        cfg.numAttrs = 1;   // the occupancy query takes the cluster shape alone
+        if (cudaOccupancyMaxActiveClusters(&n, tc::k_mlp_cluster<H, CS, ACT>, &cfg) != cudaSuccess) n = 0;
+    }
+    cudaGetLastError();
+    cap[dev] = n;
+    known[dev] = true;
+    return n;
+}
+
+template <int H, int CS, int ACT>
+cudaError_t launch_cluster(const CUtensorMap *maps, const tc::ClusterArgs &f, int32_t *status, cudaStream_t st) {
+    if (cluster_capacity<H, CS, ACT>() <= 0) return cudaErrorNotSupported;   // also sets the smem attribute
+    cudaLaunchAttribute attr[2];
+    cudaLaunchConfig_t cfg = cluster_cfg<H, CS, ACT>(f.M, st, attr);
+    return cudaLaunchKernelEx(&cfg, tc::k_mlp_cluster<H, CS, ACT>, maps[0], maps[1], maps[2], maps[3], maps[4],
+                              maps[5], maps[6], maps[7], f, status);
+}
+
+template <int H, int CS>
+cudaError_t launch_cluster_act(int act, const CUtensorMap *maps, const tc::ClusterArgs &f, int32_t *status,
+                               cudaStream_t st) {
+    return act == 0 ? launch_cluster<H, CS, 0>(maps, f, status, st) : launch_cluster<H, CS, 1>(maps, f, status, st);
+}
+}  // namespace
+
 bool mlp_fused_supported(int H) { return H == 128 || H == 256 || H == 512; }
+
+bool mlp_cluster_supported(int H, int cs) {
+    return mlp_fused_supported(H) && (cs == 2 || cs == 4 || cs == 8) && H / cs >= 64;
+}
+
+int mlp_cluster_capacity(int act, int H, int cs) {
+    if (!mlp_cluster_supported(H, cs)) return 0;
+    const bool silu = act != 0;
+#define GM_CAP(h, c) if (H == h && cs == c) return silu ? cluster_capacity<h, c, 1>() : cluster_capacity<h, c, 0>();
+    GM_CAP(512, 8) GM_CAP(512, 4) GM_CAP(512, 2) GM_CAP(256, 4) GM_CAP(256, 2) GM_CAP(128, 2)
+#undef GM_CAP
+    return 0;
+}
+
+gm_status mlp_cluster(int act, int M, int H, int cs, const __nv_bfloat16 *G, const __nv_bfloat16 *W1t,
+                      const __nv_bfloat16 *W2t, const __half *W2, const __half *W1p, const FusedMlpArgs &a,
+                      int32_t *status, cudaStream_t st) {
+    if (M <= 0) return GM_OK;
+    if (M % tc::BM || !mlp_cluster_supported(H, cs) || (long long)(M / tc::BM) * cs > 65535)
+        return GM_ERR_UNSUPPORTED;
+    const int w = H / cs, wg = NFP / cs;
+    if (!a.xa1 || !a.xdz2 || !a.xdz1) return GM_ERR_ARG;
+    CUtensorMap maps[8];
+    // operands in the [rows][2K] layout of the split path (hi slots read); the three gather
+    // arrays in the same layout
+    if (!tensor_map(G, 2 * NFP, M, tc::BM, &maps[0]) || !tensor_map(W1t, 2 * NFP, H, w, &maps[1]) ||
+        !tensor_map(W2t, 2 * H, H, w, &maps[2]) || !tensor_map(W2, 2 * H, H, w, &maps[3]) ||
+        !tensor_map(W1p, 2 * H, NFP, wg, &maps[4]) || !tensor_map(a.xa1, 2 * H, M, tc::BM, &maps[5]) ||
+        !tensor_map(a.xdz2, 2 * H, M, tc::BM, &maps[6]) || !tensor_map(a.xdz1, 2 * H, M, tc::BM, &maps[7]))
+        return GM_ERR_CUDA;
+    tc::ClusterArgs f;
+    f.M = M;
+    f.n_atoms = a.n_atoms;
+    f.n_species = a.n_species;
+    f.species = a.species;
+    f.b1 = a.b1;
+    f.b2 = a.b2;
+    f.w3 = a.w3;
+    f.sigma = a.sigma;
+    f.D1 = a.D1;
+    f.nn_part = a.nn_part;
+    f.dG = a.dG;
+    f.atom_ptr = a.atom_ptr;
+    f.n_structures = a.n_structures;
+    f.mu = a.mu;
+    f.b3 = a.b3;
+    f.red_acc = a.red_acc;
+    f.energy = a.energy;
+    cudaError_t err = cudaErrorNotSupported;
+#define GM_LAUNCH(h, c) if (H == h && cs == c) err = launch_cluster_act<h, c>(act, maps, f, status, st);
+    GM_LAUNCH(512, 8) GM_LAUNCH(512, 4) GM_LAUNCH(512, 2) GM_LAUNCH(256, 4) GM_LAUNCH(256, 2) GM_LAUNCH(128, 2)
+#undef GM_LAUNCH
+    note_launches(1);
+    if (err == cudaErrorNotSupported) return GM_ERR_UNSUPPORTED;
+    return err == cudaSuccess ? GM_OK : GM_ERR_CUDA;
+}
 
 gm_status mlp_fused(int act, int M, int H, const __nv_bfloat16 *G, const __nv_bfloat16 *W1t, const __nv_bfloat16 *W2t,
                     const __half *W2, const __half *W1p, const FusedMlpArgs &a, int32_t *status, cudaStream_t st) {

@@ -170,7 +170,8 @@ class GMNN:
                    "nl_two_pass": L.GM_TUNE_NL_TWO_PASS, "nl_items": L.GM_TUNE_NL_ITEMS,
                    "gemm_cps": L.GM_TUNE_GEMM_CPS, "pg_split_mask": L.GM_TUNE_PG_SPLIT_MASK,
                    "debug_stall": L.GM_TUNE_DEBUG_STALL, "f16_backward": L.GM_TUNE_F16_BACKWARD,
-                   "fused_mlp": L.GM_TUNE_FUSED_MLP, "forces_tpa": L.GM_TUNE_FORCES_TPA}
+                   "fused_mlp": L.GM_TUNE_FUSED_MLP, "forces_tpa": L.GM_TUNE_FORCES_TPA,
+                   "mlp_cluster": L.GM_TUNE_MLP_CLUSTER}
 
     def set_tuning(self, **knobs):
         """Speed knobs of the library (gm_model_set_tuning): pair_tpa, split_mask, pg_split_mask,
