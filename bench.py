@@ -260,7 +260,7 @@ STAGE_SOURCES = {
     "forces": ("gm_pair.cu", "gm_common.cuh"), "contract_fwd": ("gm_contract.cu",),
     "contract_bwd": ("gm_contract.cu",), "gemm_l1": ("gm_gemm_tc.cuh", "gm_gemm_tc.cu"),
     "gemm_l2": ("gm_gemm_tc.cuh", "gm_gemm_tc.cu"), "gemm_b1": ("gm_gemm_tc.cuh", "gm_gemm_tc.cu"),
-    "gemm_b0": ("gm_gemm_tc.cuh", "gm_gemm_tc.cu"), "mlp_fused": ("gm_mlp_fused.cuh", "gm_gemm_tc.cuh"),
+    "gemm_b0": ("gm_gemm_tc.cuh", "gm_gemm_tc.cu"), "mlp_fused": ("gm_mlp_fused.cuh", "gm_mlp_cluster.cuh", "gm_gemm_tc.cuh"),
 }
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
