@@ -797,12 +797,32 @@ def sampled_accuracy(batch, desc, params, F, n_rows):
     return out
 
 
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
 def cpu_baseline(cfg, budget_s):
+    """The oracle on all host threads (budget_s), then on one thread (a quarter of that)."""
+    import oracle
     n, times, threads, ref = oracle_step_seconds(cfg, budget_s, keep=True)
     value = n * len(times) / sum(times)
+    oracle.set_threads(1)
+    try:
+        _, t1, _ = oracle_step_seconds(cfg, budget_s / 4)
+    finally:
+        oracle.set_threads(threads)
     return {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{len(times)} full evaluations (brute-force neighbours + E/F/virial, FP64) of the "
-                      f"{n}-atom workload, {sum(times):.1f} s on {threads} OpenMP threads"}, ref
+                      f"{n}-atom workload, {sum(times):.1f} s on {threads} OpenMP threads",
+            "value_1core": n * len(t1) / sum(t1),
+            "sample_1core": f"{len(t1)} full evaluations, {sum(t1):.1f} s on 1 thread",
+            "cpu_model": cpu_model(), "nproc": os.cpu_count()}, ref
 
 
 # ----------------------------------------------------------------------------- main

@@ -353,6 +353,11 @@ def num_threads():
     return int(lib().or_num_threads())
 
 
+def set_threads(n: int):
+    """OpenMP threads of the oracle's later calls in this process."""
+    lib().or_set_threads(ctypes.c_int(int(n)))
+
+
 def omp_env(threads: int | None):
     """Environment for a child process that should use ``threads`` OpenMP threads."""
     env = dict(os.environ)

@@ -973,3 +973,12 @@ int or_num_threads(void) {
     return 1;
 #endif
 }
+
+/* Threads of the later parallel loops (timing on a given number of host cores). */
+void or_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
