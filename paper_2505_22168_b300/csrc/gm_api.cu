@@ -1134,6 +1134,8 @@ gm_status gm_param_grad(const gm_model *m, const gm_system *sys, const gm_nlist 
         // the A operand in the mixed path (split passes as for the energy/force GEMMs)
         const bool mixed = m->d.precision == GM_PREC_MIXED;
         const int sp = m->pg_split_mask;
+        // (the activation kernels write the hi/lo copy of the next GEMM's A operand themselves;
+        // only the features need a conversion pass)
         auto mm = [&](int which, const float *A, const float *Bf, const __nv_bfloat16 *Bh, int N_, int K_,
                       float *out) -> gm_status {
             e.out0 = out;
@@ -1141,27 +1143,28 @@ gm_status gm_param_grad(const gm_model *m, const gm_system *sys, const gm_nlist 
                 gemm_f32(EPI_STORE, 0, A, Bf, 2 * Mp, N_, K_, e, st);
                 return GM_OK;
             }
-            split_bf16(A, 2 * Mp, K_, w.hl, st);
+            if (which == 0) split_bf16(A, 2 * Mp, K_, w.hl, st);
             return gemm_bf16(EPI_STORE, 0, w.hl, Bh, 2 * Mp, N_, K_, ((sp >> which) & 1) != 0, e, status, st,
                              m->gemm_bn, m->gemm_cps);
         };
+        __nv_bfloat16 *hl = mixed ? w.hl : nullptr;
         gm_status gs;
         if ((gs = mm(0, w.GG, m->W1t, m->W1t_h, H, NFP, w.Z)) != GM_OK) return fail(gs, "network GEMM 1 failed");
-        pg_act1(act, Mp, H, w.Z, m->b1, w.A1s, w.P1, w.Q1, w.Zd1, st);
+        pg_act1(act, Mp, H, w.Z, m->b1, w.A1s, w.P1, w.Q1, w.Zd1, hl, st);
         if ((gs = mm(1, w.A1s, m->W2t, m->W2t_h, H, H, w.Z)) != GM_OK) return fail(gs, "network GEMM 2 failed");
         pg_act2(act, N, Mp, H, B, sys->atom_ptr, sys->species, S, dL_dE, m->sigma, m->w3, m->b2, m->b3, w.Z, w.Zb2s,
-                w.Y3, w.t_sig, w.t_c, w.t_cs, st);
+                w.Y3, w.t_sig, w.t_c, w.t_cs, hl, st);
         // a1 adjoints (primal, tangent)
         if ((gs = mm(2, w.Zb2s, m->W2, m->W2_h, H, H, w.Z)) != GM_OK) return fail(gs, "network GEMM 3 failed");
-        pg_act1b(Mp, H, w.Z, w.P1, w.Q1, w.Zd1, w.Zb1s, st);
+        pg_act1b(Mp, H, w.Z, w.P1, w.Q1, w.Zd1, w.Zb1s, hl, st);
         // feature adjoints
         if ((gs = mm(3, w.Zb1s, m->W1p, m->W1p_h, NFP, H, w.Gbs)) != GM_OK) return fail(gs, "network GEMM 4 failed");
         // weight and bias gradients
         wgrad(w.GG, NFP, w.Zb1s, H, 2 * Mp, NFP, H, NF, w.wg_part, grad_theta + o.W1, st);
         wgrad(w.A1s, H, w.Zb2s, H, 2 * Mp, H, H, H, w.wg_part, grad_theta + o.W2, st);
-        colsum(Mp, H, w.Zb1s, w.wg_part, grad_theta + o.b1, st);
-        colsum(Mp, H, w.Zb2s, w.wg_part, grad_theta + o.b2, st);
-        colsum(Mp, H, w.Y3, w.wg_part, grad_theta + o.w3, st);
+        const float *cs_in[3] = {w.Zb1s, w.Zb2s, w.Y3};
+        float *const cs_out[3] = {grad_theta + o.b1, grad_theta + o.b2, grad_theta + o.w3};
+        colsum3(Mp, H, cs_in, cs_out, w.wg_part, st);
         pg_tail(N, sys->species, S, w.t_sig, w.t_c, w.t_cs, w.wg_part, grad_theta + o.sigma, grad_theta + o.mu,
                 grad_theta + o.b3, st);
     }

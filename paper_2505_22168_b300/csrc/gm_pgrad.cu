@@ -27,11 +27,20 @@ struct KahanSum {
     }
 };
 
+// The mixed path's next GEMM reads its A operand as hi/lo BF16 rows [hi(H) | lo(H)] of the
+// stacked [2 Mp] rows: the kernels that produce that operand write the copy as well (hl, or
+// null in the FP32 path), instead of a separate conversion pass.
+__device__ __forceinline__ void put_split(__nv_bfloat16 *hl, size_t row, int h, int H, float x) {
+    const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+    hl[row * 2 * H + h] = hi;
+    hl[row * 2 * H + H + h] = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
 template <int ACT>
 __global__ void __launch_bounds__(256) k_pg_act1(int Mp, int H, const float *__restrict__ Z,
                                                  const float *__restrict__ b1, float *__restrict__ A1s,
                                                  float *__restrict__ P1, float *__restrict__ Q1,
-                                                 float *__restrict__ Zd1) {
+                                                 float *__restrict__ Zd1, __nv_bfloat16 *__restrict__ hl) {
     const size_t n = (size_t)Mp * H;
     for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
         const int h = (int)(q % H);
@@ -43,6 +52,11 @@ __global__ void __launch_bounds__(256) k_pg_act1(int Mp, int H, const float *__r
         P1[q] = d1;
         Q1[q] = d2;
         Zd1[q] = zd;
+        if (hl) {
+            const size_t m = q / H;
+            put_split(hl, m, h, H, a);
+            put_split(hl, Mp + m, h, H, d1 * zd);
+        }
     }
 }
 
@@ -55,7 +69,7 @@ __global__ void __launch_bounds__(256) k_pg_act2(int N, int Mp, int H, int B, co
                                                  const float *__restrict__ b3, const float *__restrict__ Z,
                                                  float *__restrict__ Zb2s, float *__restrict__ Y3,
                                                  float *__restrict__ t_sig, float *__restrict__ t_c,
-                                                 float *__restrict__ t_cs) {
+                                                 float *__restrict__ t_cs, __nv_bfloat16 *__restrict__ hl) {
     const int m = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (m >= Mp) return;
     const size_t n = (size_t)Mp * H;
@@ -75,9 +89,14 @@ __global__ void __launch_bounds__(256) k_pg_act2(int N, int Mp, int H, int B, co
         nn = fmaf(w, a, nn);
         nnd = fmaf(w, ad, nnd);
         const float a2b = c * sg * w, da2b = -sg * w;
-        Zb2s[q] = d2 * zd * da2b + d1 * a2b;
-        Zb2s[n + q] = d1 * da2b;
+        const float zb = d2 * zd * da2b + d1 * a2b, zbd = d1 * da2b;
+        Zb2s[q] = zb;
+        Zb2s[n + q] = zbd;
         Y3[q] = c * sg * a - sg * ad;
+        if (hl) {
+            put_split(hl, m, h, H, zb);
+            put_split(hl, Mp + m, h, H, zbd);
+        }
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -93,25 +112,37 @@ __global__ void __launch_bounds__(256) k_pg_act2(int N, int Mp, int H, int B, co
 
 __global__ void __launch_bounds__(256) k_pg_act1b(int Mp, int H, const float *__restrict__ Ab,
                                                   const float *__restrict__ P1, const float *__restrict__ Q1,
-                                                  const float *__restrict__ Zd1, float *__restrict__ Zb1s) {
+                                                  const float *__restrict__ Zd1, float *__restrict__ Zb1s,
+                                                  __nv_bfloat16 *__restrict__ hl) {
     const size_t n = (size_t)Mp * H;
     for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
         const float ab = Ab[q], adb = Ab[n + q], p = P1[q];
-        Zb1s[q] = Q1[q] * Zd1[q] * adb + p * ab;
-        Zb1s[n + q] = p * adb;
+        const float zb = Q1[q] * Zd1[q] * adb + p * ab, zbd = p * adb;
+        Zb1s[q] = zb;
+        Zb1s[n + q] = zbd;
+        if (hl) {
+            const size_t m = q / H;
+            const int h = (int)(q - m * H);
+            put_split(hl, m, h, H, zb);
+            put_split(hl, Mp + m, h, H, zbd);
+        }
     }
 }
 
-// Column sums out[h] = sum_{m < M} A[m][h] of A [M][H]: block (column group of 32, chunk of
-// CS_ROWS rows) writes part[chunk][col]; k_colsum_final adds the chunks in a fixed order
-// (compensated).
+// Column sums out_a[h] = sum_{m < M} A_a[m][h] of up to three arrays A_a [M][H] in one launch
+// pair: block (column group of 32, chunk of CS_ROWS rows, array a) writes
+// part[a][chunk][col]; k_colsum_final adds the chunks in a fixed order (compensated).
 constexpr int CS_ROWS = 256;
-__global__ void __launch_bounds__(256) k_colsum_part(int M, int H, const float *__restrict__ A,
-                                                     float *__restrict__ part) {
+struct ColSums {
+    const float *A[3];
+    float *out[3];
+};
+__global__ void __launch_bounds__(256) k_colsum_part(int M, int H, ColSums cs, float *__restrict__ part) {
     __shared__ float sm[8][33];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int col = blockIdx.x * 32 + lane;
     const int r0 = blockIdx.y * CS_ROWS, r1 = min(M, r0 + CS_ROWS);
+    const float *__restrict__ A = cs.A[blockIdx.z];
     float s = 0.0f;
     if (col < H)
         for (int m = r0 + warp; m < r1; m += 8) s += A[(size_t)m * H + col];
@@ -121,18 +152,17 @@ __global__ void __launch_bounds__(256) k_colsum_part(int M, int H, const float *
         float t = 0.0f;
 #pragma unroll
         for (int w = 0; w < 8; ++w) t += sm[w][lane];
-        part[(size_t)blockIdx.y * H + col] = t;
+        part[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * H + col] = t;
     }
 }
 
-__global__ void __launch_bounds__(256) k_colsum_final(int chunks, int H, const float *__restrict__ part,
-                                                      float *__restrict__ out) {
+__global__ void __launch_bounds__(256) k_colsum_final(int chunks, int H, ColSums cs, const float *__restrict__ part) {
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
     if (h >= H) return;
     KahanSum k;
 #pragma unroll 8
-    for (int r = 0; r < chunks; ++r) k.add(part[(size_t)r * H + h]);
-    out[h] = k.s;
+    for (int r = 0; r < chunks; ++r) k.add(part[((size_t)blockIdx.y * chunks + r) * H + h]);
+    cs.out[blockIdx.y][h] = k.s;
 }
 
 // C_part[z][i][j] = sum_{k in slice z} A[k][i] B[k][j] (A [K][lda], B [K][ldb], row-major):
@@ -296,40 +326,45 @@ void split_bf16(const float *src, int rows, int K, __nv_bfloat16 *dst, cudaStrea
 }
 
 void pg_act1(int act, int Mp, int H, const float *Z, const float *b1, float *A1s, float *P1, float *Q1, float *Zd1,
-             cudaStream_t st) {
+             __nv_bfloat16 *hl, cudaStream_t st) {
     const int blocks = 148 * 8;
-    if (act == 0) k_pg_act1<0><<<blocks, 256, 0, st>>>(Mp, H, Z, b1, A1s, P1, Q1, Zd1);
-    else k_pg_act1<1><<<blocks, 256, 0, st>>>(Mp, H, Z, b1, A1s, P1, Q1, Zd1);
+    if (act == 0) k_pg_act1<0><<<blocks, 256, 0, st>>>(Mp, H, Z, b1, A1s, P1, Q1, Zd1, hl);
+    else k_pg_act1<1><<<blocks, 256, 0, st>>>(Mp, H, Z, b1, A1s, P1, Q1, Zd1, hl);
     note_launches(1);
 }
 
 void pg_act2(int act, int N, int Mp, int H, int B, const int32_t *atom_ptr, const int32_t *species, int S,
              const double *gE, const float *sigma, const float *w3, const float *b2, const float *b3, const float *Z,
-             float *Zb2s, float *Y3, float *t_sig, float *t_c, float *t_cs, cudaStream_t st) {
+             float *Zb2s, float *Y3, float *t_sig, float *t_c, float *t_cs, __nv_bfloat16 *hl, cudaStream_t st) {
     const int blocks = (Mp * 32 + 255) / 256;
     if (act == 0)
         k_pg_act2<0><<<blocks, 256, 0, st>>>(N, Mp, H, B, atom_ptr, species, S, gE, sigma, w3, b2, b3, Z, Zb2s, Y3,
-                                             t_sig, t_c, t_cs);
+                                             t_sig, t_c, t_cs, hl);
     else
         k_pg_act2<1><<<blocks, 256, 0, st>>>(N, Mp, H, B, atom_ptr, species, S, gE, sigma, w3, b2, b3, Z, Zb2s, Y3,
-                                             t_sig, t_c, t_cs);
+                                             t_sig, t_c, t_cs, hl);
     note_launches(1);
 }
 
 void pg_act1b(int Mp, int H, const float *Ab, const float *P1, const float *Q1, const float *Zd1, float *Zb1s,
-              cudaStream_t st) {
-    k_pg_act1b<<<148 * 8, 256, 0, st>>>(Mp, H, Ab, P1, Q1, Zd1, Zb1s);
+              __nv_bfloat16 *hl, cudaStream_t st) {
+    k_pg_act1b<<<148 * 8, 256, 0, st>>>(Mp, H, Ab, P1, Q1, Zd1, Zb1s, hl);
     note_launches(1);
 }
 
-void colsum(int M, int H, const float *A, float *part, float *out, cudaStream_t st) {
+void colsum3(int M, int H, const float *const A[3], float *const out[3], float *part, cudaStream_t st) {
     const int chunks = (M + CS_ROWS - 1) / CS_ROWS;
-    if (chunks > 0) k_colsum_part<<<dim3((H + 31) / 32, chunks), 256, 0, st>>>(M, H, A, part);
-    k_colsum_final<<<(H + 255) / 256, 256, 0, st>>>(chunks, H, part, out);
+    ColSums cs;
+    for (int a = 0; a < 3; ++a) {
+        cs.A[a] = A[a];
+        cs.out[a] = out[a];
+    }
+    if (chunks > 0) k_colsum_part<<<dim3((H + 31) / 32, chunks, 3), 256, 0, st>>>(M, H, cs, part);
+    k_colsum_final<<<dim3((H + 255) / 256, 3), 256, 0, st>>>(chunks, H, cs, part);
     note_launches(chunks > 0 ? 2 : 1);
 }
 
-size_t colsum_part_floats(int M, int H) { return (size_t)((M + CS_ROWS - 1) / CS_ROWS) * H; }
+size_t colsum_part_floats(int M, int H) { return 3 * (size_t)((M + CS_ROWS - 1) / CS_ROWS) * H; }
 
 // K slices of the weight gradient: enough 128 x 128 tile-slices for two blocks per SM, slices
 // of at least 128 rows, at most 128 slices

@@ -5,15 +5,17 @@
 
 namespace gm {
 
+// hl (mixed path; null in the FP32 path): the kernel also writes the hi/lo BF16 rows of the
+// stacked array it produces (A1s, Zb2s, Zb1s), the next GEMM's A operand
 void pg_act1(int act, int Mp, int H, const float *Z, const float *b1, float *A1s, float *P1, float *Q1, float *Zd1,
-             cudaStream_t st);
+             __nv_bfloat16 *hl, cudaStream_t st);
 void pg_act2(int act, int N, int Mp, int H, int B, const int32_t *atom_ptr, const int32_t *species, int S,
              const double *gE, const float *sigma, const float *w3, const float *b2, const float *b3, const float *Z,
-             float *Zb2s, float *Y3, float *t_sig, float *t_c, float *t_cs, cudaStream_t st);
+             float *Zb2s, float *Y3, float *t_sig, float *t_c, float *t_cs, __nv_bfloat16 *hl, cudaStream_t st);
 void pg_act1b(int Mp, int H, const float *Ab, const float *P1, const float *Q1, const float *Zd1, float *Zb1s,
-              cudaStream_t st);
-// out[h] = sum_{m < M} A[m][h]; part holds colsum_part_floats(M, H) floats
-void colsum(int M, int H, const float *A, float *part, float *out, cudaStream_t st);
+              __nv_bfloat16 *hl, cudaStream_t st);
+// out[a][h] = sum_{m < M} A[a][m][h] for three arrays [M][H]; part holds colsum_part_floats(M, H)
+void colsum3(int M, int H, const float *const A[3], float *const out[3], float *part, cudaStream_t st);
 size_t colsum_part_floats(int M, int H);
 int wgrad_ksplit(int K, int Mo, int No);
 // out[i][j] (i < Mstore) = sum_k A[k][i] B[k][j], A [K][lda], B [K][ldb]; part holds ksplit x Mo x No
