@@ -204,8 +204,9 @@ GM_API void gm_model_destroy(gm_model *m);
  *   GM_TUNE_DEBUG_STALL 0 (default).  For tests of failure reporting only: 1 makes block 0 of
  *                       the cooperative neighbour build return before the first grid barrier,
  *                       so the other blocks' bounded waits run out; 2 makes the first network
- *                       GEMM of gm_energy_forces (mixed path) issue no operand loads, so its MMA
- *                       and epilogue waits run out.  Either way GM_ERR_TIMEOUT is written to
+ *                       GEMM of gm_energy_forces (mixed path), or the fused network kernel where
+ *                       that runs, issue no operand loads, so its MMA and epilogue waits run
+ *                       out.  Either way GM_ERR_TIMEOUT is written to
  *                       *status_dev after about a second and every block returns; nothing
  *                       asynchronous is in flight when a wait gives up, and the next call with
  *                       the knob at 0 is unaffected.

@@ -723,7 +723,7 @@ enum { MLP_GEMMS = 0, MLP_TILE = 1, MLP_CLUSTER = 2 };
 static int mlp_form(const gm_model *m, bool ens, bool from_l2, const float *head, int n_atoms, int *cs) {
     *cs = 1;
     if (m->d.precision != GM_PREC_MIXED || m->fused_mlp == 0 || !m->f16_backward || !mlp_fused_supported(m->H) ||
-        ens || from_l2 || head != nullptr || (m->split_mask & 3) != 0 || m->debug_stall != 0)
+        ens || from_l2 || head != nullptr || (m->split_mask & 3) != 0)
         return MLP_GEMMS;
     const int tiles = (n_atoms + TILE_M - 1) / TILE_M;
     if (m->mlp_cluster >= 2) {
@@ -779,6 +779,7 @@ static gm_status network_fwd_bwd(const gm_model *m, const gm_system *sys, EfWs &
         fa.D1 = reinterpret_cast<__half *>(w.D1);
         fa.nn_part = w.nn_part;
         fa.dG = w.dG;
+        fa.debug_stall = m->debug_stall == 2 ? 1 : 0;
         StageScope sc(ST_MLP_FUSED, st);
         gm_status s;
         if (form == MLP_CLUSTER) {

@@ -81,6 +81,7 @@ struct FusedMlpArgs {
     const float *b1, *b2, *w3, *sigma;
     __half *D1;               // [M][H] FP16 phi'(z1) (scratch)
     float *nn_part, *dG;
+    int debug_stall = 0;      // failure-reporting tests: no operand loads, every wait runs out
     // cluster kernel only: [M][2H] scratch arrays through which the cluster gathers a1, dZ2
     // and dZ1 (first H columns), and the structure energies summed in the kernel (energy
     // null: not summed)

@@ -255,6 +255,7 @@ gm_status mlp_cluster(int act, int M, int H, int cs, const __nv_bfloat16 *G, con
     f.D1 = a.D1;
     f.nn_part = a.nn_part;
     f.dG = a.dG;
+    f.debug_stall = a.debug_stall;
     f.atom_ptr = a.atom_ptr;
     f.n_structures = a.n_structures;
     f.mu = a.mu;
@@ -293,6 +294,7 @@ gm_status mlp_fused(int act, int M, int H, const __nv_bfloat16 *G, const __nv_bf
     f.D1 = a.D1;
     f.nn_part = a.nn_part;
     f.dG = a.dG;
+    f.debug_stall = a.debug_stall;
     cudaError_t err;
     switch (H) {
     case 128: err = act == 0 ? launch_fused<128, 0>(maps, f, status, st) : launch_fused<128, 1>(maps, f, status, st); break;

@@ -51,6 +51,7 @@ struct ClusterArgs {
     float *nn_part;           // [M][H/32]
     // the gathered layers go through [M][2H] scratch arrays (first H columns): a1, dZ2, dZ1
     float *dG;                // [M][384]
+    int debug_stall;          // failure-reporting tests: the producer issues no loads at all
     // structure energies (null energy: the caller sums them)
     const int32_t *atom_ptr;
     int n_structures;
@@ -238,23 +239,25 @@ __global__ void __launch_bounds__(320, 1)
                 tma_load_2d(dst, &tmW1p, full + s, q * BK, (int)cr * WG);
                 return true;
             };
-            for (; issued < STAGES && issued < Sh::TILES; ++issued) tile(issued);
-            griddep_wait();
-            for (int kb = 0; kb < Sh::KBG; ++kb) {
-                mbar_expect_tx(g_full + kb, BM * 128);
-                tma_load_2d(X + (size_t)kb * BM * 128, &tmG, g_full + kb, kb * BK, m0);
-            }
-            for (; issued < Sh::TILES; ++issued)
-                if (!tile(issued)) {
-                    *abort_flag = 1;
-                    break;
+            if (!f.debug_stall) {
+                for (; issued < STAGES && issued < Sh::TILES; ++issued) tile(issued);
+                griddep_wait();
+                for (int kb = 0; kb < Sh::KBG; ++kb) {
+                    mbar_expect_tx(g_full + kb, BM * 128);
+                    tma_load_2d(X + (size_t)kb * BM * 128, &tmG, g_full + kb, kb * BK, m0);
                 }
-            if (*abort_flag) {
-                // let the copies already issued land before the CTA exits (bounded)
-                volatile int never = 0;
-                for (int kb = 0; kb < Sh::KBG; ++kb) mbar_wait(g_full + kb, 0, &never);
-                for (int t = (issued > STAGES ? issued - STAGES : 0); t < issued; ++t)
-                    mbar_wait(full + (t % STAGES), (t / STAGES) & 1, &never);
+                for (; issued < Sh::TILES; ++issued)
+                    if (!tile(issued)) {
+                        *abort_flag = 1;
+                        break;
+                    }
+                if (*abort_flag) {
+                    // let the copies already issued land before the CTA exits (bounded)
+                    volatile int never = 0;
+                    for (int kb = 0; kb < Sh::KBG; ++kb) mbar_wait(g_full + kb, 0, &never);
+                    for (int t = (issued > STAGES ? issued - STAGES : 0); t < issued; ++t)
+                        mbar_wait(full + (t % STAGES), (t / STAGES) & 1, &never);
+                }
             }
         }
         cluster_wait();

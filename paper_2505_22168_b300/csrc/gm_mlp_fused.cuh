@@ -33,6 +33,7 @@ struct FusedArgs {
                               // thread; it feeds an FP16 operand, dZ1 = dA1 phi'(z1), anyway)
     float *nn_part;           // [M][H/32]
     float *dG;                // [M][384]
+    int debug_stall;          // failure-reporting tests: the producer issues no loads at all
 };
 
 template <int H>
@@ -135,21 +136,23 @@ __global__ void __launch_bounds__(320, 1)
                 tma_load_2d(dst, &tmW1p, full + s, (q % Sh::KBH) * BK, (q / Sh::KBH) * Sh::B0N);
                 return true;
             };
-            for (; issued < STAGES && issued < Sh::TILES; ++issued) tile(issued);
-            griddep_wait();
-            mbar_expect_tx(g_full, Sh::KBG * BM * 128);
-            for (int kb = 0; kb < Sh::KBG; ++kb) tma_load_2d(X + (size_t)kb * BM * 128, &tmG, g_full, kb * BK, m0);
-            for (; issued < Sh::TILES; ++issued)
-                if (!tile(issued)) {
-                    *abort_flag = 1;
-                    break;
+            if (!f.debug_stall) {
+                for (; issued < STAGES && issued < Sh::TILES; ++issued) tile(issued);
+                griddep_wait();
+                mbar_expect_tx(g_full, Sh::KBG * BM * 128);
+                for (int kb = 0; kb < Sh::KBG; ++kb) tma_load_2d(X + (size_t)kb * BM * 128, &tmG, g_full, kb * BK, m0);
+                for (; issued < Sh::TILES; ++issued)
+                    if (!tile(issued)) {
+                        *abort_flag = 1;
+                        break;
+                    }
+                if (*abort_flag) {
+                    // let the copies already issued land before the CTA exits (bounded)
+                    volatile int never = 0;
+                    mbar_wait(g_full, 0, &never);
+                    for (int t = (issued > STAGES ? issued - STAGES : 0); t < issued; ++t)
+                        mbar_wait(full + (t % STAGES), (t / STAGES) & 1, &never);
                 }
-            if (*abort_flag) {
-                // let the copies already issued land before the CTA exits (bounded)
-                volatile int never = 0;
-                mbar_wait(g_full, 0, &never);
-                for (int t = (issued > STAGES ? issued - STAGES : 0); t < issued; ++t)
-                    mbar_wait(full + (t % STAGES), (t / STAGES) & 1, &never);
             }
         }
     } else if (warp == 9) {
