@@ -1132,9 +1132,10 @@ __device__ void ph_search_block(const NlArgs &a, int bid, int nb, float4 *smem) 
 }
 
 // ------------------------------------------------------------------ brute-force search
-// Small systems whose boxes are all at least 2.001 r_cut long on every axis: each neighbour
-// has exactly one image within r_cut (the minimum image), so a warp can test its atom
-// against every atom of its structure -- no histogram, scatter or sort phases.  The row
+// Structures of at most BR_MAXN atoms whose boxes are at least r_cut long on every axis (one
+// stencil cell per axis): a warp tests its atom against every atom of its structure -- no
+// histogram, scatter or sort phases.  From 2.001 r_cut each neighbour has exactly one image
+// within r_cut (the minimum image); shorter boxes take the multi-image row (brute_row_multi).  The row
 // comes out in the cell-list order all the same: with the cell grid of the setup, the
 // stencil cell of pair (i, j, n) is d = c_j + n nc - c_i per axis (in {-1, 0, 1}, cells
 // being at least r_cut long), and the accepted pairs, found in ascending j, are placed by a
@@ -1162,12 +1163,16 @@ constexpr size_t NL_BR_OFF = ((256 * sizeof(NlStruct) > 4097 * sizeof(int32_t) ?
 static_assert(NL_BR_OFF >= 2 * NL_SCAN_ONE_BLOCK * sizeof(int32_t), "row scan of the mid-size path");
 static_assert(NL_BR_OFF + NL_WARPS * sizeof(BrBuf) <= NL_SMEM, "brute-force buffers exceed the search's shared memory");
 
+// every structure has one stencil cell per axis (box edges at least r_cut: single-image rows
+// from 2 r_cut, multi-image rows below) and at most BR_MAXN atoms (the search is quadratic)
+constexpr int BR_MAXN = 2048;
 __device__ bool nl_brute_eligible(const NlArgs &a, const NlStruct *Ss) {
     bool ok = true;
     for (int b = threadIdx.x; b < a.B; b += blockDim.x) {
         const NlStruct &q = Ss[b];
+        ok = ok && q.n <= BR_MAXN;
 #pragma unroll
-        for (int d = 0; d < 3; ++d) ok = ok && q.K[d] == 1 && q.Lf[d] >= 2.001f * (float)a.rc;
+        for (int d = 0; d < 3; ++d) ok = ok && q.K[d] == 1 && q.Lf[d] >= 1.0001f * (float)a.rc;
     }
     return __syncthreads_and(ok);
 }
@@ -1273,6 +1278,97 @@ __device__ int brute_row(const NlArgs &a, const NlStruct &q, int i, int lane, Br
     return cnt;
 }
 
+// The same for a structure with some box edge shorter than 2 r_cut (but at least r_cut: one
+// cell and images n in {-1, 0, 1} of the wrapped positions per axis, so the stencil index of
+// the key stays below 27): per axis the minimum image and, when it is also within r_cut on
+// that axis, the other neighbouring image; every combination is tested (at most 8 per
+// candidate).  A lane's accepted entries of a chunk (0..8) are placed by a warp scan, in
+// candidate order and, within a candidate, in image order, so that the counting sort of the
+// emit orders the row by stencil cell, stable in j, as for the single-image boxes.
+__device__ int brute_row_multi(const NlArgs &a, const NlStruct &q, int i, int lane, BrBuf &bb) {
+    const unsigned full = 0xffffffffu;
+    const float4 xi = a.xs[i];
+    const float L0 = q.Lf[0], L1 = q.Lf[1], L2 = q.Lf[2];
+    const float iL0 = 1.0f / L0, iL1 = 1.0f / L1, iL2 = 1.0f / L2;
+    const float lo2 = a.rc2f - q.eps2, hi2 = a.rc2f + q.eps2;
+    // an image farther than this from the centre on one axis is out of range (a margin above
+    // the FP32 rounding of the per-axis displacement)
+    const float axis_cut = sqrtf(hi2) * 1.0001f;
+    const float sc0 = (float)q.nc[0], sc1 = 3.0f * (float)q.nc[1], sc2 = 9.0f * (float)q.nc[2];
+    const float soff = 13.0f - xi.w;
+    const int aend = q.a0 + q.n;
+    int cnt = 0;
+    const float4 far4 = make_float4(3.0e30f, 3.0e30f, 3.0e30f, 0.0f);
+    float4 xn = q.a0 + lane < aend ? a.xs[q.a0 + lane] : far4;
+    for (int b0 = q.a0; b0 < aend; b0 += 32) {
+        const float4 xb = xn;
+        const int j = b0 + lane;
+        xn = b0 + 32 + lane < aend ? a.xs[b0 + 32 + lane] : far4;     // the next chunk in flight
+        const float f0 = xb.x - xi.x, f1 = xb.y - xi.y, f2 = xb.z - xi.z;
+        const float m0 = -rintf(f0 * iL0), m1 = -rintf(f1 * iL1), m2 = -rintf(f2 * iL2);
+        const float e0 = fmaf(m0, L0, f0), e1 = fmaf(m1, L1, f1), e2 = fmaf(m2, L2, f2);
+        // the other neighbouring image per axis, and whether it can be in range
+        const float t0 = e0 > 0.0f ? -1.0f : 1.0f, t1 = e1 > 0.0f ? -1.0f : 1.0f, t2 = e2 > 0.0f ? -1.0f : 1.0f;
+        const float g0 = fmaf(m0 + t0, L0, f0), g1 = fmaf(m1 + t1, L1, f1), g2 = fmaf(m2 + t2, L2, f2);
+        const bool two0 = fabsf(g0) < axis_cut, two1 = fabsf(g1) < axis_cut, two2 = fabsf(g2) < axis_cut;
+        const bool valid = j < aend;
+        unsigned key[8], inm = 0u, bandm = 0u;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const bool x1 = k & 1, y1 = (k >> 1) & 1, z1 = (k >> 2) & 1;
+            const bool act = valid && (!x1 || two0) && (!y1 || two1) && (!z1 || two2);
+            const float dx = x1 ? g0 : e0, dy = y1 ? g1 : e1, dz = z1 ? g2 : e2;
+            const float n0 = x1 ? m0 + t0 : m0, n1 = y1 ? m1 + t1 : m1, n2 = z1 ? m2 + t2 : m2;
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            const bool other = act && (j != i || n0 != 0.0f || n1 != 0.0f || n2 != 0.0f);
+            inm |= (other && r2 < lo2) ? 1u << k : 0u;
+            bandm |= (other && r2 >= lo2 && r2 <= hi2) ? 1u << k : 0u;
+            const float st = fmaf(n2, sc2, fmaf(n1, sc1, fmaf(n0, sc0, xb.w + soff)));
+            const float img = fmaf(n2, 9.0f, fmaf(n1, 3.0f, n0 + 13.0f));
+            const unsigned v = (unsigned)__float_as_int(fmaf(st, 32.0f, img) + 8388608.0f);
+            key[k] = (v << 22) | (unsigned)j;
+        }
+        if (__any_sync(full, bandm != 0u)) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                if (!((bandm >> k) & 1u)) continue;
+                const bool x1 = k & 1, y1 = (k >> 1) & 1, z1 = (k >> 2) & 1;
+                const int n0 = (int)(x1 ? m0 + t0 : m0), n1 = (int)(y1 ? m1 + t1 : m1), n2 = (int)(z1 ? m2 + t2 : m2);
+                if (exact_inside(a.xw, j, a.xw[3 * i], a.xw[3 * i + 1], a.xw[3 * i + 2], n0, n1, n2, q,
+                                 __dmul_rn(a.rc, a.rc)))
+                    inm |= 1u << k;
+            }
+        }
+        const int c = __popc(inm);
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(full, incl, o);
+            if (lane >= o) incl += y;
+        }
+        int pos = cnt + incl - c;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if ((inm >> k) & 1u) {
+                if (pos < BR_CAP) bb.key[pos] = key[k];
+                ++pos;
+            }
+        }
+        cnt += __shfl_sync(full, incl, 31);
+    }
+    return cnt;
+}
+
+// boxes shorter than 2 r_cut on some axis take the multi-image row
+__device__ __forceinline__ bool brute_multi(const NlArgs &a, const NlStruct &q) {
+    const float two = 2.001f * (float)a.rc;
+    return q.Lf[0] < two || q.Lf[1] < two || q.Lf[2] < two;
+}
+
+__device__ __forceinline__ int brute_row_any(const NlArgs &a, const NlStruct &q, int i, int lane, BrBuf &bb) {
+    return brute_multi(a, q) ? brute_row_multi(a, q, i, lane, bb) : brute_row(a, q, i, lane, bb);
+}
+
 // The buffered row (cnt <= BR_CAP entries) in stencil order, stable in j: into slab row i
 // (codes; returns false when a shift has no code) or, with csr >= 0, into the CSR list at csr
 // (slab rows go to dst: the slab row of i, or the warp buffer's row for the direct write)
@@ -1339,7 +1435,7 @@ __device__ void ph_search_brute(const NlArgs &a, int bid, int nb, const NlStruct
     const int rot = bid >= (nb >> 1) ? NL_WARPS / 4 : 0;
     for (int i = ((warp - rot + NL_WARPS) % NL_WARPS) * nb + bid; i < a.N; i += NL_WARPS * nb) {
         const NlStruct &q = Ss[structure_of(a.atom_ptr, a.B, i)];
-        const int cnt = brute_row(a, q, i, lane, bb);
+        const int cnt = brute_row_any(a, q, i, lane, bb);
         if (cnt > BR_CAP) {
             if (lane == 0) atomicExch(a.brute_over, 1);
             continue;
@@ -1423,7 +1519,7 @@ __device__ void ph_compact(const NlArgs &a, int bid, int nb, const int32_t *row_
         const int i = a.redo_list[r];
         if (brute) {                                   // rows of the brute-force search (<= BR_CAP)
             BrBuf &bb = brute[warp];
-            const int cnt = brute_row(a, a.S[structure_of(a.atom_ptr, a.B, i)], i, lane, bb);
+            const int cnt = brute_row_any(a, a.S[structure_of(a.atom_ptr, a.B, i)], i, lane, bb);
             brute_emit(a, i, min(cnt, BR_CAP), lane, bb, row_ptr[i]);
             continue;
         }
@@ -1489,6 +1585,31 @@ __device__ bool nl_brute_build(const NlArgs &a, int bid, int nb, NlStruct *Ss, i
     return true;
 }
 
+// The brute-force search for a batch of many small structures (the grids already in a.S, set
+// up by block 0): wrap, search into the slab, the row scan over the whole batch, compaction.
+// Returns false when a row was longer than BR_CAP (the cell-list phases build the list).
+__device__ bool nl_brute_build_batch(const NlArgs &a, int bid, int nb, float4 *smem) {
+    BrBuf *bufs = reinterpret_cast<BrBuf *>(reinterpret_cast<char *>(smem) + NL_BR_OFF);
+    ph_wrap_brute(a, bid, nb, a.S);
+    if (!nl_grid_sync(a.bar, a.status)) return true;
+    ph_search_brute(a, bid, nb, a.S, bufs);
+    if (!nl_grid_sync(a.bar, a.status)) return true;
+    if (*reinterpret_cast<volatile int *>(a.brute_over) != 0) {
+        if (bid == 0 && threadIdx.x == 0) *a.n_redo = 0;
+        return false;
+    }
+    if (a.N <= NL_SCAN_ONE_BLOCK) {
+        run_phase(a, PH_SCAN_ROWS_ONE, bid, nb, smem);
+    } else {
+        run_phase(a, PH_SCAN1_ROWS, bid, nb, smem);
+        if (!nl_grid_sync(a.bar, a.status)) return true;
+        run_phase(a, PH_SCAN2_ROWS, bid, nb, smem);
+    }
+    if (!nl_grid_sync(a.bar, a.status)) return true;
+    ph_compact(a, bid, nb, a.row_ptr, bufs);
+    return true;
+}
+
 __global__ void __launch_bounds__(NL_THREADS, 2) k_nl_coop(NlArgs a) {
     extern __shared__ float4 nl_smem[];
     const int bid = blockIdx.x, nb = gridDim.x;
@@ -1540,6 +1661,9 @@ __global__ void __launch_bounds__(NL_THREADS, 2) k_nl_coop(NlArgs a) {
     if (!a.mid) {
         run_phase(a, PH_SETUP, bid, nb, nl_smem);
         if (!nl_grid_sync(a.bar, a.status)) return;
+        // a batch of small structures: the brute-force search per structure (a row longer
+        // than BR_CAP sends the build on to the phases below)
+        if (a.try_brute && nl_brute_eligible(a, a.S) && nl_brute_build_batch(a, bid, nb, nl_smem)) return;
     }
     run_phase(a, PH_BIN, bid, nb, nl_smem);
     if (!nl_grid_sync(a.bar, a.status)) return;
@@ -1746,8 +1870,9 @@ gm_status nl_build(const gm_system &sys, double r_cut, int n_species, gm_nlist &
         return GM_ERR_CUDA;
     }
     a.small = (N + B <= NL_SCAN_ONE_BLOCK && B <= 256) ? 1 : 0;
-    // brute-force search (small systems, single-image boxes; decided on the device) unless the
-    // work items are set to cells, or there is no slab
+    // brute-force search (small systems and batches of small structures whose boxes are at least
+    // r_cut long; decided on the device) unless the work items are set to cells, or there is no
+    // slab
     a.try_brute = (tune.items == 0 || tune.items == 3) && a.maxn > 0 ? 1 : 0;
     a.mid = (!a.small && a.try_brute && N + B <= 2 * NL_SCAN_ONE_BLOCK && B <= 256) ? 1 : 0;
     a.brute_over = w.brute_over;

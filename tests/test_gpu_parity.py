@@ -115,7 +115,8 @@ def _ragged_batch():
 
 def _mid_size_li3po4():
     """Li3PO4-like boxes, some shorter than 2 r_cut, with 4096 < atoms + boxes <= 8192: the
-    mid-size cooperative path, whose boxes rule out the brute-force search."""
+    mid-size cooperative path, whose short boxes take the multi-image rows of the brute-force
+    search."""
     b3, d, p = synth.config(3)
     k, n = 0, 0
     while n + k + 1 + (b3.atom_ptr[k + 1] - b3.atom_ptr[k]) <= 8000:
@@ -127,11 +128,23 @@ def _mid_size_li3po4():
     return b, d, p
 
 
+def _batch_li3po4(n_struct=40):
+    """The first boxes of the Li3PO4-like batch, more than 8192 atoms + boxes (the general
+    cooperative path), some boxes shorter than 2 r_cut (multi-image rows)."""
+    b3, d, p = synth.config(3)
+    b = subset(b3, range(n_struct))
+    assert b.n_atoms + b.n_structures > 8192
+    assert (b.cell[:, 0, 0] < 2.001 * d["r_cut"]).any()
+    return b, d, p
+
+
 @pytest.mark.parametrize("case", ["config1", "li_small", "config2", "ragged", "shifted", "train_batch",
-                                  "mid_multi_image"])
+                                  "mid_multi_image", "batch_multi_image"])
 def test_neighbor_build_launch_shapes_give_identical_rows(case, li_small):
-    """(train_batch: 32 EMIM boxes, 7920 atoms -- the mid-size path's brute-force search;
-    mid_multi_image: the same path falling back to the cell list.)"""
+    """Every launch shape, the cell-list searches (nl_items 1, 2) included, gives the oracle's
+    pairs in the same rows and order.  (train_batch: 32 EMIM boxes, 7920 atoms -- the mid-size
+    path's brute-force search; mid_multi_image: the same path with multi-image rows;
+    batch_multi_image: the brute-force search of the general path, multi-image rows.)"""
     GMNN, DeviceSystem = _gm()
     if case == "li_small":
         b, d, p = li_small
@@ -141,6 +154,8 @@ def test_neighbor_build_launch_shapes_give_identical_rows(case, li_small):
         assert (b.cell[:, 0, 0] >= 2.001 * d["r_cut"]).all()
     elif case == "mid_multi_image":
         b, d, p = _mid_size_li3po4()
+    elif case == "batch_multi_image":
+        b, d, p = _batch_li3po4()
     elif case == "ragged":
         _, d, p = synth.config(1)
         b, d = _ragged_batch(), dict(d, r_cut=3.3)
