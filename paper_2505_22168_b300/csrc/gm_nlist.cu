@@ -1162,6 +1162,19 @@ constexpr size_t NL_BR_OFF = ((256 * sizeof(NlStruct) > 4097 * sizeof(int32_t) ?
 // the row scan of the mid-size brute-force path: N + 1 <= 2 NL_SCAN_ONE_BLOCK entries
 static_assert(NL_BR_OFF >= 2 * NL_SCAN_ONE_BLOCK * sizeof(int32_t), "row scan of the mid-size path");
 static_assert(NL_BR_OFF + NL_WARPS * sizeof(BrBuf) <= NL_SMEM, "brute-force buffers exceed the search's shared memory");
+// the batch path's copy of atom_ptr sits after the row buffers (at most BR_PTR_MAX entries)
+constexpr size_t NL_BR_PTR_OFF = NL_BR_OFF + NL_WARPS * sizeof(BrBuf);
+constexpr int BR_PTR_MAX = (int)((NL_SMEM - NL_BR_PTR_OFF) / sizeof(int32_t));
+
+// structure of atom i from a copy of atom_ptr (shared or global memory)
+__device__ __forceinline__ int structure_in(const int32_t *ptr, int n_struct, int i) {
+    int lo = 0, hi = n_struct - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (ptr[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
 
 // every structure has one stencil cell per axis (box edges at least r_cut: single-image rows
 // from 2 r_cut, multi-image rows below) and at most BR_MAXN atoms (the search is quadratic)
@@ -1181,7 +1194,7 @@ __device__ bool nl_brute_eligible(const NlArgs &a, const NlStruct *Ss) {
 // c_x + 3 c_y + 9 c_z (as a float) in w, indexed by atom.  One lane per axis (ten atoms per
 // warp, lanes 30 and 31 idle): the FP64 wrap of an atom runs on three lanes at once, and its
 // axis-0 lane gathers the other two by shuffles.
-__device__ void ph_wrap_brute(const NlArgs &a, int bid, int nb, const NlStruct *S) {
+__device__ void ph_wrap_brute(const NlArgs &a, int bid, int nb, const NlStruct *S, const int32_t *sptr = nullptr) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31, ga = lane / 3, d = lane - 3 * ga;
     const int l1 = min(3 * ga + 1, 31), l2 = min(3 * ga + 2, 31);
@@ -1191,7 +1204,7 @@ __device__ void ph_wrap_brute(const NlArgs &a, int bid, int nb, const NlStruct *
         float wf = 0.0f;
         int c = 0;
         if (act) {
-            const NlStruct &q = S[structure_of(a.atom_ptr, a.B, i)];
+            const NlStruct &q = S[sptr ? structure_in(sptr, a.B, i) : structure_of(a.atom_ptr, a.B, i)];
             if (d == 0) {
                 const int z = a.species[i];
                 if (z < 0 || z >= a.n_species) set_status(a.status, GM_ERR_SPECIES);
@@ -1427,18 +1440,18 @@ __device__ bool brute_emit(const NlArgs &a, int i, int cnt, int lane, BrBuf &bb,
 // there (brute_direct); otherwise it goes to the slab.
 __device__ __forceinline__ bool brute_direct(const NlArgs &a, int nb) { return a.N <= nb * NL_WARPS; }
 
-__device__ void ph_search_brute(const NlArgs &a, int bid, int nb, const NlStruct *Ss, BrBuf *bufs) {
+__device__ void ph_search_brute(const NlArgs &a, int bid, int nb, const NlStruct *Ss, BrBuf *bufs,
+                                const int32_t *sptr = nullptr) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     BrBuf &bb = bufs[warp];
     const bool direct = brute_direct(a, nb);
     if (lane == 0) bb.rowi = -1;
-    const int rot = bid >= (nb >> 1) ? NL_WARPS / 4 : 0;
-    for (int i = ((warp - rot + NL_WARPS) % NL_WARPS) * nb + bid; i < a.N; i += NL_WARPS * nb) {
-        const NlStruct &q = Ss[structure_of(a.atom_ptr, a.B, i)];
+    auto row = [&](int i) {
+        const NlStruct &q = Ss[sptr ? structure_in(sptr, a.B, i) : structure_of(a.atom_ptr, a.B, i)];
         const int cnt = brute_row_any(a, q, i, lane, bb);
         if (cnt > BR_CAP) {
             if (lane == 0) atomicExch(a.brute_over, 1);
-            continue;
+            return;
         }
         bool over = !direct && cnt > a.maxn;
         if (!over) over = !brute_emit(a, i, cnt, lane, bb, -1, direct ? bb.row : nullptr);
@@ -1451,7 +1464,9 @@ __device__ void ph_search_brute(const NlArgs &a, int bid, int nb, const NlStruct
                 bb.rowcnt = cnt;
             }
         }
-    }
+    };
+    const int rot = bid >= (nb >> 1) ? NL_WARPS / 4 : 0;
+    for (int i = ((warp - rot + NL_WARPS) % NL_WARPS) * nb + bid; i < a.N; i += NL_WARPS * nb) row(i);
 }
 
 // Compaction after the slab pass: each warp copies NL_COPY_ROWS slab rows at a time into
@@ -1590,9 +1605,28 @@ __device__ bool nl_brute_build(const NlArgs &a, int bid, int nb, NlStruct *Ss, i
 // Returns false when a row was longer than BR_CAP (the cell-list phases build the list).
 __device__ bool nl_brute_build_batch(const NlArgs &a, int bid, int nb, float4 *smem) {
     BrBuf *bufs = reinterpret_cast<BrBuf *>(reinterpret_cast<char *>(smem) + NL_BR_OFF);
-    ph_wrap_brute(a, bid, nb, a.S);
+    // each block copies the structure grids (up to 256) and atom_ptr into shared memory: the
+    // structure of a row or an atom is then a search in shared memory, not eight dependent
+    // global loads (256-box batch: build 188 -> 173 us)
+    const NlStruct *Ss = a.S;
+    if (a.B <= 256) {
+        static_assert(sizeof(NlStruct) % 16 == 0, "16-byte copies of the structure grids");
+        constexpr int W4 = (int)(sizeof(NlStruct) / 16);
+        const float4 *src = reinterpret_cast<const float4 *>(a.S);
+        float4 *dst = reinterpret_cast<float4 *>(smem);
+        for (int k = threadIdx.x; k < a.B * W4; k += NL_THREADS) dst[k] = src[k];
+        Ss = reinterpret_cast<const NlStruct *>(smem);
+    }
+    const int32_t *sptr = nullptr;
+    if (a.B + 1 <= BR_PTR_MAX) {
+        int32_t *sp = reinterpret_cast<int32_t *>(reinterpret_cast<char *>(smem) + NL_BR_PTR_OFF);
+        for (int b = threadIdx.x; b <= a.B; b += NL_THREADS) sp[b] = a.atom_ptr[b];
+        sptr = sp;
+    }
+    __syncthreads();
+    ph_wrap_brute(a, bid, nb, Ss, sptr);
     if (!nl_grid_sync(a.bar, a.status)) return true;
-    ph_search_brute(a, bid, nb, a.S, bufs);
+    ph_search_brute(a, bid, nb, Ss, bufs, sptr);
     if (!nl_grid_sync(a.bar, a.status)) return true;
     if (*reinterpret_cast<volatile int *>(a.brute_over) != 0) {
         if (bid == 0 && threadIdx.x == 0) *a.n_redo = 0;
