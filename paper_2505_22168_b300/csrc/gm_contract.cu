@@ -861,11 +861,10 @@ static_assert(ct_fwd_dual_smem() <= 227 * 1024 && ct_bwd_dual_smem() <= 227 * 10
 
 void launch_contract_fwd_dual(const float *psi, const float *psid, int N, int Mp, float *GG, cudaStream_t st) {
     const int blocks = (Mp + CT_ATOMS - 1) / CT_ATOMS;
-    static bool attr = false;
-    if (!attr) {
+    static PerDeviceOnce attr;
+    if (attr.first()) {
         cudaFuncSetAttribute(k_contract_fwd_dual<CT_FWD_DUAL_W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)ct_fwd_dual_smem());
-        attr = true;
     }
     if (blocks > 0) {
         launch_pdl(k_contract_fwd_dual<CT_FWD_DUAL_W>, dim3(blocks), dim3(CT_FWD_DUAL_W * 32), ct_fwd_dual_smem(), st,
@@ -877,11 +876,10 @@ void launch_contract_fwd_dual(const float *psi, const float *psid, int N, int Mp
 void launch_contract_bwd_dual(const float *psi, const float *psid, const float *Gbs, int N, int Mp, float *psib,
                               float *psidb, cudaStream_t st) {
     const int blocks = (N + CT_ATOMS - 1) / CT_ATOMS;
-    static bool attr = false;
-    if (!attr) {
+    static PerDeviceOnce attr;
+    if (attr.first()) {
         cudaFuncSetAttribute(k_contract_bwd_dual<CT_BWD_DUAL_W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)ct_bwd_dual_smem());
-        attr = true;
     }
     if (blocks > 0) {
         launch_pdl(k_contract_bwd_dual<CT_BWD_DUAL_W>, dim3(blocks), dim3(CT_BWD_DUAL_W * 32), ct_bwd_dual_smem(), st,
@@ -916,10 +914,9 @@ static int sm_count() {
 template <typename OutT, int W>
 static void launch_fwd_w(int blocks, const float *psi, int N, int Mp, OutT *G, float *features_out, int lo_out,
                          cudaStream_t st) {
-    static bool attr = false;
-    if (!attr) {
+    static PerDeviceOnce attr;
+    if (attr.first()) {
         cudaFuncSetAttribute(k_contract_fwd<OutT, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ct_fwd_smem());
-        attr = true;
     }
     launch_pdl(k_contract_fwd<OutT, W>, dim3(blocks), dim3(W * 32), ct_fwd_smem(), st, psi, N, Mp, G, features_out,
                lo_out);
@@ -948,10 +945,9 @@ void launch_contract_fwd_bf16(const float *psi, int N, int Mp, __nv_bfloat16 *G,
 
 template <int W>
 static void launch_bwd_w(int blocks, const float *psi, const float *dG, int N, float *dpsi, cudaStream_t st) {
-    static bool attr = false;
-    if (!attr) {
+    static PerDeviceOnce attr;
+    if (attr.first()) {
         cudaFuncSetAttribute(k_contract_bwd<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ct_bwd_smem<W>());
-        attr = true;
     }
     launch_pdl(k_contract_bwd<W>, dim3(blocks), dim3(W * 32), ct_bwd_smem<W>(), st, psi, dG, N, dpsi);
     note_launches(1);

@@ -59,13 +59,12 @@ bool tensor_map(const void *base, int inner, int rows, int box_rows, CUtensorMap
 template <int BN, int EPI, int ACT, int CPS>
 cudaError_t launch_tc(const CUtensorMap &ma, const CUtensorMap &mb, int M, int N, int K, int split,
                       const EpiArgs &e, int32_t *status, cudaStream_t st, int f16) {
-    static bool attr_set = false;
+    static PerDeviceOnce attr_set;
     const size_t smem = tc::smem_bytes_for(BN, CPS);
-    if (!attr_set) {
+    if (attr_set.first()) {
         cudaError_t err = cudaFuncSetAttribute(tc::k_gemm_tc<BN, EPI, ACT, CPS>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return err;
-        attr_set = true;
     }
     dim3 grid(N / BN, M / tc::BM);
     launch_pdl(tc::k_gemm_tc<BN, EPI, ACT, CPS>, grid, dim3(256), smem, st, ma, mb, M, N, K, split, e, status, f16);
@@ -139,12 +138,11 @@ namespace {
 template <int H, int ACT>
 cudaError_t launch_fused(const CUtensorMap *maps, const tc::FusedArgs &f, int32_t *status, cudaStream_t st) {
     using Sh = tc::FusedShape<H>;
-    static bool attr_set = false;
-    if (!attr_set) {
+    static PerDeviceOnce attr_set;
+    if (attr_set.first()) {
         cudaError_t err = cudaFuncSetAttribute(tc::k_mlp_fused<H, ACT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)Sh::SMEM);
         if (err != cudaSuccess) return err;
-        attr_set = true;
     }
     launch_pdl(tc::k_mlp_fused<H, ACT>, dim3(f.M / tc::BM), dim3(320), Sh::SMEM, st, maps[0], maps[1], maps[2],
                maps[3], maps[4], f, status);

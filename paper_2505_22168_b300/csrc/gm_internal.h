@@ -12,6 +12,19 @@
 namespace gm {
 
 // Bump allocator over the caller's workspace (256-byte aligned slices).
+// Kernel attributes (cudaFuncSetAttribute) belong to the current device: a launcher keeps one
+// flag per device and sets them the first time it launches on that device.
+struct PerDeviceOnce {
+    bool done[64] = {};
+    bool first() {
+        int d = 0;
+        if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= 64) return true;
+        if (done[d]) return false;
+        done[d] = true;
+        return true;
+    }
+};
+
 struct Carve {
     char *base;
     size_t off, cap;

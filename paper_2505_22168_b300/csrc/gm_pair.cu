@@ -613,10 +613,9 @@ static void launch_moments_t(const PairArgs &a, float *psi, cudaStream_t st) {
     const long long total = (long long)a.N * TPA;
     const int blocks = (int)((total + threads - 1) / threads);
     const size_t smem = beta_smem_bytes(a.S);
-    static bool attr = false;
-    if (!attr) {
+    static PerDeviceOnce attr;
+    if (attr.first()) {
         allow_beta_smem(k_moments<TPA, BAS>);
-        attr = true;
     }
     if (blocks > 0) {
         launch_pdl(k_moments<TPA, BAS>, dim3(blocks), dim3(threads), smem, st, a, psi);
@@ -631,10 +630,9 @@ static void launch_forces_t(const PairArgs &a, const float *dpsi, float *F, floa
     const int blocks = (int)((total + threads - 1) / threads);
     const size_t smem = beta_smem_bytes(a.S) +
                         (forces_gsmem<TPA>() ? sizeof(float) * (threads / TPA) * FG_ROW : 0);
-    static bool attr = false;
-    if (!attr) {
+    static PerDeviceOnce attr;
+    if (attr.first()) {
         allow_beta_smem(k_forces<TPA, BAS>, forces_gsmem<TPA>() ? sizeof(float) * (threads / TPA) * FG_ROW : 0);
-        attr = true;
     }
     if (blocks > 0) {
         launch_pdl(k_forces<TPA, BAS>, dim3(blocks), dim3(threads), smem, st, a, dpsi, F, vir);
@@ -686,10 +684,9 @@ static void launch_tangent_t(const PairArgs &a, const float *vel, float *psid, c
     const long long total = (long long)a.N * TPA;
     const int blocks = (int)((total + threads - 1) / threads);
     const size_t smem = beta_smem_bytes(a.S);
-    static bool attr = false;
-    if (!attr) {
+    static PerDeviceOnce attr;
+    if (attr.first()) {
         allow_beta_smem(k_moments_tangent<TPA, BAS>);
-        attr = true;
     }
     if (blocks > 0) {
         launch_pdl(k_moments_tangent<TPA, BAS>, dim3(blocks), dim3(threads), smem, st, a, vel, psid);
