@@ -24,6 +24,7 @@ SPACE = {
     "forces_tpa": (0, 8, 16, 32),
     "gemm_bn": (0, 64, 128, 256),
     "gemm_cps": (0, 1, 2),
+    "mlp_cluster": (0, 1, 2, 4, 8),
 }
 
 
@@ -63,6 +64,7 @@ def tune(model, sysd, nl, out, reps=20, cache: str | os.PathLike | None = None, 
     if model.precision != "mixed":
         space.pop("gemm_bn", None)            # the FP32 path has no tensor-core tiles
         space.pop("gemm_cps", None)
+        space.pop("mlp_cluster", None)
     if timer is None:
         def timer(m):
             return time_step(m, sysd, nl, out, reps)

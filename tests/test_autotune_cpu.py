@@ -28,7 +28,7 @@ def test_coordinate_descent_finds_the_separable_minimum():
     m = FakeModel()
     r = autotune.tune(m, None, None, None, timer=cost, key="k")
     assert r["settings"] == {"nl_items": 1, "nl_split": 4, "pair_tpa": 8, "forces_tpa": 16, "gemm_bn": 128,
-                             "gemm_cps": 2}
+                             "gemm_cps": 2, "mlp_cluster": 0}
     assert m.tuning == r["settings"]
     assert r["ms"] == min(ms for _, ms in r["trials"])
     assert r["default_ms"] == r["trials"][0][1]
@@ -38,7 +38,7 @@ def test_fp32_models_skip_the_tensor_core_knob():
     m = FakeModel()
     m.precision = "fp32"
     r = autotune.tune(m, None, None, None, timer=cost, key="k")
-    assert "gemm_bn" not in r["settings"] and "gemm_cps" not in r["settings"]
+    assert "gemm_bn" not in r["settings"] and "gemm_cps" not in r["settings"] and "mlp_cluster" not in r["settings"]
 
 
 def test_cache_round_trip(tmp_path):
