@@ -7,9 +7,11 @@
 //   L2 GEMM  A1 W2         -> dZ2, partial output sums (energies)
 //   B1 GEMM  dZ2 W2^T      -> dZ1
 //   B0 GEMM  dZ1 W1^T      -> dG [Mp][384]
+//     (mixed path: the four layers may run as one kernel per tile or per cluster, mlp_form)
 //   contraction backward   -> dpsi [N][100]
 //   forces (pair kernel)   -> F [N][3], per-atom virial
-//   per-structure FP64 reduction -> E [B], W [B][9]
+//   per-structure FP64 reduction -> E [B], W [B][9]  (without the virial, the mixed path sums
+//                             the energies inside the B1 GEMM or the cluster kernel)
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>

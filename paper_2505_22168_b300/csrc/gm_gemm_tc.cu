@@ -1,4 +1,6 @@
-// gm_gemm_tc.cu -- host side of the tcgen05 BF16 GEMM: TMA tensor maps, tile choice, launch.
+// gm_gemm_tc.cu -- host side of the tcgen05 network kernels: TMA tensor maps (cached by base,
+// shape and box), tile choice and launch of the GEMM (gm_gemm_tc.cuh), of the four layers
+// fused per tile (gm_mlp_fused.cuh) and per thread-block cluster (gm_mlp_cluster.cuh).
 #include <cudaTypedefs.h>
 
 #include <map>
