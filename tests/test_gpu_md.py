@@ -35,9 +35,11 @@ def _system(units=(24,), seed=777):
     return b, d, p, masses, vel
 
 
-def _gpu_md(b, d, p, masses, vel, params, n_steps, precision="fp32", chunks=1, graph=False):
+def _gpu_md(b, d, p, masses, vel, params, n_steps, precision="fp32", chunks=1, graph=False, tune=None):
     from paper_2505_22168_b300 import GMNN, DeviceSystem, MDState
     m = GMNN(d, p, precision=precision)
+    if tune:
+        m.set_tuning(**tune)
     sysd = DeviceSystem(b)
     nl = m.md_neighbor_list(sysd, params)
     st = MDState(sysd, masses, vel)
@@ -107,6 +109,21 @@ def test_md_matches_oracle_with_skin_rebuilds(ensemble, precision):
     assert 3 <= builds < n // 4, builds                   # the list was reused between rebuilds
     ref = _oracle_md(b, d, p, masses, vel, params, n)
     _compare(st, ref, b, masses, params, precision, n)
+
+
+@pytest.mark.parametrize("cs", [1, 2, 4])
+def test_md_with_the_fused_network_kernels(cs):
+    """The same NVT run on the mixed path with the network as one kernel per tile (cs 1) or a
+    cluster of 2 or 4 CTAs per tile (the forms the library picks for mid-size and large MD
+    systems; the 192-atom box would take the four GEMM launches): the same bounds."""
+    from paper_2505_22168_b300 import MDParams
+    b, d, p, masses, vel = _system()
+    params = MDParams(dt=0.5, skin=0.2, temperature=600.0, tau=5.0, ensemble="nvt")
+    n = 120
+    _, _, _, st = _gpu_md(b, d, p, masses, vel, params, n, "mixed", graph=True,
+                          tune=dict(fused_mlp=1, mlp_cluster=cs))
+    ref = _oracle_md(b, d, p, masses, vel, params, n)
+    _compare(st, ref, b, masses, params, "mixed", n)
 
 
 def test_skin_list_holds_every_pair_within_the_cutoff():
