@@ -157,7 +157,8 @@ GM_API void gm_model_destroy(gm_model *m);
 /* Tuning knobs of a model (they change speed, not results beyond rounding; the neighbour
  * knobs change nothing in the list):
  *   GM_TUNE_PAIR_TPA    lanes per atom in the pair kernels: 0 = by system size, or 1, 2, 4, 8, 16, 32
- *                       (the force kernel too, unless GM_TUNE_FORCES_TPA is set)
+ *                       (the force kernel too, unless GM_TUNE_FORCES_TPA is set; with 2 and 4 the
+ *                       moments kernel splits an atom's components over lane pairs)
  *   GM_TUNE_FORCES_TPA  lanes per atom of the force kernel alone: 0 = as GM_TUNE_PAIR_TPA (or by
  *                       size when that is 0), or 1, 2, 4, 8, 16, 32
  *   GM_TUNE_SPLIT_MASK  mixed path: network GEMMs that run with hi/lo split-BF16 operands

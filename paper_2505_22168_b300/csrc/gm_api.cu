@@ -441,18 +441,27 @@ PairArgs pair_args(const gm_model *m, const gm_system *s, const gm_nlist *nl, co
     return a;
 }
 
-// Lanes per atom of the moments kernel (and the tangent moments), measured on B300 over
-// Li3PO4-like crystals of 4k-131k atoms, the 1536-atom EMIM box and the 7920-atom training
-// batch: the best shape follows the waves of the 128-thread blocks (8 at 4096 atoms, 32 at
-// 8192, 4 at 16384, 8 at 32768), then one lane per atom (its 100 sums in registers) from ~49k
+// Lanes per atom of the moments kernel, measured on B300 over Li3PO4-like crystals of 4k-131k
+// atoms, the 256-box batch, the 1536-atom EMIM box and the 7920-atom training batch: the
+// reduce-scatter kernel's 128-thread blocks below 12k atoms (8 at 4096, 32 at 8192), then the
+// component-split kernel (two lanes of a pair keep 50 sums each, two blocks per SM) with 4
+// lanes per atom, and with 2 from ~25k (131,072 atoms 320 -> 265 us, the batch 112 -> 101 us
+// against one lane per atom)
 int choose_tpa(const gm_model *m, int N) {
     if (m->pair_tpa > 0) return m->pair_tpa;
-    if (N >= 49152) return 1;
-    if (N >= 24576) return 8;
+    if (N >= 24576) return 2;
     if (N >= 12288) return 4;
     if (N >= 6144) return 32;
     if (N >= 3072) return 8;
     return 32;
+}
+
+// Lanes per atom of the tangent moments (parameter gradient): at most 4, as the kernel sums
+// its 100 accumulators over the lanes with a plain all-reduce (8 lanes took 101 us against
+// 57 us for 4 at 7920 atoms); one lane per atom from ~49k atoms
+int choose_tangent_tpa(const gm_model *m, int N) {
+    if (m->pair_tpa > 0) return std::min(m->pair_tpa, 4);
+    return N >= 49152 ? 1 : 4;
 }
 
 // Lanes per atom of the force kernel: with eight or more lanes an atom's dE/dPsi sits once in
@@ -1125,9 +1134,7 @@ gm_status gm_param_grad(const gm_model *m, const gm_system *sys, const gm_nlist 
         StageScope sc(ST_PG_PAIR_FWD, st);
         launch_split_pos(N, sys->pos, sys->species, w.pos_hi, w.pos_lo, nullptr, nullptr, 0, st);
         launch_moments(a, choose_tpa(m, N), w.psi, st);
-        // at most 4 lanes per atom: the tangent kernel sums its 100 accumulators over the lanes
-        // with a plain all-reduce (8 lanes took 101 us against 57 us for 4 at 7920 atoms)
-        launch_moments_tangent(a, std::min(choose_tpa(m, N), 4), dL_dF, w.psid, st);
+        launch_moments_tangent(a, choose_tangent_tpa(m, N), dL_dF, w.psid, st);
         launch_contract_fwd_dual(w.psi, w.psid, N, Mp, w.GG, st);
     }
     {   // network forward (primal + tangent rows) and reverse

@@ -284,6 +284,92 @@ __global__ void __launch_bounds__(moments_threads<TPA>(), TPA >= 8 ? 3 : 1) k_mo
     }
 }
 
+// Moments with the components split over a lane pair (large systems, TPA = 2 or 4 lanes per
+// atom).  The TPA lanes of an atom form TPA/2 groups of two; the two lanes of a group (role
+// h = lane & 1) take one pair each per step, evaluate its radial part once, and swap their
+// R_s and the half of the monomials the other lane keeps: lane h accumulates the components
+// c in [10h, 10h + 10) of both pairs, 50 sums instead of 100, which halves the registers of
+// the one-lane kernel (two blocks per SM instead of one) without repeating the radial part.
+// With TPA = 4 the two groups take alternate pair couples of the row and add their sums with
+// one shuffle at the end.
+constexpr int NCH = NC / 2;
+template <int TPA, int BAS>
+__global__ void __launch_bounds__(256, 2) k_moments_cs(PairArgs a, float *__restrict__ psi) {
+    static_assert(TPA == 2 || TPA == 4, "component-split moments take 2 or 4 lanes per atom");
+    extern __shared__ __align__(16) float sbeta[];
+    stage_beta(a.beta, a.S, sbeta);
+    griddep_wait();
+    __syncthreads();
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int atom = g / TPA, sub = g % TPA, h = sub & 1, grp = sub >> 1;
+    const bool active = atom < a.N && !status_bad(a.status);
+    // the two lanes of this group (they run the same steps of the same row)
+    const unsigned pmask = 3u << ((threadIdx.x & 31) & ~1);
+    float acc[NR][NCH];
+#pragma unroll
+    for (int s = 0; s < NR; ++s)
+#pragma unroll
+        for (int k = 0; k < NCH; ++k) acc[s][k] = 0.0f;
+    if (active) {
+        const int b = structure_of(a.atom_ptr, a.B, atom);
+        const Centre ce(a, atom, b);
+        const int zsi = clamp_species(a.species[atom], a.S, a.status);
+        const float *brow = sbeta + zsi * a.S * (NR * BETA_ROW);
+        const int p0 = a.row_ptr[atom], p1 = a.row_ptr[atom + 1];
+        // this lane's pairs: p0 + 2 grp + h, then every TPA-th
+        PairPipe<1> pp(a, p0 + 2 * grp + h, p1, TPA);
+        for (int p = p0 + 2 * grp; p < p1; p += TPA) {
+            const NextPair cur = pp.next(a);
+            float fx = 1.0f, fy = 0.0f, fz = 0.0f;
+            int zj = 0;
+            if (cur.ok) {
+                ce.displacement(cur, fx, fy, fz);
+                zj = clamp_species(__float_as_int(cur.ph.w), a.S, a.status);
+            }
+            const float r = sqrtf(fx * fx + fy * fy + fz * fz);
+            const float rinv = 1.0f / r;
+            float B[NB], dB[NB];
+            radial_basis<false, BAS>(a.rc, r, B, dB);
+            float R[NR], Rp[NR];
+            radial_combine<false>(brow + zj * (NR * BETA_ROW), B, dB, R, Rp);
+            const float w = cur.ok ? 1.0f : 0.0f;    // a missing second pair adds exact zeros
+#pragma unroll
+            for (int s = 0; s < NR; ++s) R[s] *= w;
+            float m[NC];
+            monomials(fx * rinv, fy * rinv, fz * rinv, m);
+            // keep one half of this pair's monomials, send the other half and R to the partner
+            float mk[NCH], mo[NCH], Ro[NR];
+#pragma unroll
+            for (int k = 0; k < NCH; ++k) {
+                mk[k] = h ? m[NCH + k] : m[k];
+                mo[k] = __shfl_xor_sync(pmask, h ? m[k] : m[NCH + k], 1);
+            }
+#pragma unroll
+            for (int s = 0; s < NR; ++s) Ro[s] = __shfl_xor_sync(pmask, R[s], 1);
+#pragma unroll
+            for (int s = 0; s < NR; ++s)
+#pragma unroll
+                for (int k = 0; k < NCH; ++k) acc[s][k] = fmaf(Ro[s], mo[k], fmaf(R[s], mk[k], acc[s][k]));
+        }
+    }
+    if (TPA == 4) {
+#pragma unroll
+        for (int s = 0; s < NR; ++s)
+#pragma unroll
+            for (int k = 0; k < NCH; ++k) acc[s][k] += __shfl_xor_sync(0xffffffffu, acc[s][k], 2);
+    }
+    if (!active) return;
+    // lane h holds Psi[s][10h + k]; with TPA = 4 the two groups store alternate radial functions
+    float2 *out = reinterpret_cast<float2 *>(psi + (size_t)atom * NPSI);
+#pragma unroll
+    for (int s = 0; s < NR; ++s) {
+        if (TPA == 4 && (s & 1) != grp) continue;
+#pragma unroll
+        for (int k = 0; k < NCH / 2; ++k)
+            out[(s * NC + h * NCH) / 2 + k] = make_float2(acc[s][2 * k], acc[s][2 * k + 1]);
+    }
+}
+
 // Block shape and gradient storage of the force kernel.  With 8 or more lanes per atom the
 // atom's dE/dPsi (identical for its lanes) sits once in shared memory, transposed to
 // [component][radial function] rows of 8 (one 16-byte and one 4-byte broadcast load per
@@ -607,18 +693,21 @@ static void allow_beta_smem(Kern kernel, size_t extra = 0) {
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(beta_smem_bytes(MAX_S) + extra));
 }
 
+// 2 and 4 lanes per atom take the component-split kernel, the others k_moments
 template <int TPA, int BAS>
 static void launch_moments_t(const PairArgs &a, float *psi, cudaStream_t st) {
-    const int threads = moments_threads<TPA>();
+    constexpr bool CS = TPA == 2 || TPA == 4;
+    const int threads = CS ? 256 : moments_threads<TPA>();
     const long long total = (long long)a.N * TPA;
     const int blocks = (int)((total + threads - 1) / threads);
     const size_t smem = beta_smem_bytes(a.S);
+    auto kern = CS ? k_moments_cs<(CS ? TPA : 2), BAS> : k_moments<TPA, BAS>;
     static PerDeviceOnce attr;
     if (attr.first()) {
-        allow_beta_smem(k_moments<TPA, BAS>);
+        allow_beta_smem(kern);
     }
     if (blocks > 0) {
-        launch_pdl(k_moments<TPA, BAS>, dim3(blocks), dim3(threads), smem, st, a, psi);
+        launch_pdl(kern, dim3(blocks), dim3(threads), smem, st, a, psi);
         note_launches(1);
     }
 }

@@ -636,8 +636,9 @@ def _check_against(ref, batch, E, F, W, tol):
 @pytest.mark.parametrize("tpa", [1, 2, 4, 8, 16, 32])
 @pytest.mark.parametrize("case", ["config1", "li_small"])
 def test_energy_forces_every_pair_lane_count(case, tpa, precision, li_small):
-    """Every lanes-per-atom shape of the pair kernels (moments and forces; 1, 2 and 4 lanes
-    use their own code without the shared-memory dE/dPsi rows) against the oracle, with the
+    """Every lanes-per-atom shape of the pair kernels (moments: 1 lane, 2 and 4 lanes with the
+    component split over lane pairs, 8-32 with the reduce-scatter; forces: 1, 2 and 4 lanes
+    without the shared-memory dE/dPsi rows, 8-32 with them) against the oracle, with the
     virial, on the 96-atom box and on 24 Li3PO4 boxes (several with multiple images)."""
     b, d, p = synth.config(1) if case == "config1" else li_small
     ref = _oracle_ref(case, b, d, p)
@@ -664,11 +665,12 @@ def _li_boxes(n_boxes):
     return b, d, p
 
 
-@pytest.mark.parametrize("n_boxes,lanes,force_lanes", [(16, 32, 8), (32, 4, 8), (64, 8, 8), (96, 1, 8)])
+@pytest.mark.parametrize("n_boxes,lanes,force_lanes", [(16, 32, 8), (32, 4, 8), (64, 2, 8), (96, 2, 8)])
 def test_library_lane_choice_by_size_matches_oracle(n_boxes, lanes, force_lanes):
     """8,192, 16,384, 32,768 and 49,152 atoms: the pair-kernel shapes the library picks by size
-    for mid-size and large systems (moments 32, 4, 8 and 1 lanes per atom, forces 8, as for the
-    131,072-atom crystal and the batched Li3PO4 workload), with no forced knob, against the
+    for mid-size and large systems (moments 32 lanes per atom with the reduce-scatter kernel,
+    then 4, 2 and 2 with the component-split kernel; forces 8, as for the 131,072-atom crystal
+    and the batched Li3PO4 workload), with no forced knob, against the
     full oracle for both precisions, energies, forces and virials."""
     b, d, p = _li_boxes(n_boxes)
     ref = _oracle_ref(("li_boxes", n_boxes), b, d, p)
@@ -689,8 +691,8 @@ def test_library_lane_choice_by_size_matches_oracle(n_boxes, lanes, force_lanes)
 
 
 def test_full_size_li3po4_sampled_forces_match_oracle():
-    """131,072 atoms in the benchmark's launch configuration (moments one lane per atom, forces
-    eight, the fused network kernel): the forces
+    """131,072 atoms in the benchmark's launch configuration (moments two lanes per atom with
+    the component-split kernel, forces eight, the fused network kernel): the forces
     and the atomic energies of 12 sampled atoms equal an exact oracle evaluation of those atoms
     (their neighbours' complete environments are evaluated; nothing is truncated), for both
     precisions."""
@@ -701,7 +703,7 @@ def test_full_size_li3po4_sampled_forces_match_oracle():
     from paper_2505_22168_b300 import _lib
     for precision in ("fp32", "mixed"):
         m = GMNN(d, p, precision=precision)
-        assert _lib.gm_model_pair_lanes(m.handle, b.n_atoms) == 1
+        assert _lib.gm_model_pair_lanes(m.handle, b.n_atoms) == 2
         assert _lib.gm_model_force_lanes(m.handle, b.n_atoms) == 8
         sysd = DeviceSystem(b)
         nl = m.build_neighbors(sysd)
