@@ -184,6 +184,14 @@ __device__ __forceinline__ void bessel_basis(const RadialConst &rc, float r, flo
     }
 }
 
+// 2^x by the hardware approximation (ex2.approx.ftz.f32: relative error about 2^-22, results
+// below 2^-126 flushed to zero; a Gaussian that small adds nothing to R_s of order one)
+__device__ __forceinline__ float ex2_ftz(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // f_c Phi_k (B) and optionally its r-derivative (dB) for the 7 Gaussians.  The cutoff's
 // cosine and sine take the hardware approximation on [0, pi] (absolute error below 4e-7,
 // against f_c and Phi of order one).
@@ -203,7 +211,7 @@ __device__ __forceinline__ void radial_basis(const RadialConst &rc, float r, flo
 #pragma unroll
     for (int k = 0; k < NB; ++k) {
         const float t = r - rc.mu[k];
-        const float ph = exp2f(-rc.gamma_l2 * (t * t));
+        const float ph = ex2_ftz(-rc.gamma_l2 * (t * t));
         B[k] = fc * ph;
         if (DERIV) dB[k] = ph * fmaf(-2.0f * rc.gamma * t, fc, dfc);
     }

@@ -654,7 +654,11 @@ __device__ __forceinline__ unsigned shift_slow(const NlArgs &a, int i, int j, in
     return bytes3(s0, s1, s2);
 }
 
-// The tests of one chunk (32 staged candidates, one per lane) against the ng home atoms.
+// The tests of one chunk (32 staged candidates, one per lane) against the ng home atoms,
+// four home atoms at a time: their distance tests, ballots and row offsets are independent
+// chains, and the rare exact FP64 test is one vote per four home atoms (one home atom per
+// step left each warp waiting on its own vote -> shuffle -> store chain).  The pairs land
+// in the same slots as one home atom at a time.
 // UNI: all home atoms of the group have the same image counts, so the staged info word
 // already holds the pair's complete shift.
 template <int MODE, bool SELF, bool UNI>
@@ -662,6 +666,7 @@ __device__ __forceinline__ void test_chunk(const NlArgs &a, const float4 *home, 
                                            unsigned info, int n0, int n1, int n2, float lo2, float hi2,
                                            const NlStruct &q, double rc2, int lane, int &hacc, unsigned hmb,
                                            bool &hredo) {
+    constexpr int G = 4;
     const unsigned full = 0xffffffffu, below = (1u << lane) - 1u;
     const int st = (int)(info & 31u);
     const int selfj = (SELF && valid && st == NL_HOME_STENCIL) ? j : -1;
@@ -669,45 +674,71 @@ __device__ __forceinline__ void test_chunk(const NlArgs &a, const float4 *home, 
     // slab entry of a uniform group (shift complete at staging)
     const unsigned ucode = (MODE == SM_SLAB && UNI) ? shift_code(vb) : 0u;
     const bool maybe_nocode = MODE == SM_SLAB && (!UNI || __any_sync(full, valid && ucode == NL_NOCODE));
-#pragma unroll 4
-    for (int h = 0; h < ng; ++h) {
-        const float4 hv = home[h];
-        const int hi = __float_as_int(hv.w);
-        const float fx = cv.x - hv.x, fy = cv.y - hv.y, fz = cv.z - hv.z;
-        const float r2 = fx * fx + fy * fy + fz * fz;
-        const bool other = SELF ? (valid && selfj != hi) : valid;
-        bool in = other && r2 < lo2;
-        const bool band = other && !in && r2 <= hi2;                     // inside the band: exact FP64 test
-        if (__any_sync(full, band)) {
-            if (band) in = exact_inside(a.xw, j, a.xw[3 * hi], a.xw[3 * hi + 1], a.xw[3 * hi + 2], n0, n1, n2, q, rc2);
+    for (int h0 = 0; h0 < ng; h0 += G) {                 // ng <= 32, so h0 + G - 1 <= 31
+        bool in[G], band[G];
+        int hi[G];
+        bool anyband = false;
+#pragma unroll
+        for (int k = 0; k < G; ++k) {
+            const int h = h0 + k;
+            const float4 hv = home[h < ng ? h : h0];
+            hi[k] = __float_as_int(hv.w);
+            const float fx = cv.x - hv.x, fy = cv.y - hv.y, fz = cv.z - hv.z;
+            const float r2 = fx * fx + fy * fy + fz * fz;
+            const bool other = h < ng && (SELF ? (valid && selfj != hi[k]) : valid);
+            in[k] = other && r2 < lo2;
+            band[k] = other && !in[k] && r2 <= hi2;      // inside the band: exact FP64 test
+            anyband |= band[k];
         }
-        const unsigned ball = __ballot_sync(full, in);
-        if (MODE == SM_COUNT) {
-            if (lane == h) hacc += __popc(ball);
-        } else {
-            const int ob = __shfl_sync(full, hacc, h);
-            const unsigned mb = UNI ? 0u : __shfl_sync(full, hmb, h);
-            bool nocode = false;
-            if (in) {
-                const int pos = ob + __popc(ball & below);
-                if (MODE == SM_SLAB) {
-                    const unsigned code = UNI ? ucode : shift_code(bytes3_add(vb, mb));
-                    nocode = code == NL_NOCODE;
-                    if (pos < a.maxn) a.slab[(size_t)hi * a.maxn + pos] = (unsigned)j | (code << 27);
-                } else {
-                    unsigned sh = UNI ? vb : bytes3_add(vb, mb);
-                    if (sh & NL_FAR) sh = shift_slow(a, hi, j, n0, n1, n2);
-                    if (sh & NL_FAR) {
-                        set_status(a.status, GM_ERR_UNSUPPORTED);
-                        sh = 0;
+        if (__any_sync(full, anyband)) {
+#pragma unroll
+            for (int k = 0; k < G; ++k)
+                if (band[k])
+                    in[k] = exact_inside(a.xw, j, a.xw[3 * hi[k]], a.xw[3 * hi[k] + 1], a.xw[3 * hi[k] + 2], n0, n1,
+                                         n2, q, rc2);
+        }
+        unsigned ball[G];
+#pragma unroll
+        for (int k = 0; k < G; ++k) ball[k] = __ballot_sync(full, in[k]);
+        if (MODE != SM_COUNT) {
+            int ob[G];
+            unsigned mb[G];
+#pragma unroll
+            for (int k = 0; k < G; ++k) {
+                ob[k] = __shfl_sync(full, hacc, h0 + k);
+                mb[k] = UNI ? 0u : __shfl_sync(full, hmb, h0 + k);
+            }
+            bool nocode[G];
+#pragma unroll
+            for (int k = 0; k < G; ++k) {
+                nocode[k] = false;
+                if (in[k]) {
+                    const int pos = ob[k] + __popc(ball[k] & below);
+                    if (MODE == SM_SLAB) {
+                        const unsigned code = UNI ? ucode : shift_code(bytes3_add(vb, mb[k]));
+                        nocode[k] = code == NL_NOCODE;
+                        if (pos < a.maxn) a.slab[(size_t)hi[k] * a.maxn + pos] = (unsigned)j | (code << 27);
+                    } else {
+                        unsigned sh = UNI ? vb : bytes3_add(vb, mb[k]);
+                        if (sh & NL_FAR) sh = shift_slow(a, hi[k], j, n0, n1, n2);
+                        if (sh & NL_FAR) {
+                            set_status(a.status, GM_ERR_UNSUPPORTED);
+                            sh = 0;
+                        }
+                        a.col[pos] = j;
+                        reinterpret_cast<unsigned *>(a.shift)[pos] = sh;
                     }
-                    a.col[pos] = j;
-                    reinterpret_cast<unsigned *>(a.shift)[pos] = sh;
                 }
             }
-            if (maybe_nocode && __any_sync(full, nocode) && lane == h) hredo = true;
-            if (lane == h) hacc += __popc(ball);
+            if (maybe_nocode) {
+#pragma unroll
+                for (int k = 0; k < G; ++k)
+                    if (__any_sync(full, nocode[k]) && lane == h0 + k) hredo = true;
+            }
         }
+#pragma unroll
+        for (int k = 0; k < G; ++k)
+            if (lane == h0 + k) hacc += __popc(ball[k]);
     }
 }
 

@@ -46,6 +46,15 @@ __device__ __forceinline__ float disp_axis(float xjh, float xjl, float xih, floa
     return h3 + lo;
 }
 
+// |d| and 1/|d| of a pair from one hardware reciprocal square root (relative error a few
+// 2^-24 each, against the correctly rounded square root and division it replaces; d is never
+// zero for a listed pair)
+__device__ __forceinline__ void pair_length(float fx, float fy, float fz, float &r, float &rinv) {
+    const float r2 = fx * fx + fy * fy + fz * fz;
+    rinv = rsqrtf(r2);
+    r = r2 * rinv;
+}
+
 // One neighbour of a row: index, shift, hi/lo position (species in ph.w) and, for the
 // tangent kernels, its velocity (the direction the positions move along).
 struct NextPair {
@@ -217,8 +226,8 @@ __global__ void __launch_bounds__(moments_threads<TPA>(), TPA >= 8 ? 3 : 1) k_mo
                     ce.displacement(cur[u], fx, fy, fz);
                     zj = clamp_species(__float_as_int(cur[u].ph.w), a.S, a.status);
                 }
-                const float r = sqrtf(fx * fx + fy * fy + fz * fz);
-                const float rinv = 1.0f / r;
+                float r, rinv;
+                pair_length(fx, fy, fz, r, rinv);
                 float B[NB], dB[NB];
                 radial_basis<false, BAS>(a.rc, r, B, dB);
                 const float w = cur[u].ok ? 1.0f : 0.0f;
@@ -326,8 +335,8 @@ __global__ void __launch_bounds__(256, 2) k_moments_cs(PairArgs a, float *__rest
                 ce.displacement(cur, fx, fy, fz);
                 zj = clamp_species(__float_as_int(cur.ph.w), a.S, a.status);
             }
-            const float r = sqrtf(fx * fx + fy * fy + fz * fz);
-            const float rinv = 1.0f / r;
+            float r, rinv;
+            pair_length(fx, fy, fz, r, rinv);
             float B[NB], dB[NB];
             radial_basis<false, BAS>(a.rc, r, B, dB);
             float R[NR], Rp[NR];
@@ -425,8 +434,8 @@ __global__ void __launch_bounds__(forces_threads<TPA>(), TPA >= 8 ? 4 : 1)
             const int j = cur.j;
             float fx, fy, fz;
             ce.displacement(cur, fx, fy, fz);
-            const float r = sqrtf(fx * fx + fy * fy + fz * fz);
-            const float rinv = 1.0f / r;
+            float r, rinv;
+            pair_length(fx, fy, fz, r, rinv);
             const float ux = fx * rinv, uy = fy * rinv, uz = fz * rinv;
             float B[NB], dB[NB];
             radial_basis<true, BAS>(a.rc, r, B, dB);
@@ -544,8 +553,8 @@ __global__ void __launch_bounds__(256) k_moments_tangent(PairArgs a, const float
             if (!cur.ok) continue;
             float fx, fy, fz;
             ce.displacement(cur, fx, fy, fz);
-            const float r = sqrtf(fx * fx + fy * fy + fz * fz);
-            const float rinv = 1.0f / r;
+            float r, rinv;
+            pair_length(fx, fy, fz, r, rinv);
             const float ux = fx * rinv, uy = fy * rinv, uz = fz * rinv;
             const float ddx = cur.vx - vix, ddy = cur.vy - viy, ddz = cur.vz - viz;
             const float w = ux * ddx + uy * ddy + uz * ddz;
@@ -634,8 +643,8 @@ __global__ void __launch_bounds__(256) k_pg_beta(PairArgs a, const float *__rest
             if (!cur.ok) continue;
             float fx, fy, fz;
             ce.displacement(cur, fx, fy, fz);
-            const float r = sqrtf(fx * fx + fy * fy + fz * fz);
-            const float rinv = 1.0f / r;
+            float r, rinv;
+            pair_length(fx, fy, fz, r, rinv);
             const float ux = fx * rinv, uy = fy * rinv, uz = fz * rinv;
             const float ddx = cur.vx - vix, ddy = cur.vy - viy, ddz = cur.vz - viz;
             const float w = ux * ddx + uy * ddy + uz * ddz;
