@@ -760,7 +760,14 @@ __device__ void ph_search(const NlArgs &a, int bid, int nb, float4 *smem) {
     if (MODE == SM_FILL && __shfl_sync(full, lane == 0 ? (int)status_bad(a.status) : 0, 0)) return;
     const int items = *a.ncells * a.split;
     const double rc2 = __dmul_rn(a.rc, a.rc);
-    for (int it = bid + nb * warp; it < items; it += nb * NL_WARPS) {
+    // items are claimed from a counter (one per pass): a fixed deal of 2-3 items per warp left
+    // most warps waiting at the next grid barrier for the ones with one item more
+    int32_t *ctr = a.item_ctr + (MODE == SM_FILL ? 1 : 0);
+    for (;;) {
+        int it = 0;
+        if (lane == 0) it = atomicAdd(ctr, 1);
+        it = __shfl_sync(full, it, 0);
+        if (it >= items) break;
         const int c = it / a.split, part = it - c * a.split;
         const int h0 = a.cstart[c], nh = a.cstart[c + 1] - h0;
         if (part >= nh) continue;                                  // uniform over the warp
