@@ -387,7 +387,8 @@ __global__ void __launch_bounds__(256, 2) k_moments_cs(PairArgs a, float *__rest
 template <int TPA> __host__ __device__ constexpr bool forces_gsmem() { return TPA >= 8; }
 template <int TPA> __host__ __device__ constexpr int forces_threads() { return TPA >= 8 ? 128 : 256; }
 constexpr int FG_ROW = 168;
-template <int TPA, int BAS>
+// VIR: the per-atom virial is accumulated and stored (vir_atom), else not formed at all
+template <int TPA, int BAS, bool VIR>
 __global__ void __launch_bounds__(forces_threads<TPA>(), TPA >= 8 ? 4 : 1)
     k_forces(PairArgs a, const float *__restrict__ dpsi, float *__restrict__ F, float *__restrict__ vir_atom) {
     constexpr bool GS = forces_gsmem<TPA>();
@@ -398,9 +399,17 @@ __global__ void __launch_bounds__(forces_threads<TPA>(), TPA >= 8 ? 4 : 1)
     if (GS) {
         constexpr int APB = forces_threads<TPA>() / TPA;
         const int a_first = blockIdx.x * APB;
-        for (int q = threadIdx.x; q < APB * NPSI; q += blockDim.x) {
-            const int al = q / NPSI, e = q - al * NPSI, s = e / NC, c = e - s * NC, m = a_first + al;
-            gsm[al * FG_ROW + c * 8 + s] = m < a.N ? dpsi[(size_t)m * NPSI + e] : 0.0f;
+        // 16-byte loads: four consecutive components c..c+3 of one radial function s
+        constexpr int V4 = NPSI / 4, C4 = NC / 4;
+        for (int q = threadIdx.x; q < APB * V4; q += blockDim.x) {
+            const int al = q / V4, e4 = q - al * V4, s = e4 / C4, c = 4 * (e4 - s * C4), m = a_first + al;
+            const float4 v = m < a.N ? __ldg(reinterpret_cast<const float4 *>(dpsi + (size_t)m * NPSI) + e4)
+                                     : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            float *row = gsm + al * FG_ROW + c * 8 + s;
+            row[0] = v.x;
+            row[8] = v.y;
+            row[16] = v.z;
+            row[24] = v.w;
         }
     }
     __syncthreads();
@@ -500,9 +509,11 @@ __global__ void __launch_bounds__(forces_threads<TPA>(), TPA >= 8 ? 4 : 1)
             atomicAdd(F + 3 * j, -gx);
             atomicAdd(F + 3 * j + 1, -gy);
             atomicAdd(F + 3 * j + 2, -gz);
-            V[0] -= fx * gx; V[1] -= fx * gy; V[2] -= fx * gz;
-            V[3] -= fy * gx; V[4] -= fy * gy; V[5] -= fy * gz;
-            V[6] -= fz * gx; V[7] -= fz * gy; V[8] -= fz * gz;
+            if (VIR) {
+                V[0] -= fx * gx; V[1] -= fx * gy; V[2] -= fx * gz;
+                V[3] -= fy * gx; V[4] -= fy * gy; V[5] -= fy * gz;
+                V[6] -= fz * gx; V[7] -= fz * gy; V[8] -= fz * gz;
+            }
         }
     }
     if (TPA > 1) {
@@ -510,15 +521,17 @@ __global__ void __launch_bounds__(forces_threads<TPA>(), TPA >= 8 ? 4 : 1)
         for (int off = TPA / 2; off > 0; off >>= 1) {
 #pragma unroll
             for (int q = 0; q < 3; ++q) Fi[q] += __shfl_xor_sync(0xffffffffu, Fi[q], off);
+            if (VIR) {
 #pragma unroll
-            for (int q = 0; q < 9; ++q) V[q] += __shfl_xor_sync(0xffffffffu, V[q], off);
+                for (int q = 0; q < 9; ++q) V[q] += __shfl_xor_sync(0xffffffffu, V[q], off);
+            }
         }
     }
     if (!active || sub != 0) return;
     atomicAdd(F + 3 * atom, Fi[0]);
     atomicAdd(F + 3 * atom + 1, Fi[1]);
     atomicAdd(F + 3 * atom + 2, Fi[2]);
-    if (vir_atom) {
+    if (VIR) {
 #pragma unroll
         for (int q = 0; q < 9; ++q) vir_atom[(size_t)atom * 9 + q] = V[q];
     }
@@ -728,12 +741,15 @@ static void launch_forces_t(const PairArgs &a, const float *dpsi, float *F, floa
     const int blocks = (int)((total + threads - 1) / threads);
     const size_t smem = beta_smem_bytes(a.S) +
                         (forces_gsmem<TPA>() ? sizeof(float) * (threads / TPA) * FG_ROW : 0);
+    auto kern = vir ? k_forces<TPA, BAS, true> : k_forces<TPA, BAS, false>;
     static PerDeviceOnce attr;
     if (attr.first()) {
-        allow_beta_smem(k_forces<TPA, BAS>, forces_gsmem<TPA>() ? sizeof(float) * (threads / TPA) * FG_ROW : 0);
+        const size_t extra = forces_gsmem<TPA>() ? sizeof(float) * (threads / TPA) * FG_ROW : 0;
+        allow_beta_smem(k_forces<TPA, BAS, true>, extra);
+        allow_beta_smem(k_forces<TPA, BAS, false>, extra);
     }
     if (blocks > 0) {
-        launch_pdl(k_forces<TPA, BAS>, dim3(blocks), dim3(threads), smem, st, a, dpsi, F, vir);
+        launch_pdl(kern, dim3(blocks), dim3(threads), smem, st, a, dpsi, F, vir);
         note_launches(1);
     }
 }
