@@ -30,7 +30,9 @@ struct FusedArgs {
     const int32_t *species;
     const float *b1, *b2, *w3, *sigma;
     __half *D1;               // [M][H] phi'(z1) in FP16, written by L1's epilogue, read by B1's (same
-                              // thread; it feeds an FP16 operand, dZ1 = dA1 phi'(z1), anyway)
+                              // thread; it feeds an FP16 operand, dZ1 = dA1 phi'(z1), anyway), in a
+                              // layout private to this kernel: per tile, 8-column groups g major,
+                              // rows minor (d1_group), so a warp's 16-byte accesses are contiguous
     float *nn_part;           // [M][H/32]
     float *dG;                // [M][384]
     int debug_stall;          // failure-reporting tests: the producer issues no loads at all
@@ -56,6 +58,11 @@ struct FusedShape {
 __device__ __forceinline__ void x_store8(uint8_t *X, int r, int k0, uint4 v) {
     const int kb = k0 >> 6, j = (k0 & 63) >> 3;
     *reinterpret_cast<uint4 *>(X + (size_t)kb * (BM * 128) + r * 128 + ((j ^ (r & 7)) << 4)) = v;
+}
+
+// the 8 phi'(z1) values of row r (of the tile at m0) and column group g = column / 8
+__device__ __forceinline__ uint4 *d1_group(__half *D1, int m0, int H, int g, int r) {
+    return reinterpret_cast<uint4 *>(D1 + (size_t)m0 * H + ((size_t)g * BM + r) * 8);
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
@@ -238,9 +245,8 @@ __global__ void __launch_bounds__(320, 1)
                 for (int t = 0; t < 32; ++t) a[t] = act_fast<ACT>(v[t] + bias[t], d[t]);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) x_store8(X, r, c * 32 + 8 * q, pack8_bf16(a + 8 * q));
-                uint4 *dst = reinterpret_cast<uint4 *>(f.D1 + (size_t)m * H + c * 32);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) dst[q] = pack8_f16(d + 8 * q);
+                for (int q = 0; q < 4; ++q) *d1_group(f.D1, m0, H, 4 * c + q, r) = pack8_f16(d + 8 * q);
             }
         }
         release_x();
@@ -270,10 +276,9 @@ __global__ void __launch_bounds__(320, 1)
                 float v[32], y[32];
                 // this thread's phi'(z1) (written by itself in E1), loaded before the TMEM read
                 // so that the two latencies overlap
-                const uint4 *dsrc = reinterpret_cast<const uint4 *>(f.D1 + (size_t)m * H + c * 32);
                 uint4 dq[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) dq[q] = dsrc[q];
+                for (int q = 0; q < 4; ++q) dq[q] = *d1_group(f.D1, m0, H, 4 * c + q, r);
                 tmem_ld_32cols(tl + (uint32_t)(c * 32), v);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
