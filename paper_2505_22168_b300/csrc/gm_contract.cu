@@ -56,21 +56,25 @@ struct FeatOut {
 // (row stride GT_STRIDE, rows past N zero).  Every thread issues all of its 16-byte loads
 // before the first store, so the block waits for one memory latency instead of one per row.
 template <int NT>
-__device__ __forceinline__ void stage_rows(const float *__restrict__ src, int m0, int N, float *tile) {
+__device__ __forceinline__ void stage_rows(const float *__restrict__ src, int m0, int N, float *tile,
+                                           bool tiled = false) {
     constexpr int V4 = NF / 4, TOT = CT_ATOMS * V4, PER = (TOT + NT - 1) / NT;
+    // row-major [M][NFP], or the per-tile fused network kernel's layout: per 128-row tile,
+    // 4-column groups major and rows minor (then consecutive threads take consecutive rows)
     float4 v[PER];
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
         const int idx = threadIdx.x + u * NT;
-        const int r = idx / V4, q = idx - r * V4;
-        v[u] = (idx < TOT && m0 + r < N) ? __ldg(reinterpret_cast<const float4 *>(src + (size_t)(m0 + r) * NFP) + q)
-                                         : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        const int r = tiled ? idx % CT_ATOMS : idx / V4, q = tiled ? idx / CT_ATOMS : idx - r * V4;
+        const int m = m0 + r;
+        const size_t at = tiled ? (size_t)(m & ~127) * NFP + ((size_t)q * 128 + (m & 127)) * 4 : (size_t)m * NFP + 4 * q;
+        v[u] = (idx < TOT && m < N) ? __ldg(reinterpret_cast<const float4 *>(src + at)) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
         const int idx = threadIdx.x + u * NT;
         if (idx < TOT) {
-            const int r = idx / V4, q = idx - r * V4;
+            const int r = tiled ? idx % CT_ATOMS : idx / V4, q = tiled ? idx / CT_ATOMS : idx - r * V4;
             float *d = tile + r * GT_STRIDE + 4 * q;
             d[0] = v[u].x; d[1] = v[u].y; d[2] = v[u].z; d[3] = v[u].w;
         }
@@ -674,7 +678,7 @@ __global__ void __launch_bounds__(W * 32) k_contract_fwd(const float *__restrict
 
 template <int W>
 __global__ void __launch_bounds__(W * 32) k_contract_bwd(const float *__restrict__ psi, const float *__restrict__ dG,
-                                                         int N, float *__restrict__ dpsi) {
+                                                         int N, float *__restrict__ dpsi, int dg_tiled) {
     extern __shared__ __align__(16) float smb[];
     float *ptile = smb;                                    // [32][100] moments
     float *slots = ptile + CT_ATOMS * NPSI;                // W x [32][100] partial dE/dPsi
@@ -687,7 +691,7 @@ __global__ void __launch_bounds__(W * 32) k_contract_bwd(const float *__restrict
         float4 *mine = reinterpret_cast<float4 *>(slots + warp * CT_ATOMS * NPSI);
         for (int q = lane; q < CT_ATOMS * NPSI / 4; q += 32) mine[q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
-    stage_rows<W * 32>(dG, m0, N, gtile);                   // ends with __syncthreads()
+    stage_rows<W * 32>(dG, m0, N, gtile, dg_tiled != 0);    // ends with __syncthreads()
     const MomSrc<float> src{ptile + lane * NPSI};
     const GradIn<float> gb{gtile + lane * GT_STRIDE};
     const SlotAcc<float> acc{slots + warp * CT_ATOMS * NPSI + lane * NPSI};
@@ -944,22 +948,23 @@ void launch_contract_fwd_bf16(const float *psi, int N, int Mp, __nv_bfloat16 *G,
 }
 
 template <int W>
-static void launch_bwd_w(int blocks, const float *psi, const float *dG, int N, float *dpsi, cudaStream_t st) {
+static void launch_bwd_w(int blocks, const float *psi, const float *dG, int N, float *dpsi, int dg_tiled,
+                         cudaStream_t st) {
     static PerDeviceOnce attr;
     if (attr.first()) {
         cudaFuncSetAttribute(k_contract_bwd<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ct_bwd_smem<W>());
     }
-    launch_pdl(k_contract_bwd<W>, dim3(blocks), dim3(W * 32), ct_bwd_smem<W>(), st, psi, dG, N, dpsi);
+    launch_pdl(k_contract_bwd<W>, dim3(blocks), dim3(W * 32), ct_bwd_smem<W>(), st, psi, dG, N, dpsi, dg_tiled);
     note_launches(1);
 }
 
-void launch_contract_bwd(const float *psi, const float *dG, int N, float *dpsi, cudaStream_t st) {
+void launch_contract_bwd(const float *psi, const float *dG, int N, float *dpsi, cudaStream_t st, bool dg_tiled) {
     const int blocks = (N + CT_ATOMS - 1) / CT_ATOMS;
     if (blocks <= 0) return;
     if (blocks < sm_count())
-        launch_bwd_w<2 * CT_BWD_W>(blocks, psi, dG, N, dpsi, st);
+        launch_bwd_w<2 * CT_BWD_W>(blocks, psi, dG, N, dpsi, dg_tiled ? 1 : 0, st);
     else
-        launch_bwd_w<CT_BWD_W>(blocks, psi, dG, N, dpsi, st);
+        launch_bwd_w<CT_BWD_W>(blocks, psi, dG, N, dpsi, dg_tiled ? 1 : 0, st);
 }
 
 }  // namespace gm

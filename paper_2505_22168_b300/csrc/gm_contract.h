@@ -14,7 +14,10 @@ void launch_contract_fwd_f32(const float *psi, int N, int Mp, float *G, float *f
 void launch_contract_fwd_bf16(const float *psi, int N, int Mp, __nv_bfloat16 *G, float *features_out, bool lo_out,
                               cudaStream_t st);
 // dE/dG [Mp][384] FP32 and psi -> dE/dpsi [N][100] FP32 (unique components)
-void launch_contract_bwd(const float *psi, const float *dG, int N, float *dpsi, cudaStream_t st);
+// dg_tiled: dG in the per-tile fused network kernel's layout (per 128-row tile, 4-column groups
+// major and rows minor), else row-major [Mp][384]
+void launch_contract_bwd(const float *psi, const float *dG, int N, float *dpsi, cudaStream_t st,
+                         bool dg_tiled = false);
 
 // Parameter gradient: GG [2Mp][384] = [G; dG/dPsi . psid]; and from Gbs = [dJ/dG; dJ/dGd]
 // the moment adjoints psib, psidb [N][100] (see gm_contract.cu).

@@ -34,7 +34,8 @@ struct FusedArgs {
                               // layout private to this kernel: per tile, 8-column groups g major,
                               // rows minor (d1_group), so a warp's 16-byte accesses are contiguous
     float *nn_part;           // [M][H/32]
-    float *dG;                // [M][384]
+    float *dG;                // [M][384] dE/dG, in the layout stage_rows reads as "tiled": per 128-row
+                              // tile, 4-column groups major and rows minor
     int debug_stall;          // failure-reporting tests: the producer issues no loads at all
 };
 
@@ -300,9 +301,10 @@ __global__ void __launch_bounds__(320, 1)
             for (int c = half * 6; c < (half + 1) * 6; ++c) {
                 float v[32];
                 tmem_ld_32cols(tl + (uint32_t)(c * 32), v);
-                float4 *dst = reinterpret_cast<float4 *>(f.dG + (size_t)m * NFP + c * 32);
+                float4 *dst = reinterpret_cast<float4 *>(f.dG + (size_t)m0 * NFP) + (size_t)(8 * c) * BM + r;
 #pragma unroll
-                for (int q = 0; q < 8; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                for (int q = 0; q < 8; ++q)
+                    dst[(size_t)q * BM] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
             }
         } else if (threadIdx.x == 0) {
             set_status(status, GM_ERR_TIMEOUT);
