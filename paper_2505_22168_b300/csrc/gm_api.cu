@@ -920,9 +920,9 @@ static gm_status energy_forces_pipeline(const gm_model *m, const gm_system *sys,
         if ((s = network_fwd_bwd(m, sys, w, Mp, status, st, fused_energy ? energy : nullptr, nullptr, ens)) != GM_OK)
             return s;
         {
-            // the per-tile fused network kernel leaves dE/dG in its tiled layout
+            // the fused network kernels (per tile or per cluster) leave dE/dG in their tiled layout
             StageScope sc(ST_CONTRACT_BWD, st);
-            launch_contract_bwd(w.psi, w.dG, N, w.dpsi, st, mlp_form(m, ens, false, nullptr, N, &cs) == MLP_TILE);
+            launch_contract_bwd(w.psi, w.dG, N, w.dpsi, st, mlp_form(m, ens, false, nullptr, N, &cs) != MLP_GEMMS);
         }
         PairArgs a = pair_args(m, sys, nl, w.pos_hi, w.pos_lo, status);
         StageScope sc(ST_FORCES, st);

@@ -50,7 +50,7 @@ struct ClusterArgs {
     __half *D1;               // [M][H] phi'(z1) in FP16 (scratch)
     float *nn_part;           // [M][H/32]
     // the gathered layers go through [M][2H] scratch arrays (first H columns): a1, dZ2, dZ1
-    float *dG;                // [M][384]
+    float *dG;                // [M][384] dE/dG in the tiled layout of the per-tile kernel
     int debug_stall;          // failure-reporting tests: the producer issues no loads at all
     // structure energies (null energy: the caller sums them)
     const int32_t *atom_ptr;
@@ -465,9 +465,13 @@ __global__ void __launch_bounds__(320, 1)
             for (int q = q0; q < q1; ++q) {
                 float v[16];
                 tmem_ld_16cols(tl + (uint32_t)(q * 16), v);
-                float4 *dst = reinterpret_cast<float4 *>(f.dG + (size_t)m * NFP + cr * WG + q * 16);
+                // tiled layout (4-column groups major, rows minor per 128-row tile), as the
+                // per-tile kernel writes it: a warp's stores are 512 contiguous bytes
+                float4 *dst = reinterpret_cast<float4 *>(f.dG + (size_t)m0 * NFP) +
+                              (size_t)((cr * WG + q * 16) / 4) * BM + (m - m0);
 #pragma unroll
-                for (int u = 0; u < 4; ++u) dst[u] = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+                for (int u = 0; u < 4; ++u)
+                    dst[(size_t)u * BM] = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
             }
         }
         if (!ok && threadIdx.x == 0) set_status(status, GM_ERR_TIMEOUT);
