@@ -388,9 +388,27 @@ def run_gpu(args, cfg, precision, steps, warmup, world, rank, measure_e2e, clock
         # for every setting)
         from paper_2505_22168_b300 import autotune
         pos_buf.copy_(pos_dev[0])
-        t = autotune.tune(model, sysd, nl, out, reps=10 if n > 50000 else 20)
+        reps = 10 if n > 50000 else 20
+
+        def flushed_timer(m):
+            # the quantity the bench reports: one replay between events after an L2 flush
+            g = m.capture_step(sysd, nl, out)
+            g.replay()
+            e = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+            for e0, e1 in e:
+                flush.zero_()
+                e0.record(stream)
+                g.replay()
+                e1.record(stream)
+            stream.synchronize()
+            if m.read_status() != 0:
+                raise RuntimeError(f"device status {m.read_status()} while tuning")
+            del g
+            return float(np.median([e0.elapsed_time(e1) for e0, e1 in e]))
+
+        t = autotune.tune(model, sysd, nl, out, reps=reps, timer=flushed_timer)
         tuning = {"settings": t["settings"], "tuned_ms": round(t["ms"], 5), "default_ms": round(t["default_ms"], 5),
-                  "trials": len(t.get("trials", []))}
+                  "trials": len(t.get("trials", [])), "timed_as": "median of single replays after an L2 flush"}
 
     def step(k):                       # stream launches
         pos_buf.copy_(pos_dev[k])
