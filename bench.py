@@ -526,44 +526,65 @@ def run_gpu(args, cfg, precision, steps, warmup, world, rank, measure_e2e, clock
         e2e_steps = E2E_STEPS
         host_pos = [torch.as_tensor(path[warmup + k] if path is not None else batch.pos).pin_memory()
                     for k in range(e2e_steps)]
-        E_host = torch.empty(batch.n_structures, dtype=torch.float64).pin_memory()
-        F_host = torch.empty(n, 3, dtype=torch.float32).pin_memory()
-        # graph mode: one graph per step holding the copy of the pinned input positions to
-        # the device, the step, and the copies of energies and forces back to pinned host
-        # buffers; each step writes its positions into the pinned input (a host copy) and
-        # replays it
-        pin_in = torch.empty_like(host_pos[0]).pin_memory()
-        g_e2e = None
+        # graph mode: one graph per in-flight slot holding the copy of the slot's pinned input
+        # positions to the device, the step, and the copies of energies and forces back to the
+        # slot's pinned host buffers.  Two steps are in flight: the host writes step k's
+        # positions into a free slot and replays its graph while the GPU still runs step k - 1,
+        # then waits for step k - 1 and reads its energies and forces (the steps are
+        # independent evaluations; the device buffers are shared and the stream orders them)
+        slots = 2 if graphs else 1
+        E_host = [torch.empty(batch.n_structures, dtype=torch.float64).pin_memory() for _ in range(slots)]
+        F_host = [torch.empty(n, 3, dtype=torch.float32).pin_memory() for _ in range(slots)]
+        pin_in = [torch.empty_like(host_pos[0]).pin_memory() for _ in range(slots)]
+        g_e2e = []
         if graphs:
-            pin_in.copy_(host_pos[0])
-            torch.cuda.synchronize()
-            g_e2e = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(g_e2e):
-                pos_buf.copy_(pin_in, non_blocking=True)
-                model.step(sysd, nl, out)
-                E_host.copy_(out[0], non_blocking=True)
-                F_host.copy_(out[1], non_blocking=True)
-            g_e2e.replay()
+            for sl in range(slots):
+                pin_in[sl].copy_(host_pos[0])
+                torch.cuda.synchronize()
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g):
+                    pos_buf.copy_(pin_in[sl], non_blocking=True)
+                    model.step(sysd, nl, out)
+                    E_host[sl].copy_(out[0], non_blocking=True)
+                    F_host[sl].copy_(out[1], non_blocking=True)
+                g.replay()
+                g_e2e.append(g)
         torch.cuda.synchronize()
-        pin_np = pin_in.numpy()                       # the pinned input as the host program sees it
+        pin_np = [t.numpy() for t in pin_in]          # the pinned inputs as the host program sees them
+        E_np = [t.numpy() for t in E_host]
+        F_np = [t.numpy() for t in F_host]
         host_np = [h.numpy() for h in host_pos]
+        done = [torch.cuda.Event() for _ in range(slots)]
+        checksum = 0.0
         t0 = time.perf_counter()
-        for k in range(e2e_steps):
-            if g_e2e is not None:
-                np.copyto(pin_np, host_np[k])
-                g_e2e.replay()
+        for k in range(e2e_steps + slots - 1):
+            sl = k % slots
+            if k >= slots:                           # step k - slots: wait, read its results
+                done[sl].synchronize()
+                checksum += float(E_np[sl][0]) + float(F_np[sl][0, 0])
+            if k >= e2e_steps:
+                continue
+            if g_e2e:
+                np.copyto(pin_np[sl], host_np[k])
+                g_e2e[sl].replay()
             else:
                 pos_buf.copy_(host_pos[k], non_blocking=True)
                 model.step(sysd, nl, out)
-                E_host.copy_(out[0], non_blocking=True)
-                F_host.copy_(out[1], non_blocking=True)
-            stream.synchronize()
+                E_host[sl].copy_(out[0], non_blocking=True)
+                F_host[sl].copy_(out[1], non_blocking=True)
+            done[sl].record(stream)
+            if slots == 1:
+                done[sl].synchronize()
+                checksum += float(E_np[sl][0]) + float(F_np[sl][0, 0])
         wall = time.perf_counter() - t0
         if model.read_status() != 0:
             raise RuntimeError("device status set during the end-to-end run")
+        if not np.isfinite(checksum):
+            raise RuntimeError("non-finite energies or forces in the end-to-end run")
         res["e2e"] = {"value": world * n * e2e_steps / wall, "unit": UNIT,
                       "h2d_bytes_per_step": int(host_pos[0].numel() * 8),
-                      "d2h_bytes_per_step": int(E_host.numel() * 8 + F_host.numel() * 4), "steps": e2e_steps}
+                      "d2h_bytes_per_step": int(E_host[0].numel() * 8 + F_host[0].numel() * 4), "steps": e2e_steps,
+                      "steps_in_flight": slots}
     del pos_dev, flush
     return res
 
