@@ -758,17 +758,24 @@ __device__ void ph_search(const NlArgs &a, int bid, int nb, float4 *smem) {
     unsigned *wi = reinterpret_cast<unsigned *>(smem + NL_WARPS * NL_WIN) + warp * NL_WIN;
     const unsigned full = 0xffffffffu;
     if (MODE == SM_FILL && __shfl_sync(full, lane == 0 ? (int)status_bad(a.status) : 0, 0)) return;
-    const int items = *a.ncells * a.split;
-    const double rc2 = __dmul_rn(a.rc, a.rc);
     // items are claimed from a counter (one per pass): a fixed deal of 2-3 items per warp left
-    // most warps waiting at the next grid barrier for the ones with one item more
+    // most warps waiting at the next grid barrier for the ones with one item more.  The last
+    // cells (about one item per warp of the grid) are cut into twice as many parts, so the
+    // final round of claims is half as long
+    const int ncells = *a.ncells, s1 = a.split, s2 = 2 * s1;
+    const int xt = min(ncells, max(1, nb * NL_WARPS / s2));       // cells cut finer
+    const int head = (ncells - xt) * s1;
+    const int items = head + xt * s2;
+    const double rc2 = __dmul_rn(a.rc, a.rc);
     int32_t *ctr = a.item_ctr + (MODE == SM_FILL ? 1 : 0);
     for (;;) {
         int it = 0;
         if (lane == 0) it = atomicAdd(ctr, 1);
         it = __shfl_sync(full, it, 0);
         if (it >= items) break;
-        const int c = it / a.split, part = it - c * a.split;
+        const int sp = it < head ? s1 : s2;                       // parts of this item's cell
+        const int c = it < head ? it / s1 : ncells - xt + (it - head) / s2;
+        const int part = it < head ? it - c * s1 : (it - head) % s2;
         const int h0 = a.cstart[c], nh = a.cstart[c + 1] - h0;
         if (part >= nh) continue;                                  // uniform over the warp
         const NlStruct &q = a.S[a.cstruct[c]];
@@ -776,7 +783,7 @@ __device__ void ph_search(const NlArgs &a, int bid, int nb, float4 *smem) {
         if (!(q.K[0] == 1 && q.K[1] == 1 && q.K[2] == 1)) {
             // several images per stencil direction: per-atom search (with a slab, the
             // compaction writes these rows with the same routine)
-            for (int h = part; h < nh; h += a.split) {
+            for (int h = part; h < nh; h += sp) {
                 const float4 me = a.xs[h0 + h];
                 if (MODE == SM_FILL) {
                     search_atom_generic<true>(a, q, cl, me, lane, a.row_ptr[__float_as_int(me.w)]);
@@ -815,14 +822,14 @@ __device__ void ph_search(const NlArgs &a, int bid, int nb, float4 *smem) {
         const int home_lo = __shfl_sync(full, off, NL_HOME_STENCIL);
         const int home_hi = home_lo + __shfl_sync(full, cnt, NL_HOME_STENCIL);
         const float lo2 = a.rc2f - q.eps2, hi2 = a.rc2f + q.eps2;
-        const int nhp = (nh - part + a.split - 1) / a.split;       // home atoms of the item
+        const int nhp = (nh - part + sp - 1) / sp;                 // home atoms of the item
         for (int g0 = 0; g0 < nhp; g0 += 32) {
             const int ng = min(32, nhp - g0);
             int hidx = 0, hacc = 0;
             unsigned hmb = 0;
             bool hredo = false;
             if (lane < ng) {
-                const int hk = h0 + part + a.split * (g0 + lane);
+                const int hk = h0 + part + sp * (g0 + lane);
                 const float4 hv = a.xs[hk];
                 hidx = __float_as_int(hv.w);
                 s_home[lane] = hv;
