@@ -267,7 +267,7 @@ STAGE_SOURCES = {
 # of the stage's kernel on the named workload, with the hash of its sources at that time
 # (the capture commands and figures are under profiles/)
 TRAFFIC = {
-    ("nl_coop", WORKLOADS[2]): {"bytes_per_launch": 151040, "source_sha16": "69e6f2943c457e05",
+    ("nl_coop", WORKLOADS[2]): {"bytes_per_launch": 150784, "source_sha16": "705382e9780d2994",
                                 "capture": "profiles/nl_coop_emim1536.md"},
 }
 
