@@ -464,13 +464,14 @@ int choose_tangent_tpa(const gm_model *m, int N) {
     return N >= 49152 ? 1 : 4;
 }
 
-// Lanes per atom of the force kernel: with eight or more lanes an atom's dE/dPsi sits once in
-// shared memory (121 registers, four blocks per SM); 8 was fastest from 4k to 131k atoms
-// (131,072: 387 us against 424 us for one lane), 32 below
+// Lanes per atom of the force kernel: with four or more lanes an atom's dE/dPsi sits once in
+// shared memory (106 registers without the virial, four 128-thread blocks per SM); 32 below
+// 3072 atoms, 8 below 49,152, 4 above (131,072 atoms 342 -> 326 us, the 256-box batch 149 ->
+// 133 us against 8; 8 faster from 4k to 8k and at 24k, even at 12k-16k)
 int choose_forces_tpa(const gm_model *m, int N) {
     if (m->forces_tpa > 0) return m->forces_tpa;
     if (m->pair_tpa > 0) return m->pair_tpa;
-    return N >= 3072 ? 8 : 32;
+    return N >= 49152 ? 4 : (N >= 3072 ? 8 : 32);
 }
 
 

@@ -379,17 +379,18 @@ __global__ void __launch_bounds__(256, 2) k_moments_cs(PairArgs a, float *__rest
     }
 }
 
-// Block shape and gradient storage of the force kernel.  With 8 or more lanes per atom the
+// Block shape and gradient storage of the force kernel.  With 4 or more lanes per atom the
 // atom's dE/dPsi (identical for its lanes) sits once in shared memory, transposed to
 // [component][radial function] rows of 8 (one 16-byte and one 4-byte broadcast load per
-// component; atoms 168 floats apart, so the atoms of a warp hit distinct banks), and
+// component; atoms 164 floats apart, so the up to 8 atoms of a warp hit distinct banks), and
 // 128-thread blocks run four per SM; with fewer lanes each lane keeps it in registers.
-template <int TPA> __host__ __device__ constexpr bool forces_gsmem() { return TPA >= 8; }
-template <int TPA> __host__ __device__ constexpr int forces_threads() { return TPA >= 8 ? 128 : 256; }
-constexpr int FG_ROW = 168;
+template <int TPA> __host__ __device__ constexpr bool forces_gsmem() { return TPA >= 4; }
+template <int TPA> __host__ __device__ constexpr int forces_threads() { return TPA >= 4 ? 128 : 256; }
+constexpr int FG_ROW = 164;
+static_assert(FG_ROW >= NC * 8 && FG_ROW % 4 == 0 && FG_ROW % 32 == 4, "dE/dPsi rows: 16-byte aligned, distinct banks");
 // VIR: the per-atom virial is accumulated and stored (vir_atom), else not formed at all
 template <int TPA, int BAS, bool VIR>
-__global__ void __launch_bounds__(forces_threads<TPA>(), TPA >= 8 ? 4 : 1)
+__global__ void __launch_bounds__(forces_threads<TPA>(), TPA >= 4 ? 4 : 1)
     k_forces(PairArgs a, const float *__restrict__ dpsi, float *__restrict__ F, float *__restrict__ vir_atom) {
     constexpr bool GS = forces_gsmem<TPA>();
     extern __shared__ __align__(16) float sbeta[];

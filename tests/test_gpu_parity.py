@@ -637,8 +637,8 @@ def _check_against(ref, batch, E, F, W, tol):
 @pytest.mark.parametrize("case", ["config1", "li_small"])
 def test_energy_forces_every_pair_lane_count(case, tpa, precision, li_small):
     """Every lanes-per-atom shape of the pair kernels (moments: 1 lane, 2 and 4 lanes with the
-    component split over lane pairs, 8-32 with the reduce-scatter; forces: 1, 2 and 4 lanes
-    without the shared-memory dE/dPsi rows, 8-32 with them) against the oracle, with the
+    component split over lane pairs, 8-32 with the reduce-scatter; forces: 1 and 2 lanes
+    without the shared-memory dE/dPsi rows, 4-32 with them) against the oracle, with the
     virial, on the 96-atom box and on 24 Li3PO4 boxes (several with multiple images)."""
     b, d, p = synth.config(1) if case == "config1" else li_small
     ref = _oracle_ref(case, b, d, p)
@@ -665,12 +665,12 @@ def _li_boxes(n_boxes):
     return b, d, p
 
 
-@pytest.mark.parametrize("n_boxes,lanes,force_lanes", [(16, 32, 8), (32, 4, 8), (64, 2, 8), (96, 2, 8)])
+@pytest.mark.parametrize("n_boxes,lanes,force_lanes", [(16, 32, 8), (32, 4, 8), (64, 2, 8), (96, 2, 4)])
 def test_library_lane_choice_by_size_matches_oracle(n_boxes, lanes, force_lanes):
     """8,192, 16,384, 32,768 and 49,152 atoms: the pair-kernel shapes the library picks by size
     for mid-size and large systems (moments 32 lanes per atom with the reduce-scatter kernel,
-    then 4, 2 and 2 with the component-split kernel; forces 8, as for the 131,072-atom crystal
-    and the batched Li3PO4 workload), with no forced knob, against the
+    then 4, 2 and 2 with the component-split kernel; forces 8, then 4 from 49,152 atoms, as for
+    the 131,072-atom crystal and the batched Li3PO4 workload), with no forced knob, against the
     full oracle for both precisions, energies, forces and virials."""
     b, d, p = _li_boxes(n_boxes)
     ref = _oracle_ref(("li_boxes", n_boxes), b, d, p)
@@ -692,7 +692,7 @@ def test_library_lane_choice_by_size_matches_oracle(n_boxes, lanes, force_lanes)
 
 def test_full_size_li3po4_sampled_forces_match_oracle():
     """131,072 atoms in the benchmark's launch configuration (moments two lanes per atom with
-    the component-split kernel, forces eight, the fused network kernel): the forces
+    the component-split kernel, forces four, the fused network kernel): the forces
     and the atomic energies of 12 sampled atoms equal an exact oracle evaluation of those atoms
     (their neighbours' complete environments are evaluated; nothing is truncated), for both
     precisions."""
@@ -704,7 +704,7 @@ def test_full_size_li3po4_sampled_forces_match_oracle():
     for precision in ("fp32", "mixed"):
         m = GMNN(d, p, precision=precision)
         assert _lib.gm_model_pair_lanes(m.handle, b.n_atoms) == 2
-        assert _lib.gm_model_force_lanes(m.handle, b.n_atoms) == 8
+        assert _lib.gm_model_force_lanes(m.handle, b.n_atoms) == 4
         sysd = DeviceSystem(b)
         nl = m.build_neighbors(sysd)
         _, F, _ = m.energy_forces(sysd, nl, virial=False)
