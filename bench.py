@@ -744,6 +744,100 @@ def run_md(args, n_atoms, precision, n_inner=100, replays=5):
 
 # ----------------------------------------------------------------------------- CPU (oracle)
 
+ENS_HEADS = 8
+
+
+def run_readout_variant(args, kind, precision, steps, warmup, measure_accuracy=True):
+    """The headline workload (1536-atom EMIM+BF4- box, r_cut 6 A, MLP 2x512) with the other
+    radial basis or readout the library builds: the Bessel-like basis ("bessel"), or a
+    shallow ensemble of ENS_HEADS output heads with forces as the gradient of the mean energy
+    plus the energy spread ("ensemble-mean"), or also every head's forces and the force
+    spread ("ensemble-jacobian").  Step = neighbour rebuild + this evaluation, replayed as one
+    CUDA graph, L2 flushed between steps (base positions every step); the errors against the
+    FP64 oracle at the same positions."""
+    import torch
+
+    import oracle
+    import synth
+    from synth.configs import emim_number_density, mean_neighbours
+    from synth.params import make_params
+    from paper_2505_22168_b300 import GMNN, DeviceSystem, NeighborList
+
+    batch, desc, params = synth.config(2)
+    if kind == "bessel":
+        desc = dict(desc, basis="bessel")
+    else:
+        desc = dict(desc, n_ensemble=ENS_HEADS)
+        pe = make_params(desc["n_species"], desc["n_hidden"], 1202,
+                         mean_neighbours(emim_number_density(), desc["r_cut"]), n_ensemble=ENS_HEADS)
+        params = dict(params, w3=pe["w3"], b3=pe["b3"])
+    model = GMNN(desc, params, precision=precision)
+    sysd = DeviceSystem(batch)
+    nl = model.build_neighbors(sysd)
+    nl = NeighborList(batch.n_atoms, int(nl.capacity * 1.05) + 1024, model.device)
+    n = batch.n_atoms
+    stream = torch.cuda.current_stream()
+    out = (torch.empty(batch.n_structures, dtype=torch.float64, device=model.device),
+           torch.empty(n, 3, dtype=torch.float32, device=model.device), None)
+    mode = "jacobian" if kind == "ensemble-jacobian" else "mean"
+    res = {}
+
+    def step():
+        if kind == "bessel":
+            model.step(sysd, nl, out)
+        else:
+            model.clear_status()
+            model.build_neighbors(sysd, nl, check=False)
+            res["o"] = model.energy_forces_ensemble(sysd, nl, mode=mode)
+
+    for _ in range(warmup):
+        step()
+    stream.synchronize()
+    model.check_status()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step()
+    graph.replay()
+    stream.synchronize()
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=model.device)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for e0, e1 in ev:
+        flush.zero_()
+        e0.record(stream)
+        graph.replay()
+        e1.record(stream)
+    stream.synchronize()
+    model.check_status()
+    ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / steps
+    accuracy = None
+    if measure_accuracy:
+        onl = oracle.neighbors(batch, desc["r_cut"])
+        ap = np.asarray(batch.atom_ptr)
+        if kind == "bessel":
+            ref = oracle.energy_forces(batch, desc, params, onl, virial=False)
+            accuracy = _errors(out[0].cpu().numpy(), out[1].cpu().numpy(), ref["E"], ref["F"], ref["E_atom"], ap)
+        else:
+            ref = oracle.energy_forces_ensemble(batch, desc, params, onl, virial=False)
+            o = res["o"]
+            accuracy = _errors(o["E"].cpu().numpy(), o["F"].cpu().numpy(), ref["E"], ref["F"], ref["E_atom"], ap)
+            accuracy["energy_spread_abs"] = float(np.abs(o["E_std"].cpu().numpy() - ref["E_std"]).max())
+            accuracy["energy_spread_ref"] = float(np.abs(ref["E_std"]).max())
+            if mode == "jacobian":
+                Fh = o["F_heads"].cpu().numpy().astype(np.float64)
+                accuracy["head_force_rms_worst"] = max(
+                    _errors(None, Fh[k], None, ref["F_heads"][k], None, ap)["force_rms"] for k in range(ENS_HEADS))
+        accuracy["reference"] = "FP64 oracle at the same positions (full evaluation)"
+    del graph, flush
+    name = {"bessel": "emim-64pairs-1536-bessel (the headline box with the Bessel-like radial basis)",
+            "ensemble-mean": f"emim-64pairs-1536-ensemble{ENS_HEADS}-mean (the headline box, {ENS_HEADS}-head "
+                             "shallow ensemble: mean energy, its gradient, energy spread)",
+            "ensemble-jacobian": f"emim-64pairs-1536-ensemble{ENS_HEADS}-jacobian (the headline box, {ENS_HEADS}-head "
+                                 "shallow ensemble: also every head's forces and the force spread)"}[kind]
+    return {"workload": name, "precision": precision, "value": n * 1e3 / ms, "unit": UNIT, "ms_per_step": ms,
+            "steps": steps, "step": "neighbour rebuild + evaluation", "launch_mode": "cuda-graph replay",
+            "l2": "256 MiB buffer written between timed steps", "accuracy": accuracy}
+
+
 def oracle_step_seconds(cfg, budget_s, max_evals=None, keep=False):
     """Time the FP64 oracle (brute-force neighbours + energy/forces) on the workload's
     structure; repeats until budget_s of CPU time or max_evals evaluations.  With keep, also
@@ -985,6 +1079,13 @@ def main():
                 if prec == "mixed" and not _mixed_available():
                     continue
                 variants.append(run_md(args, n_md, prec))
+        # the Bessel-like basis and the shallow-ensemble readout on the headline box
+        for kind in ("bessel", "ensemble-mean", "ensemble-jacobian"):
+            for prec in ("fp32", "mixed"):
+                if prec == "mixed" and not _mixed_available():
+                    continue
+                variants.append(run_readout_variant(args, kind, prec, max(5, args.steps // 2), args.warmup,
+                                                    measure_accuracy=rank == 0 and not args.no_accuracy))
 
     if rank != 0:
         if world > 1:
