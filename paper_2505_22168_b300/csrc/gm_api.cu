@@ -257,10 +257,19 @@ struct EfWs {
     unsigned long long *red_acc;   // fixed-point structure sums (cleared by the position split)
     int n_red_acc;
     float4 *pos_hi, *pos_lo;   // hi/lo FP32 split of the positions (pair displacements)
-    // shallow ensembles (E > 1): per-head partial sums, head-energy accumulators, per-head forces
-    float *nn_ens, *Fk;
+    // shallow ensembles (E > 1): per-head partial sums, head-energy accumulators, per-head forces,
+    // and for the Jacobian mode the dE/dG and dE/dPsi of a chunk of heads (ens_head_chunk)
+    float *nn_ens, *Fk, *dGh, *dpsih;
     unsigned long long *ens_acc;
 };
+
+// Heads whose backward contraction and force pass share one launch in the Jacobian mode: as
+// many as keep the chunk within 16,384 virtual atoms (small systems, where one head's pass
+// leaves most of the GPU idle), one at a time above
+int ens_head_chunk(int E, int N) {
+    const int hc = N > 0 ? 16384 / N : E;
+    return hc < 1 ? 1 : (hc > E ? E : hc);
+}
 
 EfWs carve_ef(Carve &c, int B, int N, int H, int E = 1) {
     EfWs w;
@@ -280,12 +289,15 @@ EfWs carve_ef(Carve &c, int B, int N, int H, int E = 1) {
     w.vir_atom = c.take<float>(n1 * 9);
     w.red_acc = c.take<unsigned long long>(reduce_acc_words(B));
     w.n_red_acc = (int)reduce_acc_words(B);
-    w.nn_ens = w.Fk = nullptr;
+    w.nn_ens = w.Fk = w.dGh = w.dpsih = nullptr;
     w.ens_acc = nullptr;
     if (E > 1) {
         w.nn_ens = c.take<float>(m1 * E * (H / 32));
         w.Fk = c.take<float>((size_t)E * n1 * 3);
         w.ens_acc = c.take<unsigned long long>(ens_acc_words(B, E));
+        const int hc = ens_head_chunk(E, N);
+        w.dGh = hc > 1 ? c.take<float>((size_t)hc * m1 * NFP) : w.dG;
+        w.dpsih = hc > 1 ? c.take<float>((size_t)hc * n1 * NPSI) : w.dpsi;
     }
     return w;
 }
@@ -980,22 +992,30 @@ gm_status gm_energy_forces_ensemble(const gm_model *m, const gm_system *sys, con
     }
     if (mode == GM_ENS_JACOBIAN && N > 0) {
         // every head's forces: the backward pass from L2 with that head's weights (the features,
-        // the first layer and the moments of the mean pass are reused)
+        // the first layer and the moments of the mean pass are reused); the backward
+        // contraction and the force pass of a chunk of heads run as one launch each
         const int Mp = round_up(N, TILE_M);
         float *Fk = forces_heads ? forces_heads : w.Fk;
         PairArgs a = pair_args(m, sys, nl, w.pos_hi, w.pos_lo, status);
-        for (int k = 0; k < E; ++k) {
-            float *Fh = Fk + (size_t)k * N * 3;
-            if (cudaMemsetAsync(Fh, 0, sizeof(float) * 3 * N, st) != cudaSuccess)
+        const int hc = ens_head_chunk(E, N);
+        for (int k0 = 0; k0 < E; k0 += hc) {
+            const int kn = std::min(hc, E - k0);
+            float *Fh = Fk + (size_t)k0 * N * 3;
+            if (cudaMemsetAsync(Fh, 0, sizeof(float) * 3 * (size_t)N * kn, st) != cudaSuccess)
                 return fail(GM_ERR_CUDA, "memset of the head forces failed");
-            if ((s = network_fwd_bwd(m, sys, w, Mp, status, st, nullptr, m->w3e + (size_t)k * H, false, true)) != GM_OK)
-                return s;
+            for (int u = 0; u < kn; ++u) {
+                EfWs wh = w;
+                wh.dG = w.dGh + (size_t)u * Mp * NFP;
+                if ((s = network_fwd_bwd(m, sys, wh, Mp, status, st, nullptr, m->w3e + (size_t)(k0 + u) * H, false,
+                                         true)) != GM_OK)
+                    return s;
+            }
             {
                 StageScope sc(ST_CONTRACT_BWD, st);
-                launch_contract_bwd(w.psi, w.dG, N, w.dpsi, st);
+                launch_contract_bwd(w.psi, w.dGh, N, w.dpsih, st, false, kn, (size_t)Mp * NFP);
             }
             StageScope sc(ST_FORCES, st);
-            launch_forces(a, choose_forces_tpa(m, N), w.dpsi, Fh, nullptr, st);
+            launch_forces(a, choose_forces_tpa(m, N * kn), w.dpsih, Fh, nullptr, st, kn);
         }
         if (force_std) launch_ens_force_std(N, E, Fk, force_std, st);
     }

@@ -677,14 +677,20 @@ __global__ void __launch_bounds__(W * 32) k_contract_fwd(const float *__restrict
 }
 
 template <int W>
+// Shallow-ensemble heads in one launch: bph blocks per head, block b taking head b / bph with
+// its dE/dG at dG + head dg_hs and its dE/dPsi at dpsi + head dpsi_hs (one head: bph = grid)
 __global__ void __launch_bounds__(W * 32) k_contract_bwd(const float *__restrict__ psi, const float *__restrict__ dG,
-                                                         int N, float *__restrict__ dpsi, int dg_tiled) {
+                                                         int N, float *__restrict__ dpsi, int dg_tiled, int bph,
+                                                         size_t dg_hs, size_t dpsi_hs) {
     extern __shared__ __align__(16) float smb[];
     float *ptile = smb;                                    // [32][100] moments
     float *slots = ptile + CT_ATOMS * NPSI;                // W x [32][100] partial dE/dPsi
     float *gtile = slots + W * CT_ATOMS * NPSI;            // [32][GT_STRIDE] dE/dG
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * CT_ATOMS;
+    const int head = blockIdx.x / bph;
+    const int m0 = (blockIdx.x - head * bph) * CT_ATOMS;
+    dG += head * dg_hs;
+    dpsi += head * dpsi_hs;
     griddep_wait();
     stage_psi<W * 32>(psi, m0, N, ptile);
     {
@@ -948,23 +954,27 @@ void launch_contract_fwd_bf16(const float *psi, int N, int Mp, __nv_bfloat16 *G,
 }
 
 template <int W>
-static void launch_bwd_w(int blocks, const float *psi, const float *dG, int N, float *dpsi, int dg_tiled,
-                         cudaStream_t st) {
+static void launch_bwd_w(int blocks, const float *psi, const float *dG, int N, float *dpsi, int dg_tiled, int bph,
+                         size_t dg_hs, size_t dpsi_hs, cudaStream_t st) {
     static PerDeviceOnce attr;
     if (attr.first()) {
         cudaFuncSetAttribute(k_contract_bwd<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ct_bwd_smem<W>());
     }
-    launch_pdl(k_contract_bwd<W>, dim3(blocks), dim3(W * 32), ct_bwd_smem<W>(), st, psi, dG, N, dpsi, dg_tiled);
+    launch_pdl(k_contract_bwd<W>, dim3(blocks), dim3(W * 32), ct_bwd_smem<W>(), st, psi, dG, N, dpsi, dg_tiled, bph,
+               dg_hs, dpsi_hs);
     note_launches(1);
 }
 
-void launch_contract_bwd(const float *psi, const float *dG, int N, float *dpsi, cudaStream_t st, bool dg_tiled) {
-    const int blocks = (N + CT_ATOMS - 1) / CT_ATOMS;
-    if (blocks <= 0) return;
+void launch_contract_bwd(const float *psi, const float *dG, int N, float *dpsi, cudaStream_t st, bool dg_tiled,
+                         int heads, size_t dg_head_stride) {
+    const int bph = (N + CT_ATOMS - 1) / CT_ATOMS;
+    if (bph <= 0 || heads < 1) return;
+    const int blocks = bph * heads;
+    const size_t dpsi_hs = (size_t)N * NPSI;
     if (blocks < sm_count())
-        launch_bwd_w<2 * CT_BWD_W>(blocks, psi, dG, N, dpsi, dg_tiled ? 1 : 0, st);
+        launch_bwd_w<2 * CT_BWD_W>(blocks, psi, dG, N, dpsi, dg_tiled ? 1 : 0, bph, dg_head_stride, dpsi_hs, st);
     else
-        launch_bwd_w<CT_BWD_W>(blocks, psi, dG, N, dpsi, dg_tiled ? 1 : 0, st);
+        launch_bwd_w<CT_BWD_W>(blocks, psi, dG, N, dpsi, dg_tiled ? 1 : 0, bph, dg_head_stride, dpsi_hs, st);
 }
 
 }  // namespace gm

@@ -15,9 +15,10 @@ void launch_contract_fwd_bf16(const float *psi, int N, int Mp, __nv_bfloat16 *G,
                               cudaStream_t st);
 // dE/dG [Mp][384] FP32 and psi -> dE/dpsi [N][100] FP32 (unique components)
 // dg_tiled: dG in the per-tile fused network kernel's layout (per 128-row tile, 4-column groups
-// major and rows minor), else row-major [Mp][384]
+// major and rows minor), else row-major [Mp][384].  heads > 1: the dE/dG of that many
+// shallow-ensemble heads, dg_head_stride floats apart, into dpsi [heads][N][100] in one launch
 void launch_contract_bwd(const float *psi, const float *dG, int N, float *dpsi, cudaStream_t st,
-                         bool dg_tiled = false);
+                         bool dg_tiled = false, int heads = 1, size_t dg_head_stride = 0);
 
 // Parameter gradient: GG [2Mp][384] = [G; dG/dPsi . psid]; and from Gbs = [dJ/dG; dJ/dGd]
 // the moment adjoints psib, psidb [N][100] (see gm_contract.cu).

@@ -388,10 +388,14 @@ template <int TPA> __host__ __device__ constexpr bool forces_gsmem() { return TP
 template <int TPA> __host__ __device__ constexpr int forces_threads() { return TPA >= 4 ? 128 : 256; }
 constexpr int FG_ROW = 164;
 static_assert(FG_ROW >= NC * 8 && FG_ROW % 4 == 0 && FG_ROW % 32 == 4, "dE/dPsi rows: 16-byte aligned, distinct banks");
-// VIR: the per-atom virial is accumulated and stored (vir_atom), else not formed at all
+// VIR: the per-atom virial is accumulated and stored (vir_atom), else not formed at all.
+// heads > 1 (shallow-ensemble heads, no virial): heads x N virtual atoms, virtual atom
+// h N + i taking dE/dPsi row h N + i and adding into forces F[h][N][3], so that the heads'
+// force passes share one launch
 template <int TPA, int BAS, bool VIR>
 __global__ void __launch_bounds__(forces_threads<TPA>(), TPA >= 4 ? 4 : 1)
-    k_forces(PairArgs a, const float *__restrict__ dpsi, float *__restrict__ F, float *__restrict__ vir_atom) {
+    k_forces(PairArgs a, const float *__restrict__ dpsi, float *__restrict__ F, float *__restrict__ vir_atom,
+             int heads) {
     constexpr bool GS = forces_gsmem<TPA>();
     extern __shared__ __align__(16) float sbeta[];
     float *gsm = sbeta + a.S * a.S * NR * BETA_ROW;              // [atoms of the block][FG_ROW]
@@ -404,7 +408,7 @@ __global__ void __launch_bounds__(forces_threads<TPA>(), TPA >= 4 ? 4 : 1)
         constexpr int V4 = NPSI / 4, C4 = NC / 4;
         for (int q = threadIdx.x; q < APB * V4; q += blockDim.x) {
             const int al = q / V4, e4 = q - al * V4, s = e4 / C4, c = 4 * (e4 - s * C4), m = a_first + al;
-            const float4 v = m < a.N ? __ldg(reinterpret_cast<const float4 *>(dpsi + (size_t)m * NPSI) + e4)
+            const float4 v = m < a.N * heads ? __ldg(reinterpret_cast<const float4 *>(dpsi + (size_t)m * NPSI) + e4)
                                      : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             float *row = gsm + al * FG_ROW + c * 8 + s;
             row[0] = v.x;
@@ -415,8 +419,10 @@ __global__ void __launch_bounds__(forces_threads<TPA>(), TPA >= 4 ? 4 : 1)
     }
     __syncthreads();
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-    const int atom = gt / TPA, sub = gt % TPA;
-    const bool active = atom < a.N && !status_bad(a.status);
+    const int atom_v = gt / TPA, sub = gt % TPA;
+    const int head = a.N > 0 ? atom_v / a.N : 0, atom = atom_v - head * a.N;
+    const bool active = atom_v < a.N * heads && !status_bad(a.status);
+    F += (size_t)head * a.N * 3;
     float Fi[3] = {0.0f, 0.0f, 0.0f};
     float V[9];
 #pragma unroll
@@ -425,7 +431,7 @@ __global__ void __launch_bounds__(forces_threads<TPA>(), TPA >= 4 ? 4 : 1)
         float g[GS ? 1 : NPSI];
         const float *gs = gsm + (threadIdx.x / TPA) * FG_ROW;
         if (!GS) {
-            const float4 *g4 = reinterpret_cast<const float4 *>(dpsi + (size_t)atom * NPSI);
+            const float4 *g4 = reinterpret_cast<const float4 *>(dpsi + (size_t)atom_v * NPSI);
 #pragma unroll
             for (int q = 0; q < NPSI / 4; ++q) {
                 const float4 v = g4[q];
@@ -736,9 +742,10 @@ static void launch_moments_t(const PairArgs &a, float *psi, cudaStream_t st) {
 }
 
 template <int TPA, int BAS>
-static void launch_forces_t(const PairArgs &a, const float *dpsi, float *F, float *vir, cudaStream_t st) {
+static void launch_forces_t(const PairArgs &a, const float *dpsi, float *F, float *vir, cudaStream_t st,
+                            int heads) {
     const int threads = forces_threads<TPA>();
-    const long long total = (long long)a.N * TPA;
+    const long long total = (long long)a.N * heads * TPA;
     const int blocks = (int)((total + threads - 1) / threads);
     const size_t smem = beta_smem_bytes(a.S) +
                         (forces_gsmem<TPA>() ? sizeof(float) * (threads / TPA) * FG_ROW : 0);
@@ -750,7 +757,7 @@ static void launch_forces_t(const PairArgs &a, const float *dpsi, float *F, floa
         allow_beta_smem(k_forces<TPA, BAS, false>, extra);
     }
     if (blocks > 0) {
-        launch_pdl(kern, dim3(blocks), dim3(threads), smem, st, a, dpsi, F, vir);
+        launch_pdl(kern, dim3(blocks), dim3(threads), smem, st, a, dpsi, F, vir, heads);
         note_launches(1);
     }
 }
@@ -773,20 +780,22 @@ void launch_moments(const PairArgs &a, int tpa, float *psi, cudaStream_t st) {
 }
 
 template <int BAS>
-static void launch_forces_b(const PairArgs &a, int tpa, const float *dpsi, float *F, float *vir, cudaStream_t st) {
+static void launch_forces_b(const PairArgs &a, int tpa, const float *dpsi, float *F, float *vir, cudaStream_t st,
+                            int heads) {
     switch (tpa) {
-    case 1: launch_forces_t<1, BAS>(a, dpsi, F, vir, st); break;
-    case 2: launch_forces_t<2, BAS>(a, dpsi, F, vir, st); break;
-    case 4: launch_forces_t<4, BAS>(a, dpsi, F, vir, st); break;
-    case 8: launch_forces_t<8, BAS>(a, dpsi, F, vir, st); break;
-    case 16: launch_forces_t<16, BAS>(a, dpsi, F, vir, st); break;
-    default: launch_forces_t<32, BAS>(a, dpsi, F, vir, st); break;
+    case 1: launch_forces_t<1, BAS>(a, dpsi, F, vir, st, heads); break;
+    case 2: launch_forces_t<2, BAS>(a, dpsi, F, vir, st, heads); break;
+    case 4: launch_forces_t<4, BAS>(a, dpsi, F, vir, st, heads); break;
+    case 8: launch_forces_t<8, BAS>(a, dpsi, F, vir, st, heads); break;
+    case 16: launch_forces_t<16, BAS>(a, dpsi, F, vir, st, heads); break;
+    default: launch_forces_t<32, BAS>(a, dpsi, F, vir, st, heads); break;
     }
 }
 
-void launch_forces(const PairArgs &a, int tpa, const float *dpsi, float *F, float *vir, cudaStream_t st) {
-    if (a.rc.basis == BASIS_BESSEL) launch_forces_b<BASIS_BESSEL>(a, tpa, dpsi, F, vir, st);
-    else launch_forces_b<BASIS_GAUSSIAN>(a, tpa, dpsi, F, vir, st);
+void launch_forces(const PairArgs &a, int tpa, const float *dpsi, float *F, float *vir, cudaStream_t st, int heads) {
+    if (heads < 1 || (heads > 1 && vir)) return;                    // heads: no virial
+    if (a.rc.basis == BASIS_BESSEL) launch_forces_b<BASIS_BESSEL>(a, tpa, dpsi, F, vir, st, heads);
+    else launch_forces_b<BASIS_GAUSSIAN>(a, tpa, dpsi, F, vir, st, heads);
 }
 
 }  // namespace gm

@@ -26,7 +26,10 @@ struct PairArgs {
 void launch_split_pos(int N, const double *pos, const int32_t *species, float4 *hi, float4 *lo, float *zero_F,
                       unsigned long long *zero_acc, int n_acc, cudaStream_t st);
 void launch_moments(const PairArgs &a, int tpa, float *psi, cudaStream_t st);
-void launch_forces(const PairArgs &a, int tpa, const float *dpsi, float *F, float *vir_atom, cudaStream_t st);
+// heads > 1: the forces of that many shallow-ensemble heads in one launch, dpsi [heads][N][100]
+// and F [heads][N][3] (vir_atom must be null)
+void launch_forces(const PairArgs &a, int tpa, const float *dpsi, float *F, float *vir_atom, cudaStream_t st,
+                   int heads = 1);
 
 // parameter gradient: tangent moments along vel (= dL/dF) and block partials of dJ/dbeta
 // tpa: lanes per atom as for launch_moments
