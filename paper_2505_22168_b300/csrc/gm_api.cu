@@ -259,7 +259,7 @@ struct EfWs {
     float4 *pos_hi, *pos_lo;   // hi/lo FP32 split of the positions (pair displacements)
     // shallow ensembles (E > 1): per-head partial sums, head-energy accumulators, per-head forces,
     // and for the Jacobian mode the dE/dG and dE/dPsi of a chunk of heads (ens_head_chunk)
-    float *nn_ens, *Fk, *dGh, *dpsih;
+    float *nn_ens, *Fk, *dZ2h, *dZ1h, *dGh, *dpsih;
     unsigned long long *ens_acc;
 };
 
@@ -289,13 +289,15 @@ EfWs carve_ef(Carve &c, int B, int N, int H, int E = 1) {
     w.vir_atom = c.take<float>(n1 * 9);
     w.red_acc = c.take<unsigned long long>(reduce_acc_words(B));
     w.n_red_acc = (int)reduce_acc_words(B);
-    w.nn_ens = w.Fk = w.dGh = w.dpsih = nullptr;
+    w.nn_ens = w.Fk = w.dZ2h = w.dZ1h = w.dGh = w.dpsih = nullptr;
     w.ens_acc = nullptr;
     if (E > 1) {
         w.nn_ens = c.take<float>(m1 * E * (H / 32));
         w.Fk = c.take<float>((size_t)E * n1 * 3);
         w.ens_acc = c.take<unsigned long long>(ens_acc_words(B, E));
         const int hc = ens_head_chunk(E, N);
+        w.dZ2h = hc > 1 ? c.take<float>((size_t)hc * m1 * H) : w.dZ2;
+        w.dZ1h = hc > 1 ? c.take<float>((size_t)hc * m1 * H) : w.dZ1;
         w.dGh = hc > 1 ? c.take<float>((size_t)hc * m1 * NFP) : w.dG;
         w.dpsih = hc > 1 ? c.take<float>((size_t)hc * n1 * NPSI) : w.dpsi;
     }
@@ -774,9 +776,12 @@ static int mlp_form(const gm_model *m, bool ens, bool from_l2, const float *head
 //              a shallow ensemble is the heads' mean)
 //   ens:       also write every ensemble head's partial sums (w.nn_ens) in the L2 epilogue
 //   from_l2:   skip L1 (its outputs A1, D1 are still in the workspace from an earlier pass)
+//   nheads:    with from_l2 and head, the backward pass of nheads heads (weights head + u H):
+//              one L2 GEMM per head into the stacked dZ2 rows u Mp .., then B1 and B0 once
+//              over nheads Mp rows (phi'(z1) read at row mod Mp) into the stacked dZ1 and dG
 static gm_status network_fwd_bwd(const gm_model *m, const gm_system *sys, EfWs &w, int Mp, int32_t *status,
                                  cudaStream_t st, double *energy = nullptr, const float *head = nullptr,
-                                 bool ens = false, bool from_l2 = false) {
+                                 bool ens = false, bool from_l2 = false, int nheads = 1) {
     const int H = m->H;
     const int l2 = ens ? EPI_L2E : EPI_L2;
     EpiArgs e{};
@@ -850,17 +855,19 @@ static gm_status network_fwd_bwd(const gm_model *m, const gm_system *sys, EfWs &
         const bf *W2b = f16 ? reinterpret_cast<const bf *>(m->W2_f) : m->W2_h;
         const bf *W1b = f16 ? reinterpret_cast<const bf *>(m->W1p_f) : m->W1p_h;
         e.bias = m->b2;
-        e.out0 = dZ2;
         e.out1 = nullptr;
         e.lo_out = f16 ? 0 : (sp & 4) != 0;
         e.out_f16 = f16;
-        {
+        for (int u = 0; u < nheads; ++u) {
+            e.out0 = dZ2 + (size_t)u * Mp * 2 * H;          // [Mp][2H] 16-bit rows per head
+            if (nheads > 1) e.w3 = head + (size_t)u * H;
             StageScope sc(ST_GEMM_L2, st);
             if ((s = gemm_bf16(l2, m->d.activation, A1, m->W2t_h, Mp, H, H, (sp & 2) != 0, e, status, st, m->gemm_bn, m->gemm_cps)) != GM_OK)
                 return fail(s, "tcgen05 GEMM L2 failed");
         }
         e.out0 = dZ1;
         e.aux = D1;
+        e.aux_rows = nheads > 1 ? Mp : 0;
         e.lo_out = f16 ? 0 : (sp & 8) != 0;
         if (energy) {
             e.atom_ptr = sys->atom_ptr;
@@ -872,8 +879,8 @@ static gm_status network_fwd_bwd(const gm_model *m, const gm_system *sys, EfWs &
         }
         {
             StageScope sc(ST_GEMM_B1, st);
-            if ((s = gemm_bf16(EPI_B1, 0, dZ2, W2b, Mp, H, H, f16 ? 0 : (sp & 4) != 0, e, status, st, m->gemm_bn,
-                               m->gemm_cps, f16)) != GM_OK)
+            if ((s = gemm_bf16(EPI_B1, 0, dZ2, W2b, nheads * Mp, H, H, f16 ? 0 : (sp & 4) != 0, e, status, st,
+                               m->gemm_bn, m->gemm_cps, f16)) != GM_OK)
                 return fail(s, "tcgen05 GEMM B1 failed");
         }
         e.out0 = w.dG;
@@ -881,8 +888,8 @@ static gm_status network_fwd_bwd(const gm_model *m, const gm_system *sys, EfWs &
         e.out_f16 = 0;
         {
             StageScope sc(ST_GEMM_B0, st);
-            if ((s = gemm_bf16(EPI_STORE, 0, dZ1, W1b, Mp, NFP, H, f16 ? 0 : (sp & 8) != 0, e, status, st, m->gemm_bn,
-                               m->gemm_cps, f16)) != GM_OK)
+            if ((s = gemm_bf16(EPI_STORE, 0, dZ1, W1b, nheads * Mp, NFP, H, f16 ? 0 : (sp & 8) != 0, e, status, st,
+                               m->gemm_bn, m->gemm_cps, f16)) != GM_OK)
                 return fail(s, "tcgen05 GEMM B0 failed");
         }
         return GM_OK;
@@ -895,22 +902,24 @@ static gm_status network_fwd_bwd(const gm_model *m, const gm_system *sys, EfWs &
         gemm_f32(EPI_L1, m->d.activation, w.G, m->W1t, Mp, H, NFP, e, st);
     }
     e.bias = m->b2;
-    e.out0 = w.dZ2;
     e.out1 = nullptr;
-    {
+    for (int u = 0; u < nheads; ++u) {
+        e.out0 = w.dZ2 + (size_t)u * Mp * H;
+        if (nheads > 1) e.w3 = head + (size_t)u * H;
         StageScope sc(ST_GEMM_L2, st);
         gemm_f32(l2, m->d.activation, w.A1, m->W2t, Mp, H, H, e, st);
     }
     e.out0 = w.dZ1;
     e.aux = w.D1;
+    e.aux_rows = nheads > 1 ? Mp : 0;
     {
         StageScope sc(ST_GEMM_B1, st);
-        gemm_f32(EPI_B1, 0, w.dZ2, m->W2, Mp, H, H, e, st);
+        gemm_f32(EPI_B1, 0, w.dZ2, m->W2, nheads * Mp, H, H, e, st);
     }
     e.out0 = w.dG;
     {
         StageScope sc(ST_GEMM_B0, st);
-        gemm_f32(EPI_STORE, 0, w.dZ1, m->W1p, Mp, NFP, H, e, st);
+        gemm_f32(EPI_STORE, 0, w.dZ1, m->W1p, nheads * Mp, NFP, H, e, st);
     }
     return GM_OK;
 }
@@ -993,7 +1002,8 @@ gm_status gm_energy_forces_ensemble(const gm_model *m, const gm_system *sys, con
     if (mode == GM_ENS_JACOBIAN && N > 0) {
         // every head's forces: the backward pass from L2 with that head's weights (the features,
         // the first layer and the moments of the mean pass are reused); the backward
-        // contraction and the force pass of a chunk of heads run as one launch each
+        // contraction, the force pass and the two backward GEMMs of a chunk of heads run as one
+        // launch each
         const int Mp = round_up(N, TILE_M);
         float *Fk = forces_heads ? forces_heads : w.Fk;
         PairArgs a = pair_args(m, sys, nl, w.pos_hi, w.pos_lo, status);
@@ -1003,13 +1013,13 @@ gm_status gm_energy_forces_ensemble(const gm_model *m, const gm_system *sys, con
             float *Fh = Fk + (size_t)k0 * N * 3;
             if (cudaMemsetAsync(Fh, 0, sizeof(float) * 3 * (size_t)N * kn, st) != cudaSuccess)
                 return fail(GM_ERR_CUDA, "memset of the head forces failed");
-            for (int u = 0; u < kn; ++u) {
-                EfWs wh = w;
-                wh.dG = w.dGh + (size_t)u * Mp * NFP;
-                if ((s = network_fwd_bwd(m, sys, wh, Mp, status, st, nullptr, m->w3e + (size_t)(k0 + u) * H, false,
-                                         true)) != GM_OK)
-                    return s;
-            }
+            EfWs wh = w;                                // the chunk's stacked dZ2, dZ1 and dG rows
+            wh.dZ2 = w.dZ2h;
+            wh.dZ1 = w.dZ1h;
+            wh.dG = w.dGh;
+            if ((s = network_fwd_bwd(m, sys, wh, Mp, status, st, nullptr, m->w3e + (size_t)k0 * H, false, true,
+                                     kn)) != GM_OK)
+                return s;
             {
                 StageScope sc(ST_CONTRACT_BWD, st);
                 launch_contract_bwd(w.psi, w.dGh, N, w.dpsih, st, false, kn, (size_t)Mp * NFP);

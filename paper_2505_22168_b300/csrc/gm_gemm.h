@@ -28,6 +28,7 @@ struct EpiArgs {
     void *out0;              // A1 (L1), dZ2 (L2), dZ1 (B1), C (STORE); row stride N
     void *out1;              // D1 (L1)
     const void *aux;         // D1 (B1)
+    int aux_rows;            // B1: aux row = output row mod aux_rows (stacked heads), 0 = the row itself
     float *nn_part;          // [M][N/32] (L2): partial output-layer sums per 32 columns
     int n_ens;               // EPI_L2E: ensemble heads E
     const float *w3e;        // EPI_L2E: [E][N] head weights

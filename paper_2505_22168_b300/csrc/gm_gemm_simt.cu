@@ -76,7 +76,8 @@ __global__ void __launch_bounds__(256) k_gemm_f32(const float *__restrict__ A, c
         if (EPI == EPI_STORE) {
             *reinterpret_cast<float4 *>(o0) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
         } else if (EPI == EPI_B1) {
-            const float4 d = *reinterpret_cast<const float4 *>(static_cast<const float *>(e.aux) + (size_t)m * N + nb);
+            const int ma = e.aux_rows ? m % e.aux_rows : m;
+            const float4 d = *reinterpret_cast<const float4 *>(static_cast<const float *>(e.aux) + (size_t)ma * N + nb);
             *reinterpret_cast<float4 *>(o0) = make_float4(acc[i][0] * d.x, acc[i][1] * d.y, acc[i][2] * d.z, acc[i][3] * d.w);
         } else if (EPI == EPI_L1) {
             float a[4], d[4];

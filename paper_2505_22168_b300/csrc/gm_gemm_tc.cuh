@@ -261,7 +261,7 @@ __device__ __forceinline__ void epilogue32(const EpiArgs &e, int row0, int n, in
     }
     float y[32];
     if (EPI == EPI_B1) {
-        warp_load_f32(sg.d, static_cast<const float *>(e.aux), row0, N, n, lane);
+        warp_load_f32(sg.d, static_cast<const float *>(e.aux), e.aux_rows ? row0 % e.aux_rows : row0, N, n, lane);
         __syncwarp();
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
