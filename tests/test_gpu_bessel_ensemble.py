@@ -165,6 +165,29 @@ def test_shallow_ensemble_matches_oracle(case, mode, precision):
     assert force_error(F.cpu().numpy().astype(np.float64), ref)[0] <= TOL[precision]
 
 
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+@pytest.mark.parametrize("n_boxes", [16, 34])
+def test_shallow_ensemble_jacobian_head_chunks(n_boxes, precision):
+    """The Jacobian mode stacks the backward passes of as many heads as keep heads x atoms
+    within 16,384: 16 random-packed Li3PO4-like boxes of 512 atoms (8,192 atoms) run the four
+    heads in two chunks of two, 34 boxes (17,408 atoms) one head at a time in the single-head
+    buffers.  Against the oracle: every head's forces, the mean and the spreads."""
+    from synth.systems import li3po4_random, make_batch
+    from paper_2505_22168_b300 import GMNN, DeviceSystem
+    _, d, p = synth.config(3)
+    b = make_batch([li3po4_random(64, 7300 + k) for k in range(n_boxes)], 3)
+    d = dict(d, n_ensemble=N_HEADS)
+    pe = _ens_params(d, p)
+    ref = _ref(("ens_chunks", n_boxes),
+               lambda: oracle.energy_forces_ensemble(b, d, pe, oracle.neighbors(b, d["r_cut"]), virial=False))
+    m = GMNN(d, pe, precision=precision)
+    sysd = DeviceSystem(b)
+    nl = m.build_neighbors(sysd)
+    out = m.energy_forces_ensemble(sysd, nl, mode="jacobian")
+    m.check_status()
+    _ens_check(out, ref, b, precision, True)
+
+
 def test_shallow_ensemble_rejects_what_it_does_not_support():
     from paper_2505_22168_b300 import GMNN, DeviceSystem, _lib
     b, d, p = _case("config1")
