@@ -777,13 +777,15 @@ static int mlp_form(const gm_model *m, bool ens, bool from_l2, const float *head
 //   ens:       also write every ensemble head's partial sums (w.nn_ens) in the L2 epilogue
 //   from_l2:   skip L1 (its outputs A1, D1 are still in the workspace from an earlier pass)
 //   nheads:    with from_l2 and head, the backward pass of nheads heads (weights head + u H):
-//              one L2 GEMM per head into the stacked dZ2 rows u Mp .., then B1 and B0 once
-//              over nheads Mp rows (phi'(z1) read at row mod Mp) into the stacked dZ1 and dG
+//              one L2 GEMM whose epilogue writes every head's dZ2 rows (u Mp ..), then B1 and
+//              B0 once over nheads Mp rows (phi'(z1) read at row mod Mp) into the stacked dZ1
+//              and dG; no output-layer partial sums
 static gm_status network_fwd_bwd(const gm_model *m, const gm_system *sys, EfWs &w, int Mp, int32_t *status,
                                  cudaStream_t st, double *energy = nullptr, const float *head = nullptr,
                                  bool ens = false, bool from_l2 = false, int nheads = 1) {
     const int H = m->H;
-    const int l2 = ens ? EPI_L2E : EPI_L2;
+    const bool stacked = from_l2 && head != nullptr;   // the Jacobian mode's heads
+    const int l2 = stacked ? EPI_L2H : (ens ? EPI_L2E : EPI_L2);
     EpiArgs e{};
     e.n_atoms = sys->n_atoms;
     e.n_species = m->S;
@@ -794,6 +796,7 @@ static gm_status network_fwd_bwd(const gm_model *m, const gm_system *sys, EfWs &
     e.n_ens = ens ? m->E : 1;
     e.w3e = m->w3e;
     e.nn_ens = w.nn_ens;
+    e.n_heads = nheads;
     int cs = 1;
     const int form = mlp_form(m, ens, from_l2, head, sys->n_atoms, &cs);
     if (form != MLP_GEMMS) {
@@ -858,9 +861,9 @@ static gm_status network_fwd_bwd(const gm_model *m, const gm_system *sys, EfWs &
         e.out1 = nullptr;
         e.lo_out = f16 ? 0 : (sp & 4) != 0;
         e.out_f16 = f16;
-        for (int u = 0; u < nheads; ++u) {
-            e.out0 = dZ2 + (size_t)u * Mp * 2 * H;          // [Mp][2H] 16-bit rows per head
-            if (nheads > 1) e.w3 = head + (size_t)u * H;
+        e.out0 = dZ2;
+        e.head_stride = (size_t)Mp * 2 * H;                  // [Mp][2H] 16-bit rows per head
+        {
             StageScope sc(ST_GEMM_L2, st);
             if ((s = gemm_bf16(l2, m->d.activation, A1, m->W2t_h, Mp, H, H, (sp & 2) != 0, e, status, st, m->gemm_bn, m->gemm_cps)) != GM_OK)
                 return fail(s, "tcgen05 GEMM L2 failed");
@@ -903,9 +906,9 @@ static gm_status network_fwd_bwd(const gm_model *m, const gm_system *sys, EfWs &
     }
     e.bias = m->b2;
     e.out1 = nullptr;
-    for (int u = 0; u < nheads; ++u) {
-        e.out0 = w.dZ2 + (size_t)u * Mp * H;
-        if (nheads > 1) e.w3 = head + (size_t)u * H;
+    e.out0 = w.dZ2;
+    e.head_stride = (size_t)Mp * H;
+    {
         StageScope sc(ST_GEMM_L2, st);
         gemm_f32(l2, m->d.activation, w.A1, m->W2t, Mp, H, H, e, st);
     }

@@ -10,14 +10,16 @@
 //   B0  dG = dZ1 W1^T     (stored FP32)
 // A shallow ensemble (E output heads, section "Uncertainty Quantification") runs L2 as
 // EPI_L2E: w3 is the heads' mean (its gradient is the mean force) and the epilogue also
-// writes each head's partial sums of a2 . w3e[k] per 32 columns.
+// writes each head's partial sums of a2 . w3e[k] per 32 columns.  Its per-head forces (the
+// Jacobian mode, Eq. jacobian) need dZ2_k = sigma_Z w3e[k] phi'(Z2 + b2) for every head k;
+// EPI_L2H writes those stacked rows from one L2 product (Z2 does not depend on the head).
 #pragma once
 
 #include "gm_internal.h"
 
 namespace gm {
 
-enum { EPI_L1 = 0, EPI_L2 = 1, EPI_B1 = 2, EPI_STORE = 3, EPI_L2E = 4 };
+enum { EPI_L1 = 0, EPI_L2 = 1, EPI_B1 = 2, EPI_STORE = 3, EPI_L2E = 4, EPI_L2H = 5 };
 
 struct EpiArgs {
     const float *bias;       // [N] (L1, L2)
@@ -33,6 +35,8 @@ struct EpiArgs {
     int n_ens;               // EPI_L2E: ensemble heads E
     const float *w3e;        // EPI_L2E: [E][N] head weights
     float *nn_ens;           // EPI_L2E: [M][E][N/32] partial sums per head
+    int n_heads;             // EPI_L2H: heads whose dE/dz2 rows are written (w3 is [n_heads][N])
+    size_t head_stride;      // EPI_L2H: output elements from one head's [M] rows to the next's
     int lo_out;              // BF16 outputs: also write the lo half (the consumer runs split)
     // Structure energies fused into the tcgen05 B1 GEMM (energy non-null; no virial): while
     // the first N tile of each row block runs its main loop, its four idle warps add E_i of

@@ -86,6 +86,19 @@ __global__ void __launch_bounds__(256) k_gemm_f32(const float *__restrict__ A, c
             *reinterpret_cast<float4 *>(o0) = make_float4(a[0], a[1], a[2], a[3]);
             float *o1 = static_cast<float *>(e.out1) + (size_t)m * N + nb;
             *reinterpret_cast<float4 *>(o1) = make_float4(d[0], d[1], d[2], d[3]);
+        } else if (EPI == EPI_L2H) {
+            const float sg = m < e.n_atoms ? e.sigma[min(max(e.species[m], 0), e.n_species - 1)] : 0.0f;
+            float y[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float d;
+                act_fwd<ACT>(acc[i][j] + e.bias[nb + j], d);
+                y[j] = sg * d;
+            }
+            for (int k = 0; k < e.n_heads; ++k) {
+                const float4 w = *reinterpret_cast<const float4 *>(e.w3 + (size_t)k * N + nb);
+                *reinterpret_cast<float4 *>(o0 + k * e.head_stride) = make_float4(y[0] * w.x, y[1] * w.y, y[2] * w.z, y[3] * w.w);
+            }
         } else {  // EPI_L2, EPI_L2E
             const float sg = m < e.n_atoms ? e.sigma[min(max(e.species[m], 0), e.n_species - 1)] : 0.0f;
             float part = 0.0f, dz[4], av[4];
@@ -133,6 +146,7 @@ void gemm_f32(int epi, int act, const float *A, const float *B, int M, int N, in
     case EPI_L1: launch_act<EPI_L1>(act, g, A, B, M, N, K, e, st); break;
     case EPI_L2: launch_act<EPI_L2>(act, g, A, B, M, N, K, e, st); break;
     case EPI_L2E: launch_act<EPI_L2E>(act, g, A, B, M, N, K, e, st); break;
+    case EPI_L2H: launch_act<EPI_L2H>(act, g, A, B, M, N, K, e, st); break;
     case EPI_B1: launch_pdl(k_gemm_f32<EPI_B1, 0>, g, dim3(256), 0, st, A, B, M, N, K, e); break;
     default: launch_pdl(k_gemm_f32<EPI_STORE, 0>, g, dim3(256), 0, st, A, B, M, N, K, e); break;
     }

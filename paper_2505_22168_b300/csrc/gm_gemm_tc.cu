@@ -86,6 +86,9 @@ cudaError_t dispatch_epi(int epi, int act, const CUtensorMap &ma, const CUtensor
     case EPI_L2E:
         return act == 0 ? launch_tc<BN, EPI_L2E, 0, CPS>(ma, mb, M, N, K, split, e, status, st, f16)
                         : launch_tc<BN, EPI_L2E, 1, CPS>(ma, mb, M, N, K, split, e, status, st, f16);
+    case EPI_L2H:
+        return act == 0 ? launch_tc<BN, EPI_L2H, 0, CPS>(ma, mb, M, N, K, split, e, status, st, f16)
+                        : launch_tc<BN, EPI_L2H, 1, CPS>(ma, mb, M, N, K, split, e, status, st, f16);
     case EPI_B1: return launch_tc<BN, EPI_B1, 0, CPS>(ma, mb, M, N, K, split, e, status, st, f16);
     default: return launch_tc<BN, EPI_STORE, 0, CPS>(ma, mb, M, N, K, split, e, status, st, f16);
     }

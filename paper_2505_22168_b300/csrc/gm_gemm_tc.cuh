@@ -251,6 +251,41 @@ template <int EPI, int ACT>
 __device__ __forceinline__ void epilogue32(const EpiArgs &e, int row0, int n, int N, float (&v)[32], float &part,
                                            EpiStage &sg, int lane) {
     const int m = row0 + lane;
+    if (EPI == EPI_L2H) {
+        // y = sigma_Z phi'(Z2 + b2) once, then one [M][2N] block of rows per head
+        const float sg_m = m < e.n_atoms ? e.sigma[min(max(e.species[m], 0), e.n_species - 1)] : 0.0f;
+        float y[32];
+#pragma unroll
+        for (int t = 0; t < 32; ++t) {
+            float d;
+            act_fast<ACT>(v[t] + __ldg(e.bias + n + t), d);
+            y[t] = sg_m * d;
+        }
+        __nv_bfloat16 *ob = static_cast<__nv_bfloat16 *>(e.out0);
+#pragma unroll 1
+        for (int k = 0; k < e.n_heads; ++k, ob += e.head_stride) {
+            const float *wk = e.w3 + (size_t)k * N + n;
+            float yk[32];
+#pragma unroll
+            for (int t = 0; t < 32; ++t) yk[t] = y[t] * __ldg(wk + t);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (e.out_f16) {
+                    sg.hi[lane][q] = pack8_f16(yk + 8 * q);
+                } else {
+                    uint4 hi, lo;
+                    pack8_split(yk + 8 * q, hi, lo);
+                    sg.hi[lane][q] = hi;
+                    sg.lo[lane][q] = lo;
+                }
+            }
+            __syncwarp();
+            warp_store_bf16(sg.hi, ob, row0, 2 * (size_t)N, n, lane);
+            if (e.lo_out && !e.out_f16) warp_store_bf16(sg.lo, ob + N, row0, 2 * (size_t)N, n, lane);
+            __syncwarp();
+        }
+        return;
+    }
     if (EPI == EPI_STORE) {
 #pragma unroll
         for (int q = 0; q < 8; ++q) sg.d[lane][q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
