@@ -181,6 +181,9 @@ GM_API void gm_model_destroy(gm_model *m);
  *                       activations in shared memory): 0 = by size (default), 1 = one CTA per
  *                       tile, 2, 4 or 8 (hidden width / CTAs at least 64); a size the device
  *                       cannot launch falls back to the four GEMM launches
+ *   GM_TUNE_MLP_CTAS    mixed path, one-CTA-per-tile fused network: CTAs of its persistent
+ *                       launch, each taking every CTAs-th tile; 0 = one per SM (default), else
+ *                       1..4096 (at most the number of tiles)
  *   GM_TUNE_PG_SPLIT_MASK  mixed path: the same bits for the four network GEMMs of
  *                       gm_param_grad (forward, forward, backward, backward on the stacked
  *                       primal and tangent rows); default 15 (all split), which keeps every
@@ -215,7 +218,8 @@ GM_API void gm_model_destroy(gm_model *m);
 enum { GM_TUNE_PAIR_TPA = 0, GM_TUNE_SPLIT_MASK = 1, GM_TUNE_GEMM_BN = 2, GM_TUNE_NL_MODE = 3, GM_TUNE_NL_SPLIT = 4,
        GM_TUNE_NL_BLOCKS = 5, GM_TUNE_NL_TWO_PASS = 6, GM_TUNE_NL_ITEMS = 7, GM_TUNE_GEMM_CPS = 8,
        GM_TUNE_PG_SPLIT_MASK = 9, GM_TUNE_DEBUG_STALL = 10, GM_TUNE_F16_BACKWARD = 11,
-       GM_TUNE_FUSED_MLP = 12, GM_TUNE_FORCES_TPA = 13, GM_TUNE_MLP_CLUSTER = 14 };
+       GM_TUNE_FUSED_MLP = 12, GM_TUNE_FORCES_TPA = 13, GM_TUNE_MLP_CLUSTER = 14,
+       GM_TUNE_MLP_CTAS = 15 };
 enum { GM_NL_MODE_AUTO = 0, GM_NL_MODE_PHASES = 1 };
 GM_API gm_status gm_model_set_tuning(gm_model *m, int32_t key, int32_t value);
 

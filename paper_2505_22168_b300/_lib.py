@@ -163,6 +163,7 @@ GM_TUNE_F16_BACKWARD = 11
 GM_TUNE_FUSED_MLP = 12
 GM_TUNE_FORCES_TPA = 13
 GM_TUNE_MLP_CLUSTER = 14
+GM_TUNE_MLP_CTAS = 15
 GM_NL_MODE_AUTO, GM_NL_MODE_PHASES = 0, 1
 
 

@@ -120,6 +120,7 @@ struct gm_model {
     int f16_backward;      // backward GEMMs B1, B0 on FP16 operands in one pass (else split BF16)
     int fused_mlp;         // mixed path: the four network GEMMs as one kernel (where it applies)
     int mlp_cluster;       // CTAs per tile of the fused network kernel (0 by size, 1 one, 2/4/8)
+    int mlp_ctas;          // CTAs of the persistent per-tile kernel (0: one per SM)
     int pg_split_mask;     // the same for the four network GEMMs of the parameter gradient
     int gemm_bn;           // tensor-core tile width (0 = by size)
     int gemm_cps;          // tensor-core GEMM blocks per SM (0 = by tile count)
@@ -540,6 +541,7 @@ gm_status gm_model_create(const gm_model_desc *d, gm_model **out) {
     m->f16_backward = 1;
     m->fused_mlp = 2;
     m->mlp_cluster = 0;
+    m->mlp_ctas = 0;
     m->pg_split_mask = 15;
     m->gemm_bn = 0;
     m->gemm_cps = 0;
@@ -626,6 +628,10 @@ gm_status gm_model_set_tuning(gm_model *m, int32_t key, int32_t value) {
         if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8)
             return fail(GM_ERR_ARG, "network cluster size must be 0, 1, 2, 4 or 8");
         m->mlp_cluster = value;
+        return GM_OK;
+    case GM_TUNE_MLP_CTAS:
+        if (value < 0 || value > 4096) return fail(GM_ERR_ARG, "fused network CTAs must be in 0..4096");
+        m->mlp_ctas = value;
         return GM_OK;
     case GM_TUNE_F16_BACKWARD:
         if (value != 0 && value != 1) return fail(GM_ERR_ARG, "FP16 backward flag must be 0 or 1");
@@ -812,6 +818,7 @@ static gm_status network_fwd_bwd(const gm_model *m, const gm_system *sys, EfWs &
         fa.nn_part = w.nn_part;
         fa.dG = w.dG;
         fa.debug_stall = m->debug_stall == 2 ? 1 : 0;
+        fa.ctas = m->mlp_ctas;
         StageScope sc(ST_MLP_FUSED, st);
         gm_status s;
         if (form == MLP_CLUSTER) {

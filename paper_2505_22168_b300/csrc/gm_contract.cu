@@ -912,7 +912,7 @@ template <int W> constexpr size_t ct_bwd_smem() {
 }
 static_assert(ct_bwd_smem<2 * CT_BWD_W>() <= 227 * 1024, "backward with doubled warps fits in shared memory");
 
-static int sm_count() {
+int device_sm_count() {
     static int cnt[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
@@ -938,7 +938,7 @@ static void launch_fwd_items(const float *psi, int N, int Mp, OutT *G, float *fe
                              cudaStream_t st) {
     const int blocks = (Mp + CT_ATOMS - 1) / CT_ATOMS;
     if (blocks <= 0) return;
-    if (blocks < sm_count())
+    if (blocks < device_sm_count())
         launch_fwd_w<OutT, 2 * CT_FWD_W>(blocks, psi, N, Mp, G, features_out, lo_out, st);
     else
         launch_fwd_w<OutT, CT_FWD_W>(blocks, psi, N, Mp, G, features_out, lo_out, st);
@@ -971,7 +971,7 @@ void launch_contract_bwd(const float *psi, const float *dG, int N, float *dpsi, 
     if (bph <= 0 || heads < 1) return;
     const int blocks = bph * heads;
     const size_t dpsi_hs = (size_t)N * NPSI;
-    if (blocks < sm_count())
+    if (blocks < device_sm_count())
         launch_bwd_w<2 * CT_BWD_W>(blocks, psi, dG, N, dpsi, dg_tiled ? 1 : 0, bph, dg_head_stride, dpsi_hs, st);
     else
         launch_bwd_w<CT_BWD_W>(blocks, psi, dG, N, dpsi, dg_tiled ? 1 : 0, bph, dg_head_stride, dpsi_hs, st);

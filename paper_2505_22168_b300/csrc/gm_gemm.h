@@ -87,6 +87,7 @@ struct FusedMlpArgs {
     __half *D1;               // [M][H] FP16 phi'(z1) (scratch)
     float *nn_part, *dG;
     int debug_stall = 0;      // failure-reporting tests: no operand loads, every wait runs out
+    int ctas = 0;             // per-tile kernel: CTAs of the persistent launch (0: one per SM)
     // cluster kernel only: [M][2H] scratch arrays through which the cluster gathers a1, dZ2
     // and dZ1 (first H columns), and the structure energies summed in the kernel (energy
     // null: not summed)

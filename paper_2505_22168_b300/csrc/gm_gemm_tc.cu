@@ -141,7 +141,7 @@ gm_status gemm_bf16(int epi, int act, const __nv_bfloat16 *A, const __nv_bfloat1
 
 namespace {
 template <int H, int ACT>
-cudaError_t launch_fused(const CUtensorMap *maps, const tc::FusedArgs &f, int32_t *status, cudaStream_t st) {
+cudaError_t launch_fused(const CUtensorMap *maps, const tc::FusedArgs &f, int ctas, int32_t *status, cudaStream_t st) {
     using Sh = tc::FusedShape<H>;
     static PerDeviceOnce attr_set;
     if (attr_set.first()) {
@@ -149,8 +149,10 @@ cudaError_t launch_fused(const CUtensorMap *maps, const tc::FusedArgs &f, int32_
                                                (int)Sh::SMEM);
         if (err != cudaSuccess) return err;
     }
-    launch_pdl(tc::k_mlp_fused<H, ACT>, dim3(f.M / tc::BM), dim3(320), Sh::SMEM, st, maps[0], maps[1], maps[2],
-               maps[3], maps[4], f, status);
+    // persistent: one CTA per SM (or the requested number), tiles dealt round-robin
+    const int tiles = f.M / tc::BM, want = ctas > 0 ? ctas : device_sm_count();
+    launch_pdl(tc::k_mlp_fused<H, ACT>, dim3(tiles < want ? tiles : want), dim3(320), Sh::SMEM, st, maps[0],
+               maps[1], maps[2], maps[3], maps[4], f, status);
     return cudaPeekAtLastError();
 }
 }  // namespace
@@ -300,9 +302,9 @@ gm_status mlp_fused(int act, int M, int H, const __nv_bfloat16 *G, const __nv_bf
     f.debug_stall = a.debug_stall;
     cudaError_t err;
     switch (H) {
-    case 128: err = act == 0 ? launch_fused<128, 0>(maps, f, status, st) : launch_fused<128, 1>(maps, f, status, st); break;
-    case 256: err = act == 0 ? launch_fused<256, 0>(maps, f, status, st) : launch_fused<256, 1>(maps, f, status, st); break;
-    default: err = act == 0 ? launch_fused<512, 0>(maps, f, status, st) : launch_fused<512, 1>(maps, f, status, st); break;
+    case 128: err = act == 0 ? launch_fused<128, 0>(maps, f, a.ctas, status, st) : launch_fused<128, 1>(maps, f, a.ctas, status, st); break;
+    case 256: err = act == 0 ? launch_fused<256, 0>(maps, f, a.ctas, status, st) : launch_fused<256, 1>(maps, f, a.ctas, status, st); break;
+    default: err = act == 0 ? launch_fused<512, 0>(maps, f, a.ctas, status, st) : launch_fused<512, 1>(maps, f, a.ctas, status, st); break;
     }
     note_launches(1);
     return err == cudaSuccess ? GM_OK : GM_ERR_CUDA;

@@ -25,6 +25,9 @@ struct PerDeviceOnce {
     }
 };
 
+// SM count of the current device (cached per device)
+int device_sm_count();
+
 struct Carve {
     char *base;
     size_t off, cap;

@@ -171,12 +171,11 @@ class GMNN:
                    "gemm_cps": L.GM_TUNE_GEMM_CPS, "pg_split_mask": L.GM_TUNE_PG_SPLIT_MASK,
                    "debug_stall": L.GM_TUNE_DEBUG_STALL, "f16_backward": L.GM_TUNE_F16_BACKWARD,
                    "fused_mlp": L.GM_TUNE_FUSED_MLP, "forces_tpa": L.GM_TUNE_FORCES_TPA,
-                   "mlp_cluster": L.GM_TUNE_MLP_CLUSTER}
+                   "mlp_cluster": L.GM_TUNE_MLP_CLUSTER, "mlp_ctas": L.GM_TUNE_MLP_CTAS}
 
     def set_tuning(self, **knobs):
-        """Speed knobs of the library (gm_model_set_tuning): pair_tpa, split_mask, pg_split_mask,
-        gemm_bn, gemm_cps, nl_mode, nl_split, nl_blocks, nl_two_pass, nl_items.  None leaves a
-        knob unchanged."""
+        """Speed knobs of the library (gm_model_set_tuning), by the names of TUNING_KEYS (the
+        GM_TUNE_* keys of include/gm.h in lower case).  None leaves a knob unchanged."""
         for name, val in knobs.items():
             if name not in self.TUNING_KEYS:
                 raise ValueError(f"unknown tuning knob {name!r}")

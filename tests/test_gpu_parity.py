@@ -425,6 +425,35 @@ def test_fused_network_kernel_matches_oracle_and_the_four_gemms(case, act, li_sm
     assert np.sqrt(((outs[0] - outs[1]) ** 2).mean()) <= TOL["mixed"] * rms
 
 
+@pytest.mark.parametrize("case,ctas", [("config2", 1), ("config2", 5), ("li_small", 7), ("emim8", 3)])
+def test_persistent_fused_network_kernel_several_tiles_per_cta(case, ctas, li_small):
+    """The one-CTA-per-tile network kernel is persistent: with fewer CTAs than tiles each CTA
+    runs its tiles one after another (the next tile's G loading while the last epilogue runs,
+    every barrier one phase per tile, the layers' MMAs and epilogue halves overlapping).
+    Forced to 1-7 CTAs (widths 512, 256 and 128; 12-50 tiles): within the mixed tolerance of
+    the oracle, and the same energies bit for bit as one CTA per SM (a tile's arithmetic does
+    not depend on the CTA that runs it), forces up to the order of their atomic sums."""
+    if case == "li_small":
+        b, d, p = li_small
+    elif case == "emim8":
+        b, d, p = synth.config(4)
+        b = subset(b, range(8))
+    else:
+        b, d, p = synth.config(2)
+    _, sysd, nl = _nl_pair(b, d, p)
+    ref = _oracle_ref(case, b, d, p)
+    outs = []
+    for c in (ctas, 0):
+        mm = _model(d, p, "mixed")
+        mm.set_tuning(fused_mlp=1, mlp_cluster=1, mlp_ctas=c)
+        E, F, W = mm.energy_forces(sysd, nl, virial=True)
+        mm.check_status()
+        _check_against(ref, b, E, F, W, TOL["mixed"])
+        outs.append((E.cpu().numpy(), F.cpu().numpy()))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.abs(outs[0][1] - outs[1][1]).max() <= 1e-5 * np.abs(outs[1][1]).max()
+
+
 @pytest.mark.parametrize("bn", [64, 128, 256])
 def test_mixed_gemm_blocks_per_sm_give_identical_results(bn):
     """One or two tensor-core GEMM blocks per SM (a full or a halved operand ring) compute each
