@@ -258,17 +258,29 @@ def algorithmic_work(stage, n_atoms, n_pairs, H):
 STAGE_SOURCES = {
     "nl_coop": ("gm_nlist.cu",), "neighbors": ("gm_nlist.cu",), "moments": ("gm_pair.cu", "gm_common.cuh"),
     "forces": ("gm_pair.cu", "gm_common.cuh"), "contract_fwd": ("gm_contract.cu",),
-    "contract_bwd": ("gm_contract.cu",), "gemm_l1": ("gm_gemm_tc.cuh", "gm_gemm_tc.cu"),
-    "gemm_l2": ("gm_gemm_tc.cuh", "gm_gemm_tc.cu"), "gemm_b1": ("gm_gemm_tc.cuh", "gm_gemm_tc.cu"),
-    "gemm_b0": ("gm_gemm_tc.cuh", "gm_gemm_tc.cu"), "mlp_fused": ("gm_mlp_fused.cuh", "gm_mlp_cluster.cuh", "gm_gemm_tc.cuh"),
+    "contract_bwd": ("gm_contract.cu",), "mlp_fused": ("gm_mlp_fused.cuh", "gm_mlp_cluster.cuh", "gm_gemm_tc.cuh"),
 }
+# the network GEMM stages run the tensor-core kernel (mixed) or the FFMA kernel (FP32)
+STAGE_SOURCES.update({g: ("gm_gemm.h", "gm_gemm_tc.cuh", "gm_gemm_tc.cu", "gm_gemm_simt.cu")
+                      for g in ("gemm_l1", "gemm_l2", "gemm_b1", "gemm_b0")})
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
-# of the stage's kernel on the named workload, with the hash of its sources at that time
-# (the capture commands and figures are under profiles/)
+# of the stage's kernel on the named workload and precision, with the hash of its sources at
+# that time (the capture commands and figures are under profiles/).  "scaled": captured on a
+# smaller crystal of the same density and scaled by its atom (and pair) count.
 TRAFFIC = {
-    ("nl_coop", WORKLOADS[2]): {"bytes_per_launch": 150784, "source_sha16": "705382e9780d2994",
-                                "capture": "profiles/nl_coop_emim1536.md"},
+    ("nl_coop", WORKLOADS[2], "mixed"): {"bytes_per_launch": 150784, "source_sha16": "705382e9780d2994",
+                                         "capture": "profiles/nl_coop_emim1536.md"},
+    ("gemm_l2", WORKLOADS[2], "fp32"): {"bytes_per_launch": 4242432, "source_sha16": "b981e1f8d34c58c9",
+                                        "capture": "profiles/traffic_dominant_kernels.md"},
+    ("nl_coop", WORKLOADS[3], "mixed"): {"bytes_per_launch": 9254144, "source_sha16": "705382e9780d2994",
+                                         "capture": "profiles/traffic_dominant_kernels.md"},
+    ("gemm_b0", WORKLOADS[3], "fp32"): {"bytes_per_launch": 128099840, "source_sha16": "b981e1f8d34c58c9",
+                                        "capture": "profiles/traffic_dominant_kernels.md"},
+    ("forces", WORKLOADS[5], "mixed"): {"bytes_per_launch": 2 * 73158400, "source_sha16": "4e689b987fa8f6c8",
+                                        "capture": "profiles/traffic_dominant_kernels.md (65,536 atoms, scaled x2)"},
+    ("gemm_l2", WORKLOADS[5], "fp32"): {"bytes_per_launch": 2 * 236320768, "source_sha16": "b981e1f8d34c58c9",
+                                        "capture": "profiles/traffic_dominant_kernels.md (65,536 atoms, scaled x2)"},
 }
 
 
@@ -280,11 +292,13 @@ def source_sha16(stage):
     return h.hexdigest()[:16]
 
 
-def traffic_for(stage, workload):
-    t = TRAFFIC.get((stage, workload))
+def traffic_for(stage, workload, precision):
+    """(bytes per launch, capture) of the stage on the workload, or (None, None) when there is no
+    capture or the stage's sources changed since it was taken."""
+    t = TRAFFIC.get((stage, workload, precision))
     if t is None or t["source_sha16"] != source_sha16(stage):
-        return None
-    return t["bytes_per_launch"]
+        return None, None
+    return t["bytes_per_launch"], t["capture"]
 
 
 def measure_alu_peaks():
@@ -342,8 +356,9 @@ def roofline(stages, n_atoms, n_pairs, H, precision, peaks, sustained, workload=
             peak = FP32_ALU_PEAK_TFLOPS
             src = "derived: 148 SMs x 128 FP32 FMA/clk x 2 flop x 2032 MHz"
         out = {"bound": "alu", "unit": "TFLOP/s", "peak_source": src}
+    traffic, capture = traffic_for(top, workload, precision)
     out.update({"kernel": top, "achieved": round(achieved, 3), "peak": round(peak, 2),
-                "frac": round(achieved / peak, 4), "traffic": traffic_for(top, workload),
+                "frac": round(achieved / peak, 4), "traffic": traffic, "traffic_capture": capture,
                 "ms_per_launch": round(per[top], 5), "algorithmic_work_per_launch": work, "work_unit": unit})
     return out, share
 
