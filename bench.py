@@ -284,6 +284,29 @@ TRAFFIC = {
 }
 
 
+def max_over_ranks(x):
+    """The largest x over the ranks of the process group (x itself when there is none): a job of
+    independent replicas takes as long as its slowest one."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _world():
+    return int(os.environ.get("WORLD_SIZE", "1"))
+
+
+def replica_throughput(n_atoms, steps, seconds, world):
+    """Whole-job atom-steps/s of `world` independent replicas of an n_atoms-atom system, each
+    running `steps` steps, the job taking `seconds` (its slowest replica's time)."""
+    return world * n_atoms * steps / seconds
+
+
 def source_sha16(stage):
     import hashlib
     h = hashlib.sha256()
@@ -508,11 +531,9 @@ def run_gpu(args, cfg, precision, steps, warmup, world, rank, measure_e2e, clock
         _lib.gm_profile_forget_graphs()
         del gprof
         ms_stream = sum(ev0[k].elapsed_time(ev1[k]) for k in range(steps))
+    ms = max_over_ranks(ms)
     if world > 1:
         import torch.distributed as dist
-        t = torch.tensor([ms], dtype=torch.float64, device=model.device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     # device memory of the step: torch's peak (inputs, outputs, neighbour list, workspaces, the
     # captured graphs' pools) without the benchmark's own buffers, plus the model's weights
@@ -531,7 +552,7 @@ def run_gpu(args, cfg, precision, steps, warmup, world, rank, measure_e2e, clock
         accuracy = sampled_accuracy(batch, desc, params, out[1].cpu().numpy(), 12)
     res = {"ms_total": ms, "ms_per_step": ms / steps, "n_atoms": n, "n_pairs": n_pairs, "stages": stages,
            "memory": memory, "accuracy": accuracy,
-           "launches": launches, "H": desc["n_hidden"], "value": world * n * steps / (ms / 1e3),
+           "launches": launches, "H": desc["n_hidden"], "value": replica_throughput(n, steps, ms / 1e3, world),
            "launch_mode": "cuda-graph replay" if graphs else "stream launches", "tuning": tuning,
            "ms_per_step_stream_with_stage_events": ms_stream / steps}
 
@@ -571,6 +592,9 @@ def run_gpu(args, cfg, precision, steps, warmup, world, rank, measure_e2e, clock
         host_np = [h.numpy() for h in host_pos]
         done = [torch.cuda.Event() for _ in range(slots)]
         checksum = 0.0
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
         t0 = time.perf_counter()
         for k in range(e2e_steps + slots - 1):
             sl = k % slots
@@ -591,12 +615,12 @@ def run_gpu(args, cfg, precision, steps, warmup, world, rank, measure_e2e, clock
             if slots == 1:
                 done[sl].synchronize()
                 checksum += float(E_np[sl][0]) + float(F_np[sl][0, 0])
-        wall = time.perf_counter() - t0
+        wall = max_over_ranks(time.perf_counter() - t0)
         if model.read_status() != 0:
             raise RuntimeError("device status set during the end-to-end run")
         if not np.isfinite(checksum):
             raise RuntimeError("non-finite energies or forces in the end-to-end run")
-        res["e2e"] = {"value": world * n * e2e_steps / wall, "unit": UNIT,
+        res["e2e"] = {"value": replica_throughput(n, e2e_steps, wall, world), "unit": UNIT,
                       "h2d_bytes_per_step": int(host_pos[0].numel() * 8),
                       "d2h_bytes_per_step": int(E_host[0].numel() * 8 + F_host[0].numel() * 4), "steps": e2e_steps,
                       "steps_in_flight": slots}
@@ -673,10 +697,12 @@ def run_train(args, steps, warmup, precision="fp32"):
                 "param_grad_rel_l2_worst_group": max(rel.values()),
                 "param_grad_worst_group": max(rel, key=rel.get),
                 "reference": "FP64 oracle loss and parameter gradient on the same batch, parameters and labels"}
+    ms = max_over_ranks(ms)
     return {"workload": "emim-train-32 (32 EMIM+BF4- boxes, 7920 atoms, r_cut 5 A, MLP 2x128)",
             "accuracy": accuracy,
             "precision": precision, "step": "neighbours + energy/forces + loss + parameter gradient",
-            "value": batch.n_atoms * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+            "value": replica_throughput(batch.n_atoms, steps, ms / 1e3, _world()), "unit": UNIT,
+            "ms_per_step": ms / steps,
             "steps": steps, "stage_share": {k: round(v[0] / total, 4) for k, v in stages.items() if v[1] > 0}}
 
 
@@ -733,6 +759,7 @@ def run_md(args, n_atoms, precision, n_inner=100, replays=5):
     ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
     steps = n_inner * replays
     builds = int(st.n_builds.item()) - b0
+    ms = max_over_ranks(ms)
     us_atom_step = ms * 1e3 / (steps * n_atoms)
     # accuracy at the final configuration: the forces the integrator used against the oracle's
     import oracle
@@ -749,7 +776,7 @@ def run_md(args, n_atoms, precision, n_inner=100, replays=5):
     return {"workload": f"li3po4-md-{n_atoms} (Li3PO4-like crystal, {n_atoms} atoms, r_cut 5 A, MLP 2x256, "
                         f"NVT 600 K, dt 0.5 fs, NHC 3/2/3, skin 0.5 A)",
             "precision": precision, "step": "whole MD step (thermostat, Verlet, skin test, rebuilds, E/F)",
-            "value": n_atoms * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+            "value": replica_throughput(n_atoms, steps, ms / 1e3, _world()), "unit": UNIT, "ms_per_step": ms / steps,
             "us_per_atom_per_step": us_atom_step, "steps": steps, "n_inner": n_inner,
             "neighbour_builds": builds, "launches_per_step": launches_per_step,
             "launch_mode": "cuda-graph replay of n_inner steps", "accuracy": acc,
@@ -848,7 +875,9 @@ def run_readout_variant(args, kind, precision, steps, warmup, measure_accuracy=T
                              "shallow ensemble: mean energy, its gradient, energy spread)",
             "ensemble-jacobian": f"emim-64pairs-1536-ensemble{ENS_HEADS}-jacobian (the headline box, {ENS_HEADS}-head "
                                  "shallow ensemble: also every head's forces and the force spread)"}[kind]
-    return {"workload": name, "precision": precision, "value": n * 1e3 / ms, "unit": UNIT, "ms_per_step": ms,
+    ms = max_over_ranks(ms)
+    return {"workload": name, "precision": precision, "value": replica_throughput(n, 1, ms / 1e3, _world()),
+            "unit": UNIT, "ms_per_step": ms,
             "steps": steps, "step": "neighbour rebuild + evaluation", "launch_mode": "cuda-graph replay",
             "l2": "256 MiB buffer written between timed steps", "accuracy": accuracy}
 
