@@ -156,13 +156,23 @@ __global__ void __launch_bounds__(256) k_colsum_part(int M, int H, ColSums cs, f
     }
 }
 
+// 32 columns per block: thread group g (threadIdx.y) adds chunks g, g + 8, ... in order, then
+// the eight group sums are added in group order (both compensated): a fixed order.
 __global__ void __launch_bounds__(256) k_colsum_final(int chunks, int H, ColSums cs, const float *__restrict__ part) {
-    const int h = blockIdx.x * blockDim.x + threadIdx.x;
-    if (h >= H) return;
+    __shared__ float sm[8][32];
+    const int h = blockIdx.x * 32 + threadIdx.x;
     KahanSum k;
-#pragma unroll 8
-    for (int r = 0; r < chunks; ++r) k.add(part[((size_t)blockIdx.y * chunks + r) * H + h]);
-    cs.out[blockIdx.y][h] = k.s;
+    if (h < H)
+#pragma unroll 4
+        for (int r = threadIdx.y; r < chunks; r += 8) k.add(part[((size_t)blockIdx.y * chunks + r) * H + h]);
+    sm[threadIdx.y][threadIdx.x] = k.s - k.c;
+    __syncthreads();
+    if (threadIdx.y == 0 && h < H) {
+        KahanSum t;
+#pragma unroll
+        for (int g = 0; g < 8; ++g) t.add(sm[g][threadIdx.x]);
+        cs.out[blockIdx.y][h] = t.s;
+    }
 }
 
 // C_part[z][i][j] = sum_{k in slice z} A[k][i] B[k][j] (A [K][lda], B [K][ldb], row-major):
@@ -226,21 +236,33 @@ __global__ void __launch_bounds__(256) k_wgrad(const float *__restrict__ A, int 
     }
 }
 
-// The K slices in a fixed order, compensated (KahanSum).
-__global__ void __launch_bounds__(256) k_wgrad_reduce(int ksplit, int Mo, int No, int Mstore,
-                                                      const float *__restrict__ part, float *__restrict__ out) {
-    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (size_t)Mstore * No) return;
+// The K slices of 32 consecutive outputs per block: thread group g (threadIdx.y) adds slices
+// g, g + 8, ... in slice order, then the eight group sums are added in group order (both
+// compensated, KahanSum): a fixed order, so the result is the same on every run.
+constexpr int WR_OUT = 32, WR_GRP = 8;
+__global__ void __launch_bounds__(WR_OUT * WR_GRP) k_wgrad_reduce(int ksplit, int Mo, int No, int Mstore,
+                                                                 const float *__restrict__ part,
+                                                                 float *__restrict__ out) {
+    __shared__ float sm[WR_GRP][WR_OUT];
+    const size_t e = (size_t)blockIdx.x * WR_OUT + threadIdx.x, n = (size_t)Mstore * No;
     KahanSum k;
-#pragma unroll 8
-    for (int z = 0; z < ksplit; ++z) k.add(part[(size_t)z * Mo * No + e]);
-    out[e] = k.s;
+    if (e < n)
+#pragma unroll 4
+        for (int z = threadIdx.y; z < ksplit; z += WR_GRP) k.add(__ldg(part + (size_t)z * Mo * No + e));
+    sm[threadIdx.y][threadIdx.x] = k.s - k.c;
+    __syncthreads();
+    if (threadIdx.y == 0 && e < n) {
+        KahanSum t;
+#pragma unroll
+        for (int g = 0; g < WR_GRP; ++g) t.add(sm[g][threadIdx.x]);
+        out[e] = t.s;
+    }
 }
 
 // Per-species sums of the scale/shift gradients and the output-bias sum: block b sums the
 // atoms [b * TAIL_ATOMS, ...) into part[b][q], q = 0 (b3), 1 + z (sigma_z), 1 + S + z (mu_z);
 // k_pg_tail_final adds the blocks in a fixed order (compensated).
-constexpr int TAIL_ATOMS = 2048;
+constexpr int TAIL_ATOMS = 256;
 __global__ void __launch_bounds__(256) k_pg_tail_part(int N, const int32_t *__restrict__ species, int S,
                                                       const float *__restrict__ t_sig, const float *__restrict__ t_c,
                                                       const float *__restrict__ t_cs, float *__restrict__ part) {
@@ -360,7 +382,7 @@ void colsum3(int M, int H, const float *const A[3], float *const out[3], float *
         cs.out[a] = out[a];
     }
     if (chunks > 0) k_colsum_part<<<dim3((H + 31) / 32, chunks, 3), 256, 0, st>>>(M, H, cs, part);
-    k_colsum_final<<<dim3((H + 255) / 256, 3), 256, 0, st>>>(chunks, H, cs, part);
+    k_colsum_final<<<dim3((H + 31) / 32, 3), dim3(32, 8), 0, st>>>(chunks, H, cs, part);
     note_launches(chunks > 0 ? 2 : 1);
 }
 
@@ -384,7 +406,7 @@ void wgrad(const float *A, int lda, const float *B, int ldb, int K, int Mo, int 
     dim3 grid((Mo + WG_T - 1) / WG_T, (No + WG_T - 1) / WG_T, ks);
     k_wgrad<<<grid, 256, 0, st>>>(A, lda, B, ldb, K, Mo, No, kchunk, part);
     const size_t n = (size_t)Mstore * No;
-    k_wgrad_reduce<<<(int)((n + 255) / 256), 256, 0, st>>>(ks, Mo, No, Mstore, part, out);
+    k_wgrad_reduce<<<(int)((n + WR_OUT - 1) / WR_OUT), dim3(WR_OUT, WR_GRP), 0, st>>>(ks, Mo, No, Mstore, part, out);
     note_launches(2);
 }
 
