@@ -329,10 +329,17 @@ __device__ __forceinline__ void epilogue32(const EpiArgs &e, int row0, int n, in
         }
         if (EPI == EPI_L2E) {
             for (int k = 0; k < e.n_ens; ++k) {
-                const float *wk = e.w3e + (size_t)k * N + n;
+                // head k's 32 weights of this chunk: eight 16-byte loads, the same for every lane
+                const float4 *wk = reinterpret_cast<const float4 *>(e.w3e + (size_t)k * N + n);
                 float p = 0.0f;
 #pragma unroll
-                for (int t = 0; t < 32; ++t) p = fmaf(av[t], __ldg(wk + t), p);
+                for (int q = 0; q < 8; ++q) {
+                    const float4 w = __ldg(wk + q);
+                    p = fmaf(av[4 * q], w.x, p);
+                    p = fmaf(av[4 * q + 1], w.y, p);
+                    p = fmaf(av[4 * q + 2], w.z, p);
+                    p = fmaf(av[4 * q + 3], w.w, p);
+                }
                 e.nn_ens[((size_t)m * e.n_ens + k) * (N / 32) + n / 32] = p;
             }
         }
