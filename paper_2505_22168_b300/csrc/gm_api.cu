@@ -802,6 +802,7 @@ static gm_status network_fwd_bwd(const gm_model *m, const gm_system *sys, EfWs &
     e.n_ens = ens ? m->E : 1;
     e.w3e = m->w3e;
     e.nn_ens = w.nn_ens;
+    e.nn_ens_ld = (size_t)Mp;
     e.n_heads = nheads;
     int cs = 1;
     const int form = mlp_form(m, ens, from_l2, head, sys->n_atoms, &cs);
@@ -1007,7 +1008,7 @@ gm_status gm_energy_forces_ensemble(const gm_model *m, const gm_system *sys, con
     {
         StageScope sc(ST_REDUCE, st);
         launch_ens_energy(B, N, E, sys->atom_ptr, sys->species, m->S, m->sigma, m->mu, m->b3e, w.nn_ens, H / 32,
-                          w.ens_acc, energy_heads, energy_std, st);
+                          (size_t)round_up(N, TILE_M), w.ens_acc, energy_heads, energy_std, st);
     }
     if (mode == GM_ENS_JACOBIAN && N > 0) {
         // every head's forces: the backward pass from L2 with that head's weights (the features,

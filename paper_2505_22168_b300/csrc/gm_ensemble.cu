@@ -15,7 +15,7 @@ namespace gm {
 size_t ens_acc_words(int B, int E) { return (size_t)B * (E + 1) + 1; }
 
 // One thread per atom: the E head energies of atom i (from the L2 epilogue's partial sums
-// nn_ens [i][E][nparts], added in order after b3e[k]) go to its structure's fixed-point
+// nn_ens [E][nparts][ld], rows minor, added in order after b3e[k]) go to its structure's fixed-point
 // accumulators (exact integer sums, as for the energy of the mean head).  The last block
 // (ticket) converts the sums to FP64 and writes each structure's head energies, their mean's
 // spread, and resets the accumulators.  Layout per structure: E sums, then a count of
@@ -24,8 +24,8 @@ __global__ void __launch_bounds__(256) k_ens_energy(int B, int N, int E, const i
                                                     const int32_t *__restrict__ species, int S,
                                                     const float *__restrict__ sigma, const float *__restrict__ mu,
                                                     const float *__restrict__ b3e, const float *__restrict__ nn_ens,
-                                                    int nparts, unsigned long long *acc, double *energy_heads,
-                                                    double *energy_std) {
+                                                    int nparts, size_t ld, unsigned long long *acc,
+                                                    double *energy_heads, double *energy_std) {
     __shared__ bool last;
     griddep_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31;
@@ -42,9 +42,9 @@ __global__ void __launch_bounds__(256) k_ens_energy(int B, int N, int E, const i
     for (int k = 0; k < E; ++k) {
         long long v = 0;
         if (i < N) {
-            const float *row = nn_ens + ((size_t)i * E + k) * nparts;
+            const float *col = nn_ens + (size_t)k * nparts * ld + i;
             float nn = b3e[k];
-            for (int t = 0; t < nparts; ++t) nn += row[t];
+            for (int t = 0; t < nparts; ++t) nn += col[(size_t)t * ld];
             v = to_fixed(fmaf(sg, nn, mz), bad);
         }
         // one round per structure present in the warp (atoms of a structure are contiguous)
@@ -122,7 +122,8 @@ __global__ void __launch_bounds__(256) k_ens_force_std(int N, int E, const float
 
 void launch_ens_energy(int B, int N, int E, const int32_t *atom_ptr, const int32_t *species, int S,
                        const float *sigma, const float *mu, const float *b3e, const float *nn_ens, int nparts,
-                       unsigned long long *acc, double *energy_heads, double *energy_std, cudaStream_t st) {
+                       size_t ld, unsigned long long *acc, double *energy_heads, double *energy_std,
+                       cudaStream_t st) {
     if (B <= 0) return;
     if (N <= 0) {
         if (energy_heads) cudaMemsetAsync(energy_heads, 0, sizeof(double) * B * E, st);
@@ -130,7 +131,7 @@ void launch_ens_energy(int B, int N, int E, const int32_t *atom_ptr, const int32
         return;
     }
     launch_pdl(k_ens_energy, dim3((N + 255) / 256), dim3(256), 0, st, B, N, E, atom_ptr, species, S, sigma, mu, b3e,
-               nn_ens, nparts, acc, energy_heads, energy_std);
+               nn_ens, nparts, ld, acc, energy_heads, energy_std);
     note_launches(1);
 }
 

@@ -12,7 +12,8 @@ size_t ens_acc_words(int B, int E);
 // heads ([B]); either output may be null
 void launch_ens_energy(int B, int N, int E, const int32_t *atom_ptr, const int32_t *species, int S,
                        const float *sigma, const float *mu, const float *b3e, const float *nn_ens, int nparts,
-                       unsigned long long *acc, double *energy_heads, double *energy_std, cudaStream_t st);
+                       size_t ld, unsigned long long *acc, double *energy_heads, double *energy_std,
+                       cudaStream_t st);
 // per-atom standard deviation over the heads of the forces Fk [E][N][3]
 void launch_ens_force_std(int N, int E, const float *Fk, float *force_std, cudaStream_t st);
 

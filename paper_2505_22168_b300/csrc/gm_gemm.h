@@ -34,7 +34,8 @@ struct EpiArgs {
     float *nn_part;          // [M][N/32] (L2): partial output-layer sums per 32 columns
     int n_ens;               // EPI_L2E: ensemble heads E
     const float *w3e;        // EPI_L2E: [E][N] head weights
-    float *nn_ens;           // EPI_L2E: [M][E][N/32] partial sums per head
+    float *nn_ens;           // EPI_L2E: [E][N/32][nn_ens_ld] partial sums per head (rows minor)
+    size_t nn_ens_ld;        // EPI_L2E: rows of nn_ens (>= M)
     int n_heads;             // EPI_L2H: heads whose dE/dz2 rows are written (w3 is [n_heads][N])
     size_t head_stride;      // EPI_L2H: output elements from one head's [M] rows to the next's
     int lo_out;              // BF16 outputs: also write the lo half (the consumer runs split)

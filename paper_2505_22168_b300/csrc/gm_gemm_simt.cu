@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(256) k_gemm_f32(const float *__restrict__ A, c
                     for (int j = 0; j < 4; ++j) p = fmaf(av[j], wk[j], p);
 #pragma unroll
                     for (int off = 4; off > 0; off >>= 1) p += __shfl_xor_sync(0xffffffffu, p, off);
-                    if ((tx & 7) == 0) e.nn_ens[((size_t)m * e.n_ens + k) * (N / 32) + (n0 + tx * 4) / 32] = p;
+                    if ((tx & 7) == 0) e.nn_ens[((size_t)k * (N / 32) + (n0 + tx * 4) / 32) * e.nn_ens_ld + m] = p;
                 }
             }
         }

@@ -340,7 +340,7 @@ __device__ __forceinline__ void epilogue32(const EpiArgs &e, int row0, int n, in
                     p = fmaf(av[4 * q + 2], w.z, p);
                     p = fmaf(av[4 * q + 3], w.w, p);
                 }
-                e.nn_ens[((size_t)m * e.n_ens + k) * (N / 32) + n / 32] = p;
+                e.nn_ens[((size_t)k * (N / 32) + n / 32) * e.nn_ens_ld + m] = p;
             }
         }
     }
