@@ -288,14 +288,17 @@ EfWs carve_ef(Carve &c, int B, int N, int H, int E = 1) {
     w.dG = c.take<float>(m1 * NFP);
     w.nn_part = c.take<float>(m1 * (H / 32));
     w.vir_atom = c.take<float>(n1 * 9);
-    w.red_acc = c.take<unsigned long long>(reduce_acc_words(B));
-    w.n_red_acc = (int)reduce_acc_words(B);
+    // the structure sums and, for an ensemble, the head-energy sums right after them: the
+    // position-split kernel clears both
+    const size_t n_acc = reduce_acc_words(B) + (E > 1 ? ens_acc_words(B, E) : 0);
+    w.red_acc = c.take<unsigned long long>(n_acc);
+    w.n_red_acc = (int)n_acc;
     w.nn_ens = w.Fk = w.dZ2h = w.dZ1h = w.dGh = w.dpsih = nullptr;
     w.ens_acc = nullptr;
     if (E > 1) {
         w.nn_ens = c.take<float>(m1 * E * (H / 32));
         w.Fk = c.take<float>((size_t)E * n1 * 3);
-        w.ens_acc = c.take<unsigned long long>(ens_acc_words(B, E));
+        w.ens_acc = w.red_acc ? w.red_acc + reduce_acc_words(B) : nullptr;
         const int hc = ens_head_chunk(E, N);
         w.dZ2h = hc > 1 ? c.take<float>((size_t)hc * m1 * H) : w.dZ2;
         w.dZ1h = hc > 1 ? c.take<float>((size_t)hc * m1 * H) : w.dZ1;
@@ -1000,8 +1003,7 @@ gm_status gm_energy_forces_ensemble(const gm_model *m, const gm_system *sys, con
     EfWs w = carve_ef(c, B, N, H, E);
     if (!c.ok) return fail(GM_ERR_WORKSPACE, "workspace too small");
     cudaStream_t st = stream;
-    if (cudaMemsetAsync(w.ens_acc, 0, sizeof(unsigned long long) * ens_acc_words(B, E), st) != cudaSuccess)
-        return fail(GM_ERR_CUDA, "memset of the ensemble accumulators failed");
+    // (the head-energy accumulators are cleared with the structure sums by the position split)
     // the mean head: energies, forces (gradient of the mean energy) and virials, with every
     // head's partial sums written in the L2 epilogue
     if ((s = energy_forces_pipeline(m, sys, nl, energy, forces, virial, w, true, status, st)) != GM_OK) return s;
