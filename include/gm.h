@@ -170,7 +170,7 @@ GM_API void gm_model_destroy(gm_model *m);
  *                       operands, dE/dz and the weights, are bounded, and FP16's 11-bit
  *                       significand keeps forces within 2e-3), 0 on BF16 with the split mask
  *   GM_TUNE_FUSED_MLP   mixed path: 1 runs the four network GEMMs of gm_energy_forces as one
- *                       tcgen05 kernel per 128-atom tile, the layer activations kept on chip
+ *                       tcgen05 kernel over 128-atom tiles, the layer activations kept on chip
  *                       (widths 128, 256 and 512, with the FP16 backward and no split in the
  *                       forward layers); 0: four GEMM launches; 2 (default): by size -- four
  *                       launches below 16 tiles, then a cluster per tile (GM_TUNE_MLP_CLUSTER,
@@ -178,8 +178,9 @@ GM_API void gm_model_destroy(gm_model *m);
  *                       per tile
  *   GM_TUNE_MLP_CLUSTER mixed path, fused network: CTAs sharing one 128-atom tile along the
  *                       hidden width (a thread-block cluster that all-gathers each layer's
- *                       activations in shared memory): 0 = by size (default), 1 = one CTA per
- *                       tile, 2, 4 or 8 (hidden width / CTAs at least 64); a size the device
+ *                       activations in shared memory): 0 = by size (default), 1 = the per-tile
+ *                       kernel (one CTA runs whole tiles), 2, 4 or 8 (hidden width / CTAs at least
+ *                       64); a size the device
  *                       cannot launch falls back to the four GEMM launches
  *   GM_TUNE_MLP_CTAS    mixed path, one-CTA-per-tile fused network: CTAs of its persistent
  *                       launch, each taking every CTAs-th tile; 0 = one per SM (default), else
