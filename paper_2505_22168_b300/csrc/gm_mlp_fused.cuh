@@ -59,7 +59,7 @@ struct FusedShape {
     static constexpr __host__ __device__ int b0_col(int ch) { return ch * (B0_WIDE ? 256 : 128); }
     static constexpr __host__ __device__ int b0_n(int ch) { return B0_WIDE && ch == 0 ? 256 : 128; }
     static constexpr int X_BYTES = (H > NFP ? H : NFP) * BM * 2;
-    static constexpr int STAGE_BYTES = CHUNK * BK * 2;      // >= the B0 tiles (128 rows)
+    static constexpr int STAGE_BYTES = CHUNK * BK * 2;      // one weight tile (B0's too, asserted below)
     static constexpr int STAGES = (232448 - 2048 - X_BYTES) / STAGE_BYTES < 8
                                       ? (232448 - 2048 - X_BYTES) / STAGE_BYTES : 8;
     static constexpr int TILES = NCH * KBG + 2 * NCH * KBH + B0CH * KBH;   // weight tiles per row tile
