@@ -271,15 +271,15 @@ STAGE_SOURCES.update({g: ("gm_gemm.h", "gm_gemm_tc.cuh", "gm_gemm_tc.cu", "gm_ge
 TRAFFIC = {
     ("nl_coop", WORKLOADS[2], "mixed"): {"bytes_per_launch": 150784, "source_sha16": "705382e9780d2994",
                                          "capture": "profiles/nl_coop_emim1536.md"},
-    ("gemm_l2", WORKLOADS[2], "fp32"): {"bytes_per_launch": 4242432, "source_sha16": "b981e1f8d34c58c9",
+    ("gemm_l2", WORKLOADS[2], "fp32"): {"bytes_per_launch": 4241920, "source_sha16": "e58e72bb40f7f696",
                                         "capture": "profiles/traffic_dominant_kernels.md"},
     ("nl_coop", WORKLOADS[3], "mixed"): {"bytes_per_launch": 9254144, "source_sha16": "705382e9780d2994",
                                          "capture": "profiles/traffic_dominant_kernels.md"},
-    ("gemm_b0", WORKLOADS[3], "fp32"): {"bytes_per_launch": 128099840, "source_sha16": "b981e1f8d34c58c9",
+    ("gemm_b0", WORKLOADS[3], "fp32"): {"bytes_per_launch": 128016896, "source_sha16": "e58e72bb40f7f696",
                                         "capture": "profiles/traffic_dominant_kernels.md"},
     ("forces", WORKLOADS[5], "mixed"): {"bytes_per_launch": 2 * 73158400, "source_sha16": "4e689b987fa8f6c8",
                                         "capture": "profiles/traffic_dominant_kernels.md (65,536 atoms, scaled x2)"},
-    ("gemm_l2", WORKLOADS[5], "fp32"): {"bytes_per_launch": 2 * 236320768, "source_sha16": "b981e1f8d34c58c9",
+    ("gemm_l2", WORKLOADS[5], "fp32"): {"bytes_per_launch": 2 * 236163328, "source_sha16": "e58e72bb40f7f696",
                                         "capture": "profiles/traffic_dominant_kernels.md (65,536 atoms, scaled x2)"},
 }
 
